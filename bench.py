@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Benchmark of the frontier SSSP hot path on one or more B300 GPUs.
+
+Default workload: single-source SSSP on the RMAT scale-20 graph (edge factor
+16, a,b,c,d = .57,.19,.19,.05, symmetrised, deduplicated, no self-loops,
+uint32 weights U[1,255] from seed 1), source = highest-degree vertex,
+bulk-synchronous CUDA-graph loop with push/pull switching.
+
+One step = one gg_sssp call (distance init through convergence) with the
+graph resident in HBM.  value = GTEPS = m_trav / step time, m_trav = sum of
+out-degrees of the reached vertices (each edge of the reached component once).
+
+Multi-GPU (torchrun): single-source SSSP does not shard, so every rank runs
+an independent replica of the same workload ("replicas only"); value = edges
+traversed by all ranks / max-over-ranks time.  No collective touches the data
+path; ranks only meet at the timing barriers.
+
+--impl reference: the CPU oracle (binary-heap Dijkstra) on the same workload,
+a bounded sample on the host cores, printed on the same JSON schema.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SSSP GTEPS & %HBM roofline (1 B300); batched queries/s + p50/p99 vs single-source"
+L2_BYTES = 126 * 2 ** 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="gg", choices=["gg", "reference"])
+    p.add_argument("--workload", default="rmat20")
+    p.add_argument("--policy", default="graph", choices=["graph", "async", "host"])
+    p.add_argument("--direction", default="auto", choices=["auto", "push", "pull"])
+    p.add_argument("--alpha", type=int, default=0)
+    p.add_argument("--beta", type=int, default=0)
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(n, m_trav, n_reach):
+    """Per SSSP: 12 B per traversed edge (col 4 + weight 4 + dist[dst] 4),
+    20 B per reached vertex (2 row offsets 8 + dist[u] 4 + frontier write 4 +
+    frontier read 4), 4 B per vertex for the distance write."""
+    return 12 * m_trav + 20 * n_reach + 4 * n, 12 * m_trav + 20 * n_reach
+
+
+def cpu_baseline(ro, col, w, src, seconds):
+    import oracle
+    times = []
+    t_end = time.perf_counter() + seconds
+    d = None
+    while time.perf_counter() < t_end or not times:
+        t0 = time.perf_counter()
+        d = oracle.dijkstra(ro, col, w, src)
+        times.append(time.perf_counter() - t0)
+        if len(times) >= 50:
+            break
+    m_trav = oracle.traversed_edges(ro, d)
+    t = statistics.median(times)
+    return {"value": m_trav / t / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} full single-source binary-heap Dijkstra runs on the same graph and source "
+                      f"(median {t * 1e3:.1f} ms each, 1 host thread)"}
+
+
+def workload_desc(name):
+    import graphgen
+    return graphgen.WORKLOADS.get(name, name)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import graphgen
+    import oracle
+    ro, col, w, src = graphgen.workload(args.workload)
+    steps = []
+    for _ in range(args.warmup):
+        oracle.dijkstra(ro, col, w, src)
+    budget = max(args.cpu_seconds, 1.0)
+    t_end = time.perf_counter() + budget
+    d = None
+    k = 0
+    while k < args.steps and (time.perf_counter() < t_end or k == 0):
+        t0 = time.perf_counter()
+        d = oracle.dijkstra(ro, col, w, src)
+        steps.append(time.perf_counter() - t0)
+        k += 1
+    m_trav = oracle.traversed_edges(ro, d)
+    t = statistics.median(steps)
+    val = m_trav / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GTEPS", "n_gpus": 0,
+            "steps": len(steps), "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": workload_desc(args.workload), "n": int(ro.shape[0] - 1), "m": int(col.shape[0]),
+                       "source": int(src), "m_trav": m_trav},
+            "cpu_baseline": {"value": val, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(steps)} of {args.steps} requested steps, each a full single-source "
+                                       f"binary-heap Dijkstra on the host (bounded to ~{budget:.0f} s)"},
+            "e2e": {"value": val, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    import graphgen
+    import paper_2212_08200_b300 as gg
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+    gg.load()
+    ro, col, w, src = graphgen.workload(args.workload)
+    n, m = int(ro.shape[0] - 1), int(col.shape[0])
+    policy = {"graph": gg.GG_POLICY_BSP_GRAPH, "async": gg.GG_POLICY_ASYNC_PERSISTENT,
+              "host": gg.GG_POLICY_BSP_HOST}[args.policy]
+    direction = {"auto": gg.GG_DIR_AUTO, "push": gg.GG_DIR_PUSH, "pull": gg.GG_DIR_PULL}[args.direction]
+    stream = torch.cuda.current_stream()
+    g = gg.Graph(ro, col, w, symmetric=True, stream=stream)
+    dist_t = torch.empty(n, dtype=torch.uint32, device="cuda")
+    opts = gg.make_options(policy=policy, direction=direction, pull_alpha=args.alpha, pull_beta=args.beta)
+
+    def step():
+        gg.gg_sssp_ex(g.handle, src, dist_t, opts, stream)
+
+    # correctness of what is timed: stats run + invariant-free hash check vs the oracle's stored hash
+    st = gg.gg_stats()
+    gg.gg_sssp_ex(g.handle, src, dist_t, gg.make_options(policy=policy, direction=direction, pull_alpha=args.alpha,
+                                                         pull_beta=args.beta, stats=st), stream)
+    d_host = dist_t.cpu().numpy()
+    reach = d_host != gg.GG_INF
+    m_trav = int(np.diff(ro.astype(np.int64))[reach].sum())
+    n_reach = int(reach.sum())
+    stats = st.as_dict()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    # fixed per-call cost: init kernels + graph launch + one single-vertex superstep
+    fixed_opts = gg.make_options(policy=policy, direction=gg.GG_DIR_PUSH, max_iterations=1)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    fixed = []
+    for _ in range(5):
+        ev[0].record(stream)
+        gg.gg_sssp_ex(g.handle, src, dist_t, fixed_opts, stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        fixed.append(ev[0].elapsed_time(ev[1]))
+    t_fixed_ms = statistics.median(fixed)
+    step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    if pg:
+        pg.barrier()
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    total_ms = e0.elapsed_time(e1)
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = total_ms / args.steps
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * m_trav / (ms * 1e-3) / 1e9
+
+    hbm, peak_kind = peaks()
+    b_all, b_super = algorithmic_bytes(n, m_trav, n_reach)
+    super_ms = max(statistics.median(per) - t_fixed_ms, 1e-6)
+    achieved = b_super / (super_ms * 1e-3) / 1e9
+    iters = stats["iterations"]
+    launches_per_step = 2 + (iters if policy != gg.GG_POLICY_ASYNC_PERSISTENT else 1)
+    if policy == gg.GG_POLICY_ASYNC_PERSISTENT:
+        launches_per_step = 3   # init, seed, persistent kernel (plus one memset node)
+
+    # end to end through the public API with host buffers: upload the CSR from
+    # pinned memory, run, read the distances back, free the handle
+    e2e = None
+    if not args.no_e2e:
+        pin = [torch.from_numpy(a.view(np.int32)).pin_memory() for a in (ro, col, w)]
+        arrs = [p.numpy().view(np.uint32) for p in pin]
+        out_h = torch.empty(n, dtype=torch.int32).pin_memory()
+        k2 = max(3, min(args.steps, 10))
+        for it in range(k2 + 1):
+            if it == 1:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            h = gg.gg_graph_create_csr(arrs[0], arrs[1], arrs[2], symmetric=True, stream=stream)
+            gg.gg_sssp(h, src, dist_t, stream)
+            out_h.copy_(dist_t.view(torch.int32), non_blocking=True)
+            torch.cuda.synchronize()
+            gg.gg_graph_destroy(h)
+        e2e_s = (time.perf_counter() - t0) / k2
+        e2e = {"value": world * m_trav / e2e_s / 1e9, "unit": "GTEPS",
+               "h2d_bytes_per_step": 4 * (n + 1) + 8 * m, "d2h_bytes_per_step": 4 * n,
+               "ms_per_step": e2e_s * 1e3,
+               "what": "gg_graph_create_csr from pinned host CSR + gg_sssp + distances copied to pinned host "
+                       "+ gg_graph_destroy, wall clock"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(ro, col, w, src, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": workload_desc(args.workload), "n": n, "m": m, "source": int(src),
+                       "m_trav": m_trav, "n_reach": n_reach, "policy": args.policy, "direction": args.direction,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": f"inputs larger than L2 (edge array {8 * m / 2**20:.0f} MiB > 126 MiB L2); "
+                             f"dist re-initialised every step",
+                       "supersteps": iters, "pull_supersteps": stats["pull_iterations"],
+                       "edges_scanned": stats["edges_scanned"], "step_ms_min": min(per), "step_ms_max": max(per)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "k_superstep (all supersteps of one SSSP)",
+                         "algorithmic_bytes": b_super, "kernel_ms": super_ms, "fixed_ms": t_fixed_ms,
+                         "whole_step_frac": b_all / (ms * 1e-3) / 1e9 / hbm},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "gpu": torch.cuda.get_device_name(),
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

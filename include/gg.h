@@ -1,0 +1,194 @@
+/*
+ * gg.h -- C ABI of the B300 frontier single-source-shortest-path library.
+ *
+ * The library implements the native-graph decomposition of "Essentials of
+ * Parallel Graph Analytics" (Osama, Porumbescu, Owens, 2022):
+ *
+ *   graph      a CSR graph (Sec. IV-A, Listing 1) -- row offsets, column
+ *              indices and uint32 edge weights -- plus its transpose (CSC)
+ *              for pull traversals (Sec. III-C, "Push vs. Pull" box);
+ *   frontier   the active vertex set, held both as a sparse vertex queue
+ *              and as a dense bitmap (Sec. III-B, Sec. IV-B, Listing 2);
+ *   operator   neighbors_expand, the advance that relaxes every out-edge of
+ *              the frontier with an atomic minimum, fused with a filter that
+ *              deduplicates and compacts the improved vertices into the next
+ *              frontier (Sec. IV-C, Listing 3);
+ *   loop       repeat while the frontier is non-empty (the convergence
+ *              condition of Listing 4), either bulk-synchronously (the
+ *              execution::par policy) or asynchronously over a work queue
+ *              (the execution::par_nosync policy, Sec. III-A and the
+ *              "Timing Model and Parallelism" box).
+ *
+ * Numeric contract (the paper's Listing 4 with uint32 in place of float):
+ *   dist[v] = min over directed paths source ~> v of the sum of the uint32
+ *   edge weights; dist[source] = 0; GG_INF (0xFFFFFFFF) marks an unreachable
+ *   vertex.  Results are exact integers, identical for every policy,
+ *   direction and load-balance mode.  Weights may be zero; self-loops and
+ *   multi-edges are allowed (the lightest parallel edge wins).  A finite
+ *   distance of 2^32 - 1 or more cannot be represented: the run then reports
+ *   GG_ERR_OVERFLOW from gg_graph_check (the stored value saturates at
+ *   0xFFFFFFFE).
+ *
+ * Conventions:
+ *   - Every call returns a gg_status; no C++ exception crosses the ABI.
+ *     gg_last_error() gives a thread-local message for the last failure.
+ *   - Device work is stream-ordered on the cudaStream_t passed in (0 = the
+ *     legacy default stream).  Results are valid once that stream reaches
+ *     the point after the call.  Device-side failures (overflow, iteration
+ *     cap, watchdog timeout) are recorded in the graph handle and returned
+ *     by gg_graph_check(), which synchronises the stream.
+ *   - Pointers documented as "device" must be device (or managed) memory of
+ *     the current CUDA device; "host" pointers are ordinary host memory.
+ *   - One graph handle runs one SSSP at a time.  Calls on the same handle
+ *     from different streams are ordered by the library (each call waits for
+ *     the previous one on that handle).
+ */
+#ifndef GG_H
+#define GG_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GG_INF 0xFFFFFFFFu
+#define GG_ABI_VERSION 1
+
+typedef struct gg_graph* gg_graph_t;
+
+typedef enum {
+    GG_OK = 0,
+    GG_ERR_INVALID_ARG = 1,   /* bad pointer, size, index or CSR structure        */
+    GG_ERR_OUT_OF_MEMORY = 2, /* a device or host allocation failed               */
+    GG_ERR_CUDA = 3,          /* a CUDA runtime call failed (see gg_last_error)   */
+    GG_ERR_TIMEOUT = 4,       /* a bounded device wait gave up (watchdog)         */
+    GG_ERR_BUSY = 5,          /* resource in use / admission refused              */
+    GG_ERR_NOT_READY = 6,     /* asynchronous result not available yet            */
+    GG_ERR_OVERFLOW = 7,      /* a finite distance did not fit below GG_INF       */
+    GG_ERR_INTERNAL = 8,      /* iteration cap exceeded or internal invariant     */
+    GG_ERR_NOT_SUPPORTED = 9  /* option combination not available                 */
+} gg_status;
+
+/* gg_graph_create_csr flags */
+#define GG_DEVICE_PTRS 0x1u   /* row_offsets/col_indices/weights are device pointers */
+#define GG_SYMMETRIC   0x2u   /* caller asserts the graph is symmetric: the CSR is
+                                 its own transpose, so pull reuses it (no CSC built) */
+#define GG_NO_VALIDATE 0x4u   /* skip the structural checks (offsets, col < n)     */
+
+/* Execution policy: the paper's execution::par / execution::par_nosync
+ * (Sec. III-A; Listing 3 and the "Timing Model and Parallelism" box). */
+typedef enum {
+    GG_POLICY_BSP_GRAPH = 0,        /* bulk-synchronous supersteps in a CUDA graph whose
+                                       conditional WHILE node tests frontier size != 0 */
+    GG_POLICY_ASYNC_PERSISTENT = 1, /* one persistent kernel over a device work queue,
+                                       no barriers, device-side termination detection */
+    GG_POLICY_BSP_HOST = 2          /* the same supersteps launched one by one from the
+                                       host (for comparison and per-kernel timing)   */
+} gg_policy;
+
+/* Traversal direction (Sec. III-C): push over CSR, pull over CSC. */
+typedef enum { GG_DIR_AUTO = 0, GG_DIR_PUSH = 1, GG_DIR_PULL = 2 } gg_direction;
+
+/* Load balancing of the push advance (Sec. IV-C: "data parallelism and load
+ * balancing"). */
+typedef enum {
+    GG_LB_AUTO = 0,        /* library choice (merge-path)                                */
+    GG_LB_MERGE_PATH = 1,  /* equal edge ranges per CTA over the frontier's degree scan  */
+    GG_LB_BINS = 2         /* thread / warp / CTA per vertex by degree thresholds        */
+} gg_lb_mode;
+
+typedef struct {
+    uint32_t iterations;       /* supersteps run (BSP) or 0 (async)                   */
+    uint32_t pull_iterations;  /* of which pull                                        */
+    uint64_t edges_scanned;    /* edges relaxed, summed over supersteps / queue pops    */
+    uint64_t frontier_total;   /* sum of frontier sizes (vertex activations)          */
+    uint32_t max_frontier;     /* largest frontier                                     */
+    uint32_t device_status;    /* gg_status recorded on the device                     */
+} gg_stats;
+
+typedef struct {
+    uint32_t struct_size;      /* sizeof(gg_options); set by gg_options_default        */
+    gg_policy policy;
+    gg_direction direction;
+    gg_lb_mode lb_mode;
+    uint32_t warp_threshold;   /* LB_BINS: degree >= this -> warp per vertex (0 = auto)  */
+    uint32_t cta_threshold;    /* LB_BINS: degree >= this -> CTA per vertex (0 = auto)   */
+    uint32_t pull_alpha;       /* AUTO direction: go pull when frontier edges > m/alpha
+                                  (0 = auto)                                            */
+    uint32_t pull_beta;        /* AUTO direction: back to push when frontier vertices <
+                                  n/beta (0 = auto)                                     */
+    uint32_t max_iterations;   /* BSP superstep cap (0 = n + 2)                          */
+    uint64_t watchdog_ns;      /* ASYNC: give up and report GG_ERR_TIMEOUT after this
+                                  long without the queue draining (0 = 10 s)           */
+    gg_stats* stats;           /* host; if not NULL the call synchronises the stream
+                                  and fills it                                          */
+    uint32_t* trace;           /* device u32[trace_cap*4] or NULL: per superstep
+                                  (frontier size, frontier edges, direction, 0)        */
+    uint32_t trace_cap;
+} gg_options;
+
+/* ---- graph (Sec. IV-A, Listing 1) ------------------------------------- */
+
+/* Builds a graph handle from a CSR.
+ *   n            vertices, 1 <= n < 2^32 - 1
+ *   m            directed edges, m < 2^32 (offsets are uint32)
+ *   row_offsets  u32[n+1], row_offsets[0] = 0, non-decreasing, row_offsets[n] = m
+ *   col_indices  u32[m], each < n
+ *   weights      u32[m]
+ *   flags        GG_DEVICE_PTRS | GG_SYMMETRIC | GG_NO_VALIDATE
+ *   stream       stream for the upload and preprocessing; the call returns after
+ *                they are complete (it synchronises the stream)
+ *   out          receives the handle
+ * The handle owns a device copy (edges re-encoded as interleaved {col, weight}
+ * pairs, plus the transpose unless GG_SYMMETRIC); the caller's arrays may be
+ * freed after the call.  Errors: GG_ERR_INVALID_ARG for a null pointer, n or m
+ * out of range, or (unless GG_NO_VALIDATE) a CSR whose offsets are not
+ * monotone from 0 to m or whose column index is >= n; GG_ERR_OUT_OF_MEMORY;
+ * GG_ERR_CUDA.  On error *out is set to NULL. */
+gg_status gg_graph_create_csr(uint32_t n, uint64_t m, const uint32_t* row_offsets,
+                              const uint32_t* col_indices, const uint32_t* weights,
+                              uint32_t flags, cudaStream_t stream, gg_graph_t* out);
+
+/* Frees the handle and its device memory (synchronises its last stream). */
+gg_status gg_graph_destroy(gg_graph_t g);
+
+/* n, m and the device bytes held by the handle. */
+gg_status gg_graph_info(gg_graph_t g, uint32_t* n, uint64_t* m, uint64_t* device_bytes);
+
+/* Synchronises the stream of the handle's last call and returns the device
+ * status of that call: GG_OK, GG_ERR_OVERFLOW, GG_ERR_INTERNAL (superstep cap)
+ * or GG_ERR_TIMEOUT (async watchdog).  Clears the recorded status. */
+gg_status gg_graph_check(gg_graph_t g);
+
+/* ---- SSSP (Sec. IV-D, Listing 4) ---------------------------------------- */
+
+/* Fills opt with the defaults (BSP graph policy, auto direction, auto LB). */
+void gg_options_default(gg_options* opt);
+
+/* Single-source shortest paths from src.
+ *   dist_out  device u32[n], caller-owned; receives the distances.
+ * Asynchronous on `stream`.  The first call on a handle allocates its
+ * workspace (frontier queues, bitmaps: about 12n + 3n/8 bytes) and builds the
+ * CUDA graph.  Errors: GG_ERR_INVALID_ARG (null handle or dist_out, src >= n),
+ * GG_ERR_OUT_OF_MEMORY, GG_ERR_CUDA. */
+gg_status gg_sssp(gg_graph_t g, uint32_t src, uint32_t* dist_out, cudaStream_t stream);
+
+/* As gg_sssp with explicit options (opt may be NULL for the defaults). */
+gg_status gg_sssp_ex(gg_graph_t g, uint32_t src, uint32_t* dist_out, const gg_options* opt,
+                     cudaStream_t stream);
+
+/* ---- errors ------------------------------------------------------------- */
+
+const char* gg_status_string(gg_status s);
+/* Thread-local message describing the last failed call on this thread. */
+const char* gg_last_error(void);
+/* GG_ABI_VERSION of the loaded library. */
+uint32_t gg_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GG_H */

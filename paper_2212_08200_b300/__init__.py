@@ -1,0 +1,248 @@
+"""Python binding of the B300 frontier SSSP library (libgg.so, include/gg.h).
+
+Argument marshalling only: every step of an SSSP run executes in the CUDA
+kernels of libgg.so.  PyTorch supplies device memory and streams.  There is
+no CPU fallback: importing a function that needs the library raises
+``ImportError`` when libgg.so is missing, and every failing C call raises
+``GGError`` carrying the library's status and message.
+
+The functions keep the C names (``gg_graph_create_csr``, ``gg_sssp``, ...);
+``Graph`` wraps a handle with a destructor.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+__all__ = [
+    "GGError", "GG_INF", "GG_DEVICE_PTRS", "GG_SYMMETRIC", "GG_NO_VALIDATE",
+    "GG_POLICY_BSP_GRAPH", "GG_POLICY_ASYNC_PERSISTENT", "GG_POLICY_BSP_HOST",
+    "GG_DIR_AUTO", "GG_DIR_PUSH", "GG_DIR_PULL", "GG_LB_AUTO", "GG_LB_MERGE_PATH", "GG_LB_BINS",
+    "gg_graph_create_csr", "gg_graph_destroy", "gg_graph_info", "gg_graph_check", "gg_sssp", "gg_sssp_ex",
+    "gg_status_string", "gg_last_error", "gg_abi_version", "Graph", "lib_path", "load",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(HERE, "libgg.so")
+_lib = None
+_lock = threading.Lock()
+
+GG_INF = 0xFFFFFFFF
+GG_DEVICE_PTRS, GG_SYMMETRIC, GG_NO_VALIDATE = 0x1, 0x2, 0x4
+GG_POLICY_BSP_GRAPH, GG_POLICY_ASYNC_PERSISTENT, GG_POLICY_BSP_HOST = 0, 1, 2
+GG_DIR_AUTO, GG_DIR_PUSH, GG_DIR_PULL = 0, 1, 2
+GG_LB_AUTO, GG_LB_MERGE_PATH, GG_LB_BINS = 0, 1, 2
+
+STATUS = {0: "GG_OK", 1: "GG_ERR_INVALID_ARG", 2: "GG_ERR_OUT_OF_MEMORY", 3: "GG_ERR_CUDA",
+          4: "GG_ERR_TIMEOUT", 5: "GG_ERR_BUSY", 6: "GG_ERR_NOT_READY", 7: "GG_ERR_OVERFLOW",
+          8: "GG_ERR_INTERNAL", 9: "GG_ERR_NOT_SUPPORTED"}
+
+
+class GGError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        self.status_name = STATUS.get(status, str(status))
+        super().__init__(f"{where}: {self.status_name}: {msg}")
+
+
+class gg_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_uint32), ("pull_iterations", ctypes.c_uint32),
+                ("edges_scanned", ctypes.c_uint64), ("frontier_total", ctypes.c_uint64),
+                ("max_frontier", ctypes.c_uint32), ("device_status", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+class gg_options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("policy", ctypes.c_int), ("direction", ctypes.c_int),
+                ("lb_mode", ctypes.c_int), ("warp_threshold", ctypes.c_uint32), ("cta_threshold", ctypes.c_uint32),
+                ("pull_alpha", ctypes.c_uint32), ("pull_beta", ctypes.c_uint32),
+                ("max_iterations", ctypes.c_uint32), ("watchdog_ns", ctypes.c_uint64),
+                ("stats", ctypes.POINTER(gg_stats)), ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_uint32)]
+
+
+def lib_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Loads libgg.so (built by paper_2212_08200_b300.build).  Raises
+    ImportError when it is missing: there is no fallback path."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise ImportError(f"libgg.so not built at {_LIB_PATH}; run python -m paper_2212_08200_b300.build")
+        lib = ctypes.CDLL(_LIB_PATH)
+        vp, u32, u64 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64
+        P32 = ctypes.POINTER(ctypes.c_uint32)
+        sig = {
+            "gg_graph_create_csr": (ctypes.c_int, [u32, u64, vp, vp, vp, u32, vp, ctypes.POINTER(vp)]),
+            "gg_graph_destroy": (ctypes.c_int, [vp]),
+            "gg_graph_info": (ctypes.c_int, [vp, P32, ctypes.POINTER(u64), ctypes.POINTER(u64)]),
+            "gg_graph_check": (ctypes.c_int, [vp]),
+            "gg_options_default": (None, [ctypes.POINTER(gg_options)]),
+            "gg_sssp": (ctypes.c_int, [vp, u32, vp, vp]),
+            "gg_sssp_ex": (ctypes.c_int, [vp, u32, vp, ctypes.POINTER(gg_options), vp]),
+            "gg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+            "gg_last_error": (ctypes.c_char_p, []),
+            "gg_abi_version": (u32, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        raise GGError(rc, where, load().gg_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(a):
+    """(address, is_device) of a numpy array or torch tensor of uint32/int32."""
+    if isinstance(a, np.ndarray):
+        if a.dtype not in (np.uint32, np.int32) or not a.flags.c_contiguous:
+            raise TypeError("numpy arrays must be contiguous uint32")
+        return a.ctypes.data, False
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.dtype not in (torch.uint32, torch.int32) or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous uint32/int32")
+        return a.data_ptr(), a.is_cuda
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def gg_status_string(s: int) -> str:
+    return load().gg_status_string(s).decode()
+
+
+def gg_last_error() -> str:
+    return load().gg_last_error().decode(errors="replace")
+
+
+def gg_abi_version() -> int:
+    return int(load().gg_abi_version())
+
+
+def gg_graph_create_csr(row_offsets, col_indices, weights, symmetric: bool = False, validate: bool = True,
+                        stream=None) -> int:
+    """Handle (int) for a CSR given as numpy arrays (host) or CUDA tensors
+    (device).  All three must live on the same side."""
+    lib = load()
+    ro, ro_dev = _ptr(row_offsets)
+    col, col_dev = _ptr(col_indices)
+    w, w_dev = _ptr(weights)
+    if len({ro_dev, col_dev, w_dev}) != 1:
+        raise ValueError("row_offsets, col_indices and weights must all be host or all be device")
+    n = int(row_offsets.shape[0]) - 1
+    m = int(col_indices.shape[0])
+    if int(weights.shape[0]) != m:
+        raise ValueError("weights and col_indices differ in length")
+    flags = (GG_DEVICE_PTRS if ro_dev else 0) | (GG_SYMMETRIC if symmetric else 0) | (0 if validate else GG_NO_VALIDATE)
+    h = ctypes.c_void_p()
+    _check(lib.gg_graph_create_csr(n, m, ro, col if m else None, w if m else None, flags,
+                                   _stream_ptr(stream) if (stream is not None or ro_dev) else 0,
+                                   ctypes.byref(h)), "gg_graph_create_csr")
+    return h.value
+
+
+def gg_graph_destroy(handle: int):
+    _check(load().gg_graph_destroy(handle), "gg_graph_destroy")
+
+
+def gg_graph_info(handle: int):
+    n = ctypes.c_uint32()
+    m = ctypes.c_uint64()
+    b = ctypes.c_uint64()
+    _check(load().gg_graph_info(handle, ctypes.byref(n), ctypes.byref(m), ctypes.byref(b)), "gg_graph_info")
+    return int(n.value), int(m.value), int(b.value)
+
+
+def gg_graph_check(handle: int):
+    _check(load().gg_graph_check(handle), "gg_graph_check")
+
+
+def make_options(policy=GG_POLICY_BSP_GRAPH, direction=GG_DIR_AUTO, lb_mode=GG_LB_AUTO, warp_threshold=0,
+                 cta_threshold=0, pull_alpha=0, pull_beta=0, max_iterations=0, watchdog_ns=0, stats=None,
+                 trace=None, trace_cap=0) -> gg_options:
+    o = gg_options()
+    load().gg_options_default(ctypes.byref(o))
+    o.policy, o.direction, o.lb_mode = policy, direction, lb_mode
+    o.warp_threshold, o.cta_threshold = warp_threshold, cta_threshold
+    o.pull_alpha, o.pull_beta, o.max_iterations, o.watchdog_ns = pull_alpha, pull_beta, max_iterations, watchdog_ns
+    if stats is not None:
+        o.stats = ctypes.pointer(stats)
+    if trace is not None:
+        o.trace = _ptr(trace)[0]
+        o.trace_cap = trace_cap or int(trace.numel()) // 4
+    return o
+
+
+def gg_sssp(handle: int, src: int, dist_out, stream=None):
+    """Distances from src into dist_out (CUDA uint32 tensor of n), async."""
+    p, dev = _ptr(dist_out)
+    if not dev:
+        raise ValueError("dist_out must be a CUDA tensor")
+    _check(load().gg_sssp(handle, src, p, _stream_ptr(stream)), "gg_sssp")
+
+
+def gg_sssp_ex(handle: int, src: int, dist_out, options: gg_options | None = None, stream=None):
+    p, dev = _ptr(dist_out)
+    if not dev:
+        raise ValueError("dist_out must be a CUDA tensor")
+    _check(load().gg_sssp_ex(handle, src, p, ctypes.byref(options) if options is not None else None,
+                             _stream_ptr(stream)), "gg_sssp_ex")
+
+
+class Graph:
+    """Owning wrapper of a gg_graph_t."""
+
+    def __init__(self, row_offsets, col_indices, weights, symmetric: bool = False, validate: bool = True,
+                 stream=None):
+        self.handle = gg_graph_create_csr(row_offsets, col_indices, weights, symmetric, validate, stream)
+        self.n, self.m, _ = gg_graph_info(self.handle)
+
+    def sssp(self, src: int, dist_out=None, stream=None, **opts):
+        import torch
+        if dist_out is None:
+            dist_out = torch.empty(self.n, dtype=torch.uint32, device="cuda")
+        if opts:
+            gg_sssp_ex(self.handle, src, dist_out, make_options(**opts), stream)
+        else:
+            gg_sssp(self.handle, src, dist_out, stream)
+        return dist_out
+
+    def check(self):
+        gg_graph_check(self.handle)
+
+    @property
+    def device_bytes(self) -> int:
+        return gg_graph_info(self.handle)[2]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            gg_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

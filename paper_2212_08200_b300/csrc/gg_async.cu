@@ -1,0 +1,333 @@
+// gg_async.cu -- asynchronous frontier SSSP (the execution::par_nosync policy).
+//
+// The paper's asynchronous variant of neighbors_expand drops the barrier
+// between expansions (Listing 3's par_nosync overload and the "Timing Model
+// and Parallelism" box) and represents the frontier as an asynchronous queue
+// that passes active vertices as messages (Sec. III-B and the "Asynchrony and
+// Message-Passing" box).  Here that is ONE persistent kernel:
+//
+//   queue    a ring of 64-bit slots {tag, vertex} with per-slot sequence tags
+//            (a bounded multi-producer multi-consumer ring): the producer of
+//            position p waits for tag 2*lap, writes {2*lap+1, v}; the
+//            consumer waits for 2*lap+1, takes v and writes 2*lap+2.
+//   dedup    an in-queue bitmap: a vertex is enqueued only if its bit was
+//            clear; the consumer clears it before reading dist[v], so any
+//            later improvement re-enqueues it.  At most n vertices are queued
+//            at once, so a ring of >= 2n slots never needs the producer wait
+//            in practice.
+//   work     each warp reserves 32 consecutive positions, takes whichever
+//            arrive, and expands the taken vertices' edges together
+//            (warp-level merge-path over their degree prefix sums).
+//   stop     `pending` counts queued-or-running items: incremented before an
+//            item is published, decremented after it has been fully
+//            expanded.  pending == 0 can never become non-zero again, so a
+//            warp seeing it exits.
+//   watchdog every wait is bounded by a %globaltimer budget; when it runs
+//            out the kernel raises `abort`, records GG_ERR_TIMEOUT and every
+//            warp returns.  Nothing spins without a limit.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "gg_host.h"
+
+namespace gg {
+
+struct AsyncCtl {
+  unsigned long long head;
+  unsigned long long tail;
+  unsigned long long pending;
+  unsigned long long pops;
+  unsigned long long edges;
+  unsigned long long watchdog_ns;
+  unsigned long long t_start;
+  uint32_t status;
+  uint32_t abort;
+  uint32_t* dist;
+};
+
+namespace {
+
+constexpr int kABlock = 256;
+constexpr int kAWarps = kABlock / 32;
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) { return *(volatile const uint32_t*)p; }
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
+  return *(volatile const unsigned long long*)p;
+}
+
+struct AsyncArgs {
+  DevGraph g;
+  unsigned long long* Q;
+  uint32_t logcap;
+  uint32_t* inq;
+  AsyncCtl* ctl;
+};
+
+// Enqueue the improved vertices held by the lanes with want == true.
+__device__ __forceinline__ void push_warp(const AsyncArgs& a, bool want, uint32_t v, uint32_t lane) {
+  bool mine = false;
+  if (want) {
+    const uint32_t rs = __ldg(a.g.ro + v), re = __ldg(a.g.ro + v + 1);
+    if (re > rs) {
+      __threadfence();   // the dist update is visible before the in-queue bit
+      const uint32_t bit = 1u << (v & 31);
+      mine = !(atomicOr(a.inq + (v >> 5), bit) & bit);
+    }
+  }
+  const unsigned mm = __ballot_sync(0xFFFFFFFFu, mine);
+  if (!mm) return;
+  const uint32_t cnt = __popc(mm);
+  const uint32_t leader = __ffs(mm) - 1;
+  unsigned long long base = 0;
+  if (lane == leader) {
+    atomicAdd(&a.ctl->pending, (unsigned long long)cnt);
+    base = atomicAdd(&a.ctl->tail, (unsigned long long)cnt);
+  }
+  base = __shfl_sync(0xFFFFFFFFu, base, leader);
+  if (mine) {
+    const unsigned long long pos = base + __popc(mm & ((1u << lane) - 1));
+    const unsigned long long lap = pos >> a.logcap;
+    unsigned long long* slot = a.Q + (pos & ((1ull << a.logcap) - 1));
+    const uint32_t want_tag = (uint32_t)(2 * lap);
+    uint32_t spins = 0;
+    while ((uint32_t)(ld_acquire_u64(slot) >> 32) != want_tag) {
+      if (ld_volatile_u32(&a.ctl->abort)) return;
+      if (++spins > (1u << 22) || globaltimer() - a.ctl->t_start > a.ctl->watchdog_ns) {
+        atomicOr(&a.ctl->status, DS_TIMEOUT);
+        atomicExch(&a.ctl->abort, 1u);
+        return;
+      }
+      __nanosleep(64);
+    }
+    st_release_u64(slot, ((unsigned long long)(want_tag + 1) << 32) | v);
+  }
+}
+
+__global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
+  __shared__ uint32_t s_pref[kAWarps][33];
+  __shared__ uint32_t s_row[kAWarps][32];
+  __shared__ uint32_t s_du[kAWarps][32];
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  AsyncCtl* ctl = a.ctl;
+  uint32_t* dist = ctl->dist;
+  const unsigned long long cmask = (1ull << a.logcap) - 1;
+  unsigned long long my_pos = 0;
+  bool have = false;
+  uint32_t backoff = 32;
+  unsigned long long pops = 0, edges = 0;
+  bool ovf = false;
+  for (;;) {
+    if (!__any_sync(0xFFFFFFFFu, have)) {
+      unsigned long long h = 0;
+      if (lane == 0) h = atomicAdd(&ctl->head, 32ull);
+      h = __shfl_sync(0xFFFFFFFFu, h, 0);
+      my_pos = h + lane;
+      have = true;
+    }
+    bool got = false;
+    uint32_t v = 0;
+    if (have) {
+      unsigned long long* slot = a.Q + (my_pos & cmask);
+      const uint32_t lap = (uint32_t)(my_pos >> a.logcap);
+      const unsigned long long val = ld_acquire_u64(slot);
+      if ((uint32_t)(val >> 32) == 2 * lap + 1) {
+        v = (uint32_t)val;
+        got = true;
+        have = false;
+        st_release_u64(slot, (unsigned long long)(2 * lap + 2) << 32);
+        atomicAnd(a.inq + (v >> 5), ~(1u << (v & 31)));
+        __threadfence();
+      }
+    }
+    const unsigned gm = __ballot_sync(0xFFFFFFFFu, got);
+    if (gm) {
+      backoff = 32;
+      uint32_t deg = 0, rs = 0, du = 0;
+      if (got) {
+        rs = __ldg(a.g.ro + v);
+        deg = __ldg(a.g.ro + v + 1) - rs;
+        du = ld_cg(dist + v);
+      }
+      uint32_t x = deg;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+      }
+      const uint32_t total = __shfl_sync(0xFFFFFFFFu, x, 31);
+      s_pref[wid][lane] = x - deg;
+      s_row[wid][lane] = rs;
+      s_du[wid][lane] = du;
+      __syncwarp();
+      for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t gidx = base + lane;
+        bool want = false;
+        uint32_t dst = 0;
+        if (gidx < total) {
+          // last lane whose prefix is <= gidx (lanes without an item repeat the next prefix)
+          uint32_t lo = 0, len = 32;
+          while (len > 0) {
+            const uint32_t half = len >> 1;
+            if (s_pref[wid][lo + half] <= gidx) { lo += half + 1; len -= half + 1; }
+            else len = half;
+          }
+          const uint32_t k = lo - 1;
+          const uint2 ed = __ldg(a.g.edges + s_row[wid][k] + (gidx - s_pref[wid][k]));
+          const uint32_t nd = add_sat(s_du[wid][k], ed.y, ovf);
+          dst = ed.x;
+          if (nd < ld_cg(dist + dst)) {
+            const uint32_t old = atomicMin(dist + dst, nd);
+            want = nd < old;
+          }
+        }
+        push_warp(a, want, dst, lane);
+      }
+      pops += got ? 1 : 0;
+      edges += got ? deg : 0;
+      __threadfence();
+      __syncwarp();
+      if (lane == 0) atomicAdd(&ctl->pending, (unsigned long long)(-(long long)__popc(gm)));
+      if (ld_volatile_u32(&ctl->abort)) break;
+    } else {
+      int stop = 0;
+      if (lane == 0) {
+        if (ld_volatile_u64(&ctl->pending) == 0ull || ld_volatile_u32(&ctl->abort)) stop = 1;
+        else if (globaltimer() - ctl->t_start > ctl->watchdog_ns) {
+          atomicOr(&ctl->status, DS_TIMEOUT);
+          atomicExch(&ctl->abort, 1u);
+          stop = 1;
+        }
+      }
+      stop = __shfl_sync(0xFFFFFFFFu, stop, 0);
+      if (stop) break;
+      __nanosleep(backoff);
+      backoff = min(backoff * 2, 1024u);
+    }
+  }
+  // per-warp stats
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    pops += __shfl_down_sync(0xFFFFFFFFu, pops, o);
+    edges += __shfl_down_sync(0xFFFFFFFFu, edges, o);
+  }
+  const unsigned ov = __ballot_sync(0xFFFFFFFFu, ovf);
+  if (lane == 0) {
+    atomicAdd(&ctl->pops, pops);
+    atomicAdd(&ctl->edges, edges);
+    if (ov) atomicOr(&ctl->status, DS_OVERFLOW);
+  }
+}
+
+__global__ void k_async_init(DevGraph g, uint32_t* dist, uint32_t* inq) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (uint64_t i = t; i < g.n; i += stride) dist[i] = kInf;
+  for (uint64_t i = t; i < g.nwords; i += stride) inq[i] = 0u;
+}
+
+__global__ void k_async_seed(DevGraph g, uint32_t src, uint32_t* dist, unsigned long long* Q, uint32_t* inq,
+                             AsyncCtl* ctl, unsigned long long watchdog_ns) {
+  dist[src] = 0u;
+  ctl->head = 0;
+  ctl->pops = 0;
+  ctl->edges = 0;
+  ctl->status = 0;
+  ctl->abort = 0;
+  ctl->dist = dist;
+  ctl->watchdog_ns = watchdog_ns;
+  ctl->t_start = globaltimer();
+  if (g.ro[src + 1] > g.ro[src]) {
+    Q[0] = (1ull << 32) | src;
+    inq[src >> 5] = 1u << (src & 31);
+    ctl->tail = 1;
+    ctl->pending = 1;
+  } else {
+    ctl->tail = 0;
+    ctl->pending = 0;
+  }
+}
+
+}  // namespace
+
+gg_status async_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s) {
+  AsyncWorkspace& w = g->async;
+  const DeviceInfo di = device_info();
+  if (!w.block) {
+    // ring of >= 2n + (resident warps * 32) slots
+    int per_sm = 0;
+    GG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_async, kABlock, 0));
+    if (per_sm < 1) return fail(GG_ERR_INTERNAL, "async kernel does not fit on an SM");
+    w.grid = per_sm * di.num_sms;
+    const uint64_t need = 2ull * g->n + (uint64_t)w.grid * kAWarps * 32 + 1024;
+    uint32_t logcap = 10;
+    while ((1ull << logcap) < need) ++logcap;
+    const size_t qbytes = sizeof(unsigned long long) << logcap;
+    const size_t nw = (g->n + 31) / 32;
+    const size_t total = qbytes + ((sizeof(uint32_t) * nw + 255) & ~size_t(255)) + 256;
+    char* p = nullptr;
+    GG_CK(cudaMalloc(&p, total));
+    w.block = p;
+    w.bytes = total;
+    w.queue = reinterpret_cast<uint32_t*>(p);
+    w.cap = logcap;   // stored as log2 capacity
+    w.inq = reinterpret_cast<uint32_t*>(p + qbytes);
+    w.ctl = p + qbytes + ((sizeof(uint32_t) * nw + 255) & ~size_t(255));
+    if (!g->h_async) GG_CK(cudaMallocHost(&g->h_async, sizeof(AsyncCtl)));
+  }
+  const uint32_t logcap = w.cap;
+  unsigned long long* Q = reinterpret_cast<unsigned long long*>(w.queue);
+  AsyncCtl* ctl = reinterpret_cast<AsyncCtl*>(w.ctl);
+  GG_CK(cudaMemsetAsync(Q, 0, sizeof(unsigned long long) << logcap, s));
+  unsigned ib = (unsigned)std::min<uint64_t>((g->n + 255) / 256, (uint64_t)di.num_sms * 8);
+  if (ib == 0) ib = 1;
+  k_async_init<<<ib, 256, 0, s>>>(g->dg, dist, w.inq);
+  GG_CK(cudaGetLastError());
+  const unsigned long long wd = o.watchdog_ns ? o.watchdog_ns : 10000000000ull;
+  k_async_seed<<<1, 1, 0, s>>>(g->dg, src, dist, Q, w.inq, ctl, wd);
+  GG_CK(cudaGetLastError());
+  AsyncArgs a{g->dg, Q, logcap, w.inq, ctl};
+  void* args[] = {&a};
+  GG_CK(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(&k_async), dim3(w.grid), dim3(kABlock), args, 0, s));
+  return GG_OK;
+}
+
+gg_status async_status(gg_graph* g, uint32_t* ds, gg_stats* st) {
+  if (!g->async.ctl) return GG_OK;
+  AsyncCtl* h = reinterpret_cast<AsyncCtl*>(g->h_async);
+  GG_CK(cudaMemcpyAsync(h, g->async.ctl, sizeof(AsyncCtl), cudaMemcpyDeviceToHost, g->last_stream));
+  GG_CK(cudaStreamSynchronize(g->last_stream));
+  *ds = h->status;
+  if (st) {
+    st->iterations = 0;
+    st->pull_iterations = 0;
+    st->edges_scanned = h->edges;
+    st->frontier_total = h->pops;
+    st->max_frontier = 0;
+  }
+  return GG_OK;
+}
+
+gg_status async_release(gg_graph* g) {
+  if (g->async.block) cudaFree(g->async.block);
+  g->async = AsyncWorkspace{};
+  return GG_OK;
+}
+
+}  // namespace gg

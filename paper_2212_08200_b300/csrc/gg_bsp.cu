@@ -1,0 +1,495 @@
+// gg_bsp.cu -- bulk-synchronous frontier SSSP (the execution::par policy).
+//
+// The paper's SSSP (Listing 4) repeats   f = neighbors_expand(par, g, f, cond)
+// while f is non-empty, where the expand operator (Listing 3) visits every
+// out-edge (v, n, w) of every active vertex v and adds n to the output
+// frontier when   cond = (dist[v] + w  <  atomic_min(&dist[n], dist[v] + w)).
+//
+// Here one superstep is ONE kernel, k_superstep, that fuses:
+//   advance  push: every frontier out-edge relaxed with atomicMin on dist,
+//            load-balanced by a merge-path split of the frontier's edge
+//            prefix sums (equal edge ranges per CTA, whatever the degrees);
+//            or pull: a sweep of the transpose where each vertex takes the
+//            minimum over its in-edges from active vertices (dense bitmap
+//            frontier), then one atomicMin per destination row segment;
+//   filter   each improved vertex is test-and-set in the next bitmap (dedup),
+//            collected in shared memory, block-scanned and appended to the
+//            next sparse frontier with ONE 64-bit atomicAdd per CTA tile that
+//            returns both its queue position and its edge-prefix base, so the
+//            next frontier comes out already carrying its merge-path
+//            coordinates (no separate scan pass);
+//   loop     the last CTA to finish updates the counters, picks push or pull
+//            for the next superstep, and sets the CUDA-graph conditional
+//            (frontier non-empty), so the whole loop runs on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "gg_host.h"
+
+namespace gg {
+
+namespace {
+
+template <int BLOCK, int EPT>
+struct MPSmem {
+  static constexpr int TILE = BLOCK * EPT;
+  static constexpr int ECAP = TILE + 1;
+  uint32_t es[ECAP];   // entry: first merge-path coordinate
+  uint32_t eb[ECAP];   // push: CSR row start;   pull: vertex id
+  uint32_t ec[ECAP];   // push: dist of source;  pull: running min candidate
+  uint32_t qv[ECAP];   // filter output queue: vertex
+  uint32_t qr[ECAP];   //                      CSR row start
+  uint32_t qd[ECAP];   //                      out-degree (scanned in place)
+  uint32_t wsum[BLOCK / 32];
+  uint32_t qn;
+  uint32_t j;
+  uint32_t last;
+  uint32_t ovf;
+  unsigned long long base;
+};
+
+struct StepArgs {
+  DevGraph g;
+  Frontier fr;
+  Ctl* ctl;
+};
+
+// Filter: improved vertex v -> next frontier (once), unless it has no out-edges.
+template <int BLOCK, int EPT>
+__device__ __forceinline__ void filter_candidate(MPSmem<BLOCK, EPT>& sm, const uint32_t* __restrict__ ro,
+                                                 uint32_t* __restrict__ bm_next, uint32_t v) {
+  const uint32_t rs = __ldg(ro + v), re = __ldg(ro + v + 1);
+  if (re > rs) {
+    const uint32_t bit = 1u << (v & 31);
+    const uint32_t old = atomicOr(bm_next + (v >> 5), bit);
+    if (!(old & bit)) {
+      const uint32_t q = atomicAdd(&sm.qn, 1u);
+      sm.qv[q] = v;
+      sm.qr[q] = rs;
+      sm.qd[q] = re - rs;
+    }
+  }
+}
+
+// Append the CTA's collected vertices to the next frontier.
+template <int BLOCK, int EPT>
+__device__ __forceinline__ void filter_flush(MPSmem<BLOCK, EPT>& sm, unsigned long long* cnt_next,
+                                             uint32_t* __restrict__ fv, uint32_t* __restrict__ fr,
+                                             uint32_t* __restrict__ fs) {
+  __syncthreads();
+  const uint32_t qn = sm.qn;
+  if (qn == 0) return;   // uniform
+  const uint32_t tot = block_scan_excl<BLOCK>(sm.qd, qn, sm.wsum);
+  if (threadIdx.x == 0) sm.base = atomicAdd(cnt_next, ((unsigned long long)qn << 32) | tot);
+  __syncthreads();
+  const unsigned long long b = sm.base;
+  const uint32_t pos0 = (uint32_t)(b >> 32), eb0 = (uint32_t)b;
+  for (uint32_t i = threadIdx.x; i < qn; i += BLOCK) {
+    fv[pos0 + i] = sm.qv[i];
+    fr[pos0 + i] = sm.qr[i];
+    fs[pos0 + i] = eb0 + sm.qd[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) sm.qn = 0;
+  __syncthreads();
+}
+
+// Merge-path advance over entries (S strictly increasing edge coordinates,
+// F entries, Etot edges), fused with the filter.
+template <int BLOCK, int EPT, bool PULL>
+__device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t F, uint32_t Etot,
+                                           const uint32_t* __restrict__ S, const uint32_t* __restrict__ B,
+                                           const uint32_t* __restrict__ V, const uint2* __restrict__ edges,
+                                           uint32_t* __restrict__ dist, uint32_t* __restrict__ bm_cur,
+                                           uint32_t* __restrict__ bm_next, unsigned long long* cnt_next,
+                                           uint32_t* __restrict__ nfv, uint32_t* __restrict__ nfr,
+                                           uint32_t* __restrict__ nfs) {
+  constexpr uint32_t TILE = MPSmem<BLOCK, EPT>::TILE;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t G = gridDim.x;
+  const uint32_t e0 = (uint32_t)(((unsigned long long)blockIdx.x * Etot) / G);
+  const uint32_t e1 = (uint32_t)(((unsigned long long)(blockIdx.x + 1) * Etot) / G);
+  if (e0 >= e1) return;   // uniform per CTA
+  if (tid < 32) {
+    const uint32_t j = warp_search_le(S, F, e0);
+    if (tid == 0) sm.j = j;
+  }
+  __syncthreads();
+  uint32_t j = sm.j;
+  bool ovf = false;
+  for (uint32_t t0 = e0; t0 < e1; t0 += TILE) {
+    const uint32_t t1 = min(t0 + TILE, e1);
+    // stage the entries overlapping [t0, t1)
+    uint32_t nent = 0;
+    for (;;) {
+      const uint32_t idx = j + nent + tid;
+      bool valid = false;
+      uint32_t s = 0;
+      if (idx < F) {
+        s = S[idx];
+        valid = s < t1;
+      }
+      if (valid) {
+        const uint32_t slot = nent + tid;
+        sm.es[slot] = s;
+        if (!PULL) {
+          const uint32_t v = V[idx];
+          sm.eb[slot] = B[idx];
+          sm.ec[slot] = ld_cg(dist + v);
+          bm_cur[v >> 5] = 0u;   // the current bitmap is not read in push: clear as we go
+        } else {
+          sm.eb[slot] = V[idx];
+          sm.ec[slot] = kInf;
+        }
+      }
+      const int c = __syncthreads_count(valid);
+      nent += (uint32_t)c;
+      if (c < BLOCK) break;
+    }
+    // advance over this tile's edges
+    uint2 ed[EPT];
+    uint32_t ej[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const uint32_t gidx = t0 + k * BLOCK + tid;
+      ej[k] = kInf;
+      if (gidx < t1) {
+        const uint32_t jj = smem_upper_bound_minus1(sm.es, nent, gidx);
+        ej[k] = jj;
+        const uint32_t e = PULL ? gidx : sm.eb[jj] + (gidx - sm.es[jj]);
+        ed[k] = __ldg(edges + e);
+      }
+    }
+    if (!PULL) {
+      uint32_t nd[EPT], cur[EPT];
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        if (ej[k] != kInf) {
+          nd[k] = add_sat(sm.ec[ej[k]], ed[k].y, ovf);
+          cur[k] = ld_cg(dist + ed[k].x);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        if (ej[k] != kInf && nd[k] < cur[k]) {
+          const uint32_t old = atomicMin(dist + ed[k].x, nd[k]);
+          if (nd[k] < old) filter_candidate(sm, a.g.ro, bm_next, ed[k].x);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        if (ej[k] != kInf) {
+          const uint32_t u = ed[k].x;
+          if ((bm_cur[u >> 5] >> (u & 31)) & 1u) {
+            const uint32_t c = add_sat(ld_cg(dist + u), ed[k].y, ovf);
+            atomicMin(&sm.ec[ej[k]], c);
+          }
+        }
+      }
+      __syncthreads();
+      for (uint32_t i = tid; i < nent; i += BLOCK) {
+        const uint32_t c = sm.ec[i];
+        if (c != kInf) {
+          const uint32_t v = sm.eb[i];
+          if (c < ld_cg(dist + v)) {
+            const uint32_t old = atomicMin(dist + v, c);
+            if (c < old) filter_candidate(sm, a.g.ro, bm_next, v);
+          }
+        }
+      }
+    }
+    filter_flush(sm, cnt_next, nfv, nfr, nfs);
+    j = j + nent - 1;
+  }
+  if (ovf) sm.ovf = 1u;
+}
+
+template <int BLOCK, int EPT>
+__global__ void __launch_bounds__(BLOCK) k_superstep(StepArgs a, cudaGraphConditionalHandle cond, int use_cond) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  MPSmem<BLOCK, EPT>& sm = *reinterpret_cast<MPSmem<BLOCK, EPT>*>(smraw);
+  Ctl* ctl = a.ctl;
+  const uint32_t it = ctl->iter;
+  const uint32_t p = it & 1u;
+  const unsigned long long c = ctl->cnt[p];
+  const uint32_t f = (uint32_t)(c >> 32), E = (uint32_t)c;
+  const uint32_t mode = ctl->mode;
+  uint32_t* dist = ctl->dist;
+  uint32_t* bm_cur = a.fr.bm[it % 3];
+  uint32_t* bm_next = a.fr.bm[(it + 1) % 3];
+  if (threadIdx.x == 0) {
+    sm.qn = 0;
+    sm.ovf = 0;
+  }
+  if (ctl->clear_prev) {
+    uint32_t* bm_old = a.fr.bm[(it + 2) % 3];
+    for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < a.g.nwords; i += gridDim.x * BLOCK) bm_old[i] = 0u;
+  }
+  __syncthreads();
+  if (f > 0) {
+    if (mode == MODE_PUSH)
+      mp_advance<BLOCK, EPT, false>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], a.g.edges, dist, bm_cur,
+                                    bm_next, &ctl->cnt[p ^ 1u], a.fr.fv[p ^ 1u], a.fr.fr[p ^ 1u],
+                                    a.fr.fs[p ^ 1u]);
+    else
+      mp_advance<BLOCK, EPT, true>(sm, a, a.g.np, a.g.m, a.g.ps, a.g.ps, a.g.pv, a.g.t_edges, dist, bm_cur,
+                                   bm_next, &ctl->cnt[p ^ 1u], a.fr.fv[p ^ 1u], a.fr.fr[p ^ 1u],
+                                   a.fr.fs[p ^ 1u]);
+  }
+  // last CTA to arrive closes the superstep
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (sm.ovf) atomicOr(&ctl->status, DS_OVERFLOW);
+    __threadfence();
+    sm.last = (atomicAdd(&ctl->done_ctas, 1u) == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (sm.last && threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long cn = atomicAdd(&ctl->cnt[p ^ 1u], 0ull);
+    const uint32_t fn = (uint32_t)(cn >> 32), En = (uint32_t)cn;
+    if (ctl->trace && it < ctl->trace_cap) {
+      uint32_t* t = ctl->trace + 4ull * it;
+      t[0] = f;
+      t[1] = mode == MODE_PUSH ? E : a.g.m;
+      t[2] = mode;
+      t[3] = fn;
+    }
+    if (f > 0) {
+      ctl->edges_scanned += mode == MODE_PUSH ? E : a.g.m;
+      ctl->frontier_total += f;
+      ctl->max_frontier = max(ctl->max_frontier, f);
+      ctl->pull_iters += mode;
+    }
+    ctl->cnt[p] = 0ull;
+    ctl->done_ctas = 0u;
+    ctl->clear_prev = (mode == MODE_PULL) ? 1u : 0u;
+    uint32_t nm = mode;
+    if (ctl->dir == DIR_PUSH) nm = MODE_PUSH;
+    else if (ctl->dir == DIR_PULL) nm = MODE_PULL;
+    else if (mode == MODE_PUSH) nm = ((unsigned long long)En * ctl->alpha > a.g.m) ? MODE_PULL : MODE_PUSH;
+    else nm = ((unsigned long long)fn * ctl->beta < a.g.np) ? MODE_PUSH : MODE_PULL;
+    ctl->mode = nm;
+    ctl->iter = it + 1;
+    bool more = fn != 0;
+    if (more && it + 1 >= ctl->max_iter) {
+      ctl->status |= DS_ITER_CAP;
+      more = false;
+    }
+    ctl->running = more ? 1u : 0u;
+    if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+  }
+}
+
+// dist := INF except dist[src] = 0; frontier := {src}; bitmaps and counters reset.
+__global__ void k_init(StepArgs a, uint32_t src, uint32_t* dist, uint32_t dir, uint32_t alpha, uint32_t beta,
+                       uint32_t max_iter, uint32_t* trace, uint32_t trace_cap) {
+  const uint32_t n = a.g.n;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((reinterpret_cast<uintptr_t>(dist) & 15u) == 0) {
+    const uint64_t n4 = n / 4;
+    uint4* d4 = reinterpret_cast<uint4*>(dist);
+    for (uint64_t i = t; i < n4; i += stride) d4[i] = make_uint4(kInf, kInf, kInf, kInf);
+    for (uint64_t i = n4 * 4 + t; i < n; i += stride) dist[i] = kInf;
+  } else {
+    for (uint64_t i = t; i < n; i += stride) dist[i] = kInf;
+  }
+  for (uint64_t i = t; i < a.g.nwords; i += stride) {
+    a.fr.bm[0][i] = 0u;
+    a.fr.bm[1][i] = 0u;
+    a.fr.bm[2][i] = 0u;
+  }
+}
+
+__global__ void k_init_tail(StepArgs a, uint32_t src, uint32_t* dist, uint32_t dir, uint32_t alpha, uint32_t beta,
+                            uint32_t max_iter, uint32_t* trace, uint32_t trace_cap) {
+  Ctl* ctl = a.ctl;
+  dist[src] = 0u;
+  const uint32_t rs = a.g.ro[src], re = a.g.ro[src + 1];
+  if (re > rs) {
+    a.fr.fv[0][0] = src;
+    a.fr.fr[0][0] = rs;
+    a.fr.fs[0][0] = 0u;
+    a.fr.bm[0][src >> 5] = 1u << (src & 31);
+    ctl->cnt[0] = (1ull << 32) | (re - rs);
+  } else {
+    ctl->cnt[0] = 0ull;
+  }
+  ctl->cnt[1] = 0ull;
+  ctl->iter = 0;
+  ctl->done_ctas = 0;
+  ctl->status = 0;
+  ctl->mode = dir == DIR_PULL ? MODE_PULL : MODE_PUSH;
+  ctl->clear_prev = 0;
+  ctl->src = src;
+  ctl->max_iter = max_iter;
+  ctl->dir = dir;
+  ctl->alpha = alpha;
+  ctl->beta = beta;
+  ctl->running = re > rs ? 1u : 0u;
+  ctl->pull_iters = 0;
+  ctl->dist = dist;
+  ctl->trace = trace;
+  ctl->trace_cap = trace ? trace_cap : 0u;
+  ctl->max_frontier = 0;
+  ctl->edges_scanned = 0;
+  ctl->frontier_total = 0;
+}
+
+constexpr int kBlock = 256;
+constexpr int kEpt = 8;
+
+void* superstep_fn(int variant) {
+  (void)variant;
+  return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt>);
+}
+
+size_t superstep_smem(int variant) {
+  (void)variant;
+  return sizeof(MPSmem<kBlock, kEpt>);
+}
+
+gg_status ensure_workspace(gg_graph* g) {
+  BspWorkspace& w = g->bsp;
+  if (w.block) return GG_OK;
+  const size_t n = g->n;
+  const size_t nw = (n + 31) / 32;
+  const size_t fbytes = sizeof(uint32_t) * std::max<size_t>(n, 1);
+  const size_t total = 6 * fbytes + 3 * sizeof(uint32_t) * nw + 256 + sizeof(Ctl) + 256;
+  char* p = nullptr;
+  GG_CK(cudaMalloc(&p, total));
+  GG_CK(cudaMemset(p, 0, total));
+  w.block = p;
+  w.bytes = total;
+  size_t off = 0;
+  auto take = [&](size_t b) { char* q = p + off; off += (b + 255) & ~size_t(255); return q; };
+  for (int i = 0; i < 2; ++i) {
+    w.fr.fv[i] = reinterpret_cast<uint32_t*>(take(fbytes));
+    w.fr.fr[i] = reinterpret_cast<uint32_t*>(take(fbytes));
+    w.fr.fs[i] = reinterpret_cast<uint32_t*>(take(fbytes));
+  }
+  for (int i = 0; i < 3; ++i) w.fr.bm[i] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * nw));
+  w.ctl = reinterpret_cast<Ctl*>(take(sizeof(Ctl)));
+  if (off > total + 6 * 256) return fail(GG_ERR_INTERNAL, "workspace layout");
+  return GG_OK;
+}
+
+int superstep_grid(int variant) {
+  static int cached[3] = {0, 0, 0};
+  if (cached[variant]) return cached[variant];
+  const DeviceInfo di = device_info();
+  int per_sm = 0;
+  void* fn = superstep_fn(variant);
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)superstep_smem(variant));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, superstep_smem(variant));
+  if (per_sm < 1) per_sm = 1;
+  cached[variant] = per_sm * di.num_sms;
+  return cached[variant];
+}
+
+gg_status build_graph_exec(gg_graph* g, int variant) {
+  BspWorkspace& w = g->bsp;
+  if (w.exec[variant]) return GG_OK;
+  cudaGraph_t graph = nullptr;
+  GG_CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle h;
+  GG_CK(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  GG_CK(cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  StepArgs a{g->dg, w.fr, w.ctl};
+  int use_cond = 1;
+  void* args[] = {&a, &h, &use_cond};
+  cudaKernelNodeParams kp = {};
+  kp.func = superstep_fn(variant);
+  kp.gridDim = dim3(superstep_grid(variant));
+  kp.blockDim = dim3(kBlock);
+  kp.sharedMemBytes = (unsigned)superstep_smem(variant);
+  kp.kernelParams = args;
+  cudaGraphNode_t knode;
+  GG_CK(cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp));
+  cudaGraphExec_t exec = nullptr;
+  GG_CK(cudaGraphInstantiate(&exec, graph, 0));
+  w.graph[variant] = graph;
+  w.exec[variant] = exec;
+  w.grid[variant] = superstep_grid(variant);
+  return GG_OK;
+}
+
+}  // namespace
+
+gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s) {
+  gg_status st = ensure_workspace(g);
+  if (st != GG_OK) return st;
+  const int variant = 0;
+  BspWorkspace& w = g->bsp;
+  const uint32_t dir = o.direction == GG_DIR_PUSH ? DIR_PUSH : o.direction == GG_DIR_PULL ? DIR_PULL : DIR_AUTO;
+  const uint32_t alpha = o.pull_alpha ? o.pull_alpha : 4u;
+  const uint32_t beta = o.pull_beta ? o.pull_beta : 24u;
+  const uint32_t max_iter = o.max_iterations ? o.max_iterations : (g->n + 2u < g->n ? 0xFFFFFFFFu : g->n + 2u);
+  StepArgs a{g->dg, w.fr, w.ctl};
+  const DeviceInfo di = device_info();
+  const uint64_t work = std::max<uint64_t>(g->n / 4, g->dg.nwords);
+  unsigned ib = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)di.num_sms * 8);
+  if (ib == 0) ib = 1;
+  k_init<<<ib, 256, 0, s>>>(a, src, dist, dir, alpha, beta, max_iter, o.trace, o.trace_cap);
+  GG_CK(cudaGetLastError());
+  k_init_tail<<<1, 1, 0, s>>>(a, src, dist, dir, alpha, beta, max_iter, o.trace, o.trace_cap);
+  GG_CK(cudaGetLastError());
+  if (o.policy == GG_POLICY_BSP_GRAPH) {
+    st = build_graph_exec(g, variant);
+    if (st != GG_OK) return st;
+    GG_CK(cudaGraphLaunch(w.exec[variant], s));
+  } else {
+    const int grid = superstep_grid(variant);
+    const size_t smem = superstep_smem(variant);
+    cudaGraphConditionalHandle none = 0;
+    uint32_t* h_running = &g->h_ctl->running;
+    uint32_t launched = 0;
+    uint32_t check_every = 1;
+    for (;;) {
+      for (uint32_t k = 0; k < check_every; ++k) {
+        k_superstep<kBlock, kEpt><<<grid, kBlock, smem, s>>>(a, none, 0);
+        ++launched;
+      }
+      GG_CK(cudaGetLastError());
+      GG_CK(cudaMemcpyAsync(h_running, &w.ctl->running, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+      GG_CK(cudaStreamSynchronize(s));
+      if (*h_running == 0) break;
+      if (launched > max_iter + 16) break;
+      check_every = std::min<uint32_t>(check_every * 2, 16);
+    }
+  }
+  return GG_OK;
+}
+
+gg_status bsp_read_ctl(gg_graph* g, cudaStream_t s) {
+  if (!g->bsp.ctl) return GG_OK;
+  GG_CK(cudaMemcpyAsync(g->h_ctl, g->bsp.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  GG_CK(cudaStreamSynchronize(s));
+  return GG_OK;
+}
+
+gg_status bsp_release(gg_graph* g) {
+  BspWorkspace& w = g->bsp;
+  for (int i = 0; i < 3; ++i) {
+    if (w.exec[i]) cudaGraphExecDestroy(w.exec[i]);
+    if (w.graph[i]) cudaGraphDestroy(w.graph[i]);
+    w.exec[i] = nullptr;
+    w.graph[i] = nullptr;
+  }
+  if (w.block) cudaFree(w.block);
+  w.block = nullptr;
+  w.ctl = nullptr;
+  return GG_OK;
+}
+
+}  // namespace gg

@@ -1,0 +1,155 @@
+// gg_common.cuh -- shared device/host definitions of the frontier SSSP library.
+//
+// Data layout in HBM (one graph handle):
+//   ro      u32[n+1]   CSR row offsets (push direction)
+//   edges   uint2[m]   {col, weight} interleaved: one 8-byte load per edge
+//   t_ro / t_edges     the transpose (CSC) for pull; aliases ro/edges when the
+//                      graph is symmetric
+//   pv, ps  u32[np]    vertices with a non-empty CSC row and that row's start
+//                      (the entry list of the pull sweep)
+// Workspace of one SSSP run:
+//   fv/fr/fs[2]  u32[n]  sparse frontier, ping-pong by superstep parity:
+//                        vertex, its CSR row start, and the exclusive prefix
+//                        of frontier out-degrees (the merge-path coordinate)
+//   bm[3]   u32[ceil(n/32)]  dense frontier bitmaps, rotating by superstep:
+//                        current (read), next (test-and-set dedup), old
+//                        (cleared)
+//   ctl     Ctl          counters and the superstep state machine
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gg.h"
+
+namespace gg {
+
+constexpr uint32_t kInf = 0xFFFFFFFFu;
+constexpr uint32_t kSat = 0xFFFFFFFEu;   // saturated (overflowed) finite distance
+
+enum : uint32_t { MODE_PUSH = 0, MODE_PULL = 1 };
+enum : uint32_t { DIR_AUTO = 0, DIR_PUSH = 1, DIR_PULL = 2 };
+
+// device-status bits, mapped to gg_status on the host
+enum : uint32_t { DS_OVERFLOW = 1u, DS_ITER_CAP = 2u, DS_TIMEOUT = 4u, DS_INTERNAL = 8u };
+
+struct Ctl {
+  unsigned long long cnt[2];   // (count << 32) | edge total of the frontier being built, by parity
+  uint32_t iter;               // superstep index
+  uint32_t done_ctas;          // arrival counter for the last-CTA finalize
+  uint32_t status;             // DS_* bits
+  uint32_t mode;               // MODE_PUSH / MODE_PULL of the current superstep
+  uint32_t clear_prev;         // bm[(iter+2)%3] must be zeroed during this superstep
+  uint32_t src;
+  uint32_t max_iter;
+  uint32_t dir;                // DIR_*
+  uint32_t alpha, beta;        // direction switch thresholds
+  uint32_t running;            // 1 while the frontier is non-empty
+  uint32_t pull_iters;
+  uint32_t* dist;              // caller's distance array for this run
+  uint32_t* trace;             // optional per-superstep trace (4 u32 per superstep)
+  uint32_t trace_cap;
+  uint32_t max_frontier;
+  unsigned long long edges_scanned;
+  unsigned long long frontier_total;
+};
+
+struct DevGraph {
+  uint32_t n, m, np, nwords;
+  const uint32_t* ro;
+  const uint2* edges;
+  const uint32_t* t_ro;
+  const uint2* t_edges;
+  const uint32_t* pv;
+  const uint32_t* ps;
+};
+
+struct Frontier {
+  uint32_t* fv[2];
+  uint32_t* fr[2];
+  uint32_t* fs[2];
+  uint32_t* bm[3];
+};
+
+#ifdef __CUDACC__
+// L2-coherent load (bypasses L1): used for values other CTAs update with atomics.
+__device__ __forceinline__ uint32_t ld_cg(const uint32_t* p) { return __ldcg(p); }
+
+// saturating distance add; flags overflow when the sum does not fit below kInf.
+__device__ __forceinline__ uint32_t add_sat(uint32_t d, uint32_t w, bool& ovf) {
+  unsigned long long s = (unsigned long long)d + w;
+  if (s >= kInf) { ovf = true; return kSat; }
+  return (uint32_t)s;
+}
+
+// Largest j in [0, F) with S[j] <= x, for S strictly increasing with S[0] <= x.
+// Executed by a full warp (32-ary search: ceil(log32 F) dependent rounds).
+__device__ __forceinline__ uint32_t warp_search_le(const uint32_t* S, uint32_t F, uint32_t x) {
+  const int lane = threadIdx.x & 31;
+  uint32_t lo = 0, hi = F;
+  while (hi - lo > 32) {
+    const uint32_t step = (hi - lo + 31) / 32;
+    const uint32_t p = lo + lane * step;
+    const bool pred = (p < hi) && (S[p] <= x);
+    const unsigned b = __ballot_sync(0xFFFFFFFFu, pred);
+    const int last = 31 - __clz(b);
+    lo = lo + last * step;
+    hi = min(hi, lo + step);
+  }
+  const uint32_t p = lo + lane;
+  const bool pred = (p < hi) && (S[p] <= x);
+  const unsigned b = __ballot_sync(0xFFFFFFFFu, pred);
+  return lo + (31 - __clz(b));
+}
+
+// Exclusive scan in place of data[0..count) held in shared memory, by a
+// whole CTA of BLOCK threads; returns the total.  wsum: BLOCK/32 words of smem.
+template <int BLOCK>
+__device__ __forceinline__ uint32_t block_scan_excl(uint32_t* data, uint32_t count, uint32_t* wsum) {
+  constexpr int NW = BLOCK / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t items = (count + BLOCK - 1) / BLOCK;
+  const uint32_t beg = min((uint32_t)tid * items, count), end = min(beg + items, count);
+  uint32_t local = 0;
+  for (uint32_t i = beg; i < end; ++i) local += data[i];
+  uint32_t x = local;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t s = lane < NW ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < NW) wsum[lane] = s;
+  }
+  __syncthreads();
+  uint32_t run = x - local + (warp ? wsum[warp - 1] : 0);
+  const uint32_t total = wsum[NW - 1];
+  for (uint32_t i = beg; i < end; ++i) {
+    const uint32_t d = data[i];
+    data[i] = run;
+    run += d;
+  }
+  __syncthreads();
+  return total;
+}
+
+// Index of the last element <= x in the strictly increasing smem array a[0..n).
+__device__ __forceinline__ uint32_t smem_upper_bound_minus1(const uint32_t* a, uint32_t n, uint32_t x) {
+  uint32_t lo = 0, len = n;
+  while (len > 0) {
+    const uint32_t half = len >> 1;
+    if (a[lo + half] <= x) { lo += half + 1; len -= half + 1; }
+    else len = half;
+  }
+  return lo - 1;
+}
+#endif
+
+}  // namespace gg

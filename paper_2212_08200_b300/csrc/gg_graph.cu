@@ -1,0 +1,280 @@
+// gg_graph.cu -- graph handle construction (Sec. IV-A, Listing 1 of the paper:
+// a CSR queried through a graph API; the "Push vs. Pull" box: keep the
+// transposed representation beside it for pull traversals).
+//
+// Device preprocessing, run once per handle (not part of an SSSP run):
+//   validate   offsets start at 0, never decrease, end at m; every column < n
+//   interleave col/weight arrays -> uint2 {col, weight}
+//   transpose  CSC by counting sort (only for graphs not declared symmetric)
+//   pull list  vertices with a non-empty CSC row, with the row start
+#include <cuda_runtime.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "gg_host.h"
+
+namespace gg {
+
+namespace {
+
+constexpr int SCAN_BLOCK = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+__global__ void k_validate(uint32_t n, uint32_t m, const uint32_t* __restrict__ ro,
+                           const uint32_t* __restrict__ col, uint32_t* __restrict__ err) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    if (ro[i + 1] < ro[i]) atomicOr(err, 1u);
+  }
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    if (col[e] >= n) atomicOr(err, 2u);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (ro[0] != 0 || ro[n] != m) atomicOr(err, 4u);
+  }
+}
+
+__global__ void k_interleave(uint32_t m, const uint32_t* __restrict__ col, const uint32_t* __restrict__ w,
+                             uint2* __restrict__ out) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
+    out[e] = make_uint2(col[e], w[e]);
+}
+
+__global__ void k_count_in(uint32_t m, const uint2* __restrict__ edges, uint32_t* __restrict__ cnt) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
+    atomicAdd(&cnt[edges[e].x], 1u);
+}
+
+// warp per source row: scatter every edge u->v into v's CSC row as {u, w}
+__global__ void k_scatter_t(uint32_t n, const uint32_t* __restrict__ ro, const uint2* __restrict__ edges,
+                            uint32_t* __restrict__ cursor, uint2* __restrict__ t_edges) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t u = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+    for (uint32_t e = ro[u] + lane; e < ro[u + 1]; e += 32) {
+      const uint2 ed = edges[e];
+      const uint32_t pos = atomicAdd(&cursor[ed.x], 1u);
+      t_edges[pos] = make_uint2((uint32_t)u, ed.y);
+    }
+  }
+}
+
+// per-tile sums of a u32 array
+__global__ void k_scan_reduce(const uint32_t* __restrict__ in, uint64_t count, uint32_t* __restrict__ sums) {
+  __shared__ uint32_t ws[SCAN_BLOCK / 32];
+  const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+  uint32_t s = 0;
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const uint64_t i = base + (uint64_t)k * SCAN_BLOCK + threadIdx.x;
+    if (i < count) s += in[i];
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int i = 0; i < SCAN_BLOCK / 32; ++i) t += ws[i];
+    sums[blockIdx.x] = t;
+  }
+}
+
+// exclusive scan of one tile (in place), plus the tile offset
+__global__ void k_scan_tile(uint32_t* __restrict__ data, uint64_t count, const uint32_t* __restrict__ offs) {
+  __shared__ uint32_t buf[SCAN_TILE];
+  __shared__ uint32_t ws[SCAN_BLOCK / 32];
+  const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+  const uint64_t rem = count - base;
+  const uint32_t valid = rem < (uint64_t)SCAN_TILE ? (uint32_t)rem : (uint32_t)SCAN_TILE;
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const uint32_t i = k * SCAN_BLOCK + threadIdx.x;
+    buf[i] = i < valid ? data[base + i] : 0u;
+  }
+  __syncthreads();
+  block_scan_excl<SCAN_BLOCK>(buf, valid, ws);
+  const uint32_t off = offs ? offs[blockIdx.x] : 0u;
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    const uint32_t i = k * SCAN_BLOCK + threadIdx.x;
+    if (i < valid) data[base + i] = buf[i] + off;
+  }
+}
+
+// exclusive scan in place (recursive over tile sums)
+gg_status scan_excl(uint32_t* data, uint64_t count, cudaStream_t s) {
+  if (count == 0) return GG_OK;
+  const uint64_t tiles = (count + SCAN_TILE - 1) / SCAN_TILE;
+  if (tiles == 1) {
+    k_scan_tile<<<1, SCAN_BLOCK, 0, s>>>(data, count, nullptr);
+    GG_CK(cudaGetLastError());
+    return GG_OK;
+  }
+  uint32_t* sums = nullptr;
+  GG_CK(cudaMallocAsync(&sums, tiles * sizeof(uint32_t), s));
+  k_scan_reduce<<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(data, count, sums);
+  GG_CK(cudaGetLastError());
+  gg_status st = scan_excl(sums, tiles, s);
+  if (st != GG_OK) { cudaFreeAsync(sums, s); return st; }
+  k_scan_tile<<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(data, count, sums);
+  GG_CK(cudaGetLastError());
+  GG_CK(cudaFreeAsync(sums, s));
+  return GG_OK;
+}
+
+__global__ void k_nonempty_flags(uint32_t n, const uint32_t* __restrict__ t_ro, uint32_t* __restrict__ flag) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    flag[v] = t_ro[v + 1] > t_ro[v] ? 1u : 0u;
+  if (blockIdx.x == 0 && threadIdx.x == 0) flag[n] = 0;
+}
+
+__global__ void k_pull_list(uint32_t n, const uint32_t* __restrict__ t_ro, const uint32_t* __restrict__ pos,
+                            uint32_t* __restrict__ pv, uint32_t* __restrict__ ps) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    if (t_ro[v + 1] > t_ro[v]) {
+      pv[pos[v]] = (uint32_t)v;
+      ps[pos[v]] = t_ro[v];
+    }
+  }
+}
+
+unsigned grid_for(uint64_t work) {
+  const DeviceInfo di = device_info();
+  uint64_t b = (work + 255) / 256;
+  const uint64_t cap = (uint64_t)di.num_sms * 8;
+  if (b > cap) b = cap;
+  if (b == 0) b = 1;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m64, const uint32_t* ro_in, const uint32_t* col_in,
+                      const uint32_t* w_in, uint32_t flags, cudaStream_t s) {
+  const bool dev = (flags & GG_DEVICE_PTRS) != 0;
+  const bool validate = (flags & GG_NO_VALIDATE) == 0;
+  const uint32_t m = (uint32_t)m64;
+  g->n = n;
+  g->m = m;
+  g->symmetric = (flags & GG_SYMMETRIC) != 0;
+  // cheap host-side check first; monotonicity and column range are checked on
+  // the device after the upload (k_validate)
+  if (!dev && validate && (ro_in[0] != 0 || ro_in[n] != m))
+    return fail(GG_ERR_INVALID_ARG, "row_offsets must start at 0 and end at m");
+  GG_CK(cudaGetDevice(&g->device));
+
+  GG_CK(cudaMalloc(&g->ro, sizeof(uint32_t) * ((size_t)n + 1)));
+  GG_CK(cudaMalloc(&g->edges, sizeof(uint2) * std::max<size_t>(m, 1)));
+  g->bytes = sizeof(uint32_t) * ((size_t)n + 1) + sizeof(uint2) * std::max<size_t>(m, 1);
+  GG_CK(cudaMemcpyAsync(g->ro, ro_in, sizeof(uint32_t) * ((size_t)n + 1),
+                        dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  const uint32_t* dcol = col_in;
+  const uint32_t* dw = w_in;
+  uint32_t* tmp = nullptr;
+  if (m > 0) {
+    if (!dev) {
+      GG_CK(cudaMallocAsync(&tmp, sizeof(uint32_t) * 2 * (size_t)m, s));
+      GG_CK(cudaMemcpyAsync(tmp, col_in, sizeof(uint32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
+      GG_CK(cudaMemcpyAsync(tmp + m, w_in, sizeof(uint32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
+      dcol = tmp;
+      dw = tmp + m;
+    }
+    if (validate) {
+      uint32_t* derr = nullptr;
+      GG_CK(cudaMallocAsync(&derr, sizeof(uint32_t), s));
+      GG_CK(cudaMemsetAsync(derr, 0, sizeof(uint32_t), s));
+      k_validate<<<grid_for(std::max<uint64_t>(n, m)), 256, 0, s>>>(n, m, g->ro, dcol, derr);
+      GG_CK(cudaGetLastError());
+      uint32_t herr = 0;
+      GG_CK(cudaMemcpyAsync(&herr, derr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+      GG_CK(cudaFreeAsync(derr, s));
+      GG_CK(cudaStreamSynchronize(s));
+      if (herr & 4u) return fail(GG_ERR_INVALID_ARG, "row_offsets must start at 0 and end at m");
+      if (herr & 1u) return fail(GG_ERR_INVALID_ARG, "row_offsets must be non-decreasing");
+      if (herr & 2u) return fail(GG_ERR_INVALID_ARG, "col_indices must be < n");
+    }
+    k_interleave<<<grid_for(m), 256, 0, s>>>(m, dcol, dw, g->edges);
+    GG_CK(cudaGetLastError());
+  } else if (dev && validate) {
+    uint32_t h[2] = {0, 0};
+    GG_CK(cudaMemcpyAsync(h, g->ro, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    GG_CK(cudaMemcpyAsync(h + 1, g->ro + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    GG_CK(cudaStreamSynchronize(s));
+    if (h[0] != 0 || h[1] != 0) return fail(GG_ERR_INVALID_ARG, "row_offsets must start at 0 and end at m");
+  }
+  if (tmp) GG_CK(cudaFreeAsync(tmp, s));
+
+  // transpose (CSC) for pull
+  if (g->symmetric) {
+    g->t_ro = g->ro;
+    g->t_edges = g->edges;
+  } else {
+    GG_CK(cudaMalloc(&g->t_ro, sizeof(uint32_t) * ((size_t)n + 1)));
+    GG_CK(cudaMalloc(&g->t_edges, sizeof(uint2) * std::max<size_t>(m, 1)));
+    g->bytes += sizeof(uint32_t) * ((size_t)n + 1) + sizeof(uint2) * std::max<size_t>(m, 1);
+    GG_CK(cudaMemsetAsync(g->t_ro, 0, sizeof(uint32_t) * ((size_t)n + 1), s));
+    if (m > 0) {
+      k_count_in<<<grid_for(m), 256, 0, s>>>(m, g->edges, g->t_ro);
+      GG_CK(cudaGetLastError());
+    }
+    gg_status st = scan_excl(g->t_ro, (uint64_t)n + 1, s);
+    if (st != GG_OK) return st;
+    if (m > 0) {
+      uint32_t* cursor = nullptr;
+      GG_CK(cudaMallocAsync(&cursor, sizeof(uint32_t) * ((size_t)n + 1), s));
+      GG_CK(cudaMemcpyAsync(cursor, g->t_ro, sizeof(uint32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s));
+      k_scatter_t<<<grid_for((uint64_t)n * 32), 256, 0, s>>>(n, g->ro, g->edges, cursor, g->t_edges);
+      GG_CK(cudaGetLastError());
+      GG_CK(cudaFreeAsync(cursor, s));
+    }
+  }
+
+  // pull entry list: vertices with a non-empty CSC row
+  {
+    uint32_t* pos = nullptr;
+    GG_CK(cudaMallocAsync(&pos, sizeof(uint32_t) * ((size_t)n + 1), s));
+    k_nonempty_flags<<<grid_for(n), 256, 0, s>>>(n, g->t_ro, pos);
+    GG_CK(cudaGetLastError());
+    gg_status st = scan_excl(pos, (uint64_t)n + 1, s);
+    if (st != GG_OK) return st;
+    uint32_t np = 0;
+    GG_CK(cudaMemcpyAsync(&np, pos + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    GG_CK(cudaStreamSynchronize(s));
+    GG_CK(cudaMalloc(&g->pv, sizeof(uint32_t) * std::max<size_t>(np, 1)));
+    GG_CK(cudaMalloc(&g->ps, sizeof(uint32_t) * std::max<size_t>(np, 1)));
+    g->bytes += 2 * sizeof(uint32_t) * std::max<size_t>(np, 1);
+    k_pull_list<<<grid_for(n), 256, 0, s>>>(n, g->t_ro, pos, g->pv, g->ps);
+    GG_CK(cudaGetLastError());
+    GG_CK(cudaFreeAsync(pos, s));
+    g->dg.np = np;
+  }
+  GG_CK(cudaStreamSynchronize(s));
+
+  g->dg.n = n;
+  g->dg.m = m;
+  g->dg.nwords = (n + 31) / 32;
+  g->dg.ro = g->ro;
+  g->dg.edges = g->edges;
+  g->dg.t_ro = g->t_ro;
+  g->dg.t_edges = g->t_edges;
+  g->dg.pv = g->pv;
+  g->dg.ps = g->ps;
+  return GG_OK;
+}
+
+void graph_free(gg_graph* g) {
+  if (g->t_ro && g->t_ro != g->ro) cudaFree(g->t_ro);
+  if (g->t_edges && g->t_edges != g->edges) cudaFree(g->t_edges);
+  cudaFree(g->ro);
+  cudaFree(g->edges);
+  cudaFree(g->pv);
+  cudaFree(g->ps);
+  g->ro = g->t_ro = g->pv = g->ps = nullptr;
+  g->edges = g->t_edges = nullptr;
+}
+
+}  // namespace gg

@@ -1,0 +1,96 @@
+// gg_host.h -- host-side internals shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+
+#include "gg.h"
+#include "gg_common.cuh"
+
+namespace gg {
+
+// thread-local error message + status helper
+void set_error(const std::string& msg);
+gg_status fail(gg_status s, const std::string& msg);
+gg_status cuda_fail(cudaError_t e, const char* what);
+
+#define GG_CK(call)                                          \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return ::gg::cuda_fail(e_, #call); \
+  } while (0)
+
+struct DeviceInfo {
+  int device = -1;
+  int num_sms = 0;
+  int max_smem_optin = 0;
+};
+DeviceInfo device_info();
+
+// Workspace of the bulk-synchronous path (allocated on first use).
+struct BspWorkspace {
+  Frontier fr{};
+  Ctl* ctl = nullptr;
+  void* block = nullptr;      // single device allocation backing fr and ctl
+  size_t bytes = 0;
+  // CUDA graph with a conditional WHILE node around one superstep kernel,
+  // one per load-balance variant.
+  cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+  int grid[3] = {0, 0, 0};
+};
+
+// Workspace of the asynchronous persistent path.
+struct AsyncWorkspace {
+  void* block = nullptr;
+  size_t bytes = 0;
+  uint32_t* queue = nullptr;   // ring of vertex ids
+  uint32_t cap = 0;            // power of two >= n
+  uint32_t* inq = nullptr;     // in-queue bitmap
+  void* ctl = nullptr;         // AsyncCtl
+  int grid = 0;
+};
+
+}  // namespace gg
+
+struct gg_graph {
+  uint32_t n = 0;
+  uint32_t m = 0;
+  int device = -1;
+  bool symmetric = false;
+  gg::DevGraph dg{};
+  // owned device buffers
+  uint32_t* ro = nullptr;
+  uint2* edges = nullptr;
+  uint32_t* t_ro = nullptr;
+  uint2* t_edges = nullptr;
+  uint32_t* pv = nullptr;
+  uint32_t* ps = nullptr;
+  size_t bytes = 0;
+  std::mutex mu;
+  gg::BspWorkspace bsp;
+  gg::AsyncWorkspace async;
+  cudaEvent_t last_ev = nullptr;
+  cudaStream_t last_stream = nullptr;
+  bool ev_valid = false;
+  gg::Ctl* h_ctl = nullptr;      // pinned host mirror for status/stats reads
+  void* h_async = nullptr;       // pinned host mirror of the async control block
+  int last_policy = -1;
+};
+
+namespace gg {
+// gg_bsp.cu
+gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s);
+gg_status bsp_release(gg_graph* g);
+// gg_async.cu
+gg_status async_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s);
+gg_status async_release(gg_graph* g);
+gg_status async_status(gg_graph* g, uint32_t* ds, gg_stats* st);
+// gg_graph.cu
+gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m, const uint32_t* ro, const uint32_t* col,
+                      const uint32_t* w, uint32_t flags, cudaStream_t s);
+void graph_free(gg_graph* g);
+gg_status status_from_device(uint32_t ds);
+}  // namespace gg
