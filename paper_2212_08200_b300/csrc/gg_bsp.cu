@@ -358,14 +358,16 @@ gg_status ensure_workspace(gg_graph* g) {
   const size_t n = g->n;
   const size_t nw = (n + 31) / 32;
   const size_t fbytes = sizeof(uint32_t) * std::max<size_t>(n, 1);
-  const size_t total = 6 * fbytes + 3 * sizeof(uint32_t) * nw + 256 + sizeof(Ctl) + 256;
+  auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+  // every sub-buffer starts on a 256-byte boundary
+  const size_t total = 6 * r256(fbytes) + 3 * r256(sizeof(uint32_t) * nw) + r256(sizeof(Ctl));
   char* p = nullptr;
   GG_CK(cudaMalloc(&p, total));
   GG_CK(cudaMemset(p, 0, total));
   w.block = p;
   w.bytes = total;
   size_t off = 0;
-  auto take = [&](size_t b) { char* q = p + off; off += (b + 255) & ~size_t(255); return q; };
+  auto take = [&](size_t b) { char* q = p + off; off += r256(b); return q; };
   for (int i = 0; i < 2; ++i) {
     w.fr.fv[i] = reinterpret_cast<uint32_t*>(take(fbytes));
     w.fr.fr[i] = reinterpret_cast<uint32_t*>(take(fbytes));
@@ -373,7 +375,7 @@ gg_status ensure_workspace(gg_graph* g) {
   }
   for (int i = 0; i < 3; ++i) w.fr.bm[i] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * nw));
   w.ctl = reinterpret_cast<Ctl*>(take(sizeof(Ctl)));
-  if (off > total + 6 * 256) return fail(GG_ERR_INTERNAL, "workspace layout");
+  if (off != total) return fail(GG_ERR_INTERNAL, "workspace layout");
   return GG_OK;
 }
 
