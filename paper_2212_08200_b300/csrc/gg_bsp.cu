@@ -206,39 +206,117 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
   if (ovf) sm.ovf = 1u;
 }
 
+// Degree-binned push advance (thread / warp / CTA per vertex).  Each CTA
+// takes chunks of BLOCK frontier vertices; vertices of degree >= cta_thr are
+// expanded by the whole CTA one at a time, degree >= warp_thr by one warp,
+// the rest by their own thread.  Every round relaxes at most BLOCK*EPT edges,
+// then the filter queue is flushed, so the shared queue never overflows.
 template <int BLOCK, int EPT>
-__global__ void __launch_bounds__(BLOCK) k_superstep(StepArgs a, cudaGraphConditionalHandle cond, int use_cond) {
-  extern __shared__ __align__(16) unsigned char smraw[];
-  MPSmem<BLOCK, EPT>& sm = *reinterpret_cast<MPSmem<BLOCK, EPT>*>(smraw);
-  Ctl* ctl = a.ctl;
-  const uint32_t it = ctl->iter;
-  const uint32_t p = it & 1u;
-  const unsigned long long c = ctl->cnt[p];
-  const uint32_t f = (uint32_t)(c >> 32), E = (uint32_t)c;
-  const uint32_t mode = ctl->mode;
-  uint32_t* dist = ctl->dist;
-  uint32_t* bm_cur = a.fr.bm[it % 3];
-  uint32_t* bm_next = a.fr.bm[(it + 1) % 3];
+__device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t F, uint32_t Etot,
+                                             const uint32_t* __restrict__ fv, const uint32_t* __restrict__ fr,
+                                             const uint32_t* __restrict__ fs, uint32_t* __restrict__ dist,
+                                             uint32_t* __restrict__ bm_cur, uint32_t* __restrict__ bm_next,
+                                             unsigned long long* cnt_next, uint32_t* __restrict__ nfv,
+                                             uint32_t* __restrict__ nfr, uint32_t* __restrict__ nfs,
+                                             uint32_t warp_thr, uint32_t cta_thr) {
+  constexpr uint32_t NW = BLOCK / 32;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint2* __restrict__ edges = a.g.edges;
+  bool ovf = false;
+  auto relax = [&](uint32_t e, uint32_t du) {
+    const uint2 ed = __ldg(edges + e);
+    const uint32_t nd = add_sat(du, ed.y, ovf);
+    if (nd < ld_cg(dist + ed.x)) {
+      const uint32_t old = atomicMin(dist + ed.x, nd);
+      if (nd < old) filter_candidate(sm, a.g.ro, bm_next, ed.x);
+    }
+  };
+  const uint32_t nchunks = (F + BLOCK - 1) / BLOCK;
+  for (uint32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    const uint32_t i = c * BLOCK + tid;
+    uint32_t row = 0, deg = 0, du = 0;
+    if (tid == 0) { sm.j = 0; sm.last = 0; }   // large / medium list lengths
+    __syncthreads();
+    if (i < F) {
+      const uint32_t v = fv[i];
+      row = fr[i];
+      deg = (i + 1 < F ? fs[i + 1] : Etot) - fs[i];
+      du = ld_cg(dist + v);
+      bm_cur[v >> 5] = 0u;
+      if (deg >= cta_thr) {
+        const uint32_t k = atomicAdd(&sm.j, 1u);
+        sm.es[k] = row; sm.eb[k] = deg; sm.ec[k] = du;
+        deg = 0;
+      } else if (deg >= warp_thr) {
+        const uint32_t k = BLOCK + atomicAdd(&sm.last, 1u);
+        sm.es[k] = row; sm.eb[k] = deg; sm.ec[k] = du;
+        deg = 0;
+      }
+    }
+    __syncthreads();
+    const uint32_t nl = sm.j, nm = sm.last;
+    // CTA per vertex
+    for (uint32_t k = 0; k < nl; ++k) {
+      const uint32_t r = sm.es[k], d = sm.eb[k], u = sm.ec[k];
+      for (uint32_t base = 0; base < d; base += BLOCK * EPT) {
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+          const uint32_t o = base + q * BLOCK + tid;
+          if (o < d) relax(r + o, u);
+        }
+        filter_flush(sm, cnt_next, nfv, nfr, nfs);
+      }
+    }
+    // warp per vertex
+    uint32_t mi = warp, moff = 0;
+    while (__syncthreads_or(mi < nm)) {
+      if (mi < nm) {
+        const uint32_t r = sm.es[BLOCK + mi], d = sm.eb[BLOCK + mi], u = sm.ec[BLOCK + mi];
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+          const uint32_t o = moff + q * 32 + lane;
+          if (o < d) relax(r + o, u);
+        }
+        moff += 32 * EPT;
+        if (moff >= d) { mi += NW; moff = 0; }
+      }
+      filter_flush(sm, cnt_next, nfv, nfr, nfs);
+    }
+    // thread per vertex
+    uint32_t off = 0;
+    while (__syncthreads_or(off < deg)) {
+#pragma unroll
+      for (int q = 0; q < EPT; ++q)
+        if (off + q < deg) relax(row + off + q, du);
+      off += EPT;
+      filter_flush(sm, cnt_next, nfv, nfr, nfs);
+    }
+  }
+  if (ovf) sm.ovf = 1u;
+}
+
+// Shared prologue: reset the CTA's queue, clear the bitmap left by a pull step.
+template <int BLOCK, int EPT>
+__device__ __forceinline__ void superstep_prologue(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t it) {
   if (threadIdx.x == 0) {
     sm.qn = 0;
     sm.ovf = 0;
   }
-  if (ctl->clear_prev) {
+  if (a.ctl->clear_prev) {
     uint32_t* bm_old = a.fr.bm[(it + 2) % 3];
     for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < a.g.nwords; i += gridDim.x * BLOCK) bm_old[i] = 0u;
   }
   __syncthreads();
-  if (f > 0) {
-    if (mode == MODE_PUSH)
-      mp_advance<BLOCK, EPT, false>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], a.g.edges, dist, bm_cur,
-                                    bm_next, &ctl->cnt[p ^ 1u], a.fr.fv[p ^ 1u], a.fr.fr[p ^ 1u],
-                                    a.fr.fs[p ^ 1u]);
-    else
-      mp_advance<BLOCK, EPT, true>(sm, a, a.g.np, a.g.m, a.g.ps, a.g.ps, a.g.pv, a.g.t_edges, dist, bm_cur,
-                                   bm_next, &ctl->cnt[p ^ 1u], a.fr.fv[p ^ 1u], a.fr.fr[p ^ 1u],
-                                   a.fr.fs[p ^ 1u]);
-  }
-  // last CTA to arrive closes the superstep
+}
+
+// The last CTA to arrive closes the superstep: counters, trace, direction
+// choice for the next superstep, and the loop condition.
+template <int BLOCK, int EPT>
+__device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t it, uint32_t f,
+                                                   uint32_t E, uint32_t mode, cudaGraphConditionalHandle cond,
+                                                   int use_cond) {
+  Ctl* ctl = a.ctl;
+  const uint32_t p = it & 1u;
   __syncthreads();
   if (threadIdx.x == 0) {
     if (sm.ovf) atomicOr(&ctl->status, DS_OVERFLOW);
@@ -283,9 +361,53 @@ __global__ void __launch_bounds__(BLOCK) k_superstep(StepArgs a, cudaGraphCondit
   }
 }
 
-// dist := INF except dist[src] = 0; frontier := {src}; bitmaps and counters reset.
-__global__ void k_init(StepArgs a, uint32_t src, uint32_t* dist, uint32_t dir, uint32_t alpha, uint32_t beta,
-                       uint32_t max_iter, uint32_t* trace, uint32_t trace_cap) {
+// One superstep; BINS selects the degree-binned push advance instead of the
+// merge-path one (pull is the same merge-path sweep in both).
+template <int BLOCK, int EPT, bool BINS>
+__global__ void __launch_bounds__(BLOCK) k_superstep(StepArgs a, cudaGraphConditionalHandle cond, int use_cond) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  MPSmem<BLOCK, EPT>& sm = *reinterpret_cast<MPSmem<BLOCK, EPT>*>(smraw);
+  Ctl* ctl = a.ctl;
+  const uint32_t it = ctl->iter;
+  const uint32_t p = it & 1u;
+  const unsigned long long c = ctl->cnt[p];
+  const uint32_t f = (uint32_t)(c >> 32), E = (uint32_t)c;
+  const uint32_t mode = ctl->mode;
+  uint32_t* dist = ctl->dist;
+  uint32_t* bm_cur = a.fr.bm[it % 3];
+  uint32_t* bm_next = a.fr.bm[(it + 1) % 3];
+  superstep_prologue(sm, a, it);
+  if (f > 0) {
+    if (mode == MODE_PUSH) {
+      if (BINS)
+        bins_advance<BLOCK, EPT>(sm, a, f, E, a.fr.fv[p], a.fr.fr[p], a.fr.fs[p], dist, bm_cur, bm_next,
+                                 &ctl->cnt[p ^ 1u], a.fr.fv[p ^ 1u], a.fr.fr[p ^ 1u], a.fr.fs[p ^ 1u],
+                                 ctl->warp_thr, ctl->cta_thr);
+      else
+        mp_advance<BLOCK, EPT, false>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], a.g.edges, dist, bm_cur,
+                                      bm_next, &ctl->cnt[p ^ 1u], a.fr.fv[p ^ 1u], a.fr.fr[p ^ 1u],
+                                      a.fr.fs[p ^ 1u]);
+    } else {
+      mp_advance<BLOCK, EPT, true>(sm, a, a.g.np, a.g.m, a.g.ps, a.g.ps, a.g.pv, a.g.t_edges, dist, bm_cur,
+                                   bm_next, &ctl->cnt[p ^ 1u], a.fr.fv[p ^ 1u], a.fr.fr[p ^ 1u],
+                                   a.fr.fs[p ^ 1u]);
+    }
+  }
+  superstep_finalize(sm, a, it, f, E, mode, cond, use_cond);
+}
+
+// Per-run parameters written into the control block by k_init_tail.
+struct RunParams {
+  uint32_t src;
+  uint32_t* dist;
+  uint32_t dir, alpha, beta, max_iter;
+  uint32_t* trace;
+  uint32_t trace_cap;
+  uint32_t warp_thr, cta_thr;
+};
+
+// dist := INF everywhere (vectorised 16-byte stores when aligned); bitmaps := 0.
+__global__ void k_init(StepArgs a, uint32_t* dist) {
   const uint32_t n = a.g.n;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -304,10 +426,11 @@ __global__ void k_init(StepArgs a, uint32_t src, uint32_t* dist, uint32_t dir, u
   }
 }
 
-__global__ void k_init_tail(StepArgs a, uint32_t src, uint32_t* dist, uint32_t dir, uint32_t alpha, uint32_t beta,
-                            uint32_t max_iter, uint32_t* trace, uint32_t trace_cap) {
+// dist[src] := 0, frontier := {src} (when src has out-edges), counters reset.
+__global__ void k_init_tail(StepArgs a, RunParams rp) {
   Ctl* ctl = a.ctl;
-  dist[src] = 0u;
+  const uint32_t src = rp.src;
+  rp.dist[src] = 0u;
   const uint32_t rs = a.g.ro[src], re = a.g.ro[src + 1];
   if (re > rs) {
     a.fr.fv[0][0] = src;
@@ -322,35 +445,35 @@ __global__ void k_init_tail(StepArgs a, uint32_t src, uint32_t* dist, uint32_t d
   ctl->iter = 0;
   ctl->done_ctas = 0;
   ctl->status = 0;
-  ctl->mode = dir == DIR_PULL ? MODE_PULL : MODE_PUSH;
+  ctl->mode = rp.dir == DIR_PULL ? MODE_PULL : MODE_PUSH;
   ctl->clear_prev = 0;
   ctl->src = src;
-  ctl->max_iter = max_iter;
-  ctl->dir = dir;
-  ctl->alpha = alpha;
-  ctl->beta = beta;
+  ctl->max_iter = rp.max_iter;
+  ctl->dir = rp.dir;
+  ctl->alpha = rp.alpha;
+  ctl->beta = rp.beta;
   ctl->running = re > rs ? 1u : 0u;
   ctl->pull_iters = 0;
-  ctl->dist = dist;
-  ctl->trace = trace;
-  ctl->trace_cap = trace ? trace_cap : 0u;
+  ctl->dist = rp.dist;
+  ctl->trace = rp.trace;
+  ctl->trace_cap = rp.trace ? rp.trace_cap : 0u;
   ctl->max_frontier = 0;
+  ctl->warp_thr = rp.warp_thr;
+  ctl->cta_thr = rp.cta_thr;
   ctl->edges_scanned = 0;
   ctl->frontier_total = 0;
 }
 
 constexpr int kBlock = 256;
 constexpr int kEpt = 8;
+constexpr int kVariants = 2;   // 0 merge-path push, 1 degree-binned push
 
 void* superstep_fn(int variant) {
-  (void)variant;
-  return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt>);
+  return variant == 1 ? reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, true>)
+                      : reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, false>);
 }
 
-size_t superstep_smem(int variant) {
-  (void)variant;
-  return sizeof(MPSmem<kBlock, kEpt>);
-}
+size_t superstep_smem(int) { return sizeof(MPSmem<kBlock, kEpt>); }
 
 gg_status ensure_workspace(gg_graph* g) {
   BspWorkspace& w = g->bsp;
@@ -380,7 +503,7 @@ gg_status ensure_workspace(gg_graph* g) {
 }
 
 int superstep_grid(int variant) {
-  static int cached[3] = {0, 0, 0};
+  static int cached[kVariants] = {0, 0};
   if (cached[variant]) return cached[variant];
   const DeviceInfo di = device_info();
   int per_sm = 0;
@@ -431,20 +554,29 @@ gg_status build_graph_exec(gg_graph* g, int variant) {
 gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s) {
   gg_status st = ensure_workspace(g);
   if (st != GG_OK) return st;
-  const int variant = 0;
+  const int variant = o.lb_mode == GG_LB_BINS ? 1 : 0;
   BspWorkspace& w = g->bsp;
-  const uint32_t dir = o.direction == GG_DIR_PUSH ? DIR_PUSH : o.direction == GG_DIR_PULL ? DIR_PULL : DIR_AUTO;
-  const uint32_t alpha = o.pull_alpha ? o.pull_alpha : 4u;
-  const uint32_t beta = o.pull_beta ? o.pull_beta : 24u;
-  const uint32_t max_iter = o.max_iterations ? o.max_iterations : (g->n + 2u < g->n ? 0xFFFFFFFFu : g->n + 2u);
+  RunParams rp;
+  rp.src = src;
+  rp.dist = dist;
+  rp.dir = o.direction == GG_DIR_PUSH ? DIR_PUSH : o.direction == GG_DIR_PULL ? DIR_PULL : DIR_AUTO;
+  rp.alpha = o.pull_alpha ? o.pull_alpha : 4u;
+  rp.beta = o.pull_beta ? o.pull_beta : 24u;
+  rp.max_iter = o.max_iterations ? o.max_iterations : (g->n + 2u < g->n ? 0xFFFFFFFFu : g->n + 2u);
+  rp.trace = o.trace;
+  rp.trace_cap = o.trace_cap;
+  rp.warp_thr = o.warp_threshold ? o.warp_threshold : 32u;
+  rp.cta_thr = o.cta_threshold ? o.cta_threshold : 1024u;
+  if (rp.cta_thr < rp.warp_thr) rp.cta_thr = rp.warp_thr;
+  const uint32_t max_iter = rp.max_iter;
   StepArgs a{g->dg, w.fr, w.ctl};
   const DeviceInfo di = device_info();
   const uint64_t work = std::max<uint64_t>(g->n / 4, g->dg.nwords);
   unsigned ib = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)di.num_sms * 8);
   if (ib == 0) ib = 1;
-  k_init<<<ib, 256, 0, s>>>(a, src, dist, dir, alpha, beta, max_iter, o.trace, o.trace_cap);
+  k_init<<<ib, 256, 0, s>>>(a, dist);
   GG_CK(cudaGetLastError());
-  k_init_tail<<<1, 1, 0, s>>>(a, src, dist, dir, alpha, beta, max_iter, o.trace, o.trace_cap);
+  k_init_tail<<<1, 1, 0, s>>>(a, rp);
   GG_CK(cudaGetLastError());
   if (o.policy == GG_POLICY_BSP_GRAPH) {
     st = build_graph_exec(g, variant);
@@ -459,7 +591,8 @@ gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o
     uint32_t check_every = 1;
     for (;;) {
       for (uint32_t k = 0; k < check_every; ++k) {
-        k_superstep<kBlock, kEpt><<<grid, kBlock, smem, s>>>(a, none, 0);
+        if (variant == 1) k_superstep<kBlock, kEpt, true><<<grid, kBlock, smem, s>>>(a, none, 0);
+        else k_superstep<kBlock, kEpt, false><<<grid, kBlock, smem, s>>>(a, none, 0);
         ++launched;
       }
       GG_CK(cudaGetLastError());

@@ -49,6 +49,7 @@ struct Ctl {
   uint32_t* trace;             // optional per-superstep trace (4 u32 per superstep)
   uint32_t trace_cap;
   uint32_t max_frontier;
+  uint32_t warp_thr, cta_thr;  // degree bins of the binned push advance
   unsigned long long edges_scanned;
   unsigned long long frontier_total;
 };

@@ -29,14 +29,15 @@ def gg():
 
 POLICIES = {"graph": 0, "async": 1, "host": 2}
 DIRS = {"auto": 0, "push": 1, "pull": 2}
+LB = {"mp": 1, "bins": 2}
 MODES = [("graph", "auto"), ("graph", "push"), ("graph", "pull"), ("host", "auto"), ("host", "pull"),
-         ("async", "auto")]
+         ("async", "auto"), ("graph", "push", "bins"), ("host", "auto", "bins")]
 
 
-def run(g, src, policy="graph", direction="auto", **kw):
+def run(g, src, policy="graph", direction="auto", lb="mp", **kw):
     m = gg()
     st = m.gg_stats()
-    d = g.sssp(src, policy=POLICIES[policy], direction=DIRS[direction], stats=st, **kw)
+    d = g.sssp(src, policy=POLICIES[policy], direction=DIRS[direction], lb_mode=LB[lb], stats=st, **kw)
     torch.cuda.synchronize()
     return d.cpu().numpy(), st.as_dict()
 
@@ -68,7 +69,8 @@ def test_hand_worked_fixtures(name, mode):
     got, st = run(g, f["src"], *mode) if not isinstance(f["expect"], str) else (None, None)
     if isinstance(f["expect"], str):
         m = gg()
-        d = g.sssp(f["src"], policy=POLICIES[mode[0]], direction=DIRS[mode[1]])
+        d = g.sssp(f["src"], policy=POLICIES[mode[0]], direction=DIRS[mode[1]],
+                   lb_mode=LB[mode[2] if len(mode) > 2 else "mp"])
         with pytest.raises(m.GGError) as ei:
             g.check()
         assert ei.value.status_name == "GG_ERR_OVERFLOW"
@@ -101,6 +103,16 @@ def test_rmat16_multi_tile(mode, sym):
     g.close()
 
 
+@pytest.mark.parametrize("thr", [(2, 8), (32, 1024), (1, 1), (4096, 8192)])
+def test_bins_thresholds(thr):
+    ro, col, w, src = graphgen.workload("rmat16")
+    g = gg().Graph(ro, col, w, symmetric=True)
+    ref = oracle.dijkstra(ro, col, w, src)
+    got, _ = run(g, src, "graph", "push", "bins", warp_threshold=thr[0], cta_threshold=thr[1])
+    np.testing.assert_array_equal(got, ref)
+    g.close()
+
+
 def test_rmat20_config_push_pull():
     ro, col, w, src = graphgen.workload("rmat20")
     g = gg().Graph(ro, col, w, symmetric=True)
@@ -113,6 +125,8 @@ def test_rmat20_config_push_pull():
     np.testing.assert_array_equal(got, ref)
     assert st["pull_iterations"] == 0
     got, _ = run(g, src, "async")
+    np.testing.assert_array_equal(got, ref)
+    got, _ = run(g, src, "graph", "auto", "bins")
     np.testing.assert_array_equal(got, ref)
     g.close()
 
