@@ -180,6 +180,42 @@ gg_status gg_sssp(gg_graph_t g, uint32_t src, uint32_t* dist_out, cudaStream_t s
 gg_status gg_sssp_ex(gg_graph_t g, uint32_t src, uint32_t* dist_out, const gg_options* opt,
                      cudaStream_t stream);
 
+/* ---- SSSP without any device allocation ---------------------------------- */
+
+/* Largest vertex count gg_sssp_noalloc accepts. */
+#define GG_NOALLOC_MAX_VERTICES (1u << 20)
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory: for example code whose GPU memory is
+ * already owned by another allocator (a framework's caching allocator that has
+ * reserved most of the device, where a fresh cudaMalloc fails or fragments
+ * the pool), or a latency-sensitive loop that cannot afford the implicit
+ * device-wide synchronisation of cudaFree.
+ *
+ * Computes the same distances as gg_sssp, reading the caller's CSR in place:
+ *   n            vertices, 1 <= n <= GG_NOALLOC_MAX_VERTICES; larger n returns
+ *                GG_ERR_INVALID_ARG (use gg_graph_create_csr + gg_sssp)
+ *   m            edges, m < 2^32 - 1
+ *   row_offsets  device u32[n+1]; col_indices, weights: device u32[m]
+ *                (checked on the device: offsets monotone from 0 to m,
+ *                columns < n; a bad CSR returns GG_ERR_INVALID_ARG)
+ *   src          < n
+ *   dist_out     device u32[n], caller-owned
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Its working
+ * memory is one fixed array of about 24.3 MiB compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ * All calls share that array and it keeps the last call's contents: each
+ * call resets what must start at zero, and calls whose GPU work overlaps (on
+ * different streams or host threads) race on it, so the caller must order
+ * them.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * outside any stream capture.  The call synchronises `stream` and returns
+ * when dist_out is complete (push supersteps launched from the host).
+ * Returns GG_ERR_OVERFLOW when a finite distance does not fit below GG_INF. */
+gg_status gg_sssp_noalloc(uint32_t n, uint64_t m, const uint32_t* row_offsets,
+                          const uint32_t* col_indices, const uint32_t* weights, uint32_t src,
+                          uint32_t* dist_out, cudaStream_t stream);
+
 /* ---- errors ------------------------------------------------------------- */
 
 const char* gg_status_string(gg_status s);

@@ -22,7 +22,8 @@ __all__ = [
     "GG_POLICY_BSP_GRAPH", "GG_POLICY_ASYNC_PERSISTENT", "GG_POLICY_BSP_HOST",
     "GG_DIR_AUTO", "GG_DIR_PUSH", "GG_DIR_PULL", "GG_LB_AUTO", "GG_LB_MERGE_PATH", "GG_LB_BINS",
     "gg_graph_create_csr", "gg_graph_destroy", "gg_graph_info", "gg_graph_check", "gg_sssp", "gg_sssp_ex",
-    "gg_status_string", "gg_last_error", "gg_abi_version", "Graph", "lib_path", "load",
+    "gg_status_string", "gg_last_error", "gg_abi_version", "gg_sssp_noalloc", "GG_NOALLOC_MAX_VERTICES",
+    "Graph", "lib_path", "load",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -89,6 +90,7 @@ def load():
             "gg_options_default": (None, [ctypes.POINTER(gg_options)]),
             "gg_sssp": (ctypes.c_int, [vp, u32, vp, vp]),
             "gg_sssp_ex": (ctypes.c_int, [vp, u32, vp, ctypes.POINTER(gg_options), vp]),
+            "gg_sssp_noalloc": (ctypes.c_int, [u32, u64, vp, vp, vp, u32, vp, vp]),
             "gg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "gg_last_error": (ctypes.c_char_p, []),
             "gg_abi_version": (u32, []),
@@ -209,6 +211,22 @@ def gg_sssp_ex(handle: int, src: int, dist_out, options: gg_options | None = Non
         raise ValueError("dist_out must be a CUDA tensor")
     _check(load().gg_sssp_ex(handle, src, p, ctypes.byref(options) if options is not None else None,
                              _stream_ptr(stream)), "gg_sssp_ex")
+
+
+GG_NOALLOC_MAX_VERTICES = 1 << 20
+
+
+def gg_sssp_noalloc(row_offsets, col_indices, weights, src: int, dist_out, stream=None):
+    """Distances from src computed straight from a device CSR (CUDA uint32
+    tensors) without allocating any device memory; returns when dist_out is
+    complete.  For callers that must not allocate (see include/gg.h)."""
+    ptrs = [_ptr(a) for a in (row_offsets, col_indices, weights, dist_out)]
+    if not all(dev for _, dev in ptrs):
+        raise ValueError("gg_sssp_noalloc takes CUDA tensors only")
+    n = int(row_offsets.shape[0]) - 1
+    m = int(col_indices.shape[0])
+    _check(load().gg_sssp_noalloc(n, m, ptrs[0][0], ptrs[1][0] if m else None, ptrs[2][0] if m else None, src,
+                                  ptrs[3][0], _stream_ptr(stream)), "gg_sssp_noalloc")
 
 
 class Graph:
