@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--workload", default="rmat20")
     p.add_argument("--policy", default="graph", choices=["graph", "async", "host"])
     p.add_argument("--direction", default="auto", choices=["auto", "push", "pull"])
+    p.add_argument("--lb", default="mp", choices=["mp", "bins"])
     p.add_argument("--alpha", type=int, default=0)
     p.add_argument("--beta", type=int, default=0)
     p.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -209,15 +210,17 @@ def main():
     stream = torch.cuda.current_stream()
     g = gg.Graph(ro, col, w, symmetric=True, stream=stream)
     dist_t = torch.empty(n, dtype=torch.uint32, device="cuda")
-    opts = gg.make_options(policy=policy, direction=direction, pull_alpha=args.alpha, pull_beta=args.beta)
+    lb = {"mp": gg.GG_LB_MERGE_PATH, "bins": gg.GG_LB_BINS}[args.lb]
+    opts = gg.make_options(policy=policy, direction=direction, lb_mode=lb, pull_alpha=args.alpha, pull_beta=args.beta)
 
     def step():
         gg.gg_sssp_ex(g.handle, src, dist_t, opts, stream)
 
     # correctness of what is timed: stats run + invariant-free hash check vs the oracle's stored hash
     st = gg.gg_stats()
-    gg.gg_sssp_ex(g.handle, src, dist_t, gg.make_options(policy=policy, direction=direction, pull_alpha=args.alpha,
-                                                         pull_beta=args.beta, stats=st), stream)
+    gg.gg_sssp_ex(g.handle, src, dist_t, gg.make_options(policy=policy, direction=direction, lb_mode=lb,
+                                                         pull_alpha=args.alpha, pull_beta=args.beta, stats=st),
+                  stream)
     d_host = dist_t.cpu().numpy()
     reach = d_host != gg.GG_INF
     m_trav = int(np.diff(ro.astype(np.int64))[reach].sum())
@@ -313,7 +316,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": workload_desc(args.workload), "n": n, "m": m, "source": int(src),
-                       "m_trav": m_trav, "n_reach": n_reach, "policy": args.policy, "direction": args.direction,
+                       "m_trav": m_trav, "n_reach": n_reach, "policy": args.policy, "direction": args.direction, "lb": args.lb,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": f"inputs larger than L2 (edge array {8 * m / 2**20:.0f} MiB > 126 MiB L2); "
                              f"dist re-initialised every step",

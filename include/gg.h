@@ -77,6 +77,8 @@ typedef enum {
 #define GG_SYMMETRIC   0x2u   /* caller asserts the graph is symmetric: the CSR is
                                  its own transpose, so pull reuses it (no CSC built) */
 #define GG_NO_VALIDATE 0x4u   /* skip the structural checks (offsets, col < n)     */
+#define GG_NO_PACK     0x8u   /* keep 8-byte {col, weight} edges even when the
+                                 4-byte packed form (col << wbits | weight) fits  */
 
 /* Execution policy: the paper's execution::par / execution::par_nosync
  * (Sec. III-A; Listing 3 and the "Timing Model and Parallelism" box). */
@@ -138,13 +140,14 @@ typedef struct {
  *   row_offsets  u32[n+1], row_offsets[0] = 0, non-decreasing, row_offsets[n] = m
  *   col_indices  u32[m], each < n
  *   weights      u32[m]
- *   flags        GG_DEVICE_PTRS | GG_SYMMETRIC | GG_NO_VALIDATE
+ *   flags        GG_DEVICE_PTRS | GG_SYMMETRIC | GG_NO_VALIDATE | GG_NO_PACK
  *   stream       stream for the upload and preprocessing; the call returns after
  *                they are complete (it synchronises the stream)
  *   out          receives the handle
  * The handle owns a device copy (edges re-encoded as interleaved {col, weight}
- * pairs, plus the transpose unless GG_SYMMETRIC); the caller's arrays may be
- * freed after the call.  Errors: GG_ERR_INVALID_ARG for a null pointer, n or m
+ * pairs, or packed into one u32 (col << wbits) | weight when the bits of n-1
+ * and of the largest weight fit in 32, plus the transpose unless
+ * GG_SYMMETRIC); the caller's arrays may be freed after the call.  Errors: GG_ERR_INVALID_ARG for a null pointer, n or m
  * out of range, or (unless GG_NO_VALIDATE) a CSR whose offsets are not
  * monotone from 0 to m or whose column index is >= n; GG_ERR_OUT_OF_MEMORY;
  * GG_ERR_CUDA.  On error *out is set to NULL. */

@@ -32,7 +32,7 @@ _lib = None
 _lock = threading.Lock()
 
 GG_INF = 0xFFFFFFFF
-GG_DEVICE_PTRS, GG_SYMMETRIC, GG_NO_VALIDATE = 0x1, 0x2, 0x4
+GG_DEVICE_PTRS, GG_SYMMETRIC, GG_NO_VALIDATE, GG_NO_PACK = 0x1, 0x2, 0x4, 0x8
 GG_POLICY_BSP_GRAPH, GG_POLICY_ASYNC_PERSISTENT, GG_POLICY_BSP_HOST = 0, 1, 2
 GG_DIR_AUTO, GG_DIR_PUSH, GG_DIR_PULL = 0, 1, 2
 GG_LB_AUTO, GG_LB_MERGE_PATH, GG_LB_BINS = 0, 1, 2
@@ -144,7 +144,7 @@ def gg_abi_version() -> int:
 
 
 def gg_graph_create_csr(row_offsets, col_indices, weights, symmetric: bool = False, validate: bool = True,
-                        stream=None) -> int:
+                        stream=None, pack: bool = True) -> int:
     """Handle (int) for a CSR given as numpy arrays (host) or CUDA tensors
     (device).  All three must live on the same side."""
     lib = load()
@@ -157,7 +157,8 @@ def gg_graph_create_csr(row_offsets, col_indices, weights, symmetric: bool = Fal
     m = int(col_indices.shape[0])
     if int(weights.shape[0]) != m:
         raise ValueError("weights and col_indices differ in length")
-    flags = (GG_DEVICE_PTRS if ro_dev else 0) | (GG_SYMMETRIC if symmetric else 0) | (0 if validate else GG_NO_VALIDATE)
+    flags = ((GG_DEVICE_PTRS if ro_dev else 0) | (GG_SYMMETRIC if symmetric else 0) |
+             (0 if validate else GG_NO_VALIDATE) | (0 if pack else GG_NO_PACK))
     h = ctypes.c_void_p()
     _check(lib.gg_graph_create_csr(n, m, ro, col if m else None, w if m else None, flags,
                                    _stream_ptr(stream) if (stream is not None or ro_dev) else 0,
@@ -233,8 +234,8 @@ class Graph:
     """Owning wrapper of a gg_graph_t."""
 
     def __init__(self, row_offsets, col_indices, weights, symmetric: bool = False, validate: bool = True,
-                 stream=None):
-        self.handle = gg_graph_create_csr(row_offsets, col_indices, weights, symmetric, validate, stream)
+                 stream=None, pack: bool = True):
+        self.handle = gg_graph_create_csr(row_offsets, col_indices, weights, symmetric, validate, stream, pack)
         self.n, self.m, _ = gg_graph_info(self.handle)
 
     def sssp(self, src: int, dist_out=None, stream=None, **opts):

@@ -108,7 +108,8 @@ gg_status gg_graph_create_csr(uint32_t n, uint64_t m, const uint32_t* row_offset
   if (m >= 0xFFFFFFFFull) return fail(GG_ERR_INVALID_ARG, "m must be < 2^32 - 1 (uint32 row offsets)");
   if (!row_offsets) return fail(GG_ERR_INVALID_ARG, "row_offsets is NULL");
   if (m > 0 && (!col_indices || !weights)) return fail(GG_ERR_INVALID_ARG, "col_indices/weights is NULL");
-  if (flags & ~(GG_DEVICE_PTRS | GG_SYMMETRIC | GG_NO_VALIDATE)) return fail(GG_ERR_INVALID_ARG, "unknown flag");
+  if (flags & ~(GG_DEVICE_PTRS | GG_SYMMETRIC | GG_NO_VALIDATE | GG_NO_PACK))
+    return fail(GG_ERR_INVALID_ARG, "unknown flag");
   gg_graph* g = new (std::nothrow) gg_graph();
   if (!g) return fail(GG_ERR_OUT_OF_MEMORY, "host allocation failed");
   gg_status st = graph_build(g, n, m, row_offsets, col_indices, weights, flags, stream);

@@ -120,6 +120,7 @@ __device__ __forceinline__ void push_warp(const AsyncArgs& a, bool want, uint32_
   }
 }
 
+template <bool PK>
 __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
   __shared__ uint32_t s_pref[kAWarps][33];
   __shared__ uint32_t s_row[kAWarps][32];
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
             else len = half;
           }
           const uint32_t k = lo - 1;
-          const uint2 ed = __ldg(a.g.edges + s_row[wid][k] + (gidx - s_pref[wid][k]));
+          const uint2 ed = load_edge<PK>(a.g.edges, s_row[wid][k] + (gidx - s_pref[wid][k]), a.g.wbits);
           const uint32_t nd = add_sat(s_du[wid][k], ed.y, ovf);
           dst = ed.x;
           if (nd < ld_cg(dist + dst)) {
@@ -272,7 +273,10 @@ gg_status async_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options&
   if (!w.block) {
     // ring of >= 2n + (resident warps * 32) slots
     int per_sm = 0;
-    GG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_async, kABlock, 0));
+    GG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_async<false>, kABlock, 0));
+    int per_sm_pk = 0;
+    GG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_pk, k_async<true>, kABlock, 0));
+    per_sm = std::min(per_sm, per_sm_pk);
     if (per_sm < 1) return fail(GG_ERR_INTERNAL, "async kernel does not fit on an SM");
     w.grid = per_sm * di.num_sms;
     const uint64_t need = 2ull * g->n + (uint64_t)w.grid * kAWarps * 32 + 1024;
@@ -304,7 +308,8 @@ gg_status async_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options&
   GG_CK(cudaGetLastError());
   AsyncArgs a{g->dg, Q, logcap, w.inq, ctl};
   void* args[] = {&a};
-  GG_CK(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(&k_async), dim3(w.grid), dim3(kABlock), args, 0, s));
+  void* fn = g->dg.packed ? reinterpret_cast<void*>(&k_async<true>) : reinterpret_cast<void*>(&k_async<false>);
+  GG_CK(cudaLaunchCooperativeKernel(fn, dim3(w.grid), dim3(kABlock), args, 0, s));
   return GG_OK;
 }
 

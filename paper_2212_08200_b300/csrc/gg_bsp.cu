@@ -96,20 +96,26 @@ __device__ __forceinline__ void filter_flush(MPSmem<BLOCK, EPT>& sm, unsigned lo
 }
 
 // Merge-path advance over entries (S strictly increasing edge coordinates,
-// F entries, Etot edges), fused with the filter.
-template <int BLOCK, int EPT, bool PULL>
+// F entries, Etot edges), fused with the filter.  CTA b takes the edge range
+// [split(b), split(b+1)), split rounded down to 32 edges so that in pull
+// (where the coordinate is the edge index itself) every thread's 8-edge run
+// is one aligned vector load.
+template <int BLOCK, int EPT, bool PULL, bool PK>
 __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t F, uint32_t Etot,
                                            const uint32_t* __restrict__ S, const uint32_t* __restrict__ B,
-                                           const uint32_t* __restrict__ V, const uint2* __restrict__ edges,
+                                           const uint32_t* __restrict__ V, const void* __restrict__ edges,
                                            uint32_t* __restrict__ dist, uint32_t* __restrict__ bm_cur,
                                            uint32_t* __restrict__ bm_next, unsigned long long* cnt_next,
                                            uint32_t* __restrict__ nfv, uint32_t* __restrict__ nfr,
                                            uint32_t* __restrict__ nfs) {
+  static_assert(!PULL || EPT == 8, "pull uses 8-edge vector runs");
   constexpr uint32_t TILE = MPSmem<BLOCK, EPT>::TILE;
   const uint32_t tid = threadIdx.x;
   const uint32_t G = gridDim.x;
-  const uint32_t e0 = (uint32_t)(((unsigned long long)blockIdx.x * Etot) / G);
-  const uint32_t e1 = (uint32_t)(((unsigned long long)(blockIdx.x + 1) * Etot) / G);
+  const uint32_t wbits = a.g.wbits;
+  const uint32_t e0 = (uint32_t)(((unsigned long long)blockIdx.x * Etot) / G) & ~31u;
+  const uint32_t e1 =
+      blockIdx.x + 1 == G ? Etot : (uint32_t)(((unsigned long long)(blockIdx.x + 1) * Etot) / G) & ~31u;
   if (e0 >= e1) return;   // uniform per CTA
   if (tid < 32) {
     const uint32_t j = warp_search_le(S, F, e0);
@@ -147,21 +153,20 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
       nent += (uint32_t)c;
       if (c < BLOCK) break;
     }
-    // advance over this tile's edges
-    uint2 ed[EPT];
-    uint32_t ej[EPT];
-#pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-      const uint32_t gidx = t0 + k * BLOCK + tid;
-      ej[k] = kInf;
-      if (gidx < t1) {
-        const uint32_t jj = smem_upper_bound_minus1(sm.es, nent, gidx);
-        ej[k] = jj;
-        const uint32_t e = PULL ? gidx : sm.eb[jj] + (gidx - sm.es[jj]);
-        ed[k] = __ldg(edges + e);
-      }
-    }
     if (!PULL) {
+      // push: consecutive threads take consecutive edge coordinates (coalesced rows)
+      uint2 ed[EPT];
+      uint32_t ej[EPT];
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const uint32_t gidx = t0 + k * BLOCK + tid;
+        ej[k] = kInf;
+        if (gidx < t1) {
+          const uint32_t jj = smem_upper_bound_minus1(sm.es, nent, gidx);
+          ej[k] = jj;
+          ed[k] = load_edge<PK>(edges, sm.eb[jj] + (gidx - sm.es[jj]), wbits);
+        }
+      }
       uint32_t nd[EPT], cur[EPT];
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
@@ -178,15 +183,44 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
         }
       }
     } else {
+      // pull: each thread owns an aligned run of 8 in-edges, keeps a running
+      // minimum per destination row in a register and folds it into the
+      // row's shared slot only when the row changes
+      const uint32_t g0 = t0 + tid * EPT;
+      if (g0 < t1) {
+        uint32_t col[EPT], wt[EPT];
+        if (g0 + EPT <= t1) {
+          load_edges8<PK>(edges, g0, wbits, col, wt);
+        } else {
 #pragma unroll
-      for (int k = 0; k < EPT; ++k) {
-        if (ej[k] != kInf) {
-          const uint32_t u = ed[k].x;
-          if ((bm_cur[u >> 5] >> (u & 31)) & 1u) {
-            const uint32_t c = add_sat(ld_cg(dist + u), ed[k].y, ovf);
-            atomicMin(&sm.ec[ej[k]], c);
+          for (int k = 0; k < EPT; ++k) {
+            if (g0 + k < t1) {
+              const uint2 ed = load_edge<PK>(edges, g0 + k, wbits);
+              col[k] = ed.x;
+              wt[k] = ed.y;
+            }
           }
         }
+        uint32_t jj = smem_upper_bound_minus1(sm.es, nent, g0);
+        uint32_t nxt = jj + 1 < nent ? sm.es[jj + 1] : 0xFFFFFFFFu;
+        uint32_t acc = kInf;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const uint32_t gidx = g0 + k;
+          if (gidx < t1) {
+            if (gidx >= nxt) {
+              if (acc != kInf) atomicMin(&sm.ec[jj], acc);
+              acc = kInf;
+              do {
+                ++jj;
+                nxt = jj + 1 < nent ? sm.es[jj + 1] : 0xFFFFFFFFu;
+              } while (gidx >= nxt);
+            }
+            const uint32_t u = col[k];
+            if ((bm_cur[u >> 5] >> (u & 31)) & 1u) acc = min(acc, add_sat(dist[u], wt[k], ovf));
+          }
+        }
+        if (acc != kInf) atomicMin(&sm.ec[jj], acc);
       }
       __syncthreads();
       for (uint32_t i = tid; i < nent; i += BLOCK) {
@@ -211,7 +245,7 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
 // expanded by the whole CTA one at a time, degree >= warp_thr by one warp,
 // the rest by their own thread.  Every round relaxes at most BLOCK*EPT edges,
 // then the filter queue is flushed, so the shared queue never overflows.
-template <int BLOCK, int EPT>
+template <int BLOCK, int EPT, bool PK>
 __device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t F, uint32_t Etot,
                                              const uint32_t* __restrict__ fv, const uint32_t* __restrict__ fr,
                                              const uint32_t* __restrict__ fs, uint32_t* __restrict__ dist,
@@ -221,10 +255,11 @@ __device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepA
                                              uint32_t warp_thr, uint32_t cta_thr) {
   constexpr uint32_t NW = BLOCK / 32;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const uint2* __restrict__ edges = a.g.edges;
+  const void* __restrict__ edges = a.g.edges;
+  const uint32_t wbits = a.g.wbits;
   bool ovf = false;
   auto relax = [&](uint32_t e, uint32_t du) {
-    const uint2 ed = __ldg(edges + e);
+    const uint2 ed = load_edge<PK>(edges, e, wbits);
     const uint32_t nd = add_sat(du, ed.y, ovf);
     if (nd < ld_cg(dist + ed.x)) {
       const uint32_t old = atomicMin(dist + ed.x, nd);
@@ -363,7 +398,7 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
 
 // One superstep; BINS selects the degree-binned push advance instead of the
 // merge-path one (pull is the same merge-path sweep in both).
-template <int BLOCK, int EPT, bool BINS>
+template <int BLOCK, int EPT, bool BINS, bool PK>
 __global__ void __launch_bounds__(BLOCK) k_superstep(StepArgs a, cudaGraphConditionalHandle cond, int use_cond) {
   extern __shared__ __align__(16) unsigned char smraw[];
   MPSmem<BLOCK, EPT>& sm = *reinterpret_cast<MPSmem<BLOCK, EPT>*>(smraw);
@@ -380,15 +415,15 @@ __global__ void __launch_bounds__(BLOCK) k_superstep(StepArgs a, cudaGraphCondit
   if (f > 0) {
     if (mode == MODE_PUSH) {
       if (BINS)
-        bins_advance<BLOCK, EPT>(sm, a, f, E, a.fr.fv[p], a.fr.fr[p], a.fr.fs[p], dist, bm_cur, bm_next,
+        bins_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fv[p], a.fr.fr[p], a.fr.fs[p], dist, bm_cur, bm_next,
                                  &ctl->cnt[p ^ 1u], a.fr.fv[p ^ 1u], a.fr.fr[p ^ 1u], a.fr.fs[p ^ 1u],
                                  ctl->warp_thr, ctl->cta_thr);
       else
-        mp_advance<BLOCK, EPT, false>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], a.g.edges, dist, bm_cur,
+        mp_advance<BLOCK, EPT, false, PK>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], a.g.edges, dist, bm_cur,
                                       bm_next, &ctl->cnt[p ^ 1u], a.fr.fv[p ^ 1u], a.fr.fr[p ^ 1u],
                                       a.fr.fs[p ^ 1u]);
     } else {
-      mp_advance<BLOCK, EPT, true>(sm, a, a.g.np, a.g.m, a.g.ps, a.g.ps, a.g.pv, a.g.t_edges, dist, bm_cur,
+      mp_advance<BLOCK, EPT, true, PK>(sm, a, a.g.np, a.g.m, a.g.ps, a.g.ps, a.g.pv, a.g.t_edges, dist, bm_cur,
                                    bm_next, &ctl->cnt[p ^ 1u], a.fr.fv[p ^ 1u], a.fr.fr[p ^ 1u],
                                    a.fr.fs[p ^ 1u]);
     }
@@ -466,11 +501,15 @@ __global__ void k_init_tail(StepArgs a, RunParams rp) {
 
 constexpr int kBlock = 256;
 constexpr int kEpt = 8;
-constexpr int kVariants = 2;   // 0 merge-path push, 1 degree-binned push
+constexpr int kVariants = 4;   // bit 0: degree-binned push (else merge-path); bit 1: packed edges
 
 void* superstep_fn(int variant) {
-  return variant == 1 ? reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, true>)
-                      : reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, false>);
+  switch (variant) {
+    case 1: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, true, false>);
+    case 2: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, false, true>);
+    case 3: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, true, true>);
+    default: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, false, false>);
+  }
 }
 
 size_t superstep_smem(int) { return sizeof(MPSmem<kBlock, kEpt>); }
@@ -503,7 +542,7 @@ gg_status ensure_workspace(gg_graph* g) {
 }
 
 int superstep_grid(int variant) {
-  static int cached[kVariants] = {0, 0};
+  static int cached[kVariants] = {0, 0, 0, 0};
   if (cached[variant]) return cached[variant];
   const DeviceInfo di = device_info();
   int per_sm = 0;
@@ -554,7 +593,7 @@ gg_status build_graph_exec(gg_graph* g, int variant) {
 gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s) {
   gg_status st = ensure_workspace(g);
   if (st != GG_OK) return st;
-  const int variant = o.lb_mode == GG_LB_BINS ? 1 : 0;
+  const int variant = (o.lb_mode == GG_LB_BINS ? 1 : 0) | (g->dg.packed ? 2 : 0);
   BspWorkspace& w = g->bsp;
   RunParams rp;
   rp.src = src;
@@ -586,13 +625,14 @@ gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o
     const int grid = superstep_grid(variant);
     const size_t smem = superstep_smem(variant);
     cudaGraphConditionalHandle none = 0;
+    int zero = 0;
     uint32_t* h_running = &g->h_ctl->running;
     uint32_t launched = 0;
     uint32_t check_every = 1;
     for (;;) {
       for (uint32_t k = 0; k < check_every; ++k) {
-        if (variant == 1) k_superstep<kBlock, kEpt, true><<<grid, kBlock, smem, s>>>(a, none, 0);
-        else k_superstep<kBlock, kEpt, false><<<grid, kBlock, smem, s>>>(a, none, 0);
+        void* args[] = {&a, &none, &zero};
+        GG_CK(cudaLaunchKernel(superstep_fn(variant), dim3(grid), dim3(kBlock), args, smem, s));
         ++launched;
       }
       GG_CK(cudaGetLastError());
@@ -615,7 +655,7 @@ gg_status bsp_read_ctl(gg_graph* g, cudaStream_t s) {
 
 gg_status bsp_release(gg_graph* g) {
   BspWorkspace& w = g->bsp;
-  for (int i = 0; i < 3; ++i) {
+  for (int i = 0; i < kVariants; ++i) {
     if (w.exec[i]) cudaGraphExecDestroy(w.exec[i]);
     if (w.graph[i]) cudaGraphDestroy(w.graph[i]);
     w.exec[i] = nullptr;

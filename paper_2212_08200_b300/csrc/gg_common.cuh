@@ -2,8 +2,12 @@
 //
 // Data layout in HBM (one graph handle):
 //   ro      u32[n+1]   CSR row offsets (push direction)
-//   edges   uint2[m]   {col, weight} interleaved: one 8-byte load per edge
-//   t_ro / t_edges     the transpose (CSC) for pull; aliases ro/edges when the
+//   edges   uint2[m]   {col, weight} interleaved: one 8-byte load per edge, or
+//   edges4  u32[m]     the packed form (col << wbits) | weight, used whenever the
+//                      column bits of n-1 plus the bits of the largest weight
+//                      fit in 32 (halves the edge stream; e.g. RMAT-22 with
+//                      weights <= 255 uses 22 + 10 bits)
+//   t_ro / t_edges(4)  the transpose (CSC) for pull; aliases ro/edges when the
 //                      graph is symmetric
 //   pv, ps  u32[np]    vertices with a non-empty CSC row and that row's start
 //                      (the entry list of the pull sweep)
@@ -57,11 +61,13 @@ struct Ctl {
 struct DevGraph {
   uint32_t n, m, np, nwords;
   const uint32_t* ro;
-  const uint2* edges;
+  const void* edges;       // uint2[m] or, when packed, u32[m]
   const uint32_t* t_ro;
-  const uint2* t_edges;
+  const void* t_edges;
   const uint32_t* pv;
   const uint32_t* ps;
+  uint32_t packed;         // 1: edges are (col << wbits) | weight
+  uint32_t wbits;
 };
 
 struct Frontier {
@@ -74,6 +80,45 @@ struct Frontier {
 #ifdef __CUDACC__
 // L2-coherent load (bypasses L1): used for values other CTAs update with atomics.
 __device__ __forceinline__ uint32_t ld_cg(const uint32_t* p) { return __ldcg(p); }
+
+// One edge as {col, weight} from either edge encoding.
+template <bool PK>
+__device__ __forceinline__ uint2 load_edge(const void* base, uint32_t e, uint32_t wbits) {
+  if (PK) {
+    const uint32_t x = __ldg(static_cast<const uint32_t*>(base) + e);
+    return make_uint2(x >> wbits, x & ((1u << wbits) - 1u));
+  } else {
+    return __ldg(static_cast<const uint2*>(base) + e);
+  }
+}
+
+// Eight consecutive edges starting at e (e a multiple of 8, buffer 256-byte
+// aligned) with 16-byte vector loads.
+template <bool PK>
+__device__ __forceinline__ void load_edges8(const void* base, uint32_t e, uint32_t wbits, uint32_t* col,
+                                            uint32_t* w) {
+  if (PK) {
+    const uint4* p = reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(base) + e);
+    const uint4 q0 = __ldg(p), q1 = __ldg(p + 1);
+    const uint32_t x[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+    const uint32_t mask = (1u << wbits) - 1u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      col[k] = x[k] >> wbits;
+      w[k] = x[k] & mask;
+    }
+  } else {
+    const uint4* p = reinterpret_cast<const uint4*>(static_cast<const uint2*>(base) + e);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint4 q = __ldg(p + k);
+      col[2 * k] = q.x;
+      w[2 * k] = q.y;
+      col[2 * k + 1] = q.z;
+      w[2 * k + 1] = q.w;
+    }
+  }
+}
 
 // saturating distance add; flags overflow when the sum does not fit below kInf.
 __device__ __forceinline__ uint32_t add_sat(uint32_t d, uint32_t w, bool& ovf) {

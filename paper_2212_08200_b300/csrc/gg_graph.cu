@@ -38,10 +38,25 @@ __global__ void k_validate(uint32_t n, uint32_t m, const uint32_t* __restrict__ 
 }
 
 __global__ void k_interleave(uint32_t m, const uint32_t* __restrict__ col, const uint32_t* __restrict__ w,
-                             uint2* __restrict__ out) {
+                             uint2* __restrict__ out, uint32_t* __restrict__ wmax) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
-    out[e] = make_uint2(col[e], w[e]);
+  uint32_t mx = 0;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const uint32_t we = w[e];
+    out[e] = make_uint2(col[e], we);
+    mx = max(mx, we);
+  }
+  for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_down_sync(0xFFFFFFFFu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(wmax, mx);
+}
+
+// {col, w} -> (col << wbits) | w
+__global__ void k_pack(uint32_t m, const uint2* __restrict__ in, uint32_t* __restrict__ out, uint32_t wbits) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const uint2 x = in[e];
+    out[e] = (x.x << wbits) | x.y;
+  }
 }
 
 __global__ void k_count_in(uint32_t m, const uint2* __restrict__ edges, uint32_t* __restrict__ cnt) {
@@ -172,6 +187,8 @@ gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m64, const uint32_t* ro_
   g->bytes = sizeof(uint32_t) * ((size_t)n + 1) + sizeof(uint2) * std::max<size_t>(m, 1);
   GG_CK(cudaMemcpyAsync(g->ro, ro_in, sizeof(uint32_t) * ((size_t)n + 1),
                         dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  uint32_t wmax = 0;
+  uint32_t* wmax_d = nullptr;
   const uint32_t* dcol = col_in;
   const uint32_t* dw = w_in;
   uint32_t* tmp = nullptr;
@@ -197,8 +214,12 @@ gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m64, const uint32_t* ro_
       if (herr & 1u) return fail(GG_ERR_INVALID_ARG, "row_offsets must be non-decreasing");
       if (herr & 2u) return fail(GG_ERR_INVALID_ARG, "col_indices must be < n");
     }
-    k_interleave<<<grid_for(m), 256, 0, s>>>(m, dcol, dw, g->edges);
+    GG_CK(cudaMallocAsync(&wmax_d, sizeof(uint32_t), s));
+    GG_CK(cudaMemsetAsync(wmax_d, 0, sizeof(uint32_t), s));
+    k_interleave<<<grid_for(m), 256, 0, s>>>(m, dcol, dw, g->edges, wmax_d);
     GG_CK(cudaGetLastError());
+    GG_CK(cudaMemcpyAsync(&wmax, wmax_d, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    GG_CK(cudaFreeAsync(wmax_d, s));
   } else if (dev && validate) {
     uint32_t h[2] = {0, 0};
     GG_CK(cudaMemcpyAsync(h, g->ro, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
@@ -254,13 +275,39 @@ gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m64, const uint32_t* ro_
   }
   GG_CK(cudaStreamSynchronize(s));
 
+  // packed 4-byte edges when the column and weight bits fit in one word
+  uint32_t colbits = 1;
+  while (colbits < 32 && ((uint64_t)(n - 1) >> colbits) != 0) ++colbits;
+  const uint32_t wbits = 32 - colbits;
+  const bool pack = m > 0 && !(flags & GG_NO_PACK) && colbits < 32 && (uint64_t)wmax < (1ull << wbits);
+  g->dg.packed = 0;
+  g->dg.wbits = wbits;
+  if (pack) {
+    GG_CK(cudaMalloc(&g->edges4, sizeof(uint32_t) * (size_t)m));
+    k_pack<<<grid_for(m), 256, 0, s>>>(m, g->edges, g->edges4, wbits);
+    GG_CK(cudaGetLastError());
+    if (!g->symmetric) {
+      GG_CK(cudaMalloc(&g->t_edges4, sizeof(uint32_t) * (size_t)m));
+      k_pack<<<grid_for(m), 256, 0, s>>>(m, g->t_edges, g->t_edges4, wbits);
+      GG_CK(cudaGetLastError());
+    } else {
+      g->t_edges4 = g->edges4;
+    }
+    GG_CK(cudaStreamSynchronize(s));
+    if (g->t_edges != g->edges) cudaFree(g->t_edges);
+    cudaFree(g->edges);
+    g->edges = g->t_edges = nullptr;
+    g->bytes -= (g->symmetric ? 1 : 2) * sizeof(uint2) * (size_t)m;
+    g->bytes += (g->symmetric ? 1 : 2) * sizeof(uint32_t) * (size_t)m;
+    g->dg.packed = 1;
+  }
   g->dg.n = n;
   g->dg.m = m;
   g->dg.nwords = (n + 31) / 32;
   g->dg.ro = g->ro;
-  g->dg.edges = g->edges;
+  g->dg.edges = pack ? static_cast<const void*>(g->edges4) : static_cast<const void*>(g->edges);
   g->dg.t_ro = g->t_ro;
-  g->dg.t_edges = g->t_edges;
+  g->dg.t_edges = pack ? static_cast<const void*>(g->t_edges4) : static_cast<const void*>(g->t_edges);
   g->dg.pv = g->pv;
   g->dg.ps = g->ps;
   return GG_OK;
@@ -269,6 +316,9 @@ gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m64, const uint32_t* ro_
 void graph_free(gg_graph* g) {
   if (g->t_ro && g->t_ro != g->ro) cudaFree(g->t_ro);
   if (g->t_edges && g->t_edges != g->edges) cudaFree(g->t_edges);
+  if (g->t_edges4 && g->t_edges4 != g->edges4) cudaFree(g->t_edges4);
+  cudaFree(g->edges4);
+  g->edges4 = g->t_edges4 = nullptr;
   cudaFree(g->ro);
   cudaFree(g->edges);
   cudaFree(g->pv);

@@ -37,9 +37,9 @@ struct BspWorkspace {
   size_t bytes = 0;
   // CUDA graph with a conditional WHILE node around one superstep kernel,
   // one per load-balance variant.
-  cudaGraph_t graph[3] = {nullptr, nullptr, nullptr};
-  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
-  int grid[3] = {0, 0, 0};
+  cudaGraph_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};
+  int grid[4] = {0, 0, 0, 0};
 };
 
 // Workspace of the asynchronous persistent path.
@@ -66,6 +66,8 @@ struct gg_graph {
   uint2* edges = nullptr;
   uint32_t* t_ro = nullptr;
   uint2* t_edges = nullptr;
+  uint32_t* edges4 = nullptr;     // packed edges (replace edges/t_edges when used)
+  uint32_t* t_edges4 = nullptr;
   uint32_t* pv = nullptr;
   uint32_t* ps = nullptr;
   size_t bytes = 0;

@@ -92,10 +92,10 @@ def test_grid64_config(mode):
 
 
 @pytest.mark.parametrize("mode", MODES)
-@pytest.mark.parametrize("sym", [True, False])
-def test_rmat16_multi_tile(mode, sym):
+@pytest.mark.parametrize("sym,pack", [(True, True), (False, True), (True, False), (False, False)])
+def test_rmat16_multi_tile(mode, sym, pack):
     ro, col, w, src = graphgen.workload("rmat16")
-    g = gg().Graph(ro, col, w, symmetric=sym)
+    g = gg().Graph(ro, col, w, symmetric=sym, pack=pack)
     ref = oracle.dijkstra(ro, col, w, src)
     for s in (src, int(graphgen.sample_sources(ro, 1, seed=5)[0])):
         got, st = run(g, s, *mode)
@@ -210,7 +210,9 @@ def test_long_path_many_supersteps():
 
 def test_ties_zero_and_large_weights():
     ro, col, _ = graphgen.grid(57)                                 # ragged n = 3249 (not a multiple of 32)
-    for wval in (0, 7, 2 ** 20):
+    # n = 3249 needs 12 column bits, leaving 20 weight bits: 2^20 - 1 is the
+    # largest weight stored packed, 2^20 falls back to 8-byte edges
+    for wval in (0, 7, 2 ** 20 - 1, 2 ** 20):
         w = np.full(col.shape[0], wval, np.uint32)
         g = gg().Graph(ro, col, w, symmetric=True)
         for mode in MODES:
