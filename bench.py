@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--policy", default="graph", choices=["graph", "async", "host"])
     p.add_argument("--direction", default="auto", choices=["auto", "push", "pull"])
     p.add_argument("--lb", default="mp", choices=["mp", "bins"])
+    p.add_argument("--delta", type=int, default=0, help="near-far bucket width (0 = graph default, -1 = none)")
     p.add_argument("--alpha", type=int, default=0)
     p.add_argument("--beta", type=int, default=0)
     p.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -211,7 +212,9 @@ def main():
     g = gg.Graph(ro, col, w, symmetric=True, stream=stream)
     dist_t = torch.empty(n, dtype=torch.uint32, device="cuda")
     lb = {"mp": gg.GG_LB_MERGE_PATH, "bins": gg.GG_LB_BINS}[args.lb]
-    opts = gg.make_options(policy=policy, direction=direction, lb_mode=lb, pull_alpha=args.alpha, pull_beta=args.beta)
+    delta = gg.GG_DELTA_NONE if args.delta < 0 else args.delta
+    opts = gg.make_options(policy=policy, direction=direction, lb_mode=lb, pull_alpha=args.alpha, pull_beta=args.beta,
+                           delta=delta)
 
     def step():
         gg.gg_sssp_ex(g.handle, src, dist_t, opts, stream)
@@ -219,8 +222,8 @@ def main():
     # correctness of what is timed: stats run + invariant-free hash check vs the oracle's stored hash
     st = gg.gg_stats()
     gg.gg_sssp_ex(g.handle, src, dist_t, gg.make_options(policy=policy, direction=direction, lb_mode=lb,
-                                                         pull_alpha=args.alpha, pull_beta=args.beta, stats=st),
-                  stream)
+                                                         pull_alpha=args.alpha, pull_beta=args.beta, stats=st,
+                                                         delta=delta), stream)
     d_host = dist_t.cpu().numpy()
     reach = d_host != gg.GG_INF
     m_trav = int(np.diff(ro.astype(np.int64))[reach].sum())
@@ -231,7 +234,7 @@ def main():
         step()
     torch.cuda.synchronize()
     # fixed per-call cost: init kernels + graph launch + one single-vertex superstep
-    fixed_opts = gg.make_options(policy=policy, direction=gg.GG_DIR_PUSH, max_iterations=1)
+    fixed_opts = gg.make_options(policy=policy, direction=gg.GG_DIR_PUSH, max_iterations=1, delta=gg.GG_DELTA_NONE)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     fixed = []
     for _ in range(5):
@@ -316,7 +319,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": workload_desc(args.workload), "n": n, "m": m, "source": int(src),
-                       "m_trav": m_trav, "n_reach": n_reach, "policy": args.policy, "direction": args.direction, "lb": args.lb,
+                       "m_trav": m_trav, "n_reach": n_reach, "policy": args.policy, "direction": args.direction, "lb": args.lb, "delta": args.delta,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": f"inputs larger than L2 (edge array {8 * m / 2**20:.0f} MiB > 126 MiB L2); "
                              f"dist re-initialised every step",

@@ -55,7 +55,7 @@ extern "C" {
 #endif
 
 #define GG_INF 0xFFFFFFFFu
-#define GG_ABI_VERSION 1
+#define GG_ABI_VERSION 2
 
 typedef struct gg_graph* gg_graph_t;
 
@@ -123,14 +123,22 @@ typedef struct {
     uint32_t pull_beta;        /* AUTO direction: back to push when frontier vertices <
                                   n/beta (0 = auto)                                     */
     uint32_t max_iterations;   /* BSP superstep cap (0 = n + 2)                          */
-    uint64_t watchdog_ns;      /* ASYNC: give up and report GG_ERR_TIMEOUT after this
-                                  long without the queue draining (0 = 10 s)           */
+    uint64_t watchdog_ns;      /* give up and report GG_ERR_TIMEOUT after this long
+                                  (0 = 10 s for ASYNC, 60 s for the BSP policies)      */
     gg_stats* stats;           /* host; if not NULL the call synchronises the stream
                                   and fills it                                          */
     uint32_t* trace;           /* device u32[trace_cap*4] or NULL: per superstep
-                                  (frontier size, frontier edges, direction, 0)        */
+                                  (frontier size, frontier edges, kind 0 push / 1 pull
+                                  / 2 near-far split, next frontier size)              */
     uint32_t trace_cap;
+    uint32_t delta;            /* near-far bucket width: vertices improved to a distance
+                                  below the current threshold stay in the frontier, the
+                                  rest wait in a far pile until the frontier empties and
+                                  the threshold rises by delta (0 = the graph's default,
+                                  GG_DELTA_NONE = plain frontier loop, no buckets)       */
 } gg_options;
+
+#define GG_DELTA_NONE 0xFFFFFFFFu
 
 /* ---- graph (Sec. IV-A, Listing 1) ------------------------------------- */
 
@@ -182,6 +190,31 @@ gg_status gg_sssp(gg_graph_t g, uint32_t src, uint32_t* dist_out, cudaStream_t s
 /* As gg_sssp with explicit options (opt may be NULL for the defaults). */
 gg_status gg_sssp_ex(gg_graph_t g, uint32_t src, uint32_t* dist_out, const gg_options* opt,
                      cudaStream_t stream);
+
+/* ---- batched multi-source SSSP ------------------------------------------ */
+
+/* k independent single-source runs of the same frontier loop (Listing 4)
+ * fused into one bulk-synchronous loop: the frontier holds vertices with a
+ * 64-bit mask of the sources whose distance there just improved, so one read
+ * of an edge serves every such source.  Sources are processed in groups of
+ * 64 (one fused loop per group).
+ *   srcs      host u32[k], each < n (duplicates allowed)
+ *   k         >= 1
+ *   dist_out  device u32[n*k], caller-owned, vertex-major:
+ *             dist_out[v*k + s] = distance from srcs[s] to v (GG_INF if none)
+ * Asynchronous on `stream` (the source list is copied before the call
+ * returns).  Push traversal only.  The first call allocates the handle's
+ * batch workspace (about 60n bytes).  Errors: GG_ERR_INVALID_ARG (null
+ * pointers, k == 0, a source >= n), GG_ERR_OUT_OF_MEMORY, GG_ERR_CUDA;
+ * device status (overflow, superstep cap) via gg_graph_check. */
+gg_status gg_sssp_batch(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t* dist_out,
+                        cudaStream_t stream);
+
+/* As gg_sssp_batch with options: max_iterations and stats are honoured
+ * (stats summed over the 64-source groups; setting stats synchronises the
+ * stream); policy, direction and load-balance fields are ignored. */
+gg_status gg_sssp_batch_ex(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t* dist_out,
+                           const gg_options* opt, cudaStream_t stream);
 
 /* ---- SSSP without any device allocation ---------------------------------- */
 

@@ -20,8 +20,9 @@ import numpy as np
 __all__ = [
     "GGError", "GG_INF", "GG_DEVICE_PTRS", "GG_SYMMETRIC", "GG_NO_VALIDATE",
     "GG_POLICY_BSP_GRAPH", "GG_POLICY_ASYNC_PERSISTENT", "GG_POLICY_BSP_HOST",
-    "GG_DIR_AUTO", "GG_DIR_PUSH", "GG_DIR_PULL", "GG_LB_AUTO", "GG_LB_MERGE_PATH", "GG_LB_BINS",
+    "GG_DIR_AUTO", "GG_DIR_PUSH", "GG_DIR_PULL", "GG_LB_AUTO", "GG_LB_MERGE_PATH", "GG_LB_BINS", "GG_DELTA_NONE",
     "gg_graph_create_csr", "gg_graph_destroy", "gg_graph_info", "gg_graph_check", "gg_sssp", "gg_sssp_ex",
+    "gg_sssp_batch",
     "gg_status_string", "gg_last_error", "gg_abi_version", "gg_sssp_noalloc", "GG_NOALLOC_MAX_VERTICES",
     "Graph", "lib_path", "load",
 ]
@@ -36,6 +37,7 @@ GG_DEVICE_PTRS, GG_SYMMETRIC, GG_NO_VALIDATE, GG_NO_PACK = 0x1, 0x2, 0x4, 0x8
 GG_POLICY_BSP_GRAPH, GG_POLICY_ASYNC_PERSISTENT, GG_POLICY_BSP_HOST = 0, 1, 2
 GG_DIR_AUTO, GG_DIR_PUSH, GG_DIR_PULL = 0, 1, 2
 GG_LB_AUTO, GG_LB_MERGE_PATH, GG_LB_BINS = 0, 1, 2
+GG_DELTA_NONE = 0xFFFFFFFF
 
 STATUS = {0: "GG_OK", 1: "GG_ERR_INVALID_ARG", 2: "GG_ERR_OUT_OF_MEMORY", 3: "GG_ERR_CUDA",
           4: "GG_ERR_TIMEOUT", 5: "GG_ERR_BUSY", 6: "GG_ERR_NOT_READY", 7: "GG_ERR_OVERFLOW",
@@ -63,7 +65,8 @@ class gg_options(ctypes.Structure):
                 ("lb_mode", ctypes.c_int), ("warp_threshold", ctypes.c_uint32), ("cta_threshold", ctypes.c_uint32),
                 ("pull_alpha", ctypes.c_uint32), ("pull_beta", ctypes.c_uint32),
                 ("max_iterations", ctypes.c_uint32), ("watchdog_ns", ctypes.c_uint64),
-                ("stats", ctypes.POINTER(gg_stats)), ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_uint32)]
+                ("stats", ctypes.POINTER(gg_stats)), ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_uint32),
+                ("delta", ctypes.c_uint32)]
 
 
 def lib_path() -> str:
@@ -91,6 +94,8 @@ def load():
             "gg_sssp": (ctypes.c_int, [vp, u32, vp, vp]),
             "gg_sssp_ex": (ctypes.c_int, [vp, u32, vp, ctypes.POINTER(gg_options), vp]),
             "gg_sssp_noalloc": (ctypes.c_int, [u32, u64, vp, vp, vp, u32, vp, vp]),
+            "gg_sssp_batch": (ctypes.c_int, [vp, P32, u32, vp, vp]),
+            "gg_sssp_batch_ex": (ctypes.c_int, [vp, P32, u32, vp, ctypes.POINTER(gg_options), vp]),
             "gg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "gg_last_error": (ctypes.c_char_p, []),
             "gg_abi_version": (u32, []),
@@ -184,12 +189,13 @@ def gg_graph_check(handle: int):
 
 def make_options(policy=GG_POLICY_BSP_GRAPH, direction=GG_DIR_AUTO, lb_mode=GG_LB_AUTO, warp_threshold=0,
                  cta_threshold=0, pull_alpha=0, pull_beta=0, max_iterations=0, watchdog_ns=0, stats=None,
-                 trace=None, trace_cap=0) -> gg_options:
+                 trace=None, trace_cap=0, delta=0) -> gg_options:
     o = gg_options()
     load().gg_options_default(ctypes.byref(o))
     o.policy, o.direction, o.lb_mode = policy, direction, lb_mode
     o.warp_threshold, o.cta_threshold = warp_threshold, cta_threshold
     o.pull_alpha, o.pull_beta, o.max_iterations, o.watchdog_ns = pull_alpha, pull_beta, max_iterations, watchdog_ns
+    o.delta = delta
     if stats is not None:
         o.stats = ctypes.pointer(stats)
     if trace is not None:
@@ -212,6 +218,21 @@ def gg_sssp_ex(handle: int, src: int, dist_out, options: gg_options | None = Non
         raise ValueError("dist_out must be a CUDA tensor")
     _check(load().gg_sssp_ex(handle, src, p, ctypes.byref(options) if options is not None else None,
                              _stream_ptr(stream)), "gg_sssp_ex")
+
+
+def gg_sssp_batch(handle: int, srcs, dist_out, stream=None, options: gg_options | None = None):
+    """Distances from every source in srcs (host uint32 array of k) into
+    dist_out (CUDA uint32 tensor of n*k, dist_out[v*k + s]), async."""
+    srcs = np.ascontiguousarray(srcs, dtype=np.uint32)
+    p, dev = _ptr(dist_out)
+    if not dev:
+        raise ValueError("dist_out must be a CUDA tensor")
+    sp = srcs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+    if options is None:
+        _check(load().gg_sssp_batch(handle, sp, srcs.shape[0], p, _stream_ptr(stream)), "gg_sssp_batch")
+    else:
+        _check(load().gg_sssp_batch_ex(handle, sp, srcs.shape[0], p, ctypes.byref(options), _stream_ptr(stream)),
+               "gg_sssp_batch_ex")
 
 
 GG_NOALLOC_MAX_VERTICES = 1 << 20
@@ -247,6 +268,15 @@ class Graph:
         else:
             gg_sssp(self.handle, src, dist_out, stream)
         return dist_out
+
+    def sssp_batch(self, srcs, dist_out=None, stream=None, **opts):
+        """(n, k) view of the vertex-major distance matrix."""
+        import torch
+        k = len(srcs)
+        if dist_out is None:
+            dist_out = torch.empty(self.n * k, dtype=torch.uint32, device="cuda")
+        gg_sssp_batch(self.handle, srcs, dist_out, stream, make_options(**opts) if opts else None)
+        return dist_out.view(self.n, k)
 
     def check(self):
         gg_graph_check(self.handle)

@@ -139,6 +139,7 @@ gg_status gg_graph_destroy(gg_graph_t g) {
     if (g->ev_valid) cudaEventSynchronize(g->last_ev);
     bsp_release(g);
     async_release(g);
+    batch_release(g);
     graph_free(g);
     if (g->last_ev) cudaEventDestroy(g->last_ev);
     if (g->h_ctl) cudaFreeHost(g->h_ctl);
@@ -152,7 +153,7 @@ gg_status gg_graph_info(gg_graph_t g, uint32_t* n, uint64_t* m, uint64_t* device
   if (!g) return fail(GG_ERR_INVALID_ARG, "graph is NULL");
   if (n) *n = g->n;
   if (m) *m = g->m;
-  if (device_bytes) *device_bytes = g->bytes + g->bsp.bytes + g->async.bytes;
+  if (device_bytes) *device_bytes = g->bytes + g->bsp.bytes + g->async.bytes + batch_bytes(g);
   return GG_OK;
 }
 
@@ -161,6 +162,9 @@ static gg_status collect(gg_graph* g, cudaStream_t s, gg_stats* st_out) {
   gg_stats st{};
   if (g->last_policy == GG_POLICY_ASYNC_PERSISTENT) {
     gg_status r = async_status(g, &ds, &st);
+    if (r != GG_OK) return r;
+  } else if (g->last_policy == kLastBatch) {
+    gg_status r = batch_status(g, &ds);
     if (r != GG_OK) return r;
   } else if (g->last_policy >= 0) {
     gg_status r = bsp_read_ctl(g, s);
@@ -230,6 +234,44 @@ gg_status gg_sssp_ex(gg_graph_t g, uint32_t src, uint32_t* dist_out, const gg_op
 
 gg_status gg_sssp(gg_graph_t g, uint32_t src, uint32_t* dist_out, cudaStream_t stream) {
   return gg_sssp_ex(g, src, dist_out, nullptr, stream);
+}
+
+gg_status gg_sssp_batch_ex(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t* dist_out,
+                           const gg_options* opt, cudaStream_t stream) {
+  if (!g) return fail(GG_ERR_INVALID_ARG, "graph is NULL");
+  if (!srcs || !dist_out) return fail(GG_ERR_INVALID_ARG, "srcs/dist_out is NULL");
+  if (k == 0) return fail(GG_ERR_INVALID_ARG, "k must be >= 1");
+  for (uint32_t i = 0; i < k; ++i)
+    if (srcs[i] >= g->n) return fail(GG_ERR_INVALID_ARG, "a source is >= n");
+  gg_options o;
+  gg_options_default(&o);
+  if (opt) {
+    if (opt->struct_size != sizeof(gg_options)) return fail(GG_ERR_INVALID_ARG, "gg_options.struct_size mismatch");
+    o = *opt;
+  }
+  if (o.stats) *o.stats = gg_stats{};
+  int dev = -1;
+  GG_CK(cudaGetDevice(&dev));
+  if (dev != g->device) return fail(GG_ERR_INVALID_ARG, "current device differs from the graph's device");
+  std::lock_guard<std::mutex> lk(g->mu);
+  gg_status st = order_after_previous(g, stream);
+  if (st != GG_OK) return st;
+  st = batch_run(g, srcs, k, dist_out, o, stream);
+  if (st != GG_OK) return st;
+  g->last_policy = kLastBatch;
+  st = record_call(g, stream);
+  if (st != GG_OK) return st;
+  if (o.stats) {
+    const gg_status ds = status_from_device(o.stats->device_status);
+    o.stats->device_status = (uint32_t)ds;
+    if (ds != GG_OK) set_error("device status: " + std::string(gg_status_string(ds)));
+    return ds;
+  }
+  return GG_OK;
+}
+
+gg_status gg_sssp_batch(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t* dist_out, cudaStream_t stream) {
+  return gg_sssp_batch_ex(g, srcs, k, dist_out, nullptr, stream);
 }
 
 }  // extern "C"

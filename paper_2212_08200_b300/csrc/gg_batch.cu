@@ -1,0 +1,439 @@
+// gg_batch.cu -- batched multi-source SSSP: k independent single-source runs
+// of the paper's frontier loop (Listing 4) fused into one bulk-synchronous
+// loop over a shared frontier.
+//
+// Distance matrix: dist[v*k + s] (vertex-major), so the up-to-64 distances of
+// one vertex row are contiguous: lane l of a warp owns sources l and l+32 of
+// the current 64-source group, and every relaxation of an edge (u, v) reads
+// and updates v's row with two coalesced 128-byte accesses.  The col/weight
+// stream of an edge is read once for all sources whose distance at u
+// improved.
+//
+// Frontier entry = vertex u + a 64-bit mask of the sources whose dist[u][s]
+// decreased in the previous superstep (only those sources are relaxed from
+// u).  The mask array M_next is accumulated with atomicOr; the edge that takes
+// a vertex's mask from 0 to non-zero appends the vertex to the next sparse
+// frontier, with the same block-aggregated append (one 64-bit atomicAdd per
+// CTA tile returning queue position and edge-prefix base) as the
+// single-source filter.  Candidacy comes from the pre-check  nd < dist[v][s]
+// read before the atomicMin: after the atomic, dist[v][s] <= nd < that value,
+// so v did improve in this superstep and belongs in the next frontier; the
+// atomic itself is fire-and-forget.
+//
+// Three rotating frontier queues and mask arrays: superstep t reads F_t and
+// M_t, builds F_{t+1}/M_{t+1}, and zeroes the masks of F_{t-1}'s vertices
+// (their list is intact in the third queue).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "gg_host.h"
+
+namespace gg {
+
+struct BatchCtl {
+  unsigned long long cnt[3];
+  uint32_t iter, done_ctas, status, running, max_iter;
+  uint32_t k, col0, kg;
+  uint32_t max_frontier;
+  uint32_t* dist;
+  unsigned long long edges_scanned, frontier_total;
+};
+
+struct BatchBufs {
+  uint32_t* fv[3];
+  uint32_t* fr[3];
+  uint32_t* fs[3];
+  unsigned long long* mask[3];
+  BatchCtl* ctl;
+};
+
+namespace {
+
+constexpr int kBB = 256;
+constexpr int kBNW = kBB / 32;
+constexpr int kBTile = 1024;
+constexpr int kBWarpEdges = kBTile / kBNW;
+constexpr int kBCap = kBTile + 1;
+
+struct BSmem {
+  uint32_t es[kBCap], eb[kBCap], ev[kBCap];
+  unsigned long long em[kBCap];
+  uint32_t qv[kBCap], qr[kBCap], qd[kBCap];
+  uint32_t wsum[kBNW];
+  uint32_t qn, j, last, ovf;
+  unsigned long long base;
+};
+
+template <bool PK>
+__global__ void __launch_bounds__(kBB) k_batch_superstep(DevGraph g, BatchBufs w, cudaGraphConditionalHandle cond,
+                                                         int use_cond) {
+  __shared__ BSmem sm;
+  BatchCtl* ctl = w.ctl;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t it = ctl->iter;
+  const uint32_t pc = it % 3, pn = (it + 1) % 3, po = (it + 2) % 3;
+  const unsigned long long c = ctl->cnt[pc];
+  const uint32_t F = (uint32_t)(c >> 32), E = (uint32_t)c;
+  const uint32_t K = ctl->k, col0 = ctl->col0;
+  uint32_t* dist = ctl->dist;
+  const unsigned long long* Mc = w.mask[pc];
+  unsigned long long* Mn = w.mask[pn];
+  const uint32_t wbits = g.wbits;
+  // zero the masks of F_{t-1}
+  {
+    const uint32_t Fo = (uint32_t)(ctl->cnt[po] >> 32);
+    const uint32_t* fvo = w.fv[po];
+    unsigned long long* Mo = w.mask[po];
+    for (uint32_t i = blockIdx.x * kBB + tid; i < Fo; i += gridDim.x * kBB) Mo[fvo[i]] = 0ull;
+  }
+  if (tid == 0) {
+    sm.qn = 0;
+    sm.ovf = 0;
+  }
+  __syncthreads();
+  bool ovf = false;
+  const uint32_t e0 = (uint32_t)(((unsigned long long)blockIdx.x * E) / gridDim.x);
+  const uint32_t e1 = (uint32_t)(((unsigned long long)(blockIdx.x + 1) * E) / gridDim.x);
+  if (F > 0 && e0 < e1) {
+    const uint32_t* S = w.fs[pc];
+    if (tid < 32) {
+      const uint32_t j = warp_search_le(S, F, e0);
+      if (tid == 0) sm.j = j;
+    }
+    __syncthreads();
+    uint32_t j = sm.j;
+    for (uint32_t t0 = e0; t0 < e1; t0 += kBTile) {
+      const uint32_t t1 = min(t0 + (uint32_t)kBTile, e1);
+      uint32_t nent = 0;
+      for (;;) {
+        const uint32_t idx = j + nent + tid;
+        bool valid = false;
+        uint32_t s = 0;
+        if (idx < F) {
+          s = S[idx];
+          valid = s < t1;
+        }
+        if (valid) {
+          const uint32_t v = w.fv[pc][idx];
+          sm.es[nent + tid] = s;
+          sm.eb[nent + tid] = w.fr[pc][idx];
+          sm.ev[nent + tid] = v;
+          sm.em[nent + tid] = Mc[v];
+        }
+        const int cnt = __syncthreads_count(valid);
+        nent += (uint32_t)cnt;
+        if (cnt < kBB) break;
+      }
+      // each warp walks a contiguous run of the tile's edges, one edge at a
+      // time across its 32 lanes x 2 source columns
+      const uint32_t wbeg = t0 + warp * kBWarpEdges;
+      for (uint32_t r = 0; r < (uint32_t)kBWarpEdges; r += 32) {
+        const uint32_t gidx = wbeg + r + lane;
+        const bool valid = gidx < t1;
+        uint32_t jj = 0, vv = 0, ww = 0;
+        if (valid) {
+          jj = smem_upper_bound_minus1(sm.es, nent, gidx);
+          const uint2 ed = load_edge<PK>(g.edges, sm.eb[jj] + (gidx - sm.es[jj]), wbits);
+          vv = ed.x;
+          ww = ed.y;
+        }
+        const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
+        if (!vm) break;
+        uint32_t cur_j = 0xFFFFFFFFu, du_lo = kInf, du_hi = kInf;
+        bool act_lo = false, act_hi = false;
+        const int nvalid = __popc(vm);   // valid edges are a prefix of the lanes
+        for (int i = 0; i < nvalid; ++i) {
+          const uint32_t ji = __shfl_sync(0xFFFFFFFFu, jj, i);
+          const uint32_t vi = __shfl_sync(0xFFFFFFFFu, vv, i);
+          const uint32_t wi = __shfl_sync(0xFFFFFFFFu, ww, i);
+          if (ji != cur_j) {
+            cur_j = ji;
+            const uint32_t u = sm.ev[ji];
+            const unsigned long long msk = sm.em[ji];
+            const uint32_t* urow = dist + (size_t)u * K + col0;
+            act_lo = (msk >> lane) & 1ull;
+            act_hi = (msk >> (lane + 32)) & 1ull;
+            du_lo = act_lo ? ld_cg(urow + lane) : kInf;
+            du_hi = act_hi ? ld_cg(urow + lane + 32) : kInf;
+          }
+          uint32_t* vrow = dist + (size_t)vi * K + col0;
+          bool imp_lo = false, imp_hi = false;
+          if (act_lo) {
+            const uint32_t nd = add_sat(du_lo, wi, ovf);
+            if (nd < ld_cg(vrow + lane)) {
+              atomicMin(vrow + lane, nd);
+              imp_lo = true;
+            }
+          }
+          if (act_hi) {
+            const uint32_t nd = add_sat(du_hi, wi, ovf);
+            if (nd < ld_cg(vrow + lane + 32)) {
+              atomicMin(vrow + lane + 32, nd);
+              imp_hi = true;
+            }
+          }
+          const unsigned blo = __ballot_sync(0xFFFFFFFFu, imp_lo);
+          const unsigned bhi = __ballot_sync(0xFFFFFFFFu, imp_hi);
+          if (lane == 0 && (blo | bhi)) {
+            const uint32_t rs = __ldg(g.ro + vi), re = __ldg(g.ro + vi + 1);
+            if (re > rs) {
+              const unsigned long long bits = (unsigned long long)blo | ((unsigned long long)bhi << 32);
+              if (atomicOr(Mn + vi, bits) == 0ull) {
+                const uint32_t q = atomicAdd(&sm.qn, 1u);
+                sm.qv[q] = vi;
+                sm.qr[q] = rs;
+                sm.qd[q] = re - rs;
+              }
+            }
+          }
+        }
+      }
+      // append this tile's new frontier vertices
+      __syncthreads();
+      const uint32_t qn = sm.qn;
+      if (qn) {
+        const uint32_t tot = block_scan_excl<kBB>(sm.qd, qn, sm.wsum);
+        if (tid == 0) sm.base = atomicAdd(&ctl->cnt[pn], ((unsigned long long)qn << 32) | tot);
+        __syncthreads();
+        const uint32_t pos0 = (uint32_t)(sm.base >> 32), eb0 = (uint32_t)sm.base;
+        for (uint32_t i = tid; i < qn; i += kBB) {
+          w.fv[pn][pos0 + i] = sm.qv[i];
+          w.fr[pn][pos0 + i] = sm.qr[i];
+          w.fs[pn][pos0 + i] = eb0 + sm.qd[i];
+        }
+        __syncthreads();
+        if (tid == 0) sm.qn = 0;
+      }
+      __syncthreads();
+      j = j + nent - 1;
+    }
+  }
+  if (ovf) sm.ovf = 1u;
+  __syncthreads();
+  if (tid == 0) {
+    if (sm.ovf) atomicOr(&ctl->status, DS_OVERFLOW);
+    __threadfence();
+    sm.last = (atomicAdd(&ctl->done_ctas, 1u) == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (sm.last && tid == 0) {
+    __threadfence();
+    const unsigned long long cn = atomicAdd(&ctl->cnt[pn], 0ull);
+    const uint32_t fn = (uint32_t)(cn >> 32);
+    if (F > 0) {
+      ctl->edges_scanned += E;
+      ctl->frontier_total += F;
+      ctl->max_frontier = max(ctl->max_frontier, F);
+    }
+    ctl->cnt[po] = 0ull;
+    ctl->done_ctas = 0u;
+    ctl->iter = it + 1;
+    bool more = fn != 0;
+    if (more && it + 1 >= ctl->max_iter) {
+      ctl->status |= DS_ITER_CAP;
+      more = false;
+    }
+    ctl->running = more ? 1u : 0u;
+    if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+  }
+}
+
+// every entry of the n x k matrix := INF
+__global__ void k_batch_fill(uint32_t* dist, unsigned long long count) {
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if ((reinterpret_cast<uintptr_t>(dist) & 15u) == 0) {
+    uint4* d4 = reinterpret_cast<uint4*>(dist);
+    const unsigned long long c4 = count / 4;
+    for (unsigned long long i = t; i < c4; i += stride) d4[i] = make_uint4(kInf, kInf, kInf, kInf);
+    for (unsigned long long i = c4 * 4 + t; i < count; i += stride) dist[i] = kInf;
+  } else {
+    for (unsigned long long i = t; i < count; i += stride) dist[i] = kInf;
+  }
+}
+
+// group start: dist[src_s][col0+s] := 0; initial frontier = distinct sources
+// with out-edges, each carrying the mask of its columns.  One CTA of 64.
+__global__ void k_batch_seed(DevGraph g, BatchBufs w, const uint32_t* srcs, uint32_t k, uint32_t col0,
+                             uint32_t kg, uint32_t* dist, uint32_t max_iter) {
+  BatchCtl* ctl = w.ctl;
+  const uint32_t s = threadIdx.x;
+  if (s == 0) {
+    ctl->cnt[0] = 0ull;
+    ctl->cnt[1] = 0ull;
+    ctl->cnt[2] = 0ull;
+    ctl->iter = 0;
+    ctl->done_ctas = 0;
+    ctl->status = 0;
+    ctl->max_iter = max_iter;
+    ctl->k = k;
+    ctl->col0 = col0;
+    ctl->kg = kg;
+    ctl->dist = dist;
+    ctl->max_frontier = 0;
+    ctl->edges_scanned = 0;
+    ctl->frontier_total = 0;
+  }
+  __syncthreads();
+  if (s < kg) {
+    const uint32_t v = srcs[col0 + s];
+    dist[(size_t)v * k + col0 + s] = 0u;
+    const uint32_t rs = g.ro[v], re = g.ro[v + 1];
+    if (re > rs) {
+      if (atomicOr(w.mask[0] + v, 1ull << s) == 0ull) {
+        const unsigned long long b = atomicAdd(&ctl->cnt[0], (1ull << 32) | (re - rs));
+        const uint32_t pos = (uint32_t)(b >> 32);
+        w.fv[0][pos] = v;
+        w.fr[0][pos] = rs;
+        w.fs[0][pos] = (uint32_t)b;
+      }
+    }
+  }
+  __syncthreads();
+  if (s == 0) ctl->running = ctl->cnt[0] != 0ull ? 1u : 0u;
+}
+
+}  // namespace
+
+struct BatchWorkspace {
+  void* block = nullptr;
+  size_t bytes = 0;
+  BatchBufs b{};
+  uint32_t* srcs = nullptr;
+  uint32_t srcs_cap = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int grid = 0;
+  BatchCtl* h_ctl = nullptr;
+};
+
+static gg_status batch_ws(gg_graph* g, BatchWorkspace** out) {
+  if (!g->batch) {
+    BatchWorkspace* w = new BatchWorkspace();
+    const size_t n = std::max<uint32_t>(g->n, 1);
+    auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t total = 9 * r256(4 * n) + 3 * r256(8 * n) + r256(sizeof(BatchCtl));
+    char* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, total);
+    if (e != cudaSuccess) { delete w; return cuda_fail(e, "cudaMalloc(batch workspace)"); }
+    w->block = p;
+    w->bytes = total;
+    size_t off = 0;
+    auto take = [&](size_t b) { char* q = p + off; off += r256(b); return q; };
+    for (int i = 0; i < 3; ++i) {
+      w->b.fv[i] = reinterpret_cast<uint32_t*>(take(4 * n));
+      w->b.fr[i] = reinterpret_cast<uint32_t*>(take(4 * n));
+      w->b.fs[i] = reinterpret_cast<uint32_t*>(take(4 * n));
+    }
+    for (int i = 0; i < 3; ++i) w->b.mask[i] = reinterpret_cast<unsigned long long*>(take(8 * n));
+    w->b.ctl = reinterpret_cast<BatchCtl*>(take(sizeof(BatchCtl)));
+    e = cudaMallocHost(&w->h_ctl, sizeof(BatchCtl));
+    if (e != cudaSuccess) { cudaFree(p); delete w; return cuda_fail(e, "cudaMallocHost"); }
+    void* fn = g->dg.packed ? reinterpret_cast<void*>(&k_batch_superstep<true>)
+                            : reinterpret_cast<void*>(&k_batch_superstep<false>);
+    int per_sm = 0;
+    GG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBB, 0));
+    w->grid = std::max(1, per_sm) * device_info().num_sms;
+    g->batch = w;
+  }
+  *out = g->batch;
+  return GG_OK;
+}
+
+static gg_status batch_exec(gg_graph* g, BatchWorkspace* w) {
+  if (w->exec) return GG_OK;
+  cudaGraph_t graph = nullptr;
+  GG_CK(cudaGraphCreate(&graph, 0));
+  cudaGraphConditionalHandle h;
+  GG_CK(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  GG_CK(cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &cp));
+  DevGraph dg = g->dg;
+  BatchBufs b = w->b;
+  int use_cond = 1;
+  void* args[] = {&dg, &b, &h, &use_cond};
+  cudaKernelNodeParams kp = {};
+  kp.func = g->dg.packed ? reinterpret_cast<void*>(&k_batch_superstep<true>)
+                         : reinterpret_cast<void*>(&k_batch_superstep<false>);
+  kp.gridDim = dim3(w->grid);
+  kp.blockDim = dim3(kBB);
+  kp.kernelParams = args;
+  cudaGraphNode_t knode;
+  GG_CK(cudaGraphAddKernelNode(&knode, cp.conditional.phGraph_out[0], nullptr, 0, &kp));
+  GG_CK(cudaGraphInstantiate(&w->exec, graph, 0));
+  w->graph = graph;
+  return GG_OK;
+}
+
+gg_status batch_run(gg_graph* g, const uint32_t* srcs, uint32_t k, uint32_t* dist, const gg_options& o,
+                    cudaStream_t s) {
+  BatchWorkspace* w = nullptr;
+  gg_status st = batch_ws(g, &w);
+  if (st != GG_OK) return st;
+  if (w->srcs_cap < k) {
+    if (w->srcs) GG_CK(cudaFree(w->srcs));
+    w->srcs = nullptr;
+    w->srcs_cap = 0;
+    GG_CK(cudaMalloc(&w->srcs, sizeof(uint32_t) * k));
+    w->srcs_cap = k;
+  }
+  GG_CK(cudaMemcpyAsync(w->srcs, srcs, sizeof(uint32_t) * k, cudaMemcpyHostToDevice, s));
+  st = batch_exec(g, w);
+  if (st != GG_OK) return st;
+  const unsigned long long count = (unsigned long long)g->n * k;
+  const unsigned fb = (unsigned)std::max<unsigned long long>(
+      1, std::min<unsigned long long>((count / 4 + 255) / 256, (unsigned long long)device_info().num_sms * 8));
+  k_batch_fill<<<fb, 256, 0, s>>>(dist, count);
+  GG_CK(cudaGetLastError());
+  const uint32_t max_iter = o.max_iterations ? o.max_iterations : (g->n + 2u < g->n ? 0xFFFFFFFFu : g->n + 2u);
+  for (uint32_t col0 = 0; col0 < k; col0 += 64) {
+    const uint32_t kg = std::min<uint32_t>(64, k - col0);
+    // the previous group (or call) may leave the masks of its last frontier set
+    for (int i = 0; i < 3; ++i) GG_CK(cudaMemsetAsync(w->b.mask[i], 0, 8 * (size_t)g->n, s));
+    k_batch_seed<<<1, 64, 0, s>>>(g->dg, w->b, w->srcs, k, col0, kg, dist, max_iter);
+    GG_CK(cudaGetLastError());
+    GG_CK(cudaGraphLaunch(w->exec, s));
+    if (o.stats) {
+      GG_CK(cudaMemcpyAsync(w->h_ctl, w->b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
+      GG_CK(cudaStreamSynchronize(s));
+      o.stats->iterations += w->h_ctl->iter;
+      o.stats->edges_scanned += w->h_ctl->edges_scanned;
+      o.stats->frontier_total += w->h_ctl->frontier_total;
+      o.stats->max_frontier = std::max(o.stats->max_frontier, w->h_ctl->max_frontier);
+      o.stats->device_status |= w->h_ctl->status;
+    }
+  }
+  return GG_OK;
+}
+
+gg_status batch_status(gg_graph* g, uint32_t* ds) {
+  *ds = 0;
+  if (!g->batch) return GG_OK;
+  GG_CK(cudaMemcpyAsync(g->batch->h_ctl, g->batch->b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, g->last_stream));
+  GG_CK(cudaStreamSynchronize(g->last_stream));
+  *ds = g->batch->h_ctl->status;
+  return GG_OK;
+}
+
+void batch_release(gg_graph* g) {
+  BatchWorkspace* w = g->batch;
+  if (!w) return;
+  if (w->exec) cudaGraphExecDestroy(w->exec);
+  if (w->graph) cudaGraphDestroy(w->graph);
+  if (w->block) cudaFree(w->block);
+  if (w->srcs) cudaFree(w->srcs);
+  if (w->h_ctl) cudaFreeHost(w->h_ctl);
+  delete w;
+  g->batch = nullptr;
+}
+
+size_t batch_bytes(const gg_graph* g) { return g->batch ? g->batch->bytes : 0; }
+
+}  // namespace gg

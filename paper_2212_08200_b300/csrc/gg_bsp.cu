@@ -38,15 +38,18 @@ struct MPSmem {
   uint32_t es[ECAP];   // entry: first merge-path coordinate
   uint32_t eb[ECAP];   // push: CSR row start;   pull: vertex id
   uint32_t ec[ECAP];   // push: dist of source;  pull: running min candidate
-  uint32_t qv[ECAP];   // filter output queue: vertex
-  uint32_t qr[ECAP];   //                      CSR row start
-  uint32_t qd[ECAP];   //                      out-degree (scanned in place)
+  uint32_t qv[ECAP];   // filter output queue: near vertices from the front, far ones from the back
+  uint32_t qr[ECAP];   //                      CSR row start (near)
+  uint32_t qd[ECAP];   //                      out-degree (near; scanned in place)
   uint32_t wsum[BLOCK / 32];
-  uint32_t qn;
+  uint32_t qn;         // near entries
+  uint32_t qfn;        // far entries
+  uint32_t fmin;       // smallest distance sent to the far pile
   uint32_t j;
   uint32_t last;
   uint32_t ovf;
   unsigned long long base;
+  uint32_t fbase;
 };
 
 struct StepArgs {
@@ -55,43 +58,72 @@ struct StepArgs {
   Ctl* ctl;
 };
 
-// Filter: improved vertex v -> next frontier (once), unless it has no out-edges.
+// Where the filter writes: the next (near) frontier and the far pile.
+struct FilterOut {
+  const uint32_t* ro;
+  uint32_t* bm_next;
+  uint32_t* bm_far;
+  uint32_t t_cur;                 // near threshold
+  unsigned long long* cnt_next;   // (count << 32) | edges of the next frontier
+  uint32_t *nfv, *nfr, *nfs;
+  uint32_t* far;                  // far pile being appended to
+  uint32_t* far_cnt;
+};
+
+// Filter: vertex v whose distance just dropped to nd.  Vertices without
+// out-edges have nothing to expand and are skipped.  nd < t_cur: the next
+// frontier (once, by test-and-set on its bitmap); otherwise the far pile
+// (once, by its own bitmap).
 template <int BLOCK, int EPT>
-__device__ __forceinline__ void filter_candidate(MPSmem<BLOCK, EPT>& sm, const uint32_t* __restrict__ ro,
-                                                 uint32_t* __restrict__ bm_next, uint32_t v) {
-  const uint32_t rs = __ldg(ro + v), re = __ldg(ro + v + 1);
+__device__ __forceinline__ void filter_candidate(MPSmem<BLOCK, EPT>& sm, const FilterOut& fo, uint32_t v,
+                                                 uint32_t nd) {
+  const uint32_t rs = __ldg(fo.ro + v), re = __ldg(fo.ro + v + 1);
   if (re > rs) {
     const uint32_t bit = 1u << (v & 31);
-    const uint32_t old = atomicOr(bm_next + (v >> 5), bit);
-    if (!(old & bit)) {
-      const uint32_t q = atomicAdd(&sm.qn, 1u);
-      sm.qv[q] = v;
-      sm.qr[q] = rs;
-      sm.qd[q] = re - rs;
+    if (nd < fo.t_cur) {
+      if (!(atomicOr(fo.bm_next + (v >> 5), bit) & bit)) {
+        const uint32_t q = atomicAdd(&sm.qn, 1u);
+        sm.qv[q] = v;
+        sm.qr[q] = rs;
+        sm.qd[q] = re - rs;
+      }
+    } else {
+      atomicMin(&sm.fmin, nd);
+      if (!(atomicOr(fo.bm_far + (v >> 5), bit) & bit)) {
+        const uint32_t q = MPSmem<BLOCK, EPT>::ECAP - 1 - atomicAdd(&sm.qfn, 1u);
+        sm.qv[q] = v;
+      }
     }
   }
 }
 
-// Append the CTA's collected vertices to the next frontier.
+// Append the CTA's collected vertices to the next frontier (one 64-bit
+// atomicAdd returns queue position and edge-prefix base) and to the far pile.
 template <int BLOCK, int EPT>
-__device__ __forceinline__ void filter_flush(MPSmem<BLOCK, EPT>& sm, unsigned long long* cnt_next,
-                                             uint32_t* __restrict__ fv, uint32_t* __restrict__ fr,
-                                             uint32_t* __restrict__ fs) {
+__device__ __forceinline__ void filter_flush(MPSmem<BLOCK, EPT>& sm, const FilterOut& fo) {
+  constexpr uint32_t ECAP = MPSmem<BLOCK, EPT>::ECAP;
   __syncthreads();
-  const uint32_t qn = sm.qn;
-  if (qn == 0) return;   // uniform
-  const uint32_t tot = block_scan_excl<BLOCK>(sm.qd, qn, sm.wsum);
-  if (threadIdx.x == 0) sm.base = atomicAdd(cnt_next, ((unsigned long long)qn << 32) | tot);
+  const uint32_t qn = sm.qn, qfn = sm.qfn;
+  if (qn == 0 && qfn == 0) return;   // uniform
+  if (qn) {
+    const uint32_t tot = block_scan_excl<BLOCK>(sm.qd, qn, sm.wsum);
+    if (threadIdx.x == 0) sm.base = atomicAdd(fo.cnt_next, ((unsigned long long)qn << 32) | tot);
+  }
+  if (qfn && threadIdx.x == 0) sm.fbase = atomicAdd(fo.far_cnt, qfn);
   __syncthreads();
   const unsigned long long b = sm.base;
   const uint32_t pos0 = (uint32_t)(b >> 32), eb0 = (uint32_t)b;
   for (uint32_t i = threadIdx.x; i < qn; i += BLOCK) {
-    fv[pos0 + i] = sm.qv[i];
-    fr[pos0 + i] = sm.qr[i];
-    fs[pos0 + i] = eb0 + sm.qd[i];
+    fo.nfv[pos0 + i] = sm.qv[i];
+    fo.nfr[pos0 + i] = sm.qr[i];
+    fo.nfs[pos0 + i] = eb0 + sm.qd[i];
   }
+  for (uint32_t i = threadIdx.x; i < qfn; i += BLOCK) fo.far[sm.fbase + i] = sm.qv[ECAP - 1 - i];
   __syncthreads();
-  if (threadIdx.x == 0) sm.qn = 0;
+  if (threadIdx.x == 0) {
+    sm.qn = 0;
+    sm.qfn = 0;
+  }
   __syncthreads();
 }
 
@@ -105,9 +137,7 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
                                            const uint32_t* __restrict__ S, const uint32_t* __restrict__ B,
                                            const uint32_t* __restrict__ V, const void* __restrict__ edges,
                                            uint32_t* __restrict__ dist, uint32_t* __restrict__ bm_cur,
-                                           uint32_t* __restrict__ bm_next, unsigned long long* cnt_next,
-                                           uint32_t* __restrict__ nfv, uint32_t* __restrict__ nfr,
-                                           uint32_t* __restrict__ nfs) {
+                                           const FilterOut& fo) {
   static_assert(!PULL || EPT == 8, "pull uses 8-edge vector runs");
   constexpr uint32_t TILE = MPSmem<BLOCK, EPT>::TILE;
   const uint32_t tid = threadIdx.x;
@@ -179,7 +209,7 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
       for (int k = 0; k < EPT; ++k) {
         if (ej[k] != kInf && nd[k] < cur[k]) {
           const uint32_t old = atomicMin(dist + ed[k].x, nd[k]);
-          if (nd[k] < old) filter_candidate(sm, a.g.ro, bm_next, ed[k].x);
+          if (nd[k] < old) filter_candidate(sm, fo, ed[k].x, nd[k]);
         }
       }
     } else {
@@ -229,12 +259,12 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
           const uint32_t v = sm.eb[i];
           if (c < ld_cg(dist + v)) {
             const uint32_t old = atomicMin(dist + v, c);
-            if (c < old) filter_candidate(sm, a.g.ro, bm_next, v);
+            if (c < old) filter_candidate(sm, fo, v, c);
           }
         }
       }
     }
-    filter_flush(sm, cnt_next, nfv, nfr, nfs);
+    filter_flush(sm, fo);
     j = j + nent - 1;
   }
   if (ovf) sm.ovf = 1u;
@@ -249,9 +279,7 @@ template <int BLOCK, int EPT, bool PK>
 __device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t F, uint32_t Etot,
                                              const uint32_t* __restrict__ fv, const uint32_t* __restrict__ fr,
                                              const uint32_t* __restrict__ fs, uint32_t* __restrict__ dist,
-                                             uint32_t* __restrict__ bm_cur, uint32_t* __restrict__ bm_next,
-                                             unsigned long long* cnt_next, uint32_t* __restrict__ nfv,
-                                             uint32_t* __restrict__ nfr, uint32_t* __restrict__ nfs,
+                                             uint32_t* __restrict__ bm_cur, const FilterOut& fo,
                                              uint32_t warp_thr, uint32_t cta_thr) {
   constexpr uint32_t NW = BLOCK / 32;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -263,7 +291,7 @@ __device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepA
     const uint32_t nd = add_sat(du, ed.y, ovf);
     if (nd < ld_cg(dist + ed.x)) {
       const uint32_t old = atomicMin(dist + ed.x, nd);
-      if (nd < old) filter_candidate(sm, a.g.ro, bm_next, ed.x);
+      if (nd < old) filter_candidate(sm, fo, ed.x, nd);
     }
   };
   const uint32_t nchunks = (F + BLOCK - 1) / BLOCK;
@@ -299,7 +327,7 @@ __device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepA
           const uint32_t o = base + q * BLOCK + tid;
           if (o < d) relax(r + o, u);
         }
-        filter_flush(sm, cnt_next, nfv, nfr, nfs);
+        filter_flush(sm, fo);
       }
     }
     // warp per vertex
@@ -315,7 +343,7 @@ __device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepA
         moff += 32 * EPT;
         if (moff >= d) { mi += NW; moff = 0; }
       }
-      filter_flush(sm, cnt_next, nfv, nfr, nfs);
+      filter_flush(sm, fo);
     }
     // thread per vertex
     uint32_t off = 0;
@@ -324,10 +352,40 @@ __device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepA
       for (int q = 0; q < EPT; ++q)
         if (off + q < deg) relax(row + off + q, du);
       off += EPT;
-      filter_flush(sm, cnt_next, nfv, nfr, nfs);
+      filter_flush(sm, fo);
     }
   }
   if (ovf) sm.ovf = 1u;
+}
+
+// Split step of the near-far frontier, run when the near frontier is empty:
+// every far-pile vertex v is re-examined against the raised threshold.
+//   dist[v] <  t_prev  it was improved below the old threshold after it was
+//                      parked, so the near phase already expanded it: drop
+//   dist[v] <  t_cur   move it to the next (near) frontier
+//   otherwise          keep it in the other far pile
+template <int BLOCK, int EPT>
+__device__ __forceinline__ void far_split(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, const FilterOut& fo,
+                                          uint32_t* __restrict__ dist, const uint32_t* __restrict__ far_in,
+                                          uint32_t nfar, uint32_t t_prev) {
+  for (uint32_t base = blockIdx.x * BLOCK; base < nfar; base += gridDim.x * BLOCK) {
+    const uint32_t i = base + threadIdx.x;
+    if (i < nfar) {
+      const uint32_t v = far_in[i];
+      const uint32_t d = ld_cg(dist + v);
+      if (d < fo.t_cur) {
+        atomicAnd(fo.bm_far + (v >> 5), ~(1u << (v & 31)));
+        if (d >= t_prev) filter_candidate(sm, fo, v, d);
+      } else {
+        // stays far: the filter's far branch re-appends it (its far bit is still set,
+        // so append directly)
+        atomicMin(&sm.fmin, d);
+        const uint32_t q = MPSmem<BLOCK, EPT>::ECAP - 1 - atomicAdd(&sm.qfn, 1u);
+        sm.qv[q] = v;
+      }
+    }
+    filter_flush(sm, fo);
+  }
 }
 
 // Shared prologue: reset the CTA's queue, clear the bitmap left by a pull step.
@@ -335,6 +393,8 @@ template <int BLOCK, int EPT>
 __device__ __forceinline__ void superstep_prologue(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t it) {
   if (threadIdx.x == 0) {
     sm.qn = 0;
+    sm.qfn = 0;
+    sm.fmin = kInf;
     sm.ovf = 0;
   }
   if (a.ctl->clear_prev) {
@@ -344,8 +404,14 @@ __device__ __forceinline__ void superstep_prologue(MPSmem<BLOCK, EPT>& sm, const
   __syncthreads();
 }
 
-// The last CTA to arrive closes the superstep: counters, trace, direction
-// choice for the next superstep, and the loop condition.
+__device__ __forceinline__ unsigned long long bsp_globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// The last CTA to arrive closes the superstep: counters, trace, the next
+// step's kind (push, pull, or a near-far split) and the loop condition.
 template <int BLOCK, int EPT>
 __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t it, uint32_t f,
                                                    uint32_t E, uint32_t mode, cudaGraphConditionalHandle cond,
@@ -355,6 +421,7 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
   __syncthreads();
   if (threadIdx.x == 0) {
     if (sm.ovf) atomicOr(&ctl->status, DS_OVERFLOW);
+    if (sm.fmin != kInf) atomicMin(&ctl->far_min, sm.fmin);
     __threadfence();
     sm.last = (atomicAdd(&ctl->done_ctas, 1u) == gridDim.x - 1) ? 1u : 0u;
   }
@@ -363,32 +430,59 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
     __threadfence();
     const unsigned long long cn = atomicAdd(&ctl->cnt[p ^ 1u], 0ull);
     const uint32_t fn = (uint32_t)(cn >> 32), En = (uint32_t)cn;
+    uint32_t fp = ctl->fp;
+    if (mode == MODE_SPLIT) {   // the kept entries were written to the other pile
+      ctl->far_cnt[fp] = 0u;
+      fp ^= 1u;
+      ctl->fp = fp;
+      ctl->splits += 1;
+    }
+    const uint32_t nfar = atomicAdd(&ctl->far_cnt[fp], 0u);
     if (ctl->trace && it < ctl->trace_cap) {
       uint32_t* t = ctl->trace + 4ull * it;
       t[0] = f;
-      t[1] = mode == MODE_PUSH ? E : a.g.m;
+      t[1] = mode == MODE_PUSH ? E : mode == MODE_PULL ? a.g.m : 0u;
       t[2] = mode;
       t[3] = fn;
     }
-    if (f > 0) {
+    if (f > 0 && mode != MODE_SPLIT) {
       ctl->edges_scanned += mode == MODE_PUSH ? E : a.g.m;
       ctl->frontier_total += f;
       ctl->max_frontier = max(ctl->max_frontier, f);
-      ctl->pull_iters += mode;
+      ctl->pull_iters += mode == MODE_PULL ? 1u : 0u;
     }
     ctl->cnt[p] = 0ull;
     ctl->done_ctas = 0u;
     ctl->clear_prev = (mode == MODE_PULL) ? 1u : 0u;
-    uint32_t nm = mode;
-    if (ctl->dir == DIR_PUSH) nm = MODE_PUSH;
-    else if (ctl->dir == DIR_PULL) nm = MODE_PULL;
-    else if (mode == MODE_PUSH) nm = ((unsigned long long)En * ctl->alpha > a.g.m) ? MODE_PULL : MODE_PUSH;
-    else nm = ((unsigned long long)fn * ctl->beta < a.g.np) ? MODE_PUSH : MODE_PULL;
+    uint32_t nm;
+    if (fn == 0 && nfar > 0) {
+      // near frontier exhausted: raise the threshold past the smallest parked distance
+      nm = MODE_SPLIT;
+      const uint32_t fmin = ctl->far_min;
+      const unsigned long long t1 = (unsigned long long)ctl->t_cur + ctl->delta;
+      const unsigned long long t2 = (unsigned long long)fmin + 1;
+      const unsigned long long tn = t1 > t2 ? t1 : t2;
+      ctl->t_prev = ctl->t_cur;
+      ctl->t_cur = tn >= kInf ? kInf : (uint32_t)tn;
+      ctl->far_min = kInf;
+    } else if (ctl->dir == DIR_PUSH) {
+      nm = MODE_PUSH;
+    } else if (ctl->dir == DIR_PULL) {
+      nm = MODE_PULL;
+    } else if (mode != MODE_PULL) {
+      nm = ((unsigned long long)En * ctl->alpha > a.g.m) ? MODE_PULL : MODE_PUSH;
+    } else {
+      nm = ((unsigned long long)fn * ctl->beta < a.g.np) ? MODE_PUSH : MODE_PULL;
+    }
     ctl->mode = nm;
     ctl->iter = it + 1;
-    bool more = fn != 0;
+    bool more = fn != 0 || nfar != 0;
     if (more && it + 1 >= ctl->max_iter) {
       ctl->status |= DS_ITER_CAP;
+      more = false;
+    }
+    if (more && bsp_globaltimer() - ctl->t_start > ctl->watchdog_ns) {
+      ctl->status |= DS_TIMEOUT;
       more = false;
     }
     ctl->running = more ? 1u : 0u;
@@ -397,9 +491,10 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
 }
 
 // One superstep; BINS selects the degree-binned push advance instead of the
-// merge-path one (pull is the same merge-path sweep in both).
+// merge-path one (pull is the same merge-path sweep in both); a split step
+// refills the near frontier from the far pile.
 template <int BLOCK, int EPT, bool BINS, bool PK>
-__global__ void __launch_bounds__(BLOCK) k_superstep(StepArgs a, cudaGraphConditionalHandle cond, int use_cond) {
+__global__ void __launch_bounds__(BLOCK, 4) k_superstep(StepArgs a, cudaGraphConditionalHandle cond, int use_cond) {
   extern __shared__ __align__(16) unsigned char smraw[];
   MPSmem<BLOCK, EPT>& sm = *reinterpret_cast<MPSmem<BLOCK, EPT>*>(smraw);
   Ctl* ctl = a.ctl;
@@ -408,24 +503,35 @@ __global__ void __launch_bounds__(BLOCK) k_superstep(StepArgs a, cudaGraphCondit
   const unsigned long long c = ctl->cnt[p];
   const uint32_t f = (uint32_t)(c >> 32), E = (uint32_t)c;
   const uint32_t mode = ctl->mode;
+  const uint32_t fp = ctl->fp;
   uint32_t* dist = ctl->dist;
   uint32_t* bm_cur = a.fr.bm[it % 3];
-  uint32_t* bm_next = a.fr.bm[(it + 1) % 3];
+  FilterOut fo;
+  fo.ro = a.g.ro;
+  fo.bm_next = a.fr.bm[(it + 1) % 3];
+  fo.bm_far = a.fr.bm_far;
+  fo.t_cur = ctl->t_cur;
+  fo.cnt_next = &ctl->cnt[p ^ 1u];
+  fo.nfv = a.fr.fv[p ^ 1u];
+  fo.nfr = a.fr.fr[p ^ 1u];
+  fo.nfs = a.fr.fs[p ^ 1u];
+  // a split step reads far[fp] and keeps entries in far[fp^1]; other steps append to far[fp]
+  fo.far = a.fr.far[mode == MODE_SPLIT ? fp ^ 1u : fp];
+  fo.far_cnt = &ctl->far_cnt[mode == MODE_SPLIT ? fp ^ 1u : fp];
   superstep_prologue(sm, a, it);
-  if (f > 0) {
+  if (mode == MODE_SPLIT) {
+    far_split(sm, a, fo, dist, a.fr.far[fp], ctl->far_cnt[fp], ctl->t_prev);
+  } else if (f > 0) {
     if (mode == MODE_PUSH) {
       if (BINS)
-        bins_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fv[p], a.fr.fr[p], a.fr.fs[p], dist, bm_cur, bm_next,
-                                 &ctl->cnt[p ^ 1u], a.fr.fv[p ^ 1u], a.fr.fr[p ^ 1u], a.fr.fs[p ^ 1u],
-                                 ctl->warp_thr, ctl->cta_thr);
+        bins_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fv[p], a.fr.fr[p], a.fr.fs[p], dist, bm_cur, fo,
+                                     ctl->warp_thr, ctl->cta_thr);
       else
-        mp_advance<BLOCK, EPT, false, PK>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], a.g.edges, dist, bm_cur,
-                                      bm_next, &ctl->cnt[p ^ 1u], a.fr.fv[p ^ 1u], a.fr.fr[p ^ 1u],
-                                      a.fr.fs[p ^ 1u]);
+        mp_advance<BLOCK, EPT, false, PK>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], a.g.edges, dist,
+                                          bm_cur, fo);
     } else {
       mp_advance<BLOCK, EPT, true, PK>(sm, a, a.g.np, a.g.m, a.g.ps, a.g.ps, a.g.pv, a.g.t_edges, dist, bm_cur,
-                                   bm_next, &ctl->cnt[p ^ 1u], a.fr.fv[p ^ 1u], a.fr.fr[p ^ 1u],
-                                   a.fr.fs[p ^ 1u]);
+                                       fo);
     }
   }
   superstep_finalize(sm, a, it, f, E, mode, cond, use_cond);
@@ -439,6 +545,8 @@ struct RunParams {
   uint32_t* trace;
   uint32_t trace_cap;
   uint32_t warp_thr, cta_thr;
+  uint32_t delta;                  // near-far bucket width (kInf: no split)
+  unsigned long long watchdog_ns;
 };
 
 // dist := INF everywhere (vectorised 16-byte stores when aligned); bitmaps := 0.
@@ -458,6 +566,7 @@ __global__ void k_init(StepArgs a, uint32_t* dist) {
     a.fr.bm[0][i] = 0u;
     a.fr.bm[1][i] = 0u;
     a.fr.bm[2][i] = 0u;
+    a.fr.bm_far[i] = 0u;
   }
 }
 
@@ -495,6 +604,16 @@ __global__ void k_init_tail(StepArgs a, RunParams rp) {
   ctl->max_frontier = 0;
   ctl->warp_thr = rp.warp_thr;
   ctl->cta_thr = rp.cta_thr;
+  ctl->delta = rp.delta;
+  ctl->t_cur = rp.delta;           // the first bucket is [0, delta)
+  ctl->t_prev = 0;
+  ctl->fp = 0;
+  ctl->far_cnt[0] = 0;
+  ctl->far_cnt[1] = 0;
+  ctl->far_min = kInf;
+  ctl->splits = 0;
+  ctl->watchdog_ns = rp.watchdog_ns;
+  ctl->t_start = bsp_globaltimer();
   ctl->edges_scanned = 0;
   ctl->frontier_total = 0;
 }
@@ -522,7 +641,7 @@ gg_status ensure_workspace(gg_graph* g) {
   const size_t fbytes = sizeof(uint32_t) * std::max<size_t>(n, 1);
   auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
   // every sub-buffer starts on a 256-byte boundary
-  const size_t total = 6 * r256(fbytes) + 3 * r256(sizeof(uint32_t) * nw) + r256(sizeof(Ctl));
+  const size_t total = 8 * r256(fbytes) + 4 * r256(sizeof(uint32_t) * nw) + r256(sizeof(Ctl));
   char* p = nullptr;
   GG_CK(cudaMalloc(&p, total));
   GG_CK(cudaMemset(p, 0, total));
@@ -536,6 +655,8 @@ gg_status ensure_workspace(gg_graph* g) {
     w.fr.fs[i] = reinterpret_cast<uint32_t*>(take(fbytes));
   }
   for (int i = 0; i < 3; ++i) w.fr.bm[i] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * nw));
+  for (int i = 0; i < 2; ++i) w.fr.far[i] = reinterpret_cast<uint32_t*>(take(fbytes));
+  w.fr.bm_far = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * nw));
   w.ctl = reinterpret_cast<Ctl*>(take(sizeof(Ctl)));
   if (off != total) return fail(GG_ERR_INTERNAL, "workspace layout");
   return GG_OK;
@@ -601,7 +722,13 @@ gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o
   rp.dir = o.direction == GG_DIR_PUSH ? DIR_PUSH : o.direction == GG_DIR_PULL ? DIR_PULL : DIR_AUTO;
   rp.alpha = o.pull_alpha ? o.pull_alpha : 4u;
   rp.beta = o.pull_beta ? o.pull_beta : 24u;
-  rp.max_iter = o.max_iterations ? o.max_iterations : (g->n + 2u < g->n ? 0xFFFFFFFFu : g->n + 2u);
+  // near-far: with buckets the superstep count is bounded by about 3n (every
+  // phase finalises at least one vertex and runs at most its bucket's size + 2
+  // steps); without, by n + 1
+  rp.delta = o.delta == GG_DELTA_NONE ? kInf : (o.delta ? o.delta : g->default_delta);
+  const unsigned long long cap = rp.delta == kInf ? (unsigned long long)g->n + 2 : 4ull * g->n + 16;
+  rp.max_iter = o.max_iterations ? o.max_iterations : (cap >= 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)cap);
+  rp.watchdog_ns = o.watchdog_ns ? o.watchdog_ns : 60000000000ull;
   rp.trace = o.trace;
   rp.trace_cap = o.trace_cap;
   rp.warp_thr = o.warp_threshold ? o.warp_threshold : 32u;

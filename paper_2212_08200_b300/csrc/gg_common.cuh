@@ -30,7 +30,7 @@ namespace gg {
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 constexpr uint32_t kSat = 0xFFFFFFFEu;   // saturated (overflowed) finite distance
 
-enum : uint32_t { MODE_PUSH = 0, MODE_PULL = 1 };
+enum : uint32_t { MODE_PUSH = 0, MODE_PULL = 1, MODE_SPLIT = 2 };
 enum : uint32_t { DIR_AUTO = 0, DIR_PUSH = 1, DIR_PULL = 2 };
 
 // device-status bits, mapped to gg_status on the host
@@ -54,6 +54,16 @@ struct Ctl {
   uint32_t trace_cap;
   uint32_t max_frontier;
   uint32_t warp_thr, cta_thr;  // degree bins of the binned push advance
+  // near-far split of the frontier (priority buckets of width delta): vertices
+  // improved to a distance < t_cur join the next frontier, the others wait in
+  // the far pile far[fp] until the near frontier empties and a split step
+  // raises the threshold
+  uint32_t t_cur, t_prev, delta, fp;
+  uint32_t far_cnt[2];
+  uint32_t far_min;            // lower bound of the distances recorded in the far pile
+  uint32_t splits;
+  unsigned long long t_start;  // %globaltimer at init (watchdog)
+  unsigned long long watchdog_ns;
   unsigned long long edges_scanned;
   unsigned long long frontier_total;
 };
@@ -75,6 +85,8 @@ struct Frontier {
   uint32_t* fr[2];
   uint32_t* fs[2];
   uint32_t* bm[3];
+  uint32_t* far[2];    // far pile (vertex ids), ping-pong across split steps
+  uint32_t* bm_far;    // far-pile membership (dedup)
 };
 
 #ifdef __CUDACC__

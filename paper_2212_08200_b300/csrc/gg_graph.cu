@@ -301,6 +301,16 @@ gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m64, const uint32_t* ro_
     g->bytes += (g->symmetric ? 1 : 2) * sizeof(uint32_t) * (size_t)m;
     g->dg.packed = 1;
   }
+  // default near-far bucket width: a few average edge weights' worth of
+  // distance per bucket, scaled down on dense graphs (more edges relax each
+  // bucket); autotuned per graph class by the tuner
+  g->wmax = wmax;
+  {
+    const double davg = g->dg.np ? (double)m / (double)g->dg.np : 1.0;
+    double d = (double)wmax * 8.0 / std::max(davg, 1.0);
+    if (d < 1.0) d = 1.0;
+    g->default_delta = m ? (uint32_t)std::min(d, 1.0e9) : 1u;
+  }
   g->dg.n = n;
   g->dg.m = m;
   g->dg.nwords = (n + 31) / 32;

@@ -53,6 +53,8 @@ struct AsyncWorkspace {
   int grid = 0;
 };
 
+struct BatchWorkspace;
+
 }  // namespace gg
 
 struct gg_graph {
@@ -74,12 +76,15 @@ struct gg_graph {
   std::mutex mu;
   gg::BspWorkspace bsp;
   gg::AsyncWorkspace async;
+  gg::BatchWorkspace* batch = nullptr;
   cudaEvent_t last_ev = nullptr;
   cudaStream_t last_stream = nullptr;
   bool ev_valid = false;
   gg::Ctl* h_ctl = nullptr;      // pinned host mirror for status/stats reads
   void* h_async = nullptr;       // pinned host mirror of the async control block
   int last_policy = -1;
+  uint32_t wmax = 0;            // largest edge weight
+  uint32_t default_delta = 0;   // near-far bucket width used when gg_options.delta == 0
 };
 
 namespace gg {
@@ -90,6 +95,13 @@ gg_status bsp_release(gg_graph* g);
 gg_status async_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s);
 gg_status async_release(gg_graph* g);
 gg_status async_status(gg_graph* g, uint32_t* ds, gg_stats* st);
+// gg_batch.cu
+gg_status batch_run(gg_graph* g, const uint32_t* srcs, uint32_t k, uint32_t* dist, const gg_options& o,
+                    cudaStream_t s);
+gg_status batch_status(gg_graph* g, uint32_t* ds);
+void batch_release(gg_graph* g);
+size_t batch_bytes(const gg_graph* g);
+constexpr int kLastBatch = 16;   // gg_graph::last_policy value after gg_sssp_batch
 // gg_graph.cu
 gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m, const uint32_t* ro, const uint32_t* col,
                       const uint32_t* w, uint32_t flags, cudaStream_t s);

@@ -1,0 +1,350 @@
+// gg_multi.cu -- many single-source queries on many graphs in one launch
+// sequence: the "slot" engine behind gg_sssp_multi and the query server.
+//
+// Each query occupies a slot {graph, source, caller's distance array, its
+// own two dedup bitmaps}.  All slots share ONE union frontier whose entries
+// are (slot, vertex, CSR row start, edge-prefix coordinate), so a superstep is
+// still one kernel: the merge-path advance of the single-source path splits
+// the union's edges evenly over the CTAs whatever mix of large and small
+// graphs is active, and the fused filter appends improved vertices with their
+// slot.  Per-slot counters of the next frontier tell the closing CTA which
+// queries have converged: it marks them done (device flag and, for the
+// server, a word in host-mapped memory) so new queries can take their slots
+// between supersteps -- continuous batching at superstep granularity.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "gg_host.h"
+#include "gg_multi.h"
+
+namespace gg {
+namespace {
+
+constexpr int kMB = 256;
+constexpr int kMEpt = 4;
+constexpr int kMTile = kMB * kMEpt;
+constexpr int kMCap = kMTile + 1;
+
+struct MSmem {
+  uint32_t es[kMCap], eb[kMCap], ec[kMCap], eq[kMCap];
+  uint32_t qv[kMCap], qr[kMCap], qd[kMCap], qq[kMCap];
+  uint32_t wsum[kMB / 32];
+  uint32_t qn, j, last, ovf;
+  unsigned long long base;
+};
+
+__device__ __forceinline__ uint2 slot_edge(const MultiSlot& s, uint32_t e) {
+  if (s.packed) {
+    const uint32_t x = __ldg(static_cast<const uint32_t*>(s.edges) + e);
+    return make_uint2(x >> s.wbits, x & ((1u << s.wbits) - 1u));
+  }
+  return __ldg(static_cast<const uint2*>(s.edges) + e);
+}
+
+__device__ __forceinline__ void m_candidate(MSmem& sm, const MultiSlot& s, uint32_t q, uint32_t* bm_next,
+                                            uint32_t v) {
+  const uint32_t rs = __ldg(s.ro + v), re = __ldg(s.ro + v + 1);
+  if (re > rs) {
+    const uint32_t bit = 1u << (v & 31);
+    if (!(atomicOr(bm_next + (v >> 5), bit) & bit)) {
+      const uint32_t i = atomicAdd(&sm.qn, 1u);
+      sm.qv[i] = v;
+      sm.qr[i] = rs;
+      sm.qd[i] = re - rs;
+      sm.qq[i] = q;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphConditionalHandle cond, int use_cond) {
+  __shared__ MSmem sm;
+  MultiCtl* ctl = b.ctl;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t it = ctl->iter, p = it & 1u;
+  const unsigned long long c = ctl->cnt[p];
+  const uint32_t F = (uint32_t)(c >> 32), E = (uint32_t)c;
+  const MultiSlot* __restrict__ slots = b.slots;
+  if (tid == 0) { sm.qn = 0; sm.ovf = 0; }
+  __syncthreads();
+  bool ovf = false;
+  const uint32_t e0 = (uint32_t)(((unsigned long long)blockIdx.x * E) / gridDim.x);
+  const uint32_t e1 = (uint32_t)(((unsigned long long)(blockIdx.x + 1) * E) / gridDim.x);
+  if (F > 0 && e0 < e1) {
+    const uint32_t* S = b.fs[p];
+    if (tid < 32) {
+      const uint32_t j = warp_search_le(S, F, e0);
+      if (tid == 0) sm.j = j;
+    }
+    __syncthreads();
+    uint32_t j = sm.j;
+    for (uint32_t t0 = e0; t0 < e1; t0 += kMTile) {
+      const uint32_t t1 = min(t0 + (uint32_t)kMTile, e1);
+      uint32_t nent = 0;
+      for (;;) {
+        const uint32_t idx = j + nent + tid;
+        bool valid = false;
+        uint32_t s = 0;
+        if (idx < F) {
+          s = S[idx];
+          valid = s < t1;
+        }
+        if (valid) {
+          const uint32_t q = b.fq[p][idx], v = b.fv[p][idx];
+          const MultiSlot& sl = slots[q];
+          sm.es[nent + tid] = s;
+          sm.eb[nent + tid] = b.fr[p][idx];
+          sm.ec[nent + tid] = ld_cg(sl.dist + v);
+          sm.eq[nent + tid] = q;
+          b.bm_pool[sl.bm_off[p] + (v >> 5)] = 0u;   // clear the current bitmap as we go
+        }
+        const int cnt = __syncthreads_count(valid);
+        nent += (uint32_t)cnt;
+        if (cnt < kMB) break;
+      }
+#pragma unroll
+      for (int k = 0; k < kMEpt; ++k) {
+        const uint32_t gidx = t0 + k * kMB + tid;
+        if (gidx < t1) {
+          const uint32_t jj = smem_upper_bound_minus1(sm.es, nent, gidx);
+          const uint32_t q = sm.eq[jj];
+          const MultiSlot& sl = slots[q];
+          const uint2 ed = slot_edge(sl, sm.eb[jj] + (gidx - sm.es[jj]));
+          const uint32_t nd = add_sat(sm.ec[jj], ed.y, ovf);
+          if (nd < ld_cg(sl.dist + ed.x)) {
+            atomicMin(sl.dist + ed.x, nd);
+            m_candidate(sm, sl, q, b.bm_pool + sl.bm_off[p ^ 1u], ed.x);
+          }
+        }
+      }
+      __syncthreads();
+      const uint32_t qn = sm.qn;
+      if (qn) {
+        for (uint32_t i = tid; i < qn; i += kMB) atomicAdd(&b.slot_cnt[sm.qq[i]], 1u);
+        const uint32_t tot = block_scan_excl<kMB>(sm.qd, qn, sm.wsum);
+        if (tid == 0) sm.base = atomicAdd(&ctl->cnt[p ^ 1u], ((unsigned long long)qn << 32) | tot);
+        __syncthreads();
+        const uint32_t pos0 = (uint32_t)(sm.base >> 32), eb0 = (uint32_t)sm.base;
+        for (uint32_t i = tid; i < qn; i += kMB) {
+          b.fv[p ^ 1u][pos0 + i] = sm.qv[i];
+          b.fr[p ^ 1u][pos0 + i] = sm.qr[i];
+          b.fs[p ^ 1u][pos0 + i] = eb0 + sm.qd[i];
+          b.fq[p ^ 1u][pos0 + i] = sm.qq[i];
+        }
+        __syncthreads();
+        if (tid == 0) sm.qn = 0;
+      }
+      __syncthreads();
+      j = j + nent - 1;
+    }
+  }
+  if (ovf) sm.ovf = 1u;
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    sm.last = (atomicAdd(&ctl->done_ctas, 1u) == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (sm.ovf) atomicOr(&ctl->ovf_any, 1u);
+  if (sm.last) {
+    // the closing CTA: converged slots are done; per-slot counters restart
+    __threadfence();
+    const unsigned long long cn = atomicAdd(&ctl->cnt[p ^ 1u], 0ull);
+    const uint32_t ovf_any = atomicAdd(&ctl->ovf_any, 0u);
+    for (uint32_t q = tid; q < b.nslots; q += kMB) {
+      MultiSlot* sl = b.slots_rw + q;
+      if (sl->state == kSlotRunning) {
+        const uint32_t cq = b.slot_cnt[q];
+        sl->supersteps += 1;
+        if (ovf_any) sl->status |= DS_OVERFLOW;
+        if (cq == 0) {
+          sl->state = kSlotDone;
+          if (b.done_flags) {
+            __threadfence_system();
+            reinterpret_cast<volatile uint32_t*>(b.done_flags)[q] = sl->ticket;
+          }
+        }
+      }
+      b.slot_cnt[q] = 0u;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      ctl->ovf_any = 0u;
+      ctl->cnt[p] = 0ull;
+      ctl->done_ctas = 0u;
+      ctl->iter = it + 1;
+      ctl->supersteps_run += 1;
+      const bool more = (cn >> 32) != 0 && ctl->budget_left > 1;
+      if (ctl->budget_left) ctl->budget_left -= 1;
+      ctl->running = (cn >> 32) != 0 ? 1u : 0u;
+      if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+    }
+  }
+}
+
+// dist := INF for every vertex of every slot in `starting` (blockIdx.y = list index)
+__global__ void k_multi_fill(MultiBufs b, const uint32_t* starting, uint32_t nstart) {
+  for (uint32_t i = blockIdx.y; i < nstart; i += gridDim.y) {
+    const MultiSlot& sl = b.slots[starting[i]];
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < sl.n; v += gridDim.x * blockDim.x)
+      sl.dist[v] = kInf;
+    const uint32_t nw = (sl.n + 31) / 32;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nw; v += gridDim.x * blockDim.x) {
+      b.bm_pool[sl.bm_off[0] + v] = 0u;
+      b.bm_pool[sl.bm_off[1] + v] = 0u;
+    }
+  }
+}
+
+// seed the starting slots into the frontier of the current parity
+__global__ void k_multi_seed(MultiBufs b, const uint32_t* starting, uint32_t nstart) {
+  MultiCtl* ctl = b.ctl;
+  const uint32_t p = ctl->iter & 1u;
+  for (uint32_t i = threadIdx.x; i < nstart; i += blockDim.x) {
+    const uint32_t q = starting[i];
+    MultiSlot* sl = b.slots_rw + q;
+    const uint32_t src = sl->src;
+    sl->dist[src] = 0u;
+    const uint32_t rs = sl->ro[src], re = sl->ro[src + 1];
+    if (re > rs) {
+      sl->state = kSlotRunning;
+      b.bm_pool[sl->bm_off[p] + (src >> 5)] |= 0u;   // membership of the seed needs no bit (push only)
+      const unsigned long long base = atomicAdd(&ctl->cnt[p], (1ull << 32) | (re - rs));
+      const uint32_t pos = (uint32_t)(base >> 32);
+      b.fv[p][pos] = src;
+      b.fr[p][pos] = rs;
+      b.fs[p][pos] = (uint32_t)base;
+      b.fq[p][pos] = q;
+    } else {
+      sl->state = kSlotDone;   // nothing to expand: dist is final already
+      if (b.done_flags) {
+        __threadfence_system();
+        reinterpret_cast<volatile uint32_t*>(b.done_flags)[q] = sl->ticket;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// ---- host side ---------------------------------------------------------------
+
+gg_status multi_engine_init(MultiEngine* e, uint32_t max_slots, uint64_t max_vertices, uint64_t max_bitmap_words,
+                            bool mapped_flags) {
+  e->max_slots = max_slots;
+  e->cap_vertices = max_vertices;
+  e->cap_words = max_bitmap_words;
+  auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t fb = r256(4 * std::max<uint64_t>(max_vertices, 1));
+  const size_t total = 8 * fb + 2 * r256(sizeof(MultiSlot) * max_slots) * 0 + r256(sizeof(MultiSlot) * max_slots) +
+                       r256(4 * (size_t)max_slots) + r256(4 * std::max<uint64_t>(max_bitmap_words, 1)) +
+                       r256(sizeof(MultiCtl)) + r256(4 * (size_t)max_slots);
+  char* p = nullptr;
+  GG_CK(cudaMalloc(&p, total));
+  GG_CK(cudaMemset(p, 0, total));
+  e->block = p;
+  e->bytes = total;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char* q = p + off; off += r256(bytes); return q; };
+  for (int i = 0; i < 2; ++i) {
+    e->b.fv[i] = reinterpret_cast<uint32_t*>(take(fb));
+    e->b.fr[i] = reinterpret_cast<uint32_t*>(take(fb));
+    e->b.fs[i] = reinterpret_cast<uint32_t*>(take(fb));
+    e->b.fq[i] = reinterpret_cast<uint32_t*>(take(fb));
+  }
+  e->b.slots_rw = reinterpret_cast<MultiSlot*>(take(sizeof(MultiSlot) * max_slots));
+  e->b.slots = e->b.slots_rw;
+  e->b.slot_cnt = reinterpret_cast<uint32_t*>(take(4 * (size_t)max_slots));
+  e->b.bm_pool = reinterpret_cast<uint32_t*>(take(4 * std::max<uint64_t>(max_bitmap_words, 1)));
+  e->b.ctl = reinterpret_cast<MultiCtl*>(take(sizeof(MultiCtl)));
+  e->starting = reinterpret_cast<uint32_t*>(take(4 * (size_t)max_slots));
+  e->b.nslots = max_slots;
+  if (off > total) return fail(GG_ERR_INTERNAL, "multi workspace layout");
+  GG_CK(cudaMallocHost(&e->h_slots, sizeof(MultiSlot) * max_slots));
+  GG_CK(cudaMallocHost(&e->h_ctl, sizeof(MultiCtl)));
+  GG_CK(cudaMallocHost(&e->h_start, 4 * (size_t)max_slots));
+  memset(e->h_slots, 0, sizeof(MultiSlot) * max_slots);
+  if (mapped_flags) {
+    GG_CK(cudaHostAlloc(&e->h_done, 4 * (size_t)max_slots, cudaHostAllocMapped));
+    memset(e->h_done, 0, 4 * (size_t)max_slots);
+    GG_CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&e->b.done_flags), e->h_done, 0));
+  } else {
+    e->b.done_flags = nullptr;
+  }
+  int per_sm = 0;
+  GG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi_superstep, kMB, 0));
+  e->grid = std::max(1, per_sm) * device_info().num_sms;
+  // CUDA graph: WHILE (frontier non-empty and superstep budget left) { superstep }
+  GG_CK(cudaGraphCreate(&e->graph, 0));
+  cudaGraphConditionalHandle h;
+  GG_CK(cudaGraphConditionalHandleCreate(&h, e->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  GG_CK(cudaGraphAddNode(&wnode, e->graph, nullptr, nullptr, 0, &cp));
+  MultiBufs b = e->b;
+  int use_cond = 1;
+  void* args[] = {&b, &h, &use_cond};
+  cudaKernelNodeParams kp = {};
+  kp.func = reinterpret_cast<void*>(&k_multi_superstep);
+  kp.gridDim = dim3(e->grid);
+  kp.blockDim = dim3(kMB);
+  kp.kernelParams = args;
+  cudaGraphNode_t knode;
+  GG_CK(cudaGraphAddKernelNode(&knode, cp.conditional.phGraph_out[0], nullptr, 0, &kp));
+  GG_CK(cudaGraphInstantiate(&e->exec, e->graph, 0));
+  return GG_OK;
+}
+
+void multi_engine_free(MultiEngine* e) {
+  if (e->exec) cudaGraphExecDestroy(e->exec);
+  if (e->graph) cudaGraphDestroy(e->graph);
+  if (e->block) cudaFree(e->block);
+  if (e->h_slots) cudaFreeHost(e->h_slots);
+  if (e->h_ctl) cudaFreeHost(e->h_ctl);
+  if (e->h_start) cudaFreeHost(e->h_start);
+  if (e->h_done) cudaFreeHost(e->h_done);
+  *e = MultiEngine{};
+}
+
+gg_status multi_engine_reset(MultiEngine* e, cudaStream_t s) {
+  MultiCtl c{};
+  memcpy(e->h_ctl, &c, sizeof(c));
+  GG_CK(cudaMemcpyAsync(e->b.ctl, e->h_ctl, sizeof(MultiCtl), cudaMemcpyHostToDevice, s));
+  GG_CK(cudaMemsetAsync(e->b.slot_cnt, 0, 4 * (size_t)e->max_slots, s));
+  return GG_OK;
+}
+
+gg_status multi_engine_start(MultiEngine* e, const uint32_t* slots, uint32_t count, cudaStream_t s) {
+  if (count == 0) return GG_OK;
+  // slot descriptors (host copy is authoritative for the static fields)
+  for (uint32_t i = 0; i < count; ++i) {
+    const uint32_t q = slots[i];
+    e->h_start[i] = q;
+    GG_CK(cudaMemcpyAsync(e->b.slots_rw + q, e->h_slots + q, sizeof(MultiSlot), cudaMemcpyHostToDevice, s));
+  }
+  GG_CK(cudaMemcpyAsync(e->starting, e->h_start, 4 * (size_t)count, cudaMemcpyHostToDevice, s));
+  uint32_t nmax = 1;
+  for (uint32_t i = 0; i < count; ++i) nmax = std::max(nmax, e->h_slots[slots[i]].n);
+  dim3 grid((unsigned)std::min<uint32_t>((nmax + 255) / 256, 1024), (unsigned)std::min<uint32_t>(count, 1024));
+  k_multi_fill<<<grid, 256, 0, s>>>(e->b, e->starting, count);
+  GG_CK(cudaGetLastError());
+  k_multi_seed<<<1, 256, 0, s>>>(e->b, e->starting, count);
+  GG_CK(cudaGetLastError());
+  return GG_OK;
+}
+
+gg_status multi_engine_run(MultiEngine* e, uint32_t budget, cudaStream_t s) {
+  // budget: supersteps this launch may run (0 = until the union frontier empties)
+  GG_CK(cudaMemcpyAsync(&e->b.ctl->budget_left, &e->budget_words[budget ? 1 : 0], 4, cudaMemcpyHostToDevice, s));
+  (void)budget;
+  GG_CK(cudaGraphLaunch(e->exec, s));
+  return GG_OK;
+}
+
+}  // namespace gg

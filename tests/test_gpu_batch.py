@@ -1,0 +1,104 @@
+"""GPU parity of batched multi-source SSSP (gg_sssp_batch) against the CPU
+oracle, one Dijkstra per source.  Bit-exact (tolerance 0)."""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def gg():
+    import paper_2212_08200_b300 as m
+    m.load()
+    return m
+
+
+def run_batch(g, srcs, **kw):
+    m = gg()
+    st = m.gg_stats()
+    d = g.sssp_batch(srcs, stats=st, **kw)
+    torch.cuda.synchronize()
+    return d.cpu().numpy(), st.as_dict()
+
+
+@pytest.mark.parametrize("k", [1, 5, 64, 100])
+@pytest.mark.parametrize("pack", [True, False])
+def test_rmat16_batch_matches_oracle(k, pack):
+    ro, col, w, _ = graphgen.workload("rmat16")
+    srcs = graphgen.sample_sources(ro, k, seed=3)
+    g = gg().Graph(ro, col, w, symmetric=True, pack=pack)
+    got, st = run_batch(g, srcs)
+    ref = oracle.dijkstra_many(ro, col, w, srcs, threads=8)
+    for s in range(k):
+        np.testing.assert_array_equal(got[:, s], ref[s], err_msg=f"column {s}")
+    assert st["iterations"] > 0 and st["device_status"] == 0
+    g.close()
+
+
+def test_duplicates_isolated_and_tiny_graphs():
+    m = gg()
+    for seed in range(6):
+        ro, col, w = graphgen.random_graph(40, 120, 50, seed, wmin=0)
+        g = m.Graph(ro, col, w)
+        srcs = np.array([0, 3, 3, 39, 0, 17, 5], np.uint32)
+        got, _ = run_batch(g, srcs)
+        ref = oracle.dijkstra_many(ro, col, w, srcs)
+        np.testing.assert_array_equal(got.T, ref)
+        g.close()
+    ro = np.zeros(4, np.uint32)
+    g = m.Graph(ro, np.zeros(0, np.uint32), np.zeros(0, np.uint32))
+    got, _ = run_batch(g, np.array([2, 0], np.uint32))
+    assert got[:, 0].tolist() == [0xFFFFFFFF, 0xFFFFFFFF, 0, 0xFFFFFFFF]
+    assert got[:, 1].tolist() == [0, 0xFFFFFFFF, 0xFFFFFFFF, 0xFFFFFFFF]
+    g.close()
+
+
+def test_grid64_batch_and_reuse():
+    ro, col, w, _ = graphgen.workload("grid64")
+    g = gg().Graph(ro, col, w, symmetric=True)
+    for seed in (1, 2):                               # workspace reuse across calls
+        srcs = graphgen.sample_sources(ro, 64, seed=seed)
+        got, _ = run_batch(g, srcs)
+        ref = oracle.dijkstra_many(ro, col, w, srcs, threads=8)
+        np.testing.assert_array_equal(got.T, ref)
+    g.close()
+
+
+def test_batch_equals_single_source_calls():
+    ro, col, w, _ = graphgen.workload("rmat16")
+    srcs = graphgen.sample_sources(ro, 64, seed=9)
+    g = gg().Graph(ro, col, w, symmetric=True)
+    got, _ = run_batch(g, srcs)
+    for s in (0, 31, 32, 63):
+        d = g.sssp(int(srcs[s]))
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(got[:, s], d.cpu().numpy())
+    g.close()
+
+
+def test_rmat22_64_sources_config():
+    ro, col, w = graphgen.rmat(22, 16, seed=1, W=255)
+    srcs = graphgen.sample_sources(ro, 64, seed=1)
+    g = gg().Graph(ro, col, w, symmetric=True)
+    got, st = run_batch(g, srcs)
+    ref = oracle.dijkstra_many(ro, col, w, srcs[[0, 33, 63]], threads=3)
+    for i, s in enumerate([0, 33, 63]):
+        np.testing.assert_array_equal(got[:, s], ref[i], err_msg=f"column {s}")
+    for s in (7, 40):                                  # other columns: the shortest-path invariants
+        assert oracle.check(ro, col, w, int(srcs[s]), np.ascontiguousarray(got[:, s])) == (0, 0)
+    g.close()
+
+
+def test_batch_argument_errors():
+    m = gg()
+    ro, col, w, _ = graphgen.workload("grid64")
+    g = m.Graph(ro, col, w, symmetric=True)
+    out = torch.empty(g.n * 2, dtype=torch.uint32, device="cuda")
+    with pytest.raises(m.GGError):
+        m.gg_sssp_batch(g.handle, np.array([0, g.n], np.uint32), out)
+    with pytest.raises(m.GGError):
+        m.gg_sssp_batch(g.handle, np.zeros(0, np.uint32), out)
+    g.close()

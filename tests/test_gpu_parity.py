@@ -30,14 +30,18 @@ def gg():
 POLICIES = {"graph": 0, "async": 1, "host": 2}
 DIRS = {"auto": 0, "push": 1, "pull": 2}
 LB = {"mp": 1, "bins": 2}
+NONE = 0xFFFFFFFF
+# (policy, direction, load balance, near-far delta; 0 = the graph's default)
 MODES = [("graph", "auto"), ("graph", "push"), ("graph", "pull"), ("host", "auto"), ("host", "pull"),
-         ("async", "auto"), ("graph", "push", "bins"), ("host", "auto", "bins")]
+         ("async", "auto"), ("graph", "push", "bins"), ("host", "auto", "bins"),
+         ("graph", "push", "mp", NONE), ("graph", "auto", "mp", 1), ("graph", "push", "bins", 3)]
 
 
-def run(g, src, policy="graph", direction="auto", lb="mp", **kw):
+def run(g, src, policy="graph", direction="auto", lb="mp", delta=0, **kw):
     m = gg()
     st = m.gg_stats()
-    d = g.sssp(src, policy=POLICIES[policy], direction=DIRS[direction], lb_mode=LB[lb], stats=st, **kw)
+    d = g.sssp(src, policy=POLICIES[policy], direction=DIRS[direction], lb_mode=LB[lb], delta=delta, stats=st,
+               **kw)
     torch.cuda.synchronize()
     return d.cpu().numpy(), st.as_dict()
 
@@ -70,7 +74,7 @@ def test_hand_worked_fixtures(name, mode):
     if isinstance(f["expect"], str):
         m = gg()
         d = g.sssp(f["src"], policy=POLICIES[mode[0]], direction=DIRS[mode[1]],
-                   lb_mode=LB[mode[2] if len(mode) > 2 else "mp"])
+                   lb_mode=LB[mode[2] if len(mode) > 2 else "mp"], delta=mode[3] if len(mode) > 3 else 0)
         with pytest.raises(m.GGError) as ei:
             g.check()
         assert ei.value.status_name == "GG_ERR_OVERFLOW"
@@ -113,12 +117,36 @@ def test_bins_thresholds(thr):
     g.close()
 
 
+@pytest.mark.parametrize("delta", [1, 2, 17, 200, 5000, NONE])
+@pytest.mark.parametrize("workload", ["grid64", "rmat16"])
+def test_near_far_deltas(delta, workload):
+    ro, col, w, src = graphgen.workload(workload)
+    g = gg().Graph(ro, col, w, symmetric=True)
+    ref = oracle.dijkstra(ro, col, w, src)
+    for mode in [("graph", "push"), ("graph", "auto"), ("host", "push", "bins")]:
+        got, st = run(g, src, *mode, delta=delta)
+        np.testing.assert_array_equal(got, ref, err_msg=f"delta={delta} {mode}")
+    g.close()
+
+
+def test_near_far_high_diameter_grid_reduces_work():
+    ro, col, w = graphgen.grid(256, 1000, 3)
+    g = gg().Graph(ro, col, w, symmetric=True)
+    ref = oracle.dijkstra(ro, col, w, 0)
+    got, st_bf = run(g, 0, "graph", "push", delta=NONE)
+    np.testing.assert_array_equal(got, ref)
+    got, st_nf = run(g, 0, "graph", "push", delta=500)
+    np.testing.assert_array_equal(got, ref)
+    assert st_nf["edges_scanned"] < st_bf["edges_scanned"]
+    g.close()
+
+
 def test_rmat20_config_push_pull():
     ro, col, w, src = graphgen.workload("rmat20")
     g = gg().Graph(ro, col, w, symmetric=True)
     ref = oracle.dijkstra(ro, col, w, src)
     assert sha(ref) == GOLD["rmat20"]["dist_sha256"]
-    got, st = run(g, src, "graph", "auto")
+    got, st = run(g, src, "graph", "auto", delta=NONE)
     np.testing.assert_array_equal(got, ref)
     assert st["pull_iterations"] > 0          # the switch really went to pull
     got, st = run(g, src, "graph", "push")
@@ -201,10 +229,12 @@ def test_long_path_many_supersteps():
     g = gg().Graph(ro, col, w)
     ref = oracle.dijkstra(ro, col, w, 0)
     for mode in [("graph", "push"), ("async", "auto"), ("graph", "auto")]:
-        got, st = run(g, 0, *mode)
+        got, st = run(g, 0, *mode, delta=NONE)
         np.testing.assert_array_equal(got, ref)
         if mode[0] == "graph":
             assert st["iterations"] == n - 1     # one hop per superstep on a directed path
+    got, st = run(g, 0, "graph", "push", delta=7)
+    np.testing.assert_array_equal(got, ref)
     g.close()
 
 
@@ -266,7 +296,7 @@ def test_trace_and_stats():
     ro, col, w, src = graphgen.workload("grid64")
     g = m.Graph(ro, col, w, symmetric=True)
     trace = torch.zeros(4 * 4096, dtype=torch.uint32, device="cuda")
-    got, st = run(g, src, "graph", "push", trace=trace)
+    got, st = run(g, src, "graph", "push", trace=trace, delta=NONE)
     tr = trace.cpu().numpy().reshape(-1, 4)[: st["iterations"]]
     assert tr[0, 0] == 1 and tr[0, 1] == ro[src + 1] - ro[src]
     assert np.array_equal(tr[1:, 0], tr[:-1, 3])                # next frontier size feeds the next step
