@@ -48,7 +48,7 @@ def test_duplicates_isolated_and_tiny_graphs():
         ref = oracle.dijkstra_many(ro, col, w, srcs)
         np.testing.assert_array_equal(got.T, ref)
         g.close()
-    ro = np.zeros(4, np.uint32)
+    ro = np.zeros(5, np.uint32)                     # n = 4 vertices, no edges
     g = m.Graph(ro, np.zeros(0, np.uint32), np.zeros(0, np.uint32))
     got, _ = run_batch(g, np.array([2, 0], np.uint32))
     assert got[:, 0].tolist() == [0xFFFFFFFF, 0xFFFFFFFF, 0, 0xFFFFFFFF]
