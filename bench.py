@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-batch", action="store_true", help="skip the batched 64-source RMAT-22 measurement")
+    p.add_argument("--no-serve", action="store_true", help="skip the 32-graph serving measurement")
+    p.add_argument("--serve-queries", type=int, default=2000)
     return p.parse_args()
 
 
@@ -144,6 +147,96 @@ def cpu_baseline(ro, col, w, src, seconds):
     return {"value": m_trav / t / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
             "sample": f"{len(times)} full single-source binary-heap Dijkstra runs on the same graph and source "
                       f"(median {t * 1e3:.1f} ms each, 1 host thread)"}
+
+
+def run_batched(gg, torch, k=64):
+    """Batched multi-source SSSP on RMAT-22 (64 seeded sources, one fused
+    launch sequence) vs the same 64 sources as back-to-back gg_sssp calls."""
+    import graphgen
+    ro, col, w = graphgen.rmat(22, 16, seed=1, W=255)
+    srcs = graphgen.sample_sources(ro, k, seed=1)
+    g = gg.Graph(ro, col, w, symmetric=True)
+    n = g.n
+    out = torch.empty(n * k, dtype=torch.uint32, device="cuda")
+    single = torch.empty(n, dtype=torch.uint32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    st = gg.gg_stats()
+    g.sssp_batch(srcs, out, stats=st)
+    tb = []
+    for _ in range(3):
+        e0.record()
+        g.sssp_batch(srcs, out)
+        e1.record()
+        torch.cuda.synchronize()
+        tb.append(e0.elapsed_time(e1))
+    for s_ in srcs[:4]:
+        g.sssp(int(s_), single)
+    torch.cuda.synchronize()
+    e0.record()
+    for s_ in srcs:
+        g.sssp(int(s_), single)
+    e1.record()
+    torch.cuda.synchronize()
+    t1 = e0.elapsed_time(e1)
+    d = out.view(n, k)[:, 0].cpu().numpy()
+    m_trav = int(np.diff(ro.astype(np.int64))[d != gg.GG_INF].sum())
+    g.close()
+    t = statistics.median(tb)
+    return {"workload": f"RMAT scale 22 EF16, {k} seeded sources (splitmix64 seed 1), dist matrix 4M x {k} u32",
+            "queries_per_s": k / t * 1e3, "ms": t, "back_to_back_queries_per_s": k / t1 * 1e3,
+            "back_to_back_ms": t1, "speedup": t1 / t, "supersteps": st.iterations,
+            "edges_scanned": st.edges_scanned, "gteps_aggregate_est": k * m_trav / (t * 1e-3) / 1e9}
+
+
+def run_serving(gg, torch, nq=2000):
+    """Poisson stream of (graph, source) queries over the 32-graph pool into
+    the continuous-batching server, at saturation (all queued at t=0) and at
+    50 % / 90 % of the saturation rate; vs the same queries back to back."""
+    import graphgen
+    pool = [graphgen.build_pool_graph(e) for e in graphgen.serving_pool_spec()]
+    graphs = [gg.Graph(ro, col, w, symmetric=True) for ro, col, w in pool]
+    degs = [np.diff(ro.astype(np.int64)) for ro, _, _ in pool]
+    gids, srcs, _ = graphgen.poisson_queries(degs, nq, seed=1)
+    outs = [torch.empty(graphs[gi].n, dtype=torch.uint32, device="cuda") for gi in gids]
+    maxn = max(gr.n for gr in graphs)
+    srv = gg.Server(max_graph_vertices=maxn, max_slots=64, supersteps_per_launch=8)
+
+    def stream(rate):
+        _, _, arr = graphgen.poisson_queries(degs, nq, seed=1, rate_qps=rate)
+        srv.reset_stats()
+        t0 = time.perf_counter()
+        ts = []
+        for i in range(nq):
+            if rate is not None:
+                delay = arr[i] - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+            ts.append(srv.submit(graphs[gids[i]], int(srcs[i]), outs[i]))
+        bad = sum(1 for t in ts if srv.wait(t, 600000) != 0)
+        dt = time.perf_counter() - t0
+        st = srv.stats()
+        return {"queries_per_s": nq / dt, "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
+                "max_in_flight": st["max_running"], "launches": st["launches"], "failed": bad}
+
+    stream(None)                       # warm-up pass
+    sat = stream(None)
+    loads = {}
+    for frac in (0.5, 0.9):
+        loads[f"{int(frac * 100)}pct"] = stream(sat["queries_per_s"] * frac)
+    srv.close()
+    # back to back: the same queries through gg_sssp, one after another on one stream
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(nq):
+        graphs[gids[i]].sssp(int(srcs[i]), outs[i])
+    torch.cuda.synchronize()
+    b2b = nq / (time.perf_counter() - t0)
+    for gr in graphs:
+        gr.close()
+    return {"workload": "32-graph pool (RMAT scales 12-20 EF 8/16, grids 64^2-2048^2, U[1,255]), "
+                        f"{nq} queries, graph uniform, source uniform over degree>=1, Poisson seed 1",
+            "saturation": sat, "load": loads, "back_to_back_queries_per_s": b2b,
+            "speedup": sat["queries_per_s"] / b2b}
 
 
 def workload_desc(name):
@@ -309,6 +402,12 @@ def main():
                "what": "gg_graph_create_csr from pinned host CSR + gg_sssp + distances copied to pinned host "
                        "+ gg_graph_destroy, wall clock"}
 
+    batched = serving = None
+    if not args.no_batch:
+        batched = run_batched(gg, torch)
+    if not args.no_serve:
+        serving = run_serving(gg, torch, args.serve_queries)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ro, col, w, src, args.cpu_seconds)
@@ -332,6 +431,8 @@ def main():
                          "whole_step_frac": b_all / (ms * 1e-3) / 1e9 / hbm},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "batched": batched,
+            "serving": serving,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
             "gpu": torch.cuda.get_device_name(),

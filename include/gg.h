@@ -216,6 +216,83 @@ gg_status gg_sssp_batch(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t
 gg_status gg_sssp_batch_ex(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t* dist_out,
                            const gg_options* opt, cudaStream_t stream);
 
+/* ---- many graphs in one launch sequence --------------------------------- */
+
+/* One single-source query per (graphs[i], srcs[i]) pair, all advanced
+ * together: every superstep is one kernel over the union of the queries'
+ * frontiers, balanced by edges across the GPU whatever the graphs' sizes
+ * (graphs may repeat; each query has its own distance array).
+ *   graphs     host array of count handles on the current device
+ *   srcs       host u32[count], srcs[i] < n of graphs[i]
+ *   dist_outs  host array of count device pointers, dist_outs[i] u32[n_i]
+ * Asynchronous on `stream`; the arrays are read before the call returns.
+ * The library keeps one engine per device for these calls (allocated or
+ * grown on demand); calls are ordered among themselves.  Push traversal,
+ * plain frontier loop.  Errors: GG_ERR_INVALID_ARG, GG_ERR_OUT_OF_MEMORY,
+ * GG_ERR_CUDA. */
+gg_status gg_sssp_multi(const gg_graph_t* graphs, const uint32_t* srcs, uint32_t count,
+                        uint32_t* const* dist_outs, cudaStream_t stream);
+
+/* ---- query server (continuous batching) --------------------------------- */
+
+typedef struct gg_server* gg_server_t;
+
+typedef struct {
+    uint32_t struct_size;            /* sizeof(gg_server_config)                          */
+    uint32_t max_slots;              /* queries in flight at once (0 = 64)                */
+    uint32_t max_graph_vertices;     /* largest graph that may be queried (required)      */
+    uint32_t supersteps_per_launch;  /* supersteps between admission rounds (0 = 8)       */
+    uint64_t max_vertices_in_flight; /* budget: sum of n over in-flight queries
+                                        (0 = max_slots * max_graph_vertices), capped by
+                                        the free HBM at creation                          */
+    uint64_t hbm_reserve_bytes;      /* HBM the server leaves free (default 1 GiB)        */
+} gg_server_config;
+
+typedef struct {
+    uint64_t submitted, completed;
+    uint64_t launches;               /* superstep-graph launches by the worker            */
+    uint64_t vertex_budget;          /* in-flight vertex budget in force                  */
+    uint32_t queued, running, max_running;
+    uint32_t reserved;
+    double p50_us, p99_us, mean_us, max_us;   /* submit -> completion latency           */
+} gg_server_stats;
+
+void gg_server_config_default(gg_server_config* cfg);
+
+/* Creates a server on the current device: one worker thread with its own
+ * stream runs a loop of {admit queued queries into free slots while the
+ * in-flight vertex budget allows; advance every in-flight query by up to
+ * supersteps_per_launch supersteps in one CUDA-graph launch; retire the
+ * queries whose frontier emptied}.  Queries arriving while others run join
+ * the running union frontier at the next admission round.  The in-flight
+ * budget is sized from the free HBM at creation (16 bytes of frontier state
+ * per vertex, plus two bitmaps per slot); GG_ERR_OUT_OF_MEMORY if even one
+ * graph does not fit. */
+gg_status gg_server_create(const gg_server_config* cfg, gg_server_t* out);
+
+/* Queues the query (graph g, source src) whose distances go to dist_out
+ * (device u32[n], caller-owned, untouched by anyone else until the query
+ * completes).  g must stay alive until then.  Returns a ticket.  Errors:
+ * GG_ERR_INVALID_ARG (NULLs, src >= n, graph larger than
+ * max_graph_vertices), GG_ERR_BUSY after destroy began. */
+gg_status gg_server_submit(gg_server_t s, gg_graph_t g, uint32_t src, uint32_t* dist_out, uint64_t* ticket);
+
+/* GG_ERR_NOT_READY while the query is queued or running.  When it is done:
+ * returns GG_OK, sets *result to the query's own status (GG_OK or
+ * GG_ERR_OVERFLOW) and forgets the ticket. */
+gg_status gg_server_poll(gg_server_t s, uint64_t ticket, gg_status* result);
+
+/* As poll, blocking up to timeout_ms (GG_ERR_NOT_READY on timeout). */
+gg_status gg_server_wait(gg_server_t s, uint64_t ticket, uint32_t timeout_ms, gg_status* result);
+
+/* Counters and latency percentiles over the queries completed so far. */
+gg_status gg_server_get_stats(gg_server_t s, gg_server_stats* out);
+/* Forgets the latency samples and counters (queries in flight stay). */
+gg_status gg_server_reset_stats(gg_server_t s);
+
+/* Finishes every queued and in-flight query, then frees the server. */
+gg_status gg_server_destroy(gg_server_t s);
+
 /* ---- SSSP without any device allocation ---------------------------------- */
 
 /* Largest vertex count gg_sssp_noalloc accepts. */

@@ -22,7 +22,7 @@ __all__ = [
     "GG_POLICY_BSP_GRAPH", "GG_POLICY_ASYNC_PERSISTENT", "GG_POLICY_BSP_HOST",
     "GG_DIR_AUTO", "GG_DIR_PUSH", "GG_DIR_PULL", "GG_LB_AUTO", "GG_LB_MERGE_PATH", "GG_LB_BINS", "GG_DELTA_NONE",
     "gg_graph_create_csr", "gg_graph_destroy", "gg_graph_info", "gg_graph_check", "gg_sssp", "gg_sssp_ex",
-    "gg_sssp_batch",
+    "gg_sssp_batch", "gg_sssp_multi", "Server",
     "gg_status_string", "gg_last_error", "gg_abi_version", "gg_sssp_noalloc", "GG_NOALLOC_MAX_VERTICES",
     "Graph", "lib_path", "load",
 ]
@@ -69,6 +69,23 @@ class gg_options(ctypes.Structure):
                 ("delta", ctypes.c_uint32)]
 
 
+class gg_server_config(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("max_slots", ctypes.c_uint32),
+                ("max_graph_vertices", ctypes.c_uint32), ("supersteps_per_launch", ctypes.c_uint32),
+                ("max_vertices_in_flight", ctypes.c_uint64), ("hbm_reserve_bytes", ctypes.c_uint64)]
+
+
+class gg_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("vertex_budget", ctypes.c_uint64), ("queued", ctypes.c_uint32), ("running", ctypes.c_uint32),
+                ("max_running", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("p50_us", ctypes.c_double),
+                ("p99_us", ctypes.c_double), ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: (float(getattr(self, k)) if t is ctypes.c_double else int(getattr(self, k)))
+                for k, t in self._fields_ if k != "reserved"}
+
+
 def lib_path() -> str:
     return _LIB_PATH
 
@@ -96,6 +113,15 @@ def load():
             "gg_sssp_noalloc": (ctypes.c_int, [u32, u64, vp, vp, vp, u32, vp, vp]),
             "gg_sssp_batch": (ctypes.c_int, [vp, P32, u32, vp, vp]),
             "gg_sssp_batch_ex": (ctypes.c_int, [vp, P32, u32, vp, ctypes.POINTER(gg_options), vp]),
+            "gg_sssp_multi": (ctypes.c_int, [ctypes.POINTER(vp), P32, u32, ctypes.POINTER(vp), vp]),
+            "gg_server_config_default": (None, [ctypes.POINTER(gg_server_config)]),
+            "gg_server_create": (ctypes.c_int, [ctypes.POINTER(gg_server_config), ctypes.POINTER(vp)]),
+            "gg_server_submit": (ctypes.c_int, [vp, vp, u32, vp, ctypes.POINTER(u64)]),
+            "gg_server_poll": (ctypes.c_int, [vp, u64, ctypes.POINTER(ctypes.c_int)]),
+            "gg_server_wait": (ctypes.c_int, [vp, u64, u32, ctypes.POINTER(ctypes.c_int)]),
+            "gg_server_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(gg_server_stats)]),
+            "gg_server_reset_stats": (ctypes.c_int, [vp]),
+            "gg_server_destroy": (ctypes.c_int, [vp]),
             "gg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "gg_last_error": (ctypes.c_char_p, []),
             "gg_abi_version": (u32, []),
@@ -233,6 +259,94 @@ def gg_sssp_batch(handle: int, srcs, dist_out, stream=None, options: gg_options 
     else:
         _check(load().gg_sssp_batch_ex(handle, sp, srcs.shape[0], p, ctypes.byref(options), _stream_ptr(stream)),
                "gg_sssp_batch_ex")
+
+
+def gg_sssp_multi(handles, srcs, dist_outs, stream=None):
+    """One query per (handles[i], srcs[i]) into dist_outs[i] (CUDA uint32
+    tensors), all advanced together, async."""
+    k = len(handles)
+    if not (len(srcs) == len(dist_outs) == k):
+        raise ValueError("handles, srcs and dist_outs differ in length")
+    hs = (ctypes.c_void_p * k)(*handles)
+    sp = np.ascontiguousarray(srcs, dtype=np.uint32)
+    ptrs = []
+    for d in dist_outs:
+        p, dev = _ptr(d)
+        if not dev:
+            raise ValueError("dist_outs must be CUDA tensors")
+        ptrs.append(p)
+    dp = (ctypes.c_void_p * k)(*ptrs)
+    _check(load().gg_sssp_multi(hs, sp.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), k, dp, _stream_ptr(stream)),
+           "gg_sssp_multi")
+
+
+class Server:
+    """Continuous-batching query server (gg_server_*).  Submit returns a
+    ticket; results are written to the caller's CUDA tensor."""
+
+    def __init__(self, max_graph_vertices: int, max_slots: int = 64, supersteps_per_launch: int = 8,
+                 max_vertices_in_flight: int = 0, hbm_reserve_bytes: int = 1 << 30):
+        lib = load()
+        c = gg_server_config()
+        lib.gg_server_config_default(ctypes.byref(c))
+        c.max_graph_vertices = max_graph_vertices
+        c.max_slots = max_slots
+        c.supersteps_per_launch = supersteps_per_launch
+        c.max_vertices_in_flight = max_vertices_in_flight
+        c.hbm_reserve_bytes = hbm_reserve_bytes
+        h = ctypes.c_void_p()
+        _check(lib.gg_server_create(ctypes.byref(c), ctypes.byref(h)), "gg_server_create")
+        self.handle = h.value
+        self._keep = {}
+
+    def submit(self, graph, src: int, dist_out) -> int:
+        p, dev = _ptr(dist_out)
+        if not dev:
+            raise ValueError("dist_out must be a CUDA tensor")
+        t = ctypes.c_uint64()
+        gh = graph.handle if isinstance(graph, Graph) else graph
+        _check(load().gg_server_submit(self.handle, gh, src, p, ctypes.byref(t)), "gg_server_submit")
+        self._keep[t.value] = dist_out
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending, else the query's status code (0 = GG_OK)."""
+        r = ctypes.c_int()
+        rc = load().gg_server_poll(self.handle, ticket, ctypes.byref(r))
+        if rc == 6:
+            return None
+        _check(rc, "gg_server_poll")
+        self._keep.pop(ticket, None)
+        return r.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        r = ctypes.c_int()
+        rc = load().gg_server_wait(self.handle, ticket, timeout_ms, ctypes.byref(r))
+        if rc == 6:
+            return None
+        _check(rc, "gg_server_wait")
+        self._keep.pop(ticket, None)
+        return r.value
+
+    def stats(self) -> dict:
+        st = gg_server_stats()
+        _check(load().gg_server_get_stats(self.handle, ctypes.byref(st)), "gg_server_get_stats")
+        return st.as_dict()
+
+    def reset_stats(self):
+        _check(load().gg_server_reset_stats(self.handle), "gg_server_reset_stats")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(load().gg_server_destroy(self.handle), "gg_server_destroy")
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 GG_NOALLOC_MAX_VERTICES = 1 << 20

@@ -1,21 +1,22 @@
 // gg_multi.cu -- many single-source queries on many graphs in one launch
 // sequence: the "slot" engine behind gg_sssp_multi and the query server.
 //
-// Each query occupies a slot {graph, source, caller's distance array, its
-// own two dedup bitmaps}.  All slots share ONE union frontier whose entries
-// are (slot, vertex, CSR row start, edge-prefix coordinate), so a superstep is
+// Each query occupies a slot {graph, source, caller's distance array, its own
+// two dedup bitmaps}.  All slots share ONE union frontier whose entries are
+// (slot, vertex, CSR row start, edge-prefix coordinate), so a superstep is
 // still one kernel: the merge-path advance of the single-source path splits
 // the union's edges evenly over the CTAs whatever mix of large and small
 // graphs is active, and the fused filter appends improved vertices with their
 // slot.  Per-slot counters of the next frontier tell the closing CTA which
-// queries have converged: it marks them done (device flag and, for the
-// server, a word in host-mapped memory) so new queries can take their slots
-// between supersteps -- continuous batching at superstep granularity.
+// queries have converged: it marks them done (slot state and, for the
+// server, words in host-mapped memory) so that new queries can take their
+// slots between supersteps -- continuous batching at superstep granularity.
+// The slot engine runs the plain frontier loop (no near-far buckets), push
+// only.
 #include <cuda_runtime.h>
+#include <string.h>
 
 #include <algorithm>
-#include <mutex>
-#include <vector>
 
 #include "gg_host.h"
 #include "gg_multi.h"
@@ -32,7 +33,7 @@ struct MSmem {
   uint32_t es[kMCap], eb[kMCap], ec[kMCap], eq[kMCap];
   uint32_t qv[kMCap], qr[kMCap], qd[kMCap], qq[kMCap];
   uint32_t wsum[kMB / 32];
-  uint32_t qn, j, last, ovf;
+  uint32_t qn, j, last;
   unsigned long long base;
 };
 
@@ -44,32 +45,17 @@ __device__ __forceinline__ uint2 slot_edge(const MultiSlot& s, uint32_t e) {
   return __ldg(static_cast<const uint2*>(s.edges) + e);
 }
 
-__device__ __forceinline__ void m_candidate(MSmem& sm, const MultiSlot& s, uint32_t q, uint32_t* bm_next,
-                                            uint32_t v) {
-  const uint32_t rs = __ldg(s.ro + v), re = __ldg(s.ro + v + 1);
-  if (re > rs) {
-    const uint32_t bit = 1u << (v & 31);
-    if (!(atomicOr(bm_next + (v >> 5), bit) & bit)) {
-      const uint32_t i = atomicAdd(&sm.qn, 1u);
-      sm.qv[i] = v;
-      sm.qr[i] = rs;
-      sm.qd[i] = re - rs;
-      sm.qq[i] = q;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphConditionalHandle cond, int use_cond) {
+__global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphConditionalHandle cond,
+                                                         int use_cond) {
   __shared__ MSmem sm;
   MultiCtl* ctl = b.ctl;
   const uint32_t tid = threadIdx.x;
   const uint32_t it = ctl->iter, p = it & 1u;
   const unsigned long long c = ctl->cnt[p];
   const uint32_t F = (uint32_t)(c >> 32), E = (uint32_t)c;
-  const MultiSlot* __restrict__ slots = b.slots;
-  if (tid == 0) { sm.qn = 0; sm.ovf = 0; }
+  MultiSlot* slots = b.slots;
+  if (tid == 0) sm.qn = 0;
   __syncthreads();
-  bool ovf = false;
   const uint32_t e0 = (uint32_t)(((unsigned long long)blockIdx.x * E) / gridDim.x);
   const uint32_t e1 = (uint32_t)(((unsigned long long)(blockIdx.x + 1) * E) / gridDim.x);
   if (F > 0 && e0 < e1) {
@@ -98,7 +84,7 @@ __global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphC
           sm.eb[nent + tid] = b.fr[p][idx];
           sm.ec[nent + tid] = ld_cg(sl.dist + v);
           sm.eq[nent + tid] = q;
-          b.bm_pool[sl.bm_off[p] + (v >> 5)] = 0u;   // clear the current bitmap as we go
+          b.bm_pool[sl.bm_off[p] + (v >> 5)] = 0u;   // the current bitmap is not read: clear as we go
         }
         const int cnt = __syncthreads_count(valid);
         nent += (uint32_t)cnt;
@@ -112,10 +98,24 @@ __global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphC
           const uint32_t q = sm.eq[jj];
           const MultiSlot& sl = slots[q];
           const uint2 ed = slot_edge(sl, sm.eb[jj] + (gidx - sm.es[jj]));
+          bool ovf = false;
           const uint32_t nd = add_sat(sm.ec[jj], ed.y, ovf);
+          if (ovf) atomicOr(&slots[q].status, DS_OVERFLOW);
           if (nd < ld_cg(sl.dist + ed.x)) {
             atomicMin(sl.dist + ed.x, nd);
-            m_candidate(sm, sl, q, b.bm_pool + sl.bm_off[p ^ 1u], ed.x);
+            // filter: append once per slot and superstep, skip vertices without out-edges
+            const uint32_t v = ed.x;
+            const uint32_t rs = __ldg(sl.ro + v), re = __ldg(sl.ro + v + 1);
+            if (re > rs) {
+              const uint32_t bit = 1u << (v & 31);
+              if (!(atomicOr(b.bm_pool + sl.bm_off[p ^ 1u] + (v >> 5), bit) & bit)) {
+                const uint32_t i = atomicAdd(&sm.qn, 1u);
+                sm.qv[i] = v;
+                sm.qr[i] = rs;
+                sm.qd[i] = re - rs;
+                sm.qq[i] = q;
+              }
+            }
           }
         }
       }
@@ -140,30 +140,25 @@ __global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphC
       j = j + nent - 1;
     }
   }
-  if (ovf) sm.ovf = 1u;
   __syncthreads();
   if (tid == 0) {
     __threadfence();
     sm.last = (atomicAdd(&ctl->done_ctas, 1u) == gridDim.x - 1) ? 1u : 0u;
   }
   __syncthreads();
-  if (sm.ovf) atomicOr(&ctl->ovf_any, 1u);
   if (sm.last) {
-    // the closing CTA: converged slots are done; per-slot counters restart
+    // the closing CTA: slots with nothing in the next frontier have converged
     __threadfence();
-    const unsigned long long cn = atomicAdd(&ctl->cnt[p ^ 1u], 0ull);
-    const uint32_t ovf_any = atomicAdd(&ctl->ovf_any, 0u);
     for (uint32_t q = tid; q < b.nslots; q += kMB) {
-      MultiSlot* sl = b.slots_rw + q;
-      if (sl->state == kSlotRunning) {
-        const uint32_t cq = b.slot_cnt[q];
-        sl->supersteps += 1;
-        if (ovf_any) sl->status |= DS_OVERFLOW;
-        if (cq == 0) {
-          sl->state = kSlotDone;
+      MultiSlot& sl = slots[q];
+      if (sl.state == kSlotRunning) {
+        sl.supersteps += 1;
+        if (b.slot_cnt[q] == 0) {
+          sl.state = kSlotDone;
           if (b.done_flags) {
+            b.done_status[q] = sl.status;
             __threadfence_system();
-            reinterpret_cast<volatile uint32_t*>(b.done_flags)[q] = sl->ticket;
+            reinterpret_cast<volatile uint32_t*>(b.done_flags)[q] = sl.ticket;
           }
         }
       }
@@ -171,46 +166,46 @@ __global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphC
     }
     __syncthreads();
     if (tid == 0) {
-      ctl->ovf_any = 0u;
+      const unsigned long long cn = atomicAdd(&ctl->cnt[p ^ 1u], 0ull);
       ctl->cnt[p] = 0ull;
       ctl->done_ctas = 0u;
       ctl->iter = it + 1;
       ctl->supersteps_run += 1;
-      const bool more = (cn >> 32) != 0 && ctl->budget_left > 1;
-      if (ctl->budget_left) ctl->budget_left -= 1;
-      ctl->running = (cn >> 32) != 0 ? 1u : 0u;
-      if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+      const bool nonempty = (cn >> 32) != 0;
+      const uint32_t left = ctl->budget_left > 0 ? ctl->budget_left - 1 : 0;
+      ctl->budget_left = left;
+      ctl->running = nonempty ? 1u : 0u;
+      if (use_cond) cudaGraphSetConditional(cond, (nonempty && left > 0) ? 1u : 0u);
     }
   }
 }
 
-// dist := INF for every vertex of every slot in `starting` (blockIdx.y = list index)
+// dist := INF and bitmaps := 0 for every slot in `starting` (blockIdx.y walks the list)
 __global__ void k_multi_fill(MultiBufs b, const uint32_t* starting, uint32_t nstart) {
   for (uint32_t i = blockIdx.y; i < nstart; i += gridDim.y) {
     const MultiSlot& sl = b.slots[starting[i]];
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < sl.n; v += gridDim.x * blockDim.x)
-      sl.dist[v] = kInf;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < sl.n; v += stride) sl.dist[v] = kInf;
     const uint32_t nw = (sl.n + 31) / 32;
-    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nw; v += gridDim.x * blockDim.x) {
+    for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nw; v += stride) {
       b.bm_pool[sl.bm_off[0] + v] = 0u;
       b.bm_pool[sl.bm_off[1] + v] = 0u;
     }
   }
 }
 
-// seed the starting slots into the frontier of the current parity
+// seed the starting slots into the union frontier of the current parity
 __global__ void k_multi_seed(MultiBufs b, const uint32_t* starting, uint32_t nstart) {
   MultiCtl* ctl = b.ctl;
   const uint32_t p = ctl->iter & 1u;
   for (uint32_t i = threadIdx.x; i < nstart; i += blockDim.x) {
     const uint32_t q = starting[i];
-    MultiSlot* sl = b.slots_rw + q;
-    const uint32_t src = sl->src;
-    sl->dist[src] = 0u;
-    const uint32_t rs = sl->ro[src], re = sl->ro[src + 1];
+    MultiSlot& sl = b.slots[q];
+    const uint32_t src = sl.src;
+    sl.dist[src] = 0u;
+    const uint32_t rs = sl.ro[src], re = sl.ro[src + 1];
     if (re > rs) {
-      sl->state = kSlotRunning;
-      b.bm_pool[sl->bm_off[p] + (src >> 5)] |= 0u;   // membership of the seed needs no bit (push only)
+      sl.state = kSlotRunning;
       const unsigned long long base = atomicAdd(&ctl->cnt[p], (1ull << 32) | (re - rs));
       const uint32_t pos = (uint32_t)(base >> 32);
       b.fv[p][pos] = src;
@@ -218,18 +213,21 @@ __global__ void k_multi_seed(MultiBufs b, const uint32_t* starting, uint32_t nst
       b.fs[p][pos] = (uint32_t)base;
       b.fq[p][pos] = q;
     } else {
-      sl->state = kSlotDone;   // nothing to expand: dist is final already
+      sl.state = kSlotDone;   // nothing to expand: dist is final already
       if (b.done_flags) {
+        b.done_status[q] = sl.status;
         __threadfence_system();
-        reinterpret_cast<volatile uint32_t*>(b.done_flags)[q] = sl->ticket;
+        reinterpret_cast<volatile uint32_t*>(b.done_flags)[q] = sl.ticket;
       }
     }
   }
+  __syncthreads();
+  if (threadIdx.x == 0) ctl->running = ctl->cnt[p] != 0ull ? 1u : 0u;
 }
 
-}  // namespace
+__global__ void k_multi_budget(MultiCtl* ctl, uint32_t budget) { ctl->budget_left = budget; }
 
-// ---- host side ---------------------------------------------------------------
+}  // namespace
 
 gg_status multi_engine_init(MultiEngine* e, uint32_t max_slots, uint64_t max_vertices, uint64_t max_bitmap_words,
                             bool mapped_flags) {
@@ -238,14 +236,13 @@ gg_status multi_engine_init(MultiEngine* e, uint32_t max_slots, uint64_t max_ver
   e->cap_words = max_bitmap_words;
   auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t fb = r256(4 * std::max<uint64_t>(max_vertices, 1));
-  const size_t total = 8 * fb + 2 * r256(sizeof(MultiSlot) * max_slots) * 0 + r256(sizeof(MultiSlot) * max_slots) +
-                       r256(4 * (size_t)max_slots) + r256(4 * std::max<uint64_t>(max_bitmap_words, 1)) +
-                       r256(sizeof(MultiCtl)) + r256(4 * (size_t)max_slots);
+  const size_t total = 8 * fb + r256(sizeof(MultiSlot) * max_slots) + 2 * r256(4 * (size_t)max_slots) +
+                       r256(4 * std::max<uint64_t>(max_bitmap_words, 1)) + r256(sizeof(MultiCtl));
   char* p = nullptr;
   GG_CK(cudaMalloc(&p, total));
-  GG_CK(cudaMemset(p, 0, total));
   e->block = p;
   e->bytes = total;
+  GG_CK(cudaMemset(p, 0, total));
   size_t off = 0;
   auto take = [&](size_t bytes) { char* q = p + off; off += r256(bytes); return q; };
   for (int i = 0; i < 2; ++i) {
@@ -254,29 +251,31 @@ gg_status multi_engine_init(MultiEngine* e, uint32_t max_slots, uint64_t max_ver
     e->b.fs[i] = reinterpret_cast<uint32_t*>(take(fb));
     e->b.fq[i] = reinterpret_cast<uint32_t*>(take(fb));
   }
-  e->b.slots_rw = reinterpret_cast<MultiSlot*>(take(sizeof(MultiSlot) * max_slots));
-  e->b.slots = e->b.slots_rw;
+  e->b.slots = reinterpret_cast<MultiSlot*>(take(sizeof(MultiSlot) * max_slots));
   e->b.slot_cnt = reinterpret_cast<uint32_t*>(take(4 * (size_t)max_slots));
+  e->starting = reinterpret_cast<uint32_t*>(take(4 * (size_t)max_slots));
   e->b.bm_pool = reinterpret_cast<uint32_t*>(take(4 * std::max<uint64_t>(max_bitmap_words, 1)));
   e->b.ctl = reinterpret_cast<MultiCtl*>(take(sizeof(MultiCtl)));
-  e->starting = reinterpret_cast<uint32_t*>(take(4 * (size_t)max_slots));
   e->b.nslots = max_slots;
-  if (off > total) return fail(GG_ERR_INTERNAL, "multi workspace layout");
+  if (off != total) return fail(GG_ERR_INTERNAL, "multi workspace layout");
   GG_CK(cudaMallocHost(&e->h_slots, sizeof(MultiSlot) * max_slots));
   GG_CK(cudaMallocHost(&e->h_ctl, sizeof(MultiCtl)));
   GG_CK(cudaMallocHost(&e->h_start, 4 * (size_t)max_slots));
   memset(e->h_slots, 0, sizeof(MultiSlot) * max_slots);
+  e->b.done_flags = nullptr;
+  e->b.done_status = nullptr;
   if (mapped_flags) {
     GG_CK(cudaHostAlloc(&e->h_done, 4 * (size_t)max_slots, cudaHostAllocMapped));
+    GG_CK(cudaHostAlloc(&e->h_done_status, 4 * (size_t)max_slots, cudaHostAllocMapped));
     memset(e->h_done, 0, 4 * (size_t)max_slots);
+    memset(e->h_done_status, 0, 4 * (size_t)max_slots);
     GG_CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&e->b.done_flags), e->h_done, 0));
-  } else {
-    e->b.done_flags = nullptr;
+    GG_CK(cudaHostGetDevicePointer(reinterpret_cast<void**>(&e->b.done_status), e->h_done_status, 0));
   }
   int per_sm = 0;
   GG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi_superstep, kMB, 0));
   e->grid = std::max(1, per_sm) * device_info().num_sms;
-  // CUDA graph: WHILE (frontier non-empty and superstep budget left) { superstep }
+  // CUDA graph: WHILE (union frontier non-empty and budget left) { superstep }
   GG_CK(cudaGraphCreate(&e->graph, 0));
   cudaGraphConditionalHandle h;
   GG_CK(cudaGraphConditionalHandleCreate(&h, e->graph, 1, cudaGraphCondAssignDefault));
@@ -309,29 +308,27 @@ void multi_engine_free(MultiEngine* e) {
   if (e->h_ctl) cudaFreeHost(e->h_ctl);
   if (e->h_start) cudaFreeHost(e->h_start);
   if (e->h_done) cudaFreeHost(e->h_done);
+  if (e->h_done_status) cudaFreeHost(e->h_done_status);
   *e = MultiEngine{};
 }
 
 gg_status multi_engine_reset(MultiEngine* e, cudaStream_t s) {
-  MultiCtl c{};
-  memcpy(e->h_ctl, &c, sizeof(c));
-  GG_CK(cudaMemcpyAsync(e->b.ctl, e->h_ctl, sizeof(MultiCtl), cudaMemcpyHostToDevice, s));
+  GG_CK(cudaMemsetAsync(e->b.ctl, 0, sizeof(MultiCtl), s));
   GG_CK(cudaMemsetAsync(e->b.slot_cnt, 0, 4 * (size_t)e->max_slots, s));
   return GG_OK;
 }
 
 gg_status multi_engine_start(MultiEngine* e, const uint32_t* slots, uint32_t count, cudaStream_t s) {
   if (count == 0) return GG_OK;
-  // slot descriptors (host copy is authoritative for the static fields)
+  uint32_t nmax = 1;
   for (uint32_t i = 0; i < count; ++i) {
     const uint32_t q = slots[i];
     e->h_start[i] = q;
-    GG_CK(cudaMemcpyAsync(e->b.slots_rw + q, e->h_slots + q, sizeof(MultiSlot), cudaMemcpyHostToDevice, s));
+    nmax = std::max(nmax, e->h_slots[q].n);
+    GG_CK(cudaMemcpyAsync(e->b.slots + q, e->h_slots + q, sizeof(MultiSlot), cudaMemcpyHostToDevice, s));
   }
   GG_CK(cudaMemcpyAsync(e->starting, e->h_start, 4 * (size_t)count, cudaMemcpyHostToDevice, s));
-  uint32_t nmax = 1;
-  for (uint32_t i = 0; i < count; ++i) nmax = std::max(nmax, e->h_slots[slots[i]].n);
-  dim3 grid((unsigned)std::min<uint32_t>((nmax + 255) / 256, 1024), (unsigned)std::min<uint32_t>(count, 1024));
+  dim3 grid((unsigned)std::min<uint32_t>((nmax + 255) / 256, 512), (unsigned)std::min<uint32_t>(count, 1024));
   k_multi_fill<<<grid, 256, 0, s>>>(e->b, e->starting, count);
   GG_CK(cudaGetLastError());
   k_multi_seed<<<1, 256, 0, s>>>(e->b, e->starting, count);
@@ -340,9 +337,8 @@ gg_status multi_engine_start(MultiEngine* e, const uint32_t* slots, uint32_t cou
 }
 
 gg_status multi_engine_run(MultiEngine* e, uint32_t budget, cudaStream_t s) {
-  // budget: supersteps this launch may run (0 = until the union frontier empties)
-  GG_CK(cudaMemcpyAsync(&e->b.ctl->budget_left, &e->budget_words[budget ? 1 : 0], 4, cudaMemcpyHostToDevice, s));
-  (void)budget;
+  k_multi_budget<<<1, 1, 0, s>>>(e->b.ctl, budget ? budget : 0xFFFFFFFFu);
+  GG_CK(cudaGetLastError());
   GG_CK(cudaGraphLaunch(e->exec, s));
   return GG_OK;
 }
