@@ -45,7 +45,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gg", choices=["gg", "reference"])
     p.add_argument("--workload", default="rmat20")
-    p.add_argument("--policy", default="graph", choices=["graph", "async", "host"])
+    p.add_argument("--policy", default="graph", choices=["graph", "async", "host", "persistent"])
     p.add_argument("--direction", default="auto", choices=["auto", "push", "pull"])
     p.add_argument("--lb", default="mp", choices=["mp", "bins"])
     p.add_argument("--delta", type=int, default=0, help="near-far bucket width (0 = graph default, -1 = none)")
@@ -299,7 +299,7 @@ def main():
     ro, col, w, src = graphgen.workload(args.workload)
     n, m = int(ro.shape[0] - 1), int(col.shape[0])
     policy = {"graph": gg.GG_POLICY_BSP_GRAPH, "async": gg.GG_POLICY_ASYNC_PERSISTENT,
-              "host": gg.GG_POLICY_BSP_HOST}[args.policy]
+              "host": gg.GG_POLICY_BSP_HOST, "persistent": gg.GG_POLICY_BSP_PERSISTENT}[args.policy]
     direction = {"auto": gg.GG_DIR_AUTO, "push": gg.GG_DIR_PUSH, "pull": gg.GG_DIR_PULL}[args.direction]
     stream = torch.cuda.current_stream()
     g = gg.Graph(ro, col, w, symmetric=True, stream=stream)
@@ -377,6 +377,8 @@ def main():
     launches_per_step = 2 + (iters if policy != gg.GG_POLICY_ASYNC_PERSISTENT else 1)
     if policy == gg.GG_POLICY_ASYNC_PERSISTENT:
         launches_per_step = 3   # init, seed, persistent kernel (plus one memset node)
+    elif policy == gg.GG_POLICY_BSP_PERSISTENT:
+        launches_per_step = 3   # init, init tail, persistent superstep kernel
 
     # end to end through the public API with host buffers: upload the CSR from
     # pinned memory, run, read the distances back, free the handle

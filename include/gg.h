@@ -87,8 +87,11 @@ typedef enum {
                                        conditional WHILE node tests frontier size != 0 */
     GG_POLICY_ASYNC_PERSISTENT = 1, /* one persistent kernel over a device work queue,
                                        no barriers, device-side termination detection */
-    GG_POLICY_BSP_HOST = 2          /* the same supersteps launched one by one from the
+    GG_POLICY_BSP_HOST = 2,         /* the same supersteps launched one by one from the
                                        host (for comparison and per-kernel timing)   */
+    GG_POLICY_BSP_PERSISTENT = 3    /* the same supersteps in one cooperative launch,
+                                       separated by a bounded grid barrier (no launch
+                                       per superstep: for high-diameter graphs)      */
 } gg_policy;
 
 /* Traversal direction (Sec. III-C): push over CSR, pull over CSC. */

@@ -67,7 +67,8 @@ struct FilterOut {
   unsigned long long* cnt_next;   // (count << 32) | edges of the next frontier
   uint32_t *nfv, *nfr, *nfs;
   uint32_t* far;                  // far pile being appended to
-  uint32_t* far_cnt;
+  uint32_t* far_cnt;              // its append position
+  uint32_t* far_add;              // per-superstep count of far appends (or NULL)
 };
 
 // Filter: vertex v whose distance just dropped to nd.  Vertices without
@@ -109,7 +110,10 @@ __device__ __forceinline__ void filter_flush(MPSmem<BLOCK, EPT>& sm, const Filte
     const uint32_t tot = block_scan_excl<BLOCK>(sm.qd, qn, sm.wsum);
     if (threadIdx.x == 0) sm.base = atomicAdd(fo.cnt_next, ((unsigned long long)qn << 32) | tot);
   }
-  if (qfn && threadIdx.x == 0) sm.fbase = atomicAdd(fo.far_cnt, qfn);
+  if (qfn && threadIdx.x == 0) {
+    sm.fbase = atomicAdd(fo.far_cnt, qfn);
+    if (fo.far_add) atomicAdd(fo.far_add, qfn);
+  }
   __syncthreads();
   const unsigned long long b = sm.base;
   const uint32_t pos0 = (uint32_t)(b >> 32), eb0 = (uint32_t)b;
@@ -390,14 +394,15 @@ __device__ __forceinline__ void far_split(MPSmem<BLOCK, EPT>& sm, const StepArgs
 
 // Shared prologue: reset the CTA's queue, clear the bitmap left by a pull step.
 template <int BLOCK, int EPT>
-__device__ __forceinline__ void superstep_prologue(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t it) {
+__device__ __forceinline__ void superstep_prologue(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t it,
+                                                   bool clear_prev) {
   if (threadIdx.x == 0) {
     sm.qn = 0;
     sm.qfn = 0;
     sm.fmin = kInf;
     sm.ovf = 0;
   }
-  if (a.ctl->clear_prev) {
+  if (clear_prev) {
     uint32_t* bm_old = a.fr.bm[(it + 2) % 3];
     for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < a.g.nwords; i += gridDim.x * BLOCK) bm_old[i] = 0u;
   }
@@ -518,7 +523,8 @@ __global__ void __launch_bounds__(BLOCK, 4) k_superstep(StepArgs a, cudaGraphCon
   // a split step reads far[fp] and keeps entries in far[fp^1]; other steps append to far[fp]
   fo.far = a.fr.far[mode == MODE_SPLIT ? fp ^ 1u : fp];
   fo.far_cnt = &ctl->far_cnt[mode == MODE_SPLIT ? fp ^ 1u : fp];
-  superstep_prologue(sm, a, it);
+  fo.far_add = nullptr;
+  superstep_prologue(sm, a, it, ctl->clear_prev != 0);
   if (mode == MODE_SPLIT) {
     far_split(sm, a, fo, dist, a.fr.far[fp], ctl->far_cnt[fp], ctl->t_prev);
   } else if (f > 0) {
@@ -535,6 +541,176 @@ __global__ void __launch_bounds__(BLOCK, 4) k_superstep(StepArgs a, cudaGraphCon
     }
   }
   superstep_finalize(sm, a, it, f, E, mode, cond, use_cond);
+}
+
+// Bounded grid barrier for the persistent kernel: generation counter, the
+// last CTA to arrive bumps it.  Waits give up at the run's deadline (or when
+// another CTA has aborted) and raise `abort`, so no CTA spins forever.
+__device__ __forceinline__ void grid_barrier(Ctl* ctl, unsigned long long deadline) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile uint32_t* gen = &ctl->bar_gen;
+    const uint32_t g = *gen;
+    __threadfence();
+    if (atomicAdd(&ctl->bar_count, 1u) == gridDim.x - 1) {
+      ctl->bar_count = 0u;
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      uint32_t spins = 0;
+      while (*gen == g) {
+        if (*(volatile uint32_t*)&ctl->abort) break;
+        if ((++spins & 63u) == 0 && bsp_globaltimer() > deadline) {
+          atomicOr(&ctl->status, DS_TIMEOUT);
+          atomicExch(&ctl->abort, 1u);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// All supersteps of one run in one cooperative launch (grid <= co-resident
+// CTAs).  Each superstep is the same work as k_superstep; instead of a kernel
+// boundary, one grid barrier separates supersteps, after which every CTA reads
+// the same final counters and takes the same decision (next step's kind,
+// thresholds, termination) in its own registers.  Counters rotate over three
+// slots (a slot is reset two supersteps after its last reader passed a
+// barrier); the far pile rotates over three piles, one per split step.
+template <int BLOCK, int EPT, bool BINS, bool PK>
+__global__ void __launch_bounds__(BLOCK, 4) k_bsp_persistent(StepArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  MPSmem<BLOCK, EPT>& sm = *reinterpret_cast<MPSmem<BLOCK, EPT>*>(smraw);
+  Ctl* ctl = a.ctl;
+  uint32_t* dist = ctl->dist;
+  const unsigned long long deadline = ctl->t_start + ctl->watchdog_ns;
+  const uint32_t dir = ctl->dir, alpha = ctl->alpha, beta = ctl->beta, delta = ctl->delta;
+  const uint32_t max_iter = ctl->max_iter;
+  uint32_t it = 0, mode = ctl->mode, t_cur = ctl->t_cur, t_prev = 0, splits = 0, run_fmin = kInf;
+  uint32_t nfar = 0;   // far-pile size, tracked identically by every CTA
+  bool clear = false;
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  unsigned long long edges_scanned = 0, frontier_total = 0;
+  uint32_t max_frontier = 0, pull_iters = 0;
+  for (;;) {
+    const uint32_t s0 = it % 3, s1 = (it + 1) % 3, s2 = (it + 2) % 3;
+    const uint32_t pile = splits % 3, pile_out = (splits + 1) % 3;
+    const unsigned long long c = *(volatile unsigned long long*)&ctl->cnt3[s0];
+    const uint32_t f = (uint32_t)(c >> 32), E = (uint32_t)c;
+    const uint32_t p = it & 1u;
+    uint32_t* bm_cur = a.fr.bm[s0];
+    FilterOut fo;
+    fo.ro = a.g.ro;
+    fo.bm_next = a.fr.bm[s1];
+    fo.bm_far = a.fr.bm_far;
+    fo.t_cur = t_cur;
+    fo.cnt_next = &ctl->cnt3[s1];
+    fo.nfv = a.fr.fv[p ^ 1u];
+    fo.nfr = a.fr.fr[p ^ 1u];
+    fo.nfs = a.fr.fs[p ^ 1u];
+    fo.far = a.fr.far[mode == MODE_SPLIT ? pile_out : pile];
+    fo.far_cnt = &ctl->fcnt3[mode == MODE_SPLIT ? pile_out : pile];
+    fo.far_add = &ctl->fadd3[s0];
+    superstep_prologue(sm, a, it, clear);
+    if (lead) {
+      ctl->cnt3[s2] = 0ull;      // written next superstep; its readers are two barriers back
+      ctl->fm3[s1] = kInf;       // written next superstep
+      ctl->fadd3[s1] = 0u;
+      if (mode == MODE_SPLIT) ctl->fcnt3[(splits + 2) % 3] = 0u;   // output pile of the next split
+    }
+    if (mode == MODE_SPLIT) {
+      far_split(sm, a, fo, dist, a.fr.far[pile], nfar, t_prev);
+    } else if (f > 0) {
+      if (mode == MODE_PUSH) {
+        if (BINS)
+          bins_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fv[p], a.fr.fr[p], a.fr.fs[p], dist, bm_cur, fo,
+                                       ctl->warp_thr, ctl->cta_thr);
+        else
+          mp_advance<BLOCK, EPT, false, PK>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], a.g.edges, dist,
+                                            bm_cur, fo);
+      } else {
+        mp_advance<BLOCK, EPT, true, PK>(sm, a, a.g.np, a.g.m, a.g.ps, a.g.ps, a.g.pv, a.g.t_edges, dist,
+                                         bm_cur, fo);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (sm.ovf) atomicOr(&ctl->status, DS_OVERFLOW);
+      if (sm.fmin != kInf) atomicMin(&ctl->fm3[s0], sm.fmin);
+      if (blockIdx.x == 0 && bsp_globaltimer() > deadline) {
+        atomicOr(&ctl->status, DS_TIMEOUT);
+        atomicExch(&ctl->abort, 1u);
+      }
+    }
+    grid_barrier(ctl, deadline);
+    // every CTA takes the same decision from the same final counters
+    const unsigned long long cn = *(volatile unsigned long long*)&ctl->cnt3[s1];
+    const uint32_t fn = (uint32_t)(cn >> 32), En = (uint32_t)cn;
+    // far-pile size: a split keeps fadd3 entries; other steps add fadd3 entries
+    const uint32_t added = *(volatile uint32_t*)&ctl->fadd3[s0];
+    if (mode == MODE_SPLIT) {
+      ++splits;
+      nfar = added;
+    } else {
+      nfar += added;
+    }
+    run_fmin = min(run_fmin, *(volatile uint32_t*)&ctl->fm3[s0]);
+    if (lead) {
+      if (ctl->trace && it < ctl->trace_cap) {
+        uint32_t* t = ctl->trace + 4ull * it;
+        t[0] = f;
+        t[1] = mode == MODE_PUSH ? E : mode == MODE_PULL ? a.g.m : 0u;
+        t[2] = mode;
+        t[3] = fn;
+      }
+      if (f > 0 && mode != MODE_SPLIT) {
+        edges_scanned += mode == MODE_PUSH ? E : a.g.m;
+        frontier_total += f;
+        max_frontier = max(max_frontier, f);
+        pull_iters += mode == MODE_PULL ? 1u : 0u;
+      }
+    }
+    uint32_t nm;
+    if (fn == 0 && nfar > 0) {
+      nm = MODE_SPLIT;
+      const unsigned long long t1 = (unsigned long long)t_cur + delta;
+      const unsigned long long t2 = (unsigned long long)run_fmin + 1;
+      const unsigned long long tn = t1 > t2 ? t1 : t2;
+      t_prev = t_cur;
+      t_cur = tn >= kInf ? kInf : (uint32_t)tn;
+      run_fmin = kInf;
+    } else if (dir == DIR_PUSH) {
+      nm = MODE_PUSH;
+    } else if (dir == DIR_PULL) {
+      nm = MODE_PULL;
+    } else if (mode != MODE_PULL) {
+      nm = ((unsigned long long)En * alpha > a.g.m) ? MODE_PULL : MODE_PUSH;
+    } else {
+      nm = ((unsigned long long)fn * beta < a.g.np) ? MODE_PUSH : MODE_PULL;
+    }
+    clear = mode == MODE_PULL;
+    mode = nm;
+    ++it;
+    const bool more = fn != 0 || nfar != 0;
+    const bool aborted = *(volatile uint32_t*)&ctl->abort != 0;
+    if (!more || aborted || it >= max_iter) {
+      if (lead) {
+        if (more && !aborted) atomicOr(&ctl->status, DS_ITER_CAP);
+        ctl->iter = it;
+        ctl->mode = mode;
+        ctl->splits = splits;
+        ctl->edges_scanned = edges_scanned;
+        ctl->frontier_total = frontier_total;
+        ctl->max_frontier = max_frontier;
+        ctl->pull_iters = pull_iters;
+        ctl->running = 0u;
+      }
+      break;
+    }
+  }
 }
 
 // Per-run parameters written into the control block by k_init_tail.
@@ -613,6 +789,17 @@ __global__ void k_init_tail(StepArgs a, RunParams rp) {
   ctl->far_min = kInf;
   ctl->splits = 0;
   ctl->watchdog_ns = rp.watchdog_ns;
+  ctl->cnt3[0] = ctl->cnt[0];
+  ctl->cnt3[1] = 0ull;
+  ctl->cnt3[2] = 0ull;
+  for (int i = 0; i < 3; ++i) {
+    ctl->fm3[i] = kInf;
+    ctl->fcnt3[i] = 0u;
+    ctl->fadd3[i] = 0u;
+  }
+  ctl->bar_count = 0u;
+  ctl->bar_gen = 0u;
+  ctl->abort = 0u;
   ctl->t_start = bsp_globaltimer();
   ctl->edges_scanned = 0;
   ctl->frontier_total = 0;
@@ -633,6 +820,29 @@ void* superstep_fn(int variant) {
 
 size_t superstep_smem(int) { return sizeof(MPSmem<kBlock, kEpt>); }
 
+void* persistent_fn(int variant) {
+  switch (variant) {
+    case 1: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, true, false>);
+    case 2: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, false, true>);
+    case 3: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, true, true>);
+    default: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, false, false>);
+  }
+}
+
+// co-resident grid of the persistent kernel (cooperative launch limit)
+int persistent_grid(int variant) {
+  static int cached[4] = {0, 0, 0, 0};
+  if (cached[variant]) return cached[variant];
+  const DeviceInfo di = device_info();
+  int per_sm = 0;
+  void* fn = persistent_fn(variant);
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)superstep_smem(variant));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, superstep_smem(variant));
+  if (per_sm < 1) per_sm = 1;
+  cached[variant] = per_sm * di.num_sms;
+  return cached[variant];
+}
+
 gg_status ensure_workspace(gg_graph* g) {
   BspWorkspace& w = g->bsp;
   if (w.block) return GG_OK;
@@ -641,7 +851,7 @@ gg_status ensure_workspace(gg_graph* g) {
   const size_t fbytes = sizeof(uint32_t) * std::max<size_t>(n, 1);
   auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
   // every sub-buffer starts on a 256-byte boundary
-  const size_t total = 8 * r256(fbytes) + 4 * r256(sizeof(uint32_t) * nw) + r256(sizeof(Ctl));
+  const size_t total = 9 * r256(fbytes) + 4 * r256(sizeof(uint32_t) * nw) + r256(sizeof(Ctl));
   char* p = nullptr;
   GG_CK(cudaMalloc(&p, total));
   GG_CK(cudaMemset(p, 0, total));
@@ -655,7 +865,7 @@ gg_status ensure_workspace(gg_graph* g) {
     w.fr.fs[i] = reinterpret_cast<uint32_t*>(take(fbytes));
   }
   for (int i = 0; i < 3; ++i) w.fr.bm[i] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * nw));
-  for (int i = 0; i < 2; ++i) w.fr.far[i] = reinterpret_cast<uint32_t*>(take(fbytes));
+  for (int i = 0; i < 3; ++i) w.fr.far[i] = reinterpret_cast<uint32_t*>(take(fbytes));
   w.fr.bm_far = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * nw));
   w.ctl = reinterpret_cast<Ctl*>(take(sizeof(Ctl)));
   if (off != total) return fail(GG_ERR_INTERNAL, "workspace layout");
@@ -744,7 +954,11 @@ gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o
   GG_CK(cudaGetLastError());
   k_init_tail<<<1, 1, 0, s>>>(a, rp);
   GG_CK(cudaGetLastError());
-  if (o.policy == GG_POLICY_BSP_GRAPH) {
+  if (o.policy == GG_POLICY_BSP_PERSISTENT) {
+    void* args[] = {&a};
+    GG_CK(cudaLaunchCooperativeKernel(persistent_fn(variant), dim3(persistent_grid(variant)), dim3(kBlock), args,
+                                      superstep_smem(variant), s));
+  } else if (o.policy == GG_POLICY_BSP_GRAPH) {
     st = build_graph_exec(g, variant);
     if (st != GG_OK) return st;
     GG_CK(cudaGraphLaunch(w.exec[variant], s));

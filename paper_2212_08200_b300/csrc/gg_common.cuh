@@ -62,6 +62,13 @@ struct Ctl {
   uint32_t far_cnt[2];
   uint32_t far_min;            // lower bound of the distances recorded in the far pile
   uint32_t splits;
+  // persistent bulk-synchronous kernel: counters rotate over three slots so
+  // that one grid barrier per superstep suffices
+  unsigned long long cnt3[3];
+  uint32_t fm3[3];             // smallest far distance recorded in a superstep
+  uint32_t fcnt3[3];           // far-pile append positions (pile rotates with each split step)
+  uint32_t fadd3[3];           // far entries appended in a superstep (what decisions read)
+  uint32_t bar_count, bar_gen, abort;
   unsigned long long t_start;  // %globaltimer at init (watchdog)
   unsigned long long watchdog_ns;
   unsigned long long edges_scanned;
@@ -85,7 +92,8 @@ struct Frontier {
   uint32_t* fr[2];
   uint32_t* fs[2];
   uint32_t* bm[3];
-  uint32_t* far[2];    // far pile (vertex ids), ping-pong across split steps
+  uint32_t* far[3];    // far pile (vertex ids): ping-pong across split steps (three
+                       // rotating piles in the persistent kernel)
   uint32_t* bm_far;    // far-pile membership (dedup)
 };
 

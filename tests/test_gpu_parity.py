@@ -27,14 +27,16 @@ def gg():
     return m
 
 
-POLICIES = {"graph": 0, "async": 1, "host": 2}
+POLICIES = {"graph": 0, "async": 1, "host": 2, "persistent": 3}
 DIRS = {"auto": 0, "push": 1, "pull": 2}
 LB = {"mp": 1, "bins": 2}
 NONE = 0xFFFFFFFF
 # (policy, direction, load balance, near-far delta; 0 = the graph's default)
 MODES = [("graph", "auto"), ("graph", "push"), ("graph", "pull"), ("host", "auto"), ("host", "pull"),
          ("async", "auto"), ("graph", "push", "bins"), ("host", "auto", "bins"),
-         ("graph", "push", "mp", NONE), ("graph", "auto", "mp", 1), ("graph", "push", "bins", 3)]
+         ("graph", "push", "mp", NONE), ("graph", "auto", "mp", 1), ("graph", "push", "bins", 3),
+         ("persistent", "push"), ("persistent", "auto", "mp", NONE), ("persistent", "pull"),
+         ("persistent", "push", "bins", 5)]
 
 
 def run(g, src, policy="graph", direction="auto", lb="mp", delta=0, **kw):
@@ -123,7 +125,8 @@ def test_near_far_deltas(delta, workload):
     ro, col, w, src = graphgen.workload(workload)
     g = gg().Graph(ro, col, w, symmetric=True)
     ref = oracle.dijkstra(ro, col, w, src)
-    for mode in [("graph", "push"), ("graph", "auto"), ("host", "push", "bins")]:
+    for mode in [("graph", "push"), ("graph", "auto"), ("host", "push", "bins"), ("persistent", "push"),
+                 ("persistent", "auto")]:
         got, st = run(g, src, *mode, delta=delta)
         np.testing.assert_array_equal(got, ref, err_msg=f"delta={delta} {mode}")
     g.close()
@@ -163,7 +166,7 @@ def test_rmat20_config_push_pull():
 def test_full_size_configs_against_golden(name):
     ro, col, w, src = graphgen.workload(name)
     g = gg().Graph(ro, col, w, symmetric=True)
-    modes = [("graph", "auto"), ("async", "auto")]
+    modes = [("graph", "auto"), ("async", "auto"), ("persistent", "push")]
     for mode in modes:
         got, st = run(g, src, *mode)
         assert sha(got) == GOLD[name]["dist_sha256"], f"{name} {mode}"
@@ -333,6 +336,21 @@ def test_async_watchdog_reports_timeout_and_recovers():
         g.check()
     assert ei.value.status_name == "GG_ERR_TIMEOUT"
     got, _ = run(g, src, "async")                                   # the next run is unaffected
+    np.testing.assert_array_equal(got, oracle.dijkstra(ro, col, w, src))
+    g.check()
+    g.close()
+
+
+@pytest.mark.parametrize("policy", ["persistent", "graph"])
+def test_bsp_watchdog_reports_timeout_and_recovers(policy):
+    m = gg()
+    ro, col, w, src = graphgen.workload("grid64")
+    g = m.Graph(ro, col, w, symmetric=True)
+    g.sssp(src, policy=POLICIES[policy], watchdog_ns=1)              # the deadline has passed at once
+    with pytest.raises(m.GGError) as ei:
+        g.check()
+    assert ei.value.status_name == "GG_ERR_TIMEOUT"
+    got, _ = run(g, src, policy)                                     # the next run is unaffected
     np.testing.assert_array_equal(got, oracle.dijkstra(ro, col, w, src))
     g.check()
     g.close()
