@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--impl", default="gg", choices=["gg", "reference"])
     p.add_argument("--workload", default="rmat20")
     p.add_argument("--policy", default="graph", choices=["graph", "async", "host", "persistent"])
-    p.add_argument("--direction", default="auto", choices=["auto", "push", "pull"])
+    p.add_argument("--direction", default="push", choices=["auto", "push", "pull"])
     p.add_argument("--lb", default="mp", choices=["mp", "bins"])
     p.add_argument("--delta", type=int, default=0, help="near-far bucket width (0 = graph default, -1 = none)")
     p.add_argument("--alpha", type=int, default=0)
@@ -149,12 +149,30 @@ def cpu_baseline(ro, col, w, src, seconds):
                       f"(median {t * 1e3:.1f} ms each, 1 host thread)"}
 
 
-def run_batched(gg, torch, k=64):
+def shard(items, rank, world):
+    """This rank's share of a work list: items rank, rank + world, ...
+    (disjoint across ranks, together complete)."""
+    return items[rank::world]
+
+
+def reduce_over_ranks(value, op, pg):
+    """max / sum of a per-rank float over all ranks (identity without a
+    process group).  Timing only: no data-path collective."""
+    if pg is None:
+        return value
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX if op == "max" else pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+def run_batched(gg, torch, k=64, seed=1):
     """Batched multi-source SSSP on RMAT-22 (64 seeded sources, one fused
     launch sequence) vs the same 64 sources as back-to-back gg_sssp calls."""
     import graphgen
     ro, col, w = graphgen.rmat(22, 16, seed=1, W=255)
-    srcs = graphgen.sample_sources(ro, k, seed=1)
+    srcs = graphgen.sample_sources(ro, k, seed=seed)
     g = gg.Graph(ro, col, w, symmetric=True)
     n = g.n
     out = torch.empty(n * k, dtype=torch.uint32, device="cuda")
@@ -188,7 +206,7 @@ def run_batched(gg, torch, k=64):
             "edges_scanned": st.edges_scanned, "gteps_aggregate_est": k * m_trav / (t * 1e-3) / 1e9}
 
 
-def run_serving(gg, torch, nq=2000):
+def run_serving(gg, torch, nq=2000, seed=1):
     """Poisson stream of (graph, source) queries over the 32-graph pool into
     the continuous-batching server, at saturation (all queued at t=0) and at
     50 % / 90 % of the saturation rate; vs the same queries back to back."""
@@ -196,13 +214,13 @@ def run_serving(gg, torch, nq=2000):
     pool = [graphgen.build_pool_graph(e) for e in graphgen.serving_pool_spec()]
     graphs = [gg.Graph(ro, col, w, symmetric=True) for ro, col, w in pool]
     degs = [np.diff(ro.astype(np.int64)) for ro, _, _ in pool]
-    gids, srcs, _ = graphgen.poisson_queries(degs, nq, seed=1)
+    gids, srcs, _ = graphgen.poisson_queries(degs, nq, seed=seed)
     outs = [torch.empty(graphs[gi].n, dtype=torch.uint32, device="cuda") for gi in gids]
     maxn = max(gr.n for gr in graphs)
     srv = gg.Server(max_graph_vertices=maxn, max_slots=64, supersteps_per_launch=8)
 
     def stream(rate):
-        _, _, arr = graphgen.poisson_queries(degs, nq, seed=1, rate_qps=rate)
+        _, _, arr = graphgen.poisson_queries(degs, nq, seed=seed, rate_qps=rate)
         srv.reset_stats()
         t0 = time.perf_counter()
         ts = []
@@ -404,11 +422,15 @@ def main():
                "what": "gg_graph_create_csr from pinned host CSR + gg_sssp + distances copied to pinned host "
                        "+ gg_graph_destroy, wall clock"}
 
+    # batched and served queries shard naturally: every rank runs its own
+    # seeded stream (per-GPU work fixed) and the queries/s add up
     batched = serving = None
     if not args.no_batch:
-        batched = run_batched(gg, torch)
+        batched = run_batched(gg, torch, seed=1 + rank)
+        batched["queries_per_s_all_ranks"] = reduce_over_ranks(batched["queries_per_s"], "sum", pg)
     if not args.no_serve:
-        serving = run_serving(gg, torch, args.serve_queries)
+        serving = run_serving(gg, torch, args.serve_queries, seed=1 + rank)
+        serving["queries_per_s_all_ranks"] = reduce_over_ranks(serving["saturation"]["queries_per_s"], "sum", pg)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

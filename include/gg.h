@@ -122,9 +122,9 @@ typedef struct {
     uint32_t warp_threshold;   /* LB_BINS: degree >= this -> warp per vertex (0 = auto)  */
     uint32_t cta_threshold;    /* LB_BINS: degree >= this -> CTA per vertex (0 = auto)   */
     uint32_t pull_alpha;       /* AUTO direction: go pull when frontier edges > m/alpha
-                                  (0 = auto)                                            */
+                                  (0 = 4)                                               */
     uint32_t pull_beta;        /* AUTO direction: back to push when frontier vertices <
-                                  n/beta (0 = auto)                                     */
+                                  (vertices with in-edges)/beta (0 = 24)                */
     uint32_t max_iterations;   /* BSP superstep cap (0 = n + 2)                          */
     uint64_t watchdog_ns;      /* give up and report GG_ERR_TIMEOUT after this long
                                   (0 = 10 s for ASYNC, 60 s for the BSP policies)      */
@@ -179,7 +179,10 @@ gg_status gg_graph_check(gg_graph_t g);
 
 /* ---- SSSP (Sec. IV-D, Listing 4) ---------------------------------------- */
 
-/* Fills opt with the defaults (BSP graph policy, auto direction, auto LB). */
+/* Fills opt with the defaults: BSP graph policy, push direction (a pull
+ * superstep sweeps every edge of the transpose; on the measured SSSP
+ * workloads push-only was faster), merge-path load balancing, the graph's
+ * default near-far bucket width. */
 void gg_options_default(gg_options* opt);
 
 /* Single-source shortest paths from src.
@@ -193,6 +196,23 @@ gg_status gg_sssp(gg_graph_t g, uint32_t src, uint32_t* dist_out, cudaStream_t s
 /* As gg_sssp with explicit options (opt may be NULL for the defaults). */
 gg_status gg_sssp_ex(gg_graph_t g, uint32_t src, uint32_t* dist_out, const gg_options* opt,
                      cudaStream_t stream);
+
+/* ---- autotuning ----------------------------------------------------------- */
+
+/* Picks the fastest single-source options for this graph (Sec. IV-C leaves
+ * load balancing and the operator's execution choices to the implementation):
+ * coordinate descent over the loop policy (CUDA graph or persistent), the
+ * near-far bucket width, push-only vs push/pull switching thresholds, and
+ * merge-path vs degree bins with their thresholds.  Every candidate runs
+ * gg_sssp_ex from each sample source on `stream` and is timed with CUDA
+ * events (median of 3); candidates that report a device error are skipped.
+ *   srcs          host u32[nsrc], each < n
+ *   dist_scratch  device u32[n] the runs write into
+ *   best          receives the winning options (stats/trace pointers NULL)
+ *   best_ms       optional: its time per source in milliseconds
+ * Synchronous; takes roughly 50 runs per sample source. */
+gg_status gg_autotune(gg_graph_t g, const uint32_t* srcs, uint32_t nsrc, uint32_t* dist_scratch,
+                      gg_options* best, float* best_ms, cudaStream_t stream);
 
 /* ---- batched multi-source SSSP ------------------------------------------ */
 
@@ -230,11 +250,18 @@ gg_status gg_sssp_batch_ex(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint3
  *   dist_outs  host array of count device pointers, dist_outs[i] u32[n_i]
  * Asynchronous on `stream`; the arrays are read before the call returns.
  * The library keeps one engine per device for these calls (allocated or
- * grown on demand); calls are ordered among themselves.  Push traversal,
- * plain frontier loop.  Errors: GG_ERR_INVALID_ARG, GG_ERR_OUT_OF_MEMORY,
- * GG_ERR_CUDA. */
+ * grown on demand); calls are ordered among themselves.  Push traversal with
+ * each graph's default near-far bucket width; at most 1024 queries per call.
+ * Errors: GG_ERR_INVALID_ARG, GG_ERR_OUT_OF_MEMORY, GG_ERR_CUDA. */
 gg_status gg_sssp_multi(const gg_graph_t* graphs, const uint32_t* srcs, uint32_t count,
                         uint32_t* const* dist_outs, cudaStream_t stream);
+
+/* As gg_sssp_multi with an explicit near-far bucket width for every query
+ * (0 = each graph's default, GG_DELTA_NONE = plain frontier loop).  Each query
+ * keeps its own threshold and far pile; a query whose near frontier empties
+ * splits its pile during the next shared superstep. */
+gg_status gg_sssp_multi_ex(const gg_graph_t* graphs, const uint32_t* srcs, uint32_t count,
+                           uint32_t* const* dist_outs, uint32_t delta, cudaStream_t stream);
 
 /* ---- query server (continuous batching) --------------------------------- */
 
@@ -249,6 +276,9 @@ typedef struct {
                                         (0 = max_slots * max_graph_vertices), capped by
                                         the free HBM at creation                          */
     uint64_t hbm_reserve_bytes;      /* HBM the server leaves free (default 1 GiB)        */
+    uint32_t delta;                  /* near-far bucket width per query (0 = each graph's
+                                        default, GG_DELTA_NONE = plain frontier loop)     */
+    uint32_t reserved;
 } gg_server_config;
 
 typedef struct {
@@ -269,8 +299,9 @@ void gg_server_config_default(gg_server_config* cfg);
  * queries whose frontier emptied}.  Queries arriving while others run join
  * the running union frontier at the next admission round.  The in-flight
  * budget is sized from the free HBM at creation (16 bytes of frontier state
- * per vertex, plus two bitmaps per slot); GG_ERR_OUT_OF_MEMORY if even one
- * graph does not fit. */
+ * per vertex, plus per slot three bitmaps and two far piles of
+ * max_graph_vertices entries); GG_ERR_OUT_OF_MEMORY if even one graph does
+ * not fit.  max_slots <= 1024. */
 gg_status gg_server_create(const gg_server_config* cfg, gg_server_t* out);
 
 /* Queues the query (graph g, source src) whose distances go to dist_out

@@ -72,7 +72,8 @@ class gg_options(ctypes.Structure):
 class gg_server_config(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("max_slots", ctypes.c_uint32),
                 ("max_graph_vertices", ctypes.c_uint32), ("supersteps_per_launch", ctypes.c_uint32),
-                ("max_vertices_in_flight", ctypes.c_uint64), ("hbm_reserve_bytes", ctypes.c_uint64)]
+                ("max_vertices_in_flight", ctypes.c_uint64), ("hbm_reserve_bytes", ctypes.c_uint64),
+                ("delta", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class gg_server_stats(ctypes.Structure):
@@ -114,6 +115,7 @@ def load():
             "gg_sssp_batch": (ctypes.c_int, [vp, P32, u32, vp, vp]),
             "gg_sssp_batch_ex": (ctypes.c_int, [vp, P32, u32, vp, ctypes.POINTER(gg_options), vp]),
             "gg_sssp_multi": (ctypes.c_int, [ctypes.POINTER(vp), P32, u32, ctypes.POINTER(vp), vp]),
+            "gg_sssp_multi_ex": (ctypes.c_int, [ctypes.POINTER(vp), P32, u32, ctypes.POINTER(vp), u32, vp]),
             "gg_server_config_default": (None, [ctypes.POINTER(gg_server_config)]),
             "gg_server_create": (ctypes.c_int, [ctypes.POINTER(gg_server_config), ctypes.POINTER(vp)]),
             "gg_server_submit": (ctypes.c_int, [vp, vp, u32, vp, ctypes.POINTER(u64)]),
@@ -122,6 +124,8 @@ def load():
             "gg_server_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(gg_server_stats)]),
             "gg_server_reset_stats": (ctypes.c_int, [vp]),
             "gg_server_destroy": (ctypes.c_int, [vp]),
+            "gg_autotune": (ctypes.c_int, [vp, P32, u32, vp, ctypes.POINTER(gg_options),
+                                           ctypes.POINTER(ctypes.c_float), vp]),
             "gg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "gg_last_error": (ctypes.c_char_p, []),
             "gg_abi_version": (u32, []),
@@ -261,7 +265,7 @@ def gg_sssp_batch(handle: int, srcs, dist_out, stream=None, options: gg_options 
                "gg_sssp_batch_ex")
 
 
-def gg_sssp_multi(handles, srcs, dist_outs, stream=None):
+def gg_sssp_multi(handles, srcs, dist_outs, stream=None, delta: int | None = None):
     """One query per (handles[i], srcs[i]) into dist_outs[i] (CUDA uint32
     tensors), all advanced together, async."""
     k = len(handles)
@@ -276,8 +280,11 @@ def gg_sssp_multi(handles, srcs, dist_outs, stream=None):
             raise ValueError("dist_outs must be CUDA tensors")
         ptrs.append(p)
     dp = (ctypes.c_void_p * k)(*ptrs)
-    _check(load().gg_sssp_multi(hs, sp.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), k, dp, _stream_ptr(stream)),
-           "gg_sssp_multi")
+    spp = sp.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+    if delta is None:
+        _check(load().gg_sssp_multi(hs, spp, k, dp, _stream_ptr(stream)), "gg_sssp_multi")
+    else:
+        _check(load().gg_sssp_multi_ex(hs, spp, k, dp, delta, _stream_ptr(stream)), "gg_sssp_multi_ex")
 
 
 class Server:
@@ -285,7 +292,7 @@ class Server:
     ticket; results are written to the caller's CUDA tensor."""
 
     def __init__(self, max_graph_vertices: int, max_slots: int = 64, supersteps_per_launch: int = 8,
-                 max_vertices_in_flight: int = 0, hbm_reserve_bytes: int = 1 << 30):
+                 max_vertices_in_flight: int = 0, hbm_reserve_bytes: int = 1 << 30, delta: int = 0):
         lib = load()
         c = gg_server_config()
         lib.gg_server_config_default(ctypes.byref(c))
@@ -294,6 +301,7 @@ class Server:
         c.supersteps_per_launch = supersteps_per_launch
         c.max_vertices_in_flight = max_vertices_in_flight
         c.hbm_reserve_bytes = hbm_reserve_bytes
+        c.delta = delta
         h = ctypes.c_void_p()
         _check(lib.gg_server_create(ctypes.byref(c), ctypes.byref(h)), "gg_server_create")
         self.handle = h.value

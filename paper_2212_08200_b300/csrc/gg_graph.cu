@@ -301,15 +301,17 @@ gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m64, const uint32_t* ro_
     g->bytes += (g->symmetric ? 1 : 2) * sizeof(uint32_t) * (size_t)m;
     g->dg.packed = 1;
   }
-  // default near-far bucket width: a few average edge weights' worth of
-  // distance per bucket, scaled down on dense graphs (more edges relax each
-  // bucket); autotuned per graph class by the tuner
+  // default near-far bucket width (measured on B300, see the autotuner for
+  // per-graph choices): low-degree, high-diameter graphs (grids) use buckets
+  // of 16 maximum edge weights, which cut Bellman-Ford re-relaxation from
+  // ~200x to ~4x the edge count; on skewed, low-diameter graphs (mean degree
+  // >= 8, e.g. RMAT) the extra supersteps cost more than the saved edges, so
+  // they run the plain frontier loop
   g->wmax = wmax;
   {
     const double davg = g->dg.np ? (double)m / (double)g->dg.np : 1.0;
-    double d = (double)wmax * 8.0 / std::max(davg, 1.0);
-    if (d < 1.0) d = 1.0;
-    g->default_delta = m ? (uint32_t)std::min(d, 1.0e9) : 1u;
+    const double d = (double)std::max<uint32_t>(wmax, 1) * 16.0;
+    g->default_delta = (davg >= 8.0 || !m) ? GG_DELTA_NONE : (uint32_t)std::min(d, 4.0e9);
   }
   g->dg.n = n;
   g->dg.m = m;

@@ -11,8 +11,11 @@
 // queries have converged: it marks them done (slot state and, for the
 // server, words in host-mapped memory) so that new queries can take their
 // slots between supersteps -- continuous batching at superstep granularity.
-// The slot engine runs the plain frontier loop (no near-far buckets), push
-// only.
+// Push only.  Each slot runs its own near-far buckets: improved vertices at or
+// above the slot's threshold are parked in the slot's far pile; when a slot's
+// near frontier empties, the closing CTA raises its threshold and the next
+// superstep re-examines that pile (edge-balanced over all CTAs, alongside the
+// other slots' advance).
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -43,6 +46,56 @@ __device__ __forceinline__ uint2 slot_edge(const MultiSlot& s, uint32_t e) {
     return make_uint2(x >> s.wbits, x & ((1u << s.wbits) - 1u));
   }
   return __ldg(static_cast<const uint2*>(s.edges) + e);
+}
+
+// Filter of the slot engine: vertex v of slot q just dropped to nd.  Below
+// the slot's threshold it joins the union next frontier (once per slot, by its
+// near bitmap); otherwise it is parked in the slot's far pile (once, by its
+// far bitmap).  Vertices without out-edges are skipped.
+__device__ __forceinline__ void m_filter(MSmem& sm, const MultiBufs& b, MultiSlot* slots, uint32_t q,
+                                         const MultiSlot& sl, uint32_t p, uint32_t v, uint32_t nd) {
+  const uint32_t rs = __ldg(sl.ro + v), re = __ldg(sl.ro + v + 1);
+  if (re <= rs) return;
+  const uint32_t bit = 1u << (v & 31);
+  if (nd < sl.t_cur) {
+    if (!(atomicOr(b.bm_pool + sl.bm_off[p ^ 1u] + (v >> 5), bit) & bit)) {
+      const uint32_t i = atomicAdd(&sm.qn, 1u);
+      sm.qv[i] = v;
+      sm.qr[i] = rs;
+      sm.qd[i] = re - rs;
+      sm.qq[i] = q;
+    }
+  } else {
+    atomicMin(&slots[q].far_min, nd);
+    if (!(atomicOr(b.bm_pool + sl.bm_off[2] + (v >> 5), bit) & bit)) {
+      const uint32_t pile = sl.fpp;
+      const uint32_t pos = atomicAdd(&slots[q].far_cnt[pile], 1u);
+      b.far_pool[sl.far_off[pile] + pos] = v;
+    }
+  }
+}
+
+// Appends the CTA's queued (slot, vertex) entries to the union next frontier.
+__device__ __forceinline__ void m_flush(MSmem& sm, const MultiBufs& b, MultiCtl* ctl, uint32_t p) {
+  __syncthreads();
+  const uint32_t qn = sm.qn;
+  if (qn) {
+    const uint32_t tid = threadIdx.x;
+    for (uint32_t i = tid; i < qn; i += kMB) atomicAdd(&b.slot_cnt[sm.qq[i]], 1u);
+    const uint32_t tot = block_scan_excl<kMB>(sm.qd, qn, sm.wsum);
+    if (tid == 0) sm.base = atomicAdd(&ctl->cnt[p ^ 1u], ((unsigned long long)qn << 32) | tot);
+    __syncthreads();
+    const uint32_t pos0 = (uint32_t)(sm.base >> 32), eb0 = (uint32_t)sm.base;
+    for (uint32_t i = tid; i < qn; i += kMB) {
+      b.fv[p ^ 1u][pos0 + i] = sm.qv[i];
+      b.fr[p ^ 1u][pos0 + i] = sm.qr[i];
+      b.fs[p ^ 1u][pos0 + i] = eb0 + sm.qd[i];
+      b.fq[p ^ 1u][pos0 + i] = sm.qq[i];
+    }
+    __syncthreads();
+    if (tid == 0) sm.qn = 0;
+  }
+  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphConditionalHandle cond,
@@ -103,41 +156,47 @@ __global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphC
           if (ovf) atomicOr(&slots[q].status, DS_OVERFLOW);
           if (nd < ld_cg(sl.dist + ed.x)) {
             atomicMin(sl.dist + ed.x, nd);
-            // filter: append once per slot and superstep, skip vertices without out-edges
-            const uint32_t v = ed.x;
-            const uint32_t rs = __ldg(sl.ro + v), re = __ldg(sl.ro + v + 1);
-            if (re > rs) {
-              const uint32_t bit = 1u << (v & 31);
-              if (!(atomicOr(b.bm_pool + sl.bm_off[p ^ 1u] + (v >> 5), bit) & bit)) {
-                const uint32_t i = atomicAdd(&sm.qn, 1u);
-                sm.qv[i] = v;
-                sm.qr[i] = rs;
-                sm.qd[i] = re - rs;
-                sm.qq[i] = q;
-              }
-            }
+            m_filter(sm, b, slots, q, sl, p, ed.x, nd);
           }
         }
       }
-      __syncthreads();
-      const uint32_t qn = sm.qn;
-      if (qn) {
-        for (uint32_t i = tid; i < qn; i += kMB) atomicAdd(&b.slot_cnt[sm.qq[i]], 1u);
-        const uint32_t tot = block_scan_excl<kMB>(sm.qd, qn, sm.wsum);
-        if (tid == 0) sm.base = atomicAdd(&ctl->cnt[p ^ 1u], ((unsigned long long)qn << 32) | tot);
-        __syncthreads();
-        const uint32_t pos0 = (uint32_t)(sm.base >> 32), eb0 = (uint32_t)sm.base;
-        for (uint32_t i = tid; i < qn; i += kMB) {
-          b.fv[p ^ 1u][pos0 + i] = sm.qv[i];
-          b.fr[p ^ 1u][pos0 + i] = sm.qr[i];
-          b.fs[p ^ 1u][pos0 + i] = eb0 + sm.qd[i];
-          b.fq[p ^ 1u][pos0 + i] = sm.qq[i];
-        }
-        __syncthreads();
-        if (tid == 0) sm.qn = 0;
-      }
-      __syncthreads();
+      m_flush(sm, b, ctl, p);
       j = j + nent - 1;
+    }
+  }
+  // split work: the far piles of the slots flagged by the previous superstep,
+  // spread evenly over the CTAs
+  {
+    const uint32_t S = ctl->split_total, ns = ctl->nsplit;
+    const uint32_t s0 = (uint32_t)(((unsigned long long)blockIdx.x * S) / gridDim.x);
+    const uint32_t s1 = (uint32_t)(((unsigned long long)(blockIdx.x + 1) * S) / gridDim.x);
+    for (uint32_t base = s0; base < s1; base += kMB) {
+      const uint32_t i = base + tid;
+      if (i < s1) {
+        uint32_t lo = 0, len = ns;   // last k with split_pref[k] <= i
+        while (len > 0) {
+          const uint32_t half = len >> 1;
+          if (ctl->split_pref[lo + half] <= i) { lo += half + 1; len -= half + 1; }
+          else len = half;
+        }
+        const uint32_t k = lo - 1;
+        const uint32_t q = ctl->split_slot[k];
+        const MultiSlot& sl = slots[q];
+        const uint32_t v = b.far_pool[sl.far_off[sl.fpp] + (i - ctl->split_pref[k])];
+        const uint32_t d = ld_cg(sl.dist + v);
+        const uint32_t bit = 1u << (v & 31);
+        if (d < sl.t_cur) {
+          // below the raised threshold: leave the pile; expand unless already expanded below t_prev
+          atomicAnd(b.bm_pool + sl.bm_off[2] + (v >> 5), ~bit);
+          if (d >= sl.t_prev) m_filter(sm, b, slots, q, sl, p, v, d);
+        } else {
+          atomicMin(&slots[q].far_min, d);
+          const uint32_t pile = sl.fpp ^ 1u;
+          const uint32_t pos = atomicAdd(&slots[q].far_cnt[pile], 1u);
+          b.far_pool[sl.far_off[pile] + pos] = v;
+        }
+      }
+      m_flush(sm, b, ctl, p);
     }
   }
   __syncthreads();
@@ -147,18 +206,38 @@ __global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphC
   }
   __syncthreads();
   if (sm.last) {
-    // the closing CTA: slots with nothing in the next frontier have converged
+    // the closing CTA: a slot with nothing in the next frontier either splits
+    // its far pile next superstep (threshold raised past its smallest parked
+    // distance) or, with an empty pile, has converged
     __threadfence();
+    if (tid == 0) sm.j = 0;
+    __syncthreads();
     for (uint32_t q = tid; q < b.nslots; q += kMB) {
       MultiSlot& sl = slots[q];
       if (sl.state == kSlotRunning) {
         sl.supersteps += 1;
+        if (sl.split) {   // this superstep consumed pile fpp and kept the rest in the other pile
+          sl.far_cnt[sl.fpp] = 0u;
+          sl.fpp ^= 1u;
+          sl.split = 0u;
+        }
         if (b.slot_cnt[q] == 0) {
-          sl.state = kSlotDone;
-          if (b.done_flags) {
-            b.done_status[q] = sl.status;
-            __threadfence_system();
-            reinterpret_cast<volatile uint32_t*>(b.done_flags)[q] = sl.ticket;
+          if (sl.far_cnt[sl.fpp] > 0) {
+            const unsigned long long t1 = (unsigned long long)sl.t_cur + sl.delta;
+            const unsigned long long t2 = (unsigned long long)sl.far_min + 1;
+            const unsigned long long tn = t1 > t2 ? t1 : t2;
+            sl.t_prev = sl.t_cur;
+            sl.t_cur = tn >= kInf ? kInf : (uint32_t)tn;
+            sl.far_min = kInf;
+            sl.split = 1u;
+            sm.qv[atomicAdd(&sm.j, 1u)] = q;
+          } else {
+            sl.state = kSlotDone;
+            if (b.done_flags) {
+              b.done_status[q] = sl.status;
+              __threadfence_system();
+              reinterpret_cast<volatile uint32_t*>(b.done_flags)[q] = sl.ticket;
+            }
           }
         }
       }
@@ -166,12 +245,23 @@ __global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphC
     }
     __syncthreads();
     if (tid == 0) {
+      const uint32_t ns = sm.j;
+      uint32_t run = 0;
+      for (uint32_t k = 0; k < ns; ++k) {
+        const uint32_t q = sm.qv[k];
+        ctl->split_slot[k] = q;
+        ctl->split_pref[k] = run;
+        run += slots[q].far_cnt[slots[q].fpp];
+      }
+      ctl->split_pref[ns] = run;
+      ctl->nsplit = ns;
+      ctl->split_total = run;
       const unsigned long long cn = atomicAdd(&ctl->cnt[p ^ 1u], 0ull);
       ctl->cnt[p] = 0ull;
       ctl->done_ctas = 0u;
       ctl->iter = it + 1;
       ctl->supersteps_run += 1;
-      const bool nonempty = (cn >> 32) != 0;
+      const bool nonempty = (cn >> 32) != 0 || ns != 0;
       const uint32_t left = ctl->budget_left > 0 ? ctl->budget_left - 1 : 0;
       ctl->budget_left = left;
       ctl->running = nonempty ? 1u : 0u;
@@ -190,6 +280,7 @@ __global__ void k_multi_fill(MultiBufs b, const uint32_t* starting, uint32_t nst
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < nw; v += stride) {
       b.bm_pool[sl.bm_off[0] + v] = 0u;
       b.bm_pool[sl.bm_off[1] + v] = 0u;
+      b.bm_pool[sl.bm_off[2] + v] = 0u;
     }
   }
 }
@@ -229,15 +320,30 @@ __global__ void k_multi_budget(MultiCtl* ctl, uint32_t budget) { ctl->budget_lef
 
 }  // namespace
 
+void multi_slot_buckets(MultiSlot& s, uint32_t delta, uint32_t far0, uint32_t far1) {
+  s.delta = delta;
+  s.t_cur = delta;   // first bucket [0, delta); kInf: no buckets
+  s.t_prev = 0;
+  s.far_off[0] = far0;
+  s.far_off[1] = far1;
+  s.far_cnt[0] = s.far_cnt[1] = 0;
+  s.fpp = 0;
+  s.far_min = kInf;
+  s.split = 0;
+}
+
 gg_status multi_engine_init(MultiEngine* e, uint32_t max_slots, uint64_t max_vertices, uint64_t max_bitmap_words,
-                            bool mapped_flags) {
+                            uint64_t max_far, bool mapped_flags) {
+  if (max_slots > (uint32_t)kMaxSplitSlots) return fail(GG_ERR_INVALID_ARG, "at most 1024 slots");
   e->max_slots = max_slots;
   e->cap_vertices = max_vertices;
   e->cap_words = max_bitmap_words;
+  e->cap_far = max_far;
   auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t fb = r256(4 * std::max<uint64_t>(max_vertices, 1));
   const size_t total = 8 * fb + r256(sizeof(MultiSlot) * max_slots) + 2 * r256(4 * (size_t)max_slots) +
-                       r256(4 * std::max<uint64_t>(max_bitmap_words, 1)) + r256(sizeof(MultiCtl));
+                       r256(4 * std::max<uint64_t>(max_bitmap_words, 1)) + r256(4 * std::max<uint64_t>(max_far, 1)) +
+                       r256(sizeof(MultiCtl));
   char* p = nullptr;
   GG_CK(cudaMalloc(&p, total));
   e->block = p;
@@ -255,6 +361,7 @@ gg_status multi_engine_init(MultiEngine* e, uint32_t max_slots, uint64_t max_ver
   e->b.slot_cnt = reinterpret_cast<uint32_t*>(take(4 * (size_t)max_slots));
   e->starting = reinterpret_cast<uint32_t*>(take(4 * (size_t)max_slots));
   e->b.bm_pool = reinterpret_cast<uint32_t*>(take(4 * std::max<uint64_t>(max_bitmap_words, 1)));
+  e->b.far_pool = reinterpret_cast<uint32_t*>(take(4 * std::max<uint64_t>(max_far, 1)));
   e->b.ctl = reinterpret_cast<MultiCtl*>(take(sizeof(MultiCtl)));
   e->b.nslots = max_slots;
   if (off != total) return fail(GG_ERR_INTERNAL, "multi workspace layout");

@@ -18,20 +18,33 @@ struct MultiSlot {
   uint32_t n;
   uint32_t packed, wbits;
   uint32_t src;
-  uint32_t bm_off[2];
+  uint32_t bm_off[3];     // near bitmaps (by superstep parity) and the far-pile bitmap
   uint32_t state;
   uint32_t ticket;        // written to the done flag when the query converges
   uint32_t status;        // DS_* bits of this query
   uint32_t supersteps;    // supersteps the query took part in
+  // near-far buckets of this query (delta == 0xFFFFFFFF: plain frontier loop)
+  uint32_t delta, t_cur, t_prev;
+  uint32_t far_off[2];    // its two far piles in the far pool (ping-pong across splits)
+  uint32_t far_cnt[2];
+  uint32_t fpp;           // current pile
+  uint32_t far_min;
+  uint32_t split;         // 1: this superstep splits the slot's far pile
 };
+
+constexpr int kMaxSplitSlots = 1024;
 
 struct MultiCtl {
   unsigned long long cnt[2];   // (count << 32) | edges of the union frontier, by parity
   uint32_t iter;
   uint32_t done_ctas;
-  uint32_t running;            // union frontier non-empty
+  uint32_t running;            // union frontier non-empty or a split pending
   uint32_t budget_left;        // supersteps this graph launch may still run
   unsigned long long supersteps_run;
+  uint32_t nsplit;             // slots splitting in the current superstep
+  uint32_t split_total;        // their far entries
+  uint32_t split_slot[kMaxSplitSlots];
+  uint32_t split_pref[kMaxSplitSlots + 1];
 };
 
 struct MultiBufs {
@@ -42,6 +55,7 @@ struct MultiBufs {
   MultiSlot* slots;
   uint32_t* slot_cnt;          // entries each slot appended to the next frontier
   uint32_t* bm_pool;
+  uint32_t* far_pool;
   MultiCtl* ctl;
   uint32_t* done_flags;        // device view of host-mapped words (server) or NULL
   uint32_t* done_status;       // device view of host-mapped words (server) or NULL
@@ -52,6 +66,7 @@ struct MultiEngine {
   uint32_t max_slots = 0;
   uint64_t cap_vertices = 0;   // union frontier capacity
   uint64_t cap_words = 0;      // bitmap pool words
+  uint64_t cap_far = 0;        // far pool entries
   void* block = nullptr;
   size_t bytes = 0;
   MultiBufs b{};
@@ -67,7 +82,9 @@ struct MultiEngine {
 };
 
 gg_status multi_engine_init(MultiEngine* e, uint32_t max_slots, uint64_t max_vertices, uint64_t max_bitmap_words,
-                            bool mapped_flags);
+                            uint64_t max_far, bool mapped_flags);
+// fills the near-far fields of a slot descriptor (delta 0xFFFFFFFF = none)
+void multi_slot_buckets(MultiSlot& s, uint32_t delta, uint32_t far0, uint32_t far1);
 void multi_engine_free(MultiEngine* e);
 // zero the union frontier and the counters (no query in flight)
 gg_status multi_engine_reset(MultiEngine* e, cudaStream_t s);

@@ -38,7 +38,7 @@ using Clock = std::chrono::steady_clock;
 namespace {
 
 void fill_slot(MultiSlot& s, const gg_graph* g, uint32_t src, uint32_t* dist, uint32_t ticket, uint32_t off0,
-               uint32_t off1) {
+               uint32_t off1, uint32_t off2, uint32_t far0, uint32_t far1, uint32_t delta) {
   s = MultiSlot{};
   s.ro = g->dg.ro;
   s.edges = g->dg.edges;
@@ -49,8 +49,10 @@ void fill_slot(MultiSlot& s, const gg_graph* g, uint32_t src, uint32_t* dist, ui
   s.src = src;
   s.bm_off[0] = off0;
   s.bm_off[1] = off1;
+  s.bm_off[2] = off2;
   s.state = kSlotFree;
   s.ticket = ticket;
+  multi_slot_buckets(s, delta == 0 ? g->default_delta : delta, far0, far1);
 }
 
 // ---- gg_sssp_multi: a process-wide engine per device, grown on demand -------
@@ -65,8 +67,8 @@ MultiCache g_multi[16];
 
 }  // namespace
 
-extern "C" gg_status gg_sssp_multi(const gg_graph_t* graphs, const uint32_t* srcs, uint32_t count,
-                                   uint32_t* const* dist_outs, cudaStream_t stream) {
+extern "C" gg_status gg_sssp_multi_ex(const gg_graph_t* graphs, const uint32_t* srcs, uint32_t count,
+                                      uint32_t* const* dist_outs, uint32_t delta, cudaStream_t stream) {
   if (!graphs || !srcs || !dist_outs) return fail(GG_ERR_INVALID_ARG, "graphs/srcs/dist_outs is NULL");
   if (count == 0) return fail(GG_ERR_INVALID_ARG, "count must be >= 1");
   int dev = 0;
@@ -81,7 +83,7 @@ extern "C" gg_status gg_sssp_multi(const gg_graph_t* graphs, const uint32_t* src
     if (g->device != dev) return fail(GG_ERR_INVALID_ARG, "a graph lives on another device");
     if (srcs[i] >= g->n) return fail(GG_ERR_INVALID_ARG, "a source is >= its graph's n");
     total_n += g->n;
-    words += 2ull * ((g->n + 31) / 32);
+    words += 3ull * ((g->n + 31) / 32);
     nmax = std::max(nmax, g->n);
   }
   if (total_n >= 0xFFFFFFFFull || words >= 0xFFFFFFFFull)
@@ -92,11 +94,13 @@ extern "C" gg_status gg_sssp_multi(const gg_graph_t* graphs, const uint32_t* src
   if (mc.ev_valid) {
     if (mc.last != stream) GG_CK(cudaStreamWaitEvent(stream, mc.ev, 0));
   }
-  if (!e.block || e.max_slots < count || e.cap_vertices < total_n || e.cap_words < words) {
+  if (count > (uint32_t)kMaxSplitSlots) return fail(GG_ERR_INVALID_ARG, "at most 1024 queries per call");
+  if (!e.block || e.max_slots < count || e.cap_vertices < total_n || e.cap_words < words || e.cap_far < 2 * total_n) {
     if (mc.ev_valid) GG_CK(cudaEventSynchronize(mc.ev));
     if (e.block) multi_engine_free(&e);
     gg_status st = multi_engine_init(&e, std::max<uint32_t>(count, 64), std::max<uint64_t>(total_n, 1 << 16),
-                                     std::max<uint64_t>(words, 4096), false);
+                                     std::max<uint64_t>(words, 4096), std::max<uint64_t>(2 * total_n, 1 << 17),
+                                     false);
     if (st != GG_OK) { multi_engine_free(&e); return st; }
   }
   if (!mc.ev) GG_CK(cudaEventCreateWithFlags(&mc.ev, cudaEventDisableTiming));
@@ -105,11 +109,14 @@ extern "C" gg_status gg_sssp_multi(const gg_graph_t* graphs, const uint32_t* src
   gg_status st = multi_engine_reset(&e, stream);
   if (st != GG_OK) return st;
   std::vector<uint32_t> ids(count);
-  uint32_t off = 0;
+  uint32_t off = 0, foff = 0;
   for (uint32_t i = 0; i < count; ++i) {
     const uint32_t w = (graphs[i]->n + 31) / 32;
-    fill_slot(e.h_slots[i], graphs[i], srcs[i], dist_outs[i], i + 1, off, off + w);
-    off += 2 * w;
+    const uint32_t nn = graphs[i]->n;
+    fill_slot(e.h_slots[i], graphs[i], srcs[i], dist_outs[i], i + 1, off, off + w, off + 2 * w, foff, foff + nn,
+              delta);
+    off += 3 * w;
+    foff += 2 * nn;
     ids[i] = i;
   }
   // slots beyond count stay free
@@ -118,13 +125,18 @@ extern "C" gg_status gg_sssp_multi(const gg_graph_t* graphs, const uint32_t* src
                         cudaMemcpyHostToDevice, stream));
   st = multi_engine_start(&e, ids.data(), count, stream);
   if (st != GG_OK) return st;
-  // every query converges within n + 1 supersteps of the plain frontier loop
-  st = multi_engine_run(&e, nmax + 2, stream);
+  // every query converges within about 3n supersteps with buckets (n + 1 without)
+  st = multi_engine_run(&e, (uint32_t)std::min<uint64_t>(4ull * nmax + 16, 0xFFFFFFFEull), stream);
   if (st != GG_OK) return st;
   GG_CK(cudaEventRecord(mc.ev, stream));
   mc.ev_valid = true;
   mc.last = stream;
   return GG_OK;
+}
+
+extern "C" gg_status gg_sssp_multi(const gg_graph_t* graphs, const uint32_t* srcs, uint32_t count,
+                                   uint32_t* const* dist_outs, cudaStream_t stream) {
+  return gg_sssp_multi_ex(graphs, srcs, count, dist_outs, 0, stream);
 }
 
 // ---- server ------------------------------------------------------------------
@@ -182,7 +194,9 @@ void server_loop(gg_server* s) {
           s->slot_ticket[q] = t;
           s->used_vertices += r.g->n;
           r.state = 1;
-          fill_slot(s->eng.h_slots[q], r.g, r.src, r.dist, (uint32_t)t, 2 * q * words, 2 * q * words + words);
+          const uint32_t maxn = s->cfg.max_graph_vertices;
+          fill_slot(s->eng.h_slots[q], r.g, r.src, r.dist, (uint32_t)t, 3 * q * words, 3 * q * words + words,
+                    3 * q * words + 2 * words, 2 * q * maxn, 2 * q * maxn + maxn, s->cfg.delta);
           s->eng.h_done[q] = 0;
           admit.push_back(q);
           ++s->running;
@@ -263,7 +277,9 @@ gg_status gg_server_create(const gg_server_config* cfg, gg_server_t* out) {
   s->cfg = *cfg;
   if (!s->cfg.max_slots) s->cfg.max_slots = 64;
   if (!s->cfg.supersteps_per_launch) s->cfg.supersteps_per_launch = 8;
-  const uint64_t words = 2ull * s->cfg.max_slots * ((s->cfg.max_graph_vertices + 31) / 32);
+  if (s->cfg.max_slots > (uint32_t)kMaxSplitSlots) { delete s; return fail(GG_ERR_INVALID_ARG, "max_slots > 1024"); }
+  const uint64_t words = 3ull * s->cfg.max_slots * ((s->cfg.max_graph_vertices + 31) / 32);
+  const uint64_t far_entries = 2ull * s->cfg.max_slots * s->cfg.max_graph_vertices;
   uint64_t cap = s->cfg.max_vertices_in_flight ? s->cfg.max_vertices_in_flight
                                                : (uint64_t)s->cfg.max_slots * s->cfg.max_graph_vertices;
   cap = std::max<uint64_t>(cap, s->cfg.max_graph_vertices);
@@ -275,14 +291,17 @@ gg_status gg_server_create(const gg_server_config* cfg, gg_server_t* out) {
   e = cudaMemGetInfo(&free_b, &total_b);
   if (e != cudaSuccess) { delete s; return cuda_fail(e, "cudaMemGetInfo"); }
   const uint64_t avail = free_b > s->cfg.hbm_reserve_bytes ? free_b - s->cfg.hbm_reserve_bytes : 0;
-  const uint64_t fixed = 4 * words + 1024ull * s->cfg.max_slots + (1 << 20);
+  const uint64_t fixed = 4 * words + 4 * far_entries + 1024ull * s->cfg.max_slots + (1 << 20);
   if (avail < fixed + 32ull * s->cfg.max_graph_vertices) {
     delete s;
     return fail(GG_ERR_OUT_OF_MEMORY, "not enough free HBM for the server's frontier budget");
   }
   cap = std::min<uint64_t>(cap, (avail - fixed) / 32);
-  if (cap >= 0xFFFFFFFFull || words >= 0xFFFFFFFFull) { delete s; return fail(GG_ERR_INVALID_ARG, "budget too large"); }
-  gg_status st = multi_engine_init(&s->eng, s->cfg.max_slots, cap, words, true);
+  if (cap >= 0xFFFFFFFFull || words >= 0xFFFFFFFFull || far_entries >= 0xFFFFFFFFull) {
+    delete s;
+    return fail(GG_ERR_INVALID_ARG, "budget too large");
+  }
+  gg_status st = multi_engine_init(&s->eng, s->cfg.max_slots, cap, words, far_entries, true);
   if (st == GG_OK) {
     e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamCreate");

@@ -60,7 +60,7 @@ def test_options_struct_layout(lib):
     o = gg.gg_options()
     lib.gg_options_default(ctypes.byref(o))
     assert o.struct_size == ctypes.sizeof(gg.gg_options)
-    assert o.policy == gg.GG_POLICY_BSP_GRAPH and o.direction == gg.GG_DIR_AUTO
+    assert o.policy == gg.GG_POLICY_BSP_GRAPH and o.direction == gg.GG_DIR_PUSH
 
 
 def _create(lib, n, m, ro, col, w, flags=0):

@@ -34,8 +34,8 @@ def small_pool(pack=True):
     return graphs
 
 
-@pytest.mark.parametrize("pack", [True, False])
-def test_multi_matches_oracle(pack):
+@pytest.mark.parametrize("pack,delta", [(True, None), (False, None), (True, 0xFFFFFFFF), (True, 1), (False, 37)])
+def test_multi_matches_oracle(pack, delta):
     m = gg()
     pool = small_pool(pack)
     rng = np.random.Generator(np.random.PCG64(1))
@@ -45,7 +45,7 @@ def test_multi_matches_oracle(pack):
         ro = pool[gi][0]
         qs.append((gi, int(rng.integers(0, ro.shape[0] - 1))))
     outs = [torch.empty(pool[gi][3].n, dtype=torch.uint32, device="cuda") for gi, _ in qs]
-    m.gg_sssp_multi([pool[gi][3].handle for gi, _ in qs], [s for _, s in qs], outs)
+    m.gg_sssp_multi([pool[gi][3].handle for gi, _ in qs], [s for _, s in qs], outs, delta=delta)
     torch.cuda.synchronize()
     for (gi, s), d in zip(qs, outs):
         ro, col, w, _ = pool[gi]
@@ -61,10 +61,12 @@ def test_multi_matches_oracle(pack):
         g.close()
 
 
-def test_server_mixed_equals_alone_and_oracle():
+@pytest.mark.parametrize("delta", [0, 0xFFFFFFFF, 20])
+def test_server_mixed_equals_alone_and_oracle(delta):
     m = gg()
     pool = small_pool()
-    srv = m.Server(max_graph_vertices=max(g.n for *_, g in pool), max_slots=16, supersteps_per_launch=4)
+    srv = m.Server(max_graph_vertices=max(g.n for *_, g in pool), max_slots=16, supersteps_per_launch=4,
+                   delta=delta)
     rng = np.random.Generator(np.random.PCG64(3))
     qs, tickets, outs = [], [], []
     for i in range(150):
