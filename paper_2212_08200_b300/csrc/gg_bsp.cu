@@ -50,6 +50,7 @@ struct MPSmem {
   uint32_t ovf;
   unsigned long long base;
   uint32_t fbase;
+  uint16_t own[TILE];  // push: entry that owns each edge slot of the tile
 };
 
 struct StepArgs {
@@ -188,17 +189,27 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
       if (c < BLOCK) break;
     }
     if (!PULL) {
-      // push: consecutive threads take consecutive edge coordinates (coalesced rows)
+      // push: consecutive threads take consecutive edge coordinates (coalesced
+      // rows).  Owner map instead of a per-edge search: every entry after the
+      // first marks the tile slot where its edges start, and an inclusive
+      // prefix sum over the marks gives each slot its entry.
+      const uint32_t len = t1 - t0;
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) sm.own[k * BLOCK + tid] = 0;
+      __syncthreads();
+      for (uint32_t jj = 1 + tid; jj < nent; jj += BLOCK) sm.own[sm.es[jj] - t0] = 1;
+      __syncthreads();
+      block_incl_scan_u16<BLOCK, EPT>(sm.own, sm.wsum);
       uint2 ed[EPT];
       uint32_t ej[EPT];
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
-        const uint32_t gidx = t0 + k * BLOCK + tid;
+        const uint32_t o = k * BLOCK + tid;
         ej[k] = kInf;
-        if (gidx < t1) {
-          const uint32_t jj = smem_upper_bound_minus1(sm.es, nent, gidx);
+        if (o < len) {
+          const uint32_t jj = sm.own[o];
           ej[k] = jj;
-          ed[k] = load_edge<PK>(edges, sm.eb[jj] + (gidx - sm.es[jj]), wbits);
+          ed[k] = load_edge<PK>(edges, sm.eb[jj] + (t0 + o - sm.es[jj]), wbits);
         }
       }
       uint32_t nd[EPT], cur[EPT];
@@ -209,11 +220,14 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
           cur[k] = ld_cg(dist + ed[k].x);
         }
       }
+      // nd < cur read just before: after the atomic dist[v] <= nd < cur, so v
+      // improved in this superstep and belongs in the next frontier; the
+      // atomic's old value is not needed (fire-and-forget reduction)
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         if (ej[k] != kInf && nd[k] < cur[k]) {
-          const uint32_t old = atomicMin(dist + ed[k].x, nd[k]);
-          if (nd[k] < old) filter_candidate(sm, fo, ed[k].x, nd[k]);
+          atomicMin(dist + ed[k].x, nd[k]);
+          filter_candidate(sm, fo, ed[k].x, nd[k]);
         }
       }
     } else {

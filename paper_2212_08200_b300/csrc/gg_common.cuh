@@ -206,6 +206,43 @@ __device__ __forceinline__ uint32_t block_scan_excl(uint32_t* data, uint32_t cou
   return total;
 }
 
+// Inclusive prefix sum in place of the BLOCK*ITEMS u16 shared array a, by a
+// whole CTA (thread t owns ITEMS consecutive elements); wsum: BLOCK/32 words.
+template <int BLOCK, int ITEMS>
+__device__ __forceinline__ void block_incl_scan_u16(uint16_t* a, uint32_t* wsum) {
+  constexpr int NW = BLOCK / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t v[ITEMS];
+  uint32_t run = 0;
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    run += a[tid * ITEMS + i];
+    v[i] = run;
+  }
+  uint32_t x = run;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t s = lane < NW ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < NW) wsum[lane] = s;
+  }
+  __syncthreads();
+  const uint32_t base = x - run + (warp ? wsum[warp - 1] : 0);
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) a[tid * ITEMS + i] = (uint16_t)(base + v[i]);
+  __syncthreads();
+}
+
 // Index of the last element <= x in the strictly increasing smem array a[0..n).
 __device__ __forceinline__ uint32_t smem_upper_bound_minus1(const uint32_t* a, uint32_t n, uint32_t x) {
   uint32_t lo = 0, len = n;
