@@ -19,7 +19,7 @@ HEADERS = ["gg_common.cuh", "gg_host.h", "gg_multi.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3", "-I" + INCLUDE, "-I" + CSRC,
-         "--expt-relaxed-constexpr"]
+         "--expt-relaxed-constexpr"] + os.environ.get("GG_NVCC_EXTRA", "").split()
 
 
 def _newest_dep() -> float:

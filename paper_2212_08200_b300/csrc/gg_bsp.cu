@@ -27,6 +27,10 @@
 
 #include "gg_host.h"
 
+#ifndef GG_EPT
+#define GG_EPT 4   // edges per thread per tile of the superstep kernels
+#endif
+
 namespace gg {
 
 namespace {
@@ -62,6 +66,7 @@ struct StepArgs {
 // Where the filter writes: the next (near) frontier and the far pile.
 struct FilterOut {
   const uint32_t* ro;
+  uint32_t sinks;                 // graph has sinks: check the out-degree before the dedup
   uint32_t* bm_next;
   uint32_t* bm_far;
   uint32_t t_cur;                 // near threshold
@@ -79,6 +84,24 @@ struct FilterOut {
 template <int BLOCK, int EPT>
 __device__ __forceinline__ void filter_candidate(MPSmem<BLOCK, EPT>& sm, const FilterOut& fo, uint32_t v,
                                                  uint32_t nd) {
+  if (!fo.sinks) {
+    // every reached vertex has out-edges: dedup first, read the row at flush time
+    const uint32_t bit = 1u << (v & 31);
+    if (nd < fo.t_cur) {
+      if (!(atomicOr(fo.bm_next + (v >> 5), bit) & bit)) {
+        const uint32_t q = atomicAdd(&sm.qn, 1u);
+        sm.qv[q] = v;
+        sm.qd[q] = kInf;   // row read in filter_flush
+      }
+    } else {
+      atomicMin(&sm.fmin, nd);
+      if (!(atomicOr(fo.bm_far + (v >> 5), bit) & bit)) {
+        const uint32_t q = MPSmem<BLOCK, EPT>::ECAP - 1 - atomicAdd(&sm.qfn, 1u);
+        sm.qv[q] = v;
+      }
+    }
+    return;
+  }
   const uint32_t rs = __ldg(fo.ro + v), re = __ldg(fo.ro + v + 1);
   if (re > rs) {
     const uint32_t bit = 1u << (v & 31);
@@ -107,6 +130,15 @@ __device__ __forceinline__ void filter_flush(MPSmem<BLOCK, EPT>& sm, const Filte
   __syncthreads();
   const uint32_t qn = sm.qn, qfn = sm.qfn;
   if (qn == 0 && qfn == 0) return;   // uniform
+  if (qn && !fo.sinks) {
+    for (uint32_t i = threadIdx.x; i < qn; i += BLOCK) {
+      const uint32_t v = sm.qv[i];
+      const uint32_t rs = __ldg(fo.ro + v);
+      sm.qr[i] = rs;
+      sm.qd[i] = __ldg(fo.ro + v + 1) - rs;
+    }
+    __syncthreads();
+  }
   if (qn) {
     const uint32_t tot = block_scan_excl<BLOCK>(sm.qd, qn, sm.wsum);
     if (threadIdx.x == 0) sm.base = atomicAdd(fo.cnt_next, ((unsigned long long)qn << 32) | tot);
@@ -143,7 +175,7 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
                                            const uint32_t* __restrict__ V, const void* __restrict__ edges,
                                            uint32_t* __restrict__ dist, uint32_t* __restrict__ bm_cur,
                                            const FilterOut& fo) {
-  static_assert(!PULL || EPT == 8, "pull uses 8-edge vector runs");
+  static_assert(!PULL || EPT == 2 || EPT == 4 || EPT == 8, "pull uses 2-, 4- or 8-edge vector runs");
   constexpr uint32_t TILE = MPSmem<BLOCK, EPT>::TILE;
   const uint32_t tid = threadIdx.x;
   const uint32_t G = gridDim.x;
@@ -238,7 +270,7 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
       if (g0 < t1) {
         uint32_t col[EPT], wt[EPT];
         if (g0 + EPT <= t1) {
-          load_edges8<PK>(edges, g0, wbits, col, wt);
+          load_edges_run<PK, EPT>(edges, g0, wbits, col, wt);
         } else {
 #pragma unroll
           for (int k = 0; k < EPT; ++k) {
@@ -513,7 +545,8 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
 // merge-path one (pull is the same merge-path sweep in both); a split step
 // refills the near frontier from the far pile.
 template <int BLOCK, int EPT, bool BINS, bool PK>
-__global__ void __launch_bounds__(BLOCK, 4) k_superstep(StepArgs a, cudaGraphConditionalHandle cond, int use_cond) {
+__global__ void __launch_bounds__(BLOCK, EPT == 2 ? 8 : EPT == 4 ? 6 : 4) k_superstep(StepArgs a, cudaGraphConditionalHandle cond,
+                                                                       int use_cond) {
   extern __shared__ __align__(16) unsigned char smraw[];
   MPSmem<BLOCK, EPT>& sm = *reinterpret_cast<MPSmem<BLOCK, EPT>*>(smraw);
   Ctl* ctl = a.ctl;
@@ -527,6 +560,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_superstep(StepArgs a, cudaGraphCon
   uint32_t* bm_cur = a.fr.bm[it % 3];
   FilterOut fo;
   fo.ro = a.g.ro;
+  fo.sinks = a.g.sinks;
   fo.bm_next = a.fr.bm[(it + 1) % 3];
   fo.bm_far = a.fr.bm_far;
   fo.t_cur = ctl->t_cur;
@@ -595,7 +629,7 @@ __device__ __forceinline__ void grid_barrier(Ctl* ctl, unsigned long long deadli
 // slots (a slot is reset two supersteps after its last reader passed a
 // barrier); the far pile rotates over three piles, one per split step.
 template <int BLOCK, int EPT, bool BINS, bool PK>
-__global__ void __launch_bounds__(BLOCK, 4) k_bsp_persistent(StepArgs a) {
+__global__ void __launch_bounds__(BLOCK, EPT == 2 ? 8 : EPT == 4 ? 6 : 4) k_bsp_persistent(StepArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   MPSmem<BLOCK, EPT>& sm = *reinterpret_cast<MPSmem<BLOCK, EPT>*>(smraw);
   Ctl* ctl = a.ctl;
@@ -618,6 +652,7 @@ __global__ void __launch_bounds__(BLOCK, 4) k_bsp_persistent(StepArgs a) {
     uint32_t* bm_cur = a.fr.bm[s0];
     FilterOut fo;
     fo.ro = a.g.ro;
+    fo.sinks = a.g.sinks;
     fo.bm_next = a.fr.bm[s1];
     fo.bm_far = a.fr.bm_far;
     fo.t_cur = t_cur;
@@ -820,7 +855,7 @@ __global__ void k_init_tail(StepArgs a, RunParams rp) {
 }
 
 constexpr int kBlock = 256;
-constexpr int kEpt = 8;
+constexpr int kEpt = GG_EPT;
 constexpr int kVariants = 4;   // bit 0: degree-binned push (else merge-path); bit 1: packed edges
 
 void* superstep_fn(int variant) {

@@ -85,6 +85,7 @@ struct DevGraph {
   const uint32_t* ps;
   uint32_t packed;         // 1: edges are (col << wbits) | weight
   uint32_t wbits;
+  uint32_t sinks;          // 1: some vertex has in-edges but no out-edges
 };
 
 struct Frontier {
@@ -112,25 +113,36 @@ __device__ __forceinline__ uint2 load_edge(const void* base, uint32_t e, uint32_
   }
 }
 
-// Eight consecutive edges starting at e (e a multiple of 8, buffer 256-byte
-// aligned) with 16-byte vector loads.
-template <bool PK>
-__device__ __forceinline__ void load_edges8(const void* base, uint32_t e, uint32_t wbits, uint32_t* col,
-                                            uint32_t* w) {
-  if (PK) {
+// N consecutive edges (N = 2, 4 or 8) starting at e (e a multiple of N,
+// buffer 256-byte aligned) with 8- or 16-byte vector loads.
+template <bool PK, int N>
+__device__ __forceinline__ void load_edges_run(const void* base, uint32_t e, uint32_t wbits, uint32_t* col,
+                                               uint32_t* w) {
+  static_assert(N == 2 || N == 4 || N == 8, "runs of 2, 4 or 8 edges");
+  if (PK && N == 2) {
+    const uint2 q = __ldg(reinterpret_cast<const uint2*>(static_cast<const uint32_t*>(base) + e));
+    const uint32_t mask = (1u << wbits) - 1u;
+    col[0] = q.x >> wbits;
+    w[0] = q.x & mask;
+    col[1] = q.y >> wbits;
+    w[1] = q.y & mask;
+  } else if (PK) {
     const uint4* p = reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(base) + e);
-    const uint4 q0 = __ldg(p), q1 = __ldg(p + 1);
-    const uint32_t x[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
     const uint32_t mask = (1u << wbits) - 1u;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      col[k] = x[k] >> wbits;
-      w[k] = x[k] & mask;
+    for (int h = 0; h < N / 4; ++h) {
+      const uint4 q = __ldg(p + h);
+      const uint32_t x[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        col[4 * h + k] = x[k] >> wbits;
+        w[4 * h + k] = x[k] & mask;
+      }
     }
   } else {
     const uint4* p = reinterpret_cast<const uint4*>(static_cast<const uint2*>(base) + e);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < N / 2; ++k) {
       const uint4 q = __ldg(p + k);
       col[2 * k] = q.x;
       w[2 * k] = q.y;

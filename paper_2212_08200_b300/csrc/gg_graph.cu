@@ -146,6 +146,14 @@ __global__ void k_nonempty_flags(uint32_t n, const uint32_t* __restrict__ t_ro, 
   if (blockIdx.x == 0 && threadIdx.x == 0) flag[n] = 0;
 }
 
+// sinks: reachable vertices (non-empty CSC row) without out-edges
+__global__ void k_find_sinks(uint32_t n, const uint32_t* __restrict__ ro, const uint32_t* __restrict__ t_ro,
+                             uint32_t* __restrict__ flag) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    if (t_ro[v + 1] > t_ro[v] && ro[v + 1] == ro[v]) *flag = 1u;
+}
+
 __global__ void k_pull_list(uint32_t n, const uint32_t* __restrict__ t_ro, const uint32_t* __restrict__ pos,
                             uint32_t* __restrict__ pv, uint32_t* __restrict__ ps) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -270,8 +278,17 @@ gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m64, const uint32_t* ro_
     g->bytes += 2 * sizeof(uint32_t) * std::max<size_t>(np, 1);
     k_pull_list<<<grid_for(n), 256, 0, s>>>(n, g->t_ro, pos, g->pv, g->ps);
     GG_CK(cudaGetLastError());
-    GG_CK(cudaFreeAsync(pos, s));
     g->dg.np = np;
+    uint32_t sinks = 0;
+    if (!g->symmetric) {   // a symmetric graph's reachable vertices all have out-edges
+      GG_CK(cudaMemsetAsync(pos, 0, sizeof(uint32_t), s));
+      k_find_sinks<<<grid_for(n), 256, 0, s>>>(n, g->ro, g->t_ro, pos);
+      GG_CK(cudaGetLastError());
+      GG_CK(cudaMemcpyAsync(&sinks, pos, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+      GG_CK(cudaStreamSynchronize(s));
+    }
+    g->dg.sinks = sinks;
+    GG_CK(cudaFreeAsync(pos, s));
   }
   GG_CK(cudaStreamSynchronize(s));
 
