@@ -199,20 +199,23 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
       const uint32_t idx = j + nent + tid;
       bool valid = false;
       uint32_t s = 0;
+      uint32_t ev = 0, eb = 0;
       if (idx < F) {
+        // all three loads issue together; the range test waits only for S
         s = S[idx];
+        ev = V[idx];
+        if (!PULL) eb = B[idx];
         valid = s < t1;
       }
       if (valid) {
         const uint32_t slot = nent + tid;
         sm.es[slot] = s;
         if (!PULL) {
-          const uint32_t v = V[idx];
-          sm.eb[slot] = B[idx];
-          sm.ec[slot] = ld_cg(dist + v);
-          bm_cur[v >> 5] = 0u;   // the current bitmap is not read in push: clear as we go
+          sm.eb[slot] = eb;
+          sm.ec[slot] = ld_cg(dist + ev);
+          bm_cur[ev >> 5] = 0u;   // the current bitmap is not read in push: clear as we go
         } else {
-          sm.eb[slot] = V[idx];
+          sm.eb[slot] = ev;
           sm.ec[slot] = kInf;
         }
       }
