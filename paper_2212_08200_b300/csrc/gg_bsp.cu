@@ -124,7 +124,10 @@ __device__ __forceinline__ void filter_candidate(MPSmem<BLOCK, EPT>& sm, const F
 
 // Append the CTA's collected vertices to the next frontier (one 64-bit
 // atomicAdd returns queue position and edge-prefix base) and to the far pile.
-template <int BLOCK, int EPT>
+// TRAIL: end with a barrier.  Callers whose next step writes the queue
+// without an intervening barrier need it; the merge-path tile loop does not
+// (its next tile's staging barrier comes first).
+template <int BLOCK, int EPT, bool TRAIL = true>
 __device__ __forceinline__ void filter_flush(MPSmem<BLOCK, EPT>& sm, const FilterOut& fo) {
   constexpr uint32_t ECAP = MPSmem<BLOCK, EPT>::ECAP;
   __syncthreads();
@@ -150,18 +153,18 @@ __device__ __forceinline__ void filter_flush(MPSmem<BLOCK, EPT>& sm, const Filte
   __syncthreads();
   const unsigned long long b = sm.base;
   const uint32_t pos0 = (uint32_t)(b >> 32), eb0 = (uint32_t)b;
+  const uint32_t fb = sm.fbase;
+  if (threadIdx.x == 0) {   // every thread has read the counts by now
+    sm.qn = 0;
+    sm.qfn = 0;
+  }
   for (uint32_t i = threadIdx.x; i < qn; i += BLOCK) {
     fo.nfv[pos0 + i] = sm.qv[i];
     fo.nfr[pos0 + i] = sm.qr[i];
     fo.nfs[pos0 + i] = eb0 + sm.qd[i];
   }
-  for (uint32_t i = threadIdx.x; i < qfn; i += BLOCK) fo.far[sm.fbase + i] = sm.qv[ECAP - 1 - i];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    sm.qn = 0;
-    sm.qfn = 0;
-  }
-  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < qfn; i += BLOCK) fo.far[fb + i] = sm.qv[ECAP - 1 - i];
+  if (TRAIL) __syncthreads();
 }
 
 // Merge-path advance over entries (S strictly increasing edge coordinates,
@@ -195,6 +198,10 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
     const uint32_t t1 = min(t0 + TILE, e1);
     // stage the entries overlapping [t0, t1)
     uint32_t nent = 0;
+    if (!PULL) {
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) sm.own[k * BLOCK + tid] = 0;   // the owner marks of this tile
+    }
     for (;;) {
       const uint32_t idx = j + nent + tid;
       bool valid = false;
@@ -229,9 +236,6 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
       // first marks the tile slot where its edges start, and an inclusive
       // prefix sum over the marks gives each slot its entry.
       const uint32_t len = t1 - t0;
-#pragma unroll
-      for (int k = 0; k < EPT; ++k) sm.own[k * BLOCK + tid] = 0;
-      __syncthreads();
       for (uint32_t jj = 1 + tid; jj < nent; jj += BLOCK) sm.own[sm.es[jj] - t0] = 1;
       __syncthreads();
       block_incl_scan_u16<BLOCK, EPT>(sm.own, sm.wsum);
@@ -317,7 +321,7 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
         }
       }
     }
-    filter_flush(sm, fo);
+    filter_flush<BLOCK, EPT, PULL>(sm, fo);   // push: the next staging barrier protects the queue
     j = j + nent - 1;
   }
   if (ovf) sm.ovf = 1u;
