@@ -67,7 +67,7 @@ struct BSmem {
 };
 
 template <bool PK>
-__global__ void __launch_bounds__(kBB) k_batch_superstep(DevGraph g, BatchBufs w, cudaGraphConditionalHandle cond,
+__global__ void __launch_bounds__(kBB, 6) k_batch_superstep(DevGraph g, BatchBufs w, cudaGraphConditionalHandle cond,
                                                          int use_cond) {
   __shared__ BSmem sm;
   BatchCtl* ctl = w.ctl;
