@@ -56,6 +56,7 @@ constexpr int kBNW = kBB / 32;
 constexpr int kBTile = 1024;
 constexpr int kBWarpEdges = kBTile / kBNW;
 constexpr int kBCap = kBTile + 1;
+constexpr int kBU = 4;   // edges a warp relaxes concurrently
 
 struct BSmem {
   uint32_t es[kBCap], eb[kBCap], ev[kBCap];
@@ -67,7 +68,7 @@ struct BSmem {
 };
 
 template <bool PK>
-__global__ void __launch_bounds__(kBB, 6) k_batch_superstep(DevGraph g, BatchBufs w, cudaGraphConditionalHandle cond,
+__global__ void __launch_bounds__(kBB, 5) k_batch_superstep(DevGraph g, BatchBufs w, cudaGraphConditionalHandle cond,
                                                          int use_cond) {
   __shared__ BSmem sm;
   BatchCtl* ctl = w.ctl;
@@ -144,47 +145,57 @@ __global__ void __launch_bounds__(kBB, 6) k_batch_superstep(DevGraph g, BatchBuf
         uint32_t cur_j = 0xFFFFFFFFu, du_lo = kInf, du_hi = kInf;
         bool act_lo = false, act_hi = false;
         const int nvalid = __popc(vm);   // valid edges are a prefix of the lanes
-        for (int i = 0; i < nvalid; ++i) {
-          const uint32_t ji = __shfl_sync(0xFFFFFFFFu, jj, i);
-          const uint32_t vi = __shfl_sync(0xFFFFFFFFu, vv, i);
-          const uint32_t wi = __shfl_sync(0xFFFFFFFFu, ww, i);
-          if (ji != cur_j) {
-            cur_j = ji;
-            const uint32_t u = sm.ev[ji];
-            const unsigned long long msk = sm.em[ji];
-            const uint32_t* urow = dist + (size_t)u * K + col0;
-            act_lo = (msk >> lane) & 1ull;
-            act_hi = (msk >> (lane + 32)) & 1ull;
-            du_lo = act_lo ? ld_cg(urow + lane) : kInf;
-            du_hi = act_hi ? ld_cg(urow + lane + 32) : kInf;
-          }
-          uint32_t* vrow = dist + (size_t)vi * K + col0;
-          bool imp_lo = false, imp_hi = false;
-          if (act_lo) {
-            const uint32_t nd = add_sat(du_lo, wi, ovf);
-            if (nd < ld_cg(vrow + lane)) {
-              atomicMin(vrow + lane, nd);
-              imp_lo = true;
+        // four edges at a time: their row reads and relaxations are in flight together
+        for (int i0 = 0; i0 < nvalid; i0 += kBU) {
+          uint32_t vi[kBU], nlo[kBU], nhi[kBU], clo[kBU], chi[kBU];
+          bool alo[kBU], ahi[kBU];
+#pragma unroll
+          for (int u = 0; u < kBU; ++u) {
+            const int i = min(i0 + u, nvalid - 1);
+            const uint32_t ji = __shfl_sync(0xFFFFFFFFu, jj, i);
+            vi[u] = __shfl_sync(0xFFFFFFFFu, vv, i);
+            const uint32_t wi = __shfl_sync(0xFFFFFFFFu, ww, i);
+            if (ji != cur_j) {
+              cur_j = ji;
+              const uint32_t uu = sm.ev[ji];
+              const unsigned long long msk = sm.em[ji];
+              const uint32_t* urow = dist + (size_t)uu * K + col0;
+              act_lo = (msk >> lane) & 1ull;
+              act_hi = (msk >> (lane + 32)) & 1ull;
+              du_lo = act_lo ? ld_cg(urow + lane) : kInf;
+              du_hi = act_hi ? ld_cg(urow + lane + 32) : kInf;
             }
+            const bool live = i0 + u < nvalid;
+            alo[u] = live && act_lo;
+            ahi[u] = live && act_hi;
+            nlo[u] = alo[u] ? add_sat(du_lo, wi, ovf) : kInf;
+            nhi[u] = ahi[u] ? add_sat(du_hi, wi, ovf) : kInf;
           }
-          if (act_hi) {
-            const uint32_t nd = add_sat(du_hi, wi, ovf);
-            if (nd < ld_cg(vrow + lane + 32)) {
-              atomicMin(vrow + lane + 32, nd);
-              imp_hi = true;
-            }
+#pragma unroll
+          for (int u = 0; u < kBU; ++u) {
+            const uint32_t* vrow = dist + (size_t)vi[u] * K + col0;
+            clo[u] = alo[u] ? ld_cg(vrow + lane) : 0u;
+            chi[u] = ahi[u] ? ld_cg(vrow + lane + 32) : 0u;
           }
-          const unsigned blo = __ballot_sync(0xFFFFFFFFu, imp_lo);
-          const unsigned bhi = __ballot_sync(0xFFFFFFFFu, imp_hi);
-          if (lane == 0 && (blo | bhi)) {
-            const uint32_t rs = __ldg(g.ro + vi), re = __ldg(g.ro + vi + 1);
-            if (re > rs) {
-              const unsigned long long bits = (unsigned long long)blo | ((unsigned long long)bhi << 32);
-              if (atomicOr(Mn + vi, bits) == 0ull) {
-                const uint32_t q = atomicAdd(&sm.qn, 1u);
-                sm.qv[q] = vi;
-                sm.qr[q] = rs;
-                sm.qd[q] = re - rs;
+#pragma unroll
+          for (int u = 0; u < kBU; ++u) {
+            uint32_t* vrow = dist + (size_t)vi[u] * K + col0;
+            const bool imp_lo = alo[u] && nlo[u] < clo[u];
+            const bool imp_hi = ahi[u] && nhi[u] < chi[u];
+            if (imp_lo) atomicMin(vrow + lane, nlo[u]);
+            if (imp_hi) atomicMin(vrow + lane + 32, nhi[u]);
+            const unsigned blo = __ballot_sync(0xFFFFFFFFu, imp_lo);
+            const unsigned bhi = __ballot_sync(0xFFFFFFFFu, imp_hi);
+            if (lane == 0 && (blo | bhi)) {
+              const uint32_t rs = __ldg(g.ro + vi[u]), re = __ldg(g.ro + vi[u] + 1);
+              if (re > rs) {
+                const unsigned long long bits = (unsigned long long)blo | ((unsigned long long)bhi << 32);
+                if (atomicOr(Mn + vi[u], bits) == 0ull) {
+                  const uint32_t q = atomicAdd(&sm.qn, 1u);
+                  sm.qv[q] = vi[u];
+                  sm.qr[q] = rs;
+                  sm.qd[q] = re - rs;
+                }
               }
             }
           }

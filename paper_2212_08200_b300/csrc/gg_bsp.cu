@@ -63,15 +63,6 @@ struct StepArgs {
   Ctl* ctl;
 };
 
-// Conditional handles of the CUDA-graph loop: `loop` (WHILE: frontier or far
-// pile non-empty) and `sw` (SWITCH between a small grid for supersteps with at
-// most small_cap edges of work and the full co-resident grid).
-struct Conds {
-  cudaGraphConditionalHandle loop;
-  cudaGraphConditionalHandle sw;
-  uint32_t small_cap;
-};
-
 // Where the filter writes: the next (near) frontier and the far pile.
 struct FilterOut {
   const uint32_t* ro;
@@ -481,7 +472,8 @@ __device__ __forceinline__ unsigned long long bsp_globaltimer() {
 // step's kind (push, pull, or a near-far split) and the loop condition.
 template <int BLOCK, int EPT>
 __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t it, uint32_t f,
-                                                   uint32_t E, uint32_t mode, const Conds& cc, int use_cond) {
+                                                   uint32_t E, uint32_t mode, cudaGraphConditionalHandle cond,
+                                                   int use_cond) {
   Ctl* ctl = a.ctl;
   const uint32_t p = it & 1u;
   __syncthreads();
@@ -552,11 +544,7 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
       more = false;
     }
     ctl->running = more ? 1u : 0u;
-    if (use_cond) {
-      const uint32_t work = nm == MODE_PUSH ? En : nm == MODE_SPLIT ? nfar : a.g.m;
-      cudaGraphSetConditional(cc.sw, work > cc.small_cap ? 1u : 0u);
-      cudaGraphSetConditional(cc.loop, more ? 1u : 0u);
-    }
+    if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
   }
 }
 
@@ -564,8 +552,8 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
 // merge-path one (pull is the same merge-path sweep in both); a split step
 // refills the near frontier from the far pile.
 template <int BLOCK, int EPT, bool BINS, bool PK>
-__global__ void __launch_bounds__(BLOCK, EPT == 2 ? 8 : EPT == 4 ? 6 : 4) k_superstep(StepArgs a, Conds cc,
-                                                                                        int use_cond) {
+__global__ void __launch_bounds__(BLOCK, EPT == 2 ? 8 : EPT == 4 ? 6 : 4) k_superstep(StepArgs a, cudaGraphConditionalHandle cond,
+                                                                       int use_cond) {
   extern __shared__ __align__(16) unsigned char smraw[];
   MPSmem<BLOCK, EPT>& sm = *reinterpret_cast<MPSmem<BLOCK, EPT>*>(smraw);
   Ctl* ctl = a.ctl;
@@ -607,7 +595,7 @@ __global__ void __launch_bounds__(BLOCK, EPT == 2 ? 8 : EPT == 4 ? 6 : 4) k_supe
                                        fo);
     }
   }
-  superstep_finalize(sm, a, it, f, E, mode, cc, use_cond);
+  superstep_finalize(sm, a, it, f, E, mode, cond, use_cond);
 }
 
 // Bounded grid barrier for the persistent kernel: generation counter, the
@@ -953,52 +941,37 @@ int superstep_grid(int variant) {
   return cached[variant];
 }
 
-// Graph: WHILE(loop) { SWITCH(sw) { 0: superstep on a small grid,
-//                                   1: superstep on the full grid } }
 gg_status build_graph_exec(gg_graph* g, int variant) {
   BspWorkspace& w = g->bsp;
   if (w.exec[variant]) return GG_OK;
   cudaGraph_t graph = nullptr;
   GG_CK(cudaGraphCreate(&graph, 0));
-  Conds cc;
-  GG_CK(cudaGraphConditionalHandleCreate(&cc.loop, graph, 1, cudaGraphCondAssignDefault));
-  GG_CK(cudaGraphConditionalHandleCreate(&cc.sw, graph, 1, cudaGraphCondAssignDefault));
-  const int full = superstep_grid(variant);
-  const int small = std::min(full, 2 * device_info().num_sms);
-  cc.small_cap = (uint32_t)small * kBlock * kEpt;
+  cudaGraphConditionalHandle h;
+  GG_CK(cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault));
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
-  cp.conditional.handle = cc.loop;
+  cp.conditional.handle = h;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
   cudaGraphNode_t wnode;
   GG_CK(cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  cudaGraphNodeParams sp = {};
-  sp.type = cudaGraphNodeTypeConditional;
-  sp.conditional.handle = cc.sw;
-  sp.conditional.type = cudaGraphCondTypeSwitch;
-  sp.conditional.size = 2;
-  cudaGraphNode_t snode;
-  GG_CK(cudaGraphAddNode(&snode, body, nullptr, nullptr, 0, &sp));
   StepArgs a{g->dg, w.fr, w.ctl};
   int use_cond = 1;
-  void* args[] = {&a, &cc, &use_cond};
-  for (int b = 0; b < 2; ++b) {
-    cudaKernelNodeParams kp = {};
-    kp.func = superstep_fn(variant);
-    kp.gridDim = dim3(b ? full : small);
-    kp.blockDim = dim3(kBlock);
-    kp.sharedMemBytes = (unsigned)superstep_smem(variant);
-    kp.kernelParams = args;
-    cudaGraphNode_t knode;
-    GG_CK(cudaGraphAddKernelNode(&knode, sp.conditional.phGraph_out[b], nullptr, 0, &kp));
-  }
+  void* args[] = {&a, &h, &use_cond};
+  cudaKernelNodeParams kp = {};
+  kp.func = superstep_fn(variant);
+  kp.gridDim = dim3(superstep_grid(variant));
+  kp.blockDim = dim3(kBlock);
+  kp.sharedMemBytes = (unsigned)superstep_smem(variant);
+  kp.kernelParams = args;
+  cudaGraphNode_t knode;
+  GG_CK(cudaGraphAddKernelNode(&knode, body, nullptr, 0, &kp));
   cudaGraphExec_t exec = nullptr;
   GG_CK(cudaGraphInstantiate(&exec, graph, 0));
   w.graph[variant] = graph;
   w.exec[variant] = exec;
-  w.grid[variant] = full;
+  w.grid[variant] = superstep_grid(variant);
   return GG_OK;
 }
 
@@ -1048,7 +1021,7 @@ gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o
   } else {
     const int grid = superstep_grid(variant);
     const size_t smem = superstep_smem(variant);
-    Conds none{0, 0, 0};
+    cudaGraphConditionalHandle none = 0;
     int zero = 0;
     uint32_t* h_running = &g->h_ctl->running;
     uint32_t launched = 0;
