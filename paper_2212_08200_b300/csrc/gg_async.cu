@@ -25,6 +25,14 @@
 //   watchdog every wait is bounded by a %globaltimer budget; when it runs
 //            out the kernel raises `abort`, records GG_ERR_TIMEOUT and every
 //            warp returns.  Nothing spins without a limit.
+//   buckets  near-far priority without barriers: an improved vertex whose new
+//            distance is >= the threshold t_cur is parked in a far pile
+//            (deduplicated by a bitmap).  When nothing is queued or running
+//            (pending == 0), one idle warp raises the threshold and idle warps
+//            split the pile chunk by chunk: entries below the old threshold
+//            were expanded already and are dropped, entries below the new one
+//            are queued, the rest move to the other pile.  Termination:
+//            nothing queued or running, no split in progress, empty pile.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,6 +52,17 @@ struct AsyncCtl {
   uint32_t status;
   uint32_t abort;
   uint32_t* dist;
+  // near-far buckets: vertices improved to a distance >= t_cur are parked in
+  // the far pile far[sel]; when nothing is queued or running, idle warps split
+  // the pile against a raised threshold (drop / queue / keep)
+  uint32_t t_cur, t_prev, delta, sel;
+  uint32_t far_cnt[2];
+  uint32_t far_min;
+  uint32_t phase;          // 0 none, 1 starting, 2 split running
+  uint32_t epoch;          // split starts so far
+  uint32_t split_src, split_total, split_cursor, split_done;
+  uint32_t* far[2];
+  uint32_t* bm_far;
 };
 
 namespace {
@@ -80,15 +99,26 @@ struct AsyncArgs {
   AsyncCtl* ctl;
 };
 
-// Enqueue the improved vertices held by the lanes with want == true.
-__device__ __forceinline__ void push_warp(const AsyncArgs& a, bool want, uint32_t v, uint32_t lane) {
+// Enqueue the improved vertices held by the lanes with want == true (new
+// distance nd): below the threshold into the ring queue, otherwise into the
+// far pile (once, by the far bitmap).
+__device__ __forceinline__ void push_warp(const AsyncArgs& a, bool want, uint32_t v, uint32_t nd, uint32_t lane) {
   bool mine = false;
   if (want) {
     const uint32_t rs = __ldg(a.g.ro + v), re = __ldg(a.g.ro + v + 1);
     if (re > rs) {
-      __threadfence();   // the dist update is visible before the in-queue bit
+      __threadfence();   // the dist update is visible before the in-queue / far bit
       const uint32_t bit = 1u << (v & 31);
-      mine = !(atomicOr(a.inq + (v >> 5), bit) & bit);
+      if (nd < ld_volatile_u32(&a.ctl->t_cur)) {
+        mine = !(atomicOr(a.inq + (v >> 5), bit) & bit);
+      } else {
+        atomicMin(&a.ctl->far_min, nd);
+        if (!(atomicOr(a.ctl->bm_far + (v >> 5), bit) & bit)) {
+          const uint32_t sel = ld_volatile_u32(&a.ctl->sel);
+          const uint32_t pos = atomicAdd(&a.ctl->far_cnt[sel], 1u);
+          a.ctl->far[sel][pos] = v;
+        }
+      }
     }
   }
   const unsigned mm = __ballot_sync(0xFFFFFFFFu, mine);
@@ -180,7 +210,7 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
       for (uint32_t base = 0; base < total; base += 32) {
         const uint32_t gidx = base + lane;
         bool want = false;
-        uint32_t dst = 0;
+        uint32_t dst = 0, ndv = 0;
         if (gidx < total) {
           // last lane whose prefix is <= gidx (lanes without an item repeat the next prefix)
           uint32_t lo = 0, len = 32;
@@ -193,12 +223,13 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
           const uint2 ed = load_edge<PK>(a.g.edges, s_row[wid][k] + (gidx - s_pref[wid][k]), a.g.wbits);
           const uint32_t nd = add_sat(s_du[wid][k], ed.y, ovf);
           dst = ed.x;
+          ndv = nd;
           if (nd < ld_cg(dist + dst)) {
             const uint32_t old = atomicMin(dist + dst, nd);
             want = nd < old;
           }
         }
-        push_warp(a, want, dst, lane);
+        push_warp(a, want, dst, ndv, lane);
       }
       pops += got ? 1 : 0;
       edges += got ? deg : 0;
@@ -207,17 +238,96 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
       if (lane == 0) atomicAdd(&ctl->pending, (unsigned long long)(-(long long)__popc(gm)));
       if (ld_volatile_u32(&ctl->abort)) break;
     } else {
-      int stop = 0;
+      // idle: stop, start or join a far-pile split, or back off
+      int act = 0;   // 0 back off, 1 stop, 2 split work
       if (lane == 0) {
-        if (ld_volatile_u64(&ctl->pending) == 0ull || ld_volatile_u32(&ctl->abort)) stop = 1;
-        else if (globaltimer() - ctl->t_start > ctl->watchdog_ns) {
+        if (ld_volatile_u32(&ctl->abort)) {
+          act = 1;
+        } else if (globaltimer() - ctl->t_start > ctl->watchdog_ns) {
           atomicOr(&ctl->status, DS_TIMEOUT);
           atomicExch(&ctl->abort, 1u);
-          stop = 1;
+          act = 1;
+        } else {
+          const uint32_t e1 = ld_volatile_u32(&ctl->epoch);
+          const uint32_t ph = ld_volatile_u32(&ctl->phase);
+          if (ph == 2) {
+            act = 2;
+          } else if (ph == 0) {
+            const uint32_t nfar = ld_volatile_u32(&ctl->far_cnt[ld_volatile_u32(&ctl->sel)]);
+            const unsigned long long pend = ld_volatile_u64(&ctl->pending);
+            const uint32_t e2 = ld_volatile_u32(&ctl->epoch);
+            if (pend == 0ull && e1 == e2 && ld_volatile_u32(&ctl->phase) == 0) {
+              if (nfar == 0) {
+                act = 1;   // nothing queued, running or parked: done
+              } else if (atomicCAS(&ctl->phase, 0u, 1u) == 0u) {
+                // start a split; no work may be in flight (re-checked under the lock)
+                __threadfence();
+                const uint32_t src = ctl->sel;
+                const uint32_t total = ld_volatile_u32(&ctl->far_cnt[src]);
+                if (ld_volatile_u64(&ctl->pending) != 0ull || total == 0) {
+                  atomicExch(&ctl->phase, 0u);
+                } else {
+                  const unsigned long long t1 = (unsigned long long)ctl->t_cur + ctl->delta;
+                  const unsigned long long t2 = (unsigned long long)ctl->far_min + 1;
+                  const unsigned long long tn = t1 > t2 ? t1 : t2;
+                  ctl->t_prev = ctl->t_cur;
+                  ctl->t_cur = tn >= kInf ? kInf : (uint32_t)tn;
+                  ctl->far_min = kInf;
+                  ctl->split_src = src;
+                  ctl->split_total = total;
+                  ctl->split_cursor = 0;
+                  ctl->split_done = 0;
+                  ctl->sel = src ^ 1u;
+                  ctl->epoch = ctl->epoch + 1;
+                  __threadfence();
+                  atomicExch(&ctl->phase, 2u);
+                  act = 2;
+                }
+              }
+            }
+          }
         }
       }
-      stop = __shfl_sync(0xFFFFFFFFu, stop, 0);
-      if (stop) break;
+      act = __shfl_sync(0xFFFFFFFFu, act, 0);
+      if (act == 1) break;
+      if (act == 2) {
+        // one 32-entry chunk of the far pile being split
+        uint32_t chunk = 0;
+        if (lane == 0) chunk = atomicAdd(&ctl->split_cursor, 32u);
+        chunk = __shfl_sync(0xFFFFFFFFu, chunk, 0);
+        const uint32_t total = ld_volatile_u32(&ctl->split_total);
+        if (chunk < total) {
+          const uint32_t idx = chunk + lane;
+          bool want = false;
+          uint32_t v = 0, d = 0;
+          if (idx < total) {
+            const uint32_t src = ld_volatile_u32(&ctl->split_src);
+            v = ld_cg(ctl->far[src] + idx);
+            d = ld_cg(dist + v);
+            const uint32_t bit = 1u << (v & 31);
+            if (d < ld_volatile_u32(&ctl->t_cur)) {
+              atomicAnd(ctl->bm_far + (v >> 5), ~bit);
+              want = d >= ld_volatile_u32(&ctl->t_prev);   // below t_prev: expanded already
+            } else {
+              atomicMin(&ctl->far_min, d);
+              const uint32_t sel = ld_volatile_u32(&ctl->sel);
+              const uint32_t pos = atomicAdd(&ctl->far_cnt[sel], 1u);
+              ctl->far[sel][pos] = v;
+            }
+          }
+          push_warp(a, want, v, d, lane);
+          const uint32_t done = (uint32_t)min(32u, total - chunk);
+          __threadfence();
+          __syncwarp();
+          if (lane == 0 && atomicAdd(&ctl->split_done, done) + done == total) {
+            ctl->far_cnt[ld_volatile_u32(&ctl->split_src)] = 0u;
+            __threadfence();
+            atomicExch(&ctl->phase, 0u);
+          }
+          backoff = 32;
+          continue;
+        }
+      }
       __nanosleep(backoff);
       backoff = min(backoff * 2, 1024u);
     }
@@ -236,16 +346,36 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
   }
 }
 
-__global__ void k_async_init(DevGraph g, uint32_t* dist, uint32_t* inq) {
+__global__ void k_async_init(DevGraph g, uint32_t* dist, uint32_t* inq, uint32_t* bm_far) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   for (uint64_t i = t; i < g.n; i += stride) dist[i] = kInf;
-  for (uint64_t i = t; i < g.nwords; i += stride) inq[i] = 0u;
+  for (uint64_t i = t; i < g.nwords; i += stride) {
+    inq[i] = 0u;
+    bm_far[i] = 0u;
+  }
 }
 
 __global__ void k_async_seed(DevGraph g, uint32_t src, uint32_t* dist, unsigned long long* Q, uint32_t* inq,
-                             AsyncCtl* ctl, unsigned long long watchdog_ns) {
+                             AsyncCtl* ctl, unsigned long long watchdog_ns, uint32_t delta, uint32_t* far0,
+                             uint32_t* far1, uint32_t* bm_far) {
   dist[src] = 0u;
+  ctl->t_cur = delta;
+  ctl->t_prev = 0;
+  ctl->delta = delta;
+  ctl->sel = 0;
+  ctl->far_cnt[0] = 0;
+  ctl->far_cnt[1] = 0;
+  ctl->far_min = kInf;
+  ctl->phase = 0;
+  ctl->epoch = 0;
+  ctl->split_src = 0;
+  ctl->split_total = 0;
+  ctl->split_cursor = 0;
+  ctl->split_done = 0;
+  ctl->far[0] = far0;
+  ctl->far[1] = far1;
+  ctl->bm_far = bm_far;
   ctl->head = 0;
   ctl->pops = 0;
   ctl->edges = 0;
@@ -284,7 +414,9 @@ gg_status async_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options&
     while ((1ull << logcap) < need) ++logcap;
     const size_t qbytes = sizeof(unsigned long long) << logcap;
     const size_t nw = (g->n + 31) / 32;
-    const size_t total = qbytes + ((sizeof(uint32_t) * nw + 255) & ~size_t(255)) + 256;
+    const size_t r_bm = (sizeof(uint32_t) * nw + 255) & ~size_t(255);
+    const size_t r_far = (sizeof(uint32_t) * std::max<size_t>(g->n, 1) + 255) & ~size_t(255);
+    const size_t total = qbytes + 2 * r_bm + 2 * r_far + 256;
     char* p = nullptr;
     GG_CK(cudaMalloc(&p, total));
     w.block = p;
@@ -292,7 +424,10 @@ gg_status async_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options&
     w.queue = reinterpret_cast<uint32_t*>(p);
     w.cap = logcap;   // stored as log2 capacity
     w.inq = reinterpret_cast<uint32_t*>(p + qbytes);
-    w.ctl = p + qbytes + ((sizeof(uint32_t) * nw + 255) & ~size_t(255));
+    w.bm_far = reinterpret_cast<uint32_t*>(p + qbytes + r_bm);
+    w.far[0] = reinterpret_cast<uint32_t*>(p + qbytes + 2 * r_bm);
+    w.far[1] = reinterpret_cast<uint32_t*>(p + qbytes + 2 * r_bm + r_far);
+    w.ctl = p + qbytes + 2 * r_bm + 2 * r_far;
     if (!g->h_async) GG_CK(cudaMallocHost(&g->h_async, sizeof(AsyncCtl)));
   }
   const uint32_t logcap = w.cap;
@@ -301,10 +436,11 @@ gg_status async_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options&
   GG_CK(cudaMemsetAsync(Q, 0, sizeof(unsigned long long) << logcap, s));
   unsigned ib = (unsigned)std::min<uint64_t>((g->n + 255) / 256, (uint64_t)di.num_sms * 8);
   if (ib == 0) ib = 1;
-  k_async_init<<<ib, 256, 0, s>>>(g->dg, dist, w.inq);
+  k_async_init<<<ib, 256, 0, s>>>(g->dg, dist, w.inq, w.bm_far);
   GG_CK(cudaGetLastError());
   const unsigned long long wd = o.watchdog_ns ? o.watchdog_ns : 10000000000ull;
-  k_async_seed<<<1, 1, 0, s>>>(g->dg, src, dist, Q, w.inq, ctl, wd);
+  const uint32_t delta = o.delta == GG_DELTA_NONE ? kInf : (o.delta ? o.delta : g->default_delta);
+  k_async_seed<<<1, 1, 0, s>>>(g->dg, src, dist, Q, w.inq, ctl, wd, delta, w.far[0], w.far[1], w.bm_far);
   GG_CK(cudaGetLastError());
   AsyncArgs a{g->dg, Q, logcap, w.inq, ctl};
   void* args[] = {&a};

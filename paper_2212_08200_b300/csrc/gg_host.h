@@ -49,6 +49,8 @@ struct AsyncWorkspace {
   uint32_t* queue = nullptr;   // ring of vertex ids
   uint32_t cap = 0;            // power of two >= n
   uint32_t* inq = nullptr;     // in-queue bitmap
+  uint32_t* bm_far = nullptr;  // far-pile bitmap
+  uint32_t* far[2] = {nullptr, nullptr};
   void* ctl = nullptr;         // AsyncCtl
   int grid = 0;
 };

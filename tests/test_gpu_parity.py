@@ -126,7 +126,7 @@ def test_near_far_deltas(delta, workload):
     g = gg().Graph(ro, col, w, symmetric=True)
     ref = oracle.dijkstra(ro, col, w, src)
     for mode in [("graph", "push"), ("graph", "auto"), ("host", "push", "bins"), ("persistent", "push"),
-                 ("persistent", "auto")]:
+                 ("persistent", "auto"), ("async", "auto")]:
         got, st = run(g, src, *mode, delta=delta)
         np.testing.assert_array_equal(got, ref, err_msg=f"delta={delta} {mode}")
     g.close()
@@ -141,6 +141,11 @@ def test_near_far_high_diameter_grid_reduces_work():
     got, st_nf = run(g, 0, "graph", "push", delta=500)
     np.testing.assert_array_equal(got, ref)
     assert st_nf["edges_scanned"] < st_bf["edges_scanned"]
+    got, st_abf = run(g, 0, "async", delta=NONE)
+    np.testing.assert_array_equal(got, ref)
+    got, st_anf = run(g, 0, "async", delta=500)
+    np.testing.assert_array_equal(got, ref)
+    assert st_anf["edges_scanned"] < st_abf["edges_scanned"]
     g.close()
 
 
