@@ -39,6 +39,10 @@ struct BatchCtl {
   uint32_t max_frontier;
   uint32_t* dist;
   unsigned long long edges_scanned, frontier_total;
+  // near-far buckets over (vertex, source) pairs: a pair improved to a
+  // distance >= t_cur is parked as a bit of fmask[v]; the vertices with
+  // parked bits form the far list far_v[fsel]
+  uint32_t t_cur, t_prev, delta, fsel, fcnt[2], far_min, mode, splits;
 };
 
 struct BatchBufs {
@@ -46,6 +50,8 @@ struct BatchBufs {
   uint32_t* fr[3];
   uint32_t* fs[3];
   unsigned long long* mask[3];
+  unsigned long long* fmask;
+  uint32_t* far_v[2];
   BatchCtl* ctl;
 };
 
@@ -82,6 +88,7 @@ __global__ void __launch_bounds__(kBB, 5) k_batch_superstep(DevGraph g, BatchBuf
   const unsigned long long* Mc = w.mask[pc];
   unsigned long long* Mn = w.mask[pn];
   const uint32_t wbits = g.wbits;
+  const uint32_t T = ctl->t_cur, fsel = ctl->fsel, bmode = ctl->mode;
   // zero the masks of F_{t-1}
   {
     const uint32_t Fo = (uint32_t)(ctl->cnt[po] >> 32);
@@ -97,7 +104,67 @@ __global__ void __launch_bounds__(kBB, 5) k_batch_superstep(DevGraph g, BatchBuf
   bool ovf = false;
   const uint32_t e0 = (uint32_t)(((unsigned long long)blockIdx.x * E) / gridDim.x);
   const uint32_t e1 = (uint32_t)(((unsigned long long)(blockIdx.x + 1) * E) / gridDim.x);
-  if (F > 0 && e0 < e1) {
+  if (bmode == 1) {
+    // split step: every parked (vertex, source) bit is re-examined against
+    // the raised threshold: below t_prev it was expanded already (drop),
+    // below t_cur it joins the next frontier, otherwise it stays parked
+    const uint32_t nfar = ctl->fcnt[fsel];
+    const uint32_t t_prev = ctl->t_prev;
+    constexpr uint32_t R = 64;   // far vertices per warp between flushes
+    for (uint32_t base = blockIdx.x * kBNW * R; base < nfar; base += gridDim.x * kBNW * R) {
+      for (uint32_t r = 0; r < R; ++r) {
+        const uint32_t i = base + warp * R + r;
+        if (i >= nfar) break;   // warp-uniform
+        const uint32_t v = w.far_v[fsel][i];
+        const unsigned long long bits = w.fmask[v];
+        const uint32_t* vrow = dist + (size_t)v * K + col0;
+        const bool lo = (bits >> lane) & 1ull, hi = (bits >> (lane + 32)) & 1ull;
+        const uint32_t dlo = lo ? ld_cg(vrow + lane) : 0u, dhi = hi ? ld_cg(vrow + lane + 32) : 0u;
+        const bool mlo = lo && dlo >= t_prev && dlo < T, mhi = hi && dhi >= t_prev && dhi < T;
+        const bool klo = lo && dlo >= T, khi = hi && dhi >= T;
+        const unsigned nb_lo = __ballot_sync(0xFFFFFFFFu, mlo), nb_hi = __ballot_sync(0xFFFFFFFFu, mhi);
+        const unsigned kb_lo = __ballot_sync(0xFFFFFFFFu, klo), kb_hi = __ballot_sync(0xFFFFFFFFu, khi);
+        if (kb_lo | kb_hi) {
+          uint32_t fm = min(klo ? dlo : kInf, khi ? dhi : kInf);
+#pragma unroll
+          for (int o = 16; o; o >>= 1) fm = min(fm, __shfl_xor_sync(0xFFFFFFFFu, fm, o));
+          if (lane == 0) atomicMin(&ctl->far_min, fm);
+        }
+        if (lane == 0) {
+          const unsigned long long kb = (unsigned long long)kb_lo | ((unsigned long long)kb_hi << 32);
+          const unsigned long long nb = (unsigned long long)nb_lo | ((unsigned long long)nb_hi << 32);
+          w.fmask[v] = kb;
+          if (kb) {
+            const uint32_t pos = atomicAdd(&ctl->fcnt[fsel ^ 1u], 1u);
+            w.far_v[fsel ^ 1u][pos] = v;
+          }
+          if (nb && atomicOr(Mn + v, nb) == 0ull) {
+            const uint32_t rs = __ldg(g.ro + v);
+            const uint32_t q = atomicAdd(&sm.qn, 1u);
+            sm.qv[q] = v;
+            sm.qr[q] = rs;
+            sm.qd[q] = __ldg(g.ro + v + 1) - rs;
+          }
+        }
+      }
+      __syncthreads();
+      const uint32_t qn = sm.qn;
+      if (qn) {
+        const uint32_t tot = block_scan_excl<kBB>(sm.qd, qn, sm.wsum);
+        if (tid == 0) sm.base = atomicAdd(&ctl->cnt[pn], ((unsigned long long)qn << 32) | tot);
+        __syncthreads();
+        const uint32_t pos0 = (uint32_t)(sm.base >> 32), eb0 = (uint32_t)sm.base;
+        for (uint32_t i = tid; i < qn; i += kBB) {
+          w.fv[pn][pos0 + i] = sm.qv[i];
+          w.fr[pn][pos0 + i] = sm.qr[i];
+          w.fs[pn][pos0 + i] = eb0 + sm.qd[i];
+        }
+        __syncthreads();
+        if (tid == 0) sm.qn = 0;
+      }
+      __syncthreads();
+    }
+  } else if (F > 0 && e0 < e1) {
     const uint32_t* S = w.fs[pc];
     if (tid < 32) {
       const uint32_t j = warp_search_le(S, F, e0);
@@ -184,17 +251,33 @@ __global__ void __launch_bounds__(kBB, 5) k_batch_superstep(DevGraph g, BatchBuf
             const bool imp_hi = ahi[u] && nhi[u] < chi[u];
             if (imp_lo) atomicMin(vrow + lane, nlo[u]);
             if (imp_hi) atomicMin(vrow + lane + 32, nhi[u]);
-            const unsigned blo = __ballot_sync(0xFFFFFFFFu, imp_lo);
-            const unsigned bhi = __ballot_sync(0xFFFFFFFFu, imp_hi);
-            if (lane == 0 && (blo | bhi)) {
+            // near bits (new distance below the threshold) join the next
+            // frontier's mask; the others are parked in the far mask
+            const bool far_lo = imp_lo && nlo[u] >= T, far_hi = imp_hi && nhi[u] >= T;
+            const unsigned blo = __ballot_sync(0xFFFFFFFFu, imp_lo && !far_lo);
+            const unsigned bhi = __ballot_sync(0xFFFFFFFFu, imp_hi && !far_hi);
+            const unsigned flo = __ballot_sync(0xFFFFFFFFu, far_lo);
+            const unsigned fhi = __ballot_sync(0xFFFFFFFFu, far_hi);
+            if (flo | fhi) {
+              uint32_t fm = min(far_lo ? nlo[u] : kInf, far_hi ? nhi[u] : kInf);
+#pragma unroll
+              for (int o = 16; o; o >>= 1) fm = min(fm, __shfl_xor_sync(0xFFFFFFFFu, fm, o));
+              if (lane == 0) atomicMin(&ctl->far_min, fm);
+            }
+            if (lane == 0 && (blo | bhi | flo | fhi)) {
               const uint32_t rs = __ldg(g.ro + vi[u]), re = __ldg(g.ro + vi[u] + 1);
               if (re > rs) {
                 const unsigned long long bits = (unsigned long long)blo | ((unsigned long long)bhi << 32);
-                if (atomicOr(Mn + vi[u], bits) == 0ull) {
+                if (bits && atomicOr(Mn + vi[u], bits) == 0ull) {
                   const uint32_t q = atomicAdd(&sm.qn, 1u);
                   sm.qv[q] = vi[u];
                   sm.qr[q] = rs;
                   sm.qd[q] = re - rs;
+                }
+                const unsigned long long fb = (unsigned long long)flo | ((unsigned long long)fhi << 32);
+                if (fb && atomicOr(w.fmask + vi[u], fb) == 0ull) {
+                  const uint32_t pos = atomicAdd(&ctl->fcnt[fsel], 1u);
+                  w.far_v[fsel][pos] = vi[u];
                 }
               }
             }
@@ -233,15 +316,34 @@ __global__ void __launch_bounds__(kBB, 5) k_batch_superstep(DevGraph g, BatchBuf
     __threadfence();
     const unsigned long long cn = atomicAdd(&ctl->cnt[pn], 0ull);
     const uint32_t fn = (uint32_t)(cn >> 32);
-    if (F > 0) {
+    if (F > 0 && bmode == 0) {
       ctl->edges_scanned += E;
       ctl->frontier_total += F;
       ctl->max_frontier = max(ctl->max_frontier, F);
     }
+    uint32_t fs_now = fsel;
+    if (bmode == 1) {   // the kept vertices went to the other list
+      ctl->fcnt[fsel] = 0u;
+      fs_now = fsel ^ 1u;
+      ctl->fsel = fs_now;
+      ctl->splits += 1;
+    }
+    const uint32_t nfar = atomicAdd(&ctl->fcnt[fs_now], 0u);
+    if (fn == 0 && nfar > 0) {
+      const unsigned long long t1 = (unsigned long long)ctl->t_cur + ctl->delta;
+      const unsigned long long t2 = (unsigned long long)atomicAdd(&ctl->far_min, 0u) + 1;
+      const unsigned long long tn = t1 > t2 ? t1 : t2;
+      ctl->t_prev = ctl->t_cur;
+      ctl->t_cur = tn >= kInf ? kInf : (uint32_t)tn;
+      ctl->far_min = kInf;
+      ctl->mode = 1u;
+    } else {
+      ctl->mode = 0u;
+    }
     ctl->cnt[po] = 0ull;
     ctl->done_ctas = 0u;
     ctl->iter = it + 1;
-    bool more = fn != 0;
+    bool more = fn != 0 || nfar != 0;
     if (more && it + 1 >= ctl->max_iter) {
       ctl->status |= DS_ITER_CAP;
       more = false;
@@ -268,7 +370,7 @@ __global__ void k_batch_fill(uint32_t* dist, unsigned long long count) {
 // group start: dist[src_s][col0+s] := 0; initial frontier = distinct sources
 // with out-edges, each carrying the mask of its columns.  One CTA of 64.
 __global__ void k_batch_seed(DevGraph g, BatchBufs w, const uint32_t* srcs, uint32_t k, uint32_t col0,
-                             uint32_t kg, uint32_t* dist, uint32_t max_iter) {
+                             uint32_t kg, uint32_t* dist, uint32_t max_iter, uint32_t delta) {
   BatchCtl* ctl = w.ctl;
   const uint32_t s = threadIdx.x;
   if (s == 0) {
@@ -286,6 +388,15 @@ __global__ void k_batch_seed(DevGraph g, BatchBufs w, const uint32_t* srcs, uint
     ctl->max_frontier = 0;
     ctl->edges_scanned = 0;
     ctl->frontier_total = 0;
+    ctl->t_cur = delta;
+    ctl->t_prev = 0;
+    ctl->delta = delta;
+    ctl->fsel = 0;
+    ctl->fcnt[0] = 0;
+    ctl->fcnt[1] = 0;
+    ctl->far_min = kInf;
+    ctl->mode = 0;
+    ctl->splits = 0;
   }
   __syncthreads();
   if (s < kg) {
@@ -325,7 +436,7 @@ static gg_status batch_ws(gg_graph* g, BatchWorkspace** out) {
     BatchWorkspace* w = new BatchWorkspace();
     const size_t n = std::max<uint32_t>(g->n, 1);
     auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
-    const size_t total = 9 * r256(4 * n) + 3 * r256(8 * n) + r256(sizeof(BatchCtl));
+    const size_t total = 11 * r256(4 * n) + 4 * r256(8 * n) + r256(sizeof(BatchCtl));
     char* p = nullptr;
     cudaError_t e = cudaMalloc(&p, total);
     if (e != cudaSuccess) { delete w; return cuda_fail(e, "cudaMalloc(batch workspace)"); }
@@ -339,6 +450,8 @@ static gg_status batch_ws(gg_graph* g, BatchWorkspace** out) {
       w->b.fs[i] = reinterpret_cast<uint32_t*>(take(4 * n));
     }
     for (int i = 0; i < 3; ++i) w->b.mask[i] = reinterpret_cast<unsigned long long*>(take(8 * n));
+    w->b.fmask = reinterpret_cast<unsigned long long*>(take(8 * n));
+    for (int i = 0; i < 2; ++i) w->b.far_v[i] = reinterpret_cast<uint32_t*>(take(4 * n));
     w->b.ctl = reinterpret_cast<BatchCtl*>(take(sizeof(BatchCtl)));
     e = cudaMallocHost(&w->h_ctl, sizeof(BatchCtl));
     if (e != cudaSuccess) { cudaFree(p); delete w; return cuda_fail(e, "cudaMallocHost"); }
@@ -403,18 +516,23 @@ gg_status batch_run(gg_graph* g, const uint32_t* srcs, uint32_t k, uint32_t* dis
       1, std::min<unsigned long long>((count / 4 + 255) / 256, (unsigned long long)device_info().num_sms * 8));
   k_batch_fill<<<fb, 256, 0, s>>>(dist, count);
   GG_CK(cudaGetLastError());
-  const uint32_t max_iter = o.max_iterations ? o.max_iterations : (g->n + 2u < g->n ? 0xFFFFFFFFu : g->n + 2u);
+  // near-far buckets for the batch: explicit delta, else the graph's default
+  const uint32_t delta = o.delta == GG_DELTA_NONE ? kInf : (o.delta ? o.delta : g->default_delta);
+  const unsigned long long cap = delta == kInf ? (unsigned long long)g->n + 2 : 4ull * g->n + 16;
+  const uint32_t max_iter = o.max_iterations ? o.max_iterations : (cap >= 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)cap);
   for (uint32_t col0 = 0; col0 < k; col0 += 64) {
     const uint32_t kg = std::min<uint32_t>(64, k - col0);
     // the previous group (or call) may leave the masks of its last frontier set
     for (int i = 0; i < 3; ++i) GG_CK(cudaMemsetAsync(w->b.mask[i], 0, 8 * (size_t)g->n, s));
-    k_batch_seed<<<1, 64, 0, s>>>(g->dg, w->b, w->srcs, k, col0, kg, dist, max_iter);
+    GG_CK(cudaMemsetAsync(w->b.fmask, 0, 8 * (size_t)g->n, s));
+    k_batch_seed<<<1, 64, 0, s>>>(g->dg, w->b, w->srcs, k, col0, kg, dist, max_iter, delta);
     GG_CK(cudaGetLastError());
     GG_CK(cudaGraphLaunch(w->exec, s));
     if (o.stats) {
       GG_CK(cudaMemcpyAsync(w->h_ctl, w->b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
       GG_CK(cudaStreamSynchronize(s));
       o.stats->iterations += w->h_ctl->iter;
+      o.stats->pull_iterations += 0;
       o.stats->edges_scanned += w->h_ctl->edges_scanned;
       o.stats->frontier_total += w->h_ctl->frontier_total;
       o.stats->max_frontier = std::max(o.stats->max_frontier, w->h_ctl->max_frontier);

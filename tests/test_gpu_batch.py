@@ -24,13 +24,13 @@ def run_batch(g, srcs, **kw):
     return d.cpu().numpy(), st.as_dict()
 
 
-@pytest.mark.parametrize("k", [1, 5, 64, 100])
-@pytest.mark.parametrize("pack", [True, False])
-def test_rmat16_batch_matches_oracle(k, pack):
+@pytest.mark.parametrize("k,pack,delta", [(1, True, 0), (5, False, 0), (64, True, 0), (100, False, 0),
+                                          (64, True, 1), (64, False, 25), (100, True, 0xFFFFFFFF), (5, True, 300)])
+def test_rmat16_batch_matches_oracle(k, pack, delta):
     ro, col, w, _ = graphgen.workload("rmat16")
     srcs = graphgen.sample_sources(ro, k, seed=3)
     g = gg().Graph(ro, col, w, symmetric=True, pack=pack)
-    got, st = run_batch(g, srcs)
+    got, st = run_batch(g, srcs, delta=delta)
     ref = oracle.dijkstra_many(ro, col, w, srcs, threads=8)
     for s in range(k):
         np.testing.assert_array_equal(got[:, s], ref[s], err_msg=f"column {s}")
@@ -56,12 +56,13 @@ def test_duplicates_isolated_and_tiny_graphs():
     g.close()
 
 
-def test_grid64_batch_and_reuse():
+@pytest.mark.parametrize("delta", [0, 1, 50, 0xFFFFFFFF])
+def test_grid64_batch_and_reuse(delta):
     ro, col, w, _ = graphgen.workload("grid64")
     g = gg().Graph(ro, col, w, symmetric=True)
     for seed in (1, 2):                               # workspace reuse across calls
         srcs = graphgen.sample_sources(ro, 64, seed=seed)
-        got, _ = run_batch(g, srcs)
+        got, _ = run_batch(g, srcs, delta=delta)
         ref = oracle.dijkstra_many(ro, col, w, srcs, threads=8)
         np.testing.assert_array_equal(got.T, ref)
     g.close()
