@@ -233,9 +233,13 @@ gg_status gg_autotune(gg_graph_t g, const uint32_t* srcs, uint32_t nsrc, uint32_
 gg_status gg_sssp_batch(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t* dist_out,
                         cudaStream_t stream);
 
-/* As gg_sssp_batch with options: max_iterations and stats are honoured
- * (stats summed over the 64-source groups; setting stats synchronises the
- * stream); policy, direction and load-balance fields are ignored. */
+/* As gg_sssp_batch with options: max_iterations, stats (summed over the
+ * 64-source groups; setting stats synchronises the stream) and delta are
+ * honoured; policy, direction and load-balance fields are ignored.  delta
+ * 0 or GG_DELTA_NONE runs the plain frontier loop (the default: buckets make
+ * a vertex whose sources fall in different buckets expand once per bucket);
+ * another value parks (vertex, source) pairs at or above the threshold in
+ * per-vertex far masks. */
 gg_status gg_sssp_batch_ex(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t* dist_out,
                            const gg_options* opt, cudaStream_t stream);
 

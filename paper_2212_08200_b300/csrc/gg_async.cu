@@ -41,17 +41,11 @@
 
 namespace gg {
 
-// The hot counters sit on separate 128-byte lines: every warp polls or
-// updates them, and sharing a line serialises unrelated atomics.
 struct AsyncCtl {
-  alignas(128) unsigned long long head;
-  alignas(128) unsigned long long tail;
-  alignas(128) unsigned long long pending;
-  alignas(128) uint32_t phase;          // 0 none, 1 starting, 2 split running
-  uint32_t epoch;                       // split starts so far
-  alignas(128) uint32_t split_cursor;
-  alignas(128) uint32_t split_done;
-  alignas(128) unsigned long long pops;
+  unsigned long long head;
+  unsigned long long tail;
+  unsigned long long pending;
+  unsigned long long pops;
   unsigned long long edges;
   unsigned long long watchdog_ns;
   unsigned long long t_start;
@@ -64,7 +58,9 @@ struct AsyncCtl {
   uint32_t t_cur, t_prev, delta, sel;
   uint32_t far_cnt[2];
   uint32_t far_min;
-  uint32_t split_src, split_total;
+  uint32_t phase;          // 0 none, 1 starting, 2 split running
+  uint32_t epoch;          // split starts so far
+  uint32_t split_src, split_total, split_cursor, split_done;
   uint32_t* far[2];
   uint32_t* bm_far;
 };
@@ -420,7 +416,7 @@ gg_status async_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options&
     const size_t nw = (g->n + 31) / 32;
     const size_t r_bm = (sizeof(uint32_t) * nw + 255) & ~size_t(255);
     const size_t r_far = (sizeof(uint32_t) * std::max<size_t>(g->n, 1) + 255) & ~size_t(255);
-    const size_t total = qbytes + 2 * r_bm + 2 * r_far + ((sizeof(AsyncCtl) + 255) & ~size_t(255));
+    const size_t total = qbytes + 2 * r_bm + 2 * r_far + 256;
     char* p = nullptr;
     GG_CK(cudaMalloc(&p, total));
     w.block = p;

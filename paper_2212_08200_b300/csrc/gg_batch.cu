@@ -62,7 +62,7 @@ constexpr int kBNW = kBB / 32;
 constexpr int kBTile = 1024;
 constexpr int kBWarpEdges = kBTile / kBNW;
 constexpr int kBCap = kBTile + 1;
-constexpr int kBU = 4;   // edges a warp relaxes concurrently
+constexpr int kBU = 1;   // edges a warp relaxes concurrently
 
 struct BSmem {
   uint32_t es[kBCap], eb[kBCap], ev[kBCap];
@@ -85,15 +85,15 @@ __global__ void __launch_bounds__(kBB, 5) k_batch_superstep(DevGraph g, BatchBuf
   const uint32_t F = (uint32_t)(c >> 32), E = (uint32_t)c;
   const uint32_t K = ctl->k, col0 = ctl->col0;
   uint32_t* dist = ctl->dist;
-  const unsigned long long* Mc = w.mask[pc];
-  unsigned long long* Mn = w.mask[pn];
+  const unsigned long long* Mc = pick3(w.mask, pc);
+  unsigned long long* Mn = pick3(w.mask, pn);
   const uint32_t wbits = g.wbits;
   const uint32_t T = ctl->t_cur, fsel = ctl->fsel, bmode = ctl->mode;
   // zero the masks of F_{t-1}
   {
     const uint32_t Fo = (uint32_t)(ctl->cnt[po] >> 32);
-    const uint32_t* fvo = w.fv[po];
-    unsigned long long* Mo = w.mask[po];
+    const uint32_t* fvo = pick3(w.fv, po);
+    unsigned long long* Mo = pick3(w.mask, po);
     for (uint32_t i = blockIdx.x * kBB + tid; i < Fo; i += gridDim.x * kBB) Mo[fvo[i]] = 0ull;
   }
   if (tid == 0) {
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kBB, 5) k_batch_superstep(DevGraph g, BatchBuf
       for (uint32_t r = 0; r < R; ++r) {
         const uint32_t i = base + warp * R + r;
         if (i >= nfar) break;   // warp-uniform
-        const uint32_t v = w.far_v[fsel][i];
+        const uint32_t v = pick2(w.far_v, fsel)[i];
         const unsigned long long bits = w.fmask[v];
         const uint32_t* vrow = dist + (size_t)v * K + col0;
         const bool lo = (bits >> lane) & 1ull, hi = (bits >> (lane + 32)) & 1ull;
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kBB, 5) k_batch_superstep(DevGraph g, BatchBuf
           w.fmask[v] = kb;
           if (kb) {
             const uint32_t pos = atomicAdd(&ctl->fcnt[fsel ^ 1u], 1u);
-            w.far_v[fsel ^ 1u][pos] = v;
+            pick2(w.far_v, fsel ^ 1u)[pos] = v;
           }
           if (nb && atomicOr(Mn + v, nb) == 0ull) {
             const uint32_t rs = __ldg(g.ro + v);
@@ -155,9 +155,9 @@ __global__ void __launch_bounds__(kBB, 5) k_batch_superstep(DevGraph g, BatchBuf
         __syncthreads();
         const uint32_t pos0 = (uint32_t)(sm.base >> 32), eb0 = (uint32_t)sm.base;
         for (uint32_t i = tid; i < qn; i += kBB) {
-          w.fv[pn][pos0 + i] = sm.qv[i];
-          w.fr[pn][pos0 + i] = sm.qr[i];
-          w.fs[pn][pos0 + i] = eb0 + sm.qd[i];
+          pick3(w.fv, pn)[pos0 + i] = sm.qv[i];
+          pick3(w.fr, pn)[pos0 + i] = sm.qr[i];
+          pick3(w.fs, pn)[pos0 + i] = eb0 + sm.qd[i];
         }
         __syncthreads();
         if (tid == 0) sm.qn = 0;
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kBB, 5) k_batch_superstep(DevGraph g, BatchBuf
       __syncthreads();
     }
   } else if (F > 0 && e0 < e1) {
-    const uint32_t* S = w.fs[pc];
+    const uint32_t* S = pick3(w.fs, pc);
     if (tid < 32) {
       const uint32_t j = warp_search_le(S, F, e0);
       if (tid == 0) sm.j = j;
@@ -184,9 +184,9 @@ __global__ void __launch_bounds__(kBB, 5) k_batch_superstep(DevGraph g, BatchBuf
           valid = s < t1;
         }
         if (valid) {
-          const uint32_t v = w.fv[pc][idx];
+          const uint32_t v = pick3(w.fv, pc)[idx];
           sm.es[nent + tid] = s;
-          sm.eb[nent + tid] = w.fr[pc][idx];
+          sm.eb[nent + tid] = pick3(w.fr, pc)[idx];
           sm.ev[nent + tid] = v;
           sm.em[nent + tid] = Mc[v];
         }
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(kBB, 5) k_batch_superstep(DevGraph g, BatchBuf
                 const unsigned long long fb = (unsigned long long)flo | ((unsigned long long)fhi << 32);
                 if (fb && atomicOr(w.fmask + vi[u], fb) == 0ull) {
                   const uint32_t pos = atomicAdd(&ctl->fcnt[fsel], 1u);
-                  w.far_v[fsel][pos] = vi[u];
+                  pick2(w.far_v, fsel)[pos] = vi[u];
                 }
               }
             }
@@ -293,9 +293,9 @@ __global__ void __launch_bounds__(kBB, 5) k_batch_superstep(DevGraph g, BatchBuf
         __syncthreads();
         const uint32_t pos0 = (uint32_t)(sm.base >> 32), eb0 = (uint32_t)sm.base;
         for (uint32_t i = tid; i < qn; i += kBB) {
-          w.fv[pn][pos0 + i] = sm.qv[i];
-          w.fr[pn][pos0 + i] = sm.qr[i];
-          w.fs[pn][pos0 + i] = eb0 + sm.qd[i];
+          pick3(w.fv, pn)[pos0 + i] = sm.qv[i];
+          pick3(w.fr, pn)[pos0 + i] = sm.qr[i];
+          pick3(w.fs, pn)[pos0 + i] = eb0 + sm.qd[i];
         }
         __syncthreads();
         if (tid == 0) sm.qn = 0;
@@ -516,8 +516,10 @@ gg_status batch_run(gg_graph* g, const uint32_t* srcs, uint32_t k, uint32_t* dis
       1, std::min<unsigned long long>((count / 4 + 255) / 256, (unsigned long long)device_info().num_sms * 8));
   k_batch_fill<<<fb, 256, 0, s>>>(dist, count);
   GG_CK(cudaGetLastError());
-  // near-far buckets for the batch: explicit delta, else the graph's default
-  const uint32_t delta = o.delta == GG_DELTA_NONE ? kInf : (o.delta ? o.delta : g->default_delta);
+  // near-far buckets for the batch only on request: a vertex whose sources sit
+  // in different buckets is re-expanded once per bucket, which on the measured
+  // RMAT workloads cost far more edge scans than the buckets saved
+  const uint32_t delta = (o.delta == GG_DELTA_NONE || o.delta == 0) ? kInf : o.delta;
   const unsigned long long cap = delta == kInf ? (unsigned long long)g->n + 2 : 4ull * g->n + 16;
   const uint32_t max_iter = o.max_iterations ? o.max_iterations : (cap >= 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)cap);
   for (uint32_t col0 = 0; col0 < k; col0 += 64) {

@@ -102,6 +102,13 @@ struct Frontier {
 // L2-coherent load (bypasses L1): used for values other CTAs update with atomics.
 __device__ __forceinline__ uint32_t ld_cg(const uint32_t* p) { return __ldcg(p); }
 
+// Element i of a small kernel-parameter array without dynamic indexing
+// (which would copy the whole parameter struct to local memory).
+template <class T>
+__device__ __forceinline__ T pick2(const T (&a)[2], uint32_t i) { return i ? a[1] : a[0]; }
+template <class T>
+__device__ __forceinline__ T pick3(const T (&a)[3], uint32_t i) { return i == 0 ? a[0] : (i == 1 ? a[1] : a[2]); }
+
 // One edge as {col, weight} from either edge encoding.
 template <bool PK>
 __device__ __forceinline__ uint2 load_edge(const void* base, uint32_t e, uint32_t wbits) {
