@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
   const unsigned long long cmask = (1ull << a.logcap) - 1;
   unsigned long long my_pos = 0;
   bool have = false;
-  uint32_t backoff = 32;
+  uint32_t backoff = 32, idle_rounds = 0;
   unsigned long long pops = 0, edges = 0;
   bool ovf = false;
   for (;;) {
@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
     const unsigned gm = __ballot_sync(0xFFFFFFFFu, got);
     if (gm) {
       backoff = 32;
+      idle_rounds = 0;
       uint32_t deg = 0, rs = 0, du = 0;
       if (got) {
         rs = __ldg(a.g.ro + v);
@@ -238,7 +239,15 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
       if (lane == 0) atomicAdd(&ctl->pending, (unsigned long long)(-(long long)__popc(gm)));
       if (ld_volatile_u32(&ctl->abort)) break;
     } else {
-      // idle: stop, start or join a far-pile split, or back off
+      // idle: re-poll the own reserved slots (distinct lines) most of the
+      // time; only every 8th idle round read the shared state to stop, start
+      // or join a far-pile split -- thousands of idle warps polling the same
+      // counters would otherwise serialise the working warps' atomics on them
+      if ((++idle_rounds & 7u) != 0u) {
+        __nanosleep(backoff);
+        backoff = min(backoff * 2, 1024u);
+        continue;
+      }
       int act = 0;   // 0 back off, 1 stop, 2 split work
       if (lane == 0) {
         if (ld_volatile_u32(&ctl->abort)) {
