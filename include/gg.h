@@ -102,7 +102,9 @@ typedef enum { GG_DIR_AUTO = 0, GG_DIR_PUSH = 1, GG_DIR_PULL = 2 } gg_direction;
 typedef enum {
     GG_LB_AUTO = 0,        /* library choice (merge-path)                                */
     GG_LB_MERGE_PATH = 1,  /* equal edge ranges per CTA over the frontier's degree scan  */
-    GG_LB_BINS = 2         /* thread / warp / CTA per vertex by degree thresholds        */
+    GG_LB_BINS = 2,        /* thread / warp / CTA per vertex by degree thresholds        */
+    GG_LB_WARP = 3         /* equal edge ranges per warp, streamed 32 edges at a time,   */
+                           /* with no CTA barriers (push only; pull uses merge-path)     */
 } gg_lb_mode;
 
 typedef struct {

@@ -20,7 +20,7 @@ import numpy as np
 __all__ = [
     "GGError", "GG_INF", "GG_DEVICE_PTRS", "GG_SYMMETRIC", "GG_NO_VALIDATE",
     "GG_POLICY_BSP_GRAPH", "GG_POLICY_ASYNC_PERSISTENT", "GG_POLICY_BSP_HOST", "GG_POLICY_BSP_PERSISTENT",
-    "GG_DIR_AUTO", "GG_DIR_PUSH", "GG_DIR_PULL", "GG_LB_AUTO", "GG_LB_MERGE_PATH", "GG_LB_BINS", "GG_DELTA_NONE",
+    "GG_DIR_AUTO", "GG_DIR_PUSH", "GG_DIR_PULL", "GG_LB_AUTO", "GG_LB_MERGE_PATH", "GG_LB_BINS", "GG_LB_WARP", "GG_DELTA_NONE",
     "gg_graph_create_csr", "gg_graph_destroy", "gg_graph_info", "gg_graph_check", "gg_sssp", "gg_sssp_ex",
     "gg_sssp_batch", "gg_sssp_multi", "Server",
     "gg_status_string", "gg_last_error", "gg_abi_version", "gg_sssp_noalloc", "GG_NOALLOC_MAX_VERTICES",
@@ -36,7 +36,7 @@ GG_INF = 0xFFFFFFFF
 GG_DEVICE_PTRS, GG_SYMMETRIC, GG_NO_VALIDATE, GG_NO_PACK = 0x1, 0x2, 0x4, 0x8
 GG_POLICY_BSP_GRAPH, GG_POLICY_ASYNC_PERSISTENT, GG_POLICY_BSP_HOST, GG_POLICY_BSP_PERSISTENT = 0, 1, 2, 3
 GG_DIR_AUTO, GG_DIR_PUSH, GG_DIR_PULL = 0, 1, 2
-GG_LB_AUTO, GG_LB_MERGE_PATH, GG_LB_BINS = 0, 1, 2
+GG_LB_AUTO, GG_LB_MERGE_PATH, GG_LB_BINS, GG_LB_WARP = 0, 1, 2, 3
 GG_DELTA_NONE = 0xFFFFFFFF
 
 STATUS = {0: "GG_OK", 1: "GG_ERR_INVALID_ARG", 2: "GG_ERR_OUT_OF_MEMORY", 3: "GG_ERR_CUDA",

@@ -30,10 +30,26 @@
 #ifndef GG_EPT
 #define GG_EPT 4   // edges per thread per tile of the superstep kernels
 #endif
+#ifndef GG_WU
+#define GG_WU 2    // 32-edge chunks per step of the warp-streaming advance
+#endif
+#ifndef GG_WARP_MINB
+#define GG_WARP_MINB 6   // resident CTAs per SM the warp-streaming kernels are compiled for
+#endif
 
 namespace gg {
 
 namespace {
+
+// push load-balancing schemes (template argument of the superstep kernels)
+constexpr int LB_TILE = 0;   // merge-path tiles of BLOCK*EPT edges per CTA
+constexpr int LB_BINS = 1;   // degree bins: thread / warp / CTA per vertex
+constexpr int LB_WARP = 2;   // warp streaming over equal edge shares
+
+// resident CTAs per SM each superstep kernel is register-limited to
+constexpr int superstep_min_blocks(int lb, int ept) {
+  return lb == LB_WARP ? GG_WARP_MINB : ept == 2 ? 8 : ept == 4 ? 6 : 4;
+}
 
 template <int BLOCK, int EPT>
 struct MPSmem {
@@ -415,6 +431,206 @@ __device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepA
   if (ovf) sm.ovf = 1u;
 }
 
+// Warp-streaming push advance, with no block barriers.  Every warp of the
+// grid takes an equal contiguous share of the frontier's edge coordinates and
+// walks it in chunks of 32 edges, up to WU chunks per step.  The frontier
+// entries covering the current chunks sit in a sliding window of 32 entries,
+// one per lane (first coordinate, row start, distance); a lane finds its
+// edge's entry with a 5-step shuffle search over the window.  Improved
+// vertices pass the filter's dedup into a per-warp shared-memory queue that is
+// appended to the next frontier with one 64-bit atomicAdd per flush (queue
+// position and edge-prefix base), like the CTA queue of the tile advance.
+template <int BLOCK, int EPT, bool PK>
+__device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t F, uint32_t Etot,
+                                             const uint32_t* __restrict__ S, const uint32_t* __restrict__ R,
+                                             const uint32_t* __restrict__ V, uint32_t* __restrict__ dist,
+                                             uint32_t* __restrict__ bm_cur, const FilterOut& fo) {
+  constexpr uint32_t NW = BLOCK / 32;
+  constexpr uint32_t QW = 128;   // per-warp queue slots
+  constexpr int WU = GG_WU;      // chunks of 32 edges per step
+  static_assert(NW * QW <= (uint32_t)MPSmem<BLOCK, EPT>::ECAP, "per-warp queues fit the shared arrays");
+  const unsigned FULL = 0xFFFFFFFFu;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t* qv = sm.qv + warp * QW;   // near queue: vertex, row start, degree (then its prefix)
+  uint32_t* qr = sm.qr + warp * QW;
+  uint32_t* qd = sm.qd + warp * QW;
+  uint32_t* fq = sm.es + warp * QW;   // far queue (the entry arrays are unused here)
+  uint32_t qn = 0, fn = 0;            // warp-uniform queue lengths
+  uint32_t fmin = kInf;
+  bool ovf = false;
+  const void* __restrict__ edges = a.g.edges;
+  const uint32_t wbits = a.g.wbits;
+  const unsigned long long W = (unsigned long long)gridDim.x * NW;
+  const unsigned long long gw = (unsigned long long)blockIdx.x * NW + warp;
+  const uint32_t w0 = (uint32_t)((Etot * gw) / W), w1 = (uint32_t)((Etot * (gw + 1)) / W);
+
+  auto flush_near = [&]() {
+    __syncwarp();
+    uint32_t run = 0;
+    for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      uint32_t d = 0;
+      if (i < qn) {
+        if (!fo.sinks) {   // row read deferred to here
+          const uint32_t v = qv[i];
+          const uint32_t rs = __ldg(fo.ro + v);
+          d = __ldg(fo.ro + v + 1) - rs;
+          qr[i] = rs;
+        } else {
+          d = qd[i];
+        }
+      }
+      uint32_t x = d;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= (uint32_t)o) x += y;
+      }
+      if (i < qn) qd[i] = run + x - d;
+      run += __shfl_sync(FULL, x, 31);
+    }
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(fo.cnt_next, ((unsigned long long)qn << 32) | run);
+    b = __shfl_sync(FULL, b, 0);
+    __syncwarp();
+    const uint32_t pos0 = (uint32_t)(b >> 32), eb0 = (uint32_t)b;
+    for (uint32_t i = lane; i < qn; i += 32) {
+      fo.nfv[pos0 + i] = qv[i];
+      fo.nfr[pos0 + i] = qr[i];
+      fo.nfs[pos0 + i] = eb0 + qd[i];
+    }
+    qn = 0;
+    __syncwarp();
+  };
+  auto flush_far = [&]() {
+    __syncwarp();
+    uint32_t b = 0;
+    if (lane == 0) {
+      b = atomicAdd(fo.far_cnt, fn);
+      if (fo.far_add) atomicAdd(fo.far_add, fn);
+    }
+    b = __shfl_sync(FULL, b, 0);
+    for (uint32_t i = lane; i < fn; i += 32) fo.far[b + i] = fq[i];
+    fn = 0;
+    __syncwarp();
+  };
+
+  if (w0 < w1) {   // warp-uniform
+    uint32_t j = warp_search_le(S, F, w0);
+    uint32_t ws = 0, wr = 0, wd = 0, wend = 0;
+    auto load_window = [&]() {
+      const uint32_t idx = j + lane;
+      ws = 0xFFFFFFFFu;
+      if (idx < F) {
+        ws = S[idx];
+        wr = R[idx];
+        const uint32_t v = V[idx];
+        wd = ld_cg(dist + v);
+        bm_cur[v >> 5] = 0u;   // the current bitmap is not read in push: clear as we go
+      }
+      wend = j + 32 < F ? S[j + 32] : Etot;   // first coordinate past the window
+    };
+    load_window();
+    for (uint32_t b = w0; b < w1;) {
+      // slide until the window holds chunk [b, b+32): S[j] <= b and the
+      // chunk's last coordinate is below wend (at most two slides)
+      for (int guard = 0; guard < 4 && min(b + 31, w1 - 1) >= wend; ++guard) {
+        const unsigned le = __ballot_sync(FULL, ws <= b);
+        if (le == 0u) break;   // cannot happen while S[j] <= b holds
+        const uint32_t adv = (le == FULL && wend <= b) ? 32u : 31u - (uint32_t)__clz(le);
+        j += adv;
+        load_window();
+      }
+      // chunks [b + 32u, b + 32u + 32) that the window covers
+      int nc = 1;
+#pragma unroll
+      for (int u = 1; u < WU; ++u)
+        if (nc == u && b + 32u * u < w1 && min(b + 32u * u + 31u, w1 - 1) < wend) nc = u + 1;
+      uint2 ed[WU];
+      uint32_t nd[WU], cur[WU];
+      bool act[WU];
+#pragma unroll
+      for (int u = 0; u < WU; ++u) {
+        const uint32_t g = b + 32u * u + lane;
+        act[u] = u < nc && g < w1;
+        uint32_t k = 0;
+#pragma unroll
+        for (int step = 16; step; step >>= 1) {
+          const uint32_t sv = __shfl_sync(FULL, ws, k + step);
+          if (sv <= g) k += step;
+        }
+        const uint32_t ks = __shfl_sync(FULL, ws, k);
+        const uint32_t kr = __shfl_sync(FULL, wr, k);
+        const uint32_t kd = __shfl_sync(FULL, wd, k);
+        const uint32_t kn = __shfl_sync(FULL, ws, (k + 1) & 31u);
+        // the entry's range [ks, ke) holds g whenever S increases strictly; the
+        // test keeps every edge read inside the entry's row regardless
+        const uint32_t ke = k == 31 ? wend : kn;
+        act[u] = act[u] && ks <= g && g < ke;
+        nd[u] = kd;
+        if (act[u]) ed[u] = load_edge<PK>(edges, kr + (g - ks), wbits);
+      }
+#pragma unroll
+      for (int u = 0; u < WU; ++u) {
+        if (act[u]) {
+          nd[u] = add_sat(nd[u], ed[u].y, ovf);
+          cur[u] = ld_cg(dist + ed[u].x);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < WU; ++u) {
+        bool near = false, far = false;
+        uint32_t rs = 0, deg = 0;
+        const uint32_t v = ed[u].x;
+        if (act[u] && nd[u] < cur[u]) {
+          // dist[v] <= nd < cur after the atomic: v improved this superstep
+          atomicMin(dist + v, nd[u]);
+          bool ok = true;
+          if (fo.sinks) {
+            rs = __ldg(fo.ro + v);
+            deg = __ldg(fo.ro + v + 1) - rs;
+            ok = deg > 0;
+          }
+          if (ok) {
+            const uint32_t bit = 1u << (v & 31);
+            if (nd[u] < fo.t_cur) {
+              near = !(atomicOr(fo.bm_next + (v >> 5), bit) & bit);
+            } else {
+              fmin = min(fmin, nd[u]);
+              far = !(atomicOr(fo.bm_far + (v >> 5), bit) & bit);
+            }
+          }
+        }
+        const unsigned nb = __ballot_sync(FULL, near);
+        if (nb) {
+          if (near) {
+            const uint32_t off = qn + __popc(nb & lt);
+            qv[off] = v;
+            qr[off] = rs;
+            qd[off] = deg;
+          }
+          qn += __popc(nb);
+          if (qn > QW - 32) flush_near();
+        }
+        const unsigned fb = __ballot_sync(FULL, far);
+        if (fb) {
+          if (far) fq[fn + __popc(fb & lt)] = v;
+          fn += __popc(fb);
+          if (fn > QW - 32) flush_far();
+        }
+      }
+      b += 32u * nc;
+    }
+    if (qn) flush_near();
+    if (fn) flush_far();
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) fmin = min(fmin, __shfl_xor_sync(FULL, fmin, o));
+  if (lane == 0 && fmin != kInf) atomicMin(&sm.fmin, fmin);
+  if (__any_sync(FULL, ovf) && lane == 0) sm.ovf = 1u;
+}
+
 // Split step of the near-far frontier, run when the near frontier is empty:
 // every far-pile vertex v is re-examined against the raised threshold.
 //   dist[v] <  t_prev  it was improved below the old threshold after it was
@@ -548,11 +764,11 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
   }
 }
 
-// One superstep; BINS selects the degree-binned push advance instead of the
-// merge-path one (pull is the same merge-path sweep in both); a split step
+// One superstep; LB selects the push advance (merge-path tiles, degree bins
+// or warp streaming) (pull is the same merge-path sweep in both); a split step
 // refills the near frontier from the far pile.
-template <int BLOCK, int EPT, bool BINS, bool PK>
-__global__ void __launch_bounds__(BLOCK, EPT == 2 ? 8 : EPT == 4 ? 6 : 4) k_superstep(StepArgs a, cudaGraphConditionalHandle cond,
+template <int BLOCK, int EPT, int LB, bool PK>
+__global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_superstep(StepArgs a, cudaGraphConditionalHandle cond,
                                                                        int use_cond) {
   extern __shared__ __align__(16) unsigned char smraw[];
   MPSmem<BLOCK, EPT>& sm = *reinterpret_cast<MPSmem<BLOCK, EPT>*>(smraw);
@@ -584,9 +800,11 @@ __global__ void __launch_bounds__(BLOCK, EPT == 2 ? 8 : EPT == 4 ? 6 : 4) k_supe
     far_split(sm, a, fo, dist, a.fr.far[fp], ctl->far_cnt[fp], ctl->t_prev);
   } else if (f > 0) {
     if (mode == MODE_PUSH) {
-      if (BINS)
+      if (LB == LB_BINS)
         bins_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fv[p], a.fr.fr[p], a.fr.fs[p], dist, bm_cur, fo,
                                      ctl->warp_thr, ctl->cta_thr);
+      else if (LB == LB_WARP)
+        warp_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], dist, bm_cur, fo);
       else
         mp_advance<BLOCK, EPT, false, PK>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], a.g.edges, dist,
                                           bm_cur, fo);
@@ -635,8 +853,8 @@ __device__ __forceinline__ void grid_barrier(Ctl* ctl, unsigned long long deadli
 // thresholds, termination) in its own registers.  Counters rotate over three
 // slots (a slot is reset two supersteps after its last reader passed a
 // barrier); the far pile rotates over three piles, one per split step.
-template <int BLOCK, int EPT, bool BINS, bool PK>
-__global__ void __launch_bounds__(BLOCK, EPT == 2 ? 8 : EPT == 4 ? 6 : 4) k_bsp_persistent(StepArgs a) {
+template <int BLOCK, int EPT, int LB, bool PK>
+__global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_bsp_persistent(StepArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   MPSmem<BLOCK, EPT>& sm = *reinterpret_cast<MPSmem<BLOCK, EPT>*>(smraw);
   Ctl* ctl = a.ctl;
@@ -681,9 +899,11 @@ __global__ void __launch_bounds__(BLOCK, EPT == 2 ? 8 : EPT == 4 ? 6 : 4) k_bsp_
       far_split(sm, a, fo, dist, a.fr.far[pile], nfar, t_prev);
     } else if (f > 0) {
       if (mode == MODE_PUSH) {
-        if (BINS)
+        if (LB == LB_BINS)
           bins_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fv[p], a.fr.fr[p], a.fr.fs[p], dist, bm_cur, fo,
                                        ctl->warp_thr, ctl->cta_thr);
+        else if (LB == LB_WARP)
+          warp_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], dist, bm_cur, fo);
         else
           mp_advance<BLOCK, EPT, false, PK>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], a.g.edges, dist,
                                             bm_cur, fo);
@@ -863,14 +1083,16 @@ __global__ void k_init_tail(StepArgs a, RunParams rp) {
 
 constexpr int kBlock = 256;
 constexpr int kEpt = GG_EPT;
-constexpr int kVariants = 4;   // bit 0: degree-binned push (else merge-path); bit 1: packed edges
+constexpr int kVariants = 6;   // 2 * load balance (tiles, bins, warp streaming) + packed edges
 
 void* superstep_fn(int variant) {
   switch (variant) {
-    case 1: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, true, false>);
-    case 2: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, false, true>);
-    case 3: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, true, true>);
-    default: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, false, false>);
+    case 1: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, LB_TILE, true>);
+    case 2: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, LB_BINS, false>);
+    case 3: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, LB_BINS, true>);
+    case 4: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, LB_WARP, false>);
+    case 5: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, LB_WARP, true>);
+    default: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, LB_TILE, false>);
   }
 }
 
@@ -878,16 +1100,18 @@ size_t superstep_smem(int) { return sizeof(MPSmem<kBlock, kEpt>); }
 
 void* persistent_fn(int variant) {
   switch (variant) {
-    case 1: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, true, false>);
-    case 2: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, false, true>);
-    case 3: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, true, true>);
-    default: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, false, false>);
+    case 1: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, LB_TILE, true>);
+    case 2: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, LB_BINS, false>);
+    case 3: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, LB_BINS, true>);
+    case 4: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, LB_WARP, false>);
+    case 5: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, LB_WARP, true>);
+    default: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, LB_TILE, false>);
   }
 }
 
 // co-resident grid of the persistent kernel (cooperative launch limit)
 int persistent_grid(int variant) {
-  static int cached[4] = {0, 0, 0, 0};
+  static int cached[kVariants] = {};
   if (cached[variant]) return cached[variant];
   const DeviceInfo di = device_info();
   int per_sm = 0;
@@ -929,7 +1153,7 @@ gg_status ensure_workspace(gg_graph* g) {
 }
 
 int superstep_grid(int variant) {
-  static int cached[kVariants] = {0, 0, 0, 0};
+  static int cached[kVariants] = {};
   if (cached[variant]) return cached[variant];
   const DeviceInfo di = device_info();
   int per_sm = 0;
@@ -980,7 +1204,8 @@ gg_status build_graph_exec(gg_graph* g, int variant) {
 gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s) {
   gg_status st = ensure_workspace(g);
   if (st != GG_OK) return st;
-  const int variant = (o.lb_mode == GG_LB_BINS ? 1 : 0) | (g->dg.packed ? 2 : 0);
+  const int lb = o.lb_mode == GG_LB_BINS ? LB_BINS : o.lb_mode == GG_LB_WARP ? LB_WARP : LB_TILE;
+  const int variant = 2 * lb + (g->dg.packed ? 1 : 0);
   BspWorkspace& w = g->bsp;
   RunParams rp;
   rp.src = src;

@@ -37,9 +37,9 @@ struct BspWorkspace {
   size_t bytes = 0;
   // CUDA graph with a conditional WHILE node around one superstep kernel,
   // one per load-balance variant.
-  cudaGraph_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};
-  int grid[4] = {0, 0, 0, 0};
+  cudaGraph_t graph[6] = {};
+  cudaGraphExec_t exec[6] = {};
+  int grid[6] = {};
 };
 
 // Workspace of the asynchronous persistent path.

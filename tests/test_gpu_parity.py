@@ -29,14 +29,15 @@ def gg():
 
 POLICIES = {"graph": 0, "async": 1, "host": 2, "persistent": 3}
 DIRS = {"auto": 0, "push": 1, "pull": 2}
-LB = {"mp": 1, "bins": 2}
+LB = {"mp": 1, "bins": 2, "warp": 3}
 NONE = 0xFFFFFFFF
 # (policy, direction, load balance, near-far delta; 0 = the graph's default)
 MODES = [("graph", "auto"), ("graph", "push"), ("graph", "pull"), ("host", "auto"), ("host", "pull"),
          ("async", "auto"), ("graph", "push", "bins"), ("host", "auto", "bins"),
          ("graph", "push", "mp", NONE), ("graph", "auto", "mp", 1), ("graph", "push", "bins", 3),
          ("persistent", "push"), ("persistent", "auto", "mp", NONE), ("persistent", "pull"),
-         ("persistent", "push", "bins", 5)]
+         ("persistent", "push", "bins", 5), ("graph", "push", "warp"), ("host", "auto", "warp", 4),
+         ("persistent", "push", "warp", NONE), ("graph", "push", "warp", 2)]
 
 
 def run(g, src, policy="graph", direction="auto", lb="mp", delta=0, **kw):
@@ -164,6 +165,8 @@ def test_rmat20_config_push_pull():
     np.testing.assert_array_equal(got, ref)
     got, _ = run(g, src, "graph", "auto", "bins")
     np.testing.assert_array_equal(got, ref)
+    got, _ = run(g, src, "graph", "push", "warp")
+    np.testing.assert_array_equal(got, ref)
     g.close()
 
 
@@ -171,7 +174,7 @@ def test_rmat20_config_push_pull():
 def test_full_size_configs_against_golden(name):
     ro, col, w, src = graphgen.workload(name)
     g = gg().Graph(ro, col, w, symmetric=True)
-    modes = [("graph", "auto"), ("async", "auto"), ("persistent", "push")]
+    modes = [("graph", "auto"), ("async", "auto"), ("persistent", "push"), ("graph", "push", "warp")]
     for mode in modes:
         got, st = run(g, src, *mode)
         assert sha(got) == GOLD[name]["dist_sha256"], f"{name} {mode}"
