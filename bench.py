@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--workload", default="rmat20")
     p.add_argument("--policy", default="graph", choices=["graph", "async", "host", "persistent"])
     p.add_argument("--direction", default="push", choices=["auto", "push", "pull"])
-    p.add_argument("--lb", default="mp", choices=["mp", "bins", "warp"])
+    p.add_argument("--lb", default="auto", choices=["auto", "mp", "bins", "warp"])
     p.add_argument("--delta", type=int, default=0, help="near-far bucket width (0 = graph default, -1 = none)")
     p.add_argument("--alpha", type=int, default=0)
     p.add_argument("--beta", type=int, default=0)
@@ -322,7 +322,7 @@ def main():
     stream = torch.cuda.current_stream()
     g = gg.Graph(ro, col, w, symmetric=True, stream=stream)
     dist_t = torch.empty(n, dtype=torch.uint32, device="cuda")
-    lb = {"mp": gg.GG_LB_MERGE_PATH, "bins": gg.GG_LB_BINS, "warp": gg.GG_LB_WARP}[args.lb]
+    lb = {"auto": gg.GG_LB_AUTO, "mp": gg.GG_LB_MERGE_PATH, "bins": gg.GG_LB_BINS, "warp": gg.GG_LB_WARP}[args.lb]
     delta = gg.GG_DELTA_NONE if args.delta < 0 else args.delta
     opts = gg.make_options(policy=policy, direction=direction, lb_mode=lb, pull_alpha=args.alpha, pull_beta=args.beta,
                            delta=delta)

@@ -100,7 +100,7 @@ typedef enum { GG_DIR_AUTO = 0, GG_DIR_PUSH = 1, GG_DIR_PULL = 2 } gg_direction;
 /* Load balancing of the push advance (Sec. IV-C: "data parallelism and load
  * balancing"). */
 typedef enum {
-    GG_LB_AUTO = 0,        /* library choice (merge-path)                                */
+    GG_LB_AUTO = 0,        /* library choice (warp streaming)                            */
     GG_LB_MERGE_PATH = 1,  /* equal edge ranges per CTA over the frontier's degree scan  */
     GG_LB_BINS = 2,        /* thread / warp / CTA per vertex by degree thresholds        */
     GG_LB_WARP = 3         /* equal edge ranges per warp, streamed 32 edges at a time,   */

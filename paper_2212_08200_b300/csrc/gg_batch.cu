@@ -62,7 +62,13 @@ constexpr int kBNW = kBB / 32;
 constexpr int kBTile = 1024;
 constexpr int kBWarpEdges = kBTile / kBNW;
 constexpr int kBCap = kBTile + 1;
-constexpr int kBU = 1;   // edges a warp relaxes concurrently
+#ifndef GG_BU
+#define GG_BU 1
+#endif
+#ifndef GG_BMINB
+#define GG_BMINB 5
+#endif
+constexpr int kBU = GG_BU;   // edges a warp relaxes concurrently
 
 struct BSmem {
   uint32_t es[kBCap], eb[kBCap], ev[kBCap];
@@ -74,7 +80,7 @@ struct BSmem {
 };
 
 template <bool PK>
-__global__ void __launch_bounds__(kBB, 5) k_batch_superstep(DevGraph g, BatchBufs w, cudaGraphConditionalHandle cond,
+__global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, BatchBufs w, cudaGraphConditionalHandle cond,
                                                          int use_cond) {
   __shared__ BSmem sm;
   BatchCtl* ctl = w.ctl;

@@ -34,7 +34,7 @@
 #define GG_WU 2    // 32-edge chunks per step of the warp-streaming advance
 #endif
 #ifndef GG_WARP_MINB
-#define GG_WARP_MINB 6   // resident CTAs per SM the warp-streaming kernels are compiled for
+#define GG_WARP_MINB 5   // resident CTAs per SM the warp-streaming kernels are compiled for
 #endif
 
 namespace gg {
@@ -1204,7 +1204,8 @@ gg_status build_graph_exec(gg_graph* g, int variant) {
 gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s) {
   gg_status st = ensure_workspace(g);
   if (st != GG_OK) return st;
-  const int lb = o.lb_mode == GG_LB_BINS ? LB_BINS : o.lb_mode == GG_LB_WARP ? LB_WARP : LB_TILE;
+  // automatic choice: warp streaming (measured faster than merge-path tiles on RMAT, equal on grids)
+  const int lb = o.lb_mode == GG_LB_BINS ? LB_BINS : o.lb_mode == GG_LB_MERGE_PATH ? LB_TILE : LB_WARP;
   const int variant = 2 * lb + (g->dg.packed ? 1 : 0);
   BspWorkspace& w = g->bsp;
   RunParams rp;

@@ -1,7 +1,8 @@
 // gg_tune.cu -- autotuner for the single-source path: times candidate option
 // sets on the caller's graph and sample sources with CUDA events and returns
 // the fastest (coordinate descent over policy, bucket width, direction /
-// switch threshold and load balancing with its degree bins).
+// switch threshold and load balancing: warp streaming, merge-path tiles, or
+// degree bins with their thresholds).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -107,7 +108,14 @@ extern "C" gg_status gg_autotune(gg_graph_t g, const uint32_t* srcs, uint32_t ns
       if ((st = try_opt(o)) != GG_OK) return st;
     }
   }
-  // 4. load balancing: degree bins at a few thresholds
+  // 4. load balancing: merge-path tiles, or degree bins at a few thresholds
+  //    (the default is warp streaming)
+  {
+    const gg_options base = cur;
+    gg_options o = base;
+    o.lb_mode = GG_LB_MERGE_PATH;
+    if ((st = try_opt(o)) != GG_OK) return st;
+  }
   {
     const gg_options base = cur;
     for (uint32_t w : {8u, 32u}) {
