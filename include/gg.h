@@ -236,8 +236,10 @@ gg_status gg_sssp_batch(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t
                         cudaStream_t stream);
 
 /* As gg_sssp_batch with options: max_iterations, stats (summed over the
- * 64-source groups; setting stats synchronises the stream) and delta are
- * honoured; policy, direction and load-balance fields are ignored.  delta
+ * 64-source groups; setting stats synchronises the stream), delta and the
+ * policy GG_POLICY_BSP_HOST (supersteps launched one by one from the host,
+ * synchronising after each; every other policy runs the CUDA-graph loop) are
+ * honoured; direction and load-balance fields are ignored.  delta
  * 0 or GG_DELTA_NONE runs the plain frontier loop (the default: buckets make
  * a vertex whose sources fall in different buckets expand once per bucket);
  * another value parks (vertex, source) pairs at or above the threshold in

@@ -62,13 +62,9 @@ constexpr int kBNW = kBB / 32;
 constexpr int kBTile = 1024;
 constexpr int kBWarpEdges = kBTile / kBNW;
 constexpr int kBCap = kBTile + 1;
-#ifndef GG_BU
-#define GG_BU 1
-#endif
 #ifndef GG_BMINB
-#define GG_BMINB 5
+#define GG_BMINB 4   // resident CTAs per SM the batch superstep is compiled for (64 registers)
 #endif
-constexpr int kBU = GG_BU;   // edges a warp relaxes concurrently
 
 struct BSmem {
   uint32_t es[kBCap], eb[kBCap], ev[kBCap];
@@ -200,9 +196,15 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
         nent += (uint32_t)cnt;
         if (cnt < kBB) break;
       }
-      // each warp walks a contiguous run of the tile's edges, one edge at a
-      // time across its 32 lanes x 2 source columns
+      // each warp walks a contiguous run of the tile's edges, 32 at a time:
+      // the lanes load 32 edges, then the warp relaxes them four at a time,
+      // one edge per 8-lane group.  Lane l8 of a group holds sources
+      // l8 + 8q (q = 0..7) of the 64-source group, so for each q the group
+      // reads one 32-byte sector of a row, and the eight row reads of a lane
+      // (and the four edges of the warp) are in flight together.
       const uint32_t wbeg = t0 + warp * kBWarpEdges;
+      const uint32_t g4 = lane >> 3, l8 = lane & 7;
+      const bool buckets = T != kInf;   // uniform
       for (uint32_t r = 0; r < (uint32_t)kBWarpEdges; r += 32) {
         const uint32_t gidx = wbeg + r + lane;
         const bool valid = gidx < t1;
@@ -215,76 +217,88 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
         }
         const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
         if (!vm) break;
-        uint32_t cur_j = 0xFFFFFFFFu, du_lo = kInf, du_hi = kInf;
-        bool act_lo = false, act_hi = false;
         const int nvalid = __popc(vm);   // valid edges are a prefix of the lanes
-        // four edges at a time: their row reads and relaxations are in flight together
-        for (int i0 = 0; i0 < nvalid; i0 += kBU) {
-          uint32_t vi[kBU], nlo[kBU], nhi[kBU], clo[kBU], chi[kBU];
-          bool alo[kBU], ahi[kBU];
+        uint32_t cur_j = 0xFFFFFFFFu, amask = 0u;
+        uint32_t du[8];
 #pragma unroll
-          for (int u = 0; u < kBU; ++u) {
-            const int i = min(i0 + u, nvalid - 1);
-            const uint32_t ji = __shfl_sync(0xFFFFFFFFu, jj, i);
-            vi[u] = __shfl_sync(0xFFFFFFFFu, vv, i);
-            const uint32_t wi = __shfl_sync(0xFFFFFFFFu, ww, i);
-            if (ji != cur_j) {
-              cur_j = ji;
-              const uint32_t uu = sm.ev[ji];
-              const unsigned long long msk = sm.em[ji];
-              const uint32_t* urow = dist + (size_t)uu * K + col0;
-              act_lo = (msk >> lane) & 1ull;
-              act_hi = (msk >> (lane + 32)) & 1ull;
-              du_lo = act_lo ? ld_cg(urow + lane) : kInf;
-              du_hi = act_hi ? ld_cg(urow + lane + 32) : kInf;
+        for (int q = 0; q < 8; ++q) du[q] = kInf;
+        for (int i0 = 0; i0 < nvalid; i0 += 4) {
+          const int i = i0 + (int)g4;
+          const bool live = i < nvalid;
+          const int isrc = live ? i : nvalid - 1;
+          const uint32_t ji = __shfl_sync(0xFFFFFFFFu, jj, isrc);
+          const uint32_t vi = __shfl_sync(0xFFFFFFFFu, vv, isrc);
+          const uint32_t wi = __shfl_sync(0xFFFFFFFFu, ww, isrc);
+          if (live && ji != cur_j) {   // uniform within the group
+            cur_j = ji;
+            const uint32_t uu = sm.ev[ji];
+            const unsigned long long msk = sm.em[ji] >> l8;
+            const uint32_t* urow = dist + (size_t)uu * K + col0 + l8;
+            amask = 0u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const bool on = (msk >> (8 * q)) & 1ull;
+              amask |= (on ? 1u : 0u) << q;
+              du[q] = on ? ld_cg(urow + 8 * q) : kInf;
             }
-            const bool live = i0 + u < nvalid;
-            alo[u] = live && act_lo;
-            ahi[u] = live && act_hi;
-            nlo[u] = alo[u] ? add_sat(du_lo, wi, ovf) : kInf;
-            nhi[u] = ahi[u] ? add_sat(du_hi, wi, ovf) : kInf;
           }
+          const uint32_t am = live ? amask : 0u;
+          uint32_t* vrow = dist + (size_t)vi * K + col0 + l8;
+          uint32_t cv[8];
 #pragma unroll
-          for (int u = 0; u < kBU; ++u) {
-            const uint32_t* vrow = dist + (size_t)vi[u] * K + col0;
-            clo[u] = alo[u] ? ld_cg(vrow + lane) : 0u;
-            chi[u] = ahi[u] ? ld_cg(vrow + lane + 32) : 0u;
+          for (int q = 0; q < 8; ++q) cv[q] = ((am >> q) & 1u) ? ld_cg(vrow + 8 * q) : 0u;
+          uint32_t near = 0u, far = 0u, fm = kInf;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if ((am >> q) & 1u) {
+              const uint32_t nd = add_sat(du[q], wi, ovf);
+              if (nd < cv[q]) {
+                atomicMin(vrow + 8 * q, nd);
+                // near bits (new distance below the threshold) join the next
+                // frontier's mask; the others are parked in the far mask
+                if (nd < T) {
+                  near |= 1u << q;
+                } else {
+                  far |= 1u << q;
+                  fm = min(fm, nd);
+                }
+              }
+            }
           }
+          // gather the group's 64-bit masks: ballot q holds source l8 + 8q of every group
+          unsigned long long nmask = 0ull, fmask = 0ull;
 #pragma unroll
-          for (int u = 0; u < kBU; ++u) {
-            uint32_t* vrow = dist + (size_t)vi[u] * K + col0;
-            const bool imp_lo = alo[u] && nlo[u] < clo[u];
-            const bool imp_hi = ahi[u] && nhi[u] < chi[u];
-            if (imp_lo) atomicMin(vrow + lane, nlo[u]);
-            if (imp_hi) atomicMin(vrow + lane + 32, nhi[u]);
-            // near bits (new distance below the threshold) join the next
-            // frontier's mask; the others are parked in the far mask
-            const bool far_lo = imp_lo && nlo[u] >= T, far_hi = imp_hi && nhi[u] >= T;
-            const unsigned blo = __ballot_sync(0xFFFFFFFFu, imp_lo && !far_lo);
-            const unsigned bhi = __ballot_sync(0xFFFFFFFFu, imp_hi && !far_hi);
-            const unsigned flo = __ballot_sync(0xFFFFFFFFu, far_lo);
-            const unsigned fhi = __ballot_sync(0xFFFFFFFFu, far_hi);
-            if (flo | fhi) {
-              uint32_t fm = min(far_lo ? nlo[u] : kInf, far_hi ? nhi[u] : kInf);
+          for (int q = 0; q < 8; ++q) {
+            const unsigned bq = __ballot_sync(0xFFFFFFFFu, (near >> q) & 1u);
+            nmask |= (unsigned long long)((bq >> (8 * g4)) & 0xFFu) << (8 * q);
+          }
+          if (buckets) {
+            const unsigned anyf = __ballot_sync(0xFFFFFFFFu, far != 0u);
+            if (anyf) {
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const unsigned bq = __ballot_sync(0xFFFFFFFFu, (far >> q) & 1u);
+                fmask |= (unsigned long long)((bq >> (8 * g4)) & 0xFFu) << (8 * q);
+              }
 #pragma unroll
               for (int o = 16; o; o >>= 1) fm = min(fm, __shfl_xor_sync(0xFFFFFFFFu, fm, o));
               if (lane == 0) atomicMin(&ctl->far_min, fm);
             }
-            if (lane == 0 && (blo | bhi | flo | fhi)) {
-              const uint32_t rs = __ldg(g.ro + vi[u]), re = __ldg(g.ro + vi[u] + 1);
-              if (re > rs) {
-                const unsigned long long bits = (unsigned long long)blo | ((unsigned long long)bhi << 32);
-                if (bits && atomicOr(Mn + vi[u], bits) == 0ull) {
-                  const uint32_t q = atomicAdd(&sm.qn, 1u);
-                  sm.qv[q] = vi[u];
-                  sm.qr[q] = rs;
-                  sm.qd[q] = re - rs;
-                }
-                const unsigned long long fb = (unsigned long long)flo | ((unsigned long long)fhi << 32);
-                if (fb && atomicOr(w.fmask + vi[u], fb) == 0ull) {
-                  const uint32_t pos = atomicAdd(&ctl->fcnt[fsel], 1u);
-                  pick2(w.far_v, fsel)[pos] = vi[u];
-                }
+          }
+          if (l8 == 0 && (nmask | fmask)) {
+            // bit 8q + l8 of a gathered mask is source l8 + 8q: already in source order
+            const unsigned long long nb = nmask, fb = fmask;
+            const uint32_t rs = __ldg(g.ro + vi), re = __ldg(g.ro + vi + 1);
+            if (re > rs) {
+              if (nb && atomicOr(Mn + vi, nb) == 0ull) {
+                const uint32_t q = atomicAdd(&sm.qn, 1u);
+                sm.qv[q] = vi;
+                sm.qr[q] = rs;
+                sm.qd[q] = re - rs;
+              }
+              if (fb && atomicOr(w.fmask + vi, fb) == 0ull) {
+                const uint32_t pos = atomicAdd(&ctl->fcnt[fsel], 1u);
+                pick2(w.far_v, fsel)[pos] = vi;
               }
             }
           }
@@ -535,7 +549,24 @@ gg_status batch_run(gg_graph* g, const uint32_t* srcs, uint32_t k, uint32_t* dis
     GG_CK(cudaMemsetAsync(w->b.fmask, 0, 8 * (size_t)g->n, s));
     k_batch_seed<<<1, 64, 0, s>>>(g->dg, w->b, w->srcs, k, col0, kg, dist, max_iter, delta);
     GG_CK(cudaGetLastError());
-    GG_CK(cudaGraphLaunch(w->exec, s));
+    if (o.policy == GG_POLICY_BSP_HOST) {
+      // supersteps launched one by one, the loop flag read back after each
+      DevGraph dg = g->dg;
+      BatchBufs b = w->b;
+      cudaGraphConditionalHandle none = 0;
+      int zero = 0;
+      void* fn = g->dg.packed ? reinterpret_cast<void*>(&k_batch_superstep<true>)
+                              : reinterpret_cast<void*>(&k_batch_superstep<false>);
+      for (uint32_t it = 0;; ++it) {
+        void* args[] = {&dg, &b, &none, &zero};
+        GG_CK(cudaLaunchKernel(fn, dim3(w->grid), dim3(kBB), args, 0, s));
+        GG_CK(cudaMemcpyAsync(&w->h_ctl->running, &w->b.ctl->running, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+        GG_CK(cudaStreamSynchronize(s));
+        if (w->h_ctl->running == 0u || it >= max_iter) break;
+      }
+    } else {
+      GG_CK(cudaGraphLaunch(w->exec, s));
+    }
     if (o.stats) {
       GG_CK(cudaMemcpyAsync(w->h_ctl, w->b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
       GG_CK(cudaStreamSynchronize(s));

@@ -24,13 +24,15 @@ def run_batch(g, srcs, **kw):
     return d.cpu().numpy(), st.as_dict()
 
 
-@pytest.mark.parametrize("k,pack,delta", [(1, True, 0), (5, False, 0), (64, True, 0), (100, False, 0),
-                                          (64, True, 1), (64, False, 25), (100, True, 0xFFFFFFFF), (5, True, 300)])
-def test_rmat16_batch_matches_oracle(k, pack, delta):
+@pytest.mark.parametrize("k,pack,delta,policy", [(1, True, 0, 0), (5, False, 0, 0), (64, True, 0, 0),
+                                                 (100, False, 0, 0), (64, True, 1, 0), (64, False, 25, 0),
+                                                 (100, True, 0xFFFFFFFF, 0), (5, True, 300, 0), (64, True, 0, 2),
+                                                 (70, False, 9, 2)])
+def test_rmat16_batch_matches_oracle(k, pack, delta, policy):
     ro, col, w, _ = graphgen.workload("rmat16")
     srcs = graphgen.sample_sources(ro, k, seed=3)
     g = gg().Graph(ro, col, w, symmetric=True, pack=pack)
-    got, st = run_batch(g, srcs, delta=delta)
+    got, st = run_batch(g, srcs, delta=delta, policy=policy)   # policy 2: host-launched supersteps
     ref = oracle.dijkstra_many(ro, col, w, srcs, threads=8)
     for s in range(k):
         np.testing.assert_array_equal(got[:, s], ref[s], err_msg=f"column {s}")
