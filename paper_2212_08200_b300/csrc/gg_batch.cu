@@ -75,7 +75,31 @@ struct BSmem {
   unsigned long long base;
 };
 
-template <bool PK>
+// Eight consecutive distances row[0..7] into d[] where bit q of `on` is set
+// (others := fill).  VEC: the row is 16-byte aligned and read as two 16-byte
+// vectors, each only when one of its four bits is set (a set bit implies the
+// whole vector lies inside the matrix: groups are 4-aligned when VEC).
+template <bool VEC>
+__device__ __forceinline__ void load_row8(const uint32_t* row, uint32_t on, uint32_t (&d)[8], uint32_t fill) {
+  if (VEC) {
+    uint4 a = make_uint4(fill, fill, fill, fill), b = a;
+    if (on & 0x0Fu) a = __ldcg(reinterpret_cast<const uint4*>(row));
+    if (on & 0xF0u) b = __ldcg(reinterpret_cast<const uint4*>(row) + 1);
+    d[0] = (on & 1u) ? a.x : fill;
+    d[1] = (on & 2u) ? a.y : fill;
+    d[2] = (on & 4u) ? a.z : fill;
+    d[3] = (on & 8u) ? a.w : fill;
+    d[4] = (on & 16u) ? b.x : fill;
+    d[5] = (on & 32u) ? b.y : fill;
+    d[6] = (on & 64u) ? b.z : fill;
+    d[7] = (on & 128u) ? b.w : fill;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) d[q] = ((on >> q) & 1u) ? ld_cg(row + q) : fill;
+  }
+}
+
+template <bool PK, bool VEC>
 __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, BatchBufs w, cudaGraphConditionalHandle cond,
                                                          int use_cond) {
   __shared__ BSmem sm;
@@ -198,13 +222,13 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
       }
       // each warp walks a contiguous run of the tile's edges, 32 at a time:
       // the lanes load 32 edges, then the warp relaxes them four at a time,
-      // one edge per 8-lane group.  Lane l8 of a group holds sources
-      // l8 + 8q (q = 0..7) of the 64-source group, so for each q the group
-      // reads one 32-byte sector of a row, and the eight row reads of a lane
-      // (and the four edges of the warp) are in flight together.
+      // one edge per 8-lane group.  Lane l8 of a group holds the eight
+      // consecutive sources 8*l8 .. 8*l8+7 of the 64-source group: one
+      // 32-byte sector of a distance row, read as two 16-byte vectors when
+      // the matrix allows it (VEC), and the lane's byte of the group's
+      // source mask.
       const uint32_t wbeg = t0 + warp * kBWarpEdges;
       const uint32_t g4 = lane >> 3, l8 = lane & 7;
-      const bool buckets = T != kInf;   // uniform
       for (uint32_t r = 0; r < (uint32_t)kBWarpEdges; r += 32) {
         const uint32_t gidx = wbeg + r + lane;
         const bool valid = gidx < t1;
@@ -231,29 +255,20 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
           const uint32_t wi = __shfl_sync(0xFFFFFFFFu, ww, isrc);
           if (live && ji != cur_j) {   // uniform within the group
             cur_j = ji;
-            const uint32_t uu = sm.ev[ji];
-            const unsigned long long msk = sm.em[ji] >> l8;
-            const uint32_t* urow = dist + (size_t)uu * K + col0 + l8;
-            amask = 0u;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-              const bool on = (msk >> (8 * q)) & 1ull;
-              amask |= (on ? 1u : 0u) << q;
-              du[q] = on ? ld_cg(urow + 8 * q) : kInf;
-            }
+            amask = (uint32_t)(sm.em[ji] >> (8 * l8)) & 0xFFu;
+            load_row8<VEC>(dist + (size_t)sm.ev[ji] * K + col0 + 8 * l8, amask, du, kInf);
           }
           const uint32_t am = live ? amask : 0u;
-          uint32_t* vrow = dist + (size_t)vi * K + col0 + l8;
+          uint32_t* vrow = dist + (size_t)vi * K + col0 + 8 * l8;
           uint32_t cv[8];
-#pragma unroll
-          for (int q = 0; q < 8; ++q) cv[q] = ((am >> q) & 1u) ? ld_cg(vrow + 8 * q) : 0u;
+          load_row8<VEC>(vrow, am, cv, 0u);
           uint32_t near = 0u, far = 0u, fm = kInf;
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             if ((am >> q) & 1u) {
               const uint32_t nd = add_sat(du[q], wi, ovf);
               if (nd < cv[q]) {
-                atomicMin(vrow + 8 * q, nd);
+                atomicMin(vrow + q, nd);
                 // near bits (new distance below the threshold) join the next
                 // frontier's mask; the others are parked in the far mask
                 if (nd < T) {
@@ -265,38 +280,31 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
               }
             }
           }
-          // gather the group's 64-bit masks: ballot q holds source l8 + 8q of every group
-          unsigned long long nmask = 0ull, fmask = 0ull;
+          // the group's 64-bit masks: OR of the lanes' bytes over the 8-lane group
+          unsigned long long nmask = (unsigned long long)near << (8 * l8);
+          unsigned long long fmask = (unsigned long long)far << (8 * l8);
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const unsigned bq = __ballot_sync(0xFFFFFFFFu, (near >> q) & 1u);
-            nmask |= (unsigned long long)((bq >> (8 * g4)) & 0xFFu) << (8 * q);
-          }
-          if (buckets) {
+          for (int o = 1; o < 8; o <<= 1) nmask |= __shfl_xor_sync(0xFFFFFFFFu, nmask, o);
+          if (T != kInf) {   // uniform: only with buckets can anything be parked
             const unsigned anyf = __ballot_sync(0xFFFFFFFFu, far != 0u);
             if (anyf) {
 #pragma unroll
-              for (int q = 0; q < 8; ++q) {
-                const unsigned bq = __ballot_sync(0xFFFFFFFFu, (far >> q) & 1u);
-                fmask |= (unsigned long long)((bq >> (8 * g4)) & 0xFFu) << (8 * q);
-              }
+              for (int o = 1; o < 8; o <<= 1) fmask |= __shfl_xor_sync(0xFFFFFFFFu, fmask, o);
 #pragma unroll
               for (int o = 16; o; o >>= 1) fm = min(fm, __shfl_xor_sync(0xFFFFFFFFu, fm, o));
               if (lane == 0) atomicMin(&ctl->far_min, fm);
             }
           }
           if (l8 == 0 && (nmask | fmask)) {
-            // bit 8q + l8 of a gathered mask is source l8 + 8q: already in source order
-            const unsigned long long nb = nmask, fb = fmask;
             const uint32_t rs = __ldg(g.ro + vi), re = __ldg(g.ro + vi + 1);
             if (re > rs) {
-              if (nb && atomicOr(Mn + vi, nb) == 0ull) {
+              if (nmask && atomicOr(Mn + vi, nmask) == 0ull) {
                 const uint32_t q = atomicAdd(&sm.qn, 1u);
                 sm.qv[q] = vi;
                 sm.qr[q] = rs;
                 sm.qd[q] = re - rs;
               }
-              if (fb && atomicOr(w.fmask + vi, fb) == 0ull) {
+              if (fmask && atomicOr(w.fmask + vi, fmask) == 0ull) {
                 const uint32_t pos = atomicAdd(&ctl->fcnt[fsel], 1u);
                 pick2(w.far_v, fsel)[pos] = vi;
               }
@@ -445,11 +453,19 @@ struct BatchWorkspace {
   BatchBufs b{};
   uint32_t* srcs = nullptr;
   uint32_t srcs_cap = 0;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph[2] = {nullptr, nullptr};      // per row-read mode (scalar, 16-byte vectors)
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
   int grid = 0;
   BatchCtl* h_ctl = nullptr;
 };
+
+// the superstep kernel for the edge format and the row-read mode
+static void* batch_fn(bool packed, bool vec) {
+  if (packed) return vec ? reinterpret_cast<void*>(&k_batch_superstep<true, true>)
+                         : reinterpret_cast<void*>(&k_batch_superstep<true, false>);
+  return vec ? reinterpret_cast<void*>(&k_batch_superstep<false, true>)
+             : reinterpret_cast<void*>(&k_batch_superstep<false, false>);
+}
 
 static gg_status batch_ws(gg_graph* g, BatchWorkspace** out) {
   if (!g->batch) {
@@ -475,8 +491,7 @@ static gg_status batch_ws(gg_graph* g, BatchWorkspace** out) {
     w->b.ctl = reinterpret_cast<BatchCtl*>(take(sizeof(BatchCtl)));
     e = cudaMallocHost(&w->h_ctl, sizeof(BatchCtl));
     if (e != cudaSuccess) { cudaFree(p); delete w; return cuda_fail(e, "cudaMallocHost"); }
-    void* fn = g->dg.packed ? reinterpret_cast<void*>(&k_batch_superstep<true>)
-                            : reinterpret_cast<void*>(&k_batch_superstep<false>);
+    void* fn = batch_fn(g->dg.packed, false);
     int per_sm = 0;
     GG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBB, 0));
     w->grid = std::max(1, per_sm) * device_info().num_sms;
@@ -486,8 +501,8 @@ static gg_status batch_ws(gg_graph* g, BatchWorkspace** out) {
   return GG_OK;
 }
 
-static gg_status batch_exec(gg_graph* g, BatchWorkspace* w) {
-  if (w->exec) return GG_OK;
+static gg_status batch_exec(gg_graph* g, BatchWorkspace* w, bool vec) {
+  if (w->exec[vec]) return GG_OK;
   cudaGraph_t graph = nullptr;
   GG_CK(cudaGraphCreate(&graph, 0));
   cudaGraphConditionalHandle h;
@@ -504,15 +519,14 @@ static gg_status batch_exec(gg_graph* g, BatchWorkspace* w) {
   int use_cond = 1;
   void* args[] = {&dg, &b, &h, &use_cond};
   cudaKernelNodeParams kp = {};
-  kp.func = g->dg.packed ? reinterpret_cast<void*>(&k_batch_superstep<true>)
-                         : reinterpret_cast<void*>(&k_batch_superstep<false>);
+  kp.func = batch_fn(g->dg.packed, vec);
   kp.gridDim = dim3(w->grid);
   kp.blockDim = dim3(kBB);
   kp.kernelParams = args;
   cudaGraphNode_t knode;
   GG_CK(cudaGraphAddKernelNode(&knode, cp.conditional.phGraph_out[0], nullptr, 0, &kp));
-  GG_CK(cudaGraphInstantiate(&w->exec, graph, 0));
-  w->graph = graph;
+  GG_CK(cudaGraphInstantiate(&w->exec[vec], graph, 0));
+  w->graph[vec] = graph;
   return GG_OK;
 }
 
@@ -529,7 +543,9 @@ gg_status batch_run(gg_graph* g, const uint32_t* srcs, uint32_t k, uint32_t* dis
     w->srcs_cap = k;
   }
   GG_CK(cudaMemcpyAsync(w->srcs, srcs, sizeof(uint32_t) * k, cudaMemcpyHostToDevice, s));
-  st = batch_exec(g, w);
+  // 16-byte row reads need 16-byte aligned rows: k a multiple of 4 and an aligned matrix
+  const bool vec = (k % 4u) == 0u && (reinterpret_cast<uintptr_t>(dist) & 15u) == 0u;
+  st = batch_exec(g, w, vec);
   if (st != GG_OK) return st;
   const unsigned long long count = (unsigned long long)g->n * k;
   const unsigned fb = (unsigned)std::max<unsigned long long>(
@@ -555,8 +571,7 @@ gg_status batch_run(gg_graph* g, const uint32_t* srcs, uint32_t k, uint32_t* dis
       BatchBufs b = w->b;
       cudaGraphConditionalHandle none = 0;
       int zero = 0;
-      void* fn = g->dg.packed ? reinterpret_cast<void*>(&k_batch_superstep<true>)
-                              : reinterpret_cast<void*>(&k_batch_superstep<false>);
+      void* fn = batch_fn(g->dg.packed, vec);
       for (uint32_t it = 0;; ++it) {
         void* args[] = {&dg, &b, &none, &zero};
         GG_CK(cudaLaunchKernel(fn, dim3(w->grid), dim3(kBB), args, 0, s));
@@ -565,7 +580,7 @@ gg_status batch_run(gg_graph* g, const uint32_t* srcs, uint32_t k, uint32_t* dis
         if (w->h_ctl->running == 0u || it >= max_iter) break;
       }
     } else {
-      GG_CK(cudaGraphLaunch(w->exec, s));
+      GG_CK(cudaGraphLaunch(w->exec[vec], s));
     }
     if (o.stats) {
       GG_CK(cudaMemcpyAsync(w->h_ctl, w->b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
@@ -593,8 +608,10 @@ gg_status batch_status(gg_graph* g, uint32_t* ds) {
 void batch_release(gg_graph* g) {
   BatchWorkspace* w = g->batch;
   if (!w) return;
-  if (w->exec) cudaGraphExecDestroy(w->exec);
-  if (w->graph) cudaGraphDestroy(w->graph);
+  for (int i = 0; i < 2; ++i) {
+    if (w->exec[i]) cudaGraphExecDestroy(w->exec[i]);
+    if (w->graph[i]) cudaGraphDestroy(w->graph[i]);
+  }
   if (w->block) cudaFree(w->block);
   if (w->srcs) cudaFree(w->srcs);
   if (w->h_ctl) cudaFreeHost(w->h_ctl);

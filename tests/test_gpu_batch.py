@@ -82,6 +82,23 @@ def test_batch_equals_single_source_calls():
     g.close()
 
 
+@pytest.mark.parametrize("k,offset", [(64, 0), (64, 1), (68, 0), (68, 3), (12, 0)])
+def test_row_read_modes(k, offset):
+    """k a multiple of 4 on a 16-byte aligned matrix reads rows as 16-byte
+    vectors; an offset matrix or another k reads them word by word."""
+    ro, col, w, _ = graphgen.workload("rmat16")
+    srcs = graphgen.sample_sources(ro, k, seed=11)
+    g = gg().Graph(ro, col, w, symmetric=True)
+    buf = torch.empty(g.n * k + offset, dtype=torch.uint32, device="cuda")
+    out = buf[offset:]
+    g.sssp_batch(srcs, out)
+    torch.cuda.synchronize()
+    got = out.view(g.n, k).cpu().numpy()
+    ref = oracle.dijkstra_many(ro, col, w, srcs, threads=8)
+    np.testing.assert_array_equal(got.T, ref)
+    g.close()
+
+
 def test_rmat22_64_sources_config():
     ro, col, w = graphgen.rmat(22, 16, seed=1, W=255)
     srcs = graphgen.sample_sources(ro, 64, seed=1)
