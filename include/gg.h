@@ -132,9 +132,11 @@ typedef struct {
                                   (0 = 10 s for ASYNC, 60 s for the BSP policies)      */
     gg_stats* stats;           /* host; if not NULL the call synchronises the stream
                                   and fills it                                          */
-    uint32_t* trace;           /* device u32[trace_cap*4] or NULL: per superstep
+    uint32_t* trace;           /* device u32[trace_cap*4] or NULL.  BSP: per superstep
                                   (frontier size, frontier edges, kind 0 push / 1 pull
-                                  / 2 near-far split, next frontier size)              */
+                                  / 2 near-far split, next frontier size).  ASYNC: per
+                                  near-far split (split number, new threshold, far-pile
+                                  size, microseconds since the kernel started)         */
     uint32_t trace_cap;
     uint32_t delta;            /* near-far bucket width: vertices improved to a distance
                                   below the current threshold stay in the frontier, the

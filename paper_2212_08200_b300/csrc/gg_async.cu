@@ -63,6 +63,8 @@ struct AsyncCtl {
   uint32_t split_src, split_total, split_cursor, split_done;
   uint32_t* far[2];
   uint32_t* bm_far;
+  uint32_t* trace;         // per split: split number, new threshold, pile size, microseconds since start
+  uint32_t trace_cap;
 };
 
 namespace {
@@ -287,7 +289,15 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
                   ctl->split_cursor = 0;
                   ctl->split_done = 0;
                   ctl->sel = src ^ 1u;
-                  ctl->epoch = ctl->epoch + 1;
+                  const uint32_t ep = ctl->epoch;
+                  if (ctl->trace && ep < ctl->trace_cap) {
+                    uint32_t* t = ctl->trace + 4ull * ep;
+                    t[0] = ep;
+                    t[1] = ctl->t_cur;
+                    t[2] = total;
+                    t[3] = (uint32_t)((globaltimer() - ctl->t_start) / 1000ull);
+                  }
+                  ctl->epoch = ep + 1;
                   __threadfence();
                   atomicExch(&ctl->phase, 2u);
                   act = 2;
@@ -367,7 +377,7 @@ __global__ void k_async_init(DevGraph g, uint32_t* dist, uint32_t* inq, uint32_t
 
 __global__ void k_async_seed(DevGraph g, uint32_t src, uint32_t* dist, unsigned long long* Q, uint32_t* inq,
                              AsyncCtl* ctl, unsigned long long watchdog_ns, uint32_t delta, uint32_t* far0,
-                             uint32_t* far1, uint32_t* bm_far) {
+                             uint32_t* far1, uint32_t* bm_far, uint32_t* trace, uint32_t trace_cap) {
   dist[src] = 0u;
   ctl->t_cur = delta;
   ctl->t_prev = 0;
@@ -378,6 +388,8 @@ __global__ void k_async_seed(DevGraph g, uint32_t src, uint32_t* dist, unsigned 
   ctl->far_min = kInf;
   ctl->phase = 0;
   ctl->epoch = 0;
+  ctl->trace = trace;
+  ctl->trace_cap = trace ? trace_cap : 0u;
   ctl->split_src = 0;
   ctl->split_total = 0;
   ctl->split_cursor = 0;
@@ -449,7 +461,8 @@ gg_status async_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options&
   GG_CK(cudaGetLastError());
   const unsigned long long wd = o.watchdog_ns ? o.watchdog_ns : 10000000000ull;
   const uint32_t delta = o.delta == GG_DELTA_NONE ? kInf : (o.delta ? o.delta : g->default_delta);
-  k_async_seed<<<1, 1, 0, s>>>(g->dg, src, dist, Q, w.inq, ctl, wd, delta, w.far[0], w.far[1], w.bm_far);
+  k_async_seed<<<1, 1, 0, s>>>(g->dg, src, dist, Q, w.inq, ctl, wd, delta, w.far[0], w.far[1], w.bm_far, o.trace,
+                               o.trace_cap);
   GG_CK(cudaGetLastError());
   AsyncArgs a{g->dg, Q, logcap, w.inq, ctl};
   void* args[] = {&a};

@@ -63,7 +63,7 @@ constexpr int kBTile = 1024;
 constexpr int kBWarpEdges = kBTile / kBNW;
 constexpr int kBCap = kBTile + 1;
 #ifndef GG_BMINB
-#define GG_BMINB 4   // resident CTAs per SM the batch superstep is compiled for (64 registers)
+#define GG_BMINB 5   // resident CTAs per SM the batch superstep is compiled for (48 registers)
 #endif
 
 struct BSmem {
@@ -75,27 +75,29 @@ struct BSmem {
   unsigned long long base;
 };
 
-// Eight consecutive distances row[0..7] into d[] where bit q of `on` is set
-// (others := fill).  VEC: the row is 16-byte aligned and read as two 16-byte
-// vectors, each only when one of its four bits is set (a set bit implies the
-// whole vector lies inside the matrix: groups are 4-aligned when VEC).
+// Eight consecutive distances row[0..7] into d[], read only where bit q of
+// `on` is set (the other entries are left unspecified and must not be used).
+// VEC: the row is 16-byte aligned and read as two 16-byte vectors, each only
+// when one of its four bits is set (a set bit implies the whole vector lies
+// inside the matrix: groups are 4-aligned when VEC).
 template <bool VEC>
-__device__ __forceinline__ void load_row8(const uint32_t* row, uint32_t on, uint32_t (&d)[8], uint32_t fill) {
+__device__ __forceinline__ void load_row8(const uint32_t* row, uint32_t on, uint32_t (&d)[8]) {
   if (VEC) {
-    uint4 a = make_uint4(fill, fill, fill, fill), b = a;
+    uint4 a, b;
     if (on & 0x0Fu) a = __ldcg(reinterpret_cast<const uint4*>(row));
     if (on & 0xF0u) b = __ldcg(reinterpret_cast<const uint4*>(row) + 1);
-    d[0] = (on & 1u) ? a.x : fill;
-    d[1] = (on & 2u) ? a.y : fill;
-    d[2] = (on & 4u) ? a.z : fill;
-    d[3] = (on & 8u) ? a.w : fill;
-    d[4] = (on & 16u) ? b.x : fill;
-    d[5] = (on & 32u) ? b.y : fill;
-    d[6] = (on & 64u) ? b.z : fill;
-    d[7] = (on & 128u) ? b.w : fill;
+    d[0] = a.x;
+    d[1] = a.y;
+    d[2] = a.z;
+    d[3] = a.w;
+    d[4] = b.x;
+    d[5] = b.y;
+    d[6] = b.z;
+    d[7] = b.w;
   } else {
 #pragma unroll
-    for (int q = 0; q < 8; ++q) d[q] = ((on >> q) & 1u) ? ld_cg(row + q) : fill;
+    for (int q = 0; q < 8; ++q)
+      if ((on >> q) & 1u) d[q] = ld_cg(row + q);
   }
 }
 
@@ -243,9 +245,7 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
         if (!vm) break;
         const int nvalid = __popc(vm);   // valid edges are a prefix of the lanes
         uint32_t cur_j = 0xFFFFFFFFu, amask = 0u;
-        uint32_t du[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) du[q] = kInf;
+        uint32_t du[8];   // the current source row, where amask has a bit
         for (int i0 = 0; i0 < nvalid; i0 += 4) {
           const int i = i0 + (int)g4;
           const bool live = i < nvalid;
@@ -256,12 +256,12 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
           if (live && ji != cur_j) {   // uniform within the group
             cur_j = ji;
             amask = (uint32_t)(sm.em[ji] >> (8 * l8)) & 0xFFu;
-            load_row8<VEC>(dist + (size_t)sm.ev[ji] * K + col0 + 8 * l8, amask, du, kInf);
+            load_row8<VEC>(dist + (size_t)sm.ev[ji] * K + col0 + 8 * l8, amask, du);
           }
           const uint32_t am = live ? amask : 0u;
           uint32_t* vrow = dist + (size_t)vi * K + col0 + 8 * l8;
           uint32_t cv[8];
-          load_row8<VEC>(vrow, am, cv, 0u);
+          load_row8<VEC>(vrow, am, cv);
           uint32_t near = 0u, far = 0u, fm = kInf;
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
@@ -283,8 +283,10 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
           // the group's 64-bit masks: OR of the lanes' bytes over the 8-lane group
           unsigned long long nmask = (unsigned long long)near << (8 * l8);
           unsigned long long fmask = (unsigned long long)far << (8 * l8);
+          if (__any_sync(0xFFFFFFFFu, near != 0u)) {   // most late relaxations improve nothing
 #pragma unroll
-          for (int o = 1; o < 8; o <<= 1) nmask |= __shfl_xor_sync(0xFFFFFFFFu, nmask, o);
+            for (int o = 1; o < 8; o <<= 1) nmask |= __shfl_xor_sync(0xFFFFFFFFu, nmask, o);
+          }
           if (T != kInf) {   // uniform: only with buckets can anything be parked
             const unsigned anyf = __ballot_sync(0xFFFFFFFFu, far != 0u);
             if (anyf) {
