@@ -42,10 +42,15 @@
 namespace gg {
 
 struct AsyncCtl {
-  unsigned long long head;
-  unsigned long long tail;
-  unsigned long long pending;
-  unsigned long long pops;
+  // the counters every warp updates live on cache lines of their own
+  alignas(128) unsigned long long head;
+  alignas(128) unsigned long long tail;
+  alignas(128) unsigned long long pending;
+  alignas(128) uint32_t far_cnt[2];
+  alignas(128) uint32_t far_min;
+  alignas(128) uint32_t split_cursor;
+  uint32_t split_done;
+  alignas(128) unsigned long long pops;
   unsigned long long edges;
   unsigned long long watchdog_ns;
   unsigned long long t_start;
@@ -56,11 +61,9 @@ struct AsyncCtl {
   // the far pile far[sel]; when nothing is queued or running, idle warps split
   // the pile against a raised threshold (drop / queue / keep)
   uint32_t t_cur, t_prev, delta, sel;
-  uint32_t far_cnt[2];
-  uint32_t far_min;
   uint32_t phase;          // 0 none, 1 starting, 2 split running
   uint32_t epoch;          // split starts so far
-  uint32_t split_src, split_total, split_cursor, split_done;
+  uint32_t split_src, split_total;
   uint32_t* far[2];
   uint32_t* bm_far;
   uint32_t* trace;         // per split: split number, new threshold, pile size, microseconds since start
@@ -76,6 +79,13 @@ __device__ __forceinline__ unsigned long long globaltimer() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
+}
+
+// Time since t_start beyond `limit` ns?  The difference is taken as signed:
+// %globaltimer read on another SM can lag the start stamp by a little, and an
+// unsigned difference would wrap to a huge value and fire the watchdog at once.
+__device__ __forceinline__ bool past_watchdog(unsigned long long t_start, unsigned long long limit) {
+  return (long long)(globaltimer() - t_start) > (long long)limit;
 }
 
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
@@ -101,11 +111,60 @@ struct AsyncArgs {
   AsyncCtl* ctl;
 };
 
+// Warp-aggregated far-pile append: one atomicMin on far_min (the warp's
+// smallest parked distance fd, skipped when it cannot lower the minimum) and
+// one atomicAdd on the pile's count for the lanes with app == true.
+__device__ __forceinline__ void far_append_warp(AsyncCtl* ctl, bool app, uint32_t v, uint32_t fd, uint32_t lane) {
+  uint32_t m = fd;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = min(m, __shfl_xor_sync(0xFFFFFFFFu, m, o));
+  const unsigned am = __ballot_sync(0xFFFFFFFFu, app);
+  uint32_t sel = 0, base = 0;
+  if (lane == 0) {
+    if (m != kInf && m < ld_volatile_u32(&ctl->far_min)) atomicMin(&ctl->far_min, m);
+    if (am) {
+      sel = ld_volatile_u32(&ctl->sel);
+      base = atomicAdd(&ctl->far_cnt[sel], (uint32_t)__popc(am));
+    }
+  }
+  if (!am) return;
+  sel = __shfl_sync(0xFFFFFFFFu, sel, 0);
+  base = __shfl_sync(0xFFFFFFFFu, base, 0);
+  if (app) ctl->far[sel][base + __popc(am & ((1u << lane) - 1u))] = v;
+}
+
+// A lane's consumer state: the queue position it reserved (have), and an
+// item it already took from the ring but has not expanded yet (held).
+struct Taker {
+  unsigned long long pos;
+  uint32_t held_v;
+  bool have, held;
+};
+
+// Take the item at the lane's reserved position if it has been published:
+// mark the slot consumed for this lap, clear the vertex's in-queue bit (a
+// later improvement re-enqueues it) and order that before the dist read.
+__device__ __forceinline__ bool try_take(const AsyncArgs& a, Taker& tk, uint32_t& v) {
+  unsigned long long* slot = a.Q + (tk.pos & ((1ull << a.logcap) - 1));
+  const uint32_t lap = (uint32_t)(tk.pos >> a.logcap);
+  const unsigned long long val = ld_acquire_u64(slot);
+  if ((uint32_t)(val >> 32) != 2 * lap + 1) return false;
+  v = (uint32_t)val;
+  tk.have = false;
+  st_release_u64(slot, (unsigned long long)(2 * lap + 2) << 32);
+  atomicAnd(a.inq + (v >> 5), ~(1u << (v & 31)));
+  __threadfence();
+  return true;
+}
+
 // Enqueue the improved vertices held by the lanes with want == true (new
 // distance nd): below the threshold into the ring queue, otherwise into the
 // far pile (once, by the far bitmap).
-__device__ __forceinline__ void push_warp(const AsyncArgs& a, bool want, uint32_t v, uint32_t nd, uint32_t lane) {
-  bool mine = false;
+__device__ __forceinline__ void push_warp(const AsyncArgs& a, bool want, uint32_t v, uint32_t nd, uint32_t lane,
+                                          Taker& tk) {
+  if (!__any_sync(0xFFFFFFFFu, want)) return;
+  bool mine = false, fnew = false;
+  uint32_t fd = kInf;
   if (want) {
     const uint32_t rs = __ldg(a.g.ro + v), re = __ldg(a.g.ro + v + 1);
     if (re > rs) {
@@ -114,15 +173,12 @@ __device__ __forceinline__ void push_warp(const AsyncArgs& a, bool want, uint32_
       if (nd < ld_volatile_u32(&a.ctl->t_cur)) {
         mine = !(atomicOr(a.inq + (v >> 5), bit) & bit);
       } else {
-        atomicMin(&a.ctl->far_min, nd);
-        if (!(atomicOr(a.ctl->bm_far + (v >> 5), bit) & bit)) {
-          const uint32_t sel = ld_volatile_u32(&a.ctl->sel);
-          const uint32_t pos = atomicAdd(&a.ctl->far_cnt[sel], 1u);
-          a.ctl->far[sel][pos] = v;
-        }
+        fd = nd;
+        fnew = !(atomicOr(a.ctl->bm_far + (v >> 5), bit) & bit);
       }
     }
   }
+  far_append_warp(a.ctl, fnew, v, fd, lane);
   const unsigned mm = __ballot_sync(0xFFFFFFFFu, mine);
   if (!mm) return;
   const uint32_t cnt = __popc(mm);
@@ -133,22 +189,40 @@ __device__ __forceinline__ void push_warp(const AsyncArgs& a, bool want, uint32_
     base = atomicAdd(&a.ctl->tail, (unsigned long long)cnt);
   }
   base = __shfl_sync(0xFFFFFFFFu, base, leader);
-  if (mine) {
-    const unsigned long long pos = base + __popc(mm & ((1u << lane) - 1));
-    const unsigned long long lap = pos >> a.logcap;
-    unsigned long long* slot = a.Q + (pos & ((1ull << a.logcap) - 1));
-    const uint32_t want_tag = (uint32_t)(2 * lap);
-    uint32_t spins = 0;
-    while ((uint32_t)(ld_acquire_u64(slot) >> 32) != want_tag) {
-      if (ld_volatile_u32(&a.ctl->abort)) return;
-      if (++spins > (1u << 22) || globaltimer() - a.ctl->t_start > a.ctl->watchdog_ns) {
+  // Publish.  A slot is free once its previous lap was consumed.  The whole
+  // warp waits together and meanwhile takes the items published at its own
+  // reserved positions (held for its next round), so a warp never waits on a
+  // slot that only it could free, and every waiting warp keeps freeing slots.
+  const unsigned long long pos = base + __popc(mm & ((1u << lane) - 1));
+  unsigned long long* slot = a.Q + (pos & ((1ull << a.logcap) - 1));
+  const uint32_t want_tag = (uint32_t)(2 * (pos >> a.logcap));
+  bool todo = mine;
+  uint32_t spins = 0;
+  for (;;) {
+    if (todo && (uint32_t)(ld_acquire_u64(slot) >> 32) == want_tag) {
+      st_release_u64(slot, ((unsigned long long)(want_tag + 1) << 32) | v);
+      todo = false;
+    }
+    if (!__any_sync(0xFFFFFFFFu, todo)) break;
+    if (tk.have && !tk.held) {
+      uint32_t hv;
+      if (try_take(a, tk, hv)) {
+        tk.held = true;
+        tk.held_v = hv;
+      }
+    }
+    int stop = 0;
+    if (lane == 0) {
+      if (ld_volatile_u32(&a.ctl->abort)) {
+        stop = 1;
+      } else if (++spins > (1u << 22) || past_watchdog(a.ctl->t_start, a.ctl->watchdog_ns)) {
         atomicOr(&a.ctl->status, DS_TIMEOUT);
         atomicExch(&a.ctl->abort, 1u);
-        return;
+        stop = 1;
       }
-      __nanosleep(64);
     }
-    st_release_u64(slot, ((unsigned long long)(want_tag + 1) << 32) | v);
+    if (__shfl_sync(0xFFFFFFFFu, stop, 0)) return;
+    __nanosleep(64);
   }
 }
 
@@ -160,34 +234,26 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   AsyncCtl* ctl = a.ctl;
   uint32_t* dist = ctl->dist;
-  const unsigned long long cmask = (1ull << a.logcap) - 1;
-  unsigned long long my_pos = 0;
-  bool have = false;
+  Taker tk{0ull, 0u, false, false};
   uint32_t backoff = 32, idle_rounds = 0;
   unsigned long long pops = 0, edges = 0;
   bool ovf = false;
   for (;;) {
-    if (!__any_sync(0xFFFFFFFFu, have)) {
+    if (!__any_sync(0xFFFFFFFFu, tk.have)) {
       unsigned long long h = 0;
       if (lane == 0) h = atomicAdd(&ctl->head, 32ull);
       h = __shfl_sync(0xFFFFFFFFu, h, 0);
-      my_pos = h + lane;
-      have = true;
+      tk.pos = h + lane;
+      tk.have = true;
     }
     bool got = false;
     uint32_t v = 0;
-    if (have) {
-      unsigned long long* slot = a.Q + (my_pos & cmask);
-      const uint32_t lap = (uint32_t)(my_pos >> a.logcap);
-      const unsigned long long val = ld_acquire_u64(slot);
-      if ((uint32_t)(val >> 32) == 2 * lap + 1) {
-        v = (uint32_t)val;
-        got = true;
-        have = false;
-        st_release_u64(slot, (unsigned long long)(2 * lap + 2) << 32);
-        atomicAnd(a.inq + (v >> 5), ~(1u << (v & 31)));
-        __threadfence();
-      }
+    if (tk.held) {   // taken while this warp waited to publish
+      v = tk.held_v;
+      tk.held = false;
+      got = true;
+    } else if (tk.have) {
+      got = try_take(a, tk, v);
     }
     const unsigned gm = __ballot_sync(0xFFFFFFFFu, got);
     if (gm) {
@@ -232,7 +298,7 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
             want = nd < old;
           }
         }
-        push_warp(a, want, dst, ndv, lane);
+        push_warp(a, want, dst, ndv, lane, tk);
       }
       pops += got ? 1 : 0;
       edges += got ? deg : 0;
@@ -254,7 +320,7 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
       if (lane == 0) {
         if (ld_volatile_u32(&ctl->abort)) {
           act = 1;
-        } else if (globaltimer() - ctl->t_start > ctl->watchdog_ns) {
+        } else if (past_watchdog(ctl->t_start, ctl->watchdog_ns)) {
           atomicOr(&ctl->status, DS_TIMEOUT);
           atomicExch(&ctl->abort, 1u);
           act = 1;
@@ -295,7 +361,8 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
                     t[0] = ep;
                     t[1] = ctl->t_cur;
                     t[2] = total;
-                    t[3] = (uint32_t)((globaltimer() - ctl->t_start) / 1000ull);
+                    const long long el = (long long)(globaltimer() - ctl->t_start);
+                    t[3] = el > 0 ? (uint32_t)(el / 1000) : 0u;
                   }
                   ctl->epoch = ep + 1;
                   __threadfence();
@@ -317,7 +384,7 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
         const uint32_t total = ld_volatile_u32(&ctl->split_total);
         if (chunk < total) {
           const uint32_t idx = chunk + lane;
-          bool want = false;
+          bool want = false, keep = false;
           uint32_t v = 0, d = 0;
           if (idx < total) {
             const uint32_t src = ld_volatile_u32(&ctl->split_src);
@@ -328,13 +395,11 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
               atomicAnd(ctl->bm_far + (v >> 5), ~bit);
               want = d >= ld_volatile_u32(&ctl->t_prev);   // below t_prev: expanded already
             } else {
-              atomicMin(&ctl->far_min, d);
-              const uint32_t sel = ld_volatile_u32(&ctl->sel);
-              const uint32_t pos = atomicAdd(&ctl->far_cnt[sel], 1u);
-              ctl->far[sel][pos] = v;
+              keep = true;
             }
           }
-          push_warp(a, want, v, d, lane);
+          far_append_warp(ctl, keep, v, keep ? d : kInf, lane);
+          push_warp(a, want, v, d, lane, tk);
           const uint32_t done = (uint32_t)min(32u, total - chunk);
           __threadfence();
           __syncwarp();
@@ -437,7 +502,8 @@ gg_status async_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options&
     const size_t nw = (g->n + 31) / 32;
     const size_t r_bm = (sizeof(uint32_t) * nw + 255) & ~size_t(255);
     const size_t r_far = (sizeof(uint32_t) * std::max<size_t>(g->n, 1) + 255) & ~size_t(255);
-    const size_t total = qbytes + 2 * r_bm + 2 * r_far + 256;
+    const size_t r_ctl = (sizeof(AsyncCtl) + 255) & ~size_t(255);
+    const size_t total = qbytes + 2 * r_bm + 2 * r_far + r_ctl;
     char* p = nullptr;
     GG_CK(cudaMalloc(&p, total));
     w.block = p;

@@ -755,7 +755,8 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
       ctl->status |= DS_ITER_CAP;
       more = false;
     }
-    if (more && bsp_globaltimer() - ctl->t_start > ctl->watchdog_ns) {
+    // signed difference: %globaltimer on this SM may lag the start stamp slightly
+    if (more && (long long)(bsp_globaltimer() - ctl->t_start) > (long long)ctl->watchdog_ns) {
       ctl->status |= DS_TIMEOUT;
       more = false;
     }

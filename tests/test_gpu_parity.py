@@ -349,6 +349,20 @@ def test_async_watchdog_reports_timeout_and_recovers():
     g.close()
 
 
+def test_async_repeated_runs_wrap_the_ring():
+    """Each RMAT-20 run from the hub pushes more items than the ring has
+    slots, so producers wrap onto slots of the previous lap while the warp
+    expanding the hub still holds reservations: every run must drain, bit-exact."""
+    ro, col, w, src = graphgen.workload("rmat20")
+    g = gg().Graph(ro, col, w, symmetric=True)
+    ref = oracle.dijkstra(ro, col, w, src)
+    for rep in range(40):
+        got, st = run(g, src, "async")
+        assert st["device_status"] == 0, f"rep {rep}"
+        np.testing.assert_array_equal(got, ref, err_msg=f"rep {rep}")
+    g.close()
+
+
 @pytest.mark.parametrize("policy", ["persistent", "graph"])
 def test_bsp_watchdog_reports_timeout_and_recovers(policy):
     m = gg()
