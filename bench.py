@@ -48,6 +48,9 @@ def parse():
     p.add_argument("--policy", default="graph", choices=["graph", "async", "host", "persistent"])
     p.add_argument("--direction", default="push", choices=["auto", "push", "pull"])
     p.add_argument("--lb", default="auto", choices=["auto", "mp", "bins", "warp"])
+    p.add_argument("--batch-scale", type=int, default=22, help="RMAT scale of the batched run (22 = the workload)")
+    p.add_argument("--batch-policy", default="graph", choices=["graph", "host"],
+                   help="host: supersteps launched one by one (for profilers)")
     p.add_argument("--delta", type=int, default=0, help="near-far bucket width (0 = graph default, -1 = none)")
     p.add_argument("--alpha", type=int, default=0)
     p.add_argument("--beta", type=int, default=0)
@@ -71,6 +74,34 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6400.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    """sha256 of the superstep kernel's sources: a stored DRAM-traffic figure
+    is reported only while the kernel it was measured on is unchanged."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("gg_bsp.cu", "gg_common.cuh", "gg_host.h"):
+        with open(os.path.join(ROOT, "paper_2212_08200_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def kernel_traffic(workload: str, direction: str, lb: str, delta: int):
+    """DRAM bytes (read + write) of the superstep kernel over one whole SSSP,
+    from the ncu capture summarised in profiles/k_superstep_traffic.json, when
+    that capture matches this workload, these options and the current kernel
+    source; otherwise None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_superstep_traffic.json")) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    for e in d.get("captures", []):
+        if (e.get("workload") == workload and e.get("direction") == direction and e.get("lb") == lb
+                and e.get("delta") == delta and e.get("source_sha256") == kernel_source_hash()):
+            return float(e["dram_bytes_per_sssp"])
+    return None
 
 
 class ClockSampler:
@@ -167,11 +198,14 @@ def reduce_over_ranks(value, op, pg):
     return float(t.item())
 
 
-def run_batched(gg, torch, k=64, seed=1):
+def run_batched(gg, torch, k=64, seed=1, scale=22, policy="graph"):
     """Batched multi-source SSSP on RMAT-22 (64 seeded sources, one fused
-    launch sequence) vs the same 64 sources as back-to-back gg_sssp calls."""
+    launch sequence) vs the same 64 sources as back-to-back gg_sssp calls.
+    scale / policy other than 22 / graph serve profiling (ncu cannot see the
+    kernels inside the CUDA-graph loop; "host" launches them one by one)."""
     import graphgen
-    ro, col, w = graphgen.rmat(22, 16, seed=1, W=255)
+    pol = {"graph": gg.GG_POLICY_BSP_GRAPH, "host": gg.GG_POLICY_BSP_HOST}[policy]
+    ro, col, w = graphgen.rmat(scale, 16, seed=1, W=255)
     srcs = graphgen.sample_sources(ro, k, seed=seed)
     g = gg.Graph(ro, col, w, symmetric=True)
     n = g.n
@@ -179,11 +213,11 @@ def run_batched(gg, torch, k=64, seed=1):
     single = torch.empty(n, dtype=torch.uint32, device="cuda")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     st = gg.gg_stats()
-    g.sssp_batch(srcs, out, stats=st)
+    g.sssp_batch(srcs, out, stats=st, policy=pol)
     tb = []
     for _ in range(3):
         e0.record()
-        g.sssp_batch(srcs, out)
+        g.sssp_batch(srcs, out, policy=pol)
         e1.record()
         torch.cuda.synchronize()
         tb.append(e0.elapsed_time(e1))
@@ -200,7 +234,9 @@ def run_batched(gg, torch, k=64, seed=1):
     m_trav = int(np.diff(ro.astype(np.int64))[d != gg.GG_INF].sum())
     g.close()
     t = statistics.median(tb)
-    return {"workload": f"RMAT scale 22 EF16, {k} seeded sources (splitmix64 seed 1), dist matrix 4M x {k} u32",
+    return {"workload": f"RMAT scale {scale} EF16, {k} seeded sources (splitmix64 seed 1), "
+                        f"dist matrix {n} x {k} u32",
+            "policy": policy,
             "queries_per_s": k / t * 1e3, "ms": t, "back_to_back_queries_per_s": k / t1 * 1e3,
             "back_to_back_ms": t1, "speedup": t1 / t, "supersteps": st.iterations,
             "edges_scanned": st.edges_scanned, "gteps_aggregate_est": k * m_trav / (t * 1e-3) / 1e9}
@@ -284,7 +320,8 @@ def run_reference(args):
     m_trav = oracle.traversed_edges(ro, d)
     t = statistics.median(steps)
     val = m_trav / t / 1e9
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GTEPS", "n_gpus": 0,
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GTEPS", "n_gpus": args.gpus,
+            "device": "host CPU, 1 thread (the oracle uses no GPU)",
             "steps": len(steps), "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": workload_desc(args.workload), "n": int(ro.shape[0] - 1), "m": int(col.shape[0]),
@@ -332,9 +369,11 @@ def main():
 
     # correctness of what is timed: stats run + invariant-free hash check vs the oracle's stored hash
     st = gg.gg_stats()
+    torch.cuda.nvtx.range_push("gg_sssp_stats_run")   # lets a profiler select exactly one SSSP's launches
     gg.gg_sssp_ex(g.handle, src, dist_t, gg.make_options(policy=policy, direction=direction, lb_mode=lb,
                                                          pull_alpha=args.alpha, pull_beta=args.beta, stats=st,
                                                          delta=delta), stream)
+    torch.cuda.nvtx.range_pop()
     d_host = dist_t.cpu().numpy()
     reach = d_host != gg.GG_INF
     m_trav = int(np.diff(ro.astype(np.int64))[reach].sum())
@@ -417,7 +456,7 @@ def main():
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
             h = gg.gg_graph_create_csr(arrs[0], arrs[1], arrs[2], symmetric=True, stream=stream)
-            gg.gg_sssp(h, src, dist_t, stream)
+            gg.gg_sssp_ex(h, src, dist_t, opts, stream)   # the timed path's options
             out_h.copy_(dist_t.view(torch.int32), non_blocking=True)
             torch.cuda.synchronize()
             gg.gg_graph_destroy(h)
@@ -425,14 +464,14 @@ def main():
         e2e = {"value": world * m_trav / e2e_s / 1e9, "unit": "GTEPS",
                "h2d_bytes_per_step": 4 * (n + 1) + 8 * m, "d2h_bytes_per_step": 4 * n,
                "ms_per_step": e2e_s * 1e3,
-               "what": "gg_graph_create_csr from pinned host CSR + gg_sssp + distances copied to pinned host "
+               "what": "gg_graph_create_csr from pinned host CSR + gg_sssp_ex + distances copied to pinned host "
                        "+ gg_graph_destroy, wall clock"}
 
     # batched and served queries shard naturally: every rank runs its own
     # seeded stream (per-GPU work fixed) and the queries/s add up
     batched = serving = None
     if not args.no_batch:
-        batched = run_batched(gg, torch, seed=1 + rank)
+        batched = run_batched(gg, torch, seed=1 + rank, scale=args.batch_scale, policy=args.batch_policy)
         batched["queries_per_s_all_ranks"] = reduce_over_ranks(batched["queries_per_s"], "sum", pg)
     if not args.no_serve:
         serving = run_serving(gg, torch, args.serve_queries, seed=1 + rank)
@@ -455,7 +494,10 @@ def main():
                        "supersteps": iters, "pull_supersteps": stats["pull_iterations"],
                        "edges_scanned": stats["edges_scanned"], "step_ms_min": min(per), "step_ms_max": max(per)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / hbm,
+                         "traffic": kernel_traffic(args.workload, args.direction, args.lb, args.delta),
+                         "traffic_unit": "DRAM bytes per SSSP (all supersteps), ncu, cold L2",
+                         "peak_kind": peak_kind,
                          "kernel": ("k_async (the whole run)" if policy == gg.GG_POLICY_ASYNC_PERSISTENT else
                                     "k_bsp_persistent (all supersteps)" if policy == gg.GG_POLICY_BSP_PERSISTENT else
                                     "k_superstep (all supersteps of one SSSP)"),
