@@ -231,6 +231,7 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
       // source mask.
       const uint32_t wbeg = t0 + warp * kBWarpEdges;
       const uint32_t g4 = lane >> 3, l8 = lane & 7;
+      const bool buckets = T != kInf;   // uniform
       for (uint32_t r = 0; r < (uint32_t)kBWarpEdges; r += 32) {
         const uint32_t gidx = wbeg + r + lane;
         const bool valid = gidx < t1;
@@ -244,7 +245,7 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
         const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
         if (!vm) break;
         const int nvalid = __popc(vm);   // valid edges are a prefix of the lanes
-        uint32_t cur_j = 0xFFFFFFFFu, amask = 0u;
+        uint32_t cur_j = 0xFFFFFFFFu, amask = 0u, dmax = 0u;
         uint32_t du[8];   // the current source row, where amask has a bit
         for (int i0 = 0; i0 < nvalid; i0 += 4) {
           const int i = i0 + (int)g4;
@@ -257,25 +258,44 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
             cur_j = ji;
             amask = (uint32_t)(sm.em[ji] >> (8 * l8)) & 0xFFu;
             load_row8<VEC>(dist + (size_t)sm.ev[ji] * K + col0 + 8 * l8, amask, du);
+            dmax = 0u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              if ((amask >> q) & 1u) dmax = max(dmax, du[q]);
           }
           const uint32_t am = live ? amask : 0u;
           uint32_t* vrow = dist + (size_t)vi * K + col0 + 8 * l8;
           uint32_t cv[8];
           load_row8<VEC>(vrow, am, cv);
           uint32_t near = 0u, far = 0u, fm = kInf;
+          // fast path: no buckets and no sum of this row can reach kInf (the
+          // largest active source distance plus w fits), so plain adds suffice
+          if (!buckets && __all_sync(0xFFFFFFFFu, am == 0u || dmax < kInf - wi)) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            if ((am >> q) & 1u) {
-              const uint32_t nd = add_sat(du[q], wi, ovf);
-              if (nd < cv[q]) {
-                atomicMin(vrow + q, nd);
-                // near bits (new distance below the threshold) join the next
-                // frontier's mask; the others are parked in the far mask
-                if (nd < T) {
+            for (int q = 0; q < 8; ++q) {
+              if ((am >> q) & 1u) {
+                const uint32_t nd = du[q] + wi;
+                if (nd < cv[q]) {
+                  atomicMin(vrow + q, nd);
                   near |= 1u << q;
-                } else {
-                  far |= 1u << q;
-                  fm = min(fm, nd);
+                }
+              }
+            }
+          } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              if ((am >> q) & 1u) {
+                const uint32_t nd = add_sat(du[q], wi, ovf);
+                if (nd < cv[q]) {
+                  atomicMin(vrow + q, nd);
+                  // near bits (new distance below the threshold) join the next
+                  // frontier's mask; the others are parked in the far mask
+                  if (nd < T) {
+                    near |= 1u << q;
+                  } else {
+                    far |= 1u << q;
+                    fm = min(fm, nd);
+                  }
                 }
               }
             }
@@ -287,7 +307,7 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
 #pragma unroll
             for (int o = 1; o < 8; o <<= 1) nmask |= __shfl_xor_sync(0xFFFFFFFFu, nmask, o);
           }
-          if (T != kInf) {   // uniform: only with buckets can anything be parked
+          if (buckets) {   // uniform: only with buckets can anything be parked
             const unsigned anyf = __ballot_sync(0xFFFFFFFFu, far != 0u);
             if (anyf) {
 #pragma unroll
