@@ -70,6 +70,10 @@ struct BSmem {
   uint32_t es[kBCap], eb[kBCap], ev[kBCap];
   unsigned long long em[kBCap];
   uint32_t qv[kBCap], qr[kBCap], qd[kBCap];
+  // per warp, per edge of the current 32-edge chunk: target vertex and the
+  // sources it improved (near, far), appended together after the chunk
+  unsigned long long pm[kBNW][32], pf[kBNW][32];
+  uint32_t pv[kBNW][32];
   uint32_t wsum[kBNW];
   uint32_t qn, j, last, ovf;
   unsigned long long base;
@@ -178,6 +182,14 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
       __syncthreads();
       const uint32_t qn = sm.qn;
       if (qn) {
+        if (!g.sinks) {   // rows deferred from the appends
+          for (uint32_t i = tid; i < qn; i += kBB) {
+            const uint32_t rs = __ldg(g.ro + sm.qv[i]);
+            sm.qr[i] = rs;
+            sm.qd[i] = __ldg(g.ro + sm.qv[i] + 1) - rs;
+          }
+          __syncthreads();
+        }
         const uint32_t tot = block_scan_excl<kBB>(sm.qd, qn, sm.wsum);
         if (tid == 0) sm.base = atomicAdd(&ctl->cnt[pn], ((unsigned long long)qn << 32) | tot);
         __syncthreads();
@@ -317,27 +329,53 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
               if (lane == 0) atomicMin(&ctl->far_min, fm);
             }
           }
-          if (l8 == 0 && (nmask | fmask)) {
-            const uint32_t rs = __ldg(g.ro + vi), re = __ldg(g.ro + vi + 1);
+          if (l8 == 0 && live) {
+            sm.pv[warp][i] = vi;
+            sm.pm[warp][i] = nmask;
+            sm.pf[warp][i] = fmask;
+          }
+        }
+        // the chunk's appends, one edge per lane, their atomics in flight together
+        __syncwarp();
+        if (lane < (uint32_t)nvalid) {
+          const unsigned long long nb = sm.pm[warp][lane], fb = sm.pf[warp][lane];
+          if (nb | fb) {
+            const uint32_t vi = sm.pv[warp][lane];
+            // vertices without out-edges are never appended; on a graph
+            // without such sinks the row is read at the tile's flush instead
+            uint32_t rs = 0, re = 1;
+            if (g.sinks) {
+              rs = __ldg(g.ro + vi);
+              re = __ldg(g.ro + vi + 1);
+            }
             if (re > rs) {
-              if (nmask && atomicOr(Mn + vi, nmask) == 0ull) {
+              if (nb && atomicOr(Mn + vi, nb) == 0ull) {
                 const uint32_t q = atomicAdd(&sm.qn, 1u);
                 sm.qv[q] = vi;
                 sm.qr[q] = rs;
                 sm.qd[q] = re - rs;
               }
-              if (fmask && atomicOr(w.fmask + vi, fmask) == 0ull) {
+              if (fb && atomicOr(w.fmask + vi, fb) == 0ull) {
                 const uint32_t pos = atomicAdd(&ctl->fcnt[fsel], 1u);
                 pick2(w.far_v, fsel)[pos] = vi;
               }
             }
           }
         }
+        __syncwarp();
       }
       // append this tile's new frontier vertices
       __syncthreads();
       const uint32_t qn = sm.qn;
       if (qn) {
+        if (!g.sinks) {   // rows deferred from the appends
+          for (uint32_t i = tid; i < qn; i += kBB) {
+            const uint32_t rs = __ldg(g.ro + sm.qv[i]);
+            sm.qr[i] = rs;
+            sm.qd[i] = __ldg(g.ro + sm.qv[i] + 1) - rs;
+          }
+          __syncthreads();
+        }
         const uint32_t tot = block_scan_excl<kBB>(sm.qd, qn, sm.wsum);
         if (tid == 0) sm.base = atomicAdd(&ctl->cnt[pn], ((unsigned long long)qn << 32) | tot);
         __syncthreads();
