@@ -60,16 +60,15 @@ namespace {
 constexpr int kBB = 256;
 constexpr int kBNW = kBB / 32;
 constexpr int kBTile = 1024;
-constexpr int kBWarpEdges = kBTile / kBNW;
 constexpr int kBCap = kBTile + 1;
+constexpr uint32_t kBQW = 128;   // per-warp queue slots of the warp-streaming relaxation
+static_assert(kBNW * kBQW <= (uint32_t)kBCap, "per-warp queues fit the CTA queue arrays");
 #ifndef GG_BMINB
 #define GG_BMINB 5   // resident CTAs per SM the batch superstep is compiled for (48 registers)
 #endif
 
 struct BSmem {
-  uint32_t es[kBCap], eb[kBCap], ev[kBCap];
-  unsigned long long em[kBCap];
-  uint32_t qv[kBCap], qr[kBCap], qd[kBCap];
+  uint32_t qv[kBCap], qr[kBCap], qd[kBCap];   // split step: CTA queue; otherwise kBQW per warp
   // per warp, per edge of the current 32-edge chunk: target vertex and the
   // sources it improved (near, far), appended together after the chunk
   unsigned long long pm[kBNW][32], pf[kBNW][32];
@@ -134,8 +133,6 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
   }
   __syncthreads();
   bool ovf = false;
-  const uint32_t e0 = (uint32_t)(((unsigned long long)blockIdx.x * E) / gridDim.x);
-  const uint32_t e1 = (uint32_t)(((unsigned long long)(blockIdx.x + 1) * E) / gridDim.x);
   if (bmode == 1) {
     // split step: every parked (vertex, source) bit is re-examined against
     // the raised threshold: below t_prev it was expanded already (drop),
@@ -204,76 +201,145 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
       }
       __syncthreads();
     }
-  } else if (F > 0 && e0 < e1) {
+  } else if (F > 0) {
+    // Warp streaming, no block barriers: every warp of the grid takes an
+    // equal contiguous share of the frontier's edge coordinates and walks it
+    // 32 edges at a time.  The frontier entries covering the current edges
+    // sit in a sliding window of 32 entries, one per lane (first coordinate,
+    // row start, vertex, source mask); a lane finds its edge's entry with a
+    // 5-step shuffle search.  The warp then relaxes the 32 edges four at a
+    // time, one per 8-lane group: lane l8 of a group holds the eight
+    // consecutive sources 8*l8 .. 8*l8+7 of the 64-source group, one 32-byte
+    // sector of a distance row (two 16-byte vectors when VEC).
+    const unsigned FULL = 0xFFFFFFFFu;
     const uint32_t* S = pick3(w.fs, pc);
-    if (tid < 32) {
-      const uint32_t j = warp_search_le(S, F, e0);
-      if (tid == 0) sm.j = j;
-    }
-    __syncthreads();
-    uint32_t j = sm.j;
-    for (uint32_t t0 = e0; t0 < e1; t0 += kBTile) {
-      const uint32_t t1 = min(t0 + (uint32_t)kBTile, e1);
-      uint32_t nent = 0;
-      for (;;) {
-        const uint32_t idx = j + nent + tid;
-        bool valid = false;
-        uint32_t s = 0;
-        if (idx < F) {
-          s = S[idx];
-          valid = s < t1;
+    const uint32_t* R = pick3(w.fr, pc);
+    const uint32_t* V = pick3(w.fv, pc);
+    constexpr uint32_t QW = kBQW;
+    uint32_t* qv = sm.qv + warp * QW;   // this warp's queue of new frontier vertices
+    uint32_t* qr = sm.qr + warp * QW;
+    uint32_t* qd = sm.qd + warp * QW;
+    uint32_t qn = 0;                    // warp-uniform
+    const uint32_t g4 = lane >> 3, l8 = lane & 7;
+    const unsigned lt = (1u << lane) - 1u;
+    const bool buckets = T != kInf;     // uniform
+    const unsigned long long Wn = (unsigned long long)gridDim.x * kBNW;
+    const unsigned long long gw = (unsigned long long)blockIdx.x * kBNW + warp;
+    const uint32_t w0 = (uint32_t)((E * gw) / Wn), w1 = (uint32_t)((E * (gw + 1)) / Wn);
+
+    auto flush = [&]() {
+      // rows (deferred on sink-free graphs), warp scan of the degrees, one
+      // 64-bit atomic for the queue position and the edge-prefix base
+      __syncwarp();
+      uint32_t run = 0;
+      for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        uint32_t d = 0;
+        if (i < qn) {
+          if (!g.sinks) {
+            const uint32_t rs = __ldg(g.ro + qv[i]);
+            d = __ldg(g.ro + qv[i] + 1) - rs;
+            qr[i] = rs;
+          } else {
+            d = qd[i];
+          }
         }
-        if (valid) {
-          const uint32_t v = pick3(w.fv, pc)[idx];
-          sm.es[nent + tid] = s;
-          sm.eb[nent + tid] = pick3(w.fr, pc)[idx];
-          sm.ev[nent + tid] = v;
-          sm.em[nent + tid] = Mc[v];
+        uint32_t x = d;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(FULL, x, o);
+          if (lane >= (uint32_t)o) x += y;
         }
-        const int cnt = __syncthreads_count(valid);
-        nent += (uint32_t)cnt;
-        if (cnt < kBB) break;
+        if (i < qn) qd[i] = run + x - d;
+        run += __shfl_sync(FULL, x, 31);
       }
-      // each warp walks a contiguous run of the tile's edges, 32 at a time:
-      // the lanes load 32 edges, then the warp relaxes them four at a time,
-      // one edge per 8-lane group.  Lane l8 of a group holds the eight
-      // consecutive sources 8*l8 .. 8*l8+7 of the 64-source group: one
-      // 32-byte sector of a distance row, read as two 16-byte vectors when
-      // the matrix allows it (VEC), and the lane's byte of the group's
-      // source mask.
-      const uint32_t wbeg = t0 + warp * kBWarpEdges;
-      const uint32_t g4 = lane >> 3, l8 = lane & 7;
-      const bool buckets = T != kInf;   // uniform
-      for (uint32_t r = 0; r < (uint32_t)kBWarpEdges; r += 32) {
-        const uint32_t gidx = wbeg + r + lane;
-        const bool valid = gidx < t1;
-        uint32_t jj = 0, vv = 0, ww = 0;
+      unsigned long long bse = 0;
+      if (lane == 0) bse = atomicAdd(&ctl->cnt[pn], ((unsigned long long)qn << 32) | run);
+      bse = __shfl_sync(FULL, bse, 0);
+      __syncwarp();
+      const uint32_t pos0 = (uint32_t)(bse >> 32), eb0 = (uint32_t)bse;
+      for (uint32_t i = lane; i < qn; i += 32) {
+        pick3(w.fv, pn)[pos0 + i] = qv[i];
+        pick3(w.fr, pn)[pos0 + i] = qr[i];
+        pick3(w.fs, pn)[pos0 + i] = eb0 + qd[i];
+      }
+      qn = 0;
+      __syncwarp();
+    };
+
+    if (w0 < w1) {   // warp-uniform
+      uint32_t j = warp_search_le(S, F, w0);
+      uint32_t ws = 0, wr = 0, wv = 0, wend = 0;
+      unsigned long long wm = 0ull;
+      auto load_window = [&]() {
+        const uint32_t idx = j + lane;
+        ws = 0xFFFFFFFFu;
+        wm = 0ull;
+        if (idx < F) {
+          ws = S[idx];
+          wr = R[idx];
+          wv = V[idx];
+          wm = Mc[wv];
+        }
+        wend = j + 32 < F ? S[j + 32] : E;   // first coordinate past the window
+      };
+      load_window();
+      uint32_t cur_j = 0xFFFFFFFFu, amask = 0u, dmax = 0u;
+      uint32_t du[8];   // the current source row, where amask has a bit
+      for (uint32_t b = w0; b < w1; b += 32) {
+        // slide until the window holds chunk [b, b+32) (at most two slides)
+        for (int guard = 0; guard < 4 && min(b + 31, w1 - 1) >= wend; ++guard) {
+          const unsigned le = __ballot_sync(FULL, ws <= b);
+          if (le == 0u) break;   // cannot happen while S[j] <= b holds
+          const uint32_t adv = (le == FULL && wend <= b) ? 32u : 31u - (uint32_t)__clz(le);
+          j += adv;
+          load_window();
+          cur_j = 0xFFFFFFFFu;   // window positions changed
+        }
+        // each lane loads one edge of the chunk and notes its window entry
+        const uint32_t gidx = b + lane;
+        uint32_t k = 0;
+#pragma unroll
+        for (int step = 16; step; step >>= 1) {
+          const uint32_t sv = __shfl_sync(FULL, ws, k + step);
+          if (sv <= gidx) k += step;
+        }
+        const uint32_t ks = __shfl_sync(FULL, ws, k);
+        const uint32_t kr = __shfl_sync(FULL, wr, k);
+        const uint32_t kn = __shfl_sync(FULL, ws, (k + 1) & 31u);
+        const uint32_t ke = k == 31 ? wend : kn;
+        // [ks, ke) holds gidx whenever S increases strictly; the test keeps
+        // every edge read inside the entry's row regardless
+        const bool valid = gidx < w1 && ks <= gidx && gidx < ke;
+        uint32_t vv = 0, ww = 0;
         if (valid) {
-          jj = smem_upper_bound_minus1(sm.es, nent, gidx);
-          const uint2 ed = load_edge<PK>(g.edges, sm.eb[jj] + (gidx - sm.es[jj]), wbits);
+          const uint2 ed = load_edge<PK>(g.edges, kr + (gidx - ks), wbits);
           vv = ed.x;
           ww = ed.y;
         }
-        const unsigned vm = __ballot_sync(0xFFFFFFFFu, valid);
-        if (!vm) break;
+        const unsigned vm = __ballot_sync(FULL, valid);
         const int nvalid = __popc(vm);   // valid edges are a prefix of the lanes
-        uint32_t cur_j = 0xFFFFFFFFu, amask = 0u, dmax = 0u;
-        uint32_t du[8];   // the current source row, where amask has a bit
         for (int i0 = 0; i0 < nvalid; i0 += 4) {
           const int i = i0 + (int)g4;
           const bool live = i < nvalid;
           const int isrc = live ? i : nvalid - 1;
-          const uint32_t ji = __shfl_sync(0xFFFFFFFFu, jj, isrc);
-          const uint32_t vi = __shfl_sync(0xFFFFFFFFu, vv, isrc);
-          const uint32_t wi = __shfl_sync(0xFFFFFFFFu, ww, isrc);
-          if (live && ji != cur_j) {   // uniform within the group
-            cur_j = ji;
-            amask = (uint32_t)(sm.em[ji] >> (8 * l8)) & 0xFFu;
-            load_row8<VEC>(dist + (size_t)sm.ev[ji] * K + col0 + 8 * l8, amask, du);
-            dmax = 0u;
+          const uint32_t ji = __shfl_sync(FULL, k, isrc);
+          const uint32_t vi = __shfl_sync(FULL, vv, isrc);
+          const uint32_t wi = __shfl_sync(FULL, ww, isrc);
+          const bool need = live && ji != cur_j;
+          if (__any_sync(FULL, need)) {
+            const uint32_t uu = __shfl_sync(FULL, wv, ji);
+            const uint32_t mlo = __shfl_sync(FULL, (uint32_t)wm, ji);
+            const uint32_t mhi = __shfl_sync(FULL, (uint32_t)(wm >> 32), ji);
+            if (need) {   // uniform within the group
+              cur_j = ji;
+              amask = ((l8 < 4 ? mlo : mhi) >> (8 * (l8 & 3))) & 0xFFu;
+              load_row8<VEC>(dist + (size_t)uu * K + col0 + 8 * l8, amask, du);
+              dmax = 0u;
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-              if ((amask >> q) & 1u) dmax = max(dmax, du[q]);
+              for (int q = 0; q < 8; ++q)
+                if ((amask >> q) & 1u) dmax = max(dmax, du[q]);
+            }
           }
           const uint32_t am = live ? amask : 0u;
           uint32_t* vrow = dist + (size_t)vi * K + col0 + 8 * l8;
@@ -282,7 +348,7 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
           uint32_t near = 0u, far = 0u, fm = kInf;
           // fast path: no buckets and no sum of this row can reach kInf (the
           // largest active source distance plus w fits), so plain adds suffice
-          if (!buckets && __all_sync(0xFFFFFFFFu, am == 0u || dmax < kInf - wi)) {
+          if (!buckets && __all_sync(FULL, am == 0u || dmax < kInf - wi)) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
               if ((am >> q) & 1u) {
@@ -315,17 +381,17 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
           // the group's 64-bit masks: OR of the lanes' bytes over the 8-lane group
           unsigned long long nmask = (unsigned long long)near << (8 * l8);
           unsigned long long fmask = (unsigned long long)far << (8 * l8);
-          if (__any_sync(0xFFFFFFFFu, near != 0u)) {   // most late relaxations improve nothing
+          if (__any_sync(FULL, near != 0u)) {   // most late relaxations improve nothing
 #pragma unroll
-            for (int o = 1; o < 8; o <<= 1) nmask |= __shfl_xor_sync(0xFFFFFFFFu, nmask, o);
+            for (int o = 1; o < 8; o <<= 1) nmask |= __shfl_xor_sync(FULL, nmask, o);
           }
           if (buckets) {   // uniform: only with buckets can anything be parked
-            const unsigned anyf = __ballot_sync(0xFFFFFFFFu, far != 0u);
+            const unsigned anyf = __ballot_sync(FULL, far != 0u);
             if (anyf) {
 #pragma unroll
-              for (int o = 1; o < 8; o <<= 1) fmask |= __shfl_xor_sync(0xFFFFFFFFu, fmask, o);
+              for (int o = 1; o < 8; o <<= 1) fmask |= __shfl_xor_sync(FULL, fmask, o);
 #pragma unroll
-              for (int o = 16; o; o >>= 1) fm = min(fm, __shfl_xor_sync(0xFFFFFFFFu, fm, o));
+              for (int o = 16; o; o >>= 1) fm = min(fm, __shfl_xor_sync(FULL, fm, o));
               if (lane == 0) atomicMin(&ctl->far_min, fm);
             }
           }
@@ -337,59 +403,45 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
         }
         // the chunk's appends, one edge per lane, their atomics in flight together
         __syncwarp();
+        bool app = false, fapp = false;
+        uint32_t vi = 0, rs = 0, re = 1;
         if (lane < (uint32_t)nvalid) {
           const unsigned long long nb = sm.pm[warp][lane], fb = sm.pf[warp][lane];
           if (nb | fb) {
-            const uint32_t vi = sm.pv[warp][lane];
+            vi = sm.pv[warp][lane];
             // vertices without out-edges are never appended; on a graph
-            // without such sinks the row is read at the tile's flush instead
-            uint32_t rs = 0, re = 1;
+            // without such sinks the row is read at the flush instead
             if (g.sinks) {
               rs = __ldg(g.ro + vi);
               re = __ldg(g.ro + vi + 1);
             }
             if (re > rs) {
-              if (nb && atomicOr(Mn + vi, nb) == 0ull) {
-                const uint32_t q = atomicAdd(&sm.qn, 1u);
-                sm.qv[q] = vi;
-                sm.qr[q] = rs;
-                sm.qd[q] = re - rs;
-              }
-              if (fb && atomicOr(w.fmask + vi, fb) == 0ull) {
-                const uint32_t pos = atomicAdd(&ctl->fcnt[fsel], 1u);
-                pick2(w.far_v, fsel)[pos] = vi;
-              }
+              app = nb && atomicOr(Mn + vi, nb) == 0ull;
+              fapp = fb && atomicOr(w.fmask + vi, fb) == 0ull;
             }
           }
         }
+        const unsigned ab = __ballot_sync(FULL, app);
+        if (ab) {
+          if (app) {
+            const uint32_t off = qn + __popc(ab & lt);
+            qv[off] = vi;
+            qr[off] = rs;
+            qd[off] = re - rs;
+          }
+          qn += __popc(ab);
+          if (qn > QW - 32) flush();
+        }
+        const unsigned fbal = __ballot_sync(FULL, fapp);
+        if (fbal) {   // far list: one atomic per warp
+          uint32_t pos = 0;
+          if (lane == 0) pos = atomicAdd(&ctl->fcnt[fsel], (uint32_t)__popc(fbal));
+          pos = __shfl_sync(FULL, pos, 0);
+          if (fapp) pick2(w.far_v, fsel)[pos + __popc(fbal & lt)] = vi;
+        }
         __syncwarp();
       }
-      // append this tile's new frontier vertices
-      __syncthreads();
-      const uint32_t qn = sm.qn;
-      if (qn) {
-        if (!g.sinks) {   // rows deferred from the appends
-          for (uint32_t i = tid; i < qn; i += kBB) {
-            const uint32_t rs = __ldg(g.ro + sm.qv[i]);
-            sm.qr[i] = rs;
-            sm.qd[i] = __ldg(g.ro + sm.qv[i] + 1) - rs;
-          }
-          __syncthreads();
-        }
-        const uint32_t tot = block_scan_excl<kBB>(sm.qd, qn, sm.wsum);
-        if (tid == 0) sm.base = atomicAdd(&ctl->cnt[pn], ((unsigned long long)qn << 32) | tot);
-        __syncthreads();
-        const uint32_t pos0 = (uint32_t)(sm.base >> 32), eb0 = (uint32_t)sm.base;
-        for (uint32_t i = tid; i < qn; i += kBB) {
-          pick3(w.fv, pn)[pos0 + i] = sm.qv[i];
-          pick3(w.fr, pn)[pos0 + i] = sm.qr[i];
-          pick3(w.fs, pn)[pos0 + i] = eb0 + sm.qd[i];
-        }
-        __syncthreads();
-        if (tid == 0) sm.qn = 0;
-      }
-      __syncthreads();
-      j = j + nent - 1;
+      if (qn) flush();
     }
   }
   if (ovf) sm.ovf = 1u;
