@@ -13,26 +13,28 @@
 //   dedup    an in-queue bitmap: a vertex is enqueued only if its bit was
 //            clear; the consumer clears it before reading dist[v], so any
 //            later improvement re-enqueues it.  At most n vertices are queued
-//            at once, so a ring of >= 2n slots never needs the producer wait
-//            in practice.
+//            at once.  A producer whose slot still holds the previous lap's
+//            item waits for it, and while it waits its warp takes the items
+//            at its own reserved positions, so no warp waits on itself.
 //   work     each warp reserves 32 consecutive positions, takes whichever
 //            arrive, and expands the taken vertices' edges together
 //            (warp-level merge-path over their degree prefix sums).
-//   stop     `pending` counts queued-or-running items: incremented before an
-//            item is published, decremented after it has been fully
-//            expanded.  pending == 0 can never become non-zero again, so a
-//            warp seeing it exits.
+//   stop     sharded counters: items published (counted before publishing)
+//            and items expanded (counted after expanding).  A warp reads all
+//            expanded shards, then all published shards; equal sums mean
+//            nothing is queued or running, which no later step can undo, so
+//            the warp exits.
 //   watchdog every wait is bounded by a %globaltimer budget; when it runs
 //            out the kernel raises `abort`, records GG_ERR_TIMEOUT and every
 //            warp returns.  Nothing spins without a limit.
 //   buckets  near-far priority without barriers: an improved vertex whose new
 //            distance is >= the threshold t_cur is parked in a far pile
-//            (deduplicated by a bitmap).  When nothing is queued or running
-//            (pending == 0), one idle warp raises the threshold and idle warps
-//            split the pile chunk by chunk: entries below the old threshold
-//            were expanded already and are dropped, entries below the new one
-//            are queued, the rest move to the other pile.  Termination:
-//            nothing queued or running, no split in progress, empty pile.
+//            (deduplicated by a bitmap).  When nothing is queued or running,
+//            one idle warp raises the threshold and idle warps split the
+//            pile chunk by chunk: entries below the old threshold were
+//            expanded already and are dropped, entries below the new one are
+//            queued, the rest move to the other pile.  Termination: nothing
+//            queued or running, no split in progress, empty pile.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,11 +43,20 @@
 
 namespace gg {
 
+constexpr int kAShards = 32;   // termination counter shards, one cache line each (one per lane)
+static_assert(kAShards == 32, "warp_quiescent reads one shard per lane");
+
 struct AsyncCtl {
   // the counters every warp updates live on cache lines of their own
   alignas(128) unsigned long long head;
   alignas(128) unsigned long long tail;
-  alignas(128) unsigned long long pending;
+  // termination counting, sharded over cache lines: a warp adds the items it
+  // publishes to pushed[its shard] before publishing them and the items it
+  // expanded to done[its shard] after expanding them; everything is drained
+  // when a read of all done shards followed by a read of all pushed shards
+  // gives equal sums (both only grow, and done never passes pushed)
+  alignas(128) unsigned long long pushed[kAShards * 16];
+  alignas(128) unsigned long long done[kAShards * 16];
   alignas(128) uint32_t far_cnt[2];
   alignas(128) uint32_t far_min;
   alignas(128) uint32_t split_cursor;
@@ -88,6 +99,29 @@ __device__ __forceinline__ bool past_watchdog(unsigned long long t_start, unsign
   return (long long)(globaltimer() - t_start) > (long long)limit;
 }
 
+__device__ __forceinline__ uint32_t shard_of_warp() {
+  return (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) % kAShards;
+}
+
+// Whole warp: true when every published item has been expanded.  All done
+// shards are read (and ordered by a fence and the warp barrier) before any
+// pushed shard.  Since done <= pushed at every instant and both only grow,
+// equal sums mean that at the moment between the two reads nothing was
+// queued or being expanded, and nothing can be published after that (only a
+// near-far split adds work, and splits are excluded by the caller).
+__device__ __forceinline__ bool warp_quiescent(const AsyncCtl* ctl, uint32_t lane) {
+  unsigned long long d = *(volatile const unsigned long long*)&ctl->done[16 * lane];
+  __threadfence();
+  __syncwarp();
+  unsigned long long p = *(volatile const unsigned long long*)&ctl->pushed[16 * lane];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    d += __shfl_xor_sync(0xFFFFFFFFu, d, o);
+    p += __shfl_xor_sync(0xFFFFFFFFu, p, o);
+  }
+  return d == p;
+}
+
 __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -99,9 +133,6 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
 }
 
 __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) { return *(volatile const uint32_t*)p; }
-__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
-  return *(volatile const unsigned long long*)p;
-}
 
 struct AsyncArgs {
   DevGraph g;
@@ -185,7 +216,7 @@ __device__ __forceinline__ void push_warp(const AsyncArgs& a, bool want, uint32_
   const uint32_t leader = __ffs(mm) - 1;
   unsigned long long base = 0;
   if (lane == leader) {
-    atomicAdd(&a.ctl->pending, (unsigned long long)cnt);
+    atomicAdd(&a.ctl->pushed[16 * shard_of_warp()], (unsigned long long)cnt);
     base = atomicAdd(&a.ctl->tail, (unsigned long long)cnt);
   }
   base = __shfl_sync(0xFFFFFFFFu, base, leader);
@@ -304,7 +335,7 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
       edges += got ? deg : 0;
       __threadfence();
       __syncwarp();
-      if (lane == 0) atomicAdd(&ctl->pending, (unsigned long long)(-(long long)__popc(gm)));
+      if (lane == 0) atomicAdd(&ctl->done[16 * shard_of_warp()], (unsigned long long)__popc(gm));
       if (ld_volatile_u32(&ctl->abort)) break;
     } else {
       // idle: re-poll the own reserved slots (distinct lines) most of the
@@ -316,7 +347,8 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
         backoff = min(backoff * 2, 1024u);
         continue;
       }
-      int act = 0;   // 0 back off, 1 stop, 2 split work
+      int act = 0;   // 0 back off, 1 stop, 2 split work, 3 split lock taken
+      uint32_t e1 = 0, ph = 0;
       if (lane == 0) {
         if (ld_volatile_u32(&ctl->abort)) {
           act = 1;
@@ -325,51 +357,64 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
           atomicExch(&ctl->abort, 1u);
           act = 1;
         } else {
-          const uint32_t e1 = ld_volatile_u32(&ctl->epoch);
-          const uint32_t ph = ld_volatile_u32(&ctl->phase);
-          if (ph == 2) {
-            act = 2;
-          } else if (ph == 0) {
-            const uint32_t nfar = ld_volatile_u32(&ctl->far_cnt[ld_volatile_u32(&ctl->sel)]);
-            const unsigned long long pend = ld_volatile_u64(&ctl->pending);
-            const uint32_t e2 = ld_volatile_u32(&ctl->epoch);
-            if (pend == 0ull && e1 == e2 && ld_volatile_u32(&ctl->phase) == 0) {
-              if (nfar == 0) {
-                act = 1;   // nothing queued, running or parked: done
-              } else if (atomicCAS(&ctl->phase, 0u, 1u) == 0u) {
-                // start a split; no work may be in flight (re-checked under the lock)
-                __threadfence();
-                const uint32_t src = ctl->sel;
-                const uint32_t total = ld_volatile_u32(&ctl->far_cnt[src]);
-                if (ld_volatile_u64(&ctl->pending) != 0ull || total == 0) {
-                  atomicExch(&ctl->phase, 0u);
-                } else {
-                  const unsigned long long t1 = (unsigned long long)ctl->t_cur + ctl->delta;
-                  const unsigned long long t2 = (unsigned long long)ctl->far_min + 1;
-                  const unsigned long long tn = t1 > t2 ? t1 : t2;
-                  ctl->t_prev = ctl->t_cur;
-                  ctl->t_cur = tn >= kInf ? kInf : (uint32_t)tn;
-                  ctl->far_min = kInf;
-                  ctl->split_src = src;
-                  ctl->split_total = total;
-                  ctl->split_cursor = 0;
-                  ctl->split_done = 0;
-                  ctl->sel = src ^ 1u;
-                  const uint32_t ep = ctl->epoch;
-                  if (ctl->trace && ep < ctl->trace_cap) {
-                    uint32_t* t = ctl->trace + 4ull * ep;
-                    t[0] = ep;
-                    t[1] = ctl->t_cur;
-                    t[2] = total;
-                    const long long el = (long long)(globaltimer() - ctl->t_start);
-                    t[3] = el > 0 ? (uint32_t)(el / 1000) : 0u;
-                  }
-                  ctl->epoch = ep + 1;
-                  __threadfence();
-                  atomicExch(&ctl->phase, 2u);
-                  act = 2;
-                }
+          e1 = ld_volatile_u32(&ctl->epoch);
+          ph = ld_volatile_u32(&ctl->phase);
+          if (ph == 2) act = 2;
+        }
+      }
+      act = __shfl_sync(0xFFFFFFFFu, act, 0);
+      ph = __shfl_sync(0xFFFFFFFFu, ph, 0);
+      if (act == 0 && ph == 0) {
+        // quiescence is read between two reads of the split epoch, so no
+        // split can have started and ended unseen in between
+        const bool quiet = warp_quiescent(ctl, lane);
+        if (lane == 0 && quiet) {
+          const uint32_t nfar = ld_volatile_u32(&ctl->far_cnt[ld_volatile_u32(&ctl->sel)]);
+          const uint32_t e2 = ld_volatile_u32(&ctl->epoch);
+          if (e1 == e2 && ld_volatile_u32(&ctl->phase) == 0) {
+            if (nfar == 0) {
+              act = 1;   // nothing queued, running or parked: done
+            } else if (atomicCAS(&ctl->phase, 0u, 1u) == 0u) {
+              act = 3;
+            }
+          }
+        }
+        act = __shfl_sync(0xFFFFFFFFu, act, 0);
+        if (act == 3) {
+          // split lock held: start a split if still nothing is in flight
+          __threadfence();
+          const bool still = warp_quiescent(ctl, lane);
+          if (lane == 0) {
+            const uint32_t src = ctl->sel;
+            const uint32_t total = ld_volatile_u32(&ctl->far_cnt[src]);
+            if (!still || total == 0) {
+              atomicExch(&ctl->phase, 0u);
+              act = 0;
+            } else {
+              const unsigned long long t1 = (unsigned long long)ctl->t_cur + ctl->delta;
+              const unsigned long long t2 = (unsigned long long)ctl->far_min + 1;
+              const unsigned long long tn = t1 > t2 ? t1 : t2;
+              ctl->t_prev = ctl->t_cur;
+              ctl->t_cur = tn >= kInf ? kInf : (uint32_t)tn;
+              ctl->far_min = kInf;
+              ctl->split_src = src;
+              ctl->split_total = total;
+              ctl->split_cursor = 0;
+              ctl->split_done = 0;
+              ctl->sel = src ^ 1u;
+              const uint32_t ep = ctl->epoch;
+              if (ctl->trace && ep < ctl->trace_cap) {
+                uint32_t* t = ctl->trace + 4ull * ep;
+                t[0] = ep;
+                t[1] = ctl->t_cur;
+                t[2] = total;
+                const long long el = (long long)(globaltimer() - ctl->t_start);
+                t[3] = el > 0 ? (uint32_t)(el / 1000) : 0u;
               }
+              ctl->epoch = ep + 1;
+              __threadfence();
+              atomicExch(&ctl->phase, 2u);
+              act = 2;
             }
           }
         }
@@ -470,14 +515,17 @@ __global__ void k_async_seed(DevGraph g, uint32_t src, uint32_t* dist, unsigned 
   ctl->dist = dist;
   ctl->watchdog_ns = watchdog_ns;
   ctl->t_start = globaltimer();
+  for (int i = 0; i < kAShards; ++i) {
+    ctl->pushed[16 * i] = 0ull;
+    ctl->done[16 * i] = 0ull;
+  }
   if (g.ro[src + 1] > g.ro[src]) {
     Q[0] = (1ull << 32) | src;
     inq[src >> 5] = 1u << (src & 31);
     ctl->tail = 1;
-    ctl->pending = 1;
+    ctl->pushed[0] = 1ull;
   } else {
     ctl->tail = 0;
-    ctl->pending = 0;
   }
 }
 

@@ -64,7 +64,7 @@ constexpr int kBCap = kBTile + 1;
 constexpr uint32_t kBQW = 128;   // per-warp queue slots of the warp-streaming relaxation
 static_assert(kBNW * kBQW <= (uint32_t)kBCap, "per-warp queues fit the CTA queue arrays");
 #ifndef GG_BMINB
-#define GG_BMINB 5   // resident CTAs per SM the batch superstep is compiled for (48 registers)
+#define GG_BMINB 6   // resident CTAs per SM the batch superstep is compiled for (40 registers)
 #endif
 
 struct BSmem {
