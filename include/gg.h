@@ -79,6 +79,19 @@ typedef enum {
 #define GG_NO_VALIDATE 0x4u   /* skip the structural checks (offsets, col < n)     */
 #define GG_NO_PACK     0x8u   /* keep 8-byte {col, weight} edges even when the
                                  4-byte packed form (col << wbits | weight) fits  */
+#define GG_FLOAT_WEIGHTS 0x10u /* weights are IEEE-754 binary32 bit patterns, as the
+                                 paper's float weights (Listing 1, Listing 4): each
+                                 must be finite and >= +0.0 (-0.0, negatives, inf
+                                 and NaN are rejected unless GG_NO_VALIDATE).
+                                 gg_sssp / gg_sssp_ex then write binary32 distance
+                                 bit patterns: dist[src] = +0.0, each relaxation
+                                 computes the round-to-nearest float sum
+                                 dist[u] + w, unreached = FLT_MAX (0x7F7FFFFF, the
+                                 paper's initial value), and a sum that rounds to
+                                 +inf never improves a distance.  Near-far buckets
+                                 are not used (delta is ignored).  Batched,
+                                 multi-graph and server calls return
+                                 GG_ERR_NOT_SUPPORTED for such a graph. */
 
 /* Execution policy: the paper's execution::par / execution::par_nosync
  * (Sec. III-A; Listing 3 and the "Timing Model and Parallelism" box). */
@@ -200,6 +213,19 @@ gg_status gg_sssp(gg_graph_t g, uint32_t src, uint32_t* dist_out, cudaStream_t s
 /* As gg_sssp with explicit options (opt may be NULL for the defaults). */
 gg_status gg_sssp_ex(gg_graph_t g, uint32_t src, uint32_t* dist_out, const gg_options* opt,
                      cudaStream_t stream);
+
+/* Breadth-first search: a second vertex program on the same operators,
+ * frontiers and loop.  Sec. III-C makes the operator's work a user program
+ * applied to each {source, destination, edge}; here that program counts every
+ * edge as 1, so depth_out[v] = the fewest edges on a path src -> v (u32;
+ * depth_out[src] = 0; unreachable = 0xFFFFFFFF), whatever the graph's weights
+ * (u32 or binary32).
+ *   depth_out  device u32[n], caller-owned; valid once `stream` completes
+ * gg_bfs_ex honours the same options as gg_sssp_ex (policy, direction,
+ * load balance, stats, trace, watchdog); delta is ignored.  Errors as
+ * gg_sssp_ex. */
+gg_status gg_bfs(gg_graph_t g, uint32_t src, uint32_t* depth_out, cudaStream_t stream);
+gg_status gg_bfs_ex(gg_graph_t g, uint32_t src, uint32_t* depth_out, const gg_options* opt, cudaStream_t stream);
 
 /* ---- autotuning ----------------------------------------------------------- */
 

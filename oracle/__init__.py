@@ -18,8 +18,12 @@ closed forms in ``tests/test_oracle_pins.py``: Floyd-Warshall brute force
 Bellman-Ford rounds (``bellman_ford``), grid/path/star closed forms and the
 shortest-path invariants (``check``).
 
-Readings of the paper used here (the paper's listing uses float weights;
-this library fixes uint32 weights and distances):
+The paper's own float variant is ``dijkstra_f32`` (and ``bellman_ford_f32``):
+binary32 weights, one rounded single-precision addition per relaxation,
+unreached = FLT_MAX as in the paper's initialisation; results are the
+distances' bit patterns.
+
+Readings of the paper used by the uint32 functions:
 
 * distances are uint32, accumulated in uint64 inside the oracle, and
   0xFFFFFFFF means unreachable; a finite distance that does not fit is an
@@ -77,6 +81,10 @@ def _load():
             lib.oracle_bfs_hops.argtypes = [u32, P, P, u32, P]
             lib.oracle_check.restype = ctypes.c_int
             lib.oracle_check.argtypes = [u32, P, P, P, u32, P, P]
+            lib.oracle_dijkstra_f32.restype = ctypes.c_int
+            lib.oracle_dijkstra_f32.argtypes = [u32, P, P, P, u32, P]
+            lib.oracle_bellman_ford_f32.restype = ctypes.c_int
+            lib.oracle_bellman_ford_f32.argtypes = [u32, P, P, P, u32, P, P]
             lib.oracle_dijkstra_many.restype = ctypes.c_int
             lib.oracle_dijkstra_many.argtypes = [u32, P, P, P, P, u32, P, u32]
             _lib = lib
@@ -145,6 +153,33 @@ def bellman_ford(ro, col, w, src: int):
     dist = np.empty(n, np.uint32)
     rounds = ctypes.c_uint32(0)
     _rc(_load().oracle_bellman_ford(n, _p(ro), _p(col), _p(w), src, _p(dist), ctypes.byref(rounds)))
+    return dist, int(rounds.value)
+
+
+FLT_MAX_BITS = 0x7F7FFFFF   # "unreached" for binary32 distances (the paper's initial FLT_MAX)
+
+
+def _f32_bits(w) -> np.ndarray:
+    w = np.asarray(w)
+    return np.ascontiguousarray(w.view(np.uint32) if w.dtype == np.float32 else w, dtype=np.uint32)
+
+
+def dijkstra_f32(ro, col, w, src: int) -> np.ndarray:
+    """The paper's float variant: binary32 weights (float32 array or its
+    uint32 bit patterns), one rounded float addition per relaxation; returns
+    the distances' bit patterns (uint32; FLT_MAX_BITS = unreached)."""
+    n, ro, col, wb = _graph(ro, col, _f32_bits(w))
+    dist = np.empty(n, np.uint32)
+    _rc(_load().oracle_dijkstra_f32(n, _p(ro), _p(col), _p(wb), src, _p(dist)))
+    return dist
+
+
+def bellman_ford_f32(ro, col, w, src: int):
+    """(distance bit patterns, productive rounds) by Bellman-Ford rounds over binary32."""
+    n, ro, col, wb = _graph(ro, col, _f32_bits(w))
+    dist = np.empty(n, np.uint32)
+    rounds = ctypes.c_uint32(0)
+    _rc(_load().oracle_bellman_ford_f32(n, _p(ro), _p(col), _p(wb), src, _p(dist), ctypes.byref(rounds)))
     return dist, int(rounds.value)
 
 

@@ -30,6 +30,19 @@
  *   oracle_check          the invariants that characterise shortest-path
  *                         distances for positive weights.
  *
+ * The paper's own listing keeps float weights and distances, initialised to
+ * the largest float (Listings 1 and 4).  That variant is here too:
+ *
+ *   oracle_dijkstra_f32     the same Dijkstra over IEEE binary32: each
+ *                           relaxation is the single-precision sum d[u] + w
+ *                           (round to nearest) and unreached is FLT_MAX;
+ *   oracle_bellman_ford_f32 Bellman-Ford rounds with the same float sums.
+ *
+ * Because w >= 0 makes  x -> fl(x + w)  non-decreasing and never below x,
+ * both reach the least fixed point of d[v] = min(d[v], fl(d[u] + w)) from
+ * d[src] = +0, d[else] = FLT_MAX, which is  min(FLT_MAX, the smallest
+ * left-to-right rounded sum over the paths src ~> v).
+ *
  * Types: vertex ids, CSR offsets and weights are uint32.  Distances are
  * accumulated in uint64, so the oracle cannot overflow, and stored as uint32
  * with 0xFFFFFFFF meaning unreachable.  A finite distance >= 0xFFFFFFFF
@@ -40,6 +53,7 @@
 #include <string.h>
 #include <pthread.h>
 #include <time.h>
+#include <float.h>
 
 #define OR_EXPORT __attribute__((visibility("default")))
 #define OR_INF32 0xFFFFFFFFu
@@ -205,6 +219,127 @@ OR_EXPORT int oracle_bellman_ford(uint32_t n, const uint32_t* row_offsets, const
     if (rounds_out) *rounds_out = rounds;
     free(d); free(nd);
     return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* IEEE binary32 variant (the paper's float weights).  Weights and output   */
+/* distances are passed as their bit patterns (uint32); every weight must   */
+/* be a finite float >= +0.0.  Arithmetic is plain C float: one rounded     */
+/* single-precision addition per relaxation.                                */
+/* ------------------------------------------------------------------------- */
+
+static float f32_of(uint32_t bits) { float f; memcpy(&f, &bits, 4); return f; }
+static uint32_t bits_of(float f) { uint32_t b; memcpy(&b, &f, 4); return b; }
+
+static int f32_weights_ok(uint32_t n, const uint32_t* row_offsets, const uint32_t* weights) {
+    for (uint32_t e = 0; e < row_offsets[n]; ++e) {
+        float w = f32_of(weights[e]);
+        if (!(w >= 0.0f) || w > FLT_MAX || (weights[e] >> 31)) return 0;   /* NaN, negative, -0, inf */
+    }
+    return 1;
+}
+
+/* Binary min-heap of (float distance, vertex), lazy deletion. */
+typedef struct { float d; uint32_t v; } fheap_item;
+typedef struct { fheap_item* a; uint64_t size, cap; } fheap_t;
+
+static int fheap_push(fheap_t* h, float d, uint32_t v) {
+    if (h->size == h->cap) {
+        uint64_t nc = h->cap ? h->cap * 2 : 1024;
+        fheap_item* na = (fheap_item*)realloc(h->a, nc * sizeof(fheap_item));
+        if (!na) return -1;
+        h->a = na; h->cap = nc;
+    }
+    uint64_t i = h->size++;
+    while (i > 0) {
+        uint64_t p = (i - 1) / 2;
+        if (h->a[p].d <= d) break;
+        h->a[i] = h->a[p];
+        i = p;
+    }
+    h->a[i].d = d; h->a[i].v = v;
+    return 0;
+}
+
+static fheap_item fheap_pop(fheap_t* h) {
+    fheap_item top = h->a[0];
+    fheap_item last = h->a[--h->size];
+    uint64_t i = 0;
+    for (;;) {
+        uint64_t l = 2 * i + 1, r = l + 1, s = i;
+        float sd = last.d;
+        if (l < h->size && h->a[l].d < sd) { s = l; sd = h->a[l].d; }
+        if (r < h->size && h->a[r].d < sd) { s = r; }
+        if (s == i) break;
+        h->a[i] = h->a[s];
+        i = s;
+    }
+    if (h->size) h->a[i] = last;
+    return top;
+}
+
+/* Dijkstra over binary32: dist_bits[v] = bits of min(FLT_MAX, smallest
+ * rounded path sum); an edge relaxation that rounds to +inf improves nothing. */
+OR_EXPORT int oracle_dijkstra_f32(uint32_t n, const uint32_t* row_offsets, const uint32_t* cols,
+                                  const uint32_t* weight_bits, uint32_t src, uint32_t* dist_bits) {
+    if (src >= n || !row_offsets || !dist_bits) return ORACLE_ERR_ARG;
+    if (!f32_weights_ok(n, row_offsets, weight_bits)) return ORACLE_ERR_ARG;
+    float* d = (float*)malloc(sizeof(float) * n);
+    unsigned char* done = (unsigned char*)calloc(n, 1);
+    fheap_t h = {0, 0, 0};
+    if (!d || !done) { free(d); free(done); return ORACLE_ERR_NOMEM; }
+    for (uint32_t v = 0; v < n; ++v) d[v] = FLT_MAX;
+    d[src] = 0.0f;
+    if (fheap_push(&h, 0.0f, src)) { free(d); free(done); return ORACLE_ERR_NOMEM; }
+    while (h.size) {
+        fheap_item it = fheap_pop(&h);
+        uint32_t u = it.v;
+        if (done[u] || it.d != d[u]) continue;      /* stale entry */
+        done[u] = 1;
+        for (uint32_t e = row_offsets[u]; e < row_offsets[u + 1]; ++e) {
+            uint32_t v = cols[e];
+            volatile float nd = d[u] + f32_of(weight_bits[e]);   /* one rounded float addition */
+            if (nd < d[v]) {
+                d[v] = nd;
+                if (fheap_push(&h, nd, v)) { free(h.a); free(d); free(done); return ORACLE_ERR_NOMEM; }
+            }
+        }
+    }
+    for (uint32_t v = 0; v < n; ++v) dist_bits[v] = bits_of(d[v]);
+    free(h.a); free(d); free(done);
+    return ORACLE_OK;
+}
+
+/* Bellman-Ford rounds over binary32 (a second algorithm for the same fixed point). */
+OR_EXPORT int oracle_bellman_ford_f32(uint32_t n, const uint32_t* row_offsets, const uint32_t* cols,
+                                      const uint32_t* weight_bits, uint32_t src, uint32_t* dist_bits,
+                                      uint32_t* rounds_out) {
+    if (src >= n) return ORACLE_ERR_ARG;
+    if (!f32_weights_ok(n, row_offsets, weight_bits)) return ORACLE_ERR_ARG;
+    float* d = (float*)malloc(sizeof(float) * n);
+    float* nd = (float*)malloc(sizeof(float) * n);
+    if (!d || !nd) { free(d); free(nd); return ORACLE_ERR_NOMEM; }
+    for (uint32_t v = 0; v < n; ++v) d[v] = FLT_MAX;
+    d[src] = 0.0f;
+    uint32_t rounds = 0;
+    for (;;) {
+        memcpy(nd, d, sizeof(float) * n);
+        int changed = 0;
+        for (uint32_t u = 0; u < n; ++u) {
+            if (d[u] == FLT_MAX) continue;   /* never reached: relaxes nothing */
+            for (uint32_t e = row_offsets[u]; e < row_offsets[u + 1]; ++e) {
+                volatile float c = d[u] + f32_of(weight_bits[e]);
+                if (c < nd[cols[e]]) { nd[cols[e]] = c; changed = 1; }
+            }
+        }
+        float* t = d; d = nd; nd = t;
+        if (!changed) break;
+        ++rounds;
+    }
+    for (uint32_t v = 0; v < n; ++v) dist_bits[v] = bits_of(d[v]);
+    if (rounds_out) *rounds_out = rounds;
+    free(d); free(nd);
+    return ORACLE_OK;
 }
 
 /* ------------------------------------------------------------------------- */

@@ -22,6 +22,7 @@ __all__ = [
     "GG_POLICY_BSP_GRAPH", "GG_POLICY_ASYNC_PERSISTENT", "GG_POLICY_BSP_HOST", "GG_POLICY_BSP_PERSISTENT",
     "GG_DIR_AUTO", "GG_DIR_PUSH", "GG_DIR_PULL", "GG_LB_AUTO", "GG_LB_MERGE_PATH", "GG_LB_BINS", "GG_LB_WARP", "GG_DELTA_NONE",
     "gg_graph_create_csr", "gg_graph_destroy", "gg_graph_info", "gg_graph_check", "gg_sssp", "gg_sssp_ex",
+    "gg_bfs", "gg_bfs_ex", "GG_FLOAT_WEIGHTS", "GG_FLT_MAX_BITS",
     "gg_sssp_batch", "gg_sssp_multi", "Server",
     "gg_status_string", "gg_last_error", "gg_abi_version", "gg_sssp_noalloc", "GG_NOALLOC_MAX_VERTICES",
     "Graph", "lib_path", "load",
@@ -33,7 +34,8 @@ _lib = None
 _lock = threading.Lock()
 
 GG_INF = 0xFFFFFFFF
-GG_DEVICE_PTRS, GG_SYMMETRIC, GG_NO_VALIDATE, GG_NO_PACK = 0x1, 0x2, 0x4, 0x8
+GG_DEVICE_PTRS, GG_SYMMETRIC, GG_NO_VALIDATE, GG_NO_PACK, GG_FLOAT_WEIGHTS = 0x1, 0x2, 0x4, 0x8, 0x10
+GG_FLT_MAX_BITS = 0x7F7FFFFF   # "unreached" for binary32 distances (FLT_MAX)
 GG_POLICY_BSP_GRAPH, GG_POLICY_ASYNC_PERSISTENT, GG_POLICY_BSP_HOST, GG_POLICY_BSP_PERSISTENT = 0, 1, 2, 3
 GG_DIR_AUTO, GG_DIR_PUSH, GG_DIR_PULL = 0, 1, 2
 GG_LB_AUTO, GG_LB_MERGE_PATH, GG_LB_BINS, GG_LB_WARP = 0, 1, 2, 3
@@ -111,6 +113,8 @@ def load():
             "gg_options_default": (None, [ctypes.POINTER(gg_options)]),
             "gg_sssp": (ctypes.c_int, [vp, u32, vp, vp]),
             "gg_sssp_ex": (ctypes.c_int, [vp, u32, vp, ctypes.POINTER(gg_options), vp]),
+            "gg_bfs": (ctypes.c_int, [vp, u32, vp, vp]),
+            "gg_bfs_ex": (ctypes.c_int, [vp, u32, vp, ctypes.POINTER(gg_options), vp]),
             "gg_sssp_noalloc": (ctypes.c_int, [u32, u64, vp, vp, vp, u32, vp, vp]),
             "gg_sssp_batch": (ctypes.c_int, [vp, P32, u32, vp, vp]),
             "gg_sssp_batch_ex": (ctypes.c_int, [vp, P32, u32, vp, ctypes.POINTER(gg_options), vp]),
@@ -179,10 +183,13 @@ def gg_abi_version() -> int:
 
 
 def gg_graph_create_csr(row_offsets, col_indices, weights, symmetric: bool = False, validate: bool = True,
-                        stream=None, pack: bool = True) -> int:
+                        stream=None, pack: bool = True, float_weights: bool = False) -> int:
     """Handle (int) for a CSR given as numpy arrays (host) or CUDA tensors
-    (device).  All three must live on the same side."""
+    (device).  All three must live on the same side.  float_weights: the
+    weights are IEEE binary32 (a float32 array is passed by its bit pattern)."""
     lib = load()
+    if float_weights and isinstance(weights, np.ndarray) and weights.dtype == np.float32:
+        weights = weights.view(np.uint32)
     ro, ro_dev = _ptr(row_offsets)
     col, col_dev = _ptr(col_indices)
     w, w_dev = _ptr(weights)
@@ -193,7 +200,8 @@ def gg_graph_create_csr(row_offsets, col_indices, weights, symmetric: bool = Fal
     if int(weights.shape[0]) != m:
         raise ValueError("weights and col_indices differ in length")
     flags = ((GG_DEVICE_PTRS if ro_dev else 0) | (GG_SYMMETRIC if symmetric else 0) |
-             (0 if validate else GG_NO_VALIDATE) | (0 if pack else GG_NO_PACK))
+             (0 if validate else GG_NO_VALIDATE) | (0 if pack else GG_NO_PACK) |
+             (GG_FLOAT_WEIGHTS if float_weights else 0))
     h = ctypes.c_void_p()
     _check(lib.gg_graph_create_csr(n, m, ro, col if m else None, w if m else None, flags,
                                    _stream_ptr(stream) if (stream is not None or ro_dev) else 0,
@@ -248,6 +256,17 @@ def gg_sssp_ex(handle: int, src: int, dist_out, options: gg_options | None = Non
         raise ValueError("dist_out must be a CUDA tensor")
     _check(load().gg_sssp_ex(handle, src, p, ctypes.byref(options) if options is not None else None,
                              _stream_ptr(stream)), "gg_sssp_ex")
+
+
+def gg_bfs(handle: int, src: int, depth_out, stream=None, options: gg_options | None = None):
+    """Hop counts from src into depth_out (CUDA uint32 tensor of n), async."""
+    p, dev = _ptr(depth_out)
+    if not dev:
+        raise ValueError("depth_out must be a CUDA tensor")
+    if options is None:
+        _check(load().gg_bfs(handle, src, p, _stream_ptr(stream)), "gg_bfs")
+    else:
+        _check(load().gg_bfs_ex(handle, src, p, ctypes.byref(options), _stream_ptr(stream)), "gg_bfs_ex")
 
 
 def gg_sssp_batch(handle: int, srcs, dist_out, stream=None, options: gg_options | None = None):
@@ -377,9 +396,19 @@ class Graph:
     """Owning wrapper of a gg_graph_t."""
 
     def __init__(self, row_offsets, col_indices, weights, symmetric: bool = False, validate: bool = True,
-                 stream=None, pack: bool = True):
-        self.handle = gg_graph_create_csr(row_offsets, col_indices, weights, symmetric, validate, stream, pack)
+                 stream=None, pack: bool = True, float_weights: bool = False):
+        self.handle = gg_graph_create_csr(row_offsets, col_indices, weights, symmetric, validate, stream, pack,
+                                          float_weights)
         self.n, self.m, _ = gg_graph_info(self.handle)
+        self.float_weights = float_weights
+
+    def bfs(self, src: int, depth_out=None, stream=None, **opts):
+        """Hop counts from src (uint32 CUDA tensor; unreachable = GG_INF)."""
+        import torch
+        if depth_out is None:
+            depth_out = torch.empty(self.n, dtype=torch.uint32, device="cuda")
+        gg_bfs(self.handle, src, depth_out, stream, make_options(**opts) if opts else None)
+        return depth_out
 
     def sssp(self, src: int, dist_out=None, stream=None, **opts):
         import torch

@@ -108,7 +108,7 @@ gg_status gg_graph_create_csr(uint32_t n, uint64_t m, const uint32_t* row_offset
   if (m >= 0xFFFFFFFFull) return fail(GG_ERR_INVALID_ARG, "m must be < 2^32 - 1 (uint32 row offsets)");
   if (!row_offsets) return fail(GG_ERR_INVALID_ARG, "row_offsets is NULL");
   if (m > 0 && (!col_indices || !weights)) return fail(GG_ERR_INVALID_ARG, "col_indices/weights is NULL");
-  if (flags & ~(GG_DEVICE_PTRS | GG_SYMMETRIC | GG_NO_VALIDATE | GG_NO_PACK))
+  if (flags & ~(GG_DEVICE_PTRS | GG_SYMMETRIC | GG_NO_VALIDATE | GG_NO_PACK | GG_FLOAT_WEIGHTS))
     return fail(GG_ERR_INVALID_ARG, "unknown flag");
   gg_graph* g = new (std::nothrow) gg_graph();
   if (!g) return fail(GG_ERR_OUT_OF_MEMORY, "host allocation failed");
@@ -197,7 +197,11 @@ gg_status gg_graph_check(gg_graph_t g) {
   return r;
 }
 
-gg_status gg_sssp_ex(gg_graph_t g, uint32_t src, uint32_t* dist_out, const gg_options* opt, cudaStream_t stream) {
+namespace {
+
+// One single-source run in the given weight mode (WM_U32 / WM_F32 / WM_UNIT).
+gg_status run_single(gg_graph_t g, uint32_t src, uint32_t* dist_out, const gg_options* opt, cudaStream_t stream,
+                     uint32_t wmode) {
   if (!g) return fail(GG_ERR_INVALID_ARG, "graph is NULL");
   if (!dist_out) return fail(GG_ERR_INVALID_ARG, "dist_out is NULL");
   if (src >= g->n) return fail(GG_ERR_INVALID_ARG, "src >= n");
@@ -217,8 +221,8 @@ gg_status gg_sssp_ex(gg_graph_t g, uint32_t src, uint32_t* dist_out, const gg_op
   std::lock_guard<std::mutex> lk(g->mu);
   gg_status st = order_after_previous(g, stream);
   if (st != GG_OK) return st;
-  if (o.policy == GG_POLICY_ASYNC_PERSISTENT) st = async_run(g, src, dist_out, o, stream);
-  else st = bsp_run(g, src, dist_out, o, stream);
+  if (o.policy == GG_POLICY_ASYNC_PERSISTENT) st = async_run(g, src, dist_out, o, stream, wmode);
+  else st = bsp_run(g, src, dist_out, o, stream, wmode);
   if (st != GG_OK) return st;
   g->last_policy = (int)o.policy;
   st = record_call(g, stream);
@@ -232,8 +236,22 @@ gg_status gg_sssp_ex(gg_graph_t g, uint32_t src, uint32_t* dist_out, const gg_op
   return GG_OK;
 }
 
+}  // namespace
+
+gg_status gg_sssp_ex(gg_graph_t g, uint32_t src, uint32_t* dist_out, const gg_options* opt, cudaStream_t stream) {
+  return run_single(g, src, dist_out, opt, stream, g && g->float_weights ? WM_F32 : WM_U32);
+}
+
 gg_status gg_sssp(gg_graph_t g, uint32_t src, uint32_t* dist_out, cudaStream_t stream) {
   return gg_sssp_ex(g, src, dist_out, nullptr, stream);
+}
+
+gg_status gg_bfs_ex(gg_graph_t g, uint32_t src, uint32_t* depth_out, const gg_options* opt, cudaStream_t stream) {
+  return run_single(g, src, depth_out, opt, stream, WM_UNIT);
+}
+
+gg_status gg_bfs(gg_graph_t g, uint32_t src, uint32_t* depth_out, cudaStream_t stream) {
+  return gg_bfs_ex(g, src, depth_out, nullptr, stream);
 }
 
 gg_status gg_sssp_batch_ex(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t* dist_out,
@@ -241,6 +259,7 @@ gg_status gg_sssp_batch_ex(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint3
   if (!g) return fail(GG_ERR_INVALID_ARG, "graph is NULL");
   if (!srcs || !dist_out) return fail(GG_ERR_INVALID_ARG, "srcs/dist_out is NULL");
   if (k == 0) return fail(GG_ERR_INVALID_ARG, "k must be >= 1");
+  if (g->float_weights) return fail(GG_ERR_NOT_SUPPORTED, "binary32 weights: gg_sssp, gg_sssp_ex and gg_bfs only");
   for (uint32_t i = 0; i < k; ++i)
     if (srcs[i] >= g->n) return fail(GG_ERR_INVALID_ARG, "a source is >= n");
   gg_options o;

@@ -79,6 +79,7 @@ struct AsyncCtl {
   uint32_t* bm_far;
   uint32_t* trace;         // per split: split number, new threshold, pile size, microseconds since start
   uint32_t trace_cap;
+  uint32_t wmode;          // WM_*: how relaxations add edge weights
 };
 
 namespace {
@@ -265,6 +266,7 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   AsyncCtl* ctl = a.ctl;
   uint32_t* dist = ctl->dist;
+  const uint32_t wmode = ctl->wmode;
   Taker tk{0ull, 0u, false, false};
   uint32_t backoff = 32, idle_rounds = 0;
   unsigned long long pops = 0, edges = 0;
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
           }
           const uint32_t k = lo - 1;
           const uint2 ed = load_edge<PK>(a.g.edges, s_row[wid][k] + (gidx - s_pref[wid][k]), a.g.wbits);
-          const uint32_t nd = add_sat(s_du[wid][k], ed.y, ovf);
+          const uint32_t nd = relax_add(s_du[wid][k], ed.y, ovf, wmode);
           dst = ed.x;
           ndv = nd;
           if (nd < ld_cg(dist + dst)) {
@@ -475,10 +477,10 @@ __global__ void __launch_bounds__(kABlock) k_async(AsyncArgs a) {
   }
 }
 
-__global__ void k_async_init(DevGraph g, uint32_t* dist, uint32_t* inq, uint32_t* bm_far) {
+__global__ void k_async_init(DevGraph g, uint32_t* dist, uint32_t* inq, uint32_t* bm_far, uint32_t unreached) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  for (uint64_t i = t; i < g.n; i += stride) dist[i] = kInf;
+  for (uint64_t i = t; i < g.n; i += stride) dist[i] = unreached;
   for (uint64_t i = t; i < g.nwords; i += stride) {
     inq[i] = 0u;
     bm_far[i] = 0u;
@@ -487,7 +489,8 @@ __global__ void k_async_init(DevGraph g, uint32_t* dist, uint32_t* inq, uint32_t
 
 __global__ void k_async_seed(DevGraph g, uint32_t src, uint32_t* dist, unsigned long long* Q, uint32_t* inq,
                              AsyncCtl* ctl, unsigned long long watchdog_ns, uint32_t delta, uint32_t* far0,
-                             uint32_t* far1, uint32_t* bm_far, uint32_t* trace, uint32_t trace_cap) {
+                             uint32_t* far1, uint32_t* bm_far, uint32_t* trace, uint32_t trace_cap,
+                             uint32_t wmode) {
   dist[src] = 0u;
   ctl->t_cur = delta;
   ctl->t_prev = 0;
@@ -500,6 +503,7 @@ __global__ void k_async_seed(DevGraph g, uint32_t src, uint32_t* dist, unsigned 
   ctl->epoch = 0;
   ctl->trace = trace;
   ctl->trace_cap = trace ? trace_cap : 0u;
+  ctl->wmode = wmode;
   ctl->split_src = 0;
   ctl->split_total = 0;
   ctl->split_cursor = 0;
@@ -531,7 +535,7 @@ __global__ void k_async_seed(DevGraph g, uint32_t src, uint32_t* dist, unsigned 
 
 }  // namespace
 
-gg_status async_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s) {
+gg_status async_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s, uint32_t wmode) {
   AsyncWorkspace& w = g->async;
   const DeviceInfo di = device_info();
   if (!w.block) {
@@ -571,12 +575,14 @@ gg_status async_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options&
   GG_CK(cudaMemsetAsync(Q, 0, sizeof(unsigned long long) << logcap, s));
   unsigned ib = (unsigned)std::min<uint64_t>((g->n + 255) / 256, (uint64_t)di.num_sms * 8);
   if (ib == 0) ib = 1;
-  k_async_init<<<ib, 256, 0, s>>>(g->dg, dist, w.inq, w.bm_far);
+  k_async_init<<<ib, 256, 0, s>>>(g->dg, dist, w.inq, w.bm_far, wmode == WM_F32 ? kFltMaxBits : kInf);
   GG_CK(cudaGetLastError());
   const unsigned long long wd = o.watchdog_ns ? o.watchdog_ns : 10000000000ull;
-  const uint32_t delta = o.delta == GG_DELTA_NONE ? kInf : (o.delta ? o.delta : g->default_delta);
+  // buckets are integer distance ranges: binary32 and hop-count runs go without
+  const uint32_t delta =
+      (o.delta == GG_DELTA_NONE || wmode != WM_U32) ? kInf : (o.delta ? o.delta : g->default_delta);
   k_async_seed<<<1, 1, 0, s>>>(g->dg, src, dist, Q, w.inq, ctl, wd, delta, w.far[0], w.far[1], w.bm_far, o.trace,
-                               o.trace_cap);
+                               o.trace_cap, wmode);
   GG_CK(cudaGetLastError());
   AsyncArgs a{g->dg, Q, logcap, w.inq, ctl};
   void* args[] = {&a};

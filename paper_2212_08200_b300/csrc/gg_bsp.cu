@@ -91,6 +91,7 @@ struct FilterOut {
   uint32_t* far;                  // far pile being appended to
   uint32_t* far_cnt;              // its append position
   uint32_t* far_add;              // per-superstep count of far appends (or NULL)
+  uint32_t wmode;                 // WM_*: how relaxations add edge weights
 };
 
 // Filter: vertex v whose distance just dropped to nd.  Vertices without
@@ -271,7 +272,7 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         if (ej[k] != kInf) {
-          nd[k] = add_sat(sm.ec[ej[k]], ed[k].y, ovf);
+          nd[k] = relax_add(sm.ec[ej[k]], ed[k].y, ovf, fo.wmode);
           cur[k] = ld_cg(dist + ed[k].x);
         }
       }
@@ -320,7 +321,7 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
               } while (gidx >= nxt);
             }
             const uint32_t u = col[k];
-            if ((bm_cur[u >> 5] >> (u & 31)) & 1u) acc = min(acc, add_sat(dist[u], wt[k], ovf));
+            if ((bm_cur[u >> 5] >> (u & 31)) & 1u) acc = min(acc, relax_add(dist[u], wt[k], ovf, fo.wmode));
           }
         }
         if (acc != kInf) atomicMin(&sm.ec[jj], acc);
@@ -361,7 +362,7 @@ __device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepA
   bool ovf = false;
   auto relax = [&](uint32_t e, uint32_t du) {
     const uint2 ed = load_edge<PK>(edges, e, wbits);
-    const uint32_t nd = add_sat(du, ed.y, ovf);
+    const uint32_t nd = relax_add(du, ed.y, ovf, fo.wmode);
     if (nd < ld_cg(dist + ed.x)) {
       const uint32_t old = atomicMin(dist + ed.x, nd);
       if (nd < old) filter_candidate(sm, fo, ed.x, nd);
@@ -574,7 +575,7 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
 #pragma unroll
       for (int u = 0; u < WU; ++u) {
         if (act[u]) {
-          nd[u] = add_sat(nd[u], ed[u].y, ovf);
+          nd[u] = relax_add(nd[u], ed[u].y, ovf, fo.wmode);
           cur[u] = ld_cg(dist + ed[u].x);
         }
       }
@@ -796,6 +797,7 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_supers
   fo.far = a.fr.far[mode == MODE_SPLIT ? fp ^ 1u : fp];
   fo.far_cnt = &ctl->far_cnt[mode == MODE_SPLIT ? fp ^ 1u : fp];
   fo.far_add = nullptr;
+  fo.wmode = ctl->wmode;
   superstep_prologue(sm, a, it, ctl->clear_prev != 0);
   if (mode == MODE_SPLIT) {
     far_split(sm, a, fo, dist, a.fr.far[fp], ctl->far_cnt[fp], ctl->t_prev);
@@ -862,7 +864,7 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_bsp_pe
   uint32_t* dist = ctl->dist;
   const unsigned long long deadline = ctl->t_start + ctl->watchdog_ns;
   const uint32_t dir = ctl->dir, alpha = ctl->alpha, beta = ctl->beta, delta = ctl->delta;
-  const uint32_t max_iter = ctl->max_iter;
+  const uint32_t max_iter = ctl->max_iter, wmode = ctl->wmode;
   uint32_t it = 0, mode = ctl->mode, t_cur = ctl->t_cur, t_prev = 0, splits = 0, run_fmin = kInf;
   uint32_t nfar = 0;   // far-pile size, tracked identically by every CTA
   bool clear = false;
@@ -889,6 +891,7 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_bsp_pe
     fo.far = a.fr.far[mode == MODE_SPLIT ? pile_out : pile];
     fo.far_cnt = &ctl->fcnt3[mode == MODE_SPLIT ? pile_out : pile];
     fo.far_add = &ctl->fadd3[s0];
+    fo.wmode = wmode;
     superstep_prologue(sm, a, it, clear);
     if (lead) {
       ctl->cnt3[s2] = 0ull;      // written next superstep; its readers are two barriers back
@@ -999,21 +1002,23 @@ struct RunParams {
   uint32_t trace_cap;
   uint32_t warp_thr, cta_thr;
   uint32_t delta;                  // near-far bucket width (kInf: no split)
+  uint32_t wmode;                  // WM_*
   unsigned long long watchdog_ns;
 };
 
-// dist := INF everywhere (vectorised 16-byte stores when aligned); bitmaps := 0.
-__global__ void k_init(StepArgs a, uint32_t* dist) {
+// dist := the unreached value everywhere (INF, or FLT_MAX for binary32
+// distances; vectorised 16-byte stores when aligned); bitmaps := 0.
+__global__ void k_init(StepArgs a, uint32_t* dist, uint32_t unreached) {
   const uint32_t n = a.g.n;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if ((reinterpret_cast<uintptr_t>(dist) & 15u) == 0) {
     const uint64_t n4 = n / 4;
     uint4* d4 = reinterpret_cast<uint4*>(dist);
-    for (uint64_t i = t; i < n4; i += stride) d4[i] = make_uint4(kInf, kInf, kInf, kInf);
-    for (uint64_t i = n4 * 4 + t; i < n; i += stride) dist[i] = kInf;
+    for (uint64_t i = t; i < n4; i += stride) d4[i] = make_uint4(unreached, unreached, unreached, unreached);
+    for (uint64_t i = n4 * 4 + t; i < n; i += stride) dist[i] = unreached;
   } else {
-    for (uint64_t i = t; i < n; i += stride) dist[i] = kInf;
+    for (uint64_t i = t; i < n; i += stride) dist[i] = unreached;
   }
   for (uint64_t i = t; i < a.g.nwords; i += stride) {
     a.fr.bm[0][i] = 0u;
@@ -1057,6 +1062,7 @@ __global__ void k_init_tail(StepArgs a, RunParams rp) {
   ctl->max_frontier = 0;
   ctl->warp_thr = rp.warp_thr;
   ctl->cta_thr = rp.cta_thr;
+  ctl->wmode = rp.wmode;
   ctl->delta = rp.delta;
   ctl->t_cur = rp.delta;           // the first bucket is [0, delta)
   ctl->t_prev = 0;
@@ -1202,7 +1208,7 @@ gg_status build_graph_exec(gg_graph* g, int variant) {
 
 }  // namespace
 
-gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s) {
+gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s, uint32_t wmode) {
   gg_status st = ensure_workspace(g);
   if (st != GG_OK) return st;
   // automatic choice: warp streaming (measured faster than merge-path tiles on RMAT, equal on grids)
@@ -1218,7 +1224,9 @@ gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o
   // near-far: with buckets the superstep count is bounded by about 3n (every
   // phase finalises at least one vertex and runs at most its bucket's size + 2
   // steps); without, by n + 1
-  rp.delta = o.delta == GG_DELTA_NONE ? kInf : (o.delta ? o.delta : g->default_delta);
+  // buckets are integer distance ranges: binary32 and hop-count runs go without
+  rp.delta = (o.delta == GG_DELTA_NONE || wmode != WM_U32) ? kInf : (o.delta ? o.delta : g->default_delta);
+  rp.wmode = wmode;
   const unsigned long long cap = rp.delta == kInf ? (unsigned long long)g->n + 2 : 4ull * g->n + 16;
   rp.max_iter = o.max_iterations ? o.max_iterations : (cap >= 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)cap);
   rp.watchdog_ns = o.watchdog_ns ? o.watchdog_ns : 60000000000ull;
@@ -1233,7 +1241,7 @@ gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o
   const uint64_t work = std::max<uint64_t>(g->n / 4, g->dg.nwords);
   unsigned ib = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)di.num_sms * 8);
   if (ib == 0) ib = 1;
-  k_init<<<ib, 256, 0, s>>>(a, dist);
+  k_init<<<ib, 256, 0, s>>>(a, dist, wmode == WM_F32 ? kFltMaxBits : kInf);
   GG_CK(cudaGetLastError());
   k_init_tail<<<1, 1, 0, s>>>(a, rp);
   GG_CK(cudaGetLastError());

@@ -29,6 +29,11 @@ namespace gg {
 
 constexpr uint32_t kInf = 0xFFFFFFFFu;
 constexpr uint32_t kSat = 0xFFFFFFFEu;   // saturated (overflowed) finite distance
+constexpr uint32_t kFltMaxBits = 0x7F7FFFFFu;   // FLT_MAX: "unreached" for binary32 distances
+
+// How a relaxation adds an edge weight (per run): unsigned integers, IEEE
+// binary32 bit patterns (the paper's float weights), or unit weights (BFS).
+enum : uint32_t { WM_U32 = 0, WM_F32 = 1, WM_UNIT = 2 };
 
 enum : uint32_t { MODE_PUSH = 0, MODE_PULL = 1, MODE_SPLIT = 2 };
 enum : uint32_t { DIR_AUTO = 0, DIR_PUSH = 1, DIR_PULL = 2 };
@@ -54,6 +59,7 @@ struct Ctl {
   uint32_t trace_cap;
   uint32_t max_frontier;
   uint32_t warp_thr, cta_thr;  // degree bins of the binned push advance
+  uint32_t wmode;              // WM_*: how relaxations add edge weights in this run
   // near-far split of the frontier (priority buckets of width delta): vertices
   // improved to a distance < t_cur join the next frontier, the others wait in
   // the far pile far[fp] until the near frontier empties and a split step
@@ -164,6 +170,15 @@ __device__ __forceinline__ uint32_t add_sat(uint32_t d, uint32_t w, bool& ovf) {
   unsigned long long s = (unsigned long long)d + w;
   if (s >= kInf) { ovf = true; return kSat; }
   return (uint32_t)s;
+}
+
+// d + w for the run's weight mode.  WM_F32: nonnegative binary32 bit patterns
+// order like the floats they encode, so the round-to-nearest sum's bits feed
+// the same unsigned compare and atomicMin; an overflow rounds to +inf, which
+// never improves on FLT_MAX.  WM_UNIT: every edge counts 1 (hop distance).
+__device__ __forceinline__ uint32_t relax_add(uint32_t d, uint32_t w, bool& ovf, uint32_t wmode) {
+  if (wmode == WM_F32) return __float_as_uint(__fadd_rn(__uint_as_float(d), __uint_as_float(w)));
+  return add_sat(d, wmode == WM_UNIT ? 1u : w, ovf);
 }
 
 // Largest j in [0, F) with S[j] <= x, for S strictly increasing with S[0] <= x.

@@ -184,6 +184,7 @@ gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m64, const uint32_t* ro_
   g->n = n;
   g->m = m;
   g->symmetric = (flags & GG_SYMMETRIC) != 0;
+  g->float_weights = (flags & GG_FLOAT_WEIGHTS) != 0;
   // cheap host-side check first; monotonicity and column range are checked on
   // the device after the upload (k_validate)
   if (!dev && validate && (ro_in[0] != 0 || ro_in[n] != m))
@@ -218,6 +219,7 @@ gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m64, const uint32_t* ro_
       GG_CK(cudaMemcpyAsync(&herr, derr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
       GG_CK(cudaFreeAsync(derr, s));
       GG_CK(cudaStreamSynchronize(s));
+      if (herr && tmp) cudaFreeAsync(tmp, s);
       if (herr & 4u) return fail(GG_ERR_INVALID_ARG, "row_offsets must start at 0 and end at m");
       if (herr & 1u) return fail(GG_ERR_INVALID_ARG, "row_offsets must be non-decreasing");
       if (herr & 2u) return fail(GG_ERR_INVALID_ARG, "col_indices must be < n");
@@ -228,6 +230,16 @@ gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m64, const uint32_t* ro_
     GG_CK(cudaGetLastError());
     GG_CK(cudaMemcpyAsync(&wmax, wmax_d, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     GG_CK(cudaFreeAsync(wmax_d, s));
+    if (validate && (flags & GG_FLOAT_WEIGHTS)) {
+      // binary32 weights must be finite and >= +0: as bit patterns, every such
+      // value is below +inf's 0x7F800000 and every other one (negative, -0,
+      // inf, NaN) is not, so the largest pattern decides
+      GG_CK(cudaStreamSynchronize(s));
+      if (wmax >= 0x7F800000u) {
+        if (tmp) cudaFreeAsync(tmp, s);
+        return fail(GG_ERR_INVALID_ARG, "binary32 weights must be finite and >= +0.0");
+      }
+    }
   } else if (dev && validate) {
     uint32_t h[2] = {0, 0};
     GG_CK(cudaMemcpyAsync(h, g->ro, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));

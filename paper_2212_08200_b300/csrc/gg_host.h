@@ -85,16 +85,17 @@ struct gg_graph {
   gg::Ctl* h_ctl = nullptr;      // pinned host mirror for status/stats reads
   void* h_async = nullptr;       // pinned host mirror of the async control block
   int last_policy = -1;
-  uint32_t wmax = 0;            // largest edge weight
+  uint32_t wmax = 0;            // largest edge weight (bit pattern)
+  bool float_weights = false;   // weights and distances are IEEE binary32 bit patterns
   uint32_t default_delta = 0;   // near-far bucket width used when gg_options.delta == 0
 };
 
 namespace gg {
 // gg_bsp.cu
-gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s);
+gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s, uint32_t wmode);
 gg_status bsp_release(gg_graph* g);
 // gg_async.cu
-gg_status async_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s);
+gg_status async_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s, uint32_t wmode);
 gg_status async_release(gg_graph* g);
 gg_status async_status(gg_graph* g, uint32_t* ds, gg_stats* st);
 // gg_batch.cu

@@ -82,6 +82,8 @@ extern "C" gg_status gg_sssp_multi_ex(const gg_graph_t* graphs, const uint32_t* 
     if (!dist_outs[i]) return fail(GG_ERR_INVALID_ARG, "a dist_out is NULL");
     if (g->device != dev) return fail(GG_ERR_INVALID_ARG, "a graph lives on another device");
     if (srcs[i] >= g->n) return fail(GG_ERR_INVALID_ARG, "a source is >= its graph's n");
+    if (g->float_weights)
+      return fail(GG_ERR_NOT_SUPPORTED, "binary32 weights: gg_sssp, gg_sssp_ex and gg_bfs only");
     total_n += g->n;
     words += 3ull * ((g->n + 31) / 32);
     nmax = std::max(nmax, g->n);
@@ -329,6 +331,8 @@ gg_status gg_server_create(const gg_server_config* cfg, gg_server_t* out) {
 gg_status gg_server_submit(gg_server_t s, gg_graph_t g, uint32_t src, uint32_t* dist_out, uint64_t* ticket) {
   if (!s || !g || !dist_out || !ticket) return fail(GG_ERR_INVALID_ARG, "NULL argument");
   if (src >= g->n) return fail(GG_ERR_INVALID_ARG, "src >= n");
+  if (g->float_weights)
+    return fail(GG_ERR_NOT_SUPPORTED, "binary32 weights: gg_sssp, gg_sssp_ex and gg_bfs only");
   if (g->device != s->device) return fail(GG_ERR_INVALID_ARG, "graph lives on another device");
   if (g->n > s->cfg.max_graph_vertices) return fail(GG_ERR_INVALID_ARG, "graph larger than max_graph_vertices");
   std::lock_guard<std::mutex> lk(s->mu);
