@@ -769,7 +769,7 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
 // One superstep; LB selects the push advance (merge-path tiles, degree bins
 // or warp streaming) (pull is the same merge-path sweep in both); a split step
 // refills the near frontier from the far pile.
-template <int BLOCK, int EPT, int LB, bool PK>
+template <int BLOCK, int EPT, int LB, bool PK, int WM>
 __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_superstep(StepArgs a, cudaGraphConditionalHandle cond,
                                                                        int use_cond) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -797,7 +797,7 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_supers
   fo.far = a.fr.far[mode == MODE_SPLIT ? fp ^ 1u : fp];
   fo.far_cnt = &ctl->far_cnt[mode == MODE_SPLIT ? fp ^ 1u : fp];
   fo.far_add = nullptr;
-  fo.wmode = ctl->wmode;
+  fo.wmode = WM;   // compile-time: relax_add folds to one arithmetic path
   superstep_prologue(sm, a, it, ctl->clear_prev != 0);
   if (mode == MODE_SPLIT) {
     far_split(sm, a, fo, dist, a.fr.far[fp], ctl->far_cnt[fp], ctl->t_prev);
@@ -856,7 +856,7 @@ __device__ __forceinline__ void grid_barrier(Ctl* ctl, unsigned long long deadli
 // thresholds, termination) in its own registers.  Counters rotate over three
 // slots (a slot is reset two supersteps after its last reader passed a
 // barrier); the far pile rotates over three piles, one per split step.
-template <int BLOCK, int EPT, int LB, bool PK>
+template <int BLOCK, int EPT, int LB, bool PK, int WM>
 __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_bsp_persistent(StepArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   MPSmem<BLOCK, EPT>& sm = *reinterpret_cast<MPSmem<BLOCK, EPT>*>(smraw);
@@ -864,7 +864,7 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_bsp_pe
   uint32_t* dist = ctl->dist;
   const unsigned long long deadline = ctl->t_start + ctl->watchdog_ns;
   const uint32_t dir = ctl->dir, alpha = ctl->alpha, beta = ctl->beta, delta = ctl->delta;
-  const uint32_t max_iter = ctl->max_iter, wmode = ctl->wmode;
+  const uint32_t max_iter = ctl->max_iter;
   uint32_t it = 0, mode = ctl->mode, t_cur = ctl->t_cur, t_prev = 0, splits = 0, run_fmin = kInf;
   uint32_t nfar = 0;   // far-pile size, tracked identically by every CTA
   bool clear = false;
@@ -891,7 +891,7 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_bsp_pe
     fo.far = a.fr.far[mode == MODE_SPLIT ? pile_out : pile];
     fo.far_cnt = &ctl->fcnt3[mode == MODE_SPLIT ? pile_out : pile];
     fo.far_add = &ctl->fadd3[s0];
-    fo.wmode = wmode;
+    fo.wmode = WM;   // compile-time: relax_add folds to one arithmetic path
     superstep_prologue(sm, a, it, clear);
     if (lead) {
       ctl->cnt3[s2] = 0ull;      // written next superstep; its readers are two barriers back
@@ -1090,30 +1090,33 @@ __global__ void k_init_tail(StepArgs a, RunParams rp) {
 
 constexpr int kBlock = 256;
 constexpr int kEpt = GG_EPT;
-constexpr int kVariants = 6;   // 2 * load balance (tiles, bins, warp streaming) + packed edges
+// kernel variants: (load balance x packed edges) x weight mode
+constexpr int kVariants = 18;
+
+constexpr int variant_of(int lb, bool packed, uint32_t wmode) { return (lb * 2 + (packed ? 1 : 0)) * 3 + (int)wmode; }
+
+template <int LB, bool PK, int WM>
+void* superstep_ptr() { return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, LB, PK, WM>); }
+template <int LB, bool PK, int WM>
+void* persistent_ptr() { return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, LB, PK, WM>); }
+
+#define GG_VARIANT_TABLE(F)                                                                                   \
+  {F<LB_TILE, false, 0>(), F<LB_TILE, false, 1>(), F<LB_TILE, false, 2>(), F<LB_TILE, true, 0>(),              \
+   F<LB_TILE, true, 1>(),  F<LB_TILE, true, 2>(),  F<LB_BINS, false, 0>(), F<LB_BINS, false, 1>(),             \
+   F<LB_BINS, false, 2>(), F<LB_BINS, true, 0>(),  F<LB_BINS, true, 1>(),  F<LB_BINS, true, 2>(),              \
+   F<LB_WARP, false, 0>(), F<LB_WARP, false, 1>(), F<LB_WARP, false, 2>(), F<LB_WARP, true, 0>(),              \
+   F<LB_WARP, true, 1>(),  F<LB_WARP, true, 2>()}
 
 void* superstep_fn(int variant) {
-  switch (variant) {
-    case 1: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, LB_TILE, true>);
-    case 2: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, LB_BINS, false>);
-    case 3: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, LB_BINS, true>);
-    case 4: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, LB_WARP, false>);
-    case 5: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, LB_WARP, true>);
-    default: return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, LB_TILE, false>);
-  }
+  static void* const table[kVariants] = GG_VARIANT_TABLE(superstep_ptr);
+  return table[variant];
 }
 
 size_t superstep_smem(int) { return sizeof(MPSmem<kBlock, kEpt>); }
 
 void* persistent_fn(int variant) {
-  switch (variant) {
-    case 1: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, LB_TILE, true>);
-    case 2: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, LB_BINS, false>);
-    case 3: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, LB_BINS, true>);
-    case 4: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, LB_WARP, false>);
-    case 5: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, LB_WARP, true>);
-    default: return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, LB_TILE, false>);
-  }
+  static void* const table[kVariants] = GG_VARIANT_TABLE(persistent_ptr);
+  return table[variant];
 }
 
 // co-resident grid of the persistent kernel (cooperative launch limit)
@@ -1213,7 +1216,7 @@ gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o
   if (st != GG_OK) return st;
   // automatic choice: warp streaming (measured faster than merge-path tiles on RMAT, equal on grids)
   const int lb = o.lb_mode == GG_LB_BINS ? LB_BINS : o.lb_mode == GG_LB_MERGE_PATH ? LB_TILE : LB_WARP;
-  const int variant = 2 * lb + (g->dg.packed ? 1 : 0);
+  const int variant = variant_of(lb, g->dg.packed != 0, wmode);
   BspWorkspace& w = g->bsp;
   RunParams rp;
   rp.src = src;

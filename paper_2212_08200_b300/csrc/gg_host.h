@@ -36,10 +36,10 @@ struct BspWorkspace {
   void* block = nullptr;      // single device allocation backing fr and ctl
   size_t bytes = 0;
   // CUDA graph with a conditional WHILE node around one superstep kernel,
-  // one per load-balance variant.
-  cudaGraph_t graph[6] = {};
-  cudaGraphExec_t exec[6] = {};
-  int grid[6] = {};
+  // one per kernel variant (load balance x edge packing x weight mode).
+  cudaGraph_t graph[18] = {};
+  cudaGraphExec_t exec[18] = {};
+  int grid[18] = {};
 };
 
 // Workspace of the asynchronous persistent path.

@@ -31,6 +31,21 @@ def spread_weights(m, seed):
     return w
 
 
+def symmetric_spread_weights(ro, col, seed):
+    """Weights of spread magnitudes that agree on (u, v) and (v, u), as a
+    symmetric graph's CSR must (pull reads it as its own transpose)."""
+    n = ro.shape[0] - 1
+    u = np.repeat(np.arange(n, dtype=np.uint64), np.diff(ro.astype(np.int64)))
+    v = col.astype(np.uint64)
+    with np.errstate(over="ignore"):
+        x = np.minimum(u, v) * np.uint64(n) + np.maximum(u, v) + np.uint64(seed) * np.uint64(0x9E3779B97F4A7C15)
+        x = (x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        x = (x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        x = x ^ (x >> np.uint64(31))
+    unit = (x >> np.uint64(11)).astype(np.float64) / float(1 << 53)
+    return (10.0 ** (unit * 10.0 - 3.0)).astype(np.float32)
+
+
 def run_f32(g, src, mode):
     d = g.sssp(src, policy=POLICIES[mode[0]], direction=DIRS[mode[1]], lb_mode=LB[mode[2]])
     torch.cuda.synchronize()
@@ -55,7 +70,7 @@ def test_float_random_graphs(mode):
 @pytest.mark.parametrize("sym", [True, False])
 def test_float_rmat16(mode, sym):
     ro, col, _, src = graphgen.workload("rmat16")
-    w = spread_weights(col.shape[0], 3)
+    w = symmetric_spread_weights(ro, col, 3) if sym else spread_weights(col.shape[0], 3)
     g = gg().Graph(ro, col, w, symmetric=sym, float_weights=True)
     np.testing.assert_array_equal(run_f32(g, src, mode), oracle.dijkstra_f32(ro, col, w, src))
     g.close()
@@ -140,7 +155,7 @@ def test_bfs_matches_oracle_hops(mode):
 def test_bfs_on_a_float_graph_and_rmat20_hops():
     m = gg()
     ro, col, _, src = graphgen.workload("rmat16")
-    g = m.Graph(ro, col, spread_weights(col.shape[0], 1), symmetric=True, float_weights=True)
+    g = m.Graph(ro, col, symmetric_spread_weights(ro, col, 1), symmetric=True, float_weights=True)
     np.testing.assert_array_equal(run_bfs(g, src, ("graph", "push", "warp")), oracle.bfs_hops(ro, col, src))
     g.close()
     ro, col, w, src = graphgen.workload("rmat20")
