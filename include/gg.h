@@ -55,7 +55,7 @@ extern "C" {
 #endif
 
 #define GG_INF 0xFFFFFFFFu
-#define GG_ABI_VERSION 2
+#define GG_ABI_VERSION 3
 
 typedef struct gg_graph* gg_graph_t;
 
@@ -147,7 +147,8 @@ typedef struct {
                                   and fills it                                          */
     uint32_t* trace;           /* device u32[trace_cap*4] or NULL.  BSP: per superstep
                                   (frontier size, frontier edges, kind 0 push / 1 pull
-                                  / 2 near-far split, next frontier size).  ASYNC: per
+                                  / 2 near-far split / 3 heavy-edge superstep, next
+                                  frontier size).  ASYNC: per
                                   near-far split (split number, new threshold, far-pile
                                   size, microseconds since the kernel started)         */
     uint32_t trace_cap;
@@ -156,9 +157,22 @@ typedef struct {
                                   rest wait in a far pile until the frontier empties and
                                   the threshold rises by delta (0 = the graph's default,
                                   GG_DELTA_NONE = plain frontier loop, no buckets)       */
+    uint32_t light_heavy;      /* GG_LH_AUTO: with buckets, the BSP graph and host policies
+                                  relax heavy edges (weight >= delta) once per settled
+                                  vertex (Meyer-Sanders delta-stepping): near supersteps
+                                  relax only light edges, and a heavy superstep runs
+                                  when the near frontier empties.  Push direction,
+                                  integer weights, and delta <= the largest weight.  The
+                                  first such run builds a copy of the edges with each
+                                  row's light edges first (4 or 8 bytes per edge, kept
+                                  by the handle; rebuilt when delta changes).
+                                  GG_LH_OFF: every expansion relaxes all edges.
+                                  Distances are the same either way.                     */
 } gg_options;
 
 #define GG_DELTA_NONE 0xFFFFFFFFu
+#define GG_LH_AUTO 0u
+#define GG_LH_OFF 1u
 
 /* ---- graph (Sec. IV-A, Listing 1) ------------------------------------- */
 

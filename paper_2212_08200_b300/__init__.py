@@ -21,6 +21,7 @@ __all__ = [
     "GGError", "GG_INF", "GG_DEVICE_PTRS", "GG_SYMMETRIC", "GG_NO_VALIDATE",
     "GG_POLICY_BSP_GRAPH", "GG_POLICY_ASYNC_PERSISTENT", "GG_POLICY_BSP_HOST", "GG_POLICY_BSP_PERSISTENT",
     "GG_DIR_AUTO", "GG_DIR_PUSH", "GG_DIR_PULL", "GG_LB_AUTO", "GG_LB_MERGE_PATH", "GG_LB_BINS", "GG_LB_WARP", "GG_DELTA_NONE",
+    "GG_LH_AUTO", "GG_LH_OFF",
     "gg_graph_create_csr", "gg_graph_destroy", "gg_graph_info", "gg_graph_check", "gg_sssp", "gg_sssp_ex",
     "gg_bfs", "gg_bfs_ex", "GG_FLOAT_WEIGHTS", "GG_FLT_MAX_BITS",
     "gg_sssp_batch", "gg_sssp_multi", "Server",
@@ -40,6 +41,7 @@ GG_POLICY_BSP_GRAPH, GG_POLICY_ASYNC_PERSISTENT, GG_POLICY_BSP_HOST, GG_POLICY_B
 GG_DIR_AUTO, GG_DIR_PUSH, GG_DIR_PULL = 0, 1, 2
 GG_LB_AUTO, GG_LB_MERGE_PATH, GG_LB_BINS, GG_LB_WARP = 0, 1, 2, 3
 GG_DELTA_NONE = 0xFFFFFFFF
+GG_LH_AUTO, GG_LH_OFF = 0, 1
 
 STATUS = {0: "GG_OK", 1: "GG_ERR_INVALID_ARG", 2: "GG_ERR_OUT_OF_MEMORY", 3: "GG_ERR_CUDA",
           4: "GG_ERR_TIMEOUT", 5: "GG_ERR_BUSY", 6: "GG_ERR_NOT_READY", 7: "GG_ERR_OVERFLOW",
@@ -68,7 +70,7 @@ class gg_options(ctypes.Structure):
                 ("pull_alpha", ctypes.c_uint32), ("pull_beta", ctypes.c_uint32),
                 ("max_iterations", ctypes.c_uint32), ("watchdog_ns", ctypes.c_uint64),
                 ("stats", ctypes.POINTER(gg_stats)), ("trace", ctypes.c_void_p), ("trace_cap", ctypes.c_uint32),
-                ("delta", ctypes.c_uint32)]
+                ("delta", ctypes.c_uint32), ("light_heavy", ctypes.c_uint32)]
 
 
 class gg_server_config(ctypes.Structure):
@@ -227,13 +229,14 @@ def gg_graph_check(handle: int):
 
 def make_options(policy=GG_POLICY_BSP_GRAPH, direction=GG_DIR_AUTO, lb_mode=GG_LB_AUTO, warp_threshold=0,
                  cta_threshold=0, pull_alpha=0, pull_beta=0, max_iterations=0, watchdog_ns=0, stats=None,
-                 trace=None, trace_cap=0, delta=0) -> gg_options:
+                 trace=None, trace_cap=0, delta=0, light_heavy=0) -> gg_options:
     o = gg_options()
     load().gg_options_default(ctypes.byref(o))
     o.policy, o.direction, o.lb_mode = policy, direction, lb_mode
     o.warp_threshold, o.cta_threshold = warp_threshold, cta_threshold
     o.pull_alpha, o.pull_beta, o.max_iterations, o.watchdog_ns = pull_alpha, pull_beta, max_iterations, watchdog_ns
     o.delta = delta
+    o.light_heavy = light_heavy
     if stats is not None:
         o.stats = ctypes.pointer(stats)
     if trace is not None:

@@ -153,7 +153,7 @@ gg_status gg_graph_info(gg_graph_t g, uint32_t* n, uint64_t* m, uint64_t* device
   if (!g) return fail(GG_ERR_INVALID_ARG, "graph is NULL");
   if (n) *n = g->n;
   if (m) *m = g->m;
-  if (device_bytes) *device_bytes = g->bytes + g->bsp.bytes + g->async.bytes + batch_bytes(g);
+  if (device_bytes) *device_bytes = g->bytes + g->bsp.bytes + g->async.bytes + batch_bytes(g) + g->lh_bytes;
   return GG_OK;
 }
 
@@ -214,6 +214,7 @@ gg_status run_single(gg_graph_t g, uint32_t src, uint32_t* dist_out, const gg_op
   if ((unsigned)o.policy > 3u) return fail(GG_ERR_INVALID_ARG, "unknown policy");
   if ((unsigned)o.direction > 2u) return fail(GG_ERR_INVALID_ARG, "unknown direction");
   if ((unsigned)o.lb_mode > 3u) return fail(GG_ERR_INVALID_ARG, "unknown load-balance mode");
+  if (o.light_heavy > GG_LH_OFF) return fail(GG_ERR_INVALID_ARG, "unknown light_heavy mode");
   if (o.trace && o.trace_cap == 0) return fail(GG_ERR_INVALID_ARG, "trace without trace_cap");
   int dev = -1;
   GG_CK(cudaGetDevice(&dev));

@@ -36,6 +36,12 @@
 #ifndef GG_WARP_MINB
 #define GG_WARP_MINB 5   // resident CTAs per SM the warp-streaming kernels are compiled for
 #endif
+#ifndef GG_HEAVY_PULL
+#define GG_HEAVY_PULL 1   // allow heavy supersteps by pull on symmetric graphs
+#endif
+#ifndef GG_LH_DRAIN
+#define GG_LH_DRAIN 8    // light/heavy: bucketing ends once the unsettled vertices hold
+#endif                   // fewer than m / GG_LH_DRAIN heavy edges
 
 namespace gg {
 
@@ -77,6 +83,8 @@ struct StepArgs {
   DevGraph g;
   Frontier fr;
   Ctl* ctl;
+  LhBufs lb;   // light/heavy buffers (valid in light/heavy runs): kernel parameters, so
+               // the relaxation loop holds none of these pointers in registers
 };
 
 // Where the filter writes: the next (near) frontier and the far pile.
@@ -92,7 +100,68 @@ struct FilterOut {
   uint32_t* far_cnt;              // its append position
   uint32_t* far_add;              // per-superstep count of far appends (or NULL)
   uint32_t wmode;                 // WM_*: how relaxations add edge weights
+  // light/heavy buckets (lh != 0): a near vertex v joins the next frontier
+  // with its light edges [ro[v], lend[v]) and, once per epoch, the R list
+  // R[lh - 1] with its heavy edges [lend[v], ro[v+1]); vertices without edges
+  // of a kind are left out of that list
+  uint32_t lh;
 };
+
+// Append of up to 32 near vertices, one per lane (have = lane holds one) to
+// the next frontier (LHM: their light edges, plus their heavy edges to the R
+// list of the epoch): one 64-bit atomicAdd per list returns the list position
+// and the edge-prefix base of the warp's entries.  Vertices without edges of
+// a kind are left out of that list.
+template <bool LHM>
+__device__ __forceinline__ void append32(const StepArgs& a, const FilterOut& fo, bool have, uint32_t v) {
+  const unsigned FULL = 0xFFFFFFFFu;
+  const uint32_t lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t rj = fo.lh - 1u;
+  uint32_t rs = 0, le = 0, re = 0;
+  bool lgt = false, hvy = false;
+  if (have) {
+    rs = __ldg(fo.ro + v);
+    re = __ldg(fo.ro + v + 1);
+    le = LHM ? __ldg(a.lb.lend + v) : re;
+    lgt = le > rs;
+    if (LHM && re > le) {
+      const uint32_t bit = 1u << (v & 31);
+      hvy = !(atomicOr(pick2(a.lb.bm_r, rj) + (v >> 5), bit) & bit);
+    }
+  }
+#pragma unroll
+  for (int list = 0; list < (LHM ? 2 : 1); ++list) {
+    const bool mine = list == 0 ? lgt : hvy;
+    const unsigned b = __ballot_sync(FULL, mine);
+    if (b == 0u) continue;   // warp-uniform
+    const uint32_t d = mine ? (list == 0 ? le - rs : re - le) : 0u;
+    uint32_t x = d;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, x, o);
+      if (lane >= (uint32_t)o) x += y;
+    }
+    const uint32_t tot = __shfl_sync(FULL, x, 31);
+    unsigned long long base = 0;
+    if (lane == 0)
+      base = atomicAdd(list == 0 ? fo.cnt_next : &a.ctl->rcnt[rj], ((unsigned long long)__popc(b) << 32) | tot);
+    base = __shfl_sync(FULL, base, 0);
+    if (mine) {
+      const uint32_t pos = (uint32_t)(base >> 32) + __popc(b & lt);
+      const uint32_t coord = (uint32_t)base + x - d;
+      if (list == 0) {
+        fo.nfv[pos] = v;
+        fo.nfr[pos] = rs;
+        fo.nfs[pos] = coord;
+      } else {
+        pick2(a.lb.rv, rj)[pos] = v;
+        pick2(a.lb.rr, rj)[pos] = le;
+        pick2(a.lb.rs, rj)[pos] = coord;
+      }
+    }
+  }
+}
 
 // Filter: vertex v whose distance just dropped to nd.  Vertices without
 // out-edges have nothing to expand and are skipped.  nd < t_cur: the next
@@ -145,11 +214,31 @@ __device__ __forceinline__ void filter_candidate(MPSmem<BLOCK, EPT>& sm, const F
 // without an intervening barrier need it; the merge-path tile loop does not
 // (its next tile's staging barrier comes first).
 template <int BLOCK, int EPT, bool TRAIL = true>
-__device__ __forceinline__ void filter_flush(MPSmem<BLOCK, EPT>& sm, const FilterOut& fo) {
+__device__ __forceinline__ void filter_flush(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, const FilterOut& fo) {
   constexpr uint32_t ECAP = MPSmem<BLOCK, EPT>::ECAP;
   __syncthreads();
   const uint32_t qn = sm.qn, qfn = sm.qfn;
   if (qn == 0 && qfn == 0) return;   // uniform
+  if (fo.lh) {
+    // every warp appends 32-entry chunks of the near queue to both lists
+    for (uint32_t c0 = threadIdx.x & ~31u; c0 < qn; c0 += BLOCK) {
+      const uint32_t i = c0 + (threadIdx.x & 31);
+      append32<true>(a, fo, i < qn, i < qn ? sm.qv[i] : 0u);
+    }
+    if (qfn && threadIdx.x == 0) {
+      sm.fbase = atomicAdd(fo.far_cnt, qfn);
+      if (fo.far_add) atomicAdd(fo.far_add, qfn);
+    }
+    __syncthreads();
+    const uint32_t fb = sm.fbase;
+    if (threadIdx.x == 0) {   // every thread has read the counts by now
+      sm.qn = 0;
+      sm.qfn = 0;
+    }
+    for (uint32_t i = threadIdx.x; i < qfn; i += BLOCK) fo.far[fb + i] = sm.qv[ECAP - 1 - i];
+    if (TRAIL) __syncthreads();
+    return;
+  }
   if (qn && !fo.sinks) {
     for (uint32_t i = threadIdx.x; i < qn; i += BLOCK) {
       const uint32_t v = sm.qv[i];
@@ -338,7 +427,7 @@ __device__ __forceinline__ void mp_advance(MPSmem<BLOCK, EPT>& sm, const StepArg
         }
       }
     }
-    filter_flush<BLOCK, EPT, PULL>(sm, fo);   // push: the next staging barrier protects the queue
+    filter_flush<BLOCK, EPT, PULL>(sm, a, fo);   // push: the next staging barrier protects the queue
     j = j + nent - 1;
   }
   if (ovf) sm.ovf = 1u;
@@ -354,10 +443,9 @@ __device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepA
                                              const uint32_t* __restrict__ fv, const uint32_t* __restrict__ fr,
                                              const uint32_t* __restrict__ fs, uint32_t* __restrict__ dist,
                                              uint32_t* __restrict__ bm_cur, const FilterOut& fo,
-                                             uint32_t warp_thr, uint32_t cta_thr) {
+                                             uint32_t warp_thr, uint32_t cta_thr, const void* __restrict__ edges) {
   constexpr uint32_t NW = BLOCK / 32;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const void* __restrict__ edges = a.g.edges;
   const uint32_t wbits = a.g.wbits;
   bool ovf = false;
   auto relax = [&](uint32_t e, uint32_t du) {
@@ -401,7 +489,7 @@ __device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepA
           const uint32_t o = base + q * BLOCK + tid;
           if (o < d) relax(r + o, u);
         }
-        filter_flush(sm, fo);
+        filter_flush(sm, a, fo);
       }
     }
     // warp per vertex
@@ -417,7 +505,7 @@ __device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepA
         moff += 32 * EPT;
         if (moff >= d) { mi += NW; moff = 0; }
       }
-      filter_flush(sm, fo);
+      filter_flush(sm, a, fo);
     }
     // thread per vertex
     uint32_t off = 0;
@@ -426,7 +514,7 @@ __device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepA
       for (int q = 0; q < EPT; ++q)
         if (off + q < deg) relax(row + off + q, du);
       off += EPT;
-      filter_flush(sm, fo);
+      filter_flush(sm, a, fo);
     }
   }
   if (ovf) sm.ovf = 1u;
@@ -444,8 +532,9 @@ __device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepA
 template <int BLOCK, int EPT, bool PK>
 __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t F, uint32_t Etot,
                                              const uint32_t* __restrict__ S, const uint32_t* __restrict__ R,
-                                             const uint32_t* __restrict__ V, uint32_t* __restrict__ dist,
-                                             uint32_t* __restrict__ bm_cur, const FilterOut& fo) {
+                                             const uint32_t* __restrict__ V, const void* __restrict__ edges,
+                                             uint32_t* __restrict__ dist, uint32_t* __restrict__ bm_cur,
+                                             const FilterOut& fo) {
   constexpr uint32_t NW = BLOCK / 32;
   constexpr uint32_t QW = 128;   // per-warp queue slots
   constexpr int WU = GG_WU;      // chunks of 32 edges per step
@@ -460,7 +549,6 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
   uint32_t qn = 0, fn = 0;            // warp-uniform queue lengths
   uint32_t fmin = kInf;
   bool ovf = false;
-  const void* __restrict__ edges = a.g.edges;
   const uint32_t wbits = a.g.wbits;
   const unsigned long long W = (unsigned long long)gridDim.x * NW;
   const unsigned long long gw = (unsigned long long)blockIdx.x * NW + warp;
@@ -468,6 +556,15 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
 
   auto flush_near = [&]() {
     __syncwarp();
+    if (fo.lh) {
+      for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        append32<true>(a, fo, i < qn, i < qn ? qv[i] : 0u);
+      }
+      qn = 0;
+      __syncwarp();
+      return;
+    }
     uint32_t run = 0;
     for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
       const uint32_t i = i0 + lane;
@@ -638,28 +735,147 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
 //                      parked, so the near phase already expanded it: drop
 //   dist[v] <  t_cur   move it to the next (near) frontier
 //   otherwise          keep it in the other far pile
+// Warp-level: 32 entries per step, one append per warp and list, no CTA barriers.
 template <int BLOCK, int EPT>
 __device__ __forceinline__ void far_split(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, const FilterOut& fo,
                                           uint32_t* __restrict__ dist, const uint32_t* __restrict__ far_in,
                                           uint32_t nfar, uint32_t t_prev) {
-  for (uint32_t base = blockIdx.x * BLOCK; base < nfar; base += gridDim.x * BLOCK) {
-    const uint32_t i = base + threadIdx.x;
+  const unsigned FULL = 0xFFFFFFFFu;
+  const uint32_t lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t W = gridDim.x * (BLOCK / 32);
+  uint32_t fmin = kInf;
+  for (uint32_t base = (blockIdx.x * (BLOCK / 32) + (threadIdx.x >> 5)) * 32u; base < nfar; base += W * 32u) {
+    const uint32_t i = base + lane;
+    uint32_t v = 0;
+    bool near = false, keep = false;
     if (i < nfar) {
-      const uint32_t v = far_in[i];
+      v = far_in[i];
       const uint32_t d = ld_cg(dist + v);
+      const uint32_t bit = 1u << (v & 31);
       if (d < fo.t_cur) {
-        atomicAnd(fo.bm_far + (v >> 5), ~(1u << (v & 31)));
-        if (d >= t_prev) filter_candidate(sm, fo, v, d);
+        atomicAnd(fo.bm_far + (v >> 5), ~bit);
+        if (d >= t_prev) near = !(atomicOr(fo.bm_next + (v >> 5), bit) & bit);
       } else {
-        // stays far: the filter's far branch re-appends it (its far bit is still set,
-        // so append directly)
-        atomicMin(&sm.fmin, d);
-        const uint32_t q = MPSmem<BLOCK, EPT>::ECAP - 1 - atomicAdd(&sm.qfn, 1u);
-        sm.qv[q] = v;
+        keep = true;   // its far bit stays set
+        fmin = min(fmin, d);
       }
     }
-    filter_flush(sm, fo);
+    const unsigned kb = __ballot_sync(FULL, keep);
+    if (kb) {
+      uint32_t b = 0;
+      if (lane == 0) {
+        b = atomicAdd(fo.far_cnt, (uint32_t)__popc(kb));
+        if (fo.far_add) atomicAdd(fo.far_add, (uint32_t)__popc(kb));
+      }
+      b = __shfl_sync(FULL, b, 0);
+      if (keep) fo.far[b + __popc(kb & lt)] = v;
+    }
+    if (__any_sync(FULL, near)) {
+      if (fo.lh) append32<true>(a, fo, near, v);
+      else append32<false>(a, fo, near, v);
+    }
   }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) fmin = min(fmin, __shfl_xor_sync(FULL, fmin, o));
+  if (lane == 0 && fmin != kInf) atomicMin(&sm.fmin, fmin);
+}
+
+// Heavy superstep by pull (symmetric graphs, bucket no wider than delta).
+// Every vertex v not yet settled (dist[v] >= t_cur) takes the minimum of
+// dist[u] + w over its heavy edges (u, w) from settled vertices
+// (dist[u] < t_cur); in a symmetric graph these are exactly the heavy edges
+// into v.  Heavy edges of vertices settled in earlier buckets were relaxed
+// then and cannot improve v again, so the minimum covers the heavy edges of
+// the current R list, and every improvement is >= t_cur (far pile).  A warp
+// takes 32 consecutive vertices and walks their heavy edges as one list, 32
+// edges per step; each v is written by its own lane only (no atomics on
+// dist).  Chosen over the push form when R's heavy edges outnumber those of
+// the unsettled vertices (the dense core settles first on skewed graphs).
+template <int BLOCK, int EPT, bool PK>
+__device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, const FilterOut& fo,
+                                           uint32_t* __restrict__ dist, uint32_t* __restrict__ bm_r_old) {
+  const unsigned FULL = 0xFFFFFFFFu;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t n = a.g.n, t_cur = fo.t_cur, wbits = a.g.wbits;
+  const void* __restrict__ edges = a.lb.edges;
+  const uint32_t* __restrict__ lend = a.lb.lend;
+  uint32_t* wbest = sm.ec + warp * 32;
+  // the consumed R list is not read: clear its membership bitmap outright
+  for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < a.g.nwords; i += gridDim.x * BLOCK) bm_r_old[i] = 0u;
+  const uint32_t W = gridDim.x * (BLOCK / 32);
+  uint32_t fmin = kInf;
+  unsigned long long scanned = 0;
+  bool ovf = false;
+  for (uint32_t base = (blockIdx.x * (BLOCK / 32) + warp) * 32u; base < n; base += W * 32u) {
+    const uint32_t v = base + lane;
+    uint32_t dv = 0, hs = 0, deg = 0;
+    if (v < n) {
+      dv = ld_cg(dist + v);
+      if (dv >= t_cur) {
+        hs = __ldg(lend + v);
+        deg = __ldg(fo.ro + v + 1) - hs;
+      }
+    }
+    uint32_t x = deg;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(FULL, x, o);
+      if (lane >= (uint32_t)o) x += y;
+    }
+    const uint32_t T = __shfl_sync(FULL, x, 31);
+    if (T == 0) continue;   // warp-uniform
+    const uint32_t ex = x - deg;   // first list position of this lane's edges
+    wbest[lane] = kInf;
+    __syncwarp();
+    for (uint32_t c = 0; c < T; c += 32) {
+      const uint32_t j = c + lane;
+      // owner: the last lane whose first position is <= j (lanes without edges
+      // share their successor's position and come before it)
+      uint32_t k = 0;
+#pragma unroll
+      for (int step = 16; step; step >>= 1) {
+        const uint32_t sv = __shfl_sync(FULL, ex, k + step);
+        if (sv <= j) k += step;
+      }
+      const uint32_t ks = __shfl_sync(FULL, hs, k), kx = __shfl_sync(FULL, ex, k);
+      uint32_t cand = kInf;
+      if (j < T) {
+        const uint2 ed = load_edge<PK>(edges, ks + (j - kx), wbits);
+        const uint32_t du = ld_cg(dist + ed.x);
+        if (du < t_cur) cand = add_sat(du, ed.y, ovf);
+      }
+      const unsigned same = __match_any_sync(FULL, k);
+      const uint32_t r = __reduce_min_sync(same, cand);
+      if (r != kInf && lane == (uint32_t)(__ffs(same) - 1)) atomicMin(&wbest[k], r);
+    }
+    __syncwarp();
+    const uint32_t best = wbest[lane];
+    bool far = false;
+    if (v < n && best < dv) {
+      dist[v] = best;
+      fmin = min(fmin, best);
+      const uint32_t bit = 1u << (v & 31);
+      far = !(atomicOr(fo.bm_far + (v >> 5), bit) & bit);
+    }
+    const unsigned fb = __ballot_sync(FULL, far);
+    if (fb) {
+      uint32_t b = 0;
+      if (lane == 0) b = atomicAdd(fo.far_cnt, (uint32_t)__popc(fb));
+      b = __shfl_sync(FULL, b, 0);
+      if (far) fo.far[b + __popc(fb & lt)] = v;
+    }
+    scanned += T;
+    __syncwarp();
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) fmin = min(fmin, __shfl_xor_sync(FULL, fmin, o));
+  if (lane == 0) {
+    if (fmin != kInf) atomicMin(&sm.fmin, fmin);
+    if (scanned) atomicAdd(&a.ctl->edges_scanned, scanned);
+  }
+  if (__any_sync(FULL, ovf) && lane == 0) sm.ovf = 1u;
 }
 
 // Shared prologue: reset the CTA's queue, clear the bitmap left by a pull step.
@@ -713,30 +929,63 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
       ctl->splits += 1;
     }
     const uint32_t nfar = atomicAdd(&ctl->far_cnt[fp], 0u);
+    const uint32_t lh = ctl->lh;
+    uint32_t rn = 0;   // R list of the epoch the next superstep works in
+    unsigned long long rE = 0;   // and its heavy edges
+    if (lh) {
+      if (mode == MODE_HEAVY || mode == MODE_HEAVY_PULL) {   // R[epoch] is consumed: the next epoch begins
+        ctl->heavy_done += E;
+        ctl->rcnt[ctl->epoch & 1u] = 0ull;
+        ctl->epoch += 1u;
+      }
+      const unsigned long long r = atomicAdd(&ctl->rcnt[ctl->epoch & 1u], 0ull);
+      rn = (uint32_t)(r >> 32);
+      rE = (uint32_t)r;
+    }
     if (ctl->trace && it < ctl->trace_cap) {
       uint32_t* t = ctl->trace + 4ull * it;
       t[0] = f;
-      t[1] = mode == MODE_PUSH ? E : mode == MODE_PULL ? a.g.m : 0u;
+      t[1] = (mode == MODE_PUSH || mode == MODE_HEAVY || mode == MODE_HEAVY_PULL) ? E : mode == MODE_PULL ? a.g.m : 0u;
       t[2] = mode;
       t[3] = fn;
     }
     if (f > 0 && mode != MODE_SPLIT) {
-      ctl->edges_scanned += mode == MODE_PUSH ? E : a.g.m;
+      // a pull heavy step counts the edges it scans itself
+      ctl->edges_scanned += (mode == MODE_PUSH || mode == MODE_HEAVY) ? E : mode == MODE_PULL ? a.g.m : 0u;
       ctl->frontier_total += f;
       ctl->max_frontier = max(ctl->max_frontier, f);
       ctl->pull_iters += mode == MODE_PULL ? 1u : 0u;
     }
     ctl->cnt[p] = 0ull;
     ctl->done_ctas = 0u;
-    ctl->clear_prev = (mode == MODE_PULL) ? 1u : 0u;
+    // light/heavy: vertices without light edges are marked in the next
+    // bitmap but never enter the frontier, so the old bitmap is always cleared
+    ctl->clear_prev = (mode == MODE_PULL || lh) ? 1u : 0u;
     uint32_t nm;
-    if (fn == 0 && nfar > 0) {
+    if (lh && (fn > 0 || rn > 0)) {
+      // light edges of the near frontier first; when it is empty, one heavy
+      // superstep over the vertices that settled since the last one
+      nm = fn > 0 ? MODE_PUSH : MODE_HEAVY;
+      if (nm == MODE_HEAVY && ctl->heavy_pull_ok && ctl->t_cur != kInf) {
+        // pull when R's heavy edges outnumber those still unsettled (plus the
+        // cost of the dense pass over the distances)
+        const unsigned long long left = ctl->heavy_total > ctl->heavy_done + rE
+                                            ? ctl->heavy_total - ctl->heavy_done - rE : 0ull;
+        if (rE > left + a.g.n / 8) nm = MODE_HEAVY_PULL;
+      }
+    } else if (fn == 0 && nfar > 0) {
       // near frontier exhausted: raise the threshold past the smallest parked distance
       nm = MODE_SPLIT;
       const uint32_t fmin = ctl->far_min;
       const unsigned long long t1 = (unsigned long long)ctl->t_cur + ctl->delta;
       const unsigned long long t2 = (unsigned long long)fmin + 1;
-      const unsigned long long tn = t1 > t2 ? t1 : t2;
+      unsigned long long tn = t1 > t2 ? t1 : t2;
+      // light/heavy: once the vertices not yet settled hold only a small share
+      // of the heavy edges, the rest of the run is one bucket (the sparse tail
+      // of a skewed graph costs more in supersteps than in re-relaxations)
+      if (lh && ctl->drain_div &&
+          (ctl->heavy_total - min(ctl->heavy_done, ctl->heavy_total)) * ctl->drain_div < (unsigned long long)a.g.m)
+        tn = kInf;
       ctl->t_prev = ctl->t_cur;
       ctl->t_cur = tn >= kInf ? kInf : (uint32_t)tn;
       ctl->far_min = kInf;
@@ -751,7 +1000,7 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
     }
     ctl->mode = nm;
     ctl->iter = it + 1;
-    bool more = fn != 0 || nfar != 0;
+    bool more = fn != 0 || nfar != 0 || rn != 0;
     if (more && it + 1 >= ctl->max_iter) {
       ctl->status |= DS_ITER_CAP;
       more = false;
@@ -769,9 +1018,12 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
 // One superstep; LB selects the push advance (merge-path tiles, degree bins
 // or warp streaming) (pull is the same merge-path sweep in both); a split step
 // refills the near frontier from the far pile.
-template <int BLOCK, int EPT, int LB, bool PK, int WM>
+template <int BLOCK, int EPT, int LB, bool PK, int WMV>
 __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_superstep(StepArgs a, cudaGraphConditionalHandle cond,
                                                                        int use_cond) {
+  // WMV: the weight mode, or kWmU32Lh for integer weights with light/heavy buckets
+  constexpr bool LH = WMV == kWmU32Lh;
+  constexpr int WM = LH ? (int)WM_U32 : WMV;
   extern __shared__ __align__(16) unsigned char smraw[];
   MPSmem<BLOCK, EPT>& sm = *reinterpret_cast<MPSmem<BLOCK, EPT>*>(smraw);
   Ctl* ctl = a.ctl;
@@ -798,25 +1050,54 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_supers
   fo.far_cnt = &ctl->far_cnt[mode == MODE_SPLIT ? fp ^ 1u : fp];
   fo.far_add = nullptr;
   fo.wmode = WM;   // compile-time: relax_add folds to one arithmetic path
+  fo.lh = 0u;
+  const void* edges = a.g.edges;
+  const uint32_t* fS = a.fr.fs[p];
+  const uint32_t* fR = a.fr.fr[p];
+  const uint32_t* fV = a.fr.fv[p];
+  uint32_t fw = f, Ew = E;   // entries and edges this superstep works on
+  if (LH) {
+    // new near vertices join the R list of the current epoch, or of the next
+    // one while the heavy superstep consumes the current list
+    const uint32_t ep = ctl->epoch;
+    const uint32_t rj = (mode == MODE_HEAVY || mode == MODE_HEAVY_PULL ? ep + 1u : ep) & 1u;
+    fo.sinks = 0u;   // the light/heavy append checks both degrees itself
+    fo.lh = 1u + rj;
+    edges = a.lb.edges;
+    if (mode == MODE_HEAVY || mode == MODE_HEAVY_PULL) {
+      const uint32_t rc = ep & 1u;
+      const unsigned long long r = ctl->rcnt[rc];
+      fw = (uint32_t)(r >> 32);
+      Ew = (uint32_t)r;
+      fS = pick2(a.lb.rs, rc);
+      fR = pick2(a.lb.rr, rc);
+      fV = pick2(a.lb.rv, rc);
+      bm_cur = pick2(a.lb.bm_r, rc);   // R entries clear their membership words as they are loaded
+    }
+  }
   superstep_prologue(sm, a, it, ctl->clear_prev != 0);
   if (mode == MODE_SPLIT) {
     far_split(sm, a, fo, dist, a.fr.far[fp], ctl->far_cnt[fp], ctl->t_prev);
-  } else if (f > 0) {
-    if (mode == MODE_PUSH) {
+  } else if (LH && mode == MODE_HEAVY_PULL) {
+    heavy_pull<BLOCK, EPT, PK>(sm, a, fo, dist, pick2(a.lb.bm_r, ctl->epoch & 1u));
+  } else if (fw > 0) {
+    if (mode == MODE_PUSH || mode == MODE_HEAVY) {
       if (LB == LB_BINS)
-        bins_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fv[p], a.fr.fr[p], a.fr.fs[p], dist, bm_cur, fo,
-                                     ctl->warp_thr, ctl->cta_thr);
+        bins_advance<BLOCK, EPT, PK>(sm, a, fw, Ew, fV, fR, fS, dist, bm_cur, fo, ctl->warp_thr, ctl->cta_thr,
+                                     edges);
+      else if (LB == LB_WARP && LH && mode == MODE_HEAVY)   // separate copies keep the pointer selects
+        warp_advance<BLOCK, EPT, PK>(sm, a, fw, Ew, fS, fR, fV, edges, dist, bm_cur, fo);   // out of the loop
       else if (LB == LB_WARP)
-        warp_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], dist, bm_cur, fo);
+        warp_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], edges, dist,
+                                     a.fr.bm[it % 3], fo);
       else
-        mp_advance<BLOCK, EPT, false, PK>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], a.g.edges, dist,
-                                          bm_cur, fo);
+        mp_advance<BLOCK, EPT, false, PK>(sm, a, fw, Ew, fS, fR, fV, edges, dist, bm_cur, fo);
     } else {
       mp_advance<BLOCK, EPT, true, PK>(sm, a, a.g.np, a.g.m, a.g.ps, a.g.ps, a.g.pv, a.g.t_edges, dist, bm_cur,
                                        fo);
     }
   }
-  superstep_finalize(sm, a, it, f, E, mode, cond, use_cond);
+  superstep_finalize(sm, a, it, fw, Ew, mode, cond, use_cond);
 }
 
 // Bounded grid barrier for the persistent kernel: generation counter, the
@@ -892,6 +1173,7 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_bsp_pe
     fo.far_cnt = &ctl->fcnt3[mode == MODE_SPLIT ? pile_out : pile];
     fo.far_add = &ctl->fadd3[s0];
     fo.wmode = WM;   // compile-time: relax_add folds to one arithmetic path
+    fo.lh = 0u;      // light/heavy buckets run in the launched-superstep policies only
     superstep_prologue(sm, a, it, clear);
     if (lead) {
       ctl->cnt3[s2] = 0ull;      // written next superstep; its readers are two barriers back
@@ -905,9 +1187,10 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_bsp_pe
       if (mode == MODE_PUSH) {
         if (LB == LB_BINS)
           bins_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fv[p], a.fr.fr[p], a.fr.fs[p], dist, bm_cur, fo,
-                                       ctl->warp_thr, ctl->cta_thr);
+                                       ctl->warp_thr, ctl->cta_thr, a.g.edges);
         else if (LB == LB_WARP)
-          warp_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], dist, bm_cur, fo);
+          warp_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], a.g.edges, dist, bm_cur,
+                                       fo);
         else
           mp_advance<BLOCK, EPT, false, PK>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], a.g.edges, dist,
                                             bm_cur, fo);
@@ -1004,11 +1287,15 @@ struct RunParams {
   uint32_t delta;                  // near-far bucket width (kInf: no split)
   uint32_t wmode;                  // WM_*
   unsigned long long watchdog_ns;
+  uint32_t lh;                     // light/heavy buckets (StepArgs::lb holds the buffers)
+  uint32_t drain_div;
+  uint32_t heavy_pull_ok;
+  unsigned long long heavy_total;
 };
 
 // dist := the unreached value everywhere (INF, or FLT_MAX for binary32
 // distances; vectorised 16-byte stores when aligned); bitmaps := 0.
-__global__ void k_init(StepArgs a, uint32_t* dist, uint32_t unreached) {
+__global__ void k_init(StepArgs a, uint32_t* dist, uint32_t unreached, uint32_t* bm_r0, uint32_t* bm_r1) {
   const uint32_t n = a.g.n;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1025,29 +1312,53 @@ __global__ void k_init(StepArgs a, uint32_t* dist, uint32_t unreached) {
     a.fr.bm[1][i] = 0u;
     a.fr.bm[2][i] = 0u;
     a.fr.bm_far[i] = 0u;
+    if (bm_r0) {
+      bm_r0[i] = 0u;
+      bm_r1[i] = 0u;
+    }
   }
 }
 
 // dist[src] := 0, frontier := {src} (when src has out-edges), counters reset.
+// Light/heavy runs: src's light edges form the first frontier and its heavy
+// edges the first R list (a source without light edges starts with the heavy
+// superstep).
 __global__ void k_init_tail(StepArgs a, RunParams rp) {
   Ctl* ctl = a.ctl;
   const uint32_t src = rp.src;
   rp.dist[src] = 0u;
   const uint32_t rs = a.g.ro[src], re = a.g.ro[src + 1];
-  if (re > rs) {
+  const uint32_t le = rp.lh ? a.lb.lend[src] : re;   // end of the edges the first frontier relaxes
+  if (le > rs) {
     a.fr.fv[0][0] = src;
     a.fr.fr[0][0] = rs;
     a.fr.fs[0][0] = 0u;
     a.fr.bm[0][src >> 5] = 1u << (src & 31);
-    ctl->cnt[0] = (1ull << 32) | (re - rs);
+    ctl->cnt[0] = (1ull << 32) | (le - rs);
   } else {
     ctl->cnt[0] = 0ull;
   }
+  ctl->rcnt[0] = 0ull;
+  ctl->rcnt[1] = 0ull;
+  const bool heavy0 = rp.lh && re > le;
+  if (heavy0) {
+    a.lb.rv[0][0] = src;
+    a.lb.rr[0][0] = le;
+    a.lb.rs[0][0] = 0u;
+    a.lb.bm_r[0][src >> 5] = 1u << (src & 31);
+    ctl->rcnt[0] = (1ull << 32) | (re - le);
+  }
+  ctl->lh = rp.lh;
+  ctl->epoch = 0;
+  ctl->drain_div = rp.drain_div;
+  ctl->heavy_pull_ok = rp.heavy_pull_ok;
+  ctl->heavy_total = rp.heavy_total;
+  ctl->heavy_done = 0ull;
   ctl->cnt[1] = 0ull;
   ctl->iter = 0;
   ctl->done_ctas = 0;
   ctl->status = 0;
-  ctl->mode = rp.dir == DIR_PULL ? MODE_PULL : MODE_PUSH;
+  ctl->mode = rp.dir == DIR_PULL ? MODE_PULL : (le == rs && heavy0) ? MODE_HEAVY : MODE_PUSH;
   ctl->clear_prev = 0;
   ctl->src = src;
   ctl->max_iter = rp.max_iter;
@@ -1090,22 +1401,27 @@ __global__ void k_init_tail(StepArgs a, RunParams rp) {
 
 constexpr int kBlock = 256;
 constexpr int kEpt = GG_EPT;
-// kernel variants: (load balance x packed edges) x weight mode
-constexpr int kVariants = 18;
+// kernel variants: (load balance x packed edges) x (weight mode, or integer
+// weights with light/heavy buckets)
+constexpr int kVariants = kBspVariants;
+static_assert(kVariants == 3 * 2 * 4, "variant table");
 
-constexpr int variant_of(int lb, bool packed, uint32_t wmode) { return (lb * 2 + (packed ? 1 : 0)) * 3 + (int)wmode; }
+constexpr int variant_of(int lb, bool packed, uint32_t wmode, bool lh) {
+  return (lb * 2 + (packed ? 1 : 0)) * 4 + (lh ? kWmU32Lh : (int)wmode);
+}
 
 template <int LB, bool PK, int WM>
 void* superstep_ptr() { return reinterpret_cast<void*>(&k_superstep<kBlock, kEpt, LB, PK, WM>); }
+// the persistent policy has no light/heavy form: its slot holds the plain integer kernel
 template <int LB, bool PK, int WM>
-void* persistent_ptr() { return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, LB, PK, WM>); }
+void* persistent_ptr() {
+  return reinterpret_cast<void*>(&k_bsp_persistent<kBlock, kEpt, LB, PK, WM == kWmU32Lh ? 0 : WM>);
+}
 
-#define GG_VARIANT_TABLE(F)                                                                                   \
-  {F<LB_TILE, false, 0>(), F<LB_TILE, false, 1>(), F<LB_TILE, false, 2>(), F<LB_TILE, true, 0>(),              \
-   F<LB_TILE, true, 1>(),  F<LB_TILE, true, 2>(),  F<LB_BINS, false, 0>(), F<LB_BINS, false, 1>(),             \
-   F<LB_BINS, false, 2>(), F<LB_BINS, true, 0>(),  F<LB_BINS, true, 1>(),  F<LB_BINS, true, 2>(),              \
-   F<LB_WARP, false, 0>(), F<LB_WARP, false, 1>(), F<LB_WARP, false, 2>(), F<LB_WARP, true, 0>(),              \
-   F<LB_WARP, true, 1>(),  F<LB_WARP, true, 2>()}
+#define GG_VARIANT_ROW(F, LBV, PKV) F<LBV, PKV, 0>(), F<LBV, PKV, 1>(), F<LBV, PKV, 2>(), F<LBV, PKV, kWmU32Lh>()
+#define GG_VARIANT_TABLE(F)                                                                   \
+  {GG_VARIANT_ROW(F, LB_TILE, false), GG_VARIANT_ROW(F, LB_TILE, true), GG_VARIANT_ROW(F, LB_BINS, false), \
+   GG_VARIANT_ROW(F, LB_BINS, true),  GG_VARIANT_ROW(F, LB_WARP, false), GG_VARIANT_ROW(F, LB_WARP, true)}
 
 void* superstep_fn(int variant) {
   static void* const table[kVariants] = GG_VARIANT_TABLE(superstep_ptr);
@@ -1190,7 +1506,7 @@ gg_status build_graph_exec(gg_graph* g, int variant) {
   cudaGraphNode_t wnode;
   GG_CK(cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  StepArgs a{g->dg, w.fr, w.ctl};
+  StepArgs a{g->dg, w.fr, w.ctl, g->lhb};   // light/heavy variants are built after lh_prepare
   int use_cond = 1;
   void* args[] = {&a, &h, &use_cond};
   cudaKernelNodeParams kp = {};
@@ -1216,7 +1532,6 @@ gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o
   if (st != GG_OK) return st;
   // automatic choice: warp streaming (measured faster than merge-path tiles on RMAT, equal on grids)
   const int lb = o.lb_mode == GG_LB_BINS ? LB_BINS : o.lb_mode == GG_LB_MERGE_PATH ? LB_TILE : LB_WARP;
-  const int variant = variant_of(lb, g->dg.packed != 0, wmode);
   BspWorkspace& w = g->bsp;
   RunParams rp;
   rp.src = src;
@@ -1228,9 +1543,30 @@ gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o
   // phase finalises at least one vertex and runs at most its bucket's size + 2
   // steps); without, by n + 1
   // buckets are integer distance ranges: binary32 and hop-count runs go without
-  rp.delta = (o.delta == GG_DELTA_NONE || wmode != WM_U32) ? kInf : (o.delta ? o.delta : g->default_delta);
+  // light/heavy buckets: launched-superstep policies, push, integer weights,
+  // and a width that leaves some edge heavy; the graph's own default width is
+  // the light/heavy one where it has one
+  const bool lh_ok = (o.policy == GG_POLICY_BSP_GRAPH || o.policy == GG_POLICY_BSP_HOST) &&
+                     o.light_heavy != GG_LH_OFF && rp.dir == DIR_PUSH && wmode == WM_U32 && g->m > 0;
+  if (o.delta == GG_DELTA_NONE || wmode != WM_U32) rp.delta = kInf;
+  else if (o.delta) rp.delta = o.delta;
+  else rp.delta = (lh_ok && g->default_delta_lh != GG_DELTA_NONE) ? g->default_delta_lh : g->default_delta;
   rp.wmode = wmode;
-  const unsigned long long cap = rp.delta == kInf ? (unsigned long long)g->n + 2 : 4ull * g->n + 16;
+  rp.lh = (lh_ok && rp.delta != kInf && rp.delta <= g->wmax) ? 1u : 0u;
+  rp.drain_div = GG_LH_DRAIN;
+  rp.heavy_pull_ok = 0u;
+  rp.heavy_total = 0ull;
+  if (rp.lh) {
+    st = lh_prepare(g, rp.delta, s);
+    if (st != GG_OK) return st;
+    // a symmetric graph's heavy in-edges are its heavy out-edges
+    rp.heavy_pull_ok = (g->symmetric && GG_HEAVY_PULL) ? 1u : 0u;
+    rp.heavy_total = g->lh_heavy_total;
+  }
+  const int variant = variant_of(lb, g->dg.packed != 0, wmode, rp.lh != 0);
+  // a light/heavy run adds at most one heavy superstep per settled vertex
+  const unsigned long long cap = rp.delta == kInf ? (unsigned long long)g->n + 2
+                                 : rp.lh ? 6ull * g->n + 16 : 4ull * g->n + 16;
   rp.max_iter = o.max_iterations ? o.max_iterations : (cap >= 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)cap);
   rp.watchdog_ns = o.watchdog_ns ? o.watchdog_ns : 60000000000ull;
   rp.trace = o.trace;
@@ -1239,12 +1575,13 @@ gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o
   rp.cta_thr = o.cta_threshold ? o.cta_threshold : 1024u;
   if (rp.cta_thr < rp.warp_thr) rp.cta_thr = rp.warp_thr;
   const uint32_t max_iter = rp.max_iter;
-  StepArgs a{g->dg, w.fr, w.ctl};
+  StepArgs a{g->dg, w.fr, w.ctl, g->lhb};
   const DeviceInfo di = device_info();
   const uint64_t work = std::max<uint64_t>(g->n / 4, g->dg.nwords);
   unsigned ib = (unsigned)std::min<uint64_t>((work + 255) / 256, (uint64_t)di.num_sms * 8);
   if (ib == 0) ib = 1;
-  k_init<<<ib, 256, 0, s>>>(a, dist, wmode == WM_F32 ? kFltMaxBits : kInf);
+  k_init<<<ib, 256, 0, s>>>(a, dist, wmode == WM_F32 ? kFltMaxBits : kInf, rp.lh ? g->lhb.bm_r[0] : nullptr,
+                            rp.lh ? g->lhb.bm_r[1] : nullptr);
   GG_CK(cudaGetLastError());
   k_init_tail<<<1, 1, 0, s>>>(a, rp);
   GG_CK(cudaGetLastError());

@@ -35,11 +35,24 @@ constexpr uint32_t kFltMaxBits = 0x7F7FFFFFu;   // FLT_MAX: "unreached" for bina
 // binary32 bit patterns (the paper's float weights), or unit weights (BFS).
 enum : uint32_t { WM_U32 = 0, WM_F32 = 1, WM_UNIT = 2 };
 
-enum : uint32_t { MODE_PUSH = 0, MODE_PULL = 1, MODE_SPLIT = 2 };
+enum : uint32_t { MODE_PUSH = 0, MODE_PULL = 1, MODE_SPLIT = 2, MODE_HEAVY = 3, MODE_HEAVY_PULL = 4 };
 enum : uint32_t { DIR_AUTO = 0, DIR_PUSH = 1, DIR_PULL = 2 };
 
 // device-status bits, mapped to gg_status on the host
 enum : uint32_t { DS_OVERFLOW = 1u, DS_ITER_CAP = 2u, DS_TIMEOUT = 4u, DS_INTERNAL = 8u };
+
+// Buffers of the light/heavy bucket variant (allocated on first use by a
+// graph; see Ctl::lh).  Rows of lh_edges hold the same edges as the graph's
+// own array, light ones (weight < delta) first: the light edges of v are
+// [ro[v], lend[v]) and its heavy edges [lend[v], ro[v+1]).
+struct LhBufs {
+  const void* edges;   // uint2[m] or packed u32[m], rows partitioned by weight < delta
+  const uint32_t* lend;
+  uint32_t* rv[2];     // R lists by epoch parity: vertex, heavy row start, heavy-edge prefix
+  uint32_t* rr[2];
+  uint32_t* rs[2];
+  uint32_t* bm_r[2];   // R membership bitmaps by epoch parity
+};
 
 struct Ctl {
   unsigned long long cnt[2];   // (count << 32) | edge total of the frontier being built, by parity
@@ -79,6 +92,23 @@ struct Ctl {
   unsigned long long watchdog_ns;
   unsigned long long edges_scanned;
   unsigned long long frontier_total;
+  // light/heavy buckets (Meyer-Sanders delta-stepping on top of the near-far
+  // split): near supersteps relax only the light edges of their vertices; a
+  // vertex that drops below t_cur joins the R list of the current epoch once,
+  // and when the near frontier is empty one heavy superstep relaxes the heavy
+  // edges of R (each heavy edge once per settled vertex) and starts the next
+  // epoch.  Vertices of a bucket whose distance is final before its heavy
+  // superstep never re-scan heavy edges, which is where plain near-far and
+  // Bellman-Ford spend most of their re-relaxations.
+  uint32_t lh;                       // 1: this run uses light/heavy buckets
+  uint32_t epoch;                    // heavy supersteps completed
+  unsigned long long rcnt[2];        // (count << 32) | heavy-edge total of R[0], R[1]
+  uint32_t drain_div;                // unsettled heavy edges < m / drain_div end bucketing
+  // heavy superstep by pull (symmetric graphs): chosen when R's heavy edges
+  // outnumber those of the vertices not yet settled
+  uint32_t heavy_pull_ok;
+  unsigned long long heavy_total;    // heavy edges of the graph
+  unsigned long long heavy_done;     // heavy edges of the vertices settled so far
 };
 
 struct DevGraph {

@@ -15,6 +15,10 @@
 
 #include "gg_host.h"
 
+#ifndef GG_LH_K
+#define GG_LH_K 3.0   // light edges per vertex aimed at by the default light/heavy bucket width
+#endif
+
 namespace gg {
 
 namespace {
@@ -161,6 +165,55 @@ __global__ void k_pull_list(uint32_t n, const uint32_t* __restrict__ t_ro, const
     if (t_ro[v + 1] > t_ro[v]) {
       pv[pos[v]] = (uint32_t)v;
       ps[pos[v]] = t_ro[v];
+    }
+  }
+}
+
+// Light/heavy partition of every row (bucket width delta): flag[e] = 1 when
+// edge e is light (weight < delta); flag[m] = 0 closes the scan.
+template <bool PK>
+__global__ void k_lh_flags(uint32_t m, const void* __restrict__ edges, uint32_t wbits, uint32_t delta,
+                           uint32_t* __restrict__ flag) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const uint32_t w = PK ? (static_cast<const uint32_t*>(edges)[e] & ((1u << wbits) - 1u))
+                          : static_cast<const uint2*>(edges)[e].y;
+    flag[e] = w < delta ? 1u : 0u;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) flag[m] = 0u;
+}
+
+// lend[v] = ro[v] + (light edges of row v), from the exclusive scan L of the flags
+__global__ void k_lh_lend(uint32_t n, const uint32_t* __restrict__ ro, const uint32_t* __restrict__ L,
+                          uint32_t* __restrict__ lend) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    lend[v] = ro[v] + (L[ro[v + 1]] - L[ro[v]]);
+}
+
+// warp per row: light edges to the front of the row in their original order,
+// heavy edges after them in theirs
+template <bool PK>
+__global__ void k_lh_scatter(uint32_t n, const uint32_t* __restrict__ ro, const void* __restrict__ edges,
+                             const uint32_t* __restrict__ L, const uint32_t* __restrict__ lend, uint32_t wbits,
+                             uint32_t delta, void* __restrict__ out) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t u = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
+    const uint32_t r0 = ro[u], r1 = ro[u + 1];
+    if (r1 == r0) continue;
+    const uint32_t L0 = L[r0], le = lend[u];
+    for (uint32_t e = r0 + lane; e < r1; e += 32) {
+      const uint32_t before = L[e] - L0;   // light edges of the row before e
+      if (PK) {
+        const uint32_t x = static_cast<const uint32_t*>(edges)[e];
+        const uint32_t d = (x & ((1u << wbits) - 1u)) < delta ? r0 + before : le + (e - r0 - before);
+        static_cast<uint32_t*>(out)[d] = x;
+      } else {
+        const uint2 x = static_cast<const uint2*>(edges)[e];
+        const uint32_t d = x.y < delta ? r0 + before : le + (e - r0 - before);
+        static_cast<uint2*>(out)[d] = x;
+      }
     }
   }
 }
@@ -341,6 +394,14 @@ gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m64, const uint32_t* ro_
     const double davg = g->dg.np ? (double)m / (double)g->dg.np : 1.0;
     const double d = (double)std::max<uint32_t>(wmax, 1) * 16.0;
     g->default_delta = (davg >= 8.0 || !m) ? GG_DELTA_NONE : (uint32_t)std::min(d, 4.0e9);
+    // light/heavy buckets (single-source bulk-synchronous loop only) on the
+    // same skewed graphs: width ~ GG_LH_K * wmax / mean degree, so that a
+    // vertex has about GG_LH_K light edges
+    g->default_delta_lh = GG_DELTA_NONE;
+    if (davg >= 8.0 && m && !g->float_weights && wmax >= 2) {
+      const double dl = std::max(1.0, std::floor((double)wmax * GG_LH_K / davg));
+      g->default_delta_lh = (uint32_t)std::min<double>(dl, (double)wmax);
+    }
   }
   g->dg.n = n;
   g->dg.m = m;
@@ -354,7 +415,67 @@ gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m64, const uint32_t* ro_
   return GG_OK;
 }
 
+gg_status lh_prepare(gg_graph* g, uint32_t delta, cudaStream_t s) {
+  if (g->lh_block && g->lh_delta == delta) return GG_OK;
+  const size_t n = g->n, m = g->m;
+  const bool pk = g->dg.packed != 0;
+  const size_t esz = pk ? sizeof(uint32_t) : sizeof(uint2);
+  auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
+  if (!g->lh_block) {
+    const size_t nw = (n + 31) / 32;
+    const size_t vb = sizeof(uint32_t) * std::max<size_t>(n, 1);
+    const size_t total = r256(esz * std::max<size_t>(m, 1)) + 7 * r256(vb) + 2 * r256(sizeof(uint32_t) * nw);
+    char* p = nullptr;
+    GG_CK(cudaMalloc(&p, total));
+    size_t off = 0;
+    auto take = [&](size_t b) { char* q = p + off; off += r256(b); return q; };
+    g->lhb.edges = take(esz * std::max<size_t>(m, 1));
+    g->lhb.lend = reinterpret_cast<const uint32_t*>(take(vb));
+    for (int i = 0; i < 2; ++i) {
+      g->lhb.rv[i] = reinterpret_cast<uint32_t*>(take(vb));
+      g->lhb.rr[i] = reinterpret_cast<uint32_t*>(take(vb));
+      g->lhb.rs[i] = reinterpret_cast<uint32_t*>(take(vb));
+    }
+    for (int i = 0; i < 2; ++i) g->lhb.bm_r[i] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * nw));
+    if (off != total) {
+      cudaFree(p);
+      return fail(GG_ERR_INTERNAL, "light/heavy buffer layout");
+    }
+    g->lh_block = p;
+    g->lh_bytes = total;
+  }
+  g->lh_delta = 0;   // invalid until the partition below is complete
+  uint32_t* L = nullptr;
+  GG_CK(cudaMallocAsync(&L, sizeof(uint32_t) * (m + 1), s));
+  if (pk) k_lh_flags<true><<<grid_for(m), 256, 0, s>>>((uint32_t)m, g->dg.edges, g->dg.wbits, delta, L);
+  else k_lh_flags<false><<<grid_for(m), 256, 0, s>>>((uint32_t)m, g->dg.edges, g->dg.wbits, delta, L);
+  GG_CK(cudaGetLastError());
+  gg_status st = scan_excl(L, (uint64_t)m + 1, s);
+  if (st != GG_OK) { cudaFreeAsync(L, s); return st; }
+  uint32_t nlight = 0;
+  GG_CK(cudaMemcpyAsync(&nlight, L + m, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  uint32_t* lend = const_cast<uint32_t*>(g->lhb.lend);
+  k_lh_lend<<<grid_for(n), 256, 0, s>>>((uint32_t)n, g->ro, L, lend);
+  GG_CK(cudaGetLastError());
+  if (m) {
+    void* out = const_cast<void*>(g->lhb.edges);
+    if (pk) k_lh_scatter<true><<<grid_for((uint64_t)n * 32), 256, 0, s>>>((uint32_t)n, g->ro, g->dg.edges, L, lend,
+                                                                            g->dg.wbits, delta, out);
+    else k_lh_scatter<false><<<grid_for((uint64_t)n * 32), 256, 0, s>>>((uint32_t)n, g->ro, g->dg.edges, L, lend,
+                                                                          g->dg.wbits, delta, out);
+    GG_CK(cudaGetLastError());
+  }
+  GG_CK(cudaFreeAsync(L, s));
+  GG_CK(cudaStreamSynchronize(s));
+  g->lh_heavy_total = m - nlight;
+  g->lh_delta = delta;
+  return GG_OK;
+}
+
 void graph_free(gg_graph* g) {
+  if (g->lh_block) cudaFree(g->lh_block);
+  g->lh_block = nullptr;
+  g->lh_delta = 0;
   if (g->t_ro && g->t_ro != g->ro) cudaFree(g->t_ro);
   if (g->t_edges && g->t_edges != g->edges) cudaFree(g->t_edges);
   if (g->t_edges4 && g->t_edges4 != g->edges4) cudaFree(g->t_edges4);

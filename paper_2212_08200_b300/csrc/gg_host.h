@@ -29,6 +29,11 @@ struct DeviceInfo {
 };
 DeviceInfo device_info();
 
+// Superstep kernel variants: load balance (3) x edge packing (2) x weight
+// mode (u32, binary32, unit, u32 with light/heavy buckets).
+constexpr int kWmU32Lh = 3;
+constexpr int kBspVariants = 3 * 2 * 4;
+
 // Workspace of the bulk-synchronous path (allocated on first use).
 struct BspWorkspace {
   Frontier fr{};
@@ -36,10 +41,10 @@ struct BspWorkspace {
   void* block = nullptr;      // single device allocation backing fr and ctl
   size_t bytes = 0;
   // CUDA graph with a conditional WHILE node around one superstep kernel,
-  // one per kernel variant (load balance x edge packing x weight mode).
-  cudaGraph_t graph[18] = {};
-  cudaGraphExec_t exec[18] = {};
-  int grid[18] = {};
+  // one per kernel variant.
+  cudaGraph_t graph[kBspVariants] = {};
+  cudaGraphExec_t exec[kBspVariants] = {};
+  int grid[kBspVariants] = {};
 };
 
 // Workspace of the asynchronous persistent path.
@@ -88,6 +93,16 @@ struct gg_graph {
   uint32_t wmax = 0;            // largest edge weight (bit pattern)
   bool float_weights = false;   // weights and distances are IEEE binary32 bit patterns
   uint32_t default_delta = 0;   // near-far bucket width used when gg_options.delta == 0
+  // light/heavy buckets of the single-source bulk-synchronous loop: bucket
+  // width used when gg_options.delta == 0 (GG_DELTA_NONE: none), and the
+  // light-first edge copy with its buffers (lh_delta = the width it is
+  // partitioned for, 0 before the first light/heavy run)
+  uint32_t default_delta_lh = GG_DELTA_NONE;
+  uint32_t lh_delta = 0;
+  uint64_t lh_heavy_total = 0;    // edges with weight >= lh_delta
+  void* lh_block = nullptr;
+  size_t lh_bytes = 0;
+  gg::LhBufs lhb{};
 };
 
 namespace gg {
@@ -109,5 +124,8 @@ constexpr int kLastBatch = 16;   // gg_graph::last_policy value after gg_sssp_ba
 gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m, const uint32_t* ro, const uint32_t* col,
                       const uint32_t* w, uint32_t flags, cudaStream_t s);
 void graph_free(gg_graph* g);
+// light-first edge copy partitioned for bucket width delta (and the R-list
+// buffers), built on first use and re-partitioned when delta changes
+gg_status lh_prepare(gg_graph* g, uint32_t delta, cudaStream_t s);
 gg_status status_from_device(uint32_t ds);
 }  // namespace gg
