@@ -43,6 +43,17 @@ struct BatchCtl {
   // distance >= t_cur is parked as a bit of fmask[v]; the vertices with
   // parked bits form the far list far_v[fsel]
   uint32_t t_cur, t_prev, delta, fsel, fcnt[2], far_min, mode, splits;
+  // light-first rounds (lh = 1; mode 2 = heavy superstep): light supersteps
+  // relax only the light edges (weight < the graph's light/heavy width) of
+  // their (vertex, sources) entries; every pair that improves is also ORed
+  // into the R mask of the epoch, and when the light frontier empties one
+  // heavy superstep relaxes the heavy edges of the R entries for their R
+  // masks and starts the next epoch.  No distance thresholds: the rounds are a
+  // label-correcting loop in which a heavy edge is scanned once per epoch
+  // that improved its source vertex.  R buffers rotate over three epochs;
+  // the masks of a consumed R list are cleared one superstep later.
+  uint32_t lh, epoch, zero_pending, zero_par;
+  unsigned long long rcnt[3];
 };
 
 struct BatchBufs {
@@ -53,6 +64,13 @@ struct BatchBufs {
   unsigned long long* fmask;
   uint32_t* far_v[2];
   BatchCtl* ctl;
+  // light-first rounds: the graph's light-first edge copy and the R lists
+  const void* ledges;
+  const uint32_t* lend;
+  uint32_t* rv[3];
+  uint32_t* rr[3];
+  uint32_t* rs[3];
+  unsigned long long* rmask[3];
 };
 
 namespace {
@@ -73,6 +91,7 @@ struct BSmem {
   // sources it improved (near, far), appended together after the chunk
   unsigned long long pm[kBNW][32], pf[kBNW][32];
   uint32_t pv[kBNW][32];
+  uint32_t rq[kBNW * kBQW];   // light-first rounds: per-warp queue of new R entries
   uint32_t wsum[kBNW];
   uint32_t qn, j, last, ovf;
   unsigned long long base;
@@ -104,7 +123,43 @@ __device__ __forceinline__ void load_row8(const uint32_t* row, uint32_t on, uint
   }
 }
 
-template <bool PK, bool VEC>
+// Append of up to 32 vertices, one per lane (have), to the list (fv, fr, fs)
+// whose counter is cnt: each brings the edges [rs, re) of its row, read here
+// (start[v], end[v]); vertices without such edges are left out.  One 64-bit
+// atomicAdd returns the list position and the edge-prefix base.
+__device__ __forceinline__ void b_append32(bool have, uint32_t v, const uint32_t* __restrict__ start,
+                                           const uint32_t* __restrict__ end, unsigned long long* cnt,
+                                           uint32_t* fv, uint32_t* fr, uint32_t* fs) {
+  const unsigned FULL = 0xFFFFFFFFu;
+  const uint32_t lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  uint32_t rs = 0, d = 0;
+  if (have) {
+    rs = __ldg(start + v);
+    d = __ldg(end + v) - rs;
+  }
+  const bool keep = d > 0;
+  const unsigned b = __ballot_sync(FULL, keep);
+  if (b == 0u) return;
+  uint32_t x = d;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(FULL, x, o);
+    if (lane >= (uint32_t)o) x += y;
+  }
+  const uint32_t tot = __shfl_sync(FULL, x, 31);
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(cnt, ((unsigned long long)__popc(b) << 32) | tot);
+  base = __shfl_sync(FULL, base, 0);
+  if (keep) {
+    const uint32_t pos = (uint32_t)(base >> 32) + __popc(b & lt);
+    fv[pos] = v;
+    fr[pos] = rs;
+    fs[pos] = (uint32_t)base + x - d;
+  }
+}
+
+template <bool PK, bool VEC, bool LH>
 __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, BatchBufs w, cudaGraphConditionalHandle cond,
                                                          int use_cond) {
   __shared__ BSmem sm;
@@ -112,20 +167,34 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t it = ctl->iter;
   const uint32_t pc = it % 3, pn = (it + 1) % 3, po = (it + 2) % 3;
-  const unsigned long long c = ctl->cnt[pc];
+  const uint32_t bmode0 = ctl->mode;
+  const uint32_t ep = LH ? ctl->epoch : 0u;
+  const bool heavy = LH && bmode0 == 2u;
+  const unsigned long long c = heavy ? ctl->rcnt[ep % 3] : ctl->cnt[pc];
   const uint32_t F = (uint32_t)(c >> 32), E = (uint32_t)c;
   const uint32_t K = ctl->k, col0 = ctl->col0;
   uint32_t* dist = ctl->dist;
-  const unsigned long long* Mc = pick3(w.mask, pc);
+  // the entries' source masks: the frontier's, or the R list's in a heavy superstep
+  const unsigned long long* Mc = heavy ? pick3(w.rmask, ep % 3) : pick3(w.mask, pc);
   unsigned long long* Mn = pick3(w.mask, pn);
   const uint32_t wbits = g.wbits;
-  const uint32_t T = ctl->t_cur, fsel = ctl->fsel, bmode = ctl->mode;
+  const uint32_t T = ctl->t_cur, fsel = ctl->fsel, bmode = heavy ? 0u : bmode0;
+  // new R entries join the epoch in progress (the next one during a heavy superstep)
+  const uint32_t rj = (heavy ? ep + 1u : ep) % 3;
   // zero the masks of F_{t-1}
   {
     const uint32_t Fo = (uint32_t)(ctl->cnt[po] >> 32);
     const uint32_t* fvo = pick3(w.fv, po);
     unsigned long long* Mo = pick3(w.mask, po);
     for (uint32_t i = blockIdx.x * kBB + tid; i < Fo; i += gridDim.x * kBB) Mo[fvo[i]] = 0ull;
+  }
+  // and those of the R list the last heavy superstep consumed
+  if (LH && ctl->zero_pending) {
+    const uint32_t zp = ctl->zero_par;
+    const uint32_t Ro = (uint32_t)(ctl->rcnt[zp] >> 32);
+    const uint32_t* rvo = pick3(w.rv, zp);
+    unsigned long long* RMo = pick3(w.rmask, zp);
+    for (uint32_t i = blockIdx.x * kBB + tid; i < Ro; i += gridDim.x * kBB) RMo[rvo[i]] = 0ull;
   }
   if (tid == 0) {
     sm.qn = 0;
@@ -212,10 +281,13 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
     // consecutive sources 8*l8 .. 8*l8+7 of the 64-source group, one 32-byte
     // sector of a distance row (two 16-byte vectors when VEC).
     const unsigned FULL = 0xFFFFFFFFu;
-    const uint32_t* S = pick3(w.fs, pc);
-    const uint32_t* R = pick3(w.fr, pc);
-    const uint32_t* V = pick3(w.fv, pc);
+    const uint32_t* S = heavy ? pick3(w.rs, ep % 3) : pick3(w.fs, pc);
+    const uint32_t* R = heavy ? pick3(w.rr, ep % 3) : pick3(w.fr, pc);
+    const uint32_t* V = heavy ? pick3(w.rv, ep % 3) : pick3(w.fv, pc);
+    const void* edges = LH ? w.ledges : g.edges;
     constexpr uint32_t QW = kBQW;
+    uint32_t* rq = sm.rq + warp * QW;   // light-first rounds: new R entries
+    uint32_t rqn = 0;                   // warp-uniform
     uint32_t* qv = sm.qv + warp * QW;   // this warp's queue of new frontier vertices
     uint32_t* qr = sm.qr + warp * QW;
     uint32_t* qd = sm.qd + warp * QW;
@@ -231,6 +303,16 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
       // rows (deferred on sink-free graphs), warp scan of the degrees, one
       // 64-bit atomic for the queue position and the edge-prefix base
       __syncwarp();
+      if (LH) {   // light edges [ro[v], lend[v]); vertices without any are left out
+        for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
+          const uint32_t i = i0 + lane;
+          b_append32(i < qn, i < qn ? qv[i] : 0u, g.ro, w.lend, &ctl->cnt[pn], pick3(w.fv, pn), pick3(w.fr, pn),
+                     pick3(w.fs, pn));
+        }
+        qn = 0;
+        __syncwarp();
+        return;
+      }
       uint32_t run = 0;
       for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
         const uint32_t i = i0 + lane;
@@ -264,6 +346,16 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
         pick3(w.fs, pn)[pos0 + i] = eb0 + qd[i];
       }
       qn = 0;
+      __syncwarp();
+    };
+    auto rflush = [&]() {   // heavy edges [lend[v], ro[v+1]) of new R entries
+      __syncwarp();
+      for (uint32_t i0 = 0; i0 < rqn; i0 += 32) {
+        const uint32_t i = i0 + lane;
+        b_append32(i < rqn, i < rqn ? rq[i] : 0u, w.lend, g.ro + 1, &ctl->rcnt[rj], pick3(w.rv, rj),
+                   pick3(w.rr, rj), pick3(w.rs, rj));
+      }
+      rqn = 0;
       __syncwarp();
     };
 
@@ -313,7 +405,7 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
         const bool valid = gidx < w1 && ks <= gidx && gidx < ke;
         uint32_t vv = 0, ww = 0;
         if (valid) {
-          const uint2 ed = load_edge<PK>(g.edges, kr + (gidx - ks), wbits);
+          const uint2 ed = load_edge<PK>(edges, kr + (gidx - ks), wbits);
           vv = ed.x;
           ww = ed.y;
         }
@@ -403,22 +495,32 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
         }
         // the chunk's appends, one edge per lane, their atomics in flight together
         __syncwarp();
-        bool app = false, fapp = false;
+        bool app = false, fapp = false, rapp = false;
         uint32_t vi = 0, rs = 0, re = 1;
         if (lane < (uint32_t)nvalid) {
           const unsigned long long nb = sm.pm[warp][lane], fb = sm.pf[warp][lane];
           if (nb | fb) {
             vi = sm.pv[warp][lane];
             // vertices without out-edges are never appended; on a graph
-            // without such sinks the row is read at the flush instead
-            if (g.sinks) {
+            // without such sinks (and in light-first rounds, whose appends
+            // check both degrees) the row is read at the flush instead
+            if (g.sinks && !LH) {
               rs = __ldg(g.ro + vi);
               re = __ldg(g.ro + vi + 1);
             }
             if (re > rs) {
               app = nb && atomicOr(Mn + vi, nb) == 0ull;
               fapp = fb && atomicOr(w.fmask + vi, fb) == 0ull;
+              if (LH) rapp = nb && atomicOr(pick3(w.rmask, rj) + vi, nb) == 0ull;
             }
+          }
+        }
+        if (LH) {
+          const unsigned rb = __ballot_sync(FULL, rapp);
+          if (rb) {
+            if (rapp) rq[rqn + __popc(rb & lt)] = vi;
+            rqn += __popc(rb);
+            if (rqn > QW - 32) rflush();
           }
         }
         const unsigned ab = __ballot_sync(FULL, app);
@@ -442,6 +544,7 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
         __syncwarp();
       }
       if (qn) flush();
+      if (LH && rqn) rflush();
     }
   }
   if (ovf) sm.ovf = 1u;
@@ -460,6 +563,30 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
       ctl->edges_scanned += E;
       ctl->frontier_total += F;
       ctl->max_frontier = max(ctl->max_frontier, F);
+    }
+    if (LH) {
+      ctl->cnt[po] = 0ull;
+      ctl->done_ctas = 0u;
+      ctl->iter = it + 1;
+      if (ctl->zero_pending) {   // this superstep cleared that list's masks
+        ctl->rcnt[ctl->zero_par] = 0ull;
+        ctl->zero_pending = 0u;
+      }
+      if (heavy) {
+        ctl->zero_pending = 1u;
+        ctl->zero_par = ep % 3;
+        ctl->epoch = ep + 1u;
+      }
+      const uint32_t rn = (uint32_t)(atomicAdd(&ctl->rcnt[ctl->epoch % 3], 0ull) >> 32);
+      ctl->mode = fn > 0 ? 0u : 2u;
+      bool more = fn != 0 || rn != 0;
+      if (more && it + 1 >= ctl->max_iter) {
+        ctl->status |= DS_ITER_CAP;
+        more = false;
+      }
+      ctl->running = more ? 1u : 0u;
+      if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+      return;
     }
     uint32_t fs_now = fsel;
     if (bmode == 1) {   // the kept vertices went to the other list
@@ -510,7 +637,7 @@ __global__ void k_batch_fill(uint32_t* dist, unsigned long long count) {
 // group start: dist[src_s][col0+s] := 0; initial frontier = distinct sources
 // with out-edges, each carrying the mask of its columns.  One CTA of 64.
 __global__ void k_batch_seed(DevGraph g, BatchBufs w, const uint32_t* srcs, uint32_t k, uint32_t col0,
-                             uint32_t kg, uint32_t* dist, uint32_t max_iter, uint32_t delta) {
+                             uint32_t kg, uint32_t* dist, uint32_t max_iter, uint32_t delta, uint32_t lh) {
   BatchCtl* ctl = w.ctl;
   const uint32_t s = threadIdx.x;
   if (s == 0) {
@@ -537,24 +664,46 @@ __global__ void k_batch_seed(DevGraph g, BatchBufs w, const uint32_t* srcs, uint
     ctl->far_min = kInf;
     ctl->mode = 0;
     ctl->splits = 0;
+    ctl->lh = lh;
+    ctl->epoch = 0;
+    ctl->zero_pending = 0;
+    ctl->zero_par = 0;
+    ctl->rcnt[0] = 0ull;
+    ctl->rcnt[1] = 0ull;
+    ctl->rcnt[2] = 0ull;
   }
   __syncthreads();
   if (s < kg) {
     const uint32_t v = srcs[col0 + s];
     dist[(size_t)v * k + col0 + s] = 0u;
     const uint32_t rs = g.ro[v], re = g.ro[v + 1];
-    if (re > rs) {
+    // light-first rounds: the light edges form the first frontier, the heavy
+    // ones the first R list
+    const uint32_t le = lh ? w.lend[v] : re;
+    if (le > rs) {
       if (atomicOr(w.mask[0] + v, 1ull << s) == 0ull) {
-        const unsigned long long b = atomicAdd(&ctl->cnt[0], (1ull << 32) | (re - rs));
+        const unsigned long long b = atomicAdd(&ctl->cnt[0], (1ull << 32) | (le - rs));
         const uint32_t pos = (uint32_t)(b >> 32);
         w.fv[0][pos] = v;
         w.fr[0][pos] = rs;
         w.fs[0][pos] = (uint32_t)b;
       }
     }
+    if (lh && re > le) {
+      if (atomicOr(w.rmask[0] + v, 1ull << s) == 0ull) {
+        const unsigned long long b = atomicAdd(&ctl->rcnt[0], (1ull << 32) | (re - le));
+        const uint32_t pos = (uint32_t)(b >> 32);
+        w.rv[0][pos] = v;
+        w.rr[0][pos] = le;
+        w.rs[0][pos] = (uint32_t)b;
+      }
+    }
   }
   __syncthreads();
-  if (s == 0) ctl->running = ctl->cnt[0] != 0ull ? 1u : 0u;
+  if (s == 0) {
+    ctl->running = (ctl->cnt[0] != 0ull || ctl->rcnt[0] != 0ull) ? 1u : 0u;
+    if (ctl->cnt[0] == 0ull && ctl->rcnt[0] != 0ull) ctl->mode = 2u;   // sources without light edges
+  }
 }
 
 }  // namespace
@@ -565,18 +714,23 @@ struct BatchWorkspace {
   BatchBufs b{};
   uint32_t* srcs = nullptr;
   uint32_t srcs_cap = 0;
-  cudaGraph_t graph[2] = {nullptr, nullptr};      // per row-read mode (scalar, 16-byte vectors)
-  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  // per row-read mode (scalar, 16-byte vectors) x light-first rounds
+  cudaGraph_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   int grid = 0;
   BatchCtl* h_ctl = nullptr;
 };
 
-// the superstep kernel for the edge format and the row-read mode
-static void* batch_fn(bool packed, bool vec) {
-  if (packed) return vec ? reinterpret_cast<void*>(&k_batch_superstep<true, true>)
-                         : reinterpret_cast<void*>(&k_batch_superstep<true, false>);
-  return vec ? reinterpret_cast<void*>(&k_batch_superstep<false, true>)
-             : reinterpret_cast<void*>(&k_batch_superstep<false, false>);
+// the superstep kernel for the edge format, the row-read mode and the rounds
+template <bool LH>
+static void* batch_fn_lh(bool packed, bool vec) {
+  if (packed) return vec ? reinterpret_cast<void*>(&k_batch_superstep<true, true, LH>)
+                         : reinterpret_cast<void*>(&k_batch_superstep<true, false, LH>);
+  return vec ? reinterpret_cast<void*>(&k_batch_superstep<false, true, LH>)
+             : reinterpret_cast<void*>(&k_batch_superstep<false, false, LH>);
+}
+static void* batch_fn(bool packed, bool vec, bool lh) {
+  return lh ? batch_fn_lh<true>(packed, vec) : batch_fn_lh<false>(packed, vec);
 }
 
 static gg_status batch_ws(gg_graph* g, BatchWorkspace** out) {
@@ -584,7 +738,7 @@ static gg_status batch_ws(gg_graph* g, BatchWorkspace** out) {
     BatchWorkspace* w = new BatchWorkspace();
     const size_t n = std::max<uint32_t>(g->n, 1);
     auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
-    const size_t total = 11 * r256(4 * n) + 4 * r256(8 * n) + r256(sizeof(BatchCtl));
+    const size_t total = 20 * r256(4 * n) + 7 * r256(8 * n) + r256(sizeof(BatchCtl));
     char* p = nullptr;
     cudaError_t e = cudaMalloc(&p, total);
     if (e != cudaSuccess) { delete w; return cuda_fail(e, "cudaMalloc(batch workspace)"); }
@@ -600,10 +754,17 @@ static gg_status batch_ws(gg_graph* g, BatchWorkspace** out) {
     for (int i = 0; i < 3; ++i) w->b.mask[i] = reinterpret_cast<unsigned long long*>(take(8 * n));
     w->b.fmask = reinterpret_cast<unsigned long long*>(take(8 * n));
     for (int i = 0; i < 2; ++i) w->b.far_v[i] = reinterpret_cast<uint32_t*>(take(4 * n));
+    for (int i = 0; i < 3; ++i) {
+      w->b.rv[i] = reinterpret_cast<uint32_t*>(take(4 * n));
+      w->b.rr[i] = reinterpret_cast<uint32_t*>(take(4 * n));
+      w->b.rs[i] = reinterpret_cast<uint32_t*>(take(4 * n));
+    }
+    for (int i = 0; i < 3; ++i) w->b.rmask[i] = reinterpret_cast<unsigned long long*>(take(8 * n));
     w->b.ctl = reinterpret_cast<BatchCtl*>(take(sizeof(BatchCtl)));
+    if (off != total) { cudaFree(p); delete w; return fail(GG_ERR_INTERNAL, "batch workspace layout"); }
     e = cudaMallocHost(&w->h_ctl, sizeof(BatchCtl));
     if (e != cudaSuccess) { cudaFree(p); delete w; return cuda_fail(e, "cudaMallocHost"); }
-    void* fn = batch_fn(g->dg.packed, false);
+    void* fn = batch_fn(g->dg.packed, false, false);
     int per_sm = 0;
     GG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBB, 0));
     w->grid = std::max(1, per_sm) * device_info().num_sms;
@@ -613,8 +774,8 @@ static gg_status batch_ws(gg_graph* g, BatchWorkspace** out) {
   return GG_OK;
 }
 
-static gg_status batch_exec(gg_graph* g, BatchWorkspace* w, bool vec) {
-  if (w->exec[vec]) return GG_OK;
+static gg_status batch_exec(gg_graph* g, BatchWorkspace* w, bool vec, bool lh) {
+  if (w->exec[vec][lh]) return GG_OK;
   cudaGraph_t graph = nullptr;
   GG_CK(cudaGraphCreate(&graph, 0));
   cudaGraphConditionalHandle h;
@@ -631,14 +792,14 @@ static gg_status batch_exec(gg_graph* g, BatchWorkspace* w, bool vec) {
   int use_cond = 1;
   void* args[] = {&dg, &b, &h, &use_cond};
   cudaKernelNodeParams kp = {};
-  kp.func = batch_fn(g->dg.packed, vec);
+  kp.func = batch_fn(g->dg.packed, vec, lh);
   kp.gridDim = dim3(w->grid);
   kp.blockDim = dim3(kBB);
   kp.kernelParams = args;
   cudaGraphNode_t knode;
   GG_CK(cudaGraphAddKernelNode(&knode, cp.conditional.phGraph_out[0], nullptr, 0, &kp));
-  GG_CK(cudaGraphInstantiate(&w->exec[vec], graph, 0));
-  w->graph[vec] = graph;
+  GG_CK(cudaGraphInstantiate(&w->exec[vec][lh], graph, 0));
+  w->graph[vec][lh] = graph;
   return GG_OK;
 }
 
@@ -657,7 +818,17 @@ gg_status batch_run(gg_graph* g, const uint32_t* srcs, uint32_t k, uint32_t* dis
   GG_CK(cudaMemcpyAsync(w->srcs, srcs, sizeof(uint32_t) * k, cudaMemcpyHostToDevice, s));
   // 16-byte row reads need 16-byte aligned rows: k a multiple of 4 and an aligned matrix
   const bool vec = (k % 4u) == 0u && (reinterpret_cast<uintptr_t>(dist) & 15u) == 0u;
-  st = batch_exec(g, w, vec);
+  // light-first rounds with the graph's light/heavy width (skewed graphs, no
+  // explicit bucket width): the light-first edge copy is shared with the
+  // single-source loop and is in place before the rounds' graph is built
+  const bool lh = o.delta == 0 && o.light_heavy != GG_LH_OFF && g->default_delta_lh != GG_DELTA_NONE && g->m > 0;
+  if (lh) {
+    st = lh_prepare(g, g->default_delta_lh, s);
+    if (st != GG_OK) return st;
+    w->b.ledges = g->lhb.edges;
+    w->b.lend = g->lhb.lend;
+  }
+  st = batch_exec(g, w, vec, lh);
   if (st != GG_OK) return st;
   const unsigned long long count = (unsigned long long)g->n * k;
   const unsigned fb = (unsigned)std::max<unsigned long long>(
@@ -668,14 +839,17 @@ gg_status batch_run(gg_graph* g, const uint32_t* srcs, uint32_t k, uint32_t* dis
   // in different buckets is re-expanded once per bucket, which on the measured
   // RMAT workloads cost far more edge scans than the buckets saved
   const uint32_t delta = (o.delta == GG_DELTA_NONE || o.delta == 0) ? kInf : o.delta;
-  const unsigned long long cap = delta == kInf ? (unsigned long long)g->n + 2 : 4ull * g->n + 16;
+  // a light-first round adds at most one heavy superstep per improving vertex
+  const unsigned long long cap = lh ? 3ull * g->n + 16 : delta == kInf ? (unsigned long long)g->n + 2 : 4ull * g->n + 16;
   const uint32_t max_iter = o.max_iterations ? o.max_iterations : (cap >= 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)cap);
   for (uint32_t col0 = 0; col0 < k; col0 += 64) {
     const uint32_t kg = std::min<uint32_t>(64, k - col0);
     // the previous group (or call) may leave the masks of its last frontier set
     for (int i = 0; i < 3; ++i) GG_CK(cudaMemsetAsync(w->b.mask[i], 0, 8 * (size_t)g->n, s));
     GG_CK(cudaMemsetAsync(w->b.fmask, 0, 8 * (size_t)g->n, s));
-    k_batch_seed<<<1, 64, 0, s>>>(g->dg, w->b, w->srcs, k, col0, kg, dist, max_iter, delta);
+    if (lh)
+      for (int i = 0; i < 3; ++i) GG_CK(cudaMemsetAsync(w->b.rmask[i], 0, 8 * (size_t)g->n, s));
+    k_batch_seed<<<1, 64, 0, s>>>(g->dg, w->b, w->srcs, k, col0, kg, dist, max_iter, lh ? kInf : delta, lh ? 1u : 0u);
     GG_CK(cudaGetLastError());
     if (o.policy == GG_POLICY_BSP_HOST) {
       // supersteps launched one by one, the loop flag read back after each
@@ -683,7 +857,7 @@ gg_status batch_run(gg_graph* g, const uint32_t* srcs, uint32_t k, uint32_t* dis
       BatchBufs b = w->b;
       cudaGraphConditionalHandle none = 0;
       int zero = 0;
-      void* fn = batch_fn(g->dg.packed, vec);
+      void* fn = batch_fn(g->dg.packed, vec, lh);
       for (uint32_t it = 0;; ++it) {
         void* args[] = {&dg, &b, &none, &zero};
         GG_CK(cudaLaunchKernel(fn, dim3(w->grid), dim3(kBB), args, 0, s));
@@ -692,7 +866,7 @@ gg_status batch_run(gg_graph* g, const uint32_t* srcs, uint32_t k, uint32_t* dis
         if (w->h_ctl->running == 0u || it >= max_iter) break;
       }
     } else {
-      GG_CK(cudaGraphLaunch(w->exec[vec], s));
+      GG_CK(cudaGraphLaunch(w->exec[vec][lh], s));
     }
     if (o.stats) {
       GG_CK(cudaMemcpyAsync(w->h_ctl, w->b.ctl, sizeof(BatchCtl), cudaMemcpyDeviceToHost, s));
@@ -721,8 +895,10 @@ void batch_release(gg_graph* g) {
   BatchWorkspace* w = g->batch;
   if (!w) return;
   for (int i = 0; i < 2; ++i) {
-    if (w->exec[i]) cudaGraphExecDestroy(w->exec[i]);
-    if (w->graph[i]) cudaGraphDestroy(w->graph[i]);
+    for (int j = 0; j < 2; ++j) {
+      if (w->exec[i][j]) cudaGraphExecDestroy(w->exec[i][j]);
+      if (w->graph[i][j]) cudaGraphDestroy(w->graph[i][j]);
+    }
   }
   if (w->block) cudaFree(w->block);
   if (w->srcs) cudaFree(w->srcs);

@@ -192,3 +192,63 @@ def test_bad_light_heavy_value_is_rejected():
         g.sssp(src, light_heavy=2)
     assert ei.value.status_name == "GG_ERR_INVALID_ARG"
     g.close()
+
+
+# ---- batched multi-source: light-first rounds ---------------------------------
+
+def run_batch(g, srcs, **kw):
+    m = gg()
+    st = m.gg_stats()
+    d = g.sssp_batch(srcs, stats=st, **kw)
+    torch.cuda.synchronize()
+    return d.cpu().numpy(), st.as_dict()
+
+
+@pytest.mark.parametrize("k,pack,policy", [(3, True, 0), (64, True, 0), (70, False, 0), (64, False, 2)])
+def test_batch_light_first_rounds_match_oracle(k, pack, policy):
+    ro, col, w, _ = graphgen.workload("rmat16")
+    srcs = graphgen.sample_sources(ro, k, seed=21)
+    g = gg().Graph(ro, col, w, symmetric=True, pack=pack)
+    ref = oracle.dijkstra_many(ro, col, w, srcs, threads=8)
+    got, st = run_batch(g, srcs, policy=policy)
+    got_off, st_off = run_batch(g, srcs, policy=policy, light_heavy=1)
+    for s in range(k):
+        np.testing.assert_array_equal(got[:, s], ref[s], err_msg=f"column {s}")
+        np.testing.assert_array_equal(got_off[:, s], ref[s], err_msg=f"column {s} (light/heavy off)")
+    assert st["device_status"] == 0
+    assert st["edges_scanned"] < st_off["edges_scanned"]
+    g.close()
+
+
+def test_batch_directed_sinks_zero_weights_and_heavy_only_sources():
+    rng = np.random.Generator(np.random.PCG64(31))
+    n, m = 4000, 60000
+    src = rng.integers(0, 3500, m)             # vertices 3500.. have no out-edges (sinks)
+    dst = rng.integers(0, n, m)
+    w = rng.integers(0, 80, m)
+    ro, col, wt = graphgen.from_edges(n, src, dst, w)
+    # a source whose every edge is heavy starts with a heavy superstep
+    hv = 7
+    wt[ro[hv]:ro[hv + 1]] = 79
+    g = gg().Graph(ro, col, wt, symmetric=False)
+    srcs = np.array([hv, 0, 3999, 1234, hv, 42], np.uint32)
+    ref = oracle.dijkstra_many(ro, col, wt, srcs)
+    got, st = run_batch(g, srcs)
+    np.testing.assert_array_equal(got.T, ref)
+    assert st["device_status"] == 0
+    g.close()
+
+
+def test_batch_after_single_source_runs_with_other_widths():
+    """The light-first copy is shared: a single-source run with another width
+    re-partitions it, and the next batch re-partitions it back."""
+    ro, col, w, src = graphgen.workload("rmat16")
+    g = gg().Graph(ro, col, w, symmetric=True)
+    srcs = graphgen.sample_sources(ro, 8, seed=2)
+    ref = oracle.dijkstra_many(ro, col, w, srcs)
+    for delta in (40, 0, 3):
+        got1, _, _ = run(g, int(srcs[0]), delta)
+        np.testing.assert_array_equal(got1, ref[0])
+        got, _ = run_batch(g, srcs)
+        np.testing.assert_array_equal(got.T, ref)
+    g.close()
