@@ -191,29 +191,36 @@ __global__ void k_lh_lend(uint32_t n, const uint32_t* __restrict__ ro, const uin
     lend[v] = ro[v] + (L[ro[v + 1]] - L[ro[v]]);
 }
 
-// warp per row: light edges to the front of the row in their original order,
-// heavy edges after them in theirs
+// cnt[ro[v]] += 1 for every vertex whose row starts before m: after an
+// exclusive scan X of cnt (m + 1 entries), edge e lies in row X[e + 1] - 1
+// (the last vertex whose row starts at or before e)
+__global__ void k_row_starts(uint32_t n, uint32_t m, const uint32_t* __restrict__ ro, uint32_t* __restrict__ cnt) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+    if (ro[v] < m) atomicAdd(&cnt[ro[v]], 1u);
+}
+
+// thread per edge: light edges to the front of their row in their original
+// order, heavy edges after them in theirs
 template <bool PK>
-__global__ void k_lh_scatter(uint32_t n, const uint32_t* __restrict__ ro, const void* __restrict__ edges,
-                             const uint32_t* __restrict__ L, const uint32_t* __restrict__ lend, uint32_t wbits,
-                             uint32_t delta, void* __restrict__ out) {
-  const uint32_t lane = threadIdx.x & 31;
-  const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t u = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
-    const uint32_t r0 = ro[u], r1 = ro[u + 1];
-    if (r1 == r0) continue;
-    const uint32_t L0 = L[r0], le = lend[u];
-    for (uint32_t e = r0 + lane; e < r1; e += 32) {
-      const uint32_t before = L[e] - L0;   // light edges of the row before e
-      if (PK) {
-        const uint32_t x = static_cast<const uint32_t*>(edges)[e];
-        const uint32_t d = (x & ((1u << wbits) - 1u)) < delta ? r0 + before : le + (e - r0 - before);
-        static_cast<uint32_t*>(out)[d] = x;
-      } else {
-        const uint2 x = static_cast<const uint2*>(edges)[e];
-        const uint32_t d = x.y < delta ? r0 + before : le + (e - r0 - before);
-        static_cast<uint2*>(out)[d] = x;
-      }
+__global__ void k_lh_scatter(uint32_t m, const uint32_t* __restrict__ ro, const uint32_t* __restrict__ X,
+                             const void* __restrict__ edges, const uint32_t* __restrict__ L,
+                             const uint32_t* __restrict__ lend, uint32_t wbits, uint32_t delta,
+                             void* __restrict__ out) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
+    const uint32_t u = X[e + 1] - 1u;
+    const uint32_t r0 = __ldg(ro + u);
+    const uint32_t before = L[e] - __ldg(L + r0);   // light edges of the row before e
+    const uint32_t le = __ldg(lend + u);
+    if (PK) {
+      const uint32_t x = static_cast<const uint32_t*>(edges)[e];
+      const uint32_t d = (x & ((1u << wbits) - 1u)) < delta ? r0 + before : le + ((uint32_t)e - r0 - before);
+      static_cast<uint32_t*>(out)[d] = x;
+    } else {
+      const uint2 x = static_cast<const uint2*>(edges)[e];
+      const uint32_t d = x.y < delta ? r0 + before : le + ((uint32_t)e - r0 - before);
+      static_cast<uint2*>(out)[d] = x;
     }
   }
 }
@@ -458,12 +465,20 @@ gg_status lh_prepare(gg_graph* g, uint32_t delta, cudaStream_t s) {
   k_lh_lend<<<grid_for(n), 256, 0, s>>>((uint32_t)n, g->ro, L, lend);
   GG_CK(cudaGetLastError());
   if (m) {
-    void* out = const_cast<void*>(g->lhb.edges);
-    if (pk) k_lh_scatter<true><<<grid_for((uint64_t)n * 32), 256, 0, s>>>((uint32_t)n, g->ro, g->dg.edges, L, lend,
-                                                                            g->dg.wbits, delta, out);
-    else k_lh_scatter<false><<<grid_for((uint64_t)n * 32), 256, 0, s>>>((uint32_t)n, g->ro, g->dg.edges, L, lend,
-                                                                          g->dg.wbits, delta, out);
+    uint32_t* X = nullptr;
+    GG_CK(cudaMallocAsync(&X, sizeof(uint32_t) * (m + 1), s));
+    GG_CK(cudaMemsetAsync(X, 0, sizeof(uint32_t) * (m + 1), s));
+    k_row_starts<<<grid_for(n), 256, 0, s>>>((uint32_t)n, (uint32_t)m, g->ro, X);
     GG_CK(cudaGetLastError());
+    st = scan_excl(X, (uint64_t)m + 1, s);
+    if (st != GG_OK) { cudaFreeAsync(X, s); cudaFreeAsync(L, s); return st; }
+    void* out = const_cast<void*>(g->lhb.edges);
+    if (pk) k_lh_scatter<true><<<grid_for(m), 256, 0, s>>>((uint32_t)m, g->ro, X, g->dg.edges, L, lend,
+                                                            g->dg.wbits, delta, out);
+    else k_lh_scatter<false><<<grid_for(m), 256, 0, s>>>((uint32_t)m, g->ro, X, g->dg.edges, L, lend,
+                                                          g->dg.wbits, delta, out);
+    GG_CK(cudaGetLastError());
+    GG_CK(cudaFreeAsync(X, s));
   }
   GG_CK(cudaFreeAsync(L, s));
   GG_CK(cudaStreamSynchronize(s));
