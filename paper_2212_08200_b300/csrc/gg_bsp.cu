@@ -39,6 +39,9 @@
 #ifndef GG_HEAVY_PULL
 #define GG_HEAVY_PULL 1   // allow heavy supersteps by pull on symmetric graphs
 #endif
+#ifndef GG_DEFER_DEDUP
+#define GG_DEFER_DEDUP 1   // warp streaming: next-frontier test-and-set at the queue flush
+#endif
 #ifndef GG_LH_DRAIN
 #define GG_LH_DRAIN 8    // light/heavy: bucketing ends once the unsettled vertices hold
 #endif                   // fewer than m / GG_LH_DRAIN heavy edges
@@ -556,6 +559,34 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
 
   auto flush_near = [&]() {
     __syncwarp();
+    if (GG_DEFER_DEDUP && !fo.sinks) {
+      // deferred dedup: the queue holds every improved near vertex (repeats
+      // included); test-and-set them all here, the atomics of the whole queue
+      // in flight together, then append the winners
+      static_assert(QW <= 128, "four queue entries per lane");
+      uint32_t vq[4];
+      bool kp[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const uint32_t i = 32u * c + lane;
+        vq[c] = i < qn ? qv[i] : 0u;
+        kp[c] = false;
+        if (i < qn) {
+          const uint32_t bit = 1u << (vq[c] & 31);
+          kp[c] = !(atomicOr(fo.bm_next + (vq[c] >> 5), bit) & bit);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (32u * c < qn) {   // warp-uniform
+          if (fo.lh) append32<true>(a, fo, kp[c], vq[c]);
+          else append32<false>(a, fo, kp[c], vq[c]);
+        }
+      }
+      qn = 0;
+      __syncwarp();
+      return;
+    }
     if (fo.lh) {
       for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
         const uint32_t i = i0 + lane;
@@ -693,7 +724,8 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
           if (ok) {
             const uint32_t bit = 1u << (v & 31);
             if (nd[u] < fo.t_cur) {
-              near = !(atomicOr(fo.bm_next + (v >> 5), bit) & bit);
+              // with deferred dedup the bitmap is tested at the flush
+              near = (GG_DEFER_DEDUP && !fo.sinks) ? true : !(atomicOr(fo.bm_next + (v >> 5), bit) & bit);
             } else {
               fmin = min(fmin, nd[u]);
               far = !(atomicOr(fo.bm_far + (v >> 5), bit) & bit);
