@@ -401,6 +401,7 @@ gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m64, const uint32_t* ro_
     const double davg = g->dg.np ? (double)m / (double)g->dg.np : 1.0;
     const double d = (double)std::max<uint32_t>(wmax, 1) * 16.0;
     g->default_delta = (davg >= 8.0 || !m) ? GG_DELTA_NONE : (uint32_t)std::min(d, 4.0e9);
+    g->low_degree = davg < 8.0;
     // light/heavy buckets (single-source bulk-synchronous loop only) on the
     // same skewed graphs: width ~ GG_LH_K * wmax / mean degree, so that a
     // vertex has about GG_LH_K light edges

@@ -93,6 +93,7 @@ struct gg_graph {
   uint32_t wmax = 0;            // largest edge weight (bit pattern)
   bool float_weights = false;   // weights and distances are IEEE binary32 bit patterns
   uint32_t default_delta = 0;   // near-far bucket width used when gg_options.delta == 0
+  bool low_degree = false;      // mean degree < 8 (grids, paths): smaller superstep grid
   // light/heavy buckets of the single-source bulk-synchronous loop: bucket
   // width used when gg_options.delta == 0 (GG_DELTA_NONE: none), and the
   // light-first edge copy with its buffers (lh_delta = the width it is
