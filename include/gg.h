@@ -197,7 +197,11 @@ gg_status gg_graph_create_csr(uint32_t n, uint64_t m, const uint32_t* row_offset
                               const uint32_t* col_indices, const uint32_t* weights,
                               uint32_t flags, cudaStream_t stream, gg_graph_t* out);
 
-/* Frees the handle and its device memory (synchronises its last stream). */
+/* Frees the handle and its device memory (synchronises its last stream).
+ * Handles and their workspaces allocate from a stream-ordered pool per device
+ * that keeps up to 8 GiB of freed memory mapped for later handles (no device
+ * synchronisation or re-mapping per handle); that memory is released when the
+ * process exits. */
 gg_status gg_graph_destroy(gg_graph_t g);
 
 /* n, m and the device bytes held by the handle. */

@@ -26,6 +26,42 @@ gg_status cuda_fail(cudaError_t e, const char* what) {
   return GG_ERR_CUDA;
 }
 
+#ifndef GG_POOL_KEEP
+#define GG_POOL_KEEP (8ull << 30)   // freed bytes the allocation pool keeps mapped
+#endif
+
+namespace {
+cudaMemPool_t pool_for_current_device() {
+  static std::mutex mu;
+  static cudaMemPool_t pools[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = GG_POOL_KEEP;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    pools[dev] = pool;
+  }
+  return pools[dev];
+}
+}  // namespace
+
+cudaError_t dev_malloc(void** p, size_t bytes, cudaStream_t s) {
+  cudaMemPool_t pool = pool_for_current_device();
+  if (!pool) return cudaMallocAsync(p, bytes, s);
+  return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+void dev_free(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
 DeviceInfo device_info() {
   static thread_local DeviceInfo cache[16];
   int dev = 0;

@@ -1501,7 +1501,7 @@ int persistent_grid(const gg_graph* g, int variant) {
   return per_sm * device_info().num_sms;
 }
 
-gg_status ensure_workspace(gg_graph* g) {
+gg_status ensure_workspace(gg_graph* g, cudaStream_t s) {
   BspWorkspace& w = g->bsp;
   if (w.block) return GG_OK;
   const size_t n = g->n;
@@ -1511,8 +1511,8 @@ gg_status ensure_workspace(gg_graph* g) {
   // every sub-buffer starts on a 256-byte boundary
   const size_t total = 9 * r256(fbytes) + 4 * r256(sizeof(uint32_t) * nw) + r256(sizeof(Ctl));
   char* p = nullptr;
-  GG_CK(cudaMalloc(&p, total));
-  GG_CK(cudaMemset(p, 0, total));
+  GG_CK(dev_malloc(&p, total, s));
+  GG_CK(cudaMemsetAsync(p, 0, total, s));
   w.block = p;
   w.bytes = total;
   size_t off = 0;
@@ -1593,7 +1593,7 @@ gg_status build_graph_exec(gg_graph* g, int variant) {
 }  // namespace
 
 gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s, uint32_t wmode) {
-  gg_status st = ensure_workspace(g);
+  gg_status st = ensure_workspace(g, s);
   if (st != GG_OK) return st;
   // automatic choice: warp streaming (measured faster than merge-path tiles on RMAT, equal on grids)
   const int lb = o.lb_mode == GG_LB_BINS ? LB_BINS : o.lb_mode == GG_LB_MERGE_PATH ? LB_TILE : LB_WARP;
@@ -1698,7 +1698,7 @@ gg_status bsp_release(gg_graph* g) {
     w.exec[i] = nullptr;
     w.graph[i] = nullptr;
   }
-  if (w.block) cudaFree(w.block);
+  dev_free(w.block, 0);   // the handle's work has been synchronised
   w.block = nullptr;
   w.ctl = nullptr;
   return GG_OK;

@@ -3,8 +3,10 @@
 // transposed representation beside it for pull traversals).
 //
 // Device preprocessing, run once per handle (not part of an SSSP run):
-//   validate   offsets start at 0, never decrease, end at m; every column < n
-//   interleave col/weight arrays -> uint2 {col, weight}
+//   check      one pass: offsets start at 0, never decrease, end at m; every
+//              column < n; the largest weight (decides the edge encoding)
+//   encode     col/weight arrays -> packed (col << wbits) | weight words, or
+//              interleaved uint2 {col, weight} when they do not fit
 //   transpose  CSC by counting sort (only for graphs not declared symmetric)
 //   pull list  vertices with a non-empty CSC row, with the row start
 #include <cuda_runtime.h>
@@ -27,58 +29,63 @@ constexpr int SCAN_BLOCK = 256;
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
 
-__global__ void k_validate(uint32_t n, uint32_t m, const uint32_t* __restrict__ ro,
-                           const uint32_t* __restrict__ col, uint32_t* __restrict__ err) {
+// One pass over the uploaded CSR: structural checks (offsets start at 0,
+// never decrease, end at m; every column < n) when validate is set, and the
+// largest weight.  out[0]: error bits, out[1]: largest weight (bit pattern).
+__global__ void k_check(uint32_t n, uint32_t m, const uint32_t* __restrict__ ro, const uint32_t* __restrict__ col,
+                        const uint32_t* __restrict__ w, uint32_t validate, uint32_t* __restrict__ out) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    if (ro[i + 1] < ro[i]) atomicOr(err, 1u);
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t err = 0, mx = 0;
+  if (validate) {
+    for (uint64_t i = t; i < n; i += stride)
+      if (ro[i + 1] < ro[i]) err |= 1u;
+    if (t == 0 && (ro[0] != 0 || ro[n] != m)) err |= 4u;
   }
+  for (uint64_t e = t; e < m; e += stride) {
+    if (validate && col[e] >= n) err |= 2u;
+    mx = max(mx, w[e]);
+  }
+  for (int o = 16; o; o >>= 1) {
+    mx = max(mx, __shfl_down_sync(0xFFFFFFFFu, mx, o));
+    err |= __shfl_down_sync(0xFFFFFFFFu, err, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (err) atomicOr(out, err);
+    atomicMax(out + 1, mx);
+  }
+}
+
+// {col, w} arrays -> the handle's edge encoding: (col << wbits) | w when PK,
+// else interleaved uint2 {col, w}
+template <bool PK>
+__global__ void k_encode(uint32_t m, const uint32_t* __restrict__ col, const uint32_t* __restrict__ w,
+                         uint32_t wbits, void* __restrict__ out) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-    if (col[e] >= n) atomicOr(err, 2u);
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (ro[0] != 0 || ro[n] != m) atomicOr(err, 4u);
+    if (PK) static_cast<uint32_t*>(out)[e] = (col[e] << wbits) | w[e];
+    else static_cast<uint2*>(out)[e] = make_uint2(col[e], w[e]);
   }
 }
 
-__global__ void k_interleave(uint32_t m, const uint32_t* __restrict__ col, const uint32_t* __restrict__ w,
-                             uint2* __restrict__ out, uint32_t* __restrict__ wmax) {
+__global__ void k_count_cols(uint32_t m, const uint32_t* __restrict__ col, uint32_t* __restrict__ cnt) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  uint32_t mx = 0;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-    const uint32_t we = w[e];
-    out[e] = make_uint2(col[e], we);
-    mx = max(mx, we);
-  }
-  for (int o = 16; o; o >>= 1) mx = max(mx, __shfl_down_sync(0xFFFFFFFFu, mx, o));
-  if ((threadIdx.x & 31) == 0) atomicMax(wmax, mx);
+  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) atomicAdd(&cnt[col[e]], 1u);
 }
 
-// {col, w} -> (col << wbits) | w
-__global__ void k_pack(uint32_t m, const uint2* __restrict__ in, uint32_t* __restrict__ out, uint32_t wbits) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-    const uint2 x = in[e];
-    out[e] = (x.x << wbits) | x.y;
-  }
-}
-
-__global__ void k_count_in(uint32_t m, const uint2* __restrict__ edges, uint32_t* __restrict__ cnt) {
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride)
-    atomicAdd(&cnt[edges[e].x], 1u);
-}
-
-// warp per source row: scatter every edge u->v into v's CSC row as {u, w}
-__global__ void k_scatter_t(uint32_t n, const uint32_t* __restrict__ ro, const uint2* __restrict__ edges,
-                            uint32_t* __restrict__ cursor, uint2* __restrict__ t_edges) {
+// warp per source row: every edge u->v into v's CSC row as u (with its
+// weight), in the handle's edge encoding
+template <bool PK>
+__global__ void k_transpose(uint32_t n, const uint32_t* __restrict__ ro, const uint32_t* __restrict__ col,
+                            const uint32_t* __restrict__ w, uint32_t wbits, uint32_t* __restrict__ cursor,
+                            void* __restrict__ out) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   for (uint64_t u = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < n; u += warps) {
     for (uint32_t e = ro[u] + lane; e < ro[u + 1]; e += 32) {
-      const uint2 ed = edges[e];
-      const uint32_t pos = atomicAdd(&cursor[ed.x], 1u);
-      t_edges[pos] = make_uint2((uint32_t)u, ed.y);
+      const uint32_t pos = atomicAdd(&cursor[col[e]], 1u);
+      if (PK) static_cast<uint32_t*>(out)[pos] = ((uint32_t)u << wbits) | w[e];
+      else static_cast<uint2*>(out)[pos] = make_uint2((uint32_t)u, w[e]);
     }
   }
 }
@@ -132,14 +139,14 @@ gg_status scan_excl(uint32_t* data, uint64_t count, cudaStream_t s) {
     return GG_OK;
   }
   uint32_t* sums = nullptr;
-  GG_CK(cudaMallocAsync(&sums, tiles * sizeof(uint32_t), s));
+  GG_CK(dev_malloc(&sums, tiles * sizeof(uint32_t), s));
   k_scan_reduce<<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(data, count, sums);
   GG_CK(cudaGetLastError());
   gg_status st = scan_excl(sums, tiles, s);
-  if (st != GG_OK) { cudaFreeAsync(sums, s); return st; }
+  if (st != GG_OK) { dev_free(sums, s); return st; }
   k_scan_tile<<<(unsigned)tiles, SCAN_BLOCK, 0, s>>>(data, count, sums);
   GG_CK(cudaGetLastError());
-  GG_CK(cudaFreeAsync(sums, s));
+  dev_free(sums, s);
   return GG_OK;
 }
 
@@ -246,150 +253,147 @@ gg_status graph_build(gg_graph* g, uint32_t n, uint64_t m64, const uint32_t* ro_
   g->symmetric = (flags & GG_SYMMETRIC) != 0;
   g->float_weights = (flags & GG_FLOAT_WEIGHTS) != 0;
   // cheap host-side check first; monotonicity and column range are checked on
-  // the device after the upload (k_validate)
+  // the device after the upload (k_check)
   if (!dev && validate && (ro_in[0] != 0 || ro_in[n] != m))
     return fail(GG_ERR_INVALID_ARG, "row_offsets must start at 0 and end at m");
   GG_CK(cudaGetDevice(&g->device));
 
-  GG_CK(cudaMalloc(&g->ro, sizeof(uint32_t) * ((size_t)n + 1)));
-  GG_CK(cudaMalloc(&g->edges, sizeof(uint2) * std::max<size_t>(m, 1)));
-  g->bytes = sizeof(uint32_t) * ((size_t)n + 1) + sizeof(uint2) * std::max<size_t>(m, 1);
+  GG_CK(dev_malloc(&g->ro, sizeof(uint32_t) * ((size_t)n + 1), s));
+  g->bytes = sizeof(uint32_t) * ((size_t)n + 1);
   GG_CK(cudaMemcpyAsync(g->ro, ro_in, sizeof(uint32_t) * ((size_t)n + 1),
                         dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  // packed 4-byte edges when the column bits of n - 1 and the bits of the
+  // largest weight fit in one word
+  uint32_t colbits = 1;
+  while (colbits < 32 && ((uint64_t)(n - 1) >> colbits) != 0) ++colbits;
+  const uint32_t wbits = 32 - colbits;
+  bool pack = false;
   uint32_t wmax = 0;
-  uint32_t* wmax_d = nullptr;
-  const uint32_t* dcol = col_in;
-  const uint32_t* dw = w_in;
-  uint32_t* tmp = nullptr;
   if (m > 0) {
+    const uint32_t* dcol = col_in;
+    const uint32_t* dw = w_in;
+    uint32_t* tmp = nullptr;
     if (!dev) {
-      GG_CK(cudaMallocAsync(&tmp, sizeof(uint32_t) * 2 * (size_t)m, s));
+      GG_CK(dev_malloc(&tmp, sizeof(uint32_t) * 2 * (size_t)m, s));
       GG_CK(cudaMemcpyAsync(tmp, col_in, sizeof(uint32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
       GG_CK(cudaMemcpyAsync(tmp + m, w_in, sizeof(uint32_t) * (size_t)m, cudaMemcpyHostToDevice, s));
       dcol = tmp;
       dw = tmp + m;
     }
-    if (validate) {
-      uint32_t* derr = nullptr;
-      GG_CK(cudaMallocAsync(&derr, sizeof(uint32_t), s));
-      GG_CK(cudaMemsetAsync(derr, 0, sizeof(uint32_t), s));
-      k_validate<<<grid_for(std::max<uint64_t>(n, m)), 256, 0, s>>>(n, m, g->ro, dcol, derr);
-      GG_CK(cudaGetLastError());
-      uint32_t herr = 0;
-      GG_CK(cudaMemcpyAsync(&herr, derr, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-      GG_CK(cudaFreeAsync(derr, s));
-      GG_CK(cudaStreamSynchronize(s));
-      if (herr && tmp) cudaFreeAsync(tmp, s);
-      if (herr & 4u) return fail(GG_ERR_INVALID_ARG, "row_offsets must start at 0 and end at m");
-      if (herr & 1u) return fail(GG_ERR_INVALID_ARG, "row_offsets must be non-decreasing");
-      if (herr & 2u) return fail(GG_ERR_INVALID_ARG, "col_indices must be < n");
-    }
-    GG_CK(cudaMallocAsync(&wmax_d, sizeof(uint32_t), s));
-    GG_CK(cudaMemsetAsync(wmax_d, 0, sizeof(uint32_t), s));
-    k_interleave<<<grid_for(m), 256, 0, s>>>(m, dcol, dw, g->edges, wmax_d);
+    // checks and the largest weight in one pass, one read-back
+    uint32_t* chk = nullptr;
+    GG_CK(dev_malloc(&chk, 2 * sizeof(uint32_t), s));
+    GG_CK(cudaMemsetAsync(chk, 0, 2 * sizeof(uint32_t), s));
+    k_check<<<grid_for(std::max<uint64_t>(n, m)), 256, 0, s>>>(n, m, g->ro, dcol, dw, validate ? 1u : 0u, chk);
     GG_CK(cudaGetLastError());
-    GG_CK(cudaMemcpyAsync(&wmax, wmax_d, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    GG_CK(cudaFreeAsync(wmax_d, s));
-    if (validate && (flags & GG_FLOAT_WEIGHTS)) {
-      // binary32 weights must be finite and >= +0: as bit patterns, every such
-      // value is below +inf's 0x7F800000 and every other one (negative, -0,
-      // inf, NaN) is not, so the largest pattern decides
-      GG_CK(cudaStreamSynchronize(s));
-      if (wmax >= 0x7F800000u) {
-        if (tmp) cudaFreeAsync(tmp, s);
-        return fail(GG_ERR_INVALID_ARG, "binary32 weights must be finite and >= +0.0");
-      }
-    }
-  } else if (dev && validate) {
     uint32_t h[2] = {0, 0};
-    GG_CK(cudaMemcpyAsync(h, g->ro, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    GG_CK(cudaMemcpyAsync(h + 1, g->ro + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    GG_CK(cudaMemcpyAsync(h, chk, sizeof(h), cudaMemcpyDeviceToHost, s));
+    dev_free(chk, s);
     GG_CK(cudaStreamSynchronize(s));
-    if (h[0] != 0 || h[1] != 0) return fail(GG_ERR_INVALID_ARG, "row_offsets must start at 0 and end at m");
-  }
-  if (tmp) GG_CK(cudaFreeAsync(tmp, s));
-
-  // transpose (CSC) for pull
-  if (g->symmetric) {
-    g->t_ro = g->ro;
-    g->t_edges = g->edges;
-  } else {
-    GG_CK(cudaMalloc(&g->t_ro, sizeof(uint32_t) * ((size_t)n + 1)));
-    GG_CK(cudaMalloc(&g->t_edges, sizeof(uint2) * std::max<size_t>(m, 1)));
-    g->bytes += sizeof(uint32_t) * ((size_t)n + 1) + sizeof(uint2) * std::max<size_t>(m, 1);
-    GG_CK(cudaMemsetAsync(g->t_ro, 0, sizeof(uint32_t) * ((size_t)n + 1), s));
-    if (m > 0) {
-      k_count_in<<<grid_for(m), 256, 0, s>>>(m, g->edges, g->t_ro);
-      GG_CK(cudaGetLastError());
+    wmax = h[1];
+    const char* bad = (h[0] & 4u)   ? "row_offsets must start at 0 and end at m"
+                      : (h[0] & 1u) ? "row_offsets must be non-decreasing"
+                      : (h[0] & 2u) ? "col_indices must be < n"
+                      // binary32 weights must be finite and >= +0: as bit patterns, every
+                      // such value is below +inf's 0x7F800000 and every other one (negative,
+                      // -0, inf, NaN) is not, so the largest pattern decides
+                      : (validate && (flags & GG_FLOAT_WEIGHTS) && wmax >= 0x7F800000u)
+                          ? "binary32 weights must be finite and >= +0.0"
+                          : nullptr;
+    if (bad) {
+      if (tmp) dev_free(tmp, s);
+      return fail(GG_ERR_INVALID_ARG, bad);
     }
-    gg_status st = scan_excl(g->t_ro, (uint64_t)n + 1, s);
-    if (st != GG_OK) return st;
-    if (m > 0) {
-      uint32_t* cursor = nullptr;
-      GG_CK(cudaMallocAsync(&cursor, sizeof(uint32_t) * ((size_t)n + 1), s));
-      GG_CK(cudaMemcpyAsync(cursor, g->t_ro, sizeof(uint32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s));
-      k_scatter_t<<<grid_for((uint64_t)n * 32), 256, 0, s>>>(n, g->ro, g->edges, cursor, g->t_edges);
+    pack = !(flags & GG_NO_PACK) && colbits < 32 && (uint64_t)wmax < (1ull << wbits);
+    const size_t esz = pack ? sizeof(uint32_t) : sizeof(uint2);
+    void* enc = nullptr;
+    GG_CK(dev_malloc(&enc, esz * (size_t)m, s));
+    g->bytes += esz * (size_t)m;
+    if (pack) {
+      g->edges4 = static_cast<uint32_t*>(enc);
+      k_encode<true><<<grid_for(m), 256, 0, s>>>(m, dcol, dw, wbits, enc);
+    } else {
+      g->edges = static_cast<uint2*>(enc);
+      k_encode<false><<<grid_for(m), 256, 0, s>>>(m, dcol, dw, wbits, enc);
+    }
+    GG_CK(cudaGetLastError());
+    // transpose (CSC) for pull, built from the uploaded arrays
+    if (!g->symmetric) {
+      GG_CK(dev_malloc(&g->t_ro, sizeof(uint32_t) * ((size_t)n + 1), s));
+      void* tenc = nullptr;
+      GG_CK(dev_malloc(&tenc, esz * (size_t)m, s));
+      g->bytes += sizeof(uint32_t) * ((size_t)n + 1) + esz * (size_t)m;
+      if (pack) g->t_edges4 = static_cast<uint32_t*>(tenc);
+      else g->t_edges = static_cast<uint2*>(tenc);
+      GG_CK(cudaMemsetAsync(g->t_ro, 0, sizeof(uint32_t) * ((size_t)n + 1), s));
+      k_count_cols<<<grid_for(m), 256, 0, s>>>(m, dcol, g->t_ro);
       GG_CK(cudaGetLastError());
-      GG_CK(cudaFreeAsync(cursor, s));
+      gg_status st = scan_excl(g->t_ro, (uint64_t)n + 1, s);
+      if (st != GG_OK) { if (tmp) dev_free(tmp, s); return st; }
+      uint32_t* cursor = nullptr;
+      GG_CK(dev_malloc(&cursor, sizeof(uint32_t) * ((size_t)n + 1), s));
+      GG_CK(cudaMemcpyAsync(cursor, g->t_ro, sizeof(uint32_t) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, s));
+      if (pack) k_transpose<true><<<grid_for((uint64_t)n * 32), 256, 0, s>>>(n, g->ro, dcol, dw, wbits, cursor, tenc);
+      else k_transpose<false><<<grid_for((uint64_t)n * 32), 256, 0, s>>>(n, g->ro, dcol, dw, wbits, cursor, tenc);
+      GG_CK(cudaGetLastError());
+      dev_free(cursor, s);
+    } else {
+      g->t_ro = g->ro;
+      g->t_edges = g->edges;
+      g->t_edges4 = g->edges4;
+    }
+    if (tmp) dev_free(tmp, s);
+  } else {
+    if (dev && validate) {
+      uint32_t h[2] = {0, 0};
+      GG_CK(cudaMemcpyAsync(h, g->ro, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+      GG_CK(cudaMemcpyAsync(h + 1, g->ro + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+      GG_CK(cudaStreamSynchronize(s));
+      if (h[0] != 0 || h[1] != 0) return fail(GG_ERR_INVALID_ARG, "row_offsets must start at 0 and end at m");
+    }
+    GG_CK(dev_malloc(&g->edges, sizeof(uint2), s));   // a placeholder: no edge is ever read
+    g->bytes += sizeof(uint2);
+    if (g->symmetric) {
+      g->t_ro = g->ro;
+      g->t_edges = g->edges;
+    } else {
+      GG_CK(dev_malloc(&g->t_ro, sizeof(uint32_t) * ((size_t)n + 1), s));
+      GG_CK(cudaMemsetAsync(g->t_ro, 0, sizeof(uint32_t) * ((size_t)n + 1), s));
+      g->t_edges = g->edges;
+      g->bytes += sizeof(uint32_t) * ((size_t)n + 1);
     }
   }
 
   // pull entry list: vertices with a non-empty CSC row
   {
     uint32_t* pos = nullptr;
-    GG_CK(cudaMallocAsync(&pos, sizeof(uint32_t) * ((size_t)n + 1), s));
+    GG_CK(dev_malloc(&pos, sizeof(uint32_t) * ((size_t)n + 1), s));
     k_nonempty_flags<<<grid_for(n), 256, 0, s>>>(n, g->t_ro, pos);
     GG_CK(cudaGetLastError());
     gg_status st = scan_excl(pos, (uint64_t)n + 1, s);
     if (st != GG_OK) return st;
-    uint32_t np = 0;
-    GG_CK(cudaMemcpyAsync(&np, pos + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-    GG_CK(cudaStreamSynchronize(s));
-    GG_CK(cudaMalloc(&g->pv, sizeof(uint32_t) * std::max<size_t>(np, 1)));
-    GG_CK(cudaMalloc(&g->ps, sizeof(uint32_t) * std::max<size_t>(np, 1)));
-    g->bytes += 2 * sizeof(uint32_t) * std::max<size_t>(np, 1);
+    // sized for every vertex, so that no read-back of the count has to come first
+    GG_CK(dev_malloc(&g->pv, sizeof(uint32_t) * std::max<size_t>(n, 1), s));
+    GG_CK(dev_malloc(&g->ps, sizeof(uint32_t) * std::max<size_t>(n, 1), s));
+    g->bytes += 2 * sizeof(uint32_t) * std::max<size_t>(n, 1);
     k_pull_list<<<grid_for(n), 256, 0, s>>>(n, g->t_ro, pos, g->pv, g->ps);
     GG_CK(cudaGetLastError());
-    g->dg.np = np;
-    uint32_t sinks = 0;
+    uint32_t h[2] = {0, 0};   // vertices with in-edges; sinks
+    GG_CK(cudaMemcpyAsync(&h[0], pos + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     if (!g->symmetric) {   // a symmetric graph's reachable vertices all have out-edges
-      GG_CK(cudaMemsetAsync(pos, 0, sizeof(uint32_t), s));
-      k_find_sinks<<<grid_for(n), 256, 0, s>>>(n, g->ro, g->t_ro, pos);
+      GG_CK(cudaMemsetAsync(pos + n, 0, sizeof(uint32_t), s));
+      k_find_sinks<<<grid_for(n), 256, 0, s>>>(n, g->ro, g->t_ro, pos + n);
       GG_CK(cudaGetLastError());
-      GG_CK(cudaMemcpyAsync(&sinks, pos, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
-      GG_CK(cudaStreamSynchronize(s));
+      GG_CK(cudaMemcpyAsync(&h[1], pos + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
     }
-    g->dg.sinks = sinks;
-    GG_CK(cudaFreeAsync(pos, s));
-  }
-  GG_CK(cudaStreamSynchronize(s));
-
-  // packed 4-byte edges when the column and weight bits fit in one word
-  uint32_t colbits = 1;
-  while (colbits < 32 && ((uint64_t)(n - 1) >> colbits) != 0) ++colbits;
-  const uint32_t wbits = 32 - colbits;
-  const bool pack = m > 0 && !(flags & GG_NO_PACK) && colbits < 32 && (uint64_t)wmax < (1ull << wbits);
-  g->dg.packed = 0;
-  g->dg.wbits = wbits;
-  if (pack) {
-    GG_CK(cudaMalloc(&g->edges4, sizeof(uint32_t) * (size_t)m));
-    k_pack<<<grid_for(m), 256, 0, s>>>(m, g->edges, g->edges4, wbits);
-    GG_CK(cudaGetLastError());
-    if (!g->symmetric) {
-      GG_CK(cudaMalloc(&g->t_edges4, sizeof(uint32_t) * (size_t)m));
-      k_pack<<<grid_for(m), 256, 0, s>>>(m, g->t_edges, g->t_edges4, wbits);
-      GG_CK(cudaGetLastError());
-    } else {
-      g->t_edges4 = g->edges4;
-    }
+    dev_free(pos, s);
     GG_CK(cudaStreamSynchronize(s));
-    if (g->t_edges != g->edges) cudaFree(g->t_edges);
-    cudaFree(g->edges);
-    g->edges = g->t_edges = nullptr;
-    g->bytes -= (g->symmetric ? 1 : 2) * sizeof(uint2) * (size_t)m;
-    g->bytes += (g->symmetric ? 1 : 2) * sizeof(uint32_t) * (size_t)m;
-    g->dg.packed = 1;
+    g->dg.np = h[0];
+    g->dg.sinks = h[1];
   }
+
+  g->dg.packed = pack ? 1u : 0u;
+  g->dg.wbits = wbits;
   // default near-far bucket width (measured on B300, see the autotuner for
   // per-graph choices): low-degree, high-diameter graphs (grids) use buckets
   // of 16 maximum edge weights, which cut Bellman-Ford re-relaxation from
@@ -434,7 +438,7 @@ gg_status lh_prepare(gg_graph* g, uint32_t delta, cudaStream_t s) {
     const size_t vb = sizeof(uint32_t) * std::max<size_t>(n, 1);
     const size_t total = r256(esz * std::max<size_t>(m, 1)) + 7 * r256(vb) + 2 * r256(sizeof(uint32_t) * nw);
     char* p = nullptr;
-    GG_CK(cudaMalloc(&p, total));
+    GG_CK(dev_malloc(&p, total, s));
     size_t off = 0;
     auto take = [&](size_t b) { char* q = p + off; off += r256(b); return q; };
     g->lhb.edges = take(esz * std::max<size_t>(m, 1));
@@ -446,7 +450,7 @@ gg_status lh_prepare(gg_graph* g, uint32_t delta, cudaStream_t s) {
     }
     for (int i = 0; i < 2; ++i) g->lhb.bm_r[i] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * nw));
     if (off != total) {
-      cudaFree(p);
+      dev_free(p, s);
       return fail(GG_ERR_INTERNAL, "light/heavy buffer layout");
     }
     g->lh_block = p;
@@ -454,12 +458,12 @@ gg_status lh_prepare(gg_graph* g, uint32_t delta, cudaStream_t s) {
   }
   g->lh_delta = 0;   // invalid until the partition below is complete
   uint32_t* L = nullptr;
-  GG_CK(cudaMallocAsync(&L, sizeof(uint32_t) * (m + 1), s));
+  GG_CK(dev_malloc(&L, sizeof(uint32_t) * (m + 1), s));
   if (pk) k_lh_flags<true><<<grid_for(m), 256, 0, s>>>((uint32_t)m, g->dg.edges, g->dg.wbits, delta, L);
   else k_lh_flags<false><<<grid_for(m), 256, 0, s>>>((uint32_t)m, g->dg.edges, g->dg.wbits, delta, L);
   GG_CK(cudaGetLastError());
   gg_status st = scan_excl(L, (uint64_t)m + 1, s);
-  if (st != GG_OK) { cudaFreeAsync(L, s); return st; }
+  if (st != GG_OK) { dev_free(L, s); return st; }
   uint32_t nlight = 0;
   GG_CK(cudaMemcpyAsync(&nlight, L + m, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   uint32_t* lend = const_cast<uint32_t*>(g->lhb.lend);
@@ -467,40 +471,41 @@ gg_status lh_prepare(gg_graph* g, uint32_t delta, cudaStream_t s) {
   GG_CK(cudaGetLastError());
   if (m) {
     uint32_t* X = nullptr;
-    GG_CK(cudaMallocAsync(&X, sizeof(uint32_t) * (m + 1), s));
+    GG_CK(dev_malloc(&X, sizeof(uint32_t) * (m + 1), s));
     GG_CK(cudaMemsetAsync(X, 0, sizeof(uint32_t) * (m + 1), s));
     k_row_starts<<<grid_for(n), 256, 0, s>>>((uint32_t)n, (uint32_t)m, g->ro, X);
     GG_CK(cudaGetLastError());
     st = scan_excl(X, (uint64_t)m + 1, s);
-    if (st != GG_OK) { cudaFreeAsync(X, s); cudaFreeAsync(L, s); return st; }
+    if (st != GG_OK) { dev_free(X, s); dev_free(L, s); return st; }
     void* out = const_cast<void*>(g->lhb.edges);
     if (pk) k_lh_scatter<true><<<grid_for(m), 256, 0, s>>>((uint32_t)m, g->ro, X, g->dg.edges, L, lend,
                                                             g->dg.wbits, delta, out);
     else k_lh_scatter<false><<<grid_for(m), 256, 0, s>>>((uint32_t)m, g->ro, X, g->dg.edges, L, lend,
                                                           g->dg.wbits, delta, out);
     GG_CK(cudaGetLastError());
-    GG_CK(cudaFreeAsync(X, s));
+    dev_free(X, s);
   }
-  GG_CK(cudaFreeAsync(L, s));
+  dev_free(L, s);
   GG_CK(cudaStreamSynchronize(s));
   g->lh_heavy_total = m - nlight;
   g->lh_delta = delta;
   return GG_OK;
 }
 
+// Callers have synchronised the handle's work: the frees go on the legacy stream.
 void graph_free(gg_graph* g) {
-  if (g->lh_block) cudaFree(g->lh_block);
+  dev_free(g->lh_block, 0);
   g->lh_block = nullptr;
   g->lh_delta = 0;
-  if (g->t_ro && g->t_ro != g->ro) cudaFree(g->t_ro);
-  if (g->t_edges && g->t_edges != g->edges) cudaFree(g->t_edges);
-  if (g->t_edges4 && g->t_edges4 != g->edges4) cudaFree(g->t_edges4);
-  cudaFree(g->edges4);
+  if (g->t_ro && g->t_ro != g->ro) dev_free(g->t_ro, 0);
+  if (g->t_edges && g->t_edges != g->edges) dev_free(g->t_edges, 0);
+  if (g->t_edges4 && g->t_edges4 != g->edges4) dev_free(g->t_edges4, 0);
+  dev_free(g->edges4, 0);
   g->edges4 = g->t_edges4 = nullptr;
-  cudaFree(g->ro);
-  cudaFree(g->edges);
-  cudaFree(g->pv);
-  cudaFree(g->ps);
+  dev_free(g->ro, 0);
+  dev_free(g->edges, 0);
+  dev_free(g->pv, 0);
+  dev_free(g->ps, 0);
   g->ro = g->t_ro = g->pv = g->ps = nullptr;
   g->edges = g->t_edges = nullptr;
 }

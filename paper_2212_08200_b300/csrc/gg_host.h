@@ -22,6 +22,17 @@ gg_status cuda_fail(cudaError_t e, const char* what);
     if (e_ != cudaSuccess) return ::gg::cuda_fail(e_, #call); \
   } while (0)
 
+// Device memory of graph handles and their workspaces comes from one
+// stream-ordered pool per device that keeps up to GG_POOL_KEEP bytes of freed
+// memory mapped, so that creating and destroying handles does not map and
+// unmap memory (nor synchronise the device, as cudaFree does) each time.
+cudaError_t dev_malloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+template <class T>
+cudaError_t dev_malloc(T** p, size_t bytes, cudaStream_t s) {
+  return dev_malloc(reinterpret_cast<void**>(p), bytes, s);
+}
+
 struct DeviceInfo {
   int device = -1;
   int num_sms = 0;
