@@ -151,7 +151,7 @@ gg_status gg_graph_create_csr(uint32_t n, uint64_t m, const uint32_t* row_offset
   gg_status st = graph_build(g, n, m, row_offsets, col_indices, weights, flags, stream);
   if (st == GG_OK) {
     cudaError_t e = cudaEventCreateWithFlags(&g->last_ev, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaMallocHost(&g->h_ctl, sizeof(Ctl));
+    // (the pinned control-block mirror is allocated on first use: bsp_read_ctl)
     if (e != cudaSuccess) st = cuda_fail(e, "graph handle setup");
   }
   if (st != GG_OK) {

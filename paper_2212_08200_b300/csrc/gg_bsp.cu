@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "gg_host.h"
 
@@ -1663,6 +1664,7 @@ gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o
     const size_t smem = superstep_smem(variant);
     cudaGraphConditionalHandle none = 0;
     int zero = 0;
+    if (!g->h_ctl) GG_CK(cudaMallocHost(&g->h_ctl, sizeof(Ctl)));   // pinned mirror, on first use
     uint32_t* h_running = &g->h_ctl->running;
     uint32_t launched = 0;
     uint32_t check_every = 1;
@@ -1684,6 +1686,10 @@ gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o
 }
 
 gg_status bsp_read_ctl(gg_graph* g, cudaStream_t s) {
+  if (!g->h_ctl) {   // pinned mirror, allocated on first use
+    GG_CK(cudaMallocHost(&g->h_ctl, sizeof(Ctl)));
+    memset(g->h_ctl, 0, sizeof(Ctl));
+  }
   if (!g->bsp.ctl) return GG_OK;
   GG_CK(cudaMemcpyAsync(g->h_ctl, g->bsp.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
   GG_CK(cudaStreamSynchronize(s));
