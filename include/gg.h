@@ -285,11 +285,18 @@ gg_status gg_sssp_batch(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t
  * 64-source groups; setting stats synchronises the stream), delta and the
  * policy GG_POLICY_BSP_HOST (supersteps launched one by one from the host,
  * synchronising after each; every other policy runs the CUDA-graph loop) are
- * honoured; direction and load-balance fields are ignored.  delta
- * 0 or GG_DELTA_NONE runs the plain frontier loop (the default: buckets make
- * a vertex whose sources fall in different buckets expand once per bucket);
- * another value parks (vertex, source) pairs at or above the threshold in
- * per-vertex far masks. */
+ * honoured; direction and load-balance fields are ignored.  delta 0 (the
+ * default) runs light-first rounds on graphs with a light/heavy width (mean
+ * degree >= 8, integer weights) unless light_heavy is GG_LH_OFF: light
+ * supersteps relax only the light edges of the light-first edge copy (the
+ * one the single-source loop uses, built on first use), every improving
+ * (vertex, source) pair is also recorded in an R mask, and when the light
+ * frontier empties one heavy superstep relaxes the heavy edges of the R
+ * pairs.  Otherwise delta 0 or GG_DELTA_NONE runs the plain frontier loop
+ * (buckets would make a vertex whose sources fall in different buckets expand
+ * once per bucket); another value parks (vertex, source) pairs at or above
+ * the threshold in per-vertex far masks.  Distances are the same in every
+ * mode. */
 gg_status gg_sssp_batch_ex(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t* dist_out,
                            const gg_options* opt, cudaStream_t stream);
 

@@ -18,9 +18,18 @@
 //            returns both its queue position and its edge-prefix base, so the
 //            next frontier comes out already carrying its merge-path
 //            coordinates (no separate scan pass);
-//   loop     the last CTA to finish updates the counters, picks push or pull
-//            for the next superstep, and sets the CUDA-graph conditional
-//            (frontier non-empty), so the whole loop runs on the device.
+//   loop     the last CTA to finish updates the counters, picks the next
+//            superstep's kind (push, pull, near-far split, heavy push or
+//            pull), and sets the CUDA-graph conditional (work left), so the
+//            whole loop runs on the device; the graph's loop body holds eight
+//            superstep kernels per evaluation of the condition.
+// On skewed graphs the default is light/heavy buckets (Meyer-Sanders
+// delta-stepping over the near-far split): push supersteps relax only the
+// light edges of a light-first copy of the edges, and each vertex that settles
+// into the current bucket has its heavy edges relaxed once, by a heavy
+// superstep that pushes from the settled vertices or pulls into the unsettled
+// ones.  Every relaxation is the same atomicMin with the strict < test, so the
+// distances are those of the plain loop.
 #include <cuda_runtime.h>
 
 #include <algorithm>
