@@ -849,7 +849,7 @@ __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArg
   const unsigned FULL = 0xFFFFFFFFu;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  const uint32_t n = a.g.n, t_cur = fo.t_cur, wbits = a.g.wbits;
+  const uint32_t t_cur = fo.t_cur, wbits = a.g.wbits;
   const void* __restrict__ edges = a.lb.edges;
   const uint32_t* __restrict__ lend = a.lb.lend;
   uint32_t* wbest = sm.ec + warp * 32;
@@ -859,10 +859,15 @@ __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArg
   uint32_t fmin = kInf;
   unsigned long long scanned = 0;
   bool ovf = false;
-  for (uint32_t base = (blockIdx.x * (BLOCK / 32) + warp) * 32u; base < n; base += W * 32u) {
-    const uint32_t v = base + lane;
+  // the vertices with edges, in id order (the pull list; isolated vertices,
+  // 40 % of an RMAT graph, have nothing to pull)
+  const uint32_t np = a.g.np;
+  const uint32_t* __restrict__ pv = a.g.pv;
+  for (uint32_t base = (blockIdx.x * (BLOCK / 32) + warp) * 32u; base < np; base += W * 32u) {
+    const bool have = base + lane < np;
+    const uint32_t v = have ? __ldg(pv + base + lane) : 0u;
     uint32_t dv = 0, hs = 0, deg = 0;
-    if (v < n) {
+    if (have) {
       dv = ld_cg(dist + v);
       if (dv >= t_cur) {
         hs = __ldg(lend + v);
@@ -904,7 +909,7 @@ __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArg
     __syncwarp();
     const uint32_t best = wbest[lane];
     bool far = false;
-    if (v < n && best < dv) {
+    if (have && best < dv) {
       dist[v] = best;
       fmin = min(fmin, best);
       const uint32_t bit = 1u << (v & 31);
