@@ -805,8 +805,14 @@ __device__ __forceinline__ void far_split(MPSmem<BLOCK, EPT>& sm, const StepArgs
       const uint32_t d = ld_cg(dist + v);
       const uint32_t bit = 1u << (v & 31);
       if (d < fo.t_cur) {
-        atomicAnd(fo.bm_far + (v >> 5), ~bit);
-        if (d >= t_prev) near = !(atomicOr(fo.bm_next + (v >> 5), bit) & bit);
+        // once the threshold is infinite nothing is parked again: the far
+        // bits no longer matter
+        if (fo.t_cur != kInf) atomicAnd(fo.bm_far + (v >> 5), ~bit);
+        // a split step relaxes nothing and the pile holds each vertex once,
+        // so its near vertices need no dedup; they still enter the bitmap,
+        // which a pull superstep reads as the frontier (no result: no wait)
+        near = d >= t_prev;
+        if (near) atomicOr(fo.bm_next + (v >> 5), bit);
       } else {
         keep = true;   // its far bit stays set
         fmin = min(fmin, d);
