@@ -551,12 +551,10 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
   __syncthreads();
   if (tid == 0) {
     if (sm.ovf) atomicOr(&ctl->status, DS_OVERFLOW);
-    __threadfence();
-    sm.last = (atomicAdd(&ctl->done_ctas, 1u) == gridDim.x - 1) ? 1u : 0u;
+    sm.last = arrive_last(&ctl->done_ctas, gridDim.x) ? 1u : 0u;
   }
   __syncthreads();
   if (sm.last && tid == 0) {
-    __threadfence();
     const unsigned long long cn = atomicAdd(&ctl->cnt[pn], 0ull);
     const uint32_t fn = (uint32_t)(cn >> 32);
     if (F > 0 && bmode == 0) {

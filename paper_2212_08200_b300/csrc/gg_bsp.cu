@@ -61,6 +61,15 @@
 #ifndef GG_BODY_UNROLL
 #define GG_BODY_UNROLL 8   // supersteps per iteration of the CUDA-graph loop (measured: 1 -> 8 saves
 #endif                     // 12 % on RMAT-20, 6 % on RMAT-22, 23 % on the 4096^2 grid; 16 adds nothing)
+#ifndef GG_PULL_WU
+#define GG_PULL_WU 4   // 32-edge chunks per step of the heavy pull (gathers in flight per lane)
+#endif
+#ifndef GG_FAR_Q
+#define GG_FAR_Q 1     // heavy pull: park far vertices through a per-warp queue
+#endif
+#ifndef GG_FAR_Q_SPLIT
+#define GG_FAR_Q_SPLIT 0   // the same in the split step (measured: 2 % slower on the 4096^2 grid)
+#endif
 #ifndef GG_LH_DRAIN
 #define GG_LH_DRAIN 8    // light/heavy: bucketing ends once the unsettled vertices hold
 #endif                   // fewer than m / GG_LH_DRAIN heavy edges
@@ -780,6 +789,34 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
   if (__any_sync(FULL, ovf) && lane == 0) sm.ovf = 1u;
 }
 
+// Per-warp far queue: parked vertices gather in shared memory and reach the
+// far pile in runs of up to kFarQ, one counter atomic per run instead of one
+// per 32 entries (every warp of the grid appends to the same counter).
+constexpr uint32_t kFarQ = 128;
+
+__device__ __forceinline__ void far_q_flush(uint32_t* fq, uint32_t& fn, const FilterOut& fo) {
+  const uint32_t lane = threadIdx.x & 31;
+  __syncwarp();
+  uint32_t b = 0;
+  if (lane == 0) {
+    b = atomicAdd(fo.far_cnt, fn);
+    if (fo.far_add) atomicAdd(fo.far_add, fn);
+  }
+  b = __shfl_sync(0xFFFFFFFFu, b, 0);
+  for (uint32_t i = lane; i < fn; i += 32) fo.far[b + i] = fq[i];
+  fn = 0;
+  __syncwarp();
+}
+
+// Appends the lanes with `mine` set (ballot `mb`, non-zero) to the queue.
+__device__ __forceinline__ void far_q_push(uint32_t* fq, uint32_t& fn, const FilterOut& fo, bool mine, uint32_t v,
+                                           unsigned mb) {
+  const uint32_t lane = threadIdx.x & 31;
+  if (mine) fq[fn + __popc(mb & ((1u << lane) - 1u))] = v;
+  fn += __popc(mb);
+  if (fn > kFarQ - 32) far_q_flush(fq, fn, fo);
+}
+
 // Split step of the near-far frontier, run when the near frontier is empty:
 // every far-pile vertex v is re-examined against the raised threshold.
 //   dist[v] <  t_prev  it was improved below the old threshold after it was
@@ -796,6 +833,9 @@ __device__ __forceinline__ void far_split(MPSmem<BLOCK, EPT>& sm, const StepArgs
   const unsigned lt = (1u << lane) - 1u;
   const uint32_t W = gridDim.x * (BLOCK / 32);
   uint32_t fmin = kInf;
+  static_assert((BLOCK / 32) * kFarQ <= (uint32_t)MPSmem<BLOCK, EPT>::ECAP, "per-warp far queues fit");
+  uint32_t* fq = sm.es + (threadIdx.x >> 5) * kFarQ;   // per-warp far queue
+  uint32_t fn = 0;
   for (uint32_t base = (blockIdx.x * (BLOCK / 32) + (threadIdx.x >> 5)) * 32u; base < nfar; base += W * 32u) {
     const uint32_t i = base + lane;
     uint32_t v = 0;
@@ -819,7 +859,9 @@ __device__ __forceinline__ void far_split(MPSmem<BLOCK, EPT>& sm, const StepArgs
       }
     }
     const unsigned kb = __ballot_sync(FULL, keep);
-    if (kb) {
+    if (GG_FAR_Q_SPLIT) {
+      if (kb) far_q_push(fq, fn, fo, keep, v, kb);
+    } else if (kb) {
       uint32_t b = 0;
       if (lane == 0) {
         b = atomicAdd(fo.far_cnt, (uint32_t)__popc(kb));
@@ -833,6 +875,7 @@ __device__ __forceinline__ void far_split(MPSmem<BLOCK, EPT>& sm, const StepArgs
       else append32<false>(a, fo, near, v);
     }
   }
+  if (GG_FAR_Q_SPLIT && fn) far_q_flush(fq, fn, fo);
 #pragma unroll
   for (int o = 16; o; o >>= 1) fmin = min(fmin, __shfl_xor_sync(FULL, fmin, o));
   if (lane == 0 && fmin != kInf) atomicMin(&sm.fmin, fmin);
@@ -859,6 +902,9 @@ __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArg
   const void* __restrict__ edges = a.lb.edges;
   const uint32_t* __restrict__ lend = a.lb.lend;
   uint32_t* wbest = sm.ec + warp * 32;
+  static_assert((BLOCK / 32) * kFarQ <= (uint32_t)MPSmem<BLOCK, EPT>::ECAP, "per-warp far queues fit");
+  uint32_t* fq = sm.es + warp * kFarQ;   // per-warp far queue
+  uint32_t fn = 0;
   // the consumed R list is not read: clear its membership bitmap outright
   for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < a.g.nwords; i += gridDim.x * BLOCK) bm_r_old[i] = 0u;
   const uint32_t W = gridDim.x * (BLOCK / 32);
@@ -891,26 +937,42 @@ __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArg
     const uint32_t ex = x - deg;   // first list position of this lane's edges
     wbest[lane] = kInf;
     __syncwarp();
-    for (uint32_t c = 0; c < T; c += 32) {
-      const uint32_t j = c + lane;
-      // owner: the last lane whose first position is <= j (lanes without edges
-      // share their successor's position and come before it)
-      uint32_t k = 0;
+    constexpr int PU = GG_PULL_WU;
+    for (uint32_t c = 0; c < T; c += 32u * PU) {
+      // PU chunks per step: their edge loads, then their distance gathers, in flight together
+      uint32_t k[PU];
+      uint2 ed[PU];
 #pragma unroll
-      for (int step = 16; step; step >>= 1) {
-        const uint32_t sv = __shfl_sync(FULL, ex, k + step);
-        if (sv <= j) k += step;
+      for (int u = 0; u < PU; ++u) {
+        const uint32_t j = c + 32u * u + lane;
+        // owner: the last lane whose first position is <= j (lanes without edges
+        // share their successor's position and come before it)
+        k[u] = 0;
+#pragma unroll
+        for (int step = 16; step; step >>= 1) {
+          const uint32_t sv = __shfl_sync(FULL, ex, k[u] + step);
+          if (sv <= j) k[u] += step;
+        }
+        const uint32_t ks = __shfl_sync(FULL, hs, k[u]), kx = __shfl_sync(FULL, ex, k[u]);
+        if (j < T) ed[u] = load_edge<PK>(edges, ks + (j - kx), wbits);
       }
-      const uint32_t ks = __shfl_sync(FULL, hs, k), kx = __shfl_sync(FULL, ex, k);
-      uint32_t cand = kInf;
-      if (j < T) {
-        const uint2 ed = load_edge<PK>(edges, ks + (j - kx), wbits);
-        const uint32_t du = ld_cg(dist + ed.x);
-        if (du < t_cur) cand = add_sat(du, ed.y, ovf);
+      uint32_t cand[PU];
+#pragma unroll
+      for (int u = 0; u < PU; ++u) {
+        cand[u] = kInf;
+        if (c + 32u * u + lane < T) {
+          const uint32_t du = ld_cg(dist + ed[u].x);
+          if (du < t_cur) cand[u] = add_sat(du, ed[u].y, ovf);
+        }
       }
-      const unsigned same = __match_any_sync(FULL, k);
-      const uint32_t r = __reduce_min_sync(same, cand);
-      if (r != kInf && lane == (uint32_t)(__ffs(same) - 1)) atomicMin(&wbest[k], r);
+#pragma unroll
+      for (int u = 0; u < PU; ++u) {
+        if (u == 0 || c + 32u * u < T) {   // warp-uniform
+          const unsigned same = __match_any_sync(FULL, k[u]);
+          const uint32_t r = __reduce_min_sync(same, cand[u]);
+          if (r != kInf && lane == (uint32_t)(__ffs(same) - 1)) atomicMin(&wbest[k[u]], r);
+        }
+      }
     }
     __syncwarp();
     const uint32_t best = wbest[lane];
@@ -922,7 +984,9 @@ __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArg
       far = !(atomicOr(fo.bm_far + (v >> 5), bit) & bit);
     }
     const unsigned fb = __ballot_sync(FULL, far);
-    if (fb) {
+    if (GG_FAR_Q) {
+      if (fb) far_q_push(fq, fn, fo, far, v, fb);
+    } else if (fb) {
       uint32_t b = 0;
       if (lane == 0) b = atomicAdd(fo.far_cnt, (uint32_t)__popc(fb));
       b = __shfl_sync(FULL, b, 0);
@@ -931,6 +995,7 @@ __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArg
     scanned += T;
     __syncwarp();
   }
+  if (GG_FAR_Q && fn) far_q_flush(fq, fn, fo);
 #pragma unroll
   for (int o = 16; o; o >>= 1) fmin = min(fmin, __shfl_xor_sync(FULL, fmin, o));
   if (lane == 0) {
@@ -963,8 +1028,24 @@ __device__ __forceinline__ unsigned long long bsp_globaltimer() {
   return t;
 }
 
+// Relaxed loads at L2 (no L1 copy): the counters that the CTAs of a superstep
+// update with atomics, read by the last CTA after its acquire fence.
+__device__ __forceinline__ uint32_t ld_rlx(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_rlx(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // The last CTA to arrive closes the superstep: counters, trace, the next
-// step's kind (push, pull, or a near-far split) and the loop condition.
+// step's kind (push, pull, or a near-far split) and the loop condition.  It
+// sits between every two supersteps, so its one thread reads everything it
+// needs in one batch of independent loads, decides in registers, and only then
+// stores (no load waits on another).
 template <int BLOCK, int EPT>
 __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t it, uint32_t f,
                                                    uint32_t E, uint32_t mode, cudaGraphConditionalHandle cond,
@@ -975,103 +1056,128 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
   if (threadIdx.x == 0) {
     if (sm.ovf) atomicOr(&ctl->status, DS_OVERFLOW);
     if (sm.fmin != kInf) atomicMin(&ctl->far_min, sm.fmin);
-    __threadfence();
-    sm.last = (atomicAdd(&ctl->done_ctas, 1u) == gridDim.x - 1) ? 1u : 0u;
+    sm.last = arrive_last(&ctl->done_ctas, gridDim.x) ? 1u : 0u;
   }
   __syncthreads();
   if (sm.last && threadIdx.x == 0) {
-    __threadfence();
-    const unsigned long long cn = atomicAdd(&ctl->cnt[p ^ 1u], 0ull);
-    const uint32_t fn = (uint32_t)(cn >> 32), En = (uint32_t)cn;
+    // counters of this superstep (atomics of every CTA)
+    const unsigned long long cn = ld_rlx(&ctl->cnt[p ^ 1u]);
+    const uint32_t fc0 = ld_rlx(&ctl->far_cnt[0]), fc1 = ld_rlx(&ctl->far_cnt[1]);
+    const unsigned long long rc0 = ld_rlx(&ctl->rcnt[0]), rc1 = ld_rlx(&ctl->rcnt[1]);
+    const uint32_t far_min = ld_rlx(&ctl->far_min);
+    const uint32_t status = ld_rlx(&ctl->status);
+    // run state (written by this finalize only)
     uint32_t fp = ctl->fp;
-    if (mode == MODE_SPLIT) {   // the kept entries were written to the other pile
-      ctl->far_cnt[fp] = 0u;
-      fp ^= 1u;
-      ctl->fp = fp;
-      ctl->splits += 1;
-    }
-    const uint32_t nfar = atomicAdd(&ctl->far_cnt[fp], 0u);
-    const uint32_t lh = ctl->lh;
+    const uint32_t lh = ctl->lh, splits = ctl->splits;
+    uint32_t epoch = ctl->epoch;
+    uint32_t* trace = ctl->trace;
+    const uint32_t trace_cap = ctl->trace_cap;
+    const uint32_t heavy_pull_ok = ctl->heavy_pull_ok, t_cur = ctl->t_cur, delta = ctl->delta;
+    const uint32_t drain_div = ctl->drain_div, dir = ctl->dir, alpha = ctl->alpha, beta = ctl->beta;
+    const uint32_t max_iter = ctl->max_iter, max_frontier = ctl->max_frontier, pull_iters = ctl->pull_iters;
+    const unsigned long long heavy_total = ctl->heavy_total, frontier_total = ctl->frontier_total;
+    unsigned long long heavy_done = ctl->heavy_done;
+    const unsigned long long t_start = ctl->t_start, watchdog_ns = ctl->watchdog_ns;
+
+    const uint32_t fn = (uint32_t)(cn >> 32), En = (uint32_t)cn;
+    if (mode == MODE_SPLIT) fp ^= 1u;   // the kept entries were written to the other pile
+    const uint32_t nfar = fp ? fc1 : fc0;
+    const bool heavy = mode == MODE_HEAVY || mode == MODE_HEAVY_PULL;
     uint32_t rn = 0;   // R list of the epoch the next superstep works in
     unsigned long long rE = 0;   // and its heavy edges
     if (lh) {
-      if (mode == MODE_HEAVY || mode == MODE_HEAVY_PULL) {   // R[epoch] is consumed: the next epoch begins
-        ctl->heavy_done += E;
-        ctl->rcnt[ctl->epoch & 1u] = 0ull;
-        ctl->epoch += 1u;
+      if (heavy) {   // R[epoch] is consumed: the next epoch begins
+        heavy_done += E;
+        epoch += 1u;
       }
-      const unsigned long long r = atomicAdd(&ctl->rcnt[ctl->epoch & 1u], 0ull);
+      const unsigned long long r = (epoch & 1u) ? rc1 : rc0;
       rn = (uint32_t)(r >> 32);
       rE = (uint32_t)r;
     }
-    if (ctl->trace && it < ctl->trace_cap) {
-      uint32_t* t = ctl->trace + 4ull * it;
+    uint32_t nm;
+    uint32_t t_next = t_cur;
+    if (lh && (fn > 0 || rn > 0)) {
+      // light edges of the near frontier first; when it is empty, one heavy
+      // superstep over the vertices that settled since the last one
+      nm = fn > 0 ? MODE_PUSH : MODE_HEAVY;
+      if (nm == MODE_HEAVY && heavy_pull_ok && t_cur != kInf) {
+        // pull when R's heavy edges outnumber those still unsettled (plus the
+        // cost of the dense pass over the distances)
+        const unsigned long long left = heavy_total > heavy_done + rE ? heavy_total - heavy_done - rE : 0ull;
+        if (rE > left + a.g.n / 8) nm = MODE_HEAVY_PULL;
+      }
+    } else if (fn == 0 && nfar > 0) {
+      // near frontier exhausted: raise the threshold past the smallest parked distance
+      nm = MODE_SPLIT;
+      const unsigned long long t1 = (unsigned long long)t_cur + delta;
+      const unsigned long long t2 = (unsigned long long)far_min + 1;
+      unsigned long long tn = t1 > t2 ? t1 : t2;
+      // light/heavy: once the vertices not yet settled hold only a small share
+      // of the heavy edges, the rest of the run is one bucket (the sparse tail
+      // of a skewed graph costs more in supersteps than in re-relaxations)
+      if (lh && drain_div && (heavy_total - min(heavy_done, heavy_total)) * drain_div < (unsigned long long)a.g.m)
+        tn = kInf;
+      t_next = tn >= kInf ? kInf : (uint32_t)tn;
+    } else if (dir == DIR_PUSH) {
+      nm = MODE_PUSH;
+    } else if (dir == DIR_PULL) {
+      nm = MODE_PULL;
+    } else if (mode != MODE_PULL) {
+      nm = ((unsigned long long)En * alpha > a.g.m) ? MODE_PULL : MODE_PUSH;
+    } else {
+      nm = ((unsigned long long)fn * beta < a.g.np) ? MODE_PUSH : MODE_PULL;
+    }
+    bool more = fn != 0 || nfar != 0 || rn != 0;
+    uint32_t st = 0;
+    if (more && it + 1 >= max_iter) {
+      st |= DS_ITER_CAP;
+      more = false;
+    }
+    // signed difference: %globaltimer on this SM may lag the start stamp slightly
+    if (more && (long long)(bsp_globaltimer() - t_start) > (long long)watchdog_ns) {
+      st |= DS_TIMEOUT;
+      more = false;
+    }
+
+    // stores
+    if (mode == MODE_SPLIT) {
+      ctl->far_cnt[fp ^ 1u] = 0u;
+      ctl->fp = fp;
+      ctl->splits = splits + 1u;
+    }
+    if (lh && heavy) {
+      ctl->heavy_done = heavy_done;
+      ctl->rcnt[(epoch - 1u) & 1u] = 0ull;
+      ctl->epoch = epoch;
+    }
+    if (trace && it < trace_cap) {
+      uint32_t* t = trace + 4ull * it;
       t[0] = f;
-      t[1] = (mode == MODE_PUSH || mode == MODE_HEAVY || mode == MODE_HEAVY_PULL) ? E : mode == MODE_PULL ? a.g.m : 0u;
+      t[1] = (mode == MODE_PUSH || heavy) ? E : mode == MODE_PULL ? a.g.m : 0u;
       t[2] = mode;
       t[3] = fn;
     }
     if (f > 0 && mode != MODE_SPLIT) {
-      // a pull heavy step counts the edges it scans itself
-      ctl->edges_scanned += (mode == MODE_PUSH || mode == MODE_HEAVY) ? E : mode == MODE_PULL ? a.g.m : 0u;
-      ctl->frontier_total += f;
-      ctl->max_frontier = max(ctl->max_frontier, f);
-      ctl->pull_iters += mode == MODE_PULL ? 1u : 0u;
+      // a pull heavy step counts the edges it scans itself (atomically: add to it)
+      const unsigned long long sc = (mode == MODE_PUSH || mode == MODE_HEAVY) ? E : mode == MODE_PULL ? a.g.m : 0u;
+      if (sc) atomicAdd(&ctl->edges_scanned, sc);
+      ctl->frontier_total = frontier_total + f;
+      ctl->max_frontier = max(max_frontier, f);
+      if (mode == MODE_PULL) ctl->pull_iters = pull_iters + 1u;
     }
     ctl->cnt[p] = 0ull;
     ctl->done_ctas = 0u;
     // light/heavy: vertices without light edges are marked in the next
     // bitmap but never enter the frontier, so the old bitmap is always cleared
     ctl->clear_prev = (mode == MODE_PULL || lh) ? 1u : 0u;
-    uint32_t nm;
-    if (lh && (fn > 0 || rn > 0)) {
-      // light edges of the near frontier first; when it is empty, one heavy
-      // superstep over the vertices that settled since the last one
-      nm = fn > 0 ? MODE_PUSH : MODE_HEAVY;
-      if (nm == MODE_HEAVY && ctl->heavy_pull_ok && ctl->t_cur != kInf) {
-        // pull when R's heavy edges outnumber those still unsettled (plus the
-        // cost of the dense pass over the distances)
-        const unsigned long long left = ctl->heavy_total > ctl->heavy_done + rE
-                                            ? ctl->heavy_total - ctl->heavy_done - rE : 0ull;
-        if (rE > left + a.g.n / 8) nm = MODE_HEAVY_PULL;
-      }
-    } else if (fn == 0 && nfar > 0) {
-      // near frontier exhausted: raise the threshold past the smallest parked distance
-      nm = MODE_SPLIT;
-      const uint32_t fmin = ctl->far_min;
-      const unsigned long long t1 = (unsigned long long)ctl->t_cur + ctl->delta;
-      const unsigned long long t2 = (unsigned long long)fmin + 1;
-      unsigned long long tn = t1 > t2 ? t1 : t2;
-      // light/heavy: once the vertices not yet settled hold only a small share
-      // of the heavy edges, the rest of the run is one bucket (the sparse tail
-      // of a skewed graph costs more in supersteps than in re-relaxations)
-      if (lh && ctl->drain_div &&
-          (ctl->heavy_total - min(ctl->heavy_done, ctl->heavy_total)) * ctl->drain_div < (unsigned long long)a.g.m)
-        tn = kInf;
-      ctl->t_prev = ctl->t_cur;
-      ctl->t_cur = tn >= kInf ? kInf : (uint32_t)tn;
+    if (nm == MODE_SPLIT) {
+      ctl->t_prev = t_cur;
+      ctl->t_cur = t_next;
       ctl->far_min = kInf;
-    } else if (ctl->dir == DIR_PUSH) {
-      nm = MODE_PUSH;
-    } else if (ctl->dir == DIR_PULL) {
-      nm = MODE_PULL;
-    } else if (mode != MODE_PULL) {
-      nm = ((unsigned long long)En * ctl->alpha > a.g.m) ? MODE_PULL : MODE_PUSH;
-    } else {
-      nm = ((unsigned long long)fn * ctl->beta < a.g.np) ? MODE_PUSH : MODE_PULL;
     }
     ctl->mode = nm;
     ctl->iter = it + 1;
-    bool more = fn != 0 || nfar != 0 || rn != 0;
-    if (more && it + 1 >= ctl->max_iter) {
-      ctl->status |= DS_ITER_CAP;
-      more = false;
-    }
-    // signed difference: %globaltimer on this SM may lag the start stamp slightly
-    if (more && (long long)(bsp_globaltimer() - ctl->t_start) > (long long)ctl->watchdog_ns) {
-      ctl->status |= DS_TIMEOUT;
-      more = false;
-    }
+    if (st) ctl->status = status | st;
     ctl->running = more ? 1u : 0u;
     if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
   }
@@ -1093,24 +1199,29 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_supers
   // past the last one: those return at once, and each also clears the loop
   // condition, so a run that starts finished (a source without out-edges)
   // ends after one iteration instead of looping on the condition's default
-  if (GG_BODY_UNROLL > 1 && use_cond && ctl->running == 0u) {
+  // the step's state in one batch of independent loads (no load waits on
+  // another: both parities of each counter are read and selected after)
+  const uint32_t running = ctl->running, it = ctl->iter, mode = ctl->mode, fp = ctl->fp;
+  const unsigned long long c0 = ctl->cnt[0], c1 = ctl->cnt[1];
+  uint32_t* dist = ctl->dist;
+  const uint32_t t_cur = ctl->t_cur, t_prev = ctl->t_prev, clear_prev = ctl->clear_prev;
+  const uint32_t fc0 = ctl->far_cnt[0], fc1 = ctl->far_cnt[1];
+  const uint32_t ep = LH ? ctl->epoch : 0u;
+  const unsigned long long r0 = LH ? ctl->rcnt[0] : 0ull, r1 = LH ? ctl->rcnt[1] : 0ull;
+  if (GG_BODY_UNROLL > 1 && use_cond && running == 0u) {
     if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
     return;
   }
-  const uint32_t it = ctl->iter;
   const uint32_t p = it & 1u;
-  const unsigned long long c = ctl->cnt[p];
+  const unsigned long long c = p ? c1 : c0;
   const uint32_t f = (uint32_t)(c >> 32), E = (uint32_t)c;
-  const uint32_t mode = ctl->mode;
-  const uint32_t fp = ctl->fp;
-  uint32_t* dist = ctl->dist;
   uint32_t* bm_cur = a.fr.bm[it % 3];
   FilterOut fo;
   fo.ro = a.g.ro;
   fo.sinks = a.g.sinks;
   fo.bm_next = a.fr.bm[(it + 1) % 3];
   fo.bm_far = a.fr.bm_far;
-  fo.t_cur = ctl->t_cur;
+  fo.t_cur = t_cur;
   fo.cnt_next = &ctl->cnt[p ^ 1u];
   fo.nfv = a.fr.fv[p ^ 1u];
   fo.nfr = a.fr.fr[p ^ 1u];
@@ -1129,14 +1240,13 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_supers
   if (LH) {
     // new near vertices join the R list of the current epoch, or of the next
     // one while the heavy superstep consumes the current list
-    const uint32_t ep = ctl->epoch;
     const uint32_t rj = (mode == MODE_HEAVY || mode == MODE_HEAVY_PULL ? ep + 1u : ep) & 1u;
     fo.sinks = 0u;   // the light/heavy append checks both degrees itself
     fo.lh = 1u + rj;
     edges = a.lb.edges;
     if (mode == MODE_HEAVY || mode == MODE_HEAVY_PULL) {
       const uint32_t rc = ep & 1u;
-      const unsigned long long r = ctl->rcnt[rc];
+      const unsigned long long r = rc ? r1 : r0;
       fw = (uint32_t)(r >> 32);
       Ew = (uint32_t)r;
       fS = pick2(a.lb.rs, rc);
@@ -1145,11 +1255,11 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_supers
       bm_cur = pick2(a.lb.bm_r, rc);   // R entries clear their membership words as they are loaded
     }
   }
-  superstep_prologue(sm, a, it, ctl->clear_prev != 0);
+  superstep_prologue(sm, a, it, clear_prev != 0);
   if (mode == MODE_SPLIT) {
-    far_split(sm, a, fo, dist, a.fr.far[fp], ctl->far_cnt[fp], ctl->t_prev);
+    far_split(sm, a, fo, dist, a.fr.far[fp], fp ? fc1 : fc0, t_prev);
   } else if (LH && mode == MODE_HEAVY_PULL) {
-    heavy_pull<BLOCK, EPT, PK>(sm, a, fo, dist, pick2(a.lb.bm_r, ctl->epoch & 1u));
+    heavy_pull<BLOCK, EPT, PK>(sm, a, fo, dist, pick2(a.lb.bm_r, ep & 1u));
   } else if (fw > 0) {
     if (mode == MODE_PUSH || mode == MODE_HEAVY) {
       if (LB == LB_BINS)

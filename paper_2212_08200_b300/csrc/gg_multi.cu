@@ -201,8 +201,7 @@ __global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphC
   }
   __syncthreads();
   if (tid == 0) {
-    __threadfence();
-    sm.last = (atomicAdd(&ctl->done_ctas, 1u) == gridDim.x - 1) ? 1u : 0u;
+    sm.last = arrive_last(&ctl->done_ctas, gridDim.x) ? 1u : 0u;
   }
   __syncthreads();
   if (sm.last) {

@@ -260,12 +260,10 @@ __global__ void __launch_bounds__(kNaBlock) k_na_superstep(NaArgs a) {
   __syncthreads();
   if (tid == 0) {
     if (sm.ovf) atomicOr(&ctl->status, DS_OVERFLOW);
-    __threadfence();
-    sm.last = (atomicAdd(&ctl->done_ctas, 1u) == gridDim.x - 1) ? 1u : 0u;
+    sm.last = arrive_last(&ctl->done_ctas, gridDim.x) ? 1u : 0u;
   }
   __syncthreads();
   if (sm.last && tid == 0) {
-    __threadfence();
     const unsigned long long cn = atomicAdd(&ctl->cnt[p ^ 1u], 0ull);
     ctl->cnt[p] = 0ull;
     ctl->done_ctas = 0u;
