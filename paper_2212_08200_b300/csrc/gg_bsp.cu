@@ -70,6 +70,9 @@
 #ifndef GG_FAR_Q_SPLIT
 #define GG_FAR_Q_SPLIT 0   // the same in the split step (measured: 2 % slower on the 4096^2 grid)
 #endif
+#ifndef GG_LH_TAIL
+#define GG_LH_TAIL 1   // light/heavy: plain push once bucketing has ended
+#endif
 #ifndef GG_LH_DRAIN
 #define GG_LH_DRAIN 8    // light/heavy: bucketing ends once the unsettled vertices hold
 #endif                   // fewer than m / GG_LH_DRAIN heavy edges
@@ -1068,7 +1071,7 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
     const uint32_t status = ld_rlx(&ctl->status);
     // run state (written by this finalize only)
     uint32_t fp = ctl->fp;
-    const uint32_t lh = ctl->lh, splits = ctl->splits;
+    const uint32_t lh = ctl->lh, lh_tail = ctl->lh_tail, splits = ctl->splits;
     uint32_t epoch = ctl->epoch;
     uint32_t* trace = ctl->trace;
     const uint32_t trace_cap = ctl->trace_cap;
@@ -1083,9 +1086,11 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
     if (mode == MODE_SPLIT) fp ^= 1u;   // the kept entries were written to the other pile
     const uint32_t nfar = fp ? fc1 : fc0;
     const bool heavy = mode == MODE_HEAVY || mode == MODE_HEAVY_PULL;
+    const bool lhb = lh && !lh_tail;   // bucketed light/heavy supersteps
+    bool tail = false;
     uint32_t rn = 0;   // R list of the epoch the next superstep works in
     unsigned long long rE = 0;   // and its heavy edges
-    if (lh) {
+    if (lhb) {
       if (heavy) {   // R[epoch] is consumed: the next epoch begins
         heavy_done += E;
         epoch += 1u;
@@ -1096,7 +1101,7 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
     }
     uint32_t nm;
     uint32_t t_next = t_cur;
-    if (lh && (fn > 0 || rn > 0)) {
+    if (lhb && (fn > 0 || rn > 0)) {
       // light edges of the near frontier first; when it is empty, one heavy
       // superstep over the vertices that settled since the last one
       nm = fn > 0 ? MODE_PUSH : MODE_HEAVY;
@@ -1114,9 +1119,12 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
       unsigned long long tn = t1 > t2 ? t1 : t2;
       // light/heavy: once the vertices not yet settled hold only a small share
       // of the heavy edges, the rest of the run is one bucket (the sparse tail
-      // of a skewed graph costs more in supersteps than in re-relaxations)
-      if (lh && drain_div && (heavy_total - min(heavy_done, heavy_total)) * drain_div < (unsigned long long)a.g.m)
+      // of a skewed graph costs more in supersteps than in re-relaxations);
+      // the R list is empty here, and that bucket is plain push from the split on
+      if (lhb && drain_div && (heavy_total - min(heavy_done, heavy_total)) * drain_div < (unsigned long long)a.g.m) {
         tn = kInf;
+        tail = GG_LH_TAIL != 0;
+      }
       t_next = tn >= kInf ? kInf : (uint32_t)tn;
     } else if (dir == DIR_PUSH) {
       nm = MODE_PUSH;
@@ -1145,7 +1153,8 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
       ctl->fp = fp;
       ctl->splits = splits + 1u;
     }
-    if (lh && heavy) {
+    if (tail) ctl->lh_tail = 1u;
+    if (lhb && heavy) {
       ctl->heavy_done = heavy_done;
       ctl->rcnt[(epoch - 1u) & 1u] = 0ull;
       ctl->epoch = epoch;
@@ -1206,7 +1215,7 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_supers
   uint32_t* dist = ctl->dist;
   const uint32_t t_cur = ctl->t_cur, t_prev = ctl->t_prev, clear_prev = ctl->clear_prev;
   const uint32_t fc0 = ctl->far_cnt[0], fc1 = ctl->far_cnt[1];
-  const uint32_t ep = LH ? ctl->epoch : 0u;
+  const uint32_t ep = LH ? ctl->epoch : 0u, lh_tail = LH ? ctl->lh_tail : 0u;
   const unsigned long long r0 = LH ? ctl->rcnt[0] : 0ull, r1 = LH ? ctl->rcnt[1] : 0ull;
   if (GG_BODY_UNROLL > 1 && use_cond && running == 0u) {
     if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
@@ -1242,7 +1251,8 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_supers
     // one while the heavy superstep consumes the current list
     const uint32_t rj = (mode == MODE_HEAVY || mode == MODE_HEAVY_PULL ? ep + 1u : ep) & 1u;
     fo.sinks = 0u;   // the light/heavy append checks both degrees itself
-    fo.lh = 1u + rj;
+    // after bucketing: plain appends (all edges of a row of the light-first copy)
+    fo.lh = lh_tail ? 0u : 1u + rj;
     edges = a.lb.edges;
     if (mode == MODE_HEAVY || mode == MODE_HEAVY_PULL) {
       const uint32_t rc = ep & 1u;
@@ -1534,6 +1544,7 @@ __global__ void k_init_tail(StepArgs a, RunParams rp) {
   ctl->heavy_pull_ok = rp.heavy_pull_ok;
   ctl->heavy_total = rp.heavy_total;
   ctl->heavy_done = 0ull;
+  ctl->lh_tail = 0u;
   ctl->cnt[1] = 0ull;
   ctl->iter = 0;
   ctl->done_ctas = 0;

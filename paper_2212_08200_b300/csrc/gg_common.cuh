@@ -109,6 +109,10 @@ struct Ctl {
   uint32_t heavy_pull_ok;
   unsigned long long heavy_total;    // heavy edges of the graph
   unsigned long long heavy_done;     // heavy edges of the vertices settled so far
+  // once bucketing ends (the threshold becomes infinite) the rest of the run
+  // is plain push over all edges of each vertex: with one bucket left, the
+  // light/heavy alternation only adds supersteps
+  uint32_t lh_tail;
 };
 
 struct DevGraph {
