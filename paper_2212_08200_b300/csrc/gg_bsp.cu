@@ -1250,8 +1250,10 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_supers
     // new near vertices join the R list of the current epoch, or of the next
     // one while the heavy superstep consumes the current list
     const uint32_t rj = (mode == MODE_HEAVY || mode == MODE_HEAVY_PULL ? ep + 1u : ep) & 1u;
-    fo.sinks = 0u;   // the light/heavy append checks both degrees itself
-    // after bucketing: plain appends (all edges of a row of the light-first copy)
+    // the light/heavy append checks both degrees itself; after bucketing the
+    // appends are plain (all edges of a row of the light-first copy), with the
+    // plain loop's own handling of vertices without out-edges
+    fo.sinks = lh_tail ? a.g.sinks : 0u;
     fo.lh = lh_tail ? 0u : 1u + rj;
     edges = a.lb.edges;
     if (mode == MODE_HEAVY || mode == MODE_HEAVY_PULL) {

@@ -18,7 +18,7 @@
 #include "gg_host.h"
 
 #ifndef GG_LH_K
-#define GG_LH_K 3.0   // light edges per vertex aimed at by the default light/heavy bucket width
+#define GG_LH_K 2.7   // light edges per vertex aimed at by the default light/heavy bucket width
 #endif
 
 namespace gg {

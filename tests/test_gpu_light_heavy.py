@@ -184,6 +184,42 @@ def test_rmat20_default_width_is_light_heavy():
     g.close()
 
 
+def _sink_graph(seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n, m = 6000, 90000
+    src = rng.integers(0, 5000, m)             # vertices 5000.. have no out-edges (sinks)
+    dst = rng.integers(0, n, m)
+    return graphgen.from_edges(n, src, dst, rng.integers(0, 120, m))
+
+
+@pytest.mark.parametrize("lb", ["warp", "mp", "bins"])
+@pytest.mark.parametrize("graph", ["rmat18", "sinks"])
+def test_plain_push_once_bucketing_ends(graph, lb):
+    # once the unsettled vertices hold few heavy edges the threshold becomes
+    # infinite at a split, and every superstep after it is a plain push
+    # (kind 0) over all edges of each vertex
+    if graph == "rmat18":
+        ro, col, w, src = graphgen.workload("rmat18")
+        g = gg().Graph(ro, col, w, symmetric=True)
+        cases = [(src, 0), (int(graphgen.sample_sources(ro, 1, seed=5)[0]), 0)]
+    else:
+        ro, col, w = _sink_graph(13)
+        g = gg().Graph(ro, col, w, symmetric=False)
+        cases = [(0, 20), (4321, 40)]
+    ended = 0
+    for s, delta in cases:
+        got, st, kinds = run(g, s, delta, lb, trace_cap=8192)
+        np.testing.assert_array_equal(got, oracle.dijkstra(ro, col, w, s), err_msg=f"{graph} {lb} src={s}")
+        assert st["device_status"] == 0
+        splits = np.flatnonzero(kinds == 2)
+        if splits.size and not np.isin(kinds[splits[-1] + 1:], HEAVY).any():
+            tail = kinds[splits[-1] + 1:]
+            assert (tail == 0).all(), kinds
+            ended += tail.size > 0
+    assert ended > 0   # the plain tail ran in at least one case
+    g.close()
+
+
 def test_bad_light_heavy_value_is_rejected():
     m = gg()
     ro, col, w, src = graphgen.workload("grid64")
