@@ -1031,19 +1031,6 @@ __device__ __forceinline__ unsigned long long bsp_globaltimer() {
   return t;
 }
 
-// Relaxed loads at L2 (no L1 copy): the counters that the CTAs of a superstep
-// update with atomics, read by the last CTA after its acquire fence.
-__device__ __forceinline__ uint32_t ld_rlx(const uint32_t* p) {
-  uint32_t v;
-  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ unsigned long long ld_rlx(const unsigned long long* p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-
 // The last CTA to arrive closes the superstep: counters, trace, the next
 // step's kind (push, pull, or a near-far split) and the loop condition.  It
 // sits between every two supersteps, so its one thread reads everything it

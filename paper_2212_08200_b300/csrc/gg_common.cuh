@@ -151,6 +151,19 @@ __device__ __forceinline__ bool arrive_last(uint32_t* done, uint32_t ctas) {
   return old == ctas - 1u;
 }
 
+// Relaxed loads at L2 (no L1 copy): the counters that the CTAs of a superstep
+// update with atomics, read by the last CTA after its acquire.
+__device__ __forceinline__ uint32_t ld_rlx(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_rlx(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // L2-coherent load (bypasses L1): used for values other CTAs update with atomics.
 __device__ __forceinline__ uint32_t ld_cg(const uint32_t* p) { return __ldcg(p); }
 

@@ -209,7 +209,15 @@ __global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphC
     // its far pile next superstep (threshold raised past its smallest parked
     // distance) or, with an empty pile, has converged
     __threadfence();
-    if (tid == 0) sm.j = 0;
+    // the next frontier's count and the budget are loaded first; their wait
+    // overlaps the slot pass
+    unsigned long long cn = 0;
+    uint32_t budget = 0;
+    if (tid == 0) {
+      sm.j = 0;
+      cn = ld_rlx(&ctl->cnt[p ^ 1u]);
+      budget = ctl->budget_left;
+    }
     __syncthreads();
     for (uint32_t q = tid; q < b.nslots; q += kMB) {
       MultiSlot& sl = slots[q];
@@ -220,8 +228,9 @@ __global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphC
           sl.fpp ^= 1u;
           sl.split = 0u;
         }
+        const uint32_t fc = sl.far_cnt[sl.fpp];
         if (b.slot_cnt[q] == 0) {
-          if (sl.far_cnt[sl.fpp] > 0) {
+          if (fc > 0) {
             const unsigned long long t1 = (unsigned long long)sl.t_cur + sl.delta;
             const unsigned long long t2 = (unsigned long long)sl.far_min + 1;
             const unsigned long long tn = t1 > t2 ? t1 : t2;
@@ -229,7 +238,9 @@ __global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphC
             sl.t_cur = tn >= kInf ? kInf : (uint32_t)tn;
             sl.far_min = kInf;
             sl.split = 1u;
-            sm.qv[atomicAdd(&sm.j, 1u)] = q;
+            const uint32_t k = atomicAdd(&sm.j, 1u);
+            sm.qv[k] = q;
+            sm.qd[k] = fc;   // its pile's size: the prefix below reads no slot again
           } else {
             sl.state = kSlotDone;
             if (b.done_flags) {
@@ -247,21 +258,19 @@ __global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphC
       const uint32_t ns = sm.j;
       uint32_t run = 0;
       for (uint32_t k = 0; k < ns; ++k) {
-        const uint32_t q = sm.qv[k];
-        ctl->split_slot[k] = q;
+        ctl->split_slot[k] = sm.qv[k];
         ctl->split_pref[k] = run;
-        run += slots[q].far_cnt[slots[q].fpp];
+        run += sm.qd[k];
       }
       ctl->split_pref[ns] = run;
       ctl->nsplit = ns;
       ctl->split_total = run;
-      const unsigned long long cn = atomicAdd(&ctl->cnt[p ^ 1u], 0ull);
       ctl->cnt[p] = 0ull;
       ctl->done_ctas = 0u;
       ctl->iter = it + 1;
       ctl->supersteps_run += 1;
       const bool nonempty = (cn >> 32) != 0 || ns != 0;
-      const uint32_t left = ctl->budget_left > 0 ? ctl->budget_left - 1 : 0;
+      const uint32_t left = budget > 0 ? budget - 1 : 0;
       ctl->budget_left = left;
       ctl->running = nonempty ? 1u : 0u;
       if (use_cond) cudaGraphSetConditional(cond, (nonempty && left > 0) ? 1u : 0u);
