@@ -78,6 +78,7 @@ def peaks():
 
 L2_FLUSH_BYTES = 512 << 20   # > the B300's 126 MB L2
 GRAPH_LOOP_UNROLL = 8        # superstep kernels per iteration of the library's CUDA-graph loop
+NOMINAL_HBM_GBS = 8000.0     # the nominal HBM3e figure the 35 % target was also stated against (context only)
 
 
 def kernel_source_hash() -> str:
@@ -259,6 +260,7 @@ def run_batched(gg, torch, k=64, seed=1, scale=22, policy="graph"):
                 "ms": hub_t, "ms_min": min(hub_ms), "GTEPS": hub_mtrav / (hub_t * 1e-3) / 1e9, "m_trav": hub_mtrav,
                 "algorithmic_bytes": hub_bytes,
                 "roofline_frac": hub_bytes / (hub_t * 1e-3) / 1e9 / hbm, "peak_GBs": hbm, "peak_kind": peak_kind,
+                "roofline_frac_nominal_8tbs": hub_bytes / (hub_t * 1e-3) / 1e9 / NOMINAL_HBM_GBS,
                 "l2": "flushed before every timed run"}
     d = out.view(n, k)[:, 0].cpu().numpy()
     m_trav = int(np.diff(ro.astype(np.int64))[d != gg.GG_INF].sum())
@@ -538,7 +540,8 @@ def main():
                                     "k_bsp_persistent (all supersteps)" if policy == gg.GG_POLICY_BSP_PERSISTENT else
                                     "k_superstep (all supersteps of one SSSP)"),
                          "algorithmic_bytes": b_super, "kernel_ms": super_ms, "fixed_ms": t_fixed_ms,
-                         "whole_step_frac": b_all / (ms * 1e-3) / 1e9 / hbm},
+                         "whole_step_frac": b_all / (ms * 1e-3) / 1e9 / hbm,
+                         "frac_nominal_8tbs": achieved / NOMINAL_HBM_GBS},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "batched": batched,
