@@ -18,7 +18,8 @@
 //            returns both its queue position and its edge-prefix base, so the
 //            next frontier comes out already carrying its merge-path
 //            coordinates (no separate scan pass);
-//   loop     the last CTA to finish updates the counters, picks the next
+//   loop     the last CTA to arrive (one acquire-release atomic per CTA)
+//            reads the counters in one batch of loads, picks the next
 //            superstep's kind (push, pull, near-far split, heavy push or
 //            pull), and sets the CUDA-graph conditional (work left), so the
 //            whole loop runs on the device; the graph's loop body holds eight
@@ -28,8 +29,10 @@
 // light edges of a light-first copy of the edges, and each vertex that settles
 // into the current bucket has its heavy edges relaxed once, by a heavy
 // superstep that pushes from the settled vertices or pulls into the unsettled
-// ones.  Every relaxation is the same atomicMin with the strict < test, so the
-// distances are those of the plain loop.
+// ones; once the unsettled vertices hold few heavy edges the buckets end and
+// the rest of the run is the plain push loop.  Every relaxation is the same
+// atomicMin with the strict < test, so the distances are those of the plain
+// loop.
 #include <cuda_runtime.h>
 
 #include <algorithm>
