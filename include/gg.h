@@ -147,8 +147,8 @@ typedef struct {
                                   and fills it                                          */
     uint32_t* trace;           /* device u32[trace_cap*4] or NULL.  BSP: per superstep
                                   (frontier size, frontier edges, kind 0 push / 1 pull
-                                  / 2 near-far split / 3 heavy-edge superstep, next
-                                  frontier size).  ASYNC: per
+                                  / 2 near-far split / 3 heavy-edge push / 4 heavy-edge
+                                  pull, next frontier size).  ASYNC: per
                                   near-far split (split number, new threshold, far-pile
                                   size, microseconds since the kernel started)         */
     uint32_t trace_cap;
@@ -161,7 +161,12 @@ typedef struct {
                                   relax heavy edges (weight >= delta) once per settled
                                   vertex (Meyer-Sanders delta-stepping): near supersteps
                                   relax only light edges, and a heavy superstep runs
-                                  when the near frontier empties.  Push direction,
+                                  when the near frontier empties (on symmetric graphs,
+                                  by pull into the unsettled vertices when that scans
+                                  fewer edges).  Once the unsettled vertices hold fewer
+                                  than m/8 heavy edges the threshold becomes infinite
+                                  and the rest of the run is plain push supersteps
+                                  over all edges.  Push direction,
                                   integer weights, and delta <= the largest weight.  The
                                   first such run builds a copy of the edges with each
                                   row's light edges first (4 or 8 bytes per edge, kept
