@@ -1,0 +1,202 @@
+"""CPU model of the single-source light/heavy superstep schedule, checked
+against the oracle.
+
+The GPU loop orders the paper's relaxations (Listing 4) with Meyer-Sanders
+buckets:
+- light supersteps relax the light edges (weight < delta) of the near frontier;
+- each vertex that settles into a bucket joins an R list once per epoch;
+- a heavy superstep relaxes R's heavy edges, by push, or on symmetric graphs by
+  pull into the unsettled vertices;
+- a split raises the threshold past the smallest parked distance;
+- once the unsettled vertices hold fewer than m / 8 heavy edges, the threshold
+  becomes infinite, and the rest of the run is plain push over all edges.
+
+This model takes the same decisions superstep by superstep (synchronous
+relaxation within a superstep, which reaches the same fixed point as the
+kernel's atomics). It checks that the schedule itself, including the switch
+to plain push, yields the shortest distances on graphs of every shape. It
+also checks that the switch removes supersteps without changing any
+distance. No GPU is involved.
+"""
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+BIG = np.int64(1) << 40
+INF32 = 0xFFFFFFFF
+LIGHT, SPLIT, HEAVY_PUSH, HEAVY_PULL = 0, 2, 3, 4
+
+
+def schedule(ro, col, w, src, delta, symmetric, drain_div=8, tail=True):
+    """Distances (uint32, INF32 = unreached) and the kind of every superstep."""
+    ro = np.asarray(ro, np.int64)
+    n, m = ro.size - 1, len(col)
+    deg = np.diff(ro)
+    rowid = np.repeat(np.arange(n), deg)
+    w = np.asarray(w, np.int64)
+    order = np.lexsort((w >= delta, rowid))   # light edges first in each row (stable)
+    c2 = np.asarray(col, np.int64)[order]
+    w2 = w[order]
+    nl = np.bincount(rowid, weights=(w < delta), minlength=n).astype(np.int64)
+    lend = ro[:-1] + nl
+    ldeg, hdeg = nl, deg - nl
+    heavy_total = int(hdeg.sum())
+
+    dist = np.full(n, BIG)
+    dist[src] = 0
+    t_cur, t_prev = np.int64(delta), np.int64(0)
+    far = np.zeros(n, bool)
+    R = np.zeros(n, bool)
+    F = np.array([src]) if ldeg[src] > 0 else np.zeros(0, np.int64)
+    R[src] = hdeg[src] > 0
+    heavy_done = 0
+    bucketed = True
+    kinds = []
+
+    def push(us, lo, hi):
+        cnt = hi[us] - lo[us]
+        tot = int(cnt.sum())
+        if tot == 0:
+            return np.zeros(0, np.int64)
+        own = np.repeat(us, cnt)
+        e = np.repeat(lo[us] - np.concatenate(([0], np.cumsum(cnt)[:-1])), cnt) + np.arange(tot)
+        best = np.full(n, BIG)
+        np.minimum.at(best, c2[e], dist[own] + w2[e])
+        imp = np.flatnonzero(best < dist)
+        dist[imp] = best[imp]
+        return imp
+
+    def near_far(imp, r_into):
+        """Improved vertices below the threshold join the light frontier (and
+        the R list); the others are parked in the far pile."""
+        near = imp[dist[imp] < t_cur]
+        far[imp[dist[imp] >= t_cur]] = True
+        if not bucketed:
+            return near[deg[near] > 0]
+        r_into[near[hdeg[near] > 0]] = True
+        return near[ldeg[near] > 0]
+
+    while True:
+        if F.size and bucketed:
+            kinds.append(LIGHT)
+            F = near_far(push(F, ro[:-1], lend), R)
+        elif bucketed and R.any():
+            Rv = np.flatnonzero(R)
+            rE = int(hdeg[Rv].sum())
+            left = max(heavy_total - heavy_done - rE, 0)
+            R_next = np.zeros(n, bool)
+            if symmetric and t_cur < BIG and rE > left + n // 8:
+                kinds.append(HEAVY_PULL)
+                # every unsettled vertex takes the minimum over its heavy edges
+                # from settled vertices (symmetric: in-edges = out-edges)
+                un = np.flatnonzero(dist >= t_cur)
+                cnt = hdeg[un]
+                tot = int(cnt.sum())
+                imp = np.zeros(0, np.int64)
+                if tot:
+                    own = np.repeat(un, cnt)
+                    e = np.repeat(lend[un] - np.concatenate(([0], np.cumsum(cnt)[:-1])), cnt) + np.arange(tot)
+                    du = dist[c2[e]]
+                    ok = du < t_cur
+                    best = np.full(n, BIG)
+                    np.minimum.at(best, own[ok], du[ok] + w2[e][ok])
+                    imp = np.flatnonzero(best < dist)
+                    dist[imp] = best[imp]
+                far[imp] = True   # every improvement is >= t_cur
+                F = np.zeros(0, np.int64)
+            else:
+                kinds.append(HEAVY_PUSH)
+                F = near_far(push(Rv, lend, ro[1:]), R_next)
+            heavy_done += rE
+            R = R_next
+        elif F.size:   # plain push once bucketing has ended
+            kinds.append(LIGHT)
+            F = near_far(push(F, ro[:-1], ro[1:]), R)
+        elif far.any():
+            # reached only with the light frontier and (while bucketed) the R
+            # list empty, so a split that ends bucketing leaves no heavy edges
+            # pending: every vertex's edges after it are relaxed by plain push
+            kinds.append(SPLIT)
+            fv = np.flatnonzero(far)
+            tn = max(t_cur + delta, int(dist[fv].min()) + 1)
+            if bucketed and (heavy_total - min(heavy_done, heavy_total)) * drain_div < m:
+                tn = BIG
+                bucketed = not tail
+            t_prev, t_cur = t_cur, np.int64(tn)
+            moved = fv[dist[fv] < t_cur]
+            far[moved] = False
+            near = moved[dist[moved] >= t_prev]   # below t_prev: expanded already
+            if bucketed:
+                R[near[hdeg[near] > 0]] = True
+                F = near[ldeg[near] > 0]
+            else:
+                F = near[deg[near] > 0]
+        else:
+            break
+    out = np.where(dist >= BIG, INF32, dist).astype(np.uint32)
+    return out, np.array(kinds)
+
+
+def _after_drain(kinds):
+    """Kinds after the last split, when that split ended bucketing (nothing
+    heavy follows it), else None."""
+    s = np.flatnonzero(kinds == SPLIT)
+    if not s.size:
+        return None
+    rest = kinds[s[-1] + 1:]
+    return None if np.isin(rest, (HEAVY_PUSH, HEAVY_PULL)).any() else rest
+
+
+def _sink_graph(seed, n=3000, m=40000, W=90):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    src = rng.integers(0, n * 5 // 6, m)   # the last sixth of the vertices have no out-edges
+    return graphgen.from_edges(n, src, rng.integers(0, n, m), rng.integers(0, W, m))
+
+
+@pytest.mark.parametrize("scale,delta", [(10, 12), (11, 5), (12, 12), (12, 40)])
+def test_rmat_schedule_matches_oracle(scale, delta):
+    ro, col, w = graphgen.rmat(scale, 16, seed=scale, W=255)
+    for s in (graphgen.max_degree_vertex(ro), int(graphgen.sample_sources(ro, 1, seed=7)[0])):
+        got, kinds = schedule(ro, col, w, s, delta, symmetric=True)
+        np.testing.assert_array_equal(got, oracle.dijkstra(ro, col, w, s), err_msg=f"src={s}")
+        assert np.isin(kinds, (HEAVY_PUSH, HEAVY_PULL)).any()
+        rest = _after_drain(kinds)
+        if rest is not None:
+            assert (rest == LIGHT).all()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+@pytest.mark.parametrize("delta", [1, 7, 30])
+def test_directed_sinks_and_zero_weights_schedule_matches_oracle(seed, delta):
+    ro, col, w = _sink_graph(seed)
+    for s in (0, 1111, 2999):
+        got, _ = schedule(ro, col, w, s, delta, symmetric=False)
+        np.testing.assert_array_equal(got, oracle.dijkstra(ro, col, w, s), err_msg=f"seed={seed} src={s}")
+
+
+def test_path_and_grid_schedule_matches_oracle():
+    wts = np.random.Generator(np.random.PCG64(3)).integers(0, 30, 1999)
+    ro, col, w = graphgen.path_graph(2000, wts)
+    for delta in (1, 9, 29):
+        got, _ = schedule(ro, col, w, 0, delta, symmetric=False)
+        np.testing.assert_array_equal(got, oracle.dijkstra(ro, col, w, 0))
+    ro, col, w = graphgen.grid(48, 64, 5)
+    for delta in (3, 40, 64):
+        got, _ = schedule(ro, col, w, 0, delta, symmetric=True)
+        np.testing.assert_array_equal(got, oracle.dijkstra(ro, col, w, 0))
+
+
+def test_plain_tail_removes_supersteps_not_distances():
+    # after the drain the remaining distances form one unbounded bucket: the
+    # light/heavy alternation there relaxes the same edges in more supersteps
+    ro, col, w = graphgen.rmat(12, 16, seed=1, W=255)
+    hub = graphgen.max_degree_vertex(ro)
+    got_t, kinds_t = schedule(ro, col, w, hub, 12, symmetric=True, tail=True)
+    got_b, kinds_b = schedule(ro, col, w, hub, 12, symmetric=True, tail=False)
+    np.testing.assert_array_equal(got_t, got_b)
+    np.testing.assert_array_equal(got_t, oracle.dijkstra(ro, col, w, hub))
+    assert _after_drain(kinds_t) is not None   # bucketing ended in this run
+    assert HEAVY_PULL in kinds_t               # the first bucket's heavy superstep pulled
+    assert len(kinds_t) < len(kinds_b)
