@@ -29,17 +29,19 @@ INF32 = 0xFFFFFFFF
 LIGHT, SPLIT, HEAVY_PUSH, HEAVY_PULL = 0, 2, 3, 4
 
 
-def schedule(ro, col, w, src, delta, symmetric, drain_div=8, tail=True):
-    """Distances (uint32, INF32 = unreached) and the kind of every superstep."""
+def schedule(ro, col, w, src, delta, symmetric, drain_div=8, tail=True, lh=True):
+    """Distances (uint32, INF32 = unreached) and the kind of every superstep.
+    lh=False is the plain near-far loop (every edge light, no drain rule)."""
     ro = np.asarray(ro, np.int64)
     n, m = ro.size - 1, len(col)
     deg = np.diff(ro)
     rowid = np.repeat(np.arange(n), deg)
     w = np.asarray(w, np.int64)
-    order = np.lexsort((w >= delta, rowid))   # light edges first in each row (stable)
+    is_light = (w < delta) if lh else np.ones(w.size, bool)
+    order = np.lexsort((~is_light, rowid))   # light edges first in each row (stable)
     c2 = np.asarray(col, np.int64)[order]
     w2 = w[order]
-    nl = np.bincount(rowid, weights=(w < delta), minlength=n).astype(np.int64)
+    nl = np.bincount(rowid, weights=is_light, minlength=n).astype(np.int64)
     lend = ro[:-1] + nl
     ldeg, hdeg = nl, deg - nl
     heavy_total = int(hdeg.sum())
@@ -121,7 +123,7 @@ def schedule(ro, col, w, src, delta, symmetric, drain_div=8, tail=True):
             kinds.append(SPLIT)
             fv = np.flatnonzero(far)
             tn = max(t_cur + delta, int(dist[fv].min()) + 1)
-            if bucketed and (heavy_total - min(heavy_done, heavy_total)) * drain_div < m:
+            if lh and bucketed and (heavy_total - min(heavy_done, heavy_total)) * drain_div < m:
                 tn = BIG
                 bucketed = not tail
             t_prev, t_cur = t_cur, np.int64(tn)
@@ -200,3 +202,26 @@ def test_plain_tail_removes_supersteps_not_distances():
     assert _after_drain(kinds_t) is not None   # bucketing ended in this run
     assert HEAVY_PULL in kinds_t               # the first bucket's heavy superstep pulled
     assert len(kinds_t) < len(kinds_b)
+
+
+@pytest.mark.parametrize("graph", ["grid", "path", "sinks", "rmat"])
+def test_plain_near_far_schedule_matches_oracle(graph):
+    # without the light/heavy split every edge is light: near supersteps relax
+    # all edges below the threshold, the rest wait in the far pile for a split
+    if graph == "grid":
+        ro, col, w = graphgen.grid(48, 64, 5)
+        cases, sym = [(0, 16 * 64), (0, 50), (1175, 7)], True
+    elif graph == "path":
+        ro, col, w = graphgen.path_graph(1500, np.random.Generator(np.random.PCG64(9)).integers(0, 40, 1499))
+        cases, sym = [(0, 1), (0, 100)], False
+    elif graph == "sinks":
+        ro, col, w = _sink_graph(5)
+        cases, sym = [(0, 4), (777, 60)], False
+    else:
+        ro, col, w = graphgen.rmat(11, 16, seed=2, W=255)
+        cases, sym = [(graphgen.max_degree_vertex(ro), 30)], True
+    for s, delta in cases:
+        got, kinds = schedule(ro, col, w, s, delta, symmetric=sym, lh=False)
+        np.testing.assert_array_equal(got, oracle.dijkstra(ro, col, w, s), err_msg=f"{graph} src={s} delta={delta}")
+        assert not np.isin(kinds, (HEAVY_PUSH, HEAVY_PULL)).any()
+    assert SPLIT in kinds   # the far pile was used
