@@ -185,6 +185,37 @@ def cpu_baseline(ro, col, w, src, seconds):
                       f"(median {t * 1e3:.1f} ms each, 1 host thread)"}
 
 
+def cpu_baseline_batch(ro, col, w, srcs):
+    """The oracle's multi-source Dijkstra (one source per host thread) on a
+    bounded sample of the batch's sources: as many sources as host threads, at
+    most all of them, timed as one wall-clock run."""
+    import oracle
+    t = max(1, min(len(srcs), os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    oracle.dijkstra_many(ro, col, w, np.asarray(srcs[:t], np.uint32), threads=t)
+    dt = time.perf_counter() - t0
+    return {"queries_per_s": t / dt, "cores": t, "kind": "oracle",
+            "sample": f"the first {t} of the {len(srcs)} sources, one binary-heap Dijkstra per host thread "
+                      f"({dt:.2f} s wall)"}
+
+
+def cpu_baseline_queries(queries, total):
+    """The oracle's Dijkstra over a bounded sample of served queries (graph
+    CSR, source), one query per host thread at a time (the ctypes call
+    releases the GIL): twice as many queries as host threads, at most all."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    t = max(1, os.cpu_count() or 1)
+    sample = queries[:2 * t]
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(t) as ex:
+        list(ex.map(lambda q: oracle.dijkstra(*q), sample))
+    dt = time.perf_counter() - t0
+    return {"queries_per_s": len(sample) / dt, "cores": min(t, len(sample)), "kind": "oracle",
+            "sample": f"the first {len(sample)} of the {total} queries, binary-heap Dijkstra on {t} host threads "
+                      f"({dt:.2f} s wall)"}
+
+
 def shard(items, rank, world):
     """This rank's share of a work list: items rank, rank + world, ...
     (disjoint across ranks, together complete)."""
@@ -203,7 +234,7 @@ def reduce_over_ranks(value, op, pg):
     return float(t.item())
 
 
-def run_batched(gg, torch, k=64, seed=1, scale=22, policy="graph"):
+def run_batched(gg, torch, k=64, seed=1, scale=22, policy="graph", cpu_sample=True):
     """Batched multi-source SSSP on RMAT-22 (64 seeded sources, one fused
     launch sequence) vs the same 64 sources as back-to-back gg_sssp calls.
     scale / policy other than 22 / graph serve profiling (ncu cannot see the
@@ -266,16 +297,17 @@ def run_batched(gg, torch, k=64, seed=1, scale=22, policy="graph"):
     m_trav = int(np.diff(ro.astype(np.int64))[d != gg.GG_INF].sum())
     g.close()
     t = statistics.median(tb)
+    cpu = cpu_baseline_batch(ro, col, w, srcs) if cpu_sample else None
     return {"workload": f"RMAT scale {scale} EF16, {k} seeded sources (splitmix64 seed 1), "
                         f"dist matrix {n} x {k} u32",
             "policy": policy,
             "queries_per_s": k / t * 1e3, "ms": t, "back_to_back_queries_per_s": k / t1 * 1e3,
             "back_to_back_ms": t1, "speedup": t1 / t, "supersteps": st.iterations,
             "edges_scanned": st.edges_scanned, "gteps_aggregate_est": k * m_trav / (t * 1e-3) / 1e9,
-            "single_source_hub": hub_line}
+            "single_source_hub": hub_line, "cpu_baseline": cpu}
 
 
-def run_serving(gg, torch, nq=2000, seed=1):
+def run_serving(gg, torch, nq=2000, seed=1, cpu_sample=True):
     """Poisson stream of (graph, source) queries over the 32-graph pool into
     the continuous-batching server, at saturation (all queued at t=0) and at
     50 % / 90 % of the saturation rate; vs the same queries back to back."""
@@ -320,10 +352,12 @@ def run_serving(gg, torch, nq=2000, seed=1):
     b2b = nq / (time.perf_counter() - t0)
     for gr in graphs:
         gr.close()
+    cpu = (cpu_baseline_queries([(*pool[gids[i]], int(srcs[i])) for i in range(nq)], nq)
+           if cpu_sample else None)
     return {"workload": "32-graph pool (RMAT scales 12-20 EF 8/16, grids 64^2-2048^2, U[1,255]), "
                         f"{nq} queries, graph uniform, source uniform over degree>=1, Poisson seed 1",
             "saturation": sat, "load": loads, "back_to_back_queries_per_s": b2b,
-            "speedup": sat["queries_per_s"] / b2b}
+            "speedup": sat["queries_per_s"] / b2b, "cpu_baseline": cpu}
 
 
 def workload_desc(name):
@@ -508,11 +542,13 @@ def main():
     # batched and served queries shard naturally: every rank runs its own
     # seeded stream (per-GPU work fixed) and the queries/s add up
     batched = serving = None
+    cpu_sample = rank == 0 and world == 1 and not args.no_cpu_baseline   # oracle baselines: rank 0 at N=1
     if not args.no_batch:
-        batched = run_batched(gg, torch, seed=1 + rank, scale=args.batch_scale, policy=args.batch_policy)
+        batched = run_batched(gg, torch, seed=1 + rank, scale=args.batch_scale, policy=args.batch_policy,
+                              cpu_sample=cpu_sample)
         batched["queries_per_s_all_ranks"] = reduce_over_ranks(batched["queries_per_s"], "sum", pg)
     if not args.no_serve:
-        serving = run_serving(gg, torch, args.serve_queries, seed=1 + rank)
+        serving = run_serving(gg, torch, args.serve_queries, seed=1 + rank, cpu_sample=cpu_sample)
         serving["queries_per_s_all_ranks"] = reduce_over_ranks(serving["saturation"]["queries_per_s"], "sum", pg)
 
     cpu = None
