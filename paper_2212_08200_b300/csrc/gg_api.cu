@@ -8,6 +8,7 @@
 #include <string>
 
 #include "gg_host.h"
+#include "gg_nvtx.h"
 
 namespace gg {
 
@@ -138,6 +139,7 @@ void gg_options_default(gg_options* o) {
 
 gg_status gg_graph_create_csr(uint32_t n, uint64_t m, const uint32_t* row_offsets, const uint32_t* col_indices,
                               const uint32_t* weights, uint32_t flags, cudaStream_t stream, gg_graph_t* out) {
+  NvtxRange nvtx_range("gg_graph_create_csr");
   if (!out) return fail(GG_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (n == 0 || n >= 0xFFFFFFFFu) return fail(GG_ERR_INVALID_ARG, "n must be in [1, 2^32 - 2]");
@@ -169,6 +171,7 @@ gg_status gg_graph_create_csr(uint32_t n, uint64_t m, const uint32_t* row_offset
 }
 
 gg_status gg_graph_destroy(gg_graph_t g) {
+  NvtxRange nvtx_range("gg_graph_destroy");
   if (!g) return fail(GG_ERR_INVALID_ARG, "graph is NULL");
   {
     std::lock_guard<std::mutex> lk(g->mu);
@@ -276,6 +279,7 @@ gg_status run_single(gg_graph_t g, uint32_t src, uint32_t* dist_out, const gg_op
 }  // namespace
 
 gg_status gg_sssp_ex(gg_graph_t g, uint32_t src, uint32_t* dist_out, const gg_options* opt, cudaStream_t stream) {
+  NvtxRange nvtx_range("gg_sssp");
   return run_single(g, src, dist_out, opt, stream, g && g->float_weights ? WM_F32 : WM_U32);
 }
 
@@ -284,6 +288,7 @@ gg_status gg_sssp(gg_graph_t g, uint32_t src, uint32_t* dist_out, cudaStream_t s
 }
 
 gg_status gg_bfs_ex(gg_graph_t g, uint32_t src, uint32_t* depth_out, const gg_options* opt, cudaStream_t stream) {
+  NvtxRange nvtx_range("gg_bfs");
   return run_single(g, src, depth_out, opt, stream, WM_UNIT);
 }
 
@@ -293,6 +298,7 @@ gg_status gg_bfs(gg_graph_t g, uint32_t src, uint32_t* depth_out, cudaStream_t s
 
 gg_status gg_sssp_batch_ex(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t* dist_out,
                            const gg_options* opt, cudaStream_t stream) {
+  NvtxRange nvtx_range("gg_sssp_batch");
   if (!g) return fail(GG_ERR_INVALID_ARG, "graph is NULL");
   if (!srcs || !dist_out) return fail(GG_ERR_INVALID_ARG, "srcs/dist_out is NULL");
   if (k == 0) return fail(GG_ERR_INVALID_ARG, "k must be >= 1");

@@ -37,6 +37,7 @@
 #include <mutex>
 
 #include "gg_host.h"
+#include "gg_nvtx.h"
 
 namespace gg {
 namespace {
@@ -307,6 +308,7 @@ using namespace gg;
 extern "C" gg_status gg_sssp_noalloc(uint32_t n, uint64_t m, const uint32_t* row_offsets,
                                      const uint32_t* col_indices, const uint32_t* weights, uint32_t src,
                                      uint32_t* dist_out, cudaStream_t stream) {
+  NvtxRange nvtx_range("gg_sssp_noalloc");
   if (n == 0) return fail(GG_ERR_INVALID_ARG, "n must be >= 1");
   if (n > kNaMaxN)
     return fail(GG_ERR_INVALID_ARG, "gg_sssp_noalloc: n exceeds GG_NOALLOC_MAX_VERTICES (1048576); "

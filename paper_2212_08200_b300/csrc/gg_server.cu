@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "gg_host.h"
+#include "gg_nvtx.h"
 #include "gg_multi.h"
 
 using namespace gg;
@@ -69,6 +70,7 @@ MultiCache g_multi[16];
 
 extern "C" gg_status gg_sssp_multi_ex(const gg_graph_t* graphs, const uint32_t* srcs, uint32_t count,
                                       uint32_t* const* dist_outs, uint32_t delta, cudaStream_t stream) {
+  NvtxRange nvtx_range("gg_sssp_multi");
   if (!graphs || !srcs || !dist_outs) return fail(GG_ERR_INVALID_ARG, "graphs/srcs/dist_outs is NULL");
   if (count == 0) return fail(GG_ERR_INVALID_ARG, "count must be >= 1");
   int dev = 0;
@@ -329,6 +331,7 @@ gg_status gg_server_create(const gg_server_config* cfg, gg_server_t* out) {
 }
 
 gg_status gg_server_submit(gg_server_t s, gg_graph_t g, uint32_t src, uint32_t* dist_out, uint64_t* ticket) {
+  NvtxRange nvtx_range("gg_server_submit");
   if (!s || !g || !dist_out || !ticket) return fail(GG_ERR_INVALID_ARG, "NULL argument");
   if (src >= g->n) return fail(GG_ERR_INVALID_ARG, "src >= n");
   if (g->float_weights)

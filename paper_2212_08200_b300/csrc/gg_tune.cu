@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "gg_host.h"
+#include "gg_nvtx.h"
 
 using namespace gg;
 
@@ -49,6 +50,7 @@ gg_status time_options(gg_graph* g, const uint32_t* srcs, uint32_t nsrc, uint32_
 
 extern "C" gg_status gg_autotune(gg_graph_t g, const uint32_t* srcs, uint32_t nsrc, uint32_t* dist_scratch,
                                  gg_options* best, float* best_ms, cudaStream_t stream) {
+  NvtxRange nvtx_range("gg_autotune");
   if (!g || !srcs || !dist_scratch || !best) return fail(GG_ERR_INVALID_ARG, "NULL argument");
   if (nsrc == 0) return fail(GG_ERR_INVALID_ARG, "nsrc must be >= 1");
   for (uint32_t i = 0; i < nsrc; ++i)
