@@ -1,14 +1,27 @@
 #!/usr/bin/env python3
 """Benchmark of the frontier SSSP hot path on one or more B300 GPUs.
 
-Default workload: single-source SSSP on the RMAT scale-20 graph (edge factor
-16, a,b,c,d = .57,.19,.19,.05, symmetrised, deduplicated, no self-loops,
-uint32 weights U[1,255] from seed 1), source = highest-degree vertex,
-bulk-synchronous CUDA-graph loop with push/pull switching.
+Default workload (the headline): single-source SSSP on the RMAT scale-22
+graph (edge factor 16, a,b,c,d = .57,.19,.19,.05, symmetrised,
+deduplicated, no self-loops, uint32 weights U[1,255] from seed 1), source =
+highest-degree vertex, bulk-synchronous CUDA-graph loop with the library's
+defaults (light/heavy buckets, warp-streaming push).
 
 One step = one gg_sssp call (distance init through convergence) with the
 graph resident in HBM.  value = GTEPS = m_trav / step time, m_trav = sum of
 out-degrees of the reached vertices (each edge of the reached component once).
+
+Every timed result is checked before a line is printed: the distance vector
+(and the batched matrix, and every served query's vector) must hash to the
+value tests/golden/workloads.json stores for it, which tests/golden/
+make_golden.py wrote from the CPU oracle.  A mismatch prints no line and
+exits 1.
+
+Sub-objects of the line: rmat20 (single source on RMAT scale 20), grid4096
+(the 4096^2 high-diameter grid under the CUDA-graph loop, the persistent
+cooperative kernel and the asynchronous work queue), batched (64 seeded
+sources on RMAT-22 in one fused loop vs back-to-back gg_sssp) and serving
+(the 2,000-query Poisson stream over the 32-graph pool).
 
 Multi-GPU (torchrun): single-source SSSP does not shard, so every rank runs
 an independent replica of the same workload ("replicas only"); value = edges
@@ -16,7 +29,7 @@ traversed by all ranks / max-over-ranks time.  No collective touches the data
 path; ranks only meet at the timing barriers.
 
 --impl reference: the CPU oracle (binary-heap Dijkstra) on the same workload,
-a bounded sample on the host cores, printed on the same JSON schema.
+on the host cores, printed on the same JSON schema.
 """
 from __future__ import annotations
 
@@ -44,7 +57,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gg", choices=["gg", "reference"])
-    p.add_argument("--workload", default="rmat20")
+    p.add_argument("--workload", default="rmat22")
     p.add_argument("--policy", default="graph", choices=["graph", "async", "host", "persistent"])
     p.add_argument("--direction", default="push", choices=["auto", "push", "pull"])
     p.add_argument("--lb", default="auto", choices=["auto", "mp", "bins", "warp"])
@@ -60,6 +73,10 @@ def parse():
     p.add_argument("--no-batch", action="store_true", help="skip the batched 64-source RMAT-22 measurement")
     p.add_argument("--no-serve", action="store_true", help="skip the 32-graph serving measurement")
     p.add_argument("--serve-queries", type=int, default=2000)
+    p.add_argument("--no-rmat20", action="store_true", help="skip the RMAT-20 single-source sub-line")
+    p.add_argument("--no-grid", action="store_true", help="skip the 4096^2 grid policy comparison")
+    p.add_argument("--ref-seconds", type=float, default=240.0,
+                   help="--impl reference: stop adding steps once this much host time is spent")
     return p.parse_args()
 
 
@@ -234,14 +251,122 @@ def reduce_over_ranks(value, op, pg):
     return float(t.item())
 
 
-def run_batched(gg, torch, k=64, seed=1, scale=22, policy="graph", cpu_sample=True):
+def golden():
+    """The stored oracle results (tests/golden/workloads.json, written by
+    tests/golden/make_golden.py from the CPU oracle); {} when absent."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "workloads.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def sha256_u32(a) -> str:
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(a, np.uint32).tobytes()).hexdigest()
+
+
+class NotVerified(RuntimeError):
+    """A timed result differs from the stored oracle result: no line is printed."""
+
+
+def verify_single(name: str, dist_host) -> bool | None:
+    """True when the distances hash to the stored oracle hash of workload
+    `name`, None when no hash is stored for it; raises NotVerified on a
+    mismatch."""
+    rec = golden().get(name)
+    if not rec or "dist_sha256" not in rec:
+        return None
+    if sha256_u32(dist_host) != rec["dist_sha256"]:
+        raise NotVerified(f"{name}: the distances differ from the oracle's (stored sha256 {rec['dist_sha256'][:16]})")
+    return True
+
+
+def time_sssp(gg, torch, g, src, opts, stream, steps, warmup, flush):
+    """Per-step milliseconds of gg_sssp_ex(src) with the L2 flushed (flush
+    buffer written outside the events) before every timed step."""
+    dist_t = torch.empty(g.n, dtype=torch.uint32, device="cuda")
+    for _ in range(max(warmup, 1)):
+        gg.gg_sssp_ex(g.handle, src, dist_t, opts, stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k)
+        ev[k][0].record(stream)
+        gg.gg_sssp_ex(g.handle, src, dist_t, opts, stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    g.check()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def stats_run(gg, torch, g, src, policy, stream, **kw):
+    """One SSSP with statistics; (distances on the host, stats dict)."""
+    st = gg.gg_stats()
+    dist_t = torch.empty(g.n, dtype=torch.uint32, device="cuda")
+    gg.gg_sssp_ex(g.handle, src, dist_t, gg.make_options(policy=policy, stats=st, **kw), stream)
+    torch.cuda.synchronize()
+    g.check()
+    return dist_t.cpu().numpy(), st.as_dict()
+
+
+def run_rmat20(gg, torch, stream, flush, steps=10):
+    """Single source on RMAT scale 20 from the hub with the library defaults
+    (the smaller RMAT workload), verified against the stored oracle hash."""
+    import graphgen
+    ro, col, w, src = graphgen.workload("rmat20")
+    g = gg.Graph(ro, col, w, symmetric=True, stream=stream)
+    d, st = stats_run(gg, torch, g, src, gg.GG_POLICY_BSP_GRAPH, stream, direction=gg.GG_DIR_PUSH)
+    ok = verify_single("rmat20", d)
+    reach = d != gg.GG_INF
+    n, m_trav, n_reach = g.n, int(np.diff(ro.astype(np.int64))[reach].sum()), int(reach.sum())
+    per = time_sssp(gg, torch, g, src, gg.make_options(direction=gg.GG_DIR_PUSH), stream, steps, 3, flush)
+    g.close()
+    t = statistics.median(per)
+    hbm, peak_kind = peaks()
+    b_all, _ = algorithmic_bytes(n, m_trav, n_reach)
+    return {"workload": workload_desc("rmat20"), "source": int(src), "ms": t, "ms_min": min(per),
+            "GTEPS": m_trav / (t * 1e-3) / 1e9, "m_trav": m_trav, "n_reach": n_reach, "algorithmic_bytes": b_all,
+            "roofline_frac": b_all / (t * 1e-3) / 1e9 / hbm, "peak_GBs": hbm, "peak_kind": peak_kind,
+            "supersteps": st["iterations"], "edges_scanned": st["edges_scanned"], "verified": ok,
+            "l2": "flushed before every timed run", "runs": len(per)}
+
+
+def run_grid4096(gg, torch, stream, flush, steps=3):
+    """The 4096^2 grid (16.7 M vertices, 67 M edges, weights U[1,1000]) from
+    the corner under the paper's two timing models: bulk-synchronous
+    supersteps (CUDA-graph loop, and the persistent cooperative kernel) and
+    the asynchronous persistent kernel over a device work queue; each
+    verified against the stored oracle hash."""
+    import graphgen
+    ro, col, w, src = graphgen.workload("grid4096")
+    g = gg.Graph(ro, col, w, symmetric=True, stream=stream)
+    m_trav = int(col.shape[0])
+    out = {"workload": workload_desc("grid4096"), "source": int(src), "n": g.n, "m": g.m, "m_trav": m_trav}
+    for name, pol in (("bsp_cuda_graph", gg.GG_POLICY_BSP_GRAPH), ("bsp_persistent", gg.GG_POLICY_BSP_PERSISTENT),
+                      ("async_queue", gg.GG_POLICY_ASYNC_PERSISTENT)):
+        d, st = stats_run(gg, torch, g, src, pol, stream, direction=gg.GG_DIR_PUSH)
+        ok = verify_single("grid4096", d)
+        per = time_sssp(gg, torch, g, src, gg.make_options(policy=pol, direction=gg.GG_DIR_PUSH), stream, steps, 1,
+                        flush)
+        t = statistics.median(per)
+        out[name] = {"ms": t, "ms_min": min(per), "GTEPS": m_trav / (t * 1e-3) / 1e9,
+                     "supersteps": st["iterations"], "edges_scanned": st["edges_scanned"],
+                     "edges_scanned_per_m_trav": st["edges_scanned"] / m_trav, "verified": ok, "runs": len(per)}
+    g.close()
+    out["async_vs_bsp"] = out["async_queue"]["ms"] / out["bsp_cuda_graph"]["ms"]
+    return out
+
+
+def run_batched(gg, torch, k=64, seed=1, scale=22, policy="graph", cpu_sample=True, graph=None):
     """Batched multi-source SSSP on RMAT-22 (64 seeded sources, one fused
     launch sequence) vs the same 64 sources as back-to-back gg_sssp calls.
+    The whole distance matrix is checked against the stored oracle hash.
     scale / policy other than 22 / graph serve profiling (ncu cannot see the
     kernels inside the CUDA-graph loop; "host" launches them one by one)."""
     import graphgen
     pol = {"graph": gg.GG_POLICY_BSP_GRAPH, "host": gg.GG_POLICY_BSP_HOST}[policy]
-    ro, col, w = graphgen.rmat(scale, 16, seed=1, W=255)
+    ro, col, w = graph if graph is not None else graphgen.rmat(scale, 16, seed=1, W=255)
     srcs = graphgen.sample_sources(ro, k, seed=seed)
     g = gg.Graph(ro, col, w, symmetric=True)
     n = g.n
@@ -250,6 +375,19 @@ def run_batched(gg, torch, k=64, seed=1, scale=22, policy="graph", cpu_sample=Tr
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     st = gg.gg_stats()
     g.sssp_batch(srcs, out, stats=st, policy=pol)
+    g.check()
+    rec = golden().get(f"rmat{scale}_batch{k}")
+    verified = None
+    if rec and seed == 1 and [int(x) for x in srcs] == rec["sources"]:
+        host = out.cpu().numpy()
+        if sha256_u32(host) != rec["matrix_sha256"]:
+            bad = [s for s in range(k) if sha256_u32(host.reshape(n, k)[:, s]) != rec["column_sha256"][s]]
+            raise NotVerified(f"batched RMAT-{scale} x {k}: columns {bad[:8]} differ from the oracle's")
+        verified = True
+        m_trav_all = int(sum(rec["m_trav"]))
+        del host
+    else:
+        m_trav_all = None
     tb = []
     for _ in range(3):
         e0.record()
@@ -266,51 +404,26 @@ def run_batched(gg, torch, k=64, seed=1, scale=22, policy="graph", cpu_sample=Tr
     e1.record()
     torch.cuda.synchronize()
     t1 = e0.elapsed_time(e1)
-    # single source from the highest-degree vertex on the same graph (the
-    # RMAT-22 single-source roofline target): L2 flushed before each timed run
-    hub = int(graphgen.max_degree_vertex(ro))
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
-    for _ in range(3):
-        g.sssp(hub, single)
-    hub_ms = []
-    for r in range(10):
-        flush.fill_(r)
-        e0.record()
-        g.sssp(hub, single)
-        e1.record()
-        torch.cuda.synchronize()
-        hub_ms.append(e0.elapsed_time(e1))
-    del flush
-    dh = single.cpu().numpy()
-    reach = dh != gg.GG_INF
-    hub_mtrav = int(np.diff(ro.astype(np.int64))[reach].sum())
-    hub_t = statistics.median(hub_ms)
-    hub_bytes, _ = algorithmic_bytes(n, hub_mtrav, int(reach.sum()))
-    hbm, peak_kind = peaks()
-    hub_line = {"workload": f"RMAT scale {scale} EF16, source = highest-degree vertex {hub}, gg_sssp defaults",
-                "ms": hub_t, "ms_min": min(hub_ms), "GTEPS": hub_mtrav / (hub_t * 1e-3) / 1e9, "m_trav": hub_mtrav,
-                "algorithmic_bytes": hub_bytes,
-                "roofline_frac": hub_bytes / (hub_t * 1e-3) / 1e9 / hbm, "peak_GBs": hbm, "peak_kind": peak_kind,
-                "roofline_frac_nominal_8tbs": hub_bytes / (hub_t * 1e-3) / 1e9 / NOMINAL_HBM_GBS,
-                "l2": "flushed before every timed run"}
-    d = out.view(n, k)[:, 0].cpu().numpy()
-    m_trav = int(np.diff(ro.astype(np.int64))[d != gg.GG_INF].sum())
+    g.check()
     g.close()
     t = statistics.median(tb)
     cpu = cpu_baseline_batch(ro, col, w, srcs) if cpu_sample else None
-    return {"workload": f"RMAT scale {scale} EF16, {k} seeded sources (splitmix64 seed 1), "
+    return {"workload": f"RMAT scale {scale} EF16, {k} seeded sources (splitmix64 seed {seed}), "
                         f"dist matrix {n} x {k} u32",
             "policy": policy,
-            "queries_per_s": k / t * 1e3, "ms": t, "back_to_back_queries_per_s": k / t1 * 1e3,
+            "queries_per_s": k / t * 1e3, "ms": t, "ms_all": tb, "back_to_back_queries_per_s": k / t1 * 1e3,
             "back_to_back_ms": t1, "speedup": t1 / t, "supersteps": st.iterations,
-            "edges_scanned": st.edges_scanned, "gteps_aggregate_est": k * m_trav / (t * 1e-3) / 1e9,
-            "single_source_hub": hub_line, "cpu_baseline": cpu}
+            "edges_scanned": st.edges_scanned,
+            "gteps_aggregate": (m_trav_all / (t * 1e-3) / 1e9) if m_trav_all else None,
+            "verified": verified, "cpu_baseline": cpu}
 
 
 def run_serving(gg, torch, nq=2000, seed=1, cpu_sample=True):
     """Poisson stream of (graph, source) queries over the 32-graph pool into
     the continuous-batching server, at saturation (all queued at t=0) and at
-    50 % / 90 % of the saturation rate; vs the same queries back to back."""
+    50 % / 90 % of the saturation rate; vs the same queries back to back.
+    Every query's distances are checked against the stored oracle hash after
+    the saturation pass and after the back-to-back pass."""
     import graphgen
     pool = [graphgen.build_pool_graph(e) for e in graphgen.serving_pool_spec()]
     graphs = [gg.Graph(ro, col, w, symmetric=True) for ro, col, w in pool]
@@ -319,9 +432,26 @@ def run_serving(gg, torch, nq=2000, seed=1, cpu_sample=True):
     outs = [torch.empty(graphs[gi].n, dtype=torch.uint32, device="cuda") for gi in gids]
     maxn = max(gr.n for gr in graphs)
     srv = gg.Server(max_graph_vertices=maxn, max_slots=64, supersteps_per_launch=8)
+    rec = golden().get("serving_pool")
+    checkable = (rec is not None and rec["seed"] == seed and rec["queries"] == nq
+                 and rec["graph"] == [int(x) for x in gids] and rec["source"] == [int(x) for x in srcs])
+
+    def verify(what):
+        if not checkable:
+            return None
+        bad = []
+        for i in range(nq):
+            if sha256_u32(outs[i].cpu().numpy())[:16] != rec["dist_sha256_16"][i]:
+                bad.append(i)
+        if bad:
+            raise NotVerified(f"serving ({what}): queries {bad[:8]} ({len(bad)} in all) differ from the oracle's")
+        return True
 
     def stream(rate):
         _, _, arr = graphgen.poisson_queries(degs, nq, seed=seed, rate_qps=rate)
+        for o in outs:
+            o.view(torch.int32).fill_(0x5A5A5A5A)   # a query that writes nothing cannot pass the check
+        torch.cuda.synchronize()
         srv.reset_stats()
         t0 = time.perf_counter()
         ts = []
@@ -339,25 +469,30 @@ def run_serving(gg, torch, nq=2000, seed=1, cpu_sample=True):
 
     stream(None)                       # warm-up pass
     sat = stream(None)
+    verified = verify("saturation")
     loads = {}
     for frac in (0.5, 0.9):
         loads[f"{int(frac * 100)}pct"] = stream(sat["queries_per_s"] * frac)
     srv.close()
     # back to back: the same queries through gg_sssp, one after another on one stream
+    for o in outs:
+        o.view(torch.int32).fill_(0x5A5A5A5A)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(nq):
         graphs[gids[i]].sssp(int(srcs[i]), outs[i])
     torch.cuda.synchronize()
     b2b = nq / (time.perf_counter() - t0)
+    verified_b2b = verify("back to back")
     for gr in graphs:
         gr.close()
     cpu = (cpu_baseline_queries([(*pool[gids[i]], int(srcs[i])) for i in range(nq)], nq)
            if cpu_sample else None)
     return {"workload": "32-graph pool (RMAT scales 12-20 EF 8/16, grids 64^2-2048^2, U[1,255]), "
-                        f"{nq} queries, graph uniform, source uniform over degree>=1, Poisson seed 1",
+                        f"{nq} queries, graph uniform, source uniform over degree>=1, Poisson seed {seed}",
             "saturation": sat, "load": loads, "back_to_back_queries_per_s": b2b,
-            "speedup": sat["queries_per_s"] / b2b, "cpu_baseline": cpu}
+            "speedup": sat["queries_per_s"] / b2b, "verified": verified, "verified_back_to_back": verified_b2b,
+            "cpu_baseline": cpu}
 
 
 def workload_desc(name):
@@ -366,36 +501,42 @@ def workload_desc(name):
 
 
 def run_reference(args):
+    """The CPU oracle (single-thread binary-heap Dijkstra) on the workload:
+    W warm-up and K timed steps, each one full SSSP, cut short (and said so)
+    once --ref-seconds of host time are spent."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import graphgen
     import oracle
     ro, col, w, src = graphgen.workload(args.workload)
-    steps = []
+    budget = max(args.ref_seconds, 1.0)
+    t_begin = time.perf_counter()
+    warm = 0
     for _ in range(args.warmup):
+        if warm and time.perf_counter() - t_begin > budget / 4:
+            break
         oracle.dijkstra(ro, col, w, src)
-    budget = max(args.cpu_seconds, 1.0)
-    t_end = time.perf_counter() + budget
+        warm += 1
+    steps = []
     d = None
-    k = 0
-    while k < args.steps and (time.perf_counter() < t_end or k == 0):
+    while len(steps) < args.steps and (time.perf_counter() - t_begin < budget or not steps):
         t0 = time.perf_counter()
         d = oracle.dijkstra(ro, col, w, src)
         steps.append(time.perf_counter() - t0)
-        k += 1
     m_trav = oracle.traversed_edges(ro, d)
     t = statistics.median(steps)
     val = m_trav / t / 1e9
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GTEPS", "n_gpus": args.gpus,
             "device": "host CPU, 1 thread (the oracle uses no GPU)",
-            "steps": len(steps), "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "steps": len(steps), "warmup": warm, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": workload_desc(args.workload), "n": int(ro.shape[0] - 1), "m": int(col.shape[0]),
                        "source": int(src), "m_trav": m_trav},
             "cpu_baseline": {"value": val, "unit": "GTEPS", "cores": 1, "kind": "oracle",
-                             "sample": f"{len(steps)} of {args.steps} requested steps, each a full single-source "
-                                       f"binary-heap Dijkstra on the host (bounded to ~{budget:.0f} s)"},
+                             "sample": f"{len(steps)} of {args.steps} requested steps after {warm} warm-up runs, "
+                                       f"each a full single-source binary-heap Dijkstra on the host "
+                                       f"(bounded to ~{budget:.0f} s in all)"},
             "e2e": {"value": val, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -405,6 +546,14 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    try:
+        run_gg(args)
+    except NotVerified as e:
+        print(f"bench: result check failed, no line printed: {e}", file=sys.stderr, flush=True)
+        sys.exit(1)
+
+
+def run_gg(args):
     import torch
 
     import graphgen
@@ -434,14 +583,17 @@ def main():
     def step():
         gg.gg_sssp_ex(g.handle, src, dist_t, opts, stream)
 
-    # correctness of what is timed: stats run + invariant-free hash check vs the oracle's stored hash
+    # correctness of what is timed: a stats run whose distances must hash to
+    # the stored oracle hash of this workload (no line is printed otherwise)
     st = gg.gg_stats()
     torch.cuda.nvtx.range_push("gg_sssp_stats_run")   # lets a profiler select exactly one SSSP's launches
     gg.gg_sssp_ex(g.handle, src, dist_t, gg.make_options(policy=policy, direction=direction, lb_mode=lb,
                                                          pull_alpha=args.alpha, pull_beta=args.beta, stats=st,
                                                          delta=delta), stream)
     torch.cuda.nvtx.range_pop()
+    g.check()
     d_host = dist_t.cpu().numpy()
+    verified = verify_single(args.workload, d_host)
     reach = d_host != gg.GG_INF
     m_trav = int(np.diff(ro.astype(np.int64))[reach].sum())
     n_reach = int(reach.sum())
@@ -492,7 +644,10 @@ def main():
     clk = clocks.stop()
     per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = sum(per) / args.steps
-    del flush
+    # the last timed step's distances must be the verified ones too
+    g.check()
+    if verified and sha256_u32(dist_t.cpu().numpy()) != sha256_u32(d_host):
+        raise NotVerified("the last timed step's distances differ from the verified stats run's")
     if pg:
         t = torch.tensor([ms], device="cuda")
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
@@ -533,19 +688,31 @@ def main():
             torch.cuda.synchronize()
             gg.gg_graph_destroy(h)
         e2e_s = (time.perf_counter() - t0) / k2
+        if verified and sha256_u32(out_h.numpy().view(np.uint32)) != sha256_u32(d_host):
+            raise NotVerified("the end-to-end run's distances differ from the oracle's")
         e2e = {"value": world * m_trav / e2e_s / 1e9, "unit": "GTEPS",
                "h2d_bytes_per_step": 4 * (n + 1) + 8 * m, "d2h_bytes_per_step": 4 * n,
                "ms_per_step": e2e_s * 1e3,
                "what": "gg_graph_create_csr from pinned host CSR + gg_sssp_ex + distances copied to pinned host "
                        "+ gg_graph_destroy, wall clock"}
 
+    # sub-lines: the smaller RMAT and the high-diameter grid (timing models)
+    rmat20 = grid = None
+    if not args.no_rmat20:
+        rmat20 = run_rmat20(gg, torch, stream, flush)
+    if not args.no_grid:
+        grid = run_grid4096(gg, torch, stream, flush)
+    del flush
+
     # batched and served queries shard naturally: every rank runs its own
     # seeded stream (per-GPU work fixed) and the queries/s add up
     batched = serving = None
     cpu_sample = rank == 0 and world == 1 and not args.no_cpu_baseline   # oracle baselines: rank 0 at N=1
     if not args.no_batch:
+        same = args.workload == f"rmat{args.batch_scale}"
+        g.close()    # the batch builds its own handle (the headline's is no longer needed)
         batched = run_batched(gg, torch, seed=1 + rank, scale=args.batch_scale, policy=args.batch_policy,
-                              cpu_sample=cpu_sample)
+                              cpu_sample=cpu_sample, graph=(ro, col, w) if same else None)
         batched["queries_per_s_all_ranks"] = reduce_over_ranks(batched["queries_per_s"], "sum", pg)
     if not args.no_serve:
         serving = run_serving(gg, torch, args.serve_queries, seed=1 + rank, cpu_sample=cpu_sample)
@@ -560,13 +727,18 @@ def main():
             "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "verified": verified,
             "config": {"workload": workload_desc(args.workload), "n": n, "m": m, "source": int(src),
-                       "m_trav": m_trav, "n_reach": n_reach, "policy": args.policy, "direction": args.direction, "lb": args.lb, "delta": args.delta,
+                       "m_trav": m_trav, "n_reach": n_reach, "policy": args.policy, "direction": args.direction,
+                       "lb": args.lb, "delta": args.delta,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": f"L2 flushed before every timed step ({L2_FLUSH_BYTES >> 20} MiB written outside "
                              f"the step's events); dist re-initialised every step",
+                       "verified_against": "sha256 of the stats run's and the last timed step's distances = the "
+                                           "oracle's stored hash (tests/golden/workloads.json)",
                        "supersteps": iters, "pull_supersteps": stats["pull_iterations"],
-                       "edges_scanned": stats["edges_scanned"], "step_ms_min": min(per), "step_ms_max": max(per)},
+                       "edges_scanned": stats["edges_scanned"], "step_ms_min": min(per), "step_ms_max": max(per),
+                       "step_ms_median": statistics.median(per)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
                          "traffic": kernel_traffic(args.workload, args.direction, args.lb, args.delta),
@@ -580,6 +752,8 @@ def main():
                          "frac_nominal_8tbs": achieved / NOMINAL_HBM_GBS},
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "rmat20": rmat20,
+            "grid4096": grid,
             "batched": batched,
             "serving": serving,
             "gpu_launches": launches_per_step * args.steps,
@@ -587,7 +761,8 @@ def main():
             "gpu": torch.cuda.get_device_name(),
         }
         print(json.dumps(line), flush=True)
-    g.close()
+    if args.no_batch:
+        g.close()
     if pg:
         pg.destroy_process_group()
 

@@ -422,7 +422,9 @@ gg_status gg_server_destroy(gg_server_t s);
  * different streams or host threads) race on it, so the caller must order
  * them.  The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * outside any stream capture.  The call synchronises `stream` and returns
+ * outside any stream capture.  The address is kept for the life of the
+ * process: after cudaDeviceReset on a device the kept address is stale, so
+ * gg_sssp_noalloc must not be called on that device after a reset.  The call synchronises `stream` and returns
  * when dist_out is complete (push supersteps launched from the host).
  * Returns GG_ERR_OVERFLOW when a finite distance does not fit below GG_INF. */
 gg_status gg_sssp_noalloc(uint32_t n, uint64_t m, const uint32_t* row_offsets,

@@ -385,14 +385,31 @@ GG_NOALLOC_MAX_VERTICES = 1 << 20
 def gg_sssp_noalloc(row_offsets, col_indices, weights, src: int, dist_out, stream=None):
     """Distances from src computed straight from a device CSR (CUDA uint32
     tensors) without allocating any device memory; returns when dist_out is
-    complete.  For callers that must not allocate (see include/gg.h)."""
+    complete.  For callers that must not allocate (see include/gg.h).
+
+    The C call trusts the sizes it is given, so the lengths are checked here:
+    weights must hold exactly as many entries as col_indices, dist_out at
+    least n, and all four tensors must sit on one GPU.  The call runs with
+    that GPU current (its built-in scratch array is the current device's)."""
     ptrs = [_ptr(a) for a in (row_offsets, col_indices, weights, dist_out)]
     if not all(dev for _, dev in ptrs):
         raise ValueError("gg_sssp_noalloc takes CUDA tensors only")
+    devices = {a.device for a in (row_offsets, col_indices, weights, dist_out)}
+    if len(devices) != 1:
+        raise ValueError(f"gg_sssp_noalloc: row_offsets, col_indices, weights and dist_out are on "
+                         f"different devices {sorted(str(d) for d in devices)}")
+    if row_offsets.dim() != 1 or int(row_offsets.shape[0]) < 2:
+        raise ValueError("row_offsets must be a 1-D tensor of n + 1 >= 2 entries")
     n = int(row_offsets.shape[0]) - 1
-    m = int(col_indices.shape[0])
-    _check(load().gg_sssp_noalloc(n, m, ptrs[0][0], ptrs[1][0] if m else None, ptrs[2][0] if m else None, src,
-                                  ptrs[3][0], _stream_ptr(stream)), "gg_sssp_noalloc")
+    m = int(col_indices.numel())
+    if int(weights.numel()) != m:
+        raise ValueError(f"weights has {int(weights.numel())} entries, col_indices {m}: they must match")
+    if int(dist_out.numel()) < n:
+        raise ValueError(f"dist_out has {int(dist_out.numel())} entries, fewer than n = {n}")
+    import torch
+    with torch.cuda.device(row_offsets.device):
+        _check(load().gg_sssp_noalloc(n, m, ptrs[0][0], ptrs[1][0] if m else None, ptrs[2][0] if m else None,
+                                      src, ptrs[3][0], _stream_ptr(stream)), "gg_sssp_noalloc")
 
 
 class Graph:

@@ -2,7 +2,17 @@
 the generated graph and of the oracle's distance vector, plus summary
 numbers.  Calls only graphgen (inputs) and oracle (expected values).
 
+Two multi-query records sit beside the single-source workloads:
+
+* ``rmat22_batch64``: the 64 seeded sources of the batched workload (RMAT
+  scale 22, splitmix64 seed 1): the sha256 of the vertex-major distance
+  matrix (n x 64, dist[v * 64 + s]) and of each column;
+* ``serving_pool``: the 2,000-query Poisson stream (seed 1) over the 32-graph
+  pool: per query its graph, source and the first 16 hex digits of the
+  sha256 of its distance vector.
+
 Usage: python tests/golden/make_golden.py [workload ...]
+       (names: the single-source workloads, rmat22_batch64, serving_pool)
 """
 import hashlib
 import json
@@ -38,6 +48,33 @@ def record(name):
                 m_trav=oracle.traversed_edges(ro, dist))
 
 
+def record_batch(scale=22, k=64, seed=1):
+    ro, col, w = graphgen.rmat(scale, 16, seed=1, W=255)
+    srcs = graphgen.sample_sources(ro, k, seed=seed)
+    D = oracle.dijkstra_many(ro, col, w, srcs, threads=os.cpu_count() or 1)     # (k, n)
+    vm = np.ascontiguousarray(D.T)                                               # vertex-major (n, k)
+    return dict(n=int(ro.shape[0] - 1), k=k, sources=[int(x) for x in srcs], graph_sha256=sha(ro, col, w),
+                matrix_sha256=sha(vm), column_sha256=[sha(D[s]) for s in range(k)],
+                m_trav=[oracle.traversed_edges(ro, D[s]) for s in range(k)])
+
+
+def record_serving(nq=2000, seed=1):
+    from concurrent.futures import ThreadPoolExecutor
+    spec = graphgen.serving_pool_spec()
+    pool = [graphgen.build_pool_graph(e) for e in spec]
+    degs = [np.diff(ro.astype(np.int64)) for ro, _, _ in pool]
+    gids, srcs, _ = graphgen.poisson_queries(degs, nq, seed=seed)
+
+    def one(i):
+        ro, col, w = pool[gids[i]]
+        return sha(oracle.dijkstra(ro, col, w, int(srcs[i])))[:16]
+
+    with ThreadPoolExecutor(os.cpu_count() or 1) as ex:      # the ctypes call releases the GIL
+        hashes = list(ex.map(one, range(nq)))
+    return dict(queries=nq, seed=seed, graph_sha256=[sha(*g) for g in pool], graph=[int(x) for x in gids],
+                source=[int(x) for x in srcs], dist_sha256_16=hashes)
+
+
 def main(names):
     data = {}
     if os.path.exists(OUT):
@@ -47,8 +84,13 @@ def main(names):
                       "oracle (binary-heap Dijkstra); distances are uint32 little-endian, "
                       "0xFFFFFFFF = unreachable.")
     for nm in names:
-        data[nm] = record(nm)
-        print(nm, data[nm])
+        if nm == "rmat22_batch64":
+            data[nm] = record_batch()
+        elif nm == "serving_pool":
+            data[nm] = record_serving()
+        else:
+            data[nm] = record(nm)
+        print(nm, str(data[nm])[:300])
     with open(OUT, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)
 
