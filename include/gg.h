@@ -178,6 +178,8 @@ typedef struct {
 #define GG_DELTA_NONE 0xFFFFFFFFu
 #define GG_LH_AUTO 0u
 #define GG_LH_OFF 1u
+#define GG_LH_ROUNDS 2u   /* batched calls: light-first rounds without buckets (the
+                             label-correcting schedule); single source: as GG_LH_AUTO */
 
 /* ---- graph (Sec. IV-A, Listing 1) ------------------------------------- */
 
@@ -255,7 +257,9 @@ gg_status gg_bfs_ex(gg_graph_t g, uint32_t src, uint32_t* depth_out, const gg_op
 /* Picks the fastest single-source options for this graph (Sec. IV-C leaves
  * load balancing and the operator's execution choices to the implementation):
  * coordinate descent over the loop policy (CUDA graph or persistent), the
- * near-far bucket width, push-only vs push/pull switching thresholds, and
+ * bucket width (on graphs with a light/heavy width: widths giving 1.5 to 4.5
+ * light edges per vertex; otherwise the near-far width from 1/8 to 8 times
+ * the default; and no buckets), push-only vs push/pull switching thresholds, and
  * merge-path vs degree bins with their thresholds.  Every candidate runs
  * gg_sssp_ex from each sample source on `stream` and is timed with CUDA
  * events (median of 3); candidates that report a device error are skipped.
@@ -266,6 +270,20 @@ gg_status gg_bfs_ex(gg_graph_t g, uint32_t src, uint32_t* depth_out, const gg_op
  * Synchronous; takes roughly 50 runs per sample source. */
 gg_status gg_autotune(gg_graph_t g, const uint32_t* srcs, uint32_t nsrc, uint32_t* dist_scratch,
                       gg_options* best, float* best_ms, cudaStream_t stream);
+
+/* Picks the fastest batched options for this graph and these sources: the
+ * schedule (GG_LH_AUTO normalised buckets or GG_LH_ROUNDS) and the
+ * light/heavy width (delta: 1.5 to 4.5 light edges per vertex, or
+ * GG_DELTA_NONE).  Each candidate runs gg_sssp_batch_ex over all k sources on
+ * `stream`, timed with CUDA events (median of 3); candidates that report a
+ * device error are skipped.
+ *   srcs          host u32[k], each < n
+ *   dist_scratch  device u32[n*k] the runs write into
+ *   best          receives the winning options (stats/trace pointers NULL)
+ *   best_ms       optional: its time per batched call in milliseconds
+ * Synchronous; about 45 batched calls. */
+gg_status gg_autotune_batch(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t* dist_scratch,
+                            gg_options* best, float* best_ms, cudaStream_t stream);
 
 /* ---- batched multi-source SSSP ------------------------------------------ */
 
@@ -287,20 +305,36 @@ gg_status gg_sssp_batch(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t
                         cudaStream_t stream);
 
 /* As gg_sssp_batch with options: max_iterations, stats (summed over the
- * 64-source groups; setting stats synchronises the stream), delta and the
+ * 64-source groups; setting stats synchronises the stream), trace (first
+ * 64-source group only: per superstep kind | 16 once bucketing has ended
+ * (kind 0 light or plain push, 1 split, 2 heavy, 3 mask clear before the
+ * tail), entries, edges, next frontier size), delta, light_heavy and the
  * policy GG_POLICY_BSP_HOST (supersteps launched one by one from the host,
- * synchronising after each; every other policy runs the CUDA-graph loop) are
- * honoured; direction and load-balance fields are ignored.  delta 0 (the
- * default) runs light-first rounds on graphs with a light/heavy width (mean
- * degree >= 8, integer weights) unless light_heavy is GG_LH_OFF: light
- * supersteps relax only the light edges of the light-first edge copy (the
- * one the single-source loop uses, built on first use), every improving
- * (vertex, source) pair is also recorded in an R mask, and when the light
- * frontier empties one heavy superstep relaxes the heavy edges of the R
- * pairs.  Otherwise delta 0 or GG_DELTA_NONE runs the plain frontier loop
- * (buckets would make a vertex whose sources fall in different buckets expand
- * once per bucket); another value parks (vertex, source) pairs at or above
- * the threshold in per-vertex far masks.  Distances are the same in every
+ * synchronising after each; every other policy runs the CUDA-graph loop);
+ * direction and load-balance fields are ignored.
+ *
+ * On graphs with a light/heavy width (mean degree >= 8, integer weights),
+ * unless light_heavy is GG_LH_OFF or delta is GG_DELTA_NONE or exceeds the
+ * largest weight, the sources run light-first rounds over the light-first
+ * edge copy that the single-source loop uses (built on first use), with
+ * width delta (0 = the graph's width): light supersteps relax only the light
+ * edges (weight < width) of their (vertex, sources) entries, every improving
+ * pair is also recorded in an R mask, and when the light frontier empties one
+ * heavy superstep relaxes the heavy edges of the R pairs.
+ *   GG_LH_AUTO (default): normalised buckets.  Each source's distances are
+ *     shifted by sh[s] = max o - o_s, o_s its distance from the graph's
+ *     highest-degree vertex (computed once per handle by a single-source run,
+ *     kept by the handle); one shared threshold over the shifted distances
+ *     moves in steps of the width, pairs at or above it wait parked, and
+ *     each pair's heavy edges are relaxed once, when its bucket settles
+ *     (delta-stepping per source with the buckets of all sources aligned).
+ *     Once the pairs not yet settled hold fewer than 1/8 of the heavy edges,
+ *     the rest is plain push over all edges.
+ *   GG_LH_ROUNDS: the same rounds without buckets (label-correcting: a
+ *     pair's heavy edges are relaxed once per epoch in which it improved).
+ * Otherwise delta 0 or GG_DELTA_NONE runs the plain frontier loop, and
+ * another delta parks (vertex, source) pairs at or above the threshold in
+ * per-vertex far masks (near-far buckets).  Distances are the same in every
  * mode. */
 gg_status gg_sssp_batch_ex(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t* dist_out,
                            const gg_options* opt, cudaStream_t stream);

@@ -21,7 +21,7 @@ __all__ = [
     "GGError", "GG_INF", "GG_DEVICE_PTRS", "GG_SYMMETRIC", "GG_NO_VALIDATE",
     "GG_POLICY_BSP_GRAPH", "GG_POLICY_ASYNC_PERSISTENT", "GG_POLICY_BSP_HOST", "GG_POLICY_BSP_PERSISTENT",
     "GG_DIR_AUTO", "GG_DIR_PUSH", "GG_DIR_PULL", "GG_LB_AUTO", "GG_LB_MERGE_PATH", "GG_LB_BINS", "GG_LB_WARP", "GG_DELTA_NONE",
-    "GG_LH_AUTO", "GG_LH_OFF",
+    "GG_LH_AUTO", "GG_LH_OFF", "GG_LH_ROUNDS",
     "gg_graph_create_csr", "gg_graph_destroy", "gg_graph_info", "gg_graph_check", "gg_sssp", "gg_sssp_ex",
     "gg_bfs", "gg_bfs_ex", "GG_FLOAT_WEIGHTS", "GG_FLT_MAX_BITS",
     "gg_sssp_batch", "gg_sssp_multi", "Server",
@@ -41,7 +41,7 @@ GG_POLICY_BSP_GRAPH, GG_POLICY_ASYNC_PERSISTENT, GG_POLICY_BSP_HOST, GG_POLICY_B
 GG_DIR_AUTO, GG_DIR_PUSH, GG_DIR_PULL = 0, 1, 2
 GG_LB_AUTO, GG_LB_MERGE_PATH, GG_LB_BINS, GG_LB_WARP = 0, 1, 2, 3
 GG_DELTA_NONE = 0xFFFFFFFF
-GG_LH_AUTO, GG_LH_OFF = 0, 1
+GG_LH_AUTO, GG_LH_OFF, GG_LH_ROUNDS = 0, 1, 2
 
 STATUS = {0: "GG_OK", 1: "GG_ERR_INVALID_ARG", 2: "GG_ERR_OUT_OF_MEMORY", 3: "GG_ERR_CUDA",
           4: "GG_ERR_TIMEOUT", 5: "GG_ERR_BUSY", 6: "GG_ERR_NOT_READY", 7: "GG_ERR_OVERFLOW",
@@ -132,6 +132,8 @@ def load():
             "gg_server_destroy": (ctypes.c_int, [vp]),
             "gg_autotune": (ctypes.c_int, [vp, P32, u32, vp, ctypes.POINTER(gg_options),
                                            ctypes.POINTER(ctypes.c_float), vp]),
+            "gg_autotune_batch": (ctypes.c_int, [vp, P32, u32, vp, ctypes.POINTER(gg_options),
+                                                 ctypes.POINTER(ctypes.c_float), vp]),
             "gg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "gg_last_error": (ctypes.c_char_p, []),
             "gg_abi_version": (u32, []),

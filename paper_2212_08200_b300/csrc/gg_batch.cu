@@ -54,6 +54,22 @@ struct BatchCtl {
   // the masks of a consumed R list are cleared one superstep later.
   uint32_t lh, epoch, zero_pending, zero_par;
   unsigned long long rcnt[3];
+  // normalised buckets (nb = 1, light-first rounds only): one shared bucket
+  // threshold over the pairs' distances shifted by sh[s] = max_s' o_s' - o_s,
+  // where o_s is the source's distance from the graph's highest-degree vertex
+  // (the hub).  A pair (v, s) is near while dist[v][s] + sh[s] < t_cur; near
+  // pairs relax their light edges and join the R mask, far ones are parked in
+  // fmask.  Sources reach the dense core at about the same shifted distance,
+  // so one bucket holds the same vertices for most sources and each edge read
+  // still serves many of them.  Bucketing ends (tail = 1: plain push over all
+  // edges of every improved pair) once the unsettled pairs hold fewer than
+  // heavy_total_k / drain_div heavy edges.
+  uint32_t nb, tail, width, drain_div;
+  uint32_t* trace;      // optional: per superstep (kind | tail << 4, entries, edges, next frontier size)
+  uint32_t trace_cap;
+  unsigned long long heavy_total_k;   // heavy edges of the graph x sources of the group
+  unsigned long long heavy_settled;   // heavy edges of the pairs that settled into a bucket
+  uint32_t sh[64];
 };
 
 struct BatchBufs {
@@ -71,6 +87,7 @@ struct BatchBufs {
   uint32_t* rr[3];
   uint32_t* rs[3];
   unsigned long long* rmask[3];
+  const uint32_t* hubd;   // distances from the hub (normalised buckets)
 };
 
 namespace {
@@ -84,6 +101,15 @@ static_assert(kBNW * kBQW <= (uint32_t)kBCap, "per-warp queues fit the CTA queue
 #ifndef GG_BMINB
 #define GG_BMINB 6   // resident CTAs per SM the batch superstep is compiled for (40 registers)
 #endif
+#ifndef GG_NB_WIDTH
+#define GG_NB_WIDTH 1   // normalised buckets: bucket width in light/heavy widths
+#endif
+#ifndef GG_NB_DRAIN
+#define GG_NB_DRAIN 8   // normalised buckets end once the unsettled pairs hold < 1/GG_NB_DRAIN of the heavy edges
+#endif
+#ifndef GG_BATCH_UNROLL
+#define GG_BATCH_UNROLL 4   // superstep kernels per iteration of the batch's CUDA-graph loop
+#endif
 
 struct BSmem {
   uint32_t qv[kBCap], qr[kBCap], qd[kBCap];   // split step: CTA queue; otherwise kBQW per warp
@@ -93,6 +119,9 @@ struct BSmem {
   uint32_t pv[kBNW][32];
   uint32_t rq[kBNW * kBQW];   // light-first rounds: per-warp queue of new R entries
   uint32_t wsum[kBNW];
+  // per source of the group: near limit max(t_cur - sh, 0), split floor
+  // max(t_prev - sh, 0) and the shift itself (all sh = 0 without normalised buckets)
+  uint32_t tabs[64], tprev[64], shs[64];
   uint32_t qn, j, last, ovf;
   unsigned long long base;
 };
@@ -165,6 +194,10 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
   __shared__ BSmem sm;
   BatchCtl* ctl = w.ctl;
   const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (ctl->running == 0u) {   // a superstep node past the end of the loop (unrolled graph body)
+    if (use_cond && blockIdx.x == 0 && tid == 0) cudaGraphSetConditional(cond, 0u);
+    return;
+  }
   const uint32_t it = ctl->iter;
   const uint32_t pc = it % 3, pn = (it + 1) % 3, po = (it + 2) % 3;
   const uint32_t bmode0 = ctl->mode;
@@ -179,6 +212,14 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
   unsigned long long* Mn = pick3(w.mask, pn);
   const uint32_t wbits = g.wbits;
   const uint32_t T = ctl->t_cur, fsel = ctl->fsel, bmode = heavy ? 0u : bmode0;
+  const bool tailm = LH && ctl->tail != 0u;   // normalised buckets ended: full rows, no R
+  const bool nbm = LH && ctl->nb != 0u;
+  if (tid < 64) {
+    const uint32_t sh = ctl->sh[tid], tp = ctl->t_prev;
+    sm.shs[tid] = sh;
+    sm.tabs[tid] = T == kInf ? kInf : (T > sh ? T - sh : 0u);
+    sm.tprev[tid] = tp > sh ? tp - sh : 0u;
+  }
   // new R entries join the epoch in progress (the next one during a heavy superstep)
   const uint32_t rj = (heavy ? ep + 1u : ep) % 3;
   // zero the masks of F_{t-1}
@@ -202,74 +243,114 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
   }
   __syncthreads();
   bool ovf = false;
-  if (bmode == 1) {
-    // split step: every parked (vertex, source) bit is re-examined against
-    // the raised threshold: below t_prev it was expanded already (drop),
-    // below t_cur it joins the next frontier, otherwise it stays parked
-    const uint32_t nfar = ctl->fcnt[fsel];
-    const uint32_t t_prev = ctl->t_prev;
-    constexpr uint32_t R = 64;   // far vertices per warp between flushes
-    for (uint32_t base = blockIdx.x * kBNW * R; base < nfar; base += gridDim.x * kBNW * R) {
-      for (uint32_t r = 0; r < R; ++r) {
-        const uint32_t i = base + warp * R + r;
-        if (i >= nfar) break;   // warp-uniform
-        const uint32_t v = pick2(w.far_v, fsel)[i];
-        const unsigned long long bits = w.fmask[v];
-        const uint32_t* vrow = dist + (size_t)v * K + col0;
-        const bool lo = (bits >> lane) & 1ull, hi = (bits >> (lane + 32)) & 1ull;
-        const uint32_t dlo = lo ? ld_cg(vrow + lane) : 0u, dhi = hi ? ld_cg(vrow + lane + 32) : 0u;
-        const bool mlo = lo && dlo >= t_prev && dlo < T, mhi = hi && dhi >= t_prev && dhi < T;
-        const bool klo = lo && dlo >= T, khi = hi && dhi >= T;
-        const unsigned nb_lo = __ballot_sync(0xFFFFFFFFu, mlo), nb_hi = __ballot_sync(0xFFFFFFFFu, mhi);
-        const unsigned kb_lo = __ballot_sync(0xFFFFFFFFu, klo), kb_hi = __ballot_sync(0xFFFFFFFFu, khi);
-        if (kb_lo | kb_hi) {
-          uint32_t fm = min(klo ? dlo : kInf, khi ? dhi : kInf);
-#pragma unroll
-          for (int o = 16; o; o >>= 1) fm = min(fm, __shfl_xor_sync(0xFFFFFFFFu, fm, o));
-          if (lane == 0) atomicMin(&ctl->far_min, fm);
-        }
-        if (lane == 0) {
-          const unsigned long long kb = (unsigned long long)kb_lo | ((unsigned long long)kb_hi << 32);
-          const unsigned long long nb = (unsigned long long)nb_lo | ((unsigned long long)nb_hi << 32);
-          w.fmask[v] = kb;
-          if (kb) {
-            const uint32_t pos = atomicAdd(&ctl->fcnt[fsel ^ 1u], 1u);
-            pick2(w.far_v, fsel ^ 1u)[pos] = v;
-          }
-          if (nb && atomicOr(Mn + v, nb) == 0ull) {
-            const uint32_t rs = __ldg(g.ro + v);
-            const uint32_t q = atomicAdd(&sm.qn, 1u);
-            sm.qv[q] = v;
-            sm.qr[q] = rs;
-            sm.qd[q] = __ldg(g.ro + v + 1) - rs;
-          }
-        }
-      }
-      __syncthreads();
-      const uint32_t qn = sm.qn;
-      if (qn) {
-        if (!g.sinks) {   // rows deferred from the appends
-          for (uint32_t i = tid; i < qn; i += kBB) {
-            const uint32_t rs = __ldg(g.ro + sm.qv[i]);
-            sm.qr[i] = rs;
-            sm.qd[i] = __ldg(g.ro + sm.qv[i] + 1) - rs;
-          }
-          __syncthreads();
-        }
-        const uint32_t tot = block_scan_excl<kBB>(sm.qd, qn, sm.wsum);
-        if (tid == 0) sm.base = atomicAdd(&ctl->cnt[pn], ((unsigned long long)qn << 32) | tot);
-        __syncthreads();
-        const uint32_t pos0 = (uint32_t)(sm.base >> 32), eb0 = (uint32_t)sm.base;
-        for (uint32_t i = tid; i < qn; i += kBB) {
-          pick3(w.fv, pn)[pos0 + i] = sm.qv[i];
-          pick3(w.fr, pn)[pos0 + i] = sm.qr[i];
-          pick3(w.fs, pn)[pos0 + i] = eb0 + sm.qd[i];
-        }
-        __syncthreads();
-        if (tid == 0) sm.qn = 0;
-      }
-      __syncthreads();
+  if (bmode == 3) {
+    // before the tail's split: clear the three frontier mask arrays.  A vertex
+    // without light edges may hold mask bits that no frontier list carries
+    // (nothing clears them), which would keep it out of the tail's frontier.
+    for (uint32_t i = blockIdx.x * kBB + tid; i < g.n; i += gridDim.x * kBB) {
+      w.mask[0][i] = 0ull;
+      w.mask[1][i] = 0ull;
+      w.mask[2][i] = 0ull;
     }
+  } else if (bmode == 1) {
+    // split step: every parked (vertex, source) bit is re-examined against
+    // the raised threshold: below the previous threshold it was expanded
+    // already (drop), below the new one it joins the next frontier (and, in
+    // light-first rounds with buckets, the epoch's R mask), otherwise it stays
+    // parked.  One far vertex per warp; lane l holds sources l and l + 32.
+    const unsigned FULL = 0xFFFFFFFFu;
+    const uint32_t nfar = ctl->fcnt[fsel];
+    const uint32_t* fend = (LH && !tailm) ? w.lend : g.ro + 1;   // frontier rows: light edges, or all
+    const uint32_t rj = ep % 3;
+    uint32_t* qv = sm.qv + warp * kBQW;
+    uint32_t* rq = sm.rq + warp * kBQW;
+    uint32_t qn = 0, rqn = 0;   // warp-uniform
+    unsigned long long hacc = 0ull;   // lane 0: heavy edges of the pairs settling here
+    const uint32_t tp_lo = sm.tprev[lane], tp_hi = sm.tprev[lane + 32];
+    const uint32_t tc_lo = sm.tabs[lane], tc_hi = sm.tabs[lane + 32];
+    const uint32_t sh_lo = sm.shs[lane], sh_hi = sm.shs[lane + 32];
+    uint32_t wfm = kInf;
+    uint32_t* kq = sm.qd + warp * kBQW;   // vertices that keep parked bits
+    uint32_t kqn = 0;                     // warp-uniform
+    auto kflush = [&]() {
+      __syncwarp();
+      uint32_t pos = 0;
+      if (lane == 0) pos = atomicAdd(&ctl->fcnt[fsel ^ 1u], kqn);
+      pos = __shfl_sync(FULL, pos, 0);
+      for (uint32_t j = lane; j < kqn; j += 32) pick2(w.far_v, fsel ^ 1u)[pos + j] = kq[j];
+      kqn = 0;
+      __syncwarp();
+    };
+    for (uint32_t i = blockIdx.x * kBNW + warp; i < nfar; i += gridDim.x * kBNW) {   // warp-uniform
+      const uint32_t v = pick2(w.far_v, fsel)[i];
+      const unsigned long long bits = w.fmask[v];
+      const uint32_t* vrow = dist + (size_t)v * K + col0;
+      const bool lo = (bits >> lane) & 1ull, hi = (bits >> (lane + 32)) & 1ull;
+      const uint32_t dlo = lo ? ld_cg(vrow + lane) : 0u, dhi = hi ? ld_cg(vrow + lane + 32) : 0u;
+      const bool mlo = lo && dlo >= tp_lo && dlo < tc_lo, mhi = hi && dhi >= tp_hi && dhi < tc_hi;
+      const bool klo = lo && dlo >= tc_lo, khi = hi && dhi >= tc_hi;
+      const unsigned nb_lo = __ballot_sync(FULL, mlo), nb_hi = __ballot_sync(FULL, mhi);
+      const unsigned kb_lo = __ballot_sync(FULL, klo), kb_hi = __ballot_sync(FULL, khi);
+      // smallest shifted distance left parked (one atomic per warp at the end)
+      if (klo) wfm = min(wfm, (uint32_t)min(0xFFFFFFFFull, (unsigned long long)dlo + sh_lo));
+      if (khi) wfm = min(wfm, (uint32_t)min(0xFFFFFFFFull, (unsigned long long)dhi + sh_hi));
+      bool app = false, rapp = false;
+      if (kb_lo | kb_hi) {   // stays on the (other) far list: per-warp queue
+        if (lane == 0) kq[kqn] = v;
+        if (++kqn == kBQW) kflush();
+      }
+      if (lane == 0) {
+        const unsigned long long kb = (unsigned long long)kb_lo | ((unsigned long long)kb_hi << 32);
+        const unsigned long long nb = (unsigned long long)nb_lo | ((unsigned long long)nb_hi << 32);
+        w.fmask[v] = kb;
+        if (nb) {
+          app = atomicOr(Mn + v, nb) == 0ull;
+          if (LH && !tailm) {
+            const unsigned long long old = atomicOr(pick3(w.rmask, rj) + v, nb);
+            rapp = old == 0ull;
+            const unsigned long long nw = nb & ~old;
+            if (nbm && nw) hacc += (unsigned long long)__popcll(nw) * (__ldg(g.ro + v + 1) - __ldg(w.lend + v));
+          }
+        }
+      }
+      app = __shfl_sync(FULL, app, 0);
+      rapp = __shfl_sync(FULL, rapp, 0);
+      if (app) {
+        if (lane == 0) qv[qn] = v;
+        if (++qn == kBQW) {
+          __syncwarp();
+          for (uint32_t j0 = 0; j0 < qn; j0 += 32)
+            b_append32(j0 + lane < qn, j0 + lane < qn ? qv[j0 + lane] : 0u, g.ro, fend, &ctl->cnt[pn],
+                       pick3(w.fv, pn), pick3(w.fr, pn), pick3(w.fs, pn));
+          qn = 0;
+          __syncwarp();
+        }
+      }
+      if (LH && rapp) {
+        if (lane == 0) rq[rqn] = v;
+        if (++rqn == kBQW) {
+          __syncwarp();
+          for (uint32_t j0 = 0; j0 < rqn; j0 += 32)
+            b_append32(j0 + lane < rqn, j0 + lane < rqn ? rq[j0 + lane] : 0u, w.lend, g.ro + 1, &ctl->rcnt[rj],
+                       pick3(w.rv, rj), pick3(w.rr, rj), pick3(w.rs, rj));
+          rqn = 0;
+          __syncwarp();
+        }
+      }
+    }
+    __syncwarp();
+    for (uint32_t j0 = 0; j0 < qn; j0 += 32)
+      b_append32(j0 + lane < qn, j0 + lane < qn ? qv[j0 + lane] : 0u, g.ro, fend, &ctl->cnt[pn], pick3(w.fv, pn),
+                 pick3(w.fr, pn), pick3(w.fs, pn));
+    if (LH)
+      for (uint32_t j0 = 0; j0 < rqn; j0 += 32)
+        b_append32(j0 + lane < rqn, j0 + lane < rqn ? rq[j0 + lane] : 0u, w.lend, g.ro + 1, &ctl->rcnt[rj],
+                   pick3(w.rv, rj), pick3(w.rr, rj), pick3(w.rs, rj));
+    if (kqn) kflush();
+#pragma unroll
+    for (int o = 16; o; o >>= 1) wfm = min(wfm, __shfl_xor_sync(FULL, wfm, o));
+    if (lane == 0 && wfm != kInf) atomicMin(&ctl->far_min, wfm);
+    if (lane == 0 && hacc) atomicAdd(&ctl->heavy_settled, hacc);
   } else if (F > 0) {
     // Warp streaming, no block barriers: every warp of the grid takes an
     // equal contiguous share of the frontier's edge coordinates and walks it
@@ -292,6 +373,10 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
     uint32_t* qr = sm.qr + warp * QW;
     uint32_t* qd = sm.qd + warp * QW;
     uint32_t qn = 0;                    // warp-uniform
+    unsigned long long hacc = 0ull;     // warp-uniform: heavy edges of pairs that settled (normalised buckets)
+    uint32_t wfm = kInf;                // smallest shifted distance this lane parked
+    uint32_t* fq = sm.qd + warp * QW;   // light-first rounds: this warp's queue of new far-list vertices
+    uint32_t fqn = 0;                   // warp-uniform
     const uint32_t g4 = lane >> 3, l8 = lane & 7;
     const unsigned lt = (1u << lane) - 1u;
     const bool buckets = T != kInf;     // uniform
@@ -303,10 +388,11 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
       // rows (deferred on sink-free graphs), warp scan of the degrees, one
       // 64-bit atomic for the queue position and the edge-prefix base
       __syncwarp();
-      if (LH) {   // light edges [ro[v], lend[v]); vertices without any are left out
+      if (LH) {   // light edges [ro[v], lend[v]) (all edges in the tail); vertices without any are left out
+        const uint32_t* fend = tailm ? g.ro + 1 : w.lend;
         for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
           const uint32_t i = i0 + lane;
-          b_append32(i < qn, i < qn ? qv[i] : 0u, g.ro, w.lend, &ctl->cnt[pn], pick3(w.fv, pn), pick3(w.fr, pn),
+          b_append32(i < qn, i < qn ? qv[i] : 0u, g.ro, fend, &ctl->cnt[pn], pick3(w.fv, pn), pick3(w.fr, pn),
                      pick3(w.fs, pn));
         }
         qn = 0;
@@ -346,6 +432,15 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
         pick3(w.fs, pn)[pos0 + i] = eb0 + qd[i];
       }
       qn = 0;
+      __syncwarp();
+    };
+    auto ffl = [&]() {   // the warp's new far-list vertices, one atomicAdd
+      __syncwarp();
+      uint32_t pos = 0;
+      if (lane == 0) pos = atomicAdd(&ctl->fcnt[fsel], fqn);
+      pos = __shfl_sync(FULL, pos, 0);
+      for (uint32_t i = lane; i < fqn; i += 32) pick2(w.far_v, fsel)[pos + i] = fq[i];
+      fqn = 0;
       __syncwarp();
     };
     auto rflush = [&]() {   // heavy edges [lend[v], ro[v+1]) of new R entries
@@ -458,13 +553,14 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
                 const uint32_t nd = add_sat(du[q], wi, ovf);
                 if (nd < cv[q]) {
                   atomicMin(vrow + q, nd);
-                  // near bits (new distance below the threshold) join the next
-                  // frontier's mask; the others are parked in the far mask
-                  if (nd < T) {
+                  // near bits (new distance below the source's threshold) join
+                  // the next frontier's mask; the others are parked in the far
+                  // mask, and the smallest shifted distance parked is kept
+                  if (nd < sm.tabs[8 * l8 + q]) {
                     near |= 1u << q;
                   } else {
                     far |= 1u << q;
-                    fm = min(fm, nd);
+                    fm = min(fm, (uint32_t)min(0xFFFFFFFFull, (unsigned long long)nd + sm.shs[8 * l8 + q]));
                   }
                 }
               }
@@ -482,11 +578,9 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
             if (anyf) {
 #pragma unroll
               for (int o = 1; o < 8; o <<= 1) fmask |= __shfl_xor_sync(FULL, fmask, o);
-#pragma unroll
-              for (int o = 16; o; o >>= 1) fm = min(fm, __shfl_xor_sync(FULL, fm, o));
-              if (lane == 0) atomicMin(&ctl->far_min, fm);
             }
           }
+          wfm = min(wfm, fm);   // one atomic per warp at the end of the pass, not per group of edges
           if (l8 == 0 && live) {
             sm.pv[warp][i] = vi;
             sm.pm[warp][i] = nmask;
@@ -497,6 +591,7 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
         __syncwarp();
         bool app = false, fapp = false, rapp = false;
         uint32_t vi = 0, rs = 0, re = 1;
+        unsigned long long hset = 0ull;
         if (lane < (uint32_t)nvalid) {
           const unsigned long long nb = sm.pm[warp][lane], fb = sm.pf[warp][lane];
           if (nb | fb) {
@@ -511,9 +606,20 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
             if (re > rs) {
               app = nb && atomicOr(Mn + vi, nb) == 0ull;
               fapp = fb && atomicOr(w.fmask + vi, fb) == 0ull;
-              if (LH) rapp = nb && atomicOr(pick3(w.rmask, rj) + vi, nb) == 0ull;
+              if (LH && !tailm && nb) {
+                const unsigned long long old = atomicOr(pick3(w.rmask, rj) + vi, nb);
+                rapp = old == 0ull;
+                const unsigned long long nw = nb & ~old;
+                if (nbm && nw) hset = (unsigned long long)__popcll(nw) * (__ldg(g.ro + vi + 1) - __ldg(w.lend + vi));
+              }
             }
           }
+        }
+        if (nbm && __any_sync(FULL, hset != 0ull)) {   // pairs that settled into the bucket: their heavy edges
+#pragma unroll
+          for (int o = 16; o; o >>= 1) hset += __shfl_xor_sync(FULL, hset, o);
+          hacc += hset;
+          hset = 0ull;
         }
         if (LH) {
           const unsigned rb = __ballot_sync(FULL, rapp);
@@ -528,23 +634,38 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
           if (app) {
             const uint32_t off = qn + __popc(ab & lt);
             qv[off] = vi;
-            qr[off] = rs;
-            qd[off] = re - rs;
+            if (!LH) {   // light-first rounds read the rows at the flush
+              qr[off] = rs;
+              qd[off] = re - rs;
+            }
           }
           qn += __popc(ab);
           if (qn > QW - 32) flush();
         }
         const unsigned fbal = __ballot_sync(FULL, fapp);
-        if (fbal) {   // far list: one atomic per warp
-          uint32_t pos = 0;
-          if (lane == 0) pos = atomicAdd(&ctl->fcnt[fsel], (uint32_t)__popc(fbal));
-          pos = __shfl_sync(FULL, pos, 0);
-          if (fapp) pick2(w.far_v, fsel)[pos + __popc(fbal & lt)] = vi;
+        if (fbal) {
+          if (LH) {   // per-warp far queue, one atomic per flush
+            if (fapp) fq[fqn + __popc(fbal & lt)] = vi;
+            fqn += __popc(fbal);
+            if (fqn > QW - 32) ffl();
+          } else {    // far list: one atomic per warp
+            uint32_t pos = 0;
+            if (lane == 0) pos = atomicAdd(&ctl->fcnt[fsel], (uint32_t)__popc(fbal));
+            pos = __shfl_sync(FULL, pos, 0);
+            if (fapp) pick2(w.far_v, fsel)[pos + __popc(fbal & lt)] = vi;
+          }
         }
         __syncwarp();
       }
+      if (LH && fqn) ffl();
       if (qn) flush();
       if (LH && rqn) rflush();
+    }
+    if (lane == 0 && hacc) atomicAdd(&ctl->heavy_settled, hacc);
+    if (buckets) {
+#pragma unroll
+      for (int o = 16; o; o >>= 1) wfm = min(wfm, __shfl_xor_sync(FULL, wfm, o));
+      if (lane == 0 && wfm != kInf) atomicMin(&ctl->far_min, wfm);
     }
   }
   if (ovf) sm.ovf = 1u;
@@ -557,6 +678,13 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
   if (sm.last && tid == 0) {
     const unsigned long long cn = atomicAdd(&ctl->cnt[pn], 0ull);
     const uint32_t fn = (uint32_t)(cn >> 32);
+    if (ctl->trace && it < ctl->trace_cap) {
+      uint32_t* t = ctl->trace + 4ull * it;
+      t[0] = bmode0 | (tailm ? 16u : 0u);
+      t[1] = F;
+      t[2] = E;
+      t[3] = fn;
+    }
     if (F > 0 && bmode == 0) {
       ctl->edges_scanned += E;
       ctl->frontier_total += F;
@@ -576,8 +704,43 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
         ctl->epoch = ep + 1u;
       }
       const uint32_t rn = (uint32_t)(atomicAdd(&ctl->rcnt[ctl->epoch % 3], 0ull) >> 32);
-      ctl->mode = fn > 0 ? 0u : 2u;
+      uint32_t mode_next = fn > 0 ? 0u : 2u;
       bool more = fn != 0 || rn != 0;
+      if (ctl->nb) {
+        uint32_t fs_now = fsel;
+        if (bmode == 1) {   // the pairs kept parked went to the other list
+          ctl->fcnt[fsel] = 0u;
+          fs_now = fsel ^ 1u;
+          ctl->fsel = fs_now;
+          ctl->splits += 1;
+        }
+        const uint32_t nfar = atomicAdd(&ctl->fcnt[fs_now], 0u);
+        if (bmode == 3) {   // masks cleared: the tail's split follows
+          mode_next = 1u;
+          more = true;
+        } else if (!more && nfar > 0) {
+          // the bucket is settled (no near pair, no heavy edge left): raise the
+          // shared threshold to the next occupied bucket, or end bucketing once
+          // the unsettled pairs hold few heavy edges (the rest is plain push)
+          const unsigned long long hk = ctl->heavy_total_k;
+          const unsigned long long done = atomicAdd(&ctl->heavy_settled, 0ull);
+          const unsigned long long open = hk > done ? hk - done : 0ull;
+          const unsigned long long t1 = (unsigned long long)ctl->t_cur + ctl->width;
+          const unsigned long long t2 = (unsigned long long)atomicAdd(&ctl->far_min, 0u) + 1ull;
+          unsigned long long tn = t1 > t2 ? t1 : t2;
+          mode_next = 1u;
+          if (open < hk / ctl->drain_div || tn >= (unsigned long long)kInf) {
+            ctl->tail = 1u;
+            tn = kInf;
+            mode_next = 3u;   // clear the masks first
+          }
+          ctl->t_prev = ctl->t_cur;
+          ctl->t_cur = (uint32_t)tn;
+          ctl->far_min = kInf;
+          more = true;
+        }
+      }
+      ctl->mode = mode_next;
       if (more && it + 1 >= ctl->max_iter) {
         ctl->status |= DS_ITER_CAP;
         more = false;
@@ -633,11 +796,28 @@ __global__ void k_batch_fill(uint32_t* dist, unsigned long long count) {
 }
 
 // group start: dist[src_s][col0+s] := 0; initial frontier = distinct sources
-// with out-edges, each carrying the mask of its columns.  One CTA of 64.
+// with out-edges, each carrying the mask of its columns.  With normalised
+// buckets each source's shift sh[s] = max o - o_s comes from its hub distance
+// o_s (unreached from the hub: 0), and a source whose shift is not below the
+// first threshold starts parked.  One CTA of 64.
 __global__ void k_batch_seed(DevGraph g, BatchBufs w, const uint32_t* srcs, uint32_t k, uint32_t col0,
-                             uint32_t kg, uint32_t* dist, uint32_t max_iter, uint32_t delta, uint32_t lh) {
+                             uint32_t kg, uint32_t* dist, uint32_t max_iter, uint32_t delta, uint32_t lh,
+                             uint32_t nb, uint32_t width, uint32_t drain_div, unsigned long long heavy_total,
+                             uint32_t* trace, uint32_t trace_cap) {
+  __shared__ uint32_t so[64];
   BatchCtl* ctl = w.ctl;
   const uint32_t s = threadIdx.x;
+  uint32_t o = 0;
+  if (nb && s < kg) {
+    o = w.hubd[srcs[col0 + s]];
+    if (o == kInf) o = 0;
+  }
+  so[s] = o;
+  __syncthreads();
+  uint32_t omax = 0;
+  for (uint32_t i = 0; i < kg; ++i) omax = max(omax, so[i]);
+  const uint32_t sh = s < kg ? omax - o : 0u;
+  const uint32_t t0 = nb ? width : (lh ? kInf : delta);
   if (s == 0) {
     ctl->cnt[0] = 0ull;
     ctl->cnt[1] = 0ull;
@@ -653,7 +833,7 @@ __global__ void k_batch_seed(DevGraph g, BatchBufs w, const uint32_t* srcs, uint
     ctl->max_frontier = 0;
     ctl->edges_scanned = 0;
     ctl->frontier_total = 0;
-    ctl->t_cur = delta;
+    ctl->t_cur = t0;
     ctl->t_prev = 0;
     ctl->delta = delta;
     ctl->fsel = 0;
@@ -669,39 +849,77 @@ __global__ void k_batch_seed(DevGraph g, BatchBufs w, const uint32_t* srcs, uint
     ctl->rcnt[0] = 0ull;
     ctl->rcnt[1] = 0ull;
     ctl->rcnt[2] = 0ull;
+    ctl->nb = nb;
+    ctl->tail = 0;
+    ctl->width = width;
+    ctl->drain_div = max(drain_div, 1u);
+    ctl->heavy_total_k = heavy_total * kg;
+    ctl->heavy_settled = 0ull;
+    ctl->trace = trace;
+    ctl->trace_cap = trace ? trace_cap : 0u;
   }
+  ctl->sh[s] = sh;
   __syncthreads();
   if (s < kg) {
     const uint32_t v = srcs[col0 + s];
     dist[(size_t)v * k + col0 + s] = 0u;
     const uint32_t rs = g.ro[v], re = g.ro[v + 1];
-    // light-first rounds: the light edges form the first frontier, the heavy
-    // ones the first R list
-    const uint32_t le = lh ? w.lend[v] : re;
-    if (le > rs) {
-      if (atomicOr(w.mask[0] + v, 1ull << s) == 0ull) {
-        const unsigned long long b = atomicAdd(&ctl->cnt[0], (1ull << 32) | (le - rs));
-        const uint32_t pos = (uint32_t)(b >> 32);
-        w.fv[0][pos] = v;
-        w.fr[0][pos] = rs;
-        w.fs[0][pos] = (uint32_t)b;
+    if (nb && sh >= t0) {   // parked until the threshold reaches its shift
+      if (re > rs) {
+        if (atomicOr(w.fmask + v, 1ull << s) == 0ull) {
+          const uint32_t pos = atomicAdd(&ctl->fcnt[0], 1u);
+          w.far_v[0][pos] = v;
+        }
+        atomicMin(&ctl->far_min, sh);
       }
-    }
-    if (lh && re > le) {
-      if (atomicOr(w.rmask[0] + v, 1ull << s) == 0ull) {
-        const unsigned long long b = atomicAdd(&ctl->rcnt[0], (1ull << 32) | (re - le));
-        const uint32_t pos = (uint32_t)(b >> 32);
-        w.rv[0][pos] = v;
-        w.rr[0][pos] = le;
-        w.rs[0][pos] = (uint32_t)b;
+    } else {
+      // light-first rounds: the light edges form the first frontier, the heavy
+      // ones the first R list
+      const uint32_t le = lh ? w.lend[v] : re;
+      if (le > rs) {
+        if (atomicOr(w.mask[0] + v, 1ull << s) == 0ull) {
+          const unsigned long long b = atomicAdd(&ctl->cnt[0], (1ull << 32) | (le - rs));
+          const uint32_t pos = (uint32_t)(b >> 32);
+          w.fv[0][pos] = v;
+          w.fr[0][pos] = rs;
+          w.fs[0][pos] = (uint32_t)b;
+        }
+      }
+      if (lh && re > le) {
+        if (nb) atomicAdd(&ctl->heavy_settled, (unsigned long long)(re - le));
+        if (atomicOr(w.rmask[0] + v, 1ull << s) == 0ull) {
+          const unsigned long long b = atomicAdd(&ctl->rcnt[0], (1ull << 32) | (re - le));
+          const uint32_t pos = (uint32_t)(b >> 32);
+          w.rv[0][pos] = v;
+          w.rr[0][pos] = le;
+          w.rs[0][pos] = (uint32_t)b;
+        }
       }
     }
   }
   __syncthreads();
   if (s == 0) {
-    ctl->running = (ctl->cnt[0] != 0ull || ctl->rcnt[0] != 0ull) ? 1u : 0u;
+    const bool work = ctl->cnt[0] != 0ull || ctl->rcnt[0] != 0ull;
+    ctl->running = (work || ctl->fcnt[0] != 0u) ? 1u : 0u;
     if (ctl->cnt[0] == 0ull && ctl->rcnt[0] != 0ull) ctl->mode = 2u;   // sources without light edges
+    if (!work && ctl->fcnt[0] != 0u) {   // every source parked: open the bucket of the nearest
+      ctl->t_prev = 0;
+      ctl->t_cur = ctl->far_min + 1u;
+      ctl->far_min = kInf;
+      ctl->mode = 1u;
+    }
   }
+}
+
+// The vertex of largest out-degree (lowest id on ties) into *best as
+// (degree << 32) | ~v.
+__global__ void k_max_degree(uint32_t n, const uint32_t* __restrict__ ro, unsigned long long* best) {
+  unsigned long long b = 0ull;
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x)
+    b = max(b, ((unsigned long long)(ro[v + 1] - ro[v]) << 32) | (uint32_t)~v);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) b = max(b, __shfl_xor_sync(0xFFFFFFFFu, b, o));
+  if ((threadIdx.x & 31) == 0 && b) atomicMax(best, b);
 }
 
 }  // namespace
@@ -717,6 +935,11 @@ struct BatchWorkspace {
   cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   int grid = 0;
   BatchCtl* h_ctl = nullptr;
+  // normalised buckets: distances from the hub (the highest-degree vertex),
+  // a per-graph index computed by the first call that needs it
+  uint32_t* hubd = nullptr;
+  bool hub_ready = false;
+  uint32_t hub = 0;
 };
 
 // the superstep kernel for the edge format, the row-read mode and the rounds
@@ -736,7 +959,7 @@ static gg_status batch_ws(gg_graph* g, BatchWorkspace** out) {
     BatchWorkspace* w = new BatchWorkspace();
     const size_t n = std::max<uint32_t>(g->n, 1);
     auto r256 = [](size_t b) { return (b + 255) & ~size_t(255); };
-    const size_t total = 20 * r256(4 * n) + 7 * r256(8 * n) + r256(sizeof(BatchCtl));
+    const size_t total = 21 * r256(4 * n) + 7 * r256(8 * n) + r256(sizeof(BatchCtl));
     char* p = nullptr;
     cudaError_t e = cudaMalloc(&p, total);
     if (e != cudaSuccess) { delete w; return cuda_fail(e, "cudaMalloc(batch workspace)"); }
@@ -758,6 +981,8 @@ static gg_status batch_ws(gg_graph* g, BatchWorkspace** out) {
       w->b.rs[i] = reinterpret_cast<uint32_t*>(take(4 * n));
     }
     for (int i = 0; i < 3; ++i) w->b.rmask[i] = reinterpret_cast<unsigned long long*>(take(8 * n));
+    w->hubd = reinterpret_cast<uint32_t*>(take(4 * n));
+    w->b.hubd = w->hubd;
     w->b.ctl = reinterpret_cast<BatchCtl*>(take(sizeof(BatchCtl)));
     if (off != total) { cudaFree(p); delete w; return fail(GG_ERR_INTERNAL, "batch workspace layout"); }
     e = cudaMallocHost(&w->h_ctl, sizeof(BatchCtl));
@@ -794,8 +1019,14 @@ static gg_status batch_exec(gg_graph* g, BatchWorkspace* w, bool vec, bool lh) {
   kp.gridDim = dim3(w->grid);
   kp.blockDim = dim3(kBB);
   kp.kernelParams = args;
-  cudaGraphNode_t knode;
-  GG_CK(cudaGraphAddKernelNode(&knode, cp.conditional.phGraph_out[0], nullptr, 0, &kp));
+  // GG_BATCH_UNROLL supersteps per evaluation of the loop condition; a
+  // superstep that finds the loop ended returns at once and clears it
+  cudaGraphNode_t prev = nullptr;
+  for (int u = 0; u < GG_BATCH_UNROLL; ++u) {
+    cudaGraphNode_t knode;
+    GG_CK(cudaGraphAddKernelNode(&knode, cp.conditional.phGraph_out[0], prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+    prev = knode;
+  }
   GG_CK(cudaGraphInstantiate(&w->exec[vec][lh], graph, 0));
   w->graph[vec][lh] = graph;
   return GG_OK;
@@ -816,12 +1047,36 @@ gg_status batch_run(gg_graph* g, const uint32_t* srcs, uint32_t k, uint32_t* dis
   GG_CK(cudaMemcpyAsync(w->srcs, srcs, sizeof(uint32_t) * k, cudaMemcpyHostToDevice, s));
   // 16-byte row reads need 16-byte aligned rows: k a multiple of 4 and an aligned matrix
   const bool vec = (k % 4u) == 0u && (reinterpret_cast<uintptr_t>(dist) & 15u) == 0u;
-  // light-first rounds with the graph's light/heavy width (skewed graphs, no
-  // explicit bucket width): the light-first edge copy is shared with the
-  // single-source loop and is in place before the rounds' graph is built
-  const bool lh = o.delta == 0 && o.light_heavy != GG_LH_OFF && g->default_delta_lh != GG_DELTA_NONE && g->m > 0;
+  // light-first rounds on graphs with a light/heavy width (skewed graphs,
+  // integer weights): delta 0 takes the graph's width, a delta up to the
+  // largest weight is the width itself.  The light-first edge copy is shared
+  // with the single-source loop and is in place before the rounds' graph runs.
+  const bool lh_graph = o.light_heavy != GG_LH_OFF && g->default_delta_lh != GG_DELTA_NONE && g->m > 0;
+  const uint32_t lh_width = o.delta == 0 ? g->default_delta_lh : o.delta;
+  const bool lh = lh_graph && o.delta != GG_DELTA_NONE && lh_width <= g->wmax;
+  // normalised buckets (the default with light-first rounds): the sources'
+  // distances from the hub align their buckets; computed once per graph, by
+  // the single-source loop with its default options (before the light-first
+  // copy is partitioned for this call's width)
+  const bool nb = lh && o.light_heavy != GG_LH_ROUNDS;
+  if (nb && !w->hub_ready) {
+    unsigned long long* best = w->b.fmask;   // scratch word (the masks are cleared below)
+    GG_CK(cudaMemsetAsync(best, 0, sizeof(unsigned long long), s));
+    k_max_degree<<<std::max(1, std::min<int>((int)((g->n + 255) / 256), device_info().num_sms * 4)), 256, 0, s>>>(
+        g->n, g->ro, best);
+    GG_CK(cudaGetLastError());
+    unsigned long long hb = 0;
+    GG_CK(cudaMemcpyAsync(&hb, best, sizeof(hb), cudaMemcpyDeviceToHost, s));
+    GG_CK(cudaStreamSynchronize(s));
+    w->hub = ~(uint32_t)hb;
+    gg_options ho;
+    gg_options_default(&ho);
+    st = bsp_run(g, w->hub, w->hubd, ho, s, WM_U32);
+    if (st != GG_OK) return st;
+    w->hub_ready = true;
+  }
   if (lh) {
-    st = lh_prepare(g, g->default_delta_lh, s);
+    st = lh_prepare(g, lh_width, s);
     if (st != GG_OK) return st;
     w->b.ledges = g->lhb.edges;
     w->b.lend = g->lhb.lend;
@@ -838,7 +1093,9 @@ gg_status batch_run(gg_graph* g, const uint32_t* srcs, uint32_t k, uint32_t* dis
   // RMAT workloads cost far more edge scans than the buckets saved
   const uint32_t delta = (o.delta == GG_DELTA_NONE || o.delta == 0) ? kInf : o.delta;
   // a light-first round adds at most one heavy superstep per improving vertex
-  const unsigned long long cap = lh ? 3ull * g->n + 16 : delta == kInf ? (unsigned long long)g->n + 2 : 4ull * g->n + 16;
+  const unsigned long long cap = nb ? 8ull * g->n + 64 : lh ? 3ull * g->n + 16
+                                : delta == kInf ? (unsigned long long)g->n + 2 : 4ull * g->n + 16;
+  const uint32_t nb_width = (uint32_t)std::min<uint64_t>((uint64_t)lh_width * GG_NB_WIDTH, kInf - 1u);
   const uint32_t max_iter = o.max_iterations ? o.max_iterations : (cap >= 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)cap);
   for (uint32_t col0 = 0; col0 < k; col0 += 64) {
     const uint32_t kg = std::min<uint32_t>(64, k - col0);
@@ -847,7 +1104,9 @@ gg_status batch_run(gg_graph* g, const uint32_t* srcs, uint32_t k, uint32_t* dis
     GG_CK(cudaMemsetAsync(w->b.fmask, 0, 8 * (size_t)g->n, s));
     if (lh)
       for (int i = 0; i < 3; ++i) GG_CK(cudaMemsetAsync(w->b.rmask[i], 0, 8 * (size_t)g->n, s));
-    k_batch_seed<<<1, 64, 0, s>>>(g->dg, w->b, w->srcs, k, col0, kg, dist, max_iter, lh ? kInf : delta, lh ? 1u : 0u);
+    k_batch_seed<<<1, 64, 0, s>>>(g->dg, w->b, w->srcs, k, col0, kg, dist, max_iter, lh ? kInf : delta, lh ? 1u : 0u,
+                                  nb ? 1u : 0u, nb_width, GG_NB_DRAIN, (unsigned long long)g->lh_heavy_total,
+                                  col0 == 0 ? o.trace : nullptr, o.trace_cap);
     GG_CK(cudaGetLastError());
     if (o.policy == GG_POLICY_BSP_HOST) {
       // supersteps launched one by one, the loop flag read back after each

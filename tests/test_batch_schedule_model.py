@@ -1,12 +1,24 @@
-"""CPU model of the batched light-first rounds, checked against the oracle.
+"""CPU models of the batched schedules, checked against the oracle.
 
-k sources share one loop with no distance threshold: a (source, vertex) pair
-that improves joins the next light frontier (its light edges) and the current
-epoch's R mask (its heavy edges); when the light frontier is empty, one heavy
-superstep relaxes the heavy edges of the R pairs, and its improvements start
-the next epoch.  The model takes these steps in this order (synchronous
-relaxation per superstep) and must reach the oracle's distances for every
-source.  No GPU is involved.
+Light-first rounds (``rounds``): k sources share one loop with no distance
+threshold: a (source, vertex) pair that improves joins the next light
+frontier (its light edges) and the current epoch's R mask (its heavy edges);
+when the light frontier is empty, one heavy superstep relaxes the heavy edges
+of the R pairs, and its improvements start the next epoch.
+
+Normalised buckets (``normalised_buckets``, the default batched schedule on
+skewed graphs): the same light/heavy rounds inside one shared bucket
+threshold T over shifted distances dist[s][v] + sh[s], sh[s] = max o - o_s
+with o_s the source's distance from the hub.  Pairs at or above T are parked;
+when no near pair and no R pair is left, T rises to max(T + width, smallest
+parked shifted distance + 1) and a split moves the parked pairs below it into
+the frontier; once the pairs not yet settled hold fewer than 1/drain of the
+heavy edges (counted per pair when it first joins an R mask), T becomes
+infinite and the rest is plain push over all edges.
+
+The models take these steps in this order (synchronous relaxation per
+superstep) and must reach the oracle's distances for every source, whatever
+the offsets.  No GPU is involved.
 """
 import numpy as np
 import pytest
@@ -73,6 +85,122 @@ def rounds(ro, col, w, srcs, delta):
     return np.where(dist >= BIG, INF32, dist).astype(np.uint32), light, heavy
 
 
+def normalised_buckets(ro, col, w, srcs, delta, offs, width=None, drain=8, mistake=None):
+    """(k, n) distances, supersteps and splits of the normalised-bucket
+    schedule.  mistake (for the pin-strength test only) plants one error:
+    "split_floor" drops the pairs at exactly the previous threshold,
+    "split_no_r" leaves the pairs a split releases out of the R mask,
+    "tail_light" gives the tail light rows only."""
+    ro = np.asarray(ro, np.int64)
+    n, k = ro.size - 1, len(srcs)
+    width = delta if width is None else width
+    deg = np.diff(ro)
+    rowid = np.repeat(np.arange(n), deg)
+    w = np.asarray(w, np.int64)
+    order = np.lexsort((w >= delta, rowid))
+    c2 = np.asarray(col, np.int64)[order]
+    w2 = w[order]
+    nl = np.bincount(rowid, weights=(w < delta), minlength=n).astype(np.int64)
+    lend = ro[:-1] + nl
+    ldeg, hdeg = nl, deg - nl
+    offs = np.where(np.asarray(offs, np.int64) >= INF32, 0, np.asarray(offs, np.int64))
+    sh = offs.max() - offs
+    heavy_k = int(hdeg.sum()) * k
+    dist = np.full((k, n), BIG)
+    F = np.zeros((k, n), bool)
+    R = np.zeros((k, n), bool)
+    far = np.zeros((k, n), bool)
+    T, tprev, tail, settled, steps, splits = width, 0, False, 0, 0, 0
+    for s, v in enumerate(srcs):
+        dist[s, v] = 0
+        if deg[v] == 0:
+            continue
+        if sh[s] >= T:
+            far[s, v] = True
+        else:
+            F[s, v] |= ldeg[v] > 0
+            if hdeg[v] > 0:
+                settled += int(hdeg[v])
+                R[s, v] = True
+
+    def relax(S, lo, hi):
+        imp = np.zeros((k, n), bool)
+        for s in range(k):
+            us = np.flatnonzero(S[s])
+            cnt = hi[us] - lo[us]
+            tot = int(cnt.sum())
+            if tot == 0:
+                continue
+            own = np.repeat(us, cnt)
+            e = np.repeat(lo[us] - np.concatenate(([0], np.cumsum(cnt)[:-1])), cnt) + np.arange(tot)
+            best = np.full(n, BIG)
+            np.minimum.at(best, c2[e], dist[s, own] + w2[e])
+            better = best < dist[s]
+            dist[s, better] = best[better]
+            imp[s] = better
+        return imp
+
+    def place(imp):
+        nonlocal settled
+        if tail:
+            return imp & (deg > 0), np.zeros_like(imp)
+        near = imp & (dist + sh[:, None] < T)
+        newr = near & (hdeg > 0) & ~R
+        settled += int((newr * hdeg[None, :]).sum())
+        far_new = imp & ~near & (deg > 0)
+        return near, far_new
+
+    if not F.any() and not R.any() and far.any():          # every source parked
+        T = int((dist + sh[:, None])[far].min()) + 1
+        F = np.zeros((k, n), bool)
+        split_due = True
+    else:
+        split_due = False
+    while True:
+        if split_due:
+            splits += 1
+            steps += 1
+            shifted = dist + sh[:, None]
+            mv = far & ((shifted > tprev) if mistake == "split_floor" else (shifted >= tprev)) & (shifted < T)
+            keep = far & (shifted >= T)
+            far = keep
+            if tail:
+                F = mv & (deg > 0)
+            else:
+                F = mv & (ldeg > 0)
+                newr = mv & (hdeg > 0) & ~R
+                settled += int((newr * hdeg[None, :]).sum())
+                if mistake != "split_no_r":
+                    R |= mv & (hdeg > 0)
+            split_due = False
+        elif F.any():
+            steps += 1
+            imp = relax(F, ro[:-1], ro[1:] if (tail and mistake != "tail_light") else lend)
+            near, fnew = place(imp)
+            far |= fnew
+            F = near & ((deg > 0) if tail else (ldeg > 0))
+            if not tail:
+                R |= near & (hdeg > 0)
+        elif R.any():
+            steps += 1
+            imp = relax(R, lend, ro[1:])
+            R = np.zeros((k, n), bool)
+            near, fnew = place(imp)
+            far |= fnew
+            F = near & (ldeg > 0)
+            R = near & (hdeg > 0)
+        elif far.any():
+            shifted = dist + sh[:, None]
+            tn = max(T + width, int(shifted[far].min()) + 1)
+            if tail or heavy_k - settled < heavy_k // drain:
+                tail, tn = True, None
+            tprev, T = T, (BIG if tn is None else tn)
+            split_due = True
+        else:
+            break
+    return np.where(dist >= BIG, INF32, dist).astype(np.uint32), steps, splits
+
+
 @pytest.mark.parametrize("scale,delta,k", [(10, 12, 16), (11, 14, 9), (11, 60, 5)])
 def test_rmat_rounds_match_oracle(scale, delta, k):
     ro, col, w = graphgen.rmat(scale, 16, seed=scale, W=255)
@@ -95,3 +223,51 @@ def test_directed_sinks_zero_weights_and_heavy_only_sources(seed):
     for delta in (1, 20, 79):
         got, _, _ = rounds(ro, col, w, srcs, delta)
         np.testing.assert_array_equal(got, oracle.dijkstra_many(ro, col, w, srcs), err_msg=f"delta={delta}")
+
+
+@pytest.mark.parametrize("scale,delta,k,width,drain", [(10, 12, 16, None, 8), (11, 14, 9, None, 2),
+                                                       (11, 20, 64, 40, 8), (12, 12, 33, None, 1000)])
+def test_normalised_buckets_match_oracle(scale, delta, k, width, drain):
+    """Hub offsets from the oracle's own Dijkstra (the kernel takes them from
+    its single-source run): every source's distances equal the oracle's."""
+    ro, col, w = graphgen.rmat(scale, 16, seed=scale + 1, W=255)
+    srcs = graphgen.sample_sources(ro, k, seed=5)
+    hub = int(np.argmax(np.diff(ro.astype(np.int64))))
+    offs = oracle.dijkstra(ro, col, w, hub)[srcs]
+    got, steps, splits = normalised_buckets(ro, col, w, srcs, delta, offs, width, drain)
+    np.testing.assert_array_equal(got, oracle.dijkstra_many(ro, col, w, srcs))
+    assert splits >= 1
+
+
+def test_normalised_buckets_any_offsets_directed_sinks_zero_weights():
+    """Offsets change only the order of the relaxations: random offsets, a
+    directed graph with sinks and zero weights, a sink source, a heavy-only
+    source and a repeated one still give the oracle's distances."""
+    rng = np.random.Generator(np.random.PCG64(4))
+    n, m = 2500, 30000
+    src = rng.integers(0, 2000, m)
+    ro, col, w = graphgen.from_edges(n, src, rng.integers(0, n, m), rng.integers(0, 80, m))
+    hv = 11
+    w = w.copy()
+    w[ro[hv]:ro[hv + 1]] = 79
+    srcs = np.array([hv, 0, 2499, 1234, hv, 77], np.uint32)
+    for trial, delta in enumerate((1, 20, 79)):
+        offs = rng.integers(0, 300, srcs.size)
+        offs[trial] = INF32                      # a source the hub does not reach: offset 0
+        got, _, _ = normalised_buckets(ro, col, w, srcs, delta, offs)
+        np.testing.assert_array_equal(got, oracle.dijkstra_many(ro, col, w, srcs), err_msg=f"delta={delta}")
+
+
+@pytest.mark.parametrize("mistake", ["split_floor", "split_no_r", "tail_light"])
+def test_normalised_buckets_planted_mistakes_fail(mistake):
+    """Each planted mistake in the split or the tail makes the model miss
+    distances on the same inputs where the correct model matches."""
+    ro, col, w = graphgen.rmat(11, 16, seed=11, W=255)
+    srcs = graphgen.sample_sources(ro, 24, seed=5)
+    hub = int(np.argmax(np.diff(ro.astype(np.int64))))
+    offs = oracle.dijkstra(ro, col, w, hub)[srcs]
+    ref = oracle.dijkstra_many(ro, col, w, srcs)
+    got, _, _ = normalised_buckets(ro, col, w, srcs, 12, offs)
+    np.testing.assert_array_equal(got, ref)
+    bad, _, _ = normalised_buckets(ro, col, w, srcs, 12, offs, mistake=mistake)
+    assert not np.array_equal(bad, ref)
