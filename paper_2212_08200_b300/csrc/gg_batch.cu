@@ -67,6 +67,12 @@ struct BatchCtl {
   uint32_t nb, tail, width, drain_div;
   uint32_t* trace;      // optional: per superstep (kind | tail << 4, entries, edges, next frontier size)
   uint32_t trace_cap;
+  // heavy superstep by pull (mode 4; symmetric graphs, bucket width <= the
+  // light/heavy width): chosen when the pairs settled since the last heavy
+  // superstep hold more heavy edges than the pairs not yet settled
+  uint32_t pull_ok;
+  unsigned long long settled_mark;   // heavy_settled at the last heavy superstep
+  unsigned long long pull_edges;     // heavy edges the pull scanned (statistics)
   unsigned long long heavy_total_k;   // heavy edges of the graph x sources of the group
   unsigned long long heavy_settled;   // heavy edges of the pairs that settled into a bucket
   uint32_t sh[64];
@@ -106,6 +112,9 @@ static_assert(kBNW * kBQW <= (uint32_t)kBCap, "per-warp queues fit the CTA queue
 #endif
 #ifndef GG_NB_DRAIN
 #define GG_NB_DRAIN 8   // normalised buckets end once the unsettled pairs hold < 1/GG_NB_DRAIN of the heavy edges
+#endif
+#ifndef GG_BATCH_PULL
+#define GG_BATCH_PULL 1   // normalised buckets: heavy supersteps by pull on symmetric graphs
 #endif
 #ifndef GG_BATCH_UNROLL
 #define GG_BATCH_UNROLL 4   // superstep kernels per iteration of the batch's CUDA-graph loop
@@ -202,7 +211,8 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
   const uint32_t pc = it % 3, pn = (it + 1) % 3, po = (it + 2) % 3;
   const uint32_t bmode0 = ctl->mode;
   const uint32_t ep = LH ? ctl->epoch : 0u;
-  const bool heavy = LH && bmode0 == 2u;
+  const bool pull = LH && bmode0 == 4u;   // heavy superstep by pull (normalised buckets)
+  const bool heavy = LH && (bmode0 == 2u || pull);
   const unsigned long long c = heavy ? ctl->rcnt[ep % 3] : ctl->cnt[pc];
   const uint32_t F = (uint32_t)(c >> 32), E = (uint32_t)c;
   const uint32_t K = ctl->k, col0 = ctl->col0;
@@ -243,7 +253,107 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
   }
   __syncthreads();
   bool ovf = false;
-  if (bmode == 3) {
+  if (pull) {
+    // Heavy superstep by pull (symmetric graphs: the heavy in-edges of v are
+    // its heavy out-edges): every vertex with an unsettled pair (dist[v][s]
+    // at or above its source's threshold) takes, for each such source, the
+    // minimum of dist[u][s] + w over its heavy edges (u, w) from the pairs of
+    // the epoch's R masks.  One vertex per warp, lane l holds sources l and
+    // l + 32; four edges' distance rows in flight at a time.  A settled pair
+    // is never written and an unsettled one is only written by its own
+    // vertex's warp, so no atomics on dist.  With the bucket no wider than
+    // the light/heavy width every improvement is at or above the threshold:
+    // it is parked (far mask and list).
+    const unsigned FULL = 0xFFFFFFFFu;
+    const unsigned long long* Rm = pick3(w.rmask, ep % 3);
+    const uint32_t kgv = ctl->kg;
+    const bool vlo = lane < kgv, vhi = lane + 32 < kgv;
+    const uint32_t tc_lo = sm.tabs[lane], tc_hi = sm.tabs[lane + 32];
+    const uint32_t sh_lo = sm.shs[lane], sh_hi = sm.shs[lane + 32];
+    uint32_t* fq = sm.qd + warp * kBQW;
+    uint32_t fqn = 0;   // warp-uniform
+    uint32_t wfm = kInf;
+    unsigned long long scanned = 0ull;
+    auto ffl = [&]() {
+      __syncwarp();
+      uint32_t pos = 0;
+      if (lane == 0) pos = atomicAdd(&ctl->fcnt[fsel], fqn);
+      pos = __shfl_sync(FULL, pos, 0);
+      for (uint32_t j = lane; j < fqn; j += 32) pick2(w.far_v, fsel)[pos + j] = fq[j];
+      fqn = 0;
+      __syncwarp();
+    };
+    const uint32_t nwarps = gridDim.x * kBNW;
+    for (uint32_t v = blockIdx.x * kBNW + warp; v < g.n; v += nwarps) {   // warp-uniform
+      const uint32_t hs = __ldg(w.lend + v), he = __ldg(g.ro + v + 1);
+      if (hs >= he) continue;
+      uint32_t* vrow = dist + (size_t)v * K + col0;
+      const uint32_t dlo = vlo ? ld_cg(vrow + lane) : 0u, dhi = vhi ? ld_cg(vrow + lane + 32) : 0u;
+      const unsigned Ulo = __ballot_sync(FULL, vlo && dlo >= tc_lo), Uhi = __ballot_sync(FULL, vhi && dhi >= tc_hi);
+      if ((Ulo | Uhi) == 0u) continue;
+      const unsigned long long U = ((unsigned long long)Uhi << 32) | Ulo;
+      scanned += he - hs;
+      uint32_t clo = dlo, chi = dhi;
+      for (uint32_t e0 = hs; e0 < he; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        uint32_t u = 0, wt = 0;
+        unsigned long long r = 0ull;
+        if (e < he) {
+          const uint2 ed = load_edge<PK>(w.ledges, e, wbits);
+          u = ed.x;
+          wt = ed.y;
+          r = __ldcg(Rm + u) & U;
+        }
+        unsigned rb = __ballot_sync(FULL, r != 0ull);
+        while (rb) {   // warp-uniform
+          uint32_t xl[4], xh[4], ww[4];
+          bool bl[4], bh[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const bool have = rb != 0u;
+            const uint32_t j = have ? (uint32_t)(__ffs(rb) - 1) : 0u;
+            rb &= rb - 1u;
+            const uint32_t uj = __shfl_sync(FULL, u, j);
+            ww[q] = __shfl_sync(FULL, wt, j);
+            const uint32_t rl = __shfl_sync(FULL, (uint32_t)r, j), rh = __shfl_sync(FULL, (uint32_t)(r >> 32), j);
+            bl[q] = have && ((rl >> lane) & 1u);
+            bh[q] = have && ((rh >> lane) & 1u);
+            const uint32_t* urow = dist + (size_t)uj * K + col0;
+            xl[q] = bl[q] ? ld_cg(urow + lane) : 0u;
+            xh[q] = bh[q] ? ld_cg(urow + lane + 32) : 0u;
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (bl[q]) clo = min(clo, add_sat(xl[q], ww[q], ovf));
+            if (bh[q]) chi = min(chi, add_sat(xh[q], ww[q], ovf));
+          }
+        }
+      }
+      const bool il = clo < dlo, ih = chi < dhi;
+      if (il) {
+        vrow[lane] = clo;
+        wfm = min(wfm, (uint32_t)min(0xFFFFFFFFull, (unsigned long long)clo + sh_lo));
+      }
+      if (ih) {
+        vrow[lane + 32] = chi;
+        wfm = min(wfm, (uint32_t)min(0xFFFFFFFFull, (unsigned long long)chi + sh_hi));
+      }
+      const unsigned Il = __ballot_sync(FULL, il), Ih = __ballot_sync(FULL, ih);
+      if (Il | Ih) {   // park the improved pairs
+        bool fapp = false;
+        if (lane == 0) fapp = atomicOr(w.fmask + v, ((unsigned long long)Ih << 32) | Il) == 0ull;
+        if (__shfl_sync(FULL, fapp, 0)) {
+          if (lane == 0) fq[fqn] = v;
+          if (++fqn == kBQW) ffl();
+        }
+      }
+    }
+    if (fqn) ffl();
+#pragma unroll
+    for (int o = 16; o; o >>= 1) wfm = min(wfm, __shfl_xor_sync(FULL, wfm, o));
+    if (lane == 0 && wfm != kInf) atomicMin(&ctl->far_min, wfm);
+    if (lane == 0 && scanned) atomicAdd(&ctl->pull_edges, scanned);
+  } else if (bmode == 3) {
     // before the tail's split: clear the three frontier mask arrays.  A vertex
     // without light edges may hold mask bits that no frontier list carries
     // (nothing clears them), which would keep it out of the tail's frontier.
@@ -685,7 +795,11 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
       t[2] = E;
       t[3] = fn;
     }
-    if (F > 0 && bmode == 0) {
+    if (pull) {
+      ctl->edges_scanned += ctl->pull_edges;
+      ctl->pull_edges = 0ull;
+      ctl->frontier_total += F;
+    } else if (F > 0 && bmode == 0) {
       ctl->edges_scanned += E;
       ctl->frontier_total += F;
       ctl->max_frontier = max(ctl->max_frontier, F);
@@ -715,6 +829,15 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
           ctl->splits += 1;
         }
         const uint32_t nfar = atomicAdd(&ctl->fcnt[fs_now], 0u);
+        if (mode_next == 2u && fn == 0 && rn > 0) {
+          // heavy superstep: pull when the pairs settled since the last one
+          // hold more heavy edges than the pairs not settled yet
+          const unsigned long long done = atomicAdd(&ctl->heavy_settled, 0ull);
+          const unsigned long long hk = ctl->heavy_total_k;
+          const unsigned long long open = hk > done ? hk - done : 0ull;
+          if (ctl->pull_ok && done - ctl->settled_mark > open) mode_next = 4u;
+          ctl->settled_mark = done;
+        }
         if (bmode == 3) {   // masks cleared: the tail's split follows
           mode_next = 1u;
           more = true;
@@ -803,7 +926,7 @@ __global__ void k_batch_fill(uint32_t* dist, unsigned long long count) {
 __global__ void k_batch_seed(DevGraph g, BatchBufs w, const uint32_t* srcs, uint32_t k, uint32_t col0,
                              uint32_t kg, uint32_t* dist, uint32_t max_iter, uint32_t delta, uint32_t lh,
                              uint32_t nb, uint32_t width, uint32_t drain_div, unsigned long long heavy_total,
-                             uint32_t* trace, uint32_t trace_cap) {
+                             uint32_t* trace, uint32_t trace_cap, uint32_t pull_ok) {
   __shared__ uint32_t so[64];
   BatchCtl* ctl = w.ctl;
   const uint32_t s = threadIdx.x;
@@ -857,6 +980,9 @@ __global__ void k_batch_seed(DevGraph g, BatchBufs w, const uint32_t* srcs, uint
     ctl->heavy_settled = 0ull;
     ctl->trace = trace;
     ctl->trace_cap = trace ? trace_cap : 0u;
+    ctl->pull_ok = pull_ok;
+    ctl->settled_mark = 0ull;
+    ctl->pull_edges = 0ull;
   }
   ctl->sh[s] = sh;
   __syncthreads();
@@ -1106,7 +1232,8 @@ gg_status batch_run(gg_graph* g, const uint32_t* srcs, uint32_t k, uint32_t* dis
       for (int i = 0; i < 3; ++i) GG_CK(cudaMemsetAsync(w->b.rmask[i], 0, 8 * (size_t)g->n, s));
     k_batch_seed<<<1, 64, 0, s>>>(g->dg, w->b, w->srcs, k, col0, kg, dist, max_iter, lh ? kInf : delta, lh ? 1u : 0u,
                                   nb ? 1u : 0u, nb_width, GG_NB_DRAIN, (unsigned long long)g->lh_heavy_total,
-                                  col0 == 0 ? o.trace : nullptr, o.trace_cap);
+                                  col0 == 0 ? o.trace : nullptr, o.trace_cap,
+                                  (nb && g->symmetric && GG_BATCH_PULL && nb_width <= lh_width) ? 1u : 0u);
     GG_CK(cudaGetLastError());
     if (o.policy == GG_POLICY_BSP_HOST) {
       // supersteps launched one by one, the loop flag read back after each

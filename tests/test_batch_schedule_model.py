@@ -85,12 +85,13 @@ def rounds(ro, col, w, srcs, delta):
     return np.where(dist >= BIG, INF32, dist).astype(np.uint32), light, heavy
 
 
-def normalised_buckets(ro, col, w, srcs, delta, offs, width=None, drain=8, mistake=None):
+def normalised_buckets(ro, col, w, srcs, delta, offs, width=None, drain=8, mistake=None, pull=False):
     """(k, n) distances, supersteps and splits of the normalised-bucket
     schedule.  mistake (for the pin-strength test only) plants one error:
     "split_floor" drops the pairs at exactly the previous threshold,
     "split_no_r" leaves the pairs a split releases out of the R mask,
-    "tail_light" gives the tail light rows only."""
+    "tail_light" gives the tail light rows only.  pull: heavy supersteps
+    update only the pairs not yet settled (as the kernel's pull does)."""
     ro = np.asarray(ro, np.int64)
     n, k = ro.size - 1, len(srcs)
     width = delta if width is None else width
@@ -183,7 +184,16 @@ def normalised_buckets(ro, col, w, srcs, delta, offs, width=None, drain=8, mista
                 R |= near & (hdeg > 0)
         elif R.any():
             steps += 1
-            imp = relax(R, lend, ro[1:])
+            if pull:
+                # the heavy superstep by pull writes only the pairs not yet
+                # settled (shifted distance at or above the threshold)
+                keep = dist.copy()
+                open_ = dist + sh[:, None] >= T
+                imp = relax(R, lend, ro[1:])
+                dist[:] = np.where(open_, dist, keep)
+                imp &= open_
+            else:
+                imp = relax(R, lend, ro[1:])
             R = np.zeros((k, n), bool)
             near, fnew = place(imp)
             far |= fnew
@@ -225,16 +235,17 @@ def test_directed_sinks_zero_weights_and_heavy_only_sources(seed):
         np.testing.assert_array_equal(got, oracle.dijkstra_many(ro, col, w, srcs), err_msg=f"delta={delta}")
 
 
-@pytest.mark.parametrize("scale,delta,k,width,drain", [(10, 12, 16, None, 8), (11, 14, 9, None, 2),
-                                                       (11, 20, 64, 40, 8), (12, 12, 33, None, 1000)])
-def test_normalised_buckets_match_oracle(scale, delta, k, width, drain):
+@pytest.mark.parametrize("scale,delta,k,width,drain,pull", [(10, 12, 16, None, 8, False), (11, 14, 9, None, 2, False),
+                                                            (11, 20, 64, 40, 8, False), (12, 12, 33, None, 1000, False),
+                                                            (10, 12, 16, None, 8, True), (12, 12, 33, None, 1000, True)])
+def test_normalised_buckets_match_oracle(scale, delta, k, width, drain, pull):
     """Hub offsets from the oracle's own Dijkstra (the kernel takes them from
     its single-source run): every source's distances equal the oracle's."""
     ro, col, w = graphgen.rmat(scale, 16, seed=scale + 1, W=255)
     srcs = graphgen.sample_sources(ro, k, seed=5)
     hub = int(np.argmax(np.diff(ro.astype(np.int64))))
     offs = oracle.dijkstra(ro, col, w, hub)[srcs]
-    got, steps, splits = normalised_buckets(ro, col, w, srcs, delta, offs, width, drain)
+    got, steps, splits = normalised_buckets(ro, col, w, srcs, delta, offs, width, drain, pull=pull)
     np.testing.assert_array_equal(got, oracle.dijkstra_many(ro, col, w, srcs))
     assert splits >= 1
 
