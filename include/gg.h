@@ -252,6 +252,36 @@ gg_status gg_sssp_ex(gg_graph_t g, uint32_t src, uint32_t* dist_out, const gg_op
 gg_status gg_bfs(gg_graph_t g, uint32_t src, uint32_t* depth_out, cudaStream_t stream);
 gg_status gg_bfs_ex(gg_graph_t g, uint32_t src, uint32_t* depth_out, const gg_options* opt, cudaStream_t stream);
 
+/* ---- an edge-frontier program: the shortest-path DAG and predecessors ---- */
+
+/* Sec. III-C lets a frontier hold edges and the operator apply the user's
+ * program to each {source, destination, edge}.  This program runs two
+ * operators over the graph and a distance vector from src:
+ *   advance + filter  every out-edge (u, v, w) of every reached vertex u is
+ *                     tested and joins the output edge frontier when it is
+ *                     tight, dist[u] + w == dist[v] (exact 64-bit sum): the
+ *                     edges that lie on some shortest path from src;
+ *   edge operator     over that edge frontier, parent[v] = min(parent[v], u).
+ *   src          < n; dist: device u32[n], the distances from src (for
+ *                example gg_sssp's output; GG_INF = unreached)
+ *   parent_out   device u32[n], caller-owned: parent[src] = src; for every
+ *                other reached vertex the smallest u with a tight edge
+ *                (u, v) (GG_INF if dist admits none); GG_INF for unreached
+ *                vertices.  With zero-weight edges the parent map may hold
+ *                cycles among vertices of equal distance.
+ *   tight_out    device u32[tight_cap] or NULL: receives up to tight_cap
+ *                tight edges as positions in the CSR (edge ids), in no
+ *                particular order
+ *   tight_count  host, optional: the number of tight edges (may exceed
+ *                tight_cap)
+ * Synchronous on `stream` (orders after the handle's last call).  The edge
+ * frontier takes up to 8 bytes per edge of temporary device memory (4 when
+ * tight_cap >= m).  Integer-weight graphs only (GG_ERR_NOT_SUPPORTED for
+ * GG_FLOAT_WEIGHTS).  Errors: GG_ERR_INVALID_ARG (NULLs, src >= n,
+ * tight_cap > 0 with tight_out NULL), GG_ERR_OUT_OF_MEMORY, GG_ERR_CUDA. */
+gg_status gg_sssp_tree(gg_graph_t g, uint32_t src, const uint32_t* dist, uint32_t* parent_out,
+                       uint32_t* tight_out, uint64_t tight_cap, uint64_t* tight_count, cudaStream_t stream);
+
 /* ---- autotuning ----------------------------------------------------------- */
 
 /* Picks the fastest single-source options for this graph (Sec. IV-C leaves
@@ -384,7 +414,7 @@ typedef struct {
 typedef struct {
     uint64_t submitted, completed;
     uint64_t launches;               /* superstep-graph launches by the worker            */
-    uint64_t vertex_budget;          /* in-flight vertex budget in force                  */
+    uint64_t vertex_budget;          /* in-flight vertex budget of the last admission round */
     uint32_t queued, running, max_running;
     uint32_t reserved;
     double p50_us, p99_us, mean_us, max_us;   /* submit -> completion latency           */
@@ -397,11 +427,15 @@ void gg_server_config_default(gg_server_config* cfg);
  * in-flight vertex budget allows; advance every in-flight query by up to
  * supersteps_per_launch supersteps in one CUDA-graph launch; retire the
  * queries whose frontier emptied}.  Queries arriving while others run join
- * the running union frontier at the next admission round.  The in-flight
- * budget is sized from the free HBM at creation (16 bytes of frontier state
+ * the running union frontier at the next admission round.  The engine's
+ * capacity is sized from the free HBM at creation (16 bytes of frontier state
  * per vertex, plus per slot three bitmaps and two far piles of
  * max_graph_vertices entries); GG_ERR_OUT_OF_MEMORY if even one graph does
- * not fit.  max_slots <= 1024. */
+ * not fit.  Admission then follows the free HBM live: at every admission
+ * round the budget in force is min(capacity, vertices in flight +
+ * (free HBM - hbm_reserve_bytes) / 32), so when other allocations leave
+ * less than the reserve free, queued queries wait (in-flight ones finish)
+ * until memory is released.  max_slots <= 1024. */
 gg_status gg_server_create(const gg_server_config* cfg, gg_server_t* out);
 
 /* Queues the query (graph g, source src) whose distances go to dist_out

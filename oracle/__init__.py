@@ -16,7 +16,9 @@ Dijkstra (``dijkstra``), and pinned against independent algorithms and
 closed forms in ``tests/test_oracle_pins.py``: Floyd-Warshall brute force
 (``floyd_warshall``), BFS hop counts for unit weights (``bfs_hops``),
 Bellman-Ford rounds (``bellman_ford``), grid/path/star closed forms and the
-shortest-path invariants (``check``).
+shortest-path invariants (``check``).  ``sp_tree`` is the edge-frontier
+program on a distance vector: the tight edges and the smallest tight
+predecessor of each vertex.
 
 The paper's own float variant is ``dijkstra_f32`` (and ``bellman_ford_f32``):
 binary32 weights, one rounded single-precision addition per relaxation,
@@ -85,6 +87,8 @@ def _load():
             lib.oracle_dijkstra_f32.argtypes = [u32, P, P, P, u32, P]
             lib.oracle_bellman_ford_f32.restype = ctypes.c_int
             lib.oracle_bellman_ford_f32.argtypes = [u32, P, P, P, u32, P, P]
+            lib.oracle_sp_tree.restype = ctypes.c_int
+            lib.oracle_sp_tree.argtypes = [u32, P, P, P, u32, P, P, ctypes.POINTER(ctypes.c_ubyte)]
             lib.oracle_dijkstra_many.restype = ctypes.c_int
             lib.oracle_dijkstra_many.argtypes = [u32, P, P, P, P, u32, P, u32]
             _lib = lib
@@ -206,6 +210,21 @@ def check(ro, col, w, src: int, dist):
     bad = ctypes.c_uint32(0)
     rc = _load().oracle_check(n, _p(ro), _p(col), _p(w), src, _p(dist), ctypes.byref(bad))
     return int(rc), int(bad.value)
+
+
+def sp_tree(ro, col, w, src: int, dist):
+    """The edge-frontier program on a distance vector: (parent, tight) with
+    tight a bool per edge (dist[u] + w == dist[v], dist[u] finite) and
+    parent[v] the smallest u over v's tight in-edges (parent[src] = src,
+    INF when there is none)."""
+    n, ro, col, w = _graph(ro, col, w)
+    dist = _u32(dist)
+    parent = np.empty(n, np.uint32)
+    tight = np.zeros(max(col.shape[0], 1), np.uint8)
+    _rc(_load().oracle_sp_tree(n, _p(ro), _p(col), _p(w), src, _p(dist), _p(parent),
+                               tight.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))))
+    m = int(ro[-1])
+    return parent, tight[:m].astype(bool)
 
 
 def traversed_edges(ro, dist) -> int:

@@ -28,7 +28,11 @@
  *                         (a different algorithm for cross-checks);
  *   oracle_bfs_hops       queue BFS hop counts (the unit-weight special case);
  *   oracle_check          the invariants that characterise shortest-path
- *                         distances for positive weights.
+ *                         distances for positive weights;
+ *   oracle_sp_tree        the edge-frontier program: the tight edges
+ *                         (dist[u] + w == dist[v], the edges on some shortest
+ *                         path) and, per vertex, the smallest tight
+ *                         predecessor.
  *
  * The paper's own listing keeps float weights and distances, initialised to
  * the largest float (Listings 1 and 4).  That variant is here too:
@@ -406,6 +410,31 @@ OR_EXPORT int oracle_check(uint32_t n, const uint32_t* row_offsets, const uint32
     }
     free(tight); free(hops);
     return rc;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Shortest-path DAG from a distance vector (the edge-frontier program of    */
+/* Sec. III-C: an operator over the frontier of tight edges).  An edge       */
+/* (u, v, w) with dist[u] finite is tight when dist[u] + w == dist[v],        */
+/* summed in uint64; tight[e] = 1 for those edges, 0 otherwise.  parent[src] */
+/* = src; every other vertex gets the smallest u over its tight in-edges, or */
+/* OR_INF32 when it has none (every unreached vertex).                       */
+/* ------------------------------------------------------------------------- */
+OR_EXPORT int oracle_sp_tree(uint32_t n, const uint32_t* row_offsets, const uint32_t* cols,
+                             const uint32_t* weights, uint32_t src, const uint32_t* dist,
+                             uint32_t* parent, unsigned char* tight) {
+    if (src >= n) return ORACLE_ERR_ARG;
+    for (uint32_t v = 0; v < n; ++v) parent[v] = OR_INF32;
+    parent[src] = src;
+    for (uint32_t u = 0; u < n; ++u) {
+        for (uint32_t e = row_offsets[u]; e < row_offsets[u + 1]; ++e) {
+            const uint32_t v = cols[e];
+            const int t = dist[u] != OR_INF32 && (uint64_t)dist[u] + weights[e] == (uint64_t)dist[v];
+            tight[e] = (unsigned char)t;
+            if (t && v != src && u < parent[v]) parent[v] = u;
+        }
+    }
+    return ORACLE_OK;
 }
 
 /* ------------------------------------------------------------------------- */

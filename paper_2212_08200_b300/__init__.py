@@ -24,7 +24,7 @@ __all__ = [
     "GG_LH_AUTO", "GG_LH_OFF", "GG_LH_ROUNDS",
     "gg_graph_create_csr", "gg_graph_destroy", "gg_graph_info", "gg_graph_check", "gg_sssp", "gg_sssp_ex",
     "gg_bfs", "gg_bfs_ex", "GG_FLOAT_WEIGHTS", "GG_FLT_MAX_BITS",
-    "gg_sssp_batch", "gg_sssp_multi", "Server",
+    "gg_sssp_batch", "gg_sssp_multi", "gg_sssp_tree", "Server",
     "gg_status_string", "gg_last_error", "gg_abi_version", "gg_sssp_noalloc", "GG_NOALLOC_MAX_VERTICES",
     "Graph", "lib_path", "load",
 ]
@@ -134,6 +134,7 @@ def load():
                                            ctypes.POINTER(ctypes.c_float), vp]),
             "gg_autotune_batch": (ctypes.c_int, [vp, P32, u32, vp, ctypes.POINTER(gg_options),
                                                  ctypes.POINTER(ctypes.c_float), vp]),
+            "gg_sssp_tree": (ctypes.c_int, [vp, u32, vp, vp, vp, u64, ctypes.POINTER(u64), vp]),
             "gg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "gg_last_error": (ctypes.c_char_p, []),
             "gg_abi_version": (u32, []),
@@ -309,6 +310,26 @@ def gg_sssp_multi(handles, srcs, dist_outs, stream=None, delta: int | None = Non
         _check(load().gg_sssp_multi(hs, spp, k, dp, _stream_ptr(stream)), "gg_sssp_multi")
     else:
         _check(load().gg_sssp_multi_ex(hs, spp, k, dp, delta, _stream_ptr(stream)), "gg_sssp_multi_ex")
+
+
+def gg_sssp_tree(handle: int, src: int, dist, parent_out, tight_out=None, stream=None) -> int:
+    """The edge-frontier program: parent_out (CUDA uint32 tensor of n) gets
+    each reached vertex's smallest tight predecessor, tight_out (optional
+    CUDA uint32 tensor) the tight edges' CSR positions; returns the number of
+    tight edges.  Synchronous."""
+    ptrs = [_ptr(a) for a in (dist, parent_out)]
+    if not all(dev for _, dev in ptrs):
+        raise ValueError("dist and parent_out must be CUDA tensors")
+    tp, cap = None, 0
+    if tight_out is not None:
+        p, dev = _ptr(tight_out)
+        if not dev:
+            raise ValueError("tight_out must be a CUDA tensor")
+        tp, cap = p, int(tight_out.numel())
+    cnt = ctypes.c_uint64()
+    _check(load().gg_sssp_tree(handle, src, ptrs[0][0], ptrs[1][0], tp, cap, ctypes.byref(cnt), _stream_ptr(stream)),
+           "gg_sssp_tree")
+    return int(cnt.value)
 
 
 class Server:

@@ -6,7 +6,10 @@
 //   submit   enqueues a request (thread-safe) and returns a ticket;
 //   worker   one host thread per server owns a CUDA stream and loops:
 //              admit    queued requests take free slots while the in-flight
-//                       vertex budget (sized from free HBM at creation) allows;
+//                       vertex budget allows: the engine's capacity (sized
+//                       from free HBM at creation), re-derived at every
+//                       admission round from the device's free HBM, so that
+//                       memory other allocations take later defers admission;
 //                       each admitted query's distances are reset and its
 //                       source seeded straight into the running union frontier
 //              run      a CUDA graph advances every in-flight query by up to
@@ -170,12 +173,29 @@ struct gg_server {
   std::vector<uint64_t> slot_ticket;   // 0 = free
   uint64_t next_ticket = 1;
   uint64_t used_vertices = 0;
+  uint64_t live_budget = 0;   // vertex budget of the last admission round
   uint32_t running = 0;
   std::vector<double> lat_us;
   gg_server_stats st{};
 };
 
 namespace {
+
+// Device bytes charged per in-flight vertex when the budget is re-derived
+// from free HBM (frontier state, bitmaps and far piles, with headroom).
+constexpr uint64_t kBytesPerFlightVertex = 32;
+
+// The in-flight vertex budget in force now: the engine's capacity, capped by
+// the vertices already in flight plus what the device's free HBM above the
+// reserve would hold.  Other allocations on the device that leave less than
+// the reserve free therefore stop admission until memory is released.
+uint64_t live_budget(const gg_server* s) {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return s->used_vertices;   // defer on error
+  const uint64_t head = free_b > s->cfg.hbm_reserve_bytes ? (free_b - s->cfg.hbm_reserve_bytes) / kBytesPerFlightVertex
+                                                          : 0ull;
+  return std::min<uint64_t>(s->eng.cap_vertices, s->used_vertices + head);
+}
 
 void server_loop(gg_server* s) {
   cudaSetDevice(s->device);
@@ -186,11 +206,12 @@ void server_loop(gg_server* s) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
       for (;;) {
-        // admission: free slot and room in the in-flight vertex budget
+        // admission: free slot and room in the in-flight vertex budget in force
+        if (!s->queue.empty()) s->live_budget = live_budget(s);
         while (!s->queue.empty()) {
           const uint64_t t = s->queue.front();
           gg_server::Req& r = s->reqs[t];
-          if (s->used_vertices + r.g->n > s->eng.cap_vertices) break;
+          if (s->used_vertices + r.g->n > s->live_budget) break;
           uint32_t q = 0;
           while (q < s->eng.max_slots && s->slot_ticket[q]) ++q;
           if (q == s->eng.max_slots) break;
@@ -325,6 +346,7 @@ gg_status gg_server_create(const gg_server_config* cfg, gg_server_t* out) {
     return st;
   }
   s->slot_ticket.assign(s->eng.max_slots, 0);
+  s->live_budget = s->eng.cap_vertices;
   s->worker = std::thread(server_loop, s);
   *out = s;
   return GG_OK;
@@ -402,7 +424,7 @@ gg_status gg_server_get_stats(gg_server_t s, gg_server_stats* out) {
   for (double v : s->lat_us) { sum += v; mx = std::max(mx, v); }
   st.mean_us = s->lat_us.empty() ? 0.0 : sum / s->lat_us.size();
   st.max_us = mx;
-  st.vertex_budget = s->eng.cap_vertices;
+  st.vertex_budget = s->live_budget;
   *out = st;
   return GG_OK;
 }

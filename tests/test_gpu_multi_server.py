@@ -119,3 +119,38 @@ def test_server_poll_errors_and_budget():
     srv.close()
     big.close()
     g.close()
+
+
+def test_server_admission_follows_free_hbm():
+    """Admission re-reads the device's free HBM at every round: while another
+    allocation leaves less than hbm_reserve_bytes free, queued queries wait
+    (the budget in force drops to the vertices in flight); once the memory is
+    released they are admitted, and their distances equal the oracle's."""
+    m = gg()
+    ro, col, w = graphgen.grid(64, W=255, seed=1)
+    g = m.Graph(ro, col, w, symmetric=True)
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    reserve = free - (512 << 20)                  # about 512 MiB above the reserve
+    srv = m.Server(max_graph_vertices=g.n, max_slots=8, hbm_reserve_bytes=reserve)
+    free2, _ = torch.cuda.mem_get_info()
+    hog = torch.empty(free2 - reserve + (64 << 20), dtype=torch.uint8, device="cuda")   # 64 MiB below the reserve
+    torch.cuda.synchronize()
+    srcs = [0, 77, 4095]
+    outs = [torch.empty(g.n, dtype=torch.uint32, device="cuda") for _ in srcs]
+    ts = [srv.submit(g, s, d) for s, d in zip(srcs, outs)]
+    time.sleep(0.3)
+    st = srv.stats()
+    assert st["running"] == 0 and st["queued"] == len(srcs) and st["completed"] == 0
+    assert st["vertex_budget"] == 0
+    assert all(srv.poll(t) is None for t in ts)
+    del hog
+    torch.cuda.empty_cache()                      # hand the memory back to the driver
+    for t in ts:
+        assert srv.wait(t, 60000) == 0
+    for s, d in zip(srcs, outs):
+        np.testing.assert_array_equal(d.cpu().numpy(), oracle.dijkstra(ro, col, w, s))
+    assert srv.stats()["vertex_budget"] > 0
+    srv.close()
+    g.close()
