@@ -393,6 +393,60 @@ gg_status gg_sssp_multi(const gg_graph_t* graphs, const uint32_t* srcs, uint32_t
 gg_status gg_sssp_multi_ex(const gg_graph_t* graphs, const uint32_t* srcs, uint32_t count,
                            uint32_t* const* dist_outs, uint32_t delta, cudaStream_t stream);
 
+/* ---- single source over a 1D vertex partition (one part per rank) -------- */
+
+/* Sec. III-D and Table I place the graph on several processors by a
+ * partition of its vertices (random partitioning being the simplest).  Each
+ * rank (one process per GPU) holds a part: the out-edges of the vertices it
+ * owns, with global column ids, and those vertices' distances.  One
+ * superstep is
+ *   gg_part_advance   relax the part's frontier: updates to owned vertices
+ *                     are applied at once (atomicMin; a vertex whose distance
+ *                     dropped joins the next frontier once), updates to other
+ *                     ranks' vertices are written to send_pairs, grouped by
+ *                     destination rank;
+ *   (the caller exchanges the groups between ranks: a collective)
+ *   gg_part_apply     relax the received pairs the same way and close the
+ *                     superstep.
+ * The run ends when every rank's next frontier is empty (the caller reduces
+ * next_size over the ranks).  The fixed point is the one of the one-GPU loop.
+ * Parts are independent handles: no call waits on another rank. */
+typedef struct gg_part* gg_part_t;
+
+/* route: host u32[n_global], route[v] = (owner rank << 24) | (index of v
+ * among its owner's vertices, in the owner's row order); nranks <= 256,
+ * n_local <= 2^24.  row_offsets: host u32[n_local + 1] over the owned
+ * vertices in local order; cols (global ids < n_global), weights: host
+ * u32[m_local].  Uploads and synchronises `stream`.  Errors:
+ * GG_ERR_INVALID_ARG (NULLs, ranks out of range, offsets not monotone from
+ * 0, a column >= n_global, a route to a rank >= nranks, a local index
+ * >= n_local, or a route that gives this rank other than n_local vertices),
+ * GG_ERR_CUDA. */
+gg_status gg_part_create(uint32_t n_global, uint32_t rank, uint32_t nranks, uint32_t n_local, const uint32_t* route,
+                         const uint32_t* row_offsets, const uint32_t* cols, const uint32_t* weights,
+                         cudaStream_t stream, gg_part_t* out);
+gg_status gg_part_destroy(gg_part_t p);
+/* n_local and the part's edge count (the most remote updates one superstep can emit). */
+gg_status gg_part_info(gg_part_t p, uint32_t* n_local, uint64_t* m_local);
+/* dist := GG_INF on the part; the source's owner seeds dist = 0 and its
+ * frontier.  Every rank calls it with the same src_global. */
+gg_status gg_part_begin(gg_part_t p, uint32_t src_global, cudaStream_t stream);
+/* send_pairs: device u32[2 * cap]; receives (index on the destination rank,
+ * distance) pairs, destination d's from offset sum(send_counts[0..d)) on.
+ * send_counts: host u64[nranks] (this rank's own entry is 0).  Synchronous.
+ * GG_ERR_INVALID_ARG when the pairs exceed cap (cap = m_local always
+ * suffices). */
+gg_status gg_part_advance(gg_part_t p, cudaStream_t stream, uint32_t* send_pairs, uint64_t cap,
+                          uint64_t* send_counts);
+/* recv_pairs: device u32[2 * count], pairs addressed to this rank (local
+ * index, distance).  Closes the superstep; next_size (host) receives this
+ * rank's next frontier size.  Synchronous.  GG_ERR_OVERFLOW when a finite
+ * distance did not fit below GG_INF. */
+gg_status gg_part_apply(gg_part_t p, const uint32_t* recv_pairs, uint64_t count, cudaStream_t stream,
+                        uint32_t* next_size);
+/* The part's distances (device u32[n_local], local order). */
+gg_status gg_part_distances(gg_part_t p, uint32_t* dist_out, cudaStream_t stream);
+
 /* ---- query server (continuous batching) --------------------------------- */
 
 typedef struct gg_server* gg_server_t;

@@ -135,6 +135,13 @@ def load():
             "gg_autotune_batch": (ctypes.c_int, [vp, P32, u32, vp, ctypes.POINTER(gg_options),
                                                  ctypes.POINTER(ctypes.c_float), vp]),
             "gg_sssp_tree": (ctypes.c_int, [vp, u32, vp, vp, vp, u64, ctypes.POINTER(u64), vp]),
+            "gg_part_create": (ctypes.c_int, [u32, u32, u32, u32, vp, vp, vp, vp, vp, ctypes.POINTER(vp)]),
+            "gg_part_destroy": (ctypes.c_int, [vp]),
+            "gg_part_info": (ctypes.c_int, [vp, P32, ctypes.POINTER(u64)]),
+            "gg_part_begin": (ctypes.c_int, [vp, u32, vp]),
+            "gg_part_advance": (ctypes.c_int, [vp, vp, vp, u64, ctypes.POINTER(u64)]),
+            "gg_part_apply": (ctypes.c_int, [vp, vp, u64, vp, P32]),
+            "gg_part_distances": (ctypes.c_int, [vp, vp, vp]),
             "gg_status_string": (ctypes.c_char_p, [ctypes.c_int]),
             "gg_last_error": (ctypes.c_char_p, []),
             "gg_abi_version": (u32, []),

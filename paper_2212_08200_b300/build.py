@@ -13,7 +13,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libgg.so")
 OBJDIR = os.path.join(ROOT, "_build", "gg")
 
-SOURCES = ["gg_api.cu", "gg_graph.cu", "gg_bsp.cu", "gg_async.cu", "gg_noalloc.cu", "gg_batch.cu", "gg_multi.cu", "gg_server.cu", "gg_tune.cu", "gg_edge.cu"]
+SOURCES = ["gg_api.cu", "gg_graph.cu", "gg_bsp.cu", "gg_async.cu", "gg_noalloc.cu", "gg_batch.cu", "gg_multi.cu", "gg_server.cu", "gg_tune.cu", "gg_edge.cu", "gg_part.cu"]
 HEADERS = ["gg_common.cuh", "gg_host.h", "gg_multi.h"]
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

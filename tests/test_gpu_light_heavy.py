@@ -225,8 +225,14 @@ def test_bad_light_heavy_value_is_rejected():
     ro, col, w, src = graphgen.workload("grid64")
     g = m.Graph(ro, col, w, symmetric=True)
     with pytest.raises(m.GGError) as ei:
-        g.sssp(src, light_heavy=2)
+        g.sssp(src, light_heavy=3)
     assert ei.value.status_name == "GG_ERR_INVALID_ARG"
+    with pytest.raises(m.GGError) as ei:
+        g.sssp_batch(np.array([src], np.uint32), light_heavy=3)
+    assert ei.value.status_name == "GG_ERR_INVALID_ARG"
+    d = g.sssp(src, light_heavy=m.GG_LH_ROUNDS)        # the batch-only schedule: single source runs as AUTO
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(d.cpu().numpy(), oracle.dijkstra(ro, col, w, src))
     g.close()
 
 
