@@ -55,7 +55,7 @@ extern "C" {
 #endif
 
 #define GG_INF 0xFFFFFFFFu
-#define GG_ABI_VERSION 3
+#define GG_ABI_VERSION 4
 
 typedef struct gg_graph* gg_graph_t;
 

@@ -50,7 +50,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_status_strings_and_abi(lib):
     import paper_2212_08200_b300 as gg
-    assert gg.gg_abi_version() == 3
+    assert gg.gg_abi_version() == 4
     for code, name in gg.STATUS.items():
         assert gg.gg_status_string(code) == name
 
