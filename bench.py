@@ -60,7 +60,7 @@ def parse():
     p.add_argument("--workload", default="rmat22")
     p.add_argument("--policy", default="graph", choices=["graph", "async", "host", "persistent"])
     p.add_argument("--direction", default="push", choices=["auto", "push", "pull"])
-    p.add_argument("--lb", default="auto", choices=["auto", "mp", "bins", "warp"])
+    p.add_argument("--lb", default="auto", choices=["auto", "mp", "bins", "warp", "local"])
     p.add_argument("--batch-scale", type=int, default=22, help="RMAT scale of the batched run (22 = the workload)")
     p.add_argument("--batch-policy", default="graph", choices=["graph", "host"],
                    help="host: supersteps launched one by one (for profilers)")
@@ -584,7 +584,8 @@ def run_gg(args):
     stream = torch.cuda.current_stream()
     g = gg.Graph(ro, col, w, symmetric=True, stream=stream)
     dist_t = torch.empty(n, dtype=torch.uint32, device="cuda")
-    lb = {"auto": gg.GG_LB_AUTO, "mp": gg.GG_LB_MERGE_PATH, "bins": gg.GG_LB_BINS, "warp": gg.GG_LB_WARP}[args.lb]
+    lb = {"auto": gg.GG_LB_AUTO, "mp": gg.GG_LB_MERGE_PATH, "bins": gg.GG_LB_BINS, "warp": gg.GG_LB_WARP,
+          "local": gg.GG_LB_LOCAL}[args.lb]
     delta = gg.GG_DELTA_NONE if args.delta < 0 else args.delta
     opts = gg.make_options(policy=policy, direction=direction, lb_mode=lb, pull_alpha=args.alpha, pull_beta=args.beta,
                            delta=delta)

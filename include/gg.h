@@ -113,11 +113,17 @@ typedef enum { GG_DIR_AUTO = 0, GG_DIR_PUSH = 1, GG_DIR_PULL = 2 } gg_direction;
 /* Load balancing of the push advance (Sec. IV-C: "data parallelism and load
  * balancing"). */
 typedef enum {
-    GG_LB_AUTO = 0,        /* library choice (warp streaming)                            */
+    GG_LB_AUTO = 0,        /* library choice: warp streaming, with warp-local rounds on  */
+                           /* graphs of mean degree < 8                                 */
     GG_LB_MERGE_PATH = 1,  /* equal edge ranges per CTA over the frontier's degree scan  */
     GG_LB_BINS = 2,        /* thread / warp / CTA per vertex by degree thresholds        */
-    GG_LB_WARP = 3         /* equal edge ranges per warp, streamed 32 edges at a time,   */
+    GG_LB_WARP = 3,        /* equal edge ranges per warp, streamed 32 edges at a time,   */
                            /* with no CTA barriers (push only; pull uses merge-path)     */
+    GG_LB_LOCAL = 4        /* warp streaming, then up to 16 warp-local rounds per        */
+                           /* superstep: the near vertices a warp improves are expanded  */
+                           /* by that warp at once (rows of <= 32 edges), the rest goes  */
+                           /* to the next frontier (BSP graph and host policies; for     */
+                           /* high-diameter graphs: several hops per superstep)          */
 } gg_lb_mode;
 
 typedef struct {
@@ -290,7 +296,8 @@ gg_status gg_sssp_tree(gg_graph_t g, uint32_t src, const uint32_t* dist, uint32_
  * bucket width (on graphs with a light/heavy width: widths giving 1.5 to 4.5
  * light edges per vertex; otherwise the near-far width from 1/8 to 8 times
  * the default; and no buckets), push-only vs push/pull switching thresholds, and
- * merge-path vs degree bins with their thresholds.  Every candidate runs
+ * warp streaming with or without warp-local rounds vs merge-path vs degree
+ * bins with their thresholds.  Every candidate runs
  * gg_sssp_ex from each sample source on `stream` and is timed with CUDA
  * events (median of 3); candidates that report a device error are skipped.
  *   srcs          host u32[nsrc], each < n

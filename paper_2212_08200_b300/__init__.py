@@ -20,7 +20,7 @@ import numpy as np
 __all__ = [
     "GGError", "GG_INF", "GG_DEVICE_PTRS", "GG_SYMMETRIC", "GG_NO_VALIDATE",
     "GG_POLICY_BSP_GRAPH", "GG_POLICY_ASYNC_PERSISTENT", "GG_POLICY_BSP_HOST", "GG_POLICY_BSP_PERSISTENT",
-    "GG_DIR_AUTO", "GG_DIR_PUSH", "GG_DIR_PULL", "GG_LB_AUTO", "GG_LB_MERGE_PATH", "GG_LB_BINS", "GG_LB_WARP", "GG_DELTA_NONE",
+    "GG_DIR_AUTO", "GG_DIR_PUSH", "GG_DIR_PULL", "GG_LB_AUTO", "GG_LB_MERGE_PATH", "GG_LB_BINS", "GG_LB_WARP", "GG_LB_LOCAL", "GG_DELTA_NONE",
     "GG_LH_AUTO", "GG_LH_OFF", "GG_LH_ROUNDS",
     "gg_graph_create_csr", "gg_graph_destroy", "gg_graph_info", "gg_graph_check", "gg_sssp", "gg_sssp_ex",
     "gg_bfs", "gg_bfs_ex", "GG_FLOAT_WEIGHTS", "GG_FLT_MAX_BITS",
@@ -39,7 +39,7 @@ GG_DEVICE_PTRS, GG_SYMMETRIC, GG_NO_VALIDATE, GG_NO_PACK, GG_FLOAT_WEIGHTS = 0x1
 GG_FLT_MAX_BITS = 0x7F7FFFFF   # "unreached" for binary32 distances (FLT_MAX)
 GG_POLICY_BSP_GRAPH, GG_POLICY_ASYNC_PERSISTENT, GG_POLICY_BSP_HOST, GG_POLICY_BSP_PERSISTENT = 0, 1, 2, 3
 GG_DIR_AUTO, GG_DIR_PUSH, GG_DIR_PULL = 0, 1, 2
-GG_LB_AUTO, GG_LB_MERGE_PATH, GG_LB_BINS, GG_LB_WARP = 0, 1, 2, 3
+GG_LB_AUTO, GG_LB_MERGE_PATH, GG_LB_BINS, GG_LB_WARP, GG_LB_LOCAL = 0, 1, 2, 3, 4
 GG_DELTA_NONE = 0xFFFFFFFF
 GG_LH_AUTO, GG_LH_OFF, GG_LH_ROUNDS = 0, 1, 2
 

@@ -252,7 +252,7 @@ gg_status run_single(gg_graph_t g, uint32_t src, uint32_t* dist_out, const gg_op
   }
   if ((unsigned)o.policy > 3u) return fail(GG_ERR_INVALID_ARG, "unknown policy");
   if ((unsigned)o.direction > 2u) return fail(GG_ERR_INVALID_ARG, "unknown direction");
-  if ((unsigned)o.lb_mode > 3u) return fail(GG_ERR_INVALID_ARG, "unknown load-balance mode");
+  if ((unsigned)o.lb_mode > 4u) return fail(GG_ERR_INVALID_ARG, "unknown load-balance mode");
   if (o.light_heavy > GG_LH_ROUNDS) return fail(GG_ERR_INVALID_ARG, "unknown light_heavy mode");
   if (o.trace && o.trace_cap == 0) return fail(GG_ERR_INVALID_ARG, "trace without trace_cap");
   int dev = -1;

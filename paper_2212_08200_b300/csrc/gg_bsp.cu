@@ -76,6 +76,12 @@
 #ifndef GG_LH_TAIL
 #define GG_LH_TAIL 1   // light/heavy: plain push once bucketing has ended
 #endif
+#ifndef GG_LOCAL_ROUNDS
+#define GG_LOCAL_ROUNDS 16   // warp-local rounds per superstep (load balance GG_LB_LOCAL; 4096^2 grid: 43 ms at 4, 36 at 8, 34 at 16)
+#endif
+#ifndef GG_LOCAL_MAX_DEG
+#define GG_LOCAL_MAX_DEG 32   // vertices with more out-edges leave local rounds for the next frontier
+#endif
 #ifndef GG_LH_DRAIN
 #define GG_LH_DRAIN 8    // light/heavy: bucketing ends once the unsettled vertices hold
 #endif                   // fewer than m / GG_LH_DRAIN heavy edges
@@ -88,10 +94,11 @@ namespace {
 constexpr int LB_TILE = 0;   // merge-path tiles of BLOCK*EPT edges per CTA
 constexpr int LB_BINS = 1;   // degree bins: thread / warp / CTA per vertex
 constexpr int LB_WARP = 2;   // warp streaming over equal edge shares
+constexpr int LB_LOCAL = 3;  // warp streaming, then warp-local rounds over the near vertices each warp improved
 
 // resident CTAs per SM each superstep kernel is register-limited to
 constexpr int superstep_min_blocks(int lb, int ept) {
-  return lb == LB_WARP ? GG_WARP_MINB : ept == 2 ? 8 : ept == 4 ? 6 : 4;
+  return (lb == LB_WARP || lb == LB_LOCAL) ? GG_WARP_MINB : ept == 2 ? 8 : ept == 4 ? 6 : 4;
 }
 
 template <int BLOCK, int EPT>
@@ -113,6 +120,7 @@ struct MPSmem {
   uint32_t ovf;
   unsigned long long base;
   uint32_t fbase;
+  uint32_t ledges;     // edges relaxed in warp-local rounds (statistics)
   uint16_t own[TILE];  // push: entry that owns each edge slot of the tile
 };
 
@@ -566,7 +574,19 @@ __device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepA
 // vertices pass the filter's dedup into a per-warp shared-memory queue that is
 // appended to the next frontier with one 64-bit atomicAdd per flush (queue
 // position and edge-prefix base), like the CTA queue of the tile advance.
-template <int BLOCK, int EPT, bool PK>
+// LOCAL (load balance GG_LB_LOCAL, plain integer or float runs): near
+// vertices a warp improves are not deduplicated into the next frontier but
+// kept in a per-warp local queue, and after its share of the frontier the
+// warp runs up to GG_LOCAL_ROUNDS local rounds over that queue: each queued
+// vertex (read with its current distance) relaxes its out-edges, and the near
+// vertices those improve form the next local queue.  Every relaxation that
+// lowers a distance below the threshold queues the vertex (a queue entry per
+// improvement, no bitmap), so a vertex is expanded after its last decrease.
+// What the rounds leave (and what overflows a queue, and rows longer than
+// GG_LOCAL_MAX_DEG) goes to the next frontier through the bitmap as usual.
+// On a high-diameter graph this advances the wavefront several hops per
+// superstep.
+template <int BLOCK, int EPT, bool PK, bool LOCAL = false>
 __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t F, uint32_t Etot,
                                              const uint32_t* __restrict__ S, const uint32_t* __restrict__ R,
                                              const uint32_t* __restrict__ V, const void* __restrict__ edges,
@@ -584,6 +604,23 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
   uint32_t* qd = sm.qd + warp * QW;
   uint32_t* fq = sm.es + warp * QW;   // far queue (the entry arrays are unused here)
   uint32_t qn = 0, fn = 0;            // warp-uniform queue lengths
+  // LOCAL: two local queues of QL (vertex, distance it was queued with)
+  // entries: vertices in [0, QL), distances in [QL, 2 QL) of the unused entry
+  // arrays eb / ec; the near queue keeps the distance in qr
+  constexpr uint32_t QL = QW / 2;
+  uint32_t* const lqa = sm.eb + warp * QW;
+  uint32_t* const lqb = sm.ec + warp * QW;
+  uint32_t* lq_next = lqa;
+  uint32_t lqn = 0;                   // warp-uniform: entries in lq_next
+  // one entry per lane (have) into the next frontier: test-and-set, append the winners
+  auto handoff_lane = [&](bool have, uint32_t v) {
+    bool win = false;
+    if (have) {
+      const uint32_t bit = 1u << (v & 31);
+      win = !(atomicOr(fo.bm_next + (v >> 5), bit) & bit);
+    }
+    append32<false>(a, fo, win, v);
+  };
   uint32_t fmin = kInf;
   bool ovf = false;
   const uint32_t wbits = a.g.wbits;
@@ -593,6 +630,19 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
 
   auto flush_near = [&]() {
     __syncwarp();
+    if (LOCAL) {
+      // into the local queue; what does not fit goes to the next frontier
+      const uint32_t take = min(QL - lqn, qn);
+      for (uint32_t i = lane; i < take; i += 32) {
+        lq_next[lqn + i] = qv[i];
+        lq_next[QL + lqn + i] = qr[i];
+      }
+      for (uint32_t i0 = take; i0 < qn; i0 += 32) handoff_lane(i0 + lane < qn, i0 + lane < qn ? qv[i0 + lane] : 0u);
+      lqn += take;
+      qn = 0;
+      __syncwarp();
+      return;
+    }
     if (GG_DEFER_DEDUP && !fo.sinks) {
       // deferred dedup: the queue holds every improved near vertex (repeats
       // included); test-and-set them all here, the atomics of the whole queue
@@ -759,7 +809,7 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
             const uint32_t bit = 1u << (v & 31);
             if (nd[u] < fo.t_cur) {
               // with deferred dedup the bitmap is tested at the flush
-              near = (GG_DEFER_DEDUP && !fo.sinks) ? true : !(atomicOr(fo.bm_next + (v >> 5), bit) & bit);
+              near = (LOCAL || (GG_DEFER_DEDUP && !fo.sinks)) ? true : !(atomicOr(fo.bm_next + (v >> 5), bit) & bit);
             } else {
               fmin = min(fmin, nd[u]);
               far = !(atomicOr(fo.bm_far + (v >> 5), bit) & bit);
@@ -771,7 +821,7 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
           if (near) {
             const uint32_t off = qn + __popc(nb & lt);
             qv[off] = v;
-            qr[off] = rs;
+            qr[off] = LOCAL ? nd[u] : rs;   // LOCAL: the distance v is queued with
             qd[off] = deg;
           }
           qn += __popc(nb);
@@ -788,6 +838,92 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
     }
     if (qn) flush_near();
     if (fn) flush_far();
+  }
+  if (LOCAL) {
+    uint32_t ledges = 0;   // warp-uniform
+    for (int r = 0; r < GG_LOCAL_ROUNDS && lqn > 0; ++r) {   // warp-uniform
+      uint32_t* const cur = lq_next;
+      const uint32_t ncur = lqn;
+      lq_next = cur == lqa ? lqb : lqa;
+      lqn = 0;
+      __syncwarp();
+      for (uint32_t i0 = 0; i0 < ncur; i0 += 32) {   // warp-uniform
+        const uint32_t i = i0 + lane;
+        uint32_t v = 0, du = 0, rs = 0, deg = 0;
+        if (i < ncur) {
+          v = cur[i];
+          du = ld_cg(dist + v);
+          rs = __ldg(fo.ro + v);
+          deg = __ldg(fo.ro + v + 1) - rs;
+          // a later improvement queued v again with a smaller distance: that
+          // entry expands it, this one is stale
+          if (du < cur[QL + i]) deg = 0;
+        }
+        const bool big = deg > GG_LOCAL_MAX_DEG;   // long rows: the next frontier's balanced advance
+        if (__any_sync(FULL, big)) handoff_lane(big, v);
+        if (big) deg = 0;
+        const uint32_t dmax = __reduce_max_sync(FULL, deg);
+        ledges += __reduce_add_sync(FULL, deg);
+        for (uint32_t k = 0; k < dmax; k += 4) {   // warp-uniform; four edges per lane in flight
+          uint2 ed[4];
+          uint32_t nd[4], cv[4];
+          bool act[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            act[q] = k + q < deg;
+            if (act[q]) ed[q] = load_edge<PK>(edges, rs + k + q, wbits);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (act[q]) {
+              nd[q] = relax_add(du, ed[q].y, ovf, fo.wmode);
+              cv[q] = ld_cg(dist + ed[q].x);
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            bool near = false, far = false;
+            const uint32_t t = ed[q].x;
+            if (act[q] && nd[q] < cv[q]) {
+              atomicMin(dist + t, nd[q]);
+              bool ok = true;
+              if (fo.sinks) ok = __ldg(fo.ro + t + 1) > __ldg(fo.ro + t);
+              if (ok) {
+                if (nd[q] < fo.t_cur) {
+                  near = true;
+                } else {
+                  const uint32_t bit = 1u << (t & 31);
+                  fmin = min(fmin, nd[q]);
+                  far = !(atomicOr(fo.bm_far + (t >> 5), bit) & bit);
+                }
+              }
+            }
+            const unsigned nb = __ballot_sync(FULL, near);
+            if (nb) {
+              if (near) {
+                qv[qn + __popc(nb & lt)] = t;
+                qr[qn + __popc(nb & lt)] = nd[q];
+              }
+              qn += __popc(nb);
+              if (qn > QW - 32) flush_near();
+            }
+            const unsigned fb = __ballot_sync(FULL, far);
+            if (fb) {
+              if (far) fq[fn + __popc(fb & lt)] = t;
+              fn += __popc(fb);
+              if (fn > QW - 32) flush_far();
+            }
+          }
+        }
+      }
+      if (qn) flush_near();
+      if (fn) flush_far();
+    }
+    __syncwarp();
+    for (uint32_t i0 = 0; i0 < lqn; i0 += 32)   // what the rounds leave: the next frontier
+      handoff_lane(i0 + lane < lqn, i0 + lane < lqn ? lq_next[i0 + lane] : 0u);
+    lqn = 0;
+    if (lane == 0 && ledges) atomicAdd(&sm.ledges, ledges);
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) fmin = min(fmin, __shfl_xor_sync(FULL, fmin, o));
@@ -1020,6 +1156,7 @@ __device__ __forceinline__ void superstep_prologue(MPSmem<BLOCK, EPT>& sm, const
     sm.qfn = 0;
     sm.fmin = kInf;
     sm.ovf = 0;
+    sm.ledges = 0;
   }
   if (clear_prev) {
     uint32_t* bm_old = a.fr.bm[(it + 2) % 3];
@@ -1049,6 +1186,7 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
   if (threadIdx.x == 0) {
     if (sm.ovf) atomicOr(&ctl->status, DS_OVERFLOW);
     if (sm.fmin != kInf) atomicMin(&ctl->far_min, sm.fmin);
+    if (sm.ledges) atomicAdd(&ctl->edges_scanned, (unsigned long long)sm.ledges);   // warp-local rounds
     sm.last = arrive_last(&ctl->done_ctas, gridDim.x) ? 1u : 0u;
   }
   __syncthreads();
@@ -1267,11 +1405,11 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_supers
       if (LB == LB_BINS)
         bins_advance<BLOCK, EPT, PK>(sm, a, fw, Ew, fV, fR, fS, dist, bm_cur, fo, ctl->warp_thr, ctl->cta_thr,
                                      edges);
-      else if (LB == LB_WARP && LH && mode == MODE_HEAVY)   // separate copies keep the pointer selects
-        warp_advance<BLOCK, EPT, PK>(sm, a, fw, Ew, fS, fR, fV, edges, dist, bm_cur, fo);   // out of the loop
-      else if (LB == LB_WARP)
-        warp_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], edges, dist,
-                                     a.fr.bm[it % 3], fo);
+      else if ((LB == LB_WARP || LB == LB_LOCAL) && LH && mode == MODE_HEAVY)   // separate copies keep the
+        warp_advance<BLOCK, EPT, PK>(sm, a, fw, Ew, fS, fR, fV, edges, dist, bm_cur, fo);   // pointer selects out
+      else if (LB == LB_WARP || LB == LB_LOCAL)                                              // of the loop
+        warp_advance<BLOCK, EPT, PK, LB == LB_LOCAL && !LH>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], edges,
+                                                            dist, a.fr.bm[it % 3], fo);
       else
         mp_advance<BLOCK, EPT, false, PK>(sm, a, fw, Ew, fS, fR, fV, edges, dist, bm_cur, fo);
     } else {
@@ -1370,7 +1508,7 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_bsp_pe
         if (LB == LB_BINS)
           bins_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fv[p], a.fr.fr[p], a.fr.fs[p], dist, bm_cur, fo,
                                        ctl->warp_thr, ctl->cta_thr, a.g.edges);
-        else if (LB == LB_WARP)
+        else if (LB == LB_WARP || LB == LB_LOCAL)
           warp_advance<BLOCK, EPT, PK>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], a.g.edges, dist, bm_cur,
                                        fo);
         else
@@ -1587,7 +1725,7 @@ constexpr int kEpt = GG_EPT;
 // kernel variants: (load balance x packed edges) x (weight mode, or integer
 // weights with light/heavy buckets)
 constexpr int kVariants = kBspVariants;
-static_assert(kVariants == 3 * 2 * 4, "variant table");
+static_assert(kVariants == 4 * 2 * 4, "variant table");
 
 constexpr int variant_of(int lb, bool packed, uint32_t wmode, bool lh) {
   return (lb * 2 + (packed ? 1 : 0)) * 4 + (lh ? kWmU32Lh : (int)wmode);
@@ -1604,7 +1742,8 @@ void* persistent_ptr() {
 #define GG_VARIANT_ROW(F, LBV, PKV) F<LBV, PKV, 0>(), F<LBV, PKV, 1>(), F<LBV, PKV, 2>(), F<LBV, PKV, kWmU32Lh>()
 #define GG_VARIANT_TABLE(F)                                                                   \
   {GG_VARIANT_ROW(F, LB_TILE, false), GG_VARIANT_ROW(F, LB_TILE, true), GG_VARIANT_ROW(F, LB_BINS, false), \
-   GG_VARIANT_ROW(F, LB_BINS, true),  GG_VARIANT_ROW(F, LB_WARP, false), GG_VARIANT_ROW(F, LB_WARP, true)}
+   GG_VARIANT_ROW(F, LB_BINS, true),  GG_VARIANT_ROW(F, LB_WARP, false), GG_VARIANT_ROW(F, LB_WARP, true),  \
+   GG_VARIANT_ROW(F, LB_LOCAL, false), GG_VARIANT_ROW(F, LB_LOCAL, true)}
 
 void* superstep_fn(int variant) {
   static void* const table[kVariants] = GG_VARIANT_TABLE(superstep_ptr);
@@ -1729,8 +1868,12 @@ gg_status build_graph_exec(gg_graph* g, int variant) {
 gg_status bsp_run(gg_graph* g, uint32_t src, uint32_t* dist, const gg_options& o, cudaStream_t s, uint32_t wmode) {
   gg_status st = ensure_workspace(g, s);
   if (st != GG_OK) return st;
-  // automatic choice: warp streaming (measured faster than merge-path tiles on RMAT, equal on grids)
-  const int lb = o.lb_mode == GG_LB_BINS ? LB_BINS : o.lb_mode == GG_LB_MERGE_PATH ? LB_TILE : LB_WARP;
+  // automatic choice: warp streaming (measured faster than merge-path tiles on
+  // RMAT, equal on grids), with warp-local rounds on low-degree graphs (the
+  // 4096^2 grid: 95 -> 34-36 ms, a tenth of the supersteps)
+  const int lb = o.lb_mode == GG_LB_BINS ? LB_BINS : o.lb_mode == GG_LB_MERGE_PATH ? LB_TILE
+               : o.lb_mode == GG_LB_LOCAL ? LB_LOCAL : o.lb_mode == GG_LB_WARP ? LB_WARP
+               : g->low_degree ? LB_LOCAL : LB_WARP;
   BspWorkspace& w = g->bsp;
   RunParams rp;
   rp.src = src;

@@ -40,10 +40,10 @@ struct DeviceInfo {
 };
 DeviceInfo device_info();
 
-// Superstep kernel variants: load balance (3) x edge packing (2) x weight
+// Superstep kernel variants: load balance (4) x edge packing (2) x weight
 // mode (u32, binary32, unit, u32 with light/heavy buckets).
 constexpr int kWmU32Lh = 3;
-constexpr int kBspVariants = 3 * 2 * 4;
+constexpr int kBspVariants = 4 * 2 * 4;
 
 // Workspace of the bulk-synchronous path (allocated on first use).
 struct BspWorkspace {

@@ -3,8 +3,9 @@
 //   gg_autotune        single source: coordinate descent over policy, bucket
 //                      width (the light/heavy width on skewed graphs, the
 //                      near-far width otherwise), direction / switch
-//                      threshold and load balancing (warp streaming,
-//                      merge-path tiles, or degree bins with thresholds);
+//                      threshold and load balancing (warp streaming with or
+//                      without warp-local rounds, merge-path tiles, or degree
+//                      bins with thresholds);
 //   gg_autotune_batch  batched sources: schedule (normalised buckets or
 //                      light-first rounds) and light/heavy width.
 #include <cuda_runtime.h>
@@ -194,13 +195,15 @@ extern "C" gg_status gg_autotune(gg_graph_t g, const uint32_t* srcs, uint32_t ns
       if ((st = try_opt(o)) != GG_OK) return st;
     }
   }
-  // 4. load balancing: merge-path tiles, or degree bins at a few thresholds
-  //    (the default is warp streaming)
+  // 4. load balancing: warp streaming with and without warp-local rounds,
+  //    merge-path tiles, or degree bins at a few thresholds
   {
     const gg_options base = cur;
-    gg_options o = base;
-    o.lb_mode = GG_LB_MERGE_PATH;
-    if ((st = try_opt(o)) != GG_OK) return st;
+    for (gg_lb_mode lb : {GG_LB_WARP, GG_LB_LOCAL, GG_LB_MERGE_PATH}) {
+      gg_options o = base;
+      o.lb_mode = lb;
+      if ((st = try_opt(o)) != GG_OK) return st;
+    }
   }
   {
     const gg_options base = cur;

@@ -12,10 +12,10 @@ pytestmark = pytest.mark.gpu
 FMAX = oracle.FLT_MAX_BITS
 POLICIES = {"graph": 0, "async": 1, "host": 2, "persistent": 3}
 DIRS = {"auto": 0, "push": 1, "pull": 2}
-LB = {"mp": 1, "bins": 2, "warp": 3}
+LB = {"mp": 1, "bins": 2, "warp": 3, "local": 4}
 MODES = [("graph", "push", "warp"), ("graph", "auto", "warp"), ("graph", "pull", "mp"), ("host", "push", "mp"),
          ("host", "auto", "bins"), ("persistent", "push", "warp"), ("persistent", "auto", "mp"),
-         ("async", "push", "warp")]
+         ("async", "push", "warp"), ("graph", "push", "local"), ("host", "auto", "local")]
 
 
 def gg():

@@ -29,7 +29,7 @@ def gg():
 
 POLICIES = {"graph": 0, "async": 1, "host": 2, "persistent": 3}
 DIRS = {"auto": 0, "push": 1, "pull": 2}
-LB = {"mp": 1, "bins": 2, "warp": 3}
+LB = {"mp": 1, "bins": 2, "warp": 3, "local": 4}
 NONE = 0xFFFFFFFF
 # (policy, direction, load balance, near-far delta; 0 = the graph's default)
 MODES = [("graph", "auto"), ("graph", "push"), ("graph", "pull"), ("host", "auto"), ("host", "pull"),
@@ -37,7 +37,9 @@ MODES = [("graph", "auto"), ("graph", "push"), ("graph", "pull"), ("host", "auto
          ("graph", "push", "mp", NONE), ("graph", "auto", "mp", 1), ("graph", "push", "bins", 3),
          ("persistent", "push"), ("persistent", "auto", "mp", NONE), ("persistent", "pull"),
          ("persistent", "push", "bins", 5), ("graph", "push", "warp"), ("host", "auto", "warp", 4),
-         ("persistent", "push", "warp", NONE), ("graph", "push", "warp", 2)]
+         ("persistent", "push", "warp", NONE), ("graph", "push", "warp", 2),
+         ("graph", "push", "local"), ("host", "push", "local", 3), ("graph", "push", "local", NONE),
+         ("graph", "auto", "local")]
 
 
 def run(g, src, policy="graph", direction="auto", lb="mp", delta=0, **kw):
@@ -386,4 +388,39 @@ def test_iteration_cap_reports_internal():
     with pytest.raises(m.GGError) as ei:
         g.check()
     assert ei.value.status_name == "GG_ERR_INTERNAL"
+    g.close()
+
+
+@pytest.mark.parametrize("side,delta", [(512, 0), (300, 0), (256, NONE), (128, 40)])
+def test_local_rounds_on_grids(side, delta):
+    """Warp-local rounds (GG_LB_LOCAL) on high-diameter grids: the oracle's
+    distances in fewer supersteps than plain warp streaming."""
+    ro, col, w = graphgen.grid(side, 1000, 3)
+    g = gg().Graph(ro, col, w, symmetric=True)
+    ref = oracle.dijkstra(ro, col, w, 0)
+    got, st = run(g, 0, "graph", "push", "local", delta)
+    np.testing.assert_array_equal(got, ref)
+    _, st_w = run(g, 0, "graph", "push", "warp", delta)
+    assert st["iterations"] <= st_w["iterations"]
+    if delta == 0:   # the graph's bucket width leaves room for several hops per superstep
+        assert st["iterations"] < st_w["iterations"]
+    g.close()
+
+
+@pytest.mark.parametrize("name", ["rmat16", "grid64"])
+def test_local_rounds_float_and_bfs(name):
+    """The local rounds under the other weight modes: binary32 weights (the
+    paper's float variant) and unit weights (BFS)."""
+    m = gg()
+    ro, col, w, src = graphgen.workload(name)
+    wf = (w.astype(np.float32) * np.float32(0.37)).astype(np.float32)
+    gf = m.Graph(ro, col, wf, symmetric=True, float_weights=True)
+    d = gf.sssp(src, lb_mode=LB["local"], direction=DIRS["push"])
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(d.cpu().numpy(), oracle.dijkstra_f32(ro, col, wf, src))
+    gf.close()
+    g = m.Graph(ro, col, w, symmetric=True)
+    h = g.bfs(src, lb_mode=LB["local"], direction=DIRS["push"])
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(h.cpu().numpy(), oracle.bfs_hops(ro, col, src))
     g.close()
