@@ -337,20 +337,23 @@ def run_rmat20(gg, torch, stream, flush, steps=10):
 def run_grid4096(gg, torch, stream, flush, steps=3):
     """The 4096^2 grid (16.7 M vertices, 67 M edges, weights U[1,1000]) from
     the corner under the paper's two timing models: bulk-synchronous
-    supersteps (CUDA-graph loop, and the persistent cooperative kernel) and
-    the asynchronous persistent kernel over a device work queue; each
-    verified against the stored oracle hash."""
+    supersteps (CUDA-graph loop with the library's defaults, which on this
+    low-degree graph include warp-local rounds; the same loop without them;
+    the persistent cooperative kernel) and the asynchronous persistent kernel
+    over a device work queue; each verified against the stored oracle hash."""
     import graphgen
     ro, col, w, src = graphgen.workload("grid4096")
     g = gg.Graph(ro, col, w, symmetric=True, stream=stream)
     m_trav = int(col.shape[0])
     out = {"workload": workload_desc("grid4096"), "source": int(src), "n": g.n, "m": g.m, "m_trav": m_trav}
-    for name, pol in (("bsp_cuda_graph", gg.GG_POLICY_BSP_GRAPH), ("bsp_persistent", gg.GG_POLICY_BSP_PERSISTENT),
-                      ("async_queue", gg.GG_POLICY_ASYNC_PERSISTENT)):
-        d, st = stats_run(gg, torch, g, src, pol, stream, direction=gg.GG_DIR_PUSH)
+    for name, pol, lb in (("bsp_cuda_graph", gg.GG_POLICY_BSP_GRAPH, gg.GG_LB_AUTO),
+                          ("bsp_cuda_graph_no_local_rounds", gg.GG_POLICY_BSP_GRAPH, gg.GG_LB_WARP),
+                          ("bsp_persistent", gg.GG_POLICY_BSP_PERSISTENT, gg.GG_LB_AUTO),
+                          ("async_queue", gg.GG_POLICY_ASYNC_PERSISTENT, gg.GG_LB_AUTO)):
+        d, st = stats_run(gg, torch, g, src, pol, stream, direction=gg.GG_DIR_PUSH, lb_mode=lb)
         ok = verify_single("grid4096", d)
-        per = time_sssp(gg, torch, g, src, gg.make_options(policy=pol, direction=gg.GG_DIR_PUSH), stream, steps, 1,
-                        flush)
+        per = time_sssp(gg, torch, g, src, gg.make_options(policy=pol, direction=gg.GG_DIR_PUSH, lb_mode=lb), stream,
+                        steps, 1, flush)
         t = statistics.median(per)
         out[name] = {"ms": t, "ms_min": min(per), "GTEPS": m_trav / (t * 1e-3) / 1e9,
                      "supersteps": st["iterations"], "edges_scanned": st["edges_scanned"],

@@ -496,7 +496,14 @@ void gg_server_config_default(gg_server_config* cfg);
  * round the budget in force is min(capacity, vertices in flight +
  * (free HBM - hbm_reserve_bytes) / 32), so when other allocations leave
  * less than the reserve free, queued queries wait (in-flight ones finish)
- * until memory is released.  max_slots <= 1024. */
+ * until memory is released.  max_slots <= 1024.
+ * Queries on graphs with a light/heavy width (mean degree >= 8, integer
+ * weights), when cfg.delta is 0, do not take slots: they are coalesced per
+ * graph, up to 64 queued sources of one graph at a time (round robin over the
+ * graphs), into one batched call (gg_sssp_batch_ex on the server's second
+ * stream, overlapping the slot launches) whose matrix columns are then copied
+ * to the queries' arrays.  A batch starts when the free HBM above the reserve
+ * holds its n x k distance matrix. */
 gg_status gg_server_create(const gg_server_config* cfg, gg_server_t* out);
 
 /* Queues the query (graph g, source src) whose distances go to dist_out

@@ -156,9 +156,11 @@ struct FilterOut {
 // the next frontier (LHM: their light edges, plus their heavy edges to the R
 // list of the epoch): one 64-bit atomicAdd per list returns the list position
 // and the edge-prefix base of the warp's entries.  Vertices without edges of
-// a kind are left out of that list.
+// a kind are left out of that list.  to_frontier = false: the R list only
+// (warp-local rounds expand the light edges themselves).
 template <bool LHM>
-__device__ __forceinline__ void append32(const StepArgs& a, const FilterOut& fo, bool have, uint32_t v) {
+__device__ __forceinline__ void append32(const StepArgs& a, const FilterOut& fo, bool have, uint32_t v,
+                                         bool to_frontier = true) {
   const unsigned FULL = 0xFFFFFFFFu;
   const uint32_t lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
@@ -177,7 +179,7 @@ __device__ __forceinline__ void append32(const StepArgs& a, const FilterOut& fo,
   }
 #pragma unroll
   for (int list = 0; list < (LHM ? 2 : 1); ++list) {
-    const bool mine = list == 0 ? lgt : hvy;
+    const bool mine = list == 0 ? (lgt && to_frontier) : hvy;
     const unsigned b = __ballot_sync(FULL, mine);
     if (b == 0u) continue;   // warp-uniform
     const uint32_t d = mine ? (list == 0 ? le - rs : re - le) : 0u;
@@ -574,18 +576,20 @@ __device__ __forceinline__ void bins_advance(MPSmem<BLOCK, EPT>& sm, const StepA
 // vertices pass the filter's dedup into a per-warp shared-memory queue that is
 // appended to the next frontier with one 64-bit atomicAdd per flush (queue
 // position and edge-prefix base), like the CTA queue of the tile advance.
-// LOCAL (load balance GG_LB_LOCAL, plain integer or float runs): near
-// vertices a warp improves are not deduplicated into the next frontier but
-// kept in a per-warp local queue, and after its share of the frontier the
-// warp runs up to GG_LOCAL_ROUNDS local rounds over that queue: each queued
-// vertex (read with its current distance) relaxes its out-edges, and the near
-// vertices those improve form the next local queue.  Every relaxation that
-// lowers a distance below the threshold queues the vertex (a queue entry per
-// improvement, no bitmap), so a vertex is expanded after its last decrease.
-// What the rounds leave (and what overflows a queue, and rows longer than
-// GG_LOCAL_MAX_DEG) goes to the next frontier through the bitmap as usual.
-// On a high-diameter graph this advances the wavefront several hops per
-// superstep.
+// LOCAL (load balance GG_LB_LOCAL; push supersteps other than the heavy
+// one): near vertices a warp improves are not deduplicated into the next
+// frontier but kept in a per-warp local queue, and after its share of the
+// frontier the warp runs up to GG_LOCAL_ROUNDS local rounds over that queue:
+// each queued vertex (read with its current distance) relaxes its out-edges,
+// and the near vertices those improve form the next local queue.  Every
+// relaxation that lowers a distance below the threshold queues the vertex (a
+// queue entry per improvement, no bitmap), so a vertex is expanded after its
+// last decrease.  What the rounds leave (and what overflows a queue, and rows
+// longer than GG_LOCAL_MAX_DEG) goes to the next frontier through the bitmap
+// as usual.  With light/heavy buckets the rounds expand light rows, and every
+// queued vertex joins the epoch's R list once (by its R bitmap) as in the
+// plain filter.  On a high-diameter graph this advances the wavefront several
+// hops per superstep.
 template <int BLOCK, int EPT, bool PK, bool LOCAL = false>
 __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, uint32_t F, uint32_t Etot,
                                              const uint32_t* __restrict__ S, const uint32_t* __restrict__ R,
@@ -619,7 +623,8 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
       const uint32_t bit = 1u << (v & 31);
       win = !(atomicOr(fo.bm_next + (v >> 5), bit) & bit);
     }
-    append32<false>(a, fo, win, v);
+    if (fo.lh) append32<true>(a, fo, win, v);   // warp-uniform
+    else append32<false>(a, fo, win, v);
   };
   uint32_t fmin = kInf;
   bool ovf = false;
@@ -631,6 +636,12 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
   auto flush_near = [&]() {
     __syncwarp();
     if (LOCAL) {
+      // light/heavy buckets: every near vertex joins the epoch's R list once
+      // (its heavy edges wait for the heavy superstep); the light edges are
+      // expanded by the local rounds or, after a hand-off, the next frontier
+      if (fo.lh)
+        for (uint32_t i0 = 0; i0 < qn; i0 += 32)
+          append32<true>(a, fo, i0 + lane < qn, i0 + lane < qn ? qv[i0 + lane] : 0u, false);
       // into the local queue; what does not fit goes to the next frontier
       const uint32_t take = min(QL - lqn, qn);
       for (uint32_t i = lane; i < take; i += 32) {
@@ -854,7 +865,7 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
           v = cur[i];
           du = ld_cg(dist + v);
           rs = __ldg(fo.ro + v);
-          deg = __ldg(fo.ro + v + 1) - rs;
+          deg = (fo.lh ? __ldg(a.lb.lend + v) : __ldg(fo.ro + v + 1)) - rs;   // light/heavy: light row
           // a later improvement queued v again with a smaller distance: that
           // entry expands it, this one is stale
           if (du < cur[QL + i]) deg = 0;
@@ -1408,8 +1419,8 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_supers
       else if ((LB == LB_WARP || LB == LB_LOCAL) && LH && mode == MODE_HEAVY)   // separate copies keep the
         warp_advance<BLOCK, EPT, PK>(sm, a, fw, Ew, fS, fR, fV, edges, dist, bm_cur, fo);   // pointer selects out
       else if (LB == LB_WARP || LB == LB_LOCAL)                                              // of the loop
-        warp_advance<BLOCK, EPT, PK, LB == LB_LOCAL && !LH>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], edges,
-                                                            dist, a.fr.bm[it % 3], fo);
+        warp_advance<BLOCK, EPT, PK, LB == LB_LOCAL>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], edges, dist,
+                                                     a.fr.bm[it % 3], fo);
       else
         mp_advance<BLOCK, EPT, false, PK>(sm, a, fw, Ew, fS, fR, fV, edges, dist, bm_cur, fo);
     } else {

@@ -31,14 +31,26 @@ constexpr int kMB = 256;
 constexpr int kMEpt = 4;
 constexpr int kMTile = kMB * kMEpt;
 constexpr int kMCap = kMTile + 1;
+#ifndef GG_MULTI_LOCAL_ROUNDS
+#define GG_MULTI_LOCAL_ROUNDS 8   // CTA-local rounds per superstep (0: none)
+#endif
+constexpr uint32_t kMLocalCap = 256;      // entries of each CTA-local queue
+constexpr uint32_t kMLocalMaxDeg = 4;     // longer rows go to the union next frontier
 
 struct MSmem {
   uint32_t es[kMCap], eb[kMCap], ec[kMCap], eq[kMCap];
   uint32_t qv[kMCap], qr[kMCap], qd[kMCap], qq[kMCap];
   uint32_t wsum[kMB / 32];
   uint32_t qn, j, last;
+  // CTA-local rounds: two queues of (vertex, distance it was queued with, slot)
+  uint32_t lv[2][kMLocalCap], ld[2][kMLocalCap], lq[2][kMLocalCap];
+  uint32_t ln[2];
   unsigned long long base;
 };
+
+__device__ __forceinline__ uint32_t* lq_v(MSmem& sm, uint32_t k) { return sm.lv[k]; }
+__device__ __forceinline__ uint32_t* lq_d(MSmem& sm, uint32_t k) { return sm.ld[k]; }
+__device__ __forceinline__ uint32_t* lq_q(MSmem& sm, uint32_t k) { return sm.lq[k]; }
 
 __device__ __forceinline__ uint2 slot_edge(const MultiSlot& s, uint32_t e) {
   if (s.packed) {
@@ -75,6 +87,24 @@ __device__ __forceinline__ void m_filter(MSmem& sm, const MultiBufs& b, MultiSlo
   }
 }
 
+// Filter with CTA-local rounds: a near vertex goes to local queue k (no
+// bitmap: one entry per improvement, with the distance it was improved to)
+// while there is room, else through the bitmap to the union next frontier;
+// far vertices are parked as in m_filter.
+__device__ __forceinline__ void m_filter_local(MSmem& sm, const MultiBufs& b, MultiSlot* slots, uint32_t q,
+                                               const MultiSlot& sl, uint32_t p, uint32_t v, uint32_t nd, uint32_t k) {
+  if (nd < sl.t_cur) {
+    const uint32_t i = atomicAdd(&sm.ln[k], 1u);
+    if (i < kMLocalCap) {
+      lq_v(sm, k)[i] = v;
+      lq_d(sm, k)[i] = nd;
+      lq_q(sm, k)[i] = q;
+      return;
+    }
+  }
+  m_filter(sm, b, slots, q, sl, p, v, nd);
+}
+
 // Appends the CTA's queued (slot, vertex) entries to the union next frontier.
 __device__ __forceinline__ void m_flush(MSmem& sm, const MultiBufs& b, MultiCtl* ctl, uint32_t p) {
   __syncthreads();
@@ -107,7 +137,11 @@ __global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphC
   const unsigned long long c = ctl->cnt[p];
   const uint32_t F = (uint32_t)(c >> 32), E = (uint32_t)c;
   MultiSlot* slots = b.slots;
-  if (tid == 0) sm.qn = 0;
+  if (tid == 0) {
+    sm.qn = 0;
+    sm.ln[0] = 0;
+    sm.ln[1] = 0;
+  }
   __syncthreads();
   const uint32_t e0 = (uint32_t)(((unsigned long long)blockIdx.x * E) / gridDim.x);
   const uint32_t e1 = (uint32_t)(((unsigned long long)(blockIdx.x + 1) * E) / gridDim.x);
@@ -156,12 +190,69 @@ __global__ void __launch_bounds__(kMB) k_multi_superstep(MultiBufs b, cudaGraphC
           if (ovf) atomicOr(&slots[q].status, DS_OVERFLOW);
           if (nd < ld_cg(sl.dist + ed.x)) {
             atomicMin(sl.dist + ed.x, nd);
-            m_filter(sm, b, slots, q, sl, p, ed.x, nd);
+            if (GG_MULTI_LOCAL_ROUNDS) m_filter_local(sm, b, slots, q, sl, p, ed.x, nd, 0);
+            else m_filter(sm, b, slots, q, sl, p, ed.x, nd);
           }
         }
       }
       m_flush(sm, b, ctl, p);
       j = j + nent - 1;
+    }
+  }
+  // CTA-local rounds: the near vertices this CTA improved are expanded here,
+  // up to GG_MULTI_LOCAL_ROUNDS times, before the rest joins the union next
+  // frontier.  An entry whose vertex has dropped below the distance it was
+  // queued with is stale (the later decrease queued it again); rows longer
+  // than kMLocalMaxDeg go to the next frontier through the bitmap.  On
+  // high-diameter graphs a superstep covers several hops.
+  if (GG_MULTI_LOCAL_ROUNDS) {
+    uint32_t k = 0;
+    for (int r = 0; r < GG_MULTI_LOCAL_ROUNDS; ++r) {
+      __syncthreads();
+      const uint32_t n_cur = min(sm.ln[k], kMLocalCap);
+      if (n_cur == 0) break;   // CTA-uniform
+      __syncthreads();
+      if (tid == 0) sm.ln[k ^ 1u] = 0;
+      __syncthreads();
+      for (uint32_t base = 0; base < n_cur; base += kMB) {   // CTA-uniform
+        const uint32_t i = base + tid;
+        if (i < n_cur) {
+          const uint32_t v = sm.lv[k][i], nq = sm.ld[k][i], q = sm.lq[k][i];
+          const MultiSlot& sl = slots[q];
+          const uint32_t du = ld_cg(sl.dist + v);
+          if (du >= nq) {
+            const uint32_t rs = __ldg(sl.ro + v), re = __ldg(sl.ro + v + 1);
+            if (re - rs > kMLocalMaxDeg) {
+              m_filter(sm, b, slots, q, sl, p, v, du);
+            } else {
+              for (uint32_t e = rs; e < re; ++e) {
+                const uint2 ed = slot_edge(sl, e);
+                bool ovf = false;
+                const uint32_t nd = add_sat(du, ed.y, ovf);
+                if (ovf) atomicOr(&slots[q].status, DS_OVERFLOW);
+                if (nd < ld_cg(sl.dist + ed.x)) {
+                  atomicMin(sl.dist + ed.x, nd);
+                  m_filter_local(sm, b, slots, q, sl, p, ed.x, nd, k ^ 1u);
+                }
+              }
+            }
+          }
+        }
+        m_flush(sm, b, ctl, p);
+      }
+      k ^= 1u;
+    }
+    __syncthreads();
+    // what the rounds leave: the union next frontier, through the bitmap
+    const uint32_t n_left = min(sm.ln[k], kMLocalCap);
+    for (uint32_t base = 0; base < n_left; base += kMB) {   // CTA-uniform
+      const uint32_t i = base + tid;
+      if (i < n_left) {
+        const uint32_t v = sm.lv[k][i], q = sm.lq[k][i];
+        const MultiSlot& sl = slots[q];
+        m_filter(sm, b, slots, q, sl, p, v, ld_cg(sl.dist + v));
+      }
+      m_flush(sm, b, ctl, p);
     }
   }
   // split work: the far piles of the slots flagged by the previous superstep,

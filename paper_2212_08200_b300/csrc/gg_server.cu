@@ -21,6 +21,16 @@
 // New queries therefore join while others are mid-flight and share every
 // superstep launch with them; a query's result does not depend on what it
 // shared the GPU with (distances are exact integers).
+//
+// Queries on graphs with a light/heavy width (skewed graphs with integer
+// weights, when the server uses the graphs' default bucket widths) are
+// coalesced per graph instead: the worker takes up to 64 queued sources of
+// one graph (round robin over the graphs with queued queries) into one
+// batched call (gg_sssp_batch_ex: normalised buckets, light-first rounds with
+// a pulled heavy superstep) on a second stream, then copies each column of
+// the distance matrix to its query's array.  Such a batch overlaps the slot
+// engine's launches; queries arriving meanwhile wait for the next batch of
+// their graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,6 +51,17 @@ using Clock = std::chrono::steady_clock;
 
 namespace {
 
+#ifndef GG_MULTI_SKEW_DELTA
+#define GG_MULTI_SKEW_DELTA 0   // multiple of the light/heavy width used as the slot's near-far width on
+#endif                          // skewed graphs (0: the graph's own default, no buckets)
+
+// Near-far width of a query slot when the caller asks for the graph's default.
+uint32_t slot_default_delta(const gg_graph* g) {
+  if (GG_MULTI_SKEW_DELTA && g->default_delta == GG_DELTA_NONE && g->default_delta_lh != GG_DELTA_NONE)
+    return (uint32_t)std::min<uint64_t>((uint64_t)g->default_delta_lh * GG_MULTI_SKEW_DELTA, 0xFFFFFFFEull);
+  return g->default_delta;
+}
+
 void fill_slot(MultiSlot& s, const gg_graph* g, uint32_t src, uint32_t* dist, uint32_t ticket, uint32_t off0,
                uint32_t off1, uint32_t off2, uint32_t far0, uint32_t far1, uint32_t delta) {
   s = MultiSlot{};
@@ -56,7 +77,7 @@ void fill_slot(MultiSlot& s, const gg_graph* g, uint32_t src, uint32_t* dist, ui
   s.bm_off[2] = off2;
   s.state = kSlotFree;
   s.ticket = ticket;
-  multi_slot_buckets(s, delta == 0 ? g->default_delta : delta, far0, far1);
+  multi_slot_buckets(s, delta == 0 ? slot_default_delta(g) : delta, far0, far1);
 }
 
 // ---- gg_sssp_multi: a process-wide engine per device, grown on demand -------
@@ -177,6 +198,16 @@ struct gg_server {
   uint32_t running = 0;
   std::vector<double> lat_us;
   gg_server_stats st{};
+  // per-graph source batches (skewed graphs)
+  std::unordered_map<gg_graph*, std::deque<uint64_t>> gq;   // queued tickets per graph
+  std::deque<gg_graph*> gorder;                             // graphs with queued tickets, round robin
+  cudaStream_t bstream = nullptr;
+  cudaEvent_t bev = nullptr;
+  std::vector<uint64_t> btickets;   // the batch in flight (empty: none)
+  gg_graph* bgraph = nullptr;
+  uint32_t* bmat = nullptr;         // its distance matrix (n x k) and the k output pointers after it
+  uint32_t** h_bptr = nullptr;      // pinned staging of the output pointers
+  uint32_t* h_bsrc = nullptr;       // pinned staging of the sources
 };
 
 namespace {
@@ -195,6 +226,104 @@ uint64_t live_budget(const gg_server* s) {
   const uint64_t head = free_b > s->cfg.hbm_reserve_bytes ? (free_b - s->cfg.hbm_reserve_bytes) / kBytesPerFlightVertex
                                                           : 0ull;
   return std::min<uint64_t>(s->eng.cap_vertices, s->used_vertices + head);
+}
+
+constexpr uint32_t kServerBatch = 64;
+
+// Whether a query on g goes to a per-graph source batch.
+bool batched_graph(const gg_server* s, const gg_graph* g) {
+  return s->cfg.delta == 0 && g->default_delta_lh != GG_DELTA_NONE && g->m > 0 && !g->float_weights;
+}
+
+// out[s][v] := mat[v * k + s]: one thread per vertex, row read once, each
+// column written coalesced across the warp
+__global__ void k_scatter_columns(const uint32_t* __restrict__ mat, uint32_t n, uint32_t k,
+                                  uint32_t* const* __restrict__ out) {
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    const uint32_t* row = mat + (size_t)v * k;
+    for (uint32_t c = 0; c < k; ++c) out[c][v] = row[c];
+  }
+}
+
+// Starts the next per-graph batch on the batch stream when none is in flight
+// and the free HBM above the reserve holds its distance matrix.  Called with
+// the server lock held; returns false when nothing was started.
+bool start_batch(gg_server* s) {
+  if (!s->btickets.empty() || s->gorder.empty()) return false;
+  gg_graph* g = s->gorder.front();
+  std::deque<uint64_t>& q = s->gq[g];
+  const uint32_t k = (uint32_t)std::min<size_t>(q.size(), kServerBatch);
+  const uint64_t mat_bytes = 4ull * g->n * k + 8ull * kServerBatch + 256;
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || free_b < s->cfg.hbm_reserve_bytes + mat_bytes)
+    return false;   // wait for memory (other work finishes first)
+  s->gorder.pop_front();
+  for (uint32_t i = 0; i < k; ++i) {
+    const uint64_t t = q.front();
+    q.pop_front();
+    gg_server::Req& r = s->reqs[t];
+    r.state = 1;
+    s->btickets.push_back(t);
+    s->h_bsrc[i] = r.src;
+    s->h_bptr[i] = r.dist;
+  }
+  if (!q.empty()) s->gorder.push_back(g);   // more of this graph: after the other graphs
+  else s->gq.erase(g);
+  s->bgraph = g;
+  gg_status st = GG_OK;
+  char* buf = nullptr;
+  cudaError_t e = dev_malloc(&buf, mat_bytes, s->bstream);
+  if (e == cudaSuccess) {
+    s->bmat = reinterpret_cast<uint32_t*>(buf);
+    uint32_t** dptr = reinterpret_cast<uint32_t**>(buf + ((4ull * g->n * k + 255) & ~255ull));
+    e = cudaMemcpyAsync(dptr, s->h_bptr, sizeof(uint32_t*) * k, cudaMemcpyHostToDevice, s->bstream);
+    if (e == cudaSuccess) st = gg_sssp_batch_ex(g, s->h_bsrc, k, s->bmat, nullptr, s->bstream);
+    if (e == cudaSuccess && st == GG_OK) {
+      const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((g->n + 255) / 256, 4096));
+      k_scatter_columns<<<grid, 256, 0, s->bstream>>>(s->bmat, g->n, k, dptr);
+      e = cudaGetLastError();
+    }
+    dev_free(buf, s->bstream);
+    s->bmat = nullptr;
+  }
+  if (e == cudaSuccess && st == GG_OK) e = cudaEventRecord(s->bev, s->bstream);
+  if (e != cudaSuccess || st != GG_OK) {
+    // the batch could not be launched: its queries fail with the error
+    const gg_status fs = st != GG_OK ? st : GG_ERR_CUDA;
+    const Clock::time_point now = Clock::now();
+    for (uint64_t t : s->btickets) {
+      gg_server::Req& r = s->reqs[t];
+      r.state = 2;
+      r.status = fs;
+      r.t_done = now;
+    }
+    s->btickets.clear();
+    s->cv_done.notify_all();
+    return false;
+  }
+  return true;
+}
+
+// Retires the batch in flight once its event completed (wait: block for it).
+// Called with the server lock held.
+void finish_batch(gg_server* s, bool wait) {
+  if (s->btickets.empty()) return;
+  cudaError_t e = wait ? cudaEventSynchronize(s->bev) : cudaEventQuery(s->bev);
+  if (e == cudaErrorNotReady) return;
+  gg_status st = e == cudaSuccess ? gg_graph_check(s->bgraph) : GG_ERR_CUDA;
+  const Clock::time_point now = Clock::now();
+  for (uint64_t t : s->btickets) {
+    gg_server::Req& r = s->reqs[t];
+    r.state = 2;
+    r.status = st;
+    r.t_done = now;
+    s->lat_us.push_back(std::chrono::duration<double, std::micro>(now - r.t_submit).count());
+    s->st.completed += 1;
+  }
+  s->st.launches += 1;
+  s->btickets.clear();
+  s->bgraph = nullptr;
+  s->cv_done.notify_all();
 }
 
 void server_loop(gg_server* s) {
@@ -227,8 +356,19 @@ void server_loop(gg_server* s) {
           ++s->running;
         }
         s->st.max_running = std::max(s->st.max_running, s->running);
+        // per-graph batches: retire a finished one, start the next
+        finish_batch(s, false);
+        start_batch(s);
+        s->st.max_running = std::max<uint32_t>(s->st.max_running, s->running + (uint32_t)s->btickets.size());
         if (s->running > 0 || !admit.empty()) break;
-        if (s->stop) return;
+        if (!s->btickets.empty()) {   // only a batch in flight: wait for it without the lock
+          lk.unlock();
+          cudaEventSynchronize(s->bev);
+          lk.lock();
+          finish_batch(s, false);
+          continue;
+        }
+        if (s->stop && s->gorder.empty()) return;
         s->cv_work.wait_for(lk, std::chrono::milliseconds(2));
       }
     }
@@ -329,7 +469,11 @@ gg_status gg_server_create(const gg_server_config* cfg, gg_server_t* out) {
   gg_status st = multi_engine_init(&s->eng, s->cfg.max_slots, cap, words, far_entries, true);
   if (st == GG_OK) {
     e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamCreate");
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->bstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->bev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_bptr, sizeof(uint32_t*) * kServerBatch);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->h_bsrc, sizeof(uint32_t) * kServerBatch);
+    if (e != cudaSuccess) st = cuda_fail(e, "server streams");
   }
   if (st == GG_OK) st = multi_engine_reset(&s->eng, s->stream);
   if (st == GG_OK) {
@@ -342,6 +486,10 @@ gg_status gg_server_create(const gg_server_config* cfg, gg_server_t* out) {
   if (st != GG_OK) {
     multi_engine_free(&s->eng);
     if (s->stream) cudaStreamDestroy(s->stream);
+    if (s->bstream) cudaStreamDestroy(s->bstream);
+    if (s->bev) cudaEventDestroy(s->bev);
+    if (s->h_bptr) cudaFreeHost(s->h_bptr);
+    if (s->h_bsrc) cudaFreeHost(s->h_bsrc);
     delete s;
     return st;
   }
@@ -374,7 +522,13 @@ gg_status gg_server_submit(gg_server_t s, gg_graph_t g, uint32_t src, uint32_t* 
   r.dist = dist_out;
   r.t_submit = Clock::now();
   s->reqs[t] = r;
-  s->queue.push_back(t);
+  if (batched_graph(s, g)) {   // per-graph source batch
+    std::deque<uint64_t>& q = s->gq[g];
+    if (q.empty()) s->gorder.push_back(g);
+    q.push_back(t);
+  } else {
+    s->queue.push_back(t);
+  }
   s->st.submitted += 1;
   *ticket = t;
   s->cv_work.notify_one();
@@ -416,8 +570,10 @@ gg_status gg_server_get_stats(gg_server_t s, gg_server_stats* out) {
   if (!s || !out) return fail(GG_ERR_INVALID_ARG, "NULL argument");
   std::lock_guard<std::mutex> lk(s->mu);
   gg_server_stats st = s->st;
-  st.queued = (uint32_t)s->queue.size();
-  st.running = s->running;
+  size_t gq = 0;
+  for (const auto& kv : s->gq) gq += kv.second.size();
+  st.queued = (uint32_t)(s->queue.size() + gq);
+  st.running = s->running + (uint32_t)s->btickets.size();
   st.p50_us = percentile(s->lat_us, 0.50);
   st.p99_us = percentile(s->lat_us, 0.99);
   double sum = 0, mx = 0;
@@ -448,8 +604,13 @@ gg_status gg_server_destroy(gg_server_t s) {
   s->cv_work.notify_all();
   if (s->worker.joinable()) s->worker.join();   // drains queued and in-flight queries first
   cudaStreamSynchronize(s->stream);
+  cudaStreamSynchronize(s->bstream);
   multi_engine_free(&s->eng);
   cudaStreamDestroy(s->stream);
+  cudaStreamDestroy(s->bstream);
+  cudaEventDestroy(s->bev);
+  cudaFreeHost(s->h_bptr);
+  cudaFreeHost(s->h_bsrc);
   delete s;
   return GG_OK;
 }
