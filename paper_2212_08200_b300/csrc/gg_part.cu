@@ -227,8 +227,10 @@ gg_status gg_part_create(uint32_t n_global, uint32_t rank, uint32_t nranks, uint
     }
   }
   if (mine != n_local) return fail(GG_ERR_INVALID_ARG, "route assigns a different number of vertices to this rank");
+  int device = -1;
+  GG_CK(cudaGetDevice(&device));
   gg_part* p = new gg_part();
-  GG_CK(cudaGetDevice(&p->device));
+  p->device = device;
   p->n_global = n_global;
   p->rank = rank;
   p->nranks = nranks;

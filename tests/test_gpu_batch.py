@@ -135,3 +135,32 @@ def test_batch_argument_errors():
     with pytest.raises(m.GGError):
         m.gg_sssp_batch(g.handle, np.zeros(0, np.uint32), out)
     g.close()
+
+
+@pytest.mark.parametrize("lh,delta", [(2, 0), (2, 20), (0, 20), (0, 255), (1, 0)])
+def test_batch_schedules_and_widths(lh, delta):
+    """The batched schedules side by side on a skewed graph: light-first
+    rounds (GG_LH_ROUNDS), normalised buckets at an explicit light/heavy
+    width, the largest width (every edge light) and no light/heavy split
+    (GG_LH_OFF): the same distances as the oracle."""
+    ro, col, w, _ = graphgen.workload("rmat16")
+    srcs = graphgen.sample_sources(ro, 40, seed=13)
+    g = gg().Graph(ro, col, w, symmetric=True)
+    got, st = run_batch(g, srcs, light_heavy=lh, delta=delta)
+    np.testing.assert_array_equal(got.T, oracle.dijkstra_many(ro, col, w, srcs, threads=8))
+    assert st["device_status"] == 0
+    g.close()
+
+
+def test_batch_directed_graph_normalised_buckets():
+    """A directed skewed graph (no pull: its heavy in-edges are not its
+    out-edges) with sinks: normalised buckets with the heavy push."""
+    rng = np.random.Generator(np.random.PCG64(8))
+    n, m = 20000, 400000
+    src = rng.integers(0, 15000, m)                  # vertices 15000.. have no out-edges
+    ro, col, w = graphgen.from_edges(n, src, rng.integers(0, n, m), rng.integers(1, 256, m))
+    srcs = graphgen.sample_sources(ro, 33, seed=2)
+    g = gg().Graph(ro, col, w)
+    got, _ = run_batch(g, srcs)
+    np.testing.assert_array_equal(got.T, oracle.dijkstra_many(ro, col, w, srcs, threads=8))
+    g.close()
