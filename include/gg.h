@@ -154,7 +154,9 @@ typedef struct {
     uint32_t* trace;           /* device u32[trace_cap*4] or NULL.  BSP: per superstep
                                   (frontier size, frontier edges, kind 0 push / 1 pull
                                   / 2 near-far split / 3 heavy-edge push / 4 heavy-edge
-                                  pull, next frontier size).  ASYNC: per
+                                  pull / 5 heavy-edge pull that ends the buckets and
+                                  writes the plain push's first frontier, next
+                                  frontier size).  ASYNC: per
                                   near-far split (split number, new threshold, far-pile
                                   size, microseconds since the kernel started)         */
     uint32_t trace_cap;

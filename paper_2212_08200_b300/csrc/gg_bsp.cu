@@ -76,6 +76,9 @@
 #ifndef GG_LH_TAIL
 #define GG_LH_TAIL 1   // light/heavy: plain push once bucketing has ended
 #endif
+#ifndef GG_PULL_TAIL
+#define GG_PULL_TAIL 1   // a heavy pull after which bucketing ends writes the plain tail's frontier
+#endif
 #ifndef GG_LOCAL_ROUNDS
 #define GG_LOCAL_ROUNDS 16   // warp-local rounds per superstep (load balance GG_LB_LOCAL; 4096^2 grid: 43 ms at 4, 36 at 8, 34 at 16)
 #endif
@@ -1045,7 +1048,12 @@ __device__ __forceinline__ void far_split(MPSmem<BLOCK, EPT>& sm, const StepArgs
 // edges per step; each v is written by its own lane only (no atomics on
 // dist).  Chosen over the push form when R's heavy edges outnumber those of
 // the unsettled vertices (the dense core settles first on skewed graphs).
-template <int BLOCK, int EPT, bool PK>
+// TAIL: bucketing ends after this step (threshold infinite, plain push over
+// all edges).  The unsettled vertices with a finite distance are then exactly
+// the vertices the split would move from the far pile into the frontier, so
+// they go straight to the next frontier (all edges of their rows, through a
+// per-warp queue) and the split step is skipped.
+template <int BLOCK, int EPT, bool PK, bool TAIL>
 __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, const FilterOut& fo,
                                            uint32_t* __restrict__ dist, uint32_t* __restrict__ bm_r_old) {
   const unsigned FULL = 0xFFFFFFFFu;
@@ -1058,6 +1066,42 @@ __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArg
   static_assert((BLOCK / 32) * kFarQ <= (uint32_t)MPSmem<BLOCK, EPT>::ECAP, "per-warp far queues fit");
   uint32_t* fq = sm.es + warp * kFarQ;   // per-warp far queue
   uint32_t fn = 0;
+  // TAIL: per-warp queue of next-frontier entries (vertex, row start, degree
+  // and then its prefix), one counter atomic per run of up to kTailQ
+  constexpr uint32_t kTailQ = 128;
+  static_assert((BLOCK / 32) * kTailQ <= (uint32_t)MPSmem<BLOCK, EPT>::ECAP, "per-warp tail queues fit");
+  uint32_t* tqv = sm.qv + warp * kTailQ;
+  uint32_t* tqr = sm.qr + warp * kTailQ;
+  uint32_t* tqd = sm.qd + warp * kTailQ;
+  uint32_t tqn = 0;   // warp-uniform
+  auto tail_flush = [&]() {
+    __syncwarp();
+    uint32_t run = 0;
+    for (uint32_t i0 = 0; i0 < tqn; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      const uint32_t d = i < tqn ? tqd[i] : 0u;
+      uint32_t x = d;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= (uint32_t)o) x += y;
+      }
+      if (i < tqn) tqd[i] = run + x - d;
+      run += __shfl_sync(FULL, x, 31);
+    }
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(fo.cnt_next, ((unsigned long long)tqn << 32) | run);
+    b = __shfl_sync(FULL, b, 0);
+    __syncwarp();
+    const uint32_t pos0 = (uint32_t)(b >> 32), eb0 = (uint32_t)b;
+    for (uint32_t i = lane; i < tqn; i += 32) {
+      fo.nfv[pos0 + i] = tqv[i];
+      fo.nfr[pos0 + i] = tqr[i];
+      fo.nfs[pos0 + i] = eb0 + tqd[i];
+    }
+    tqn = 0;
+    __syncwarp();
+  };
   // the consumed R list is not read: clear its membership bitmap outright
   for (uint32_t i = blockIdx.x * BLOCK + threadIdx.x; i < a.g.nwords; i += gridDim.x * BLOCK) bm_r_old[i] = 0u;
   const uint32_t W = gridDim.x * (BLOCK / 32);
@@ -1086,7 +1130,7 @@ __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArg
       if (lane >= (uint32_t)o) x += y;
     }
     const uint32_t T = __shfl_sync(FULL, x, 31);
-    if (T == 0) continue;   // warp-uniform
+    if (!TAIL && T == 0) continue;   // warp-uniform
     const uint32_t ex = x - deg;   // first list position of this lane's edges
     wbest[lane] = kInf;
     __syncwarp();
@@ -1129,6 +1173,32 @@ __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArg
     }
     __syncwarp();
     const uint32_t best = wbest[lane];
+    if (TAIL) {
+      bool join = false;
+      uint32_t rs = 0, full = 0;
+      if (have && dv >= t_cur) {
+        if (best < dv) dist[v] = best;
+        if (min(best, dv) != kInf) {
+          rs = __ldg(fo.ro + v);
+          full = hs + deg - rs;   // the whole row: [ro[v], ro[v+1])
+          join = full > 0;
+        }
+      }
+      const unsigned jb = __ballot_sync(FULL, join);
+      if (jb) {   // warp-uniform
+        if (join) {
+          const uint32_t off = tqn + __popc(jb & lt);
+          tqv[off] = v;
+          tqr[off] = rs;
+          tqd[off] = full;
+        }
+        tqn += __popc(jb);
+        if (tqn > kTailQ - 32) tail_flush();
+      }
+      scanned += T;
+      __syncwarp();
+      continue;
+    }
     bool far = false;
     if (have && best < dv) {
       dist[v] = best;
@@ -1149,6 +1219,7 @@ __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArg
     __syncwarp();
   }
   if (GG_FAR_Q && fn) far_q_flush(fq, fn, fo);
+  if (TAIL && tqn) tail_flush();
 #pragma unroll
   for (int o = 16; o; o >>= 1) fmin = min(fmin, __shfl_xor_sync(FULL, fmin, o));
   if (lane == 0) {
@@ -1223,8 +1294,10 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
 
     const uint32_t fn = (uint32_t)(cn >> 32), En = (uint32_t)cn;
     if (mode == MODE_SPLIT) fp ^= 1u;   // the kept entries were written to the other pile
-    const uint32_t nfar = fp ? fc1 : fc0;
-    const bool heavy = mode == MODE_HEAVY || mode == MODE_HEAVY_PULL;
+    // a pull that ended bucketing consumed the far pile into the next frontier
+    const bool pulled_tail = mode == MODE_HEAVY_PULL_TAIL;
+    const uint32_t nfar = pulled_tail ? 0u : fp ? fc1 : fc0;
+    const bool heavy = mode == MODE_HEAVY || mode == MODE_HEAVY_PULL || pulled_tail;
     const bool lhb = lh && !lh_tail;   // bucketed light/heavy supersteps
     bool tail = false;
     uint32_t rn = 0;   // R list of the epoch the next superstep works in
@@ -1240,7 +1313,7 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
     }
     uint32_t nm;
     uint32_t t_next = t_cur;
-    if (lhb && (fn > 0 || rn > 0)) {
+    if (lhb && !pulled_tail && (fn > 0 || rn > 0)) {
       // light edges of the near frontier first; when it is empty, one heavy
       // superstep over the vertices that settled since the last one
       nm = fn > 0 ? MODE_PUSH : MODE_HEAVY;
@@ -1248,7 +1321,14 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
         // pull when R's heavy edges outnumber those still unsettled (plus the
         // cost of the dense pass over the distances)
         const unsigned long long left = heavy_total > heavy_done + rE ? heavy_total - heavy_done - rE : 0ull;
-        if (rE > left + a.g.n / 8) nm = MODE_HEAVY_PULL;
+        if (rE > left + a.g.n / 8) {
+          nm = MODE_HEAVY_PULL;
+          // the split after this pull would end bucketing (the drain rule
+          // below, on the heavy edges left once R's are relaxed): the pull
+          // writes the plain tail's first frontier itself
+          if (GG_PULL_TAIL && GG_LH_TAIL && drain_div && left * drain_div < (unsigned long long)a.g.m)
+            nm = MODE_HEAVY_PULL_TAIL;
+        }
       }
     } else if (fn == 0 && nfar > 0) {
       // near frontier exhausted: raise the threshold past the smallest parked distance
@@ -1292,7 +1372,11 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
       ctl->fp = fp;
       ctl->splits = splits + 1u;
     }
-    if (tail) ctl->lh_tail = 1u;
+    if (tail || pulled_tail) ctl->lh_tail = 1u;
+    if (pulled_tail) {
+      ctl->far_cnt[0] = 0u;
+      ctl->far_cnt[1] = 0u;
+    }
     if (lhb && heavy) {
       ctl->heavy_done = heavy_done;
       ctl->rcnt[(epoch - 1u) & 1u] = 0ull;
@@ -1321,6 +1405,10 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
     if (nm == MODE_SPLIT) {
       ctl->t_prev = t_cur;
       ctl->t_cur = t_next;
+      ctl->far_min = kInf;
+    } else if (pulled_tail) {   // one unbounded bucket from here on
+      ctl->t_prev = t_cur;
+      ctl->t_cur = kInf;
       ctl->far_min = kInf;
     }
     ctl->mode = nm;
@@ -1388,14 +1476,15 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_supers
   if (LH) {
     // new near vertices join the R list of the current epoch, or of the next
     // one while the heavy superstep consumes the current list
-    const uint32_t rj = (mode == MODE_HEAVY || mode == MODE_HEAVY_PULL ? ep + 1u : ep) & 1u;
+    const bool hv = mode == MODE_HEAVY || mode == MODE_HEAVY_PULL || mode == MODE_HEAVY_PULL_TAIL;
+    const uint32_t rj = (hv ? ep + 1u : ep) & 1u;
     // the light/heavy append checks both degrees itself; after bucketing the
     // appends are plain (all edges of a row of the light-first copy), with the
     // plain loop's own handling of vertices without out-edges
     fo.sinks = lh_tail ? a.g.sinks : 0u;
     fo.lh = lh_tail ? 0u : 1u + rj;
     edges = a.lb.edges;
-    if (mode == MODE_HEAVY || mode == MODE_HEAVY_PULL) {
+    if (hv) {
       const uint32_t rc = ep & 1u;
       const unsigned long long r = rc ? r1 : r0;
       fw = (uint32_t)(r >> 32);
@@ -1410,7 +1499,9 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_supers
   if (mode == MODE_SPLIT) {
     far_split(sm, a, fo, dist, a.fr.far[fp], fp ? fc1 : fc0, t_prev);
   } else if (LH && mode == MODE_HEAVY_PULL) {
-    heavy_pull<BLOCK, EPT, PK>(sm, a, fo, dist, pick2(a.lb.bm_r, ep & 1u));
+    heavy_pull<BLOCK, EPT, PK, false>(sm, a, fo, dist, pick2(a.lb.bm_r, ep & 1u));
+  } else if (LH && mode == MODE_HEAVY_PULL_TAIL) {
+    heavy_pull<BLOCK, EPT, PK, true>(sm, a, fo, dist, pick2(a.lb.bm_r, ep & 1u));
   } else if (fw > 0) {
     if (mode == MODE_PUSH || mode == MODE_HEAVY) {
       if (LB == LB_BINS)

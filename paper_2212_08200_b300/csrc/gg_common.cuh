@@ -35,7 +35,10 @@ constexpr uint32_t kFltMaxBits = 0x7F7FFFFFu;   // FLT_MAX: "unreached" for bina
 // binary32 bit patterns (the paper's float weights), or unit weights (BFS).
 enum : uint32_t { WM_U32 = 0, WM_F32 = 1, WM_UNIT = 2 };
 
-enum : uint32_t { MODE_PUSH = 0, MODE_PULL = 1, MODE_SPLIT = 2, MODE_HEAVY = 3, MODE_HEAVY_PULL = 4 };
+// MODE_HEAVY_PULL_TAIL: a heavy pull after which bucketing ends; it writes the
+// plain tail's first frontier itself (no split step follows)
+enum : uint32_t { MODE_PUSH = 0, MODE_PULL = 1, MODE_SPLIT = 2, MODE_HEAVY = 3, MODE_HEAVY_PULL = 4,
+                  MODE_HEAVY_PULL_TAIL = 5 };
 enum : uint32_t { DIR_AUTO = 0, DIR_PUSH = 1, DIR_PULL = 2 };
 
 // device-status bits, mapped to gg_status on the host

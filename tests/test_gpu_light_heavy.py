@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 NONE = 0xFFFFFFFF
 POL = {"graph": 0, "host": 2, "persistent": 3, "async": 1}
 LB = {"mp": 1, "bins": 2, "warp": 3}
-HEAVY = (3, 4)   # trace kinds of a heavy-edge superstep (push, pull)
+HEAVY = (3, 4, 5)   # trace kinds of a heavy-edge superstep (push, pull, pull that ends bucketing)
 
 
 def gg():
@@ -93,9 +93,9 @@ def test_push_and_pull_heavy_supersteps_agree():
             np.testing.assert_array_equal(got, ref, err_msg=f"sym={sym} delta={delta}")
             kinds_seen |= set(int(k) for k in kinds)
             if not sym:
-                assert 4 not in kinds
+                assert not {4, 5} & set(int(k) for k in kinds)
         g.close()
-    assert {3, 4} <= kinds_seen
+    assert 3 in kinds_seen and {4, 5} & kinds_seen
 
 
 def test_width_changes_rebuild_the_partition():
@@ -196,8 +196,8 @@ def _sink_graph(seed):
 @pytest.mark.parametrize("graph", ["rmat18", "sinks"])
 def test_plain_push_once_bucketing_ends(graph, lb):
     # once the unsettled vertices hold few heavy edges the threshold becomes
-    # infinite at a split, and every superstep after it is a plain push
-    # (kind 0) over all edges of each vertex
+    # infinite, and every superstep after that is a plain push (kind 0) over
+    # all edges of each vertex
     if graph == "rmat18":
         ro, col, w, src = graphgen.workload("rmat18")
         g = gg().Graph(ro, col, w, symmetric=True)
@@ -211,13 +211,43 @@ def test_plain_push_once_bucketing_ends(graph, lb):
         got, st, kinds = run(g, s, delta, lb, trace_cap=8192)
         np.testing.assert_array_equal(got, oracle.dijkstra(ro, col, w, s), err_msg=f"{graph} {lb} src={s}")
         assert st["device_status"] == 0
-        splits = np.flatnonzero(kinds == 2)
-        if splits.size and not np.isin(kinds[splits[-1] + 1:], HEAVY).any():
-            tail = kinds[splits[-1] + 1:]
+        # the threshold becomes infinite at a split, or at a heavy pull that
+        # writes the plain tail's frontier itself (kind 5, no split after it)
+        ends = np.flatnonzero((kinds == 2) | (kinds == 5))
+        if ends.size and not np.isin(kinds[ends[-1] + 1:], HEAVY).any():
+            tail = kinds[ends[-1] + 1:]
             assert (tail == 0).all(), kinds
             ended += tail.size > 0
     assert ended > 0   # the plain tail ran in at least one case
     g.close()
+
+
+def test_heavy_pull_that_ends_bucketing_writes_the_tail_frontier():
+    """From an RMAT hub the dense core settles in the first bucket; once its
+    heavy pull leaves fewer than m / 8 heavy edges unsettled, that pull ends
+    bucketing itself (kind 5): its next frontier is every unsettled vertex
+    with a finite distance, and only plain pushes follow (no split)."""
+    for name in ("rmat18", "rmat20"):
+        ro, col, w, src = graphgen.workload(name)
+        g = gg().Graph(ro, col, w, symmetric=True)
+        for policy in ("graph", "host"):
+            trace = torch.zeros(4 * 4096, dtype=torch.uint32, device="cuda")
+            m = gg()
+            st = m.gg_stats()
+            d = g.sssp(src, policy=POL[policy], direction=1, lb_mode=LB["warp"], stats=st, trace=trace,
+                       trace_cap=4096)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(d.cpu().numpy(), oracle.dijkstra(ro, col, w, src),
+                                          err_msg=f"{name} {policy}")
+            tr = trace.cpu().numpy().reshape(-1, 4)[: st.iterations]
+            kinds = tr[:, 2]
+            k5 = np.flatnonzero(kinds == 5)
+            assert k5.size == 1, kinds
+            rest = kinds[k5[0] + 1:]
+            assert rest.size > 0 and (rest == 0).all(), kinds
+            assert tr[k5[0], 3] > 0 and tr[k5[0] + 1, 0] == tr[k5[0], 3]
+            assert st.device_status == 0
+        g.close()
 
 
 def test_bad_light_heavy_value_is_rejected():

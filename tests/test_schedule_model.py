@@ -9,7 +9,10 @@ buckets:
   pull into the unsettled vertices;
 - a split raises the threshold past the smallest parked distance;
 - once the unsettled vertices hold fewer than m / 8 heavy edges, the threshold
-  becomes infinite, and the rest of the run is plain push over all edges.
+  becomes infinite, and the rest of the run is plain push over all edges;
+- when a heavy pull is what brings them below that share, the pull itself
+  ends bucketing: every unsettled vertex with a finite distance forms the
+  plain push's first frontier, and no split follows.
 
 This model takes the same decisions superstep by superstep (synchronous
 relaxation within a superstep, which reaches the same fixed point as the
@@ -26,12 +29,13 @@ import oracle
 
 BIG = np.int64(1) << 40
 INF32 = 0xFFFFFFFF
-LIGHT, SPLIT, HEAVY_PUSH, HEAVY_PULL = 0, 2, 3, 4
+LIGHT, SPLIT, HEAVY_PUSH, HEAVY_PULL, HEAVY_PULL_TAIL = 0, 2, 3, 4, 5
 
 
-def schedule(ro, col, w, src, delta, symmetric, drain_div=8, tail=True, lh=True):
+def schedule(ro, col, w, src, delta, symmetric, drain_div=8, tail=True, lh=True, pull_tail=True):
     """Distances (uint32, INF32 = unreached) and the kind of every superstep.
-    lh=False is the plain near-far loop (every edge light, no drain rule)."""
+    lh=False is the plain near-far loop (every edge light, no drain rule);
+    pull_tail=False keeps the split after a heavy pull that ends bucketing."""
     ro = np.asarray(ro, np.int64)
     n, m = ro.size - 1, len(col)
     deg = np.diff(ro)
@@ -90,7 +94,8 @@ def schedule(ro, col, w, src, delta, symmetric, drain_div=8, tail=True, lh=True)
             left = max(heavy_total - heavy_done - rE, 0)
             R_next = np.zeros(n, bool)
             if symmetric and t_cur < BIG and rE > left + n // 8:
-                kinds.append(HEAVY_PULL)
+                ends = pull_tail and tail and left * drain_div < m
+                kinds.append(HEAVY_PULL_TAIL if ends else HEAVY_PULL)
                 # every unsettled vertex takes the minimum over its heavy edges
                 # from settled vertices (symmetric: in-edges = out-edges)
                 un = np.flatnonzero(dist >= t_cur)
@@ -108,6 +113,15 @@ def schedule(ro, col, w, src, delta, symmetric, drain_div=8, tail=True, lh=True)
                     dist[imp] = best[imp]
                 far[imp] = True   # every improvement is >= t_cur
                 F = np.zeros(0, np.int64)
+                if ends:
+                    # the kernel takes every unsettled vertex with a finite
+                    # distance: the vertices the split would move from the pile
+                    fv = np.flatnonzero((dist >= t_cur) & (dist < BIG))
+                    assert np.array_equal(fv, np.flatnonzero(far & (dist >= t_cur)))
+                    far[:] = False
+                    t_prev, t_cur = t_cur, BIG
+                    bucketed = False
+                    F = fv[deg[fv] > 0]
             else:
                 kinds.append(HEAVY_PUSH)
                 F = near_far(push(Rv, lend, ro[1:]), R_next)
@@ -142,13 +156,13 @@ def schedule(ro, col, w, src, delta, symmetric, drain_div=8, tail=True, lh=True)
 
 
 def _after_drain(kinds):
-    """Kinds after the last split, when that split ended bucketing (nothing
-    heavy follows it), else None."""
-    s = np.flatnonzero(kinds == SPLIT)
+    """Kinds after the step that ended bucketing (the last split, or a heavy
+    pull that ended it), when nothing heavy follows it, else None."""
+    s = np.flatnonzero((kinds == SPLIT) | (kinds == HEAVY_PULL_TAIL))
     if not s.size:
         return None
     rest = kinds[s[-1] + 1:]
-    return None if np.isin(rest, (HEAVY_PUSH, HEAVY_PULL)).any() else rest
+    return None if np.isin(rest, (HEAVY_PUSH, HEAVY_PULL, HEAVY_PULL_TAIL)).any() else rest
 
 
 def _sink_graph(seed, n=3000, m=40000, W=90):
@@ -163,7 +177,7 @@ def test_rmat_schedule_matches_oracle(scale, delta):
     for s in (graphgen.max_degree_vertex(ro), int(graphgen.sample_sources(ro, 1, seed=7)[0])):
         got, kinds = schedule(ro, col, w, s, delta, symmetric=True)
         np.testing.assert_array_equal(got, oracle.dijkstra(ro, col, w, s), err_msg=f"src={s}")
-        assert np.isin(kinds, (HEAVY_PUSH, HEAVY_PULL)).any()
+        assert np.isin(kinds, (HEAVY_PUSH, HEAVY_PULL, HEAVY_PULL_TAIL)).any()
         rest = _after_drain(kinds)
         if rest is not None:
             assert (rest == LIGHT).all()
@@ -200,8 +214,27 @@ def test_plain_tail_removes_supersteps_not_distances():
     np.testing.assert_array_equal(got_t, got_b)
     np.testing.assert_array_equal(got_t, oracle.dijkstra(ro, col, w, hub))
     assert _after_drain(kinds_t) is not None   # bucketing ended in this run
-    assert HEAVY_PULL in kinds_t               # the first bucket's heavy superstep pulled
+    assert {HEAVY_PULL, HEAVY_PULL_TAIL} & set(kinds_t.tolist())   # the first bucket's heavy superstep pulled
     assert len(kinds_t) < len(kinds_b)
+
+
+@pytest.mark.parametrize("scale,seed,delta", [(12, 1, 20), (13, 3, 20), (14, 5, 12)])
+def test_pull_that_ends_bucketing_replaces_the_split(scale, seed, delta):
+    # the pull after which the drain rule holds writes the plain frontier
+    # itself: the same distances, one superstep (the split) fewer, and the
+    # first plain push works on the vertices the split would have moved
+    ro, col, w = graphgen.rmat(scale, 16, seed=seed, W=255)
+    hub = graphgen.max_degree_vertex(ro)
+    got_p, kinds_p = schedule(ro, col, w, hub, delta, symmetric=True)
+    got_s, kinds_s = schedule(ro, col, w, hub, delta, symmetric=True, pull_tail=False)
+    np.testing.assert_array_equal(got_p, oracle.dijkstra(ro, col, w, hub))
+    np.testing.assert_array_equal(got_s, got_p)
+    k = np.flatnonzero(kinds_p == HEAVY_PULL_TAIL)
+    assert k.size == 1
+    # without it: a pull, then the split that ends bucketing
+    assert kinds_s[k[0]] == HEAVY_PULL and kinds_s[k[0] + 1] == SPLIT
+    np.testing.assert_array_equal(kinds_p[k[0] + 1:], kinds_s[k[0] + 2:])
+    assert (kinds_p[k[0] + 1:] == LIGHT).all()
 
 
 @pytest.mark.parametrize("graph", ["grid", "path", "sinks", "rmat"])
@@ -223,5 +256,5 @@ def test_plain_near_far_schedule_matches_oracle(graph):
     for s, delta in cases:
         got, kinds = schedule(ro, col, w, s, delta, symmetric=sym, lh=False)
         np.testing.assert_array_equal(got, oracle.dijkstra(ro, col, w, s), err_msg=f"{graph} src={s} delta={delta}")
-        assert not np.isin(kinds, (HEAVY_PUSH, HEAVY_PULL)).any()
+        assert not np.isin(kinds, (HEAVY_PUSH, HEAVY_PULL, HEAVY_PULL_TAIL)).any()
     assert SPLIT in kinds   # the far pile was used
