@@ -77,6 +77,9 @@ def parse():
     p.add_argument("--no-grid", action="store_true", help="skip the 4096^2 grid policy comparison")
     p.add_argument("--batch-trace", default="",
                    help="write the batched run's per-superstep trace (kind, entries, edges, next size) to this file")
+    p.add_argument("--trace", default="",
+                   help="write the single-source stats run's per-superstep trace (frontier size, frontier edges, "
+                        "kind, next frontier size) to this file")
     p.add_argument("--ref-seconds", type=float, default=240.0,
                    help="--impl reference: stop adding steps once this much host time is spent")
     return p.parse_args()
@@ -599,12 +602,19 @@ def run_gg(args):
     # correctness of what is timed: a stats run whose distances must hash to
     # the stored oracle hash of this workload (no line is printed otherwise)
     st = gg.gg_stats()
+    trace = torch.zeros(4 * 65536, dtype=torch.uint32, device="cuda") if args.trace else None
     torch.cuda.nvtx.range_push("gg_sssp_stats_run")   # lets a profiler select exactly one SSSP's launches
     gg.gg_sssp_ex(g.handle, src, dist_t, gg.make_options(policy=policy, direction=direction, lb_mode=lb,
                                                          pull_alpha=args.alpha, pull_beta=args.beta, stats=st,
-                                                         delta=delta), stream)
+                                                         delta=delta,
+                                                         **({"trace": trace, "trace_cap": 65536} if args.trace
+                                                            else {})), stream)
     torch.cuda.nvtx.range_pop()
     g.check()
+    if args.trace:
+        np.savetxt(args.trace, trace.cpu().numpy().reshape(-1, 4)[:min(st.iterations, 65536)], fmt="%d",
+                   header="frontier size, frontier edges, kind (0 push, 1 pull, 2 split, 3 heavy push, "
+                          "4 heavy pull, 5 heavy pull that ends the buckets), next frontier size")
     d_host = dist_t.cpu().numpy()
     verified = verify_single(args.workload, d_host)
     reach = d_host != gg.GG_INF

@@ -76,6 +76,12 @@
 #ifndef GG_LH_TAIL
 #define GG_LH_TAIL 1   // light/heavy: plain push once bucketing has ended
 #endif
+#ifndef GG_WARP_MIN_EDGES
+#define GG_WARP_MIN_EDGES 32   // warp streaming: smallest edge share per warp (0: every warp takes a share)
+#endif
+#ifndef GG_CTA_FLUSH
+#define GG_CTA_FLUSH 1   // warp streaming: the near queues left at the end go out in one append per CTA
+#endif
 #ifndef GG_PULL_TAIL
 #define GG_PULL_TAIL 1   // a heavy pull after which bucketing ends writes the plain tail's frontier
 #endif
@@ -123,7 +129,8 @@ struct MPSmem {
   uint32_t ovf;
   unsigned long long base;
   uint32_t fbase;
-  uint32_t ledges;     // edges relaxed in warp-local rounds (statistics)
+  uint32_t ledges;     // edges relaxed in warp-local rounds or scanned by a heavy pull (statistics)
+  uint32_t wq[BLOCK / 32][4];   // warp streaming, end flush: per warp (entries, edges) of both lists, then bases
   uint16_t own[TILE];  // push: entry that owns each edge slot of the tile
 };
 
@@ -632,9 +639,19 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
   uint32_t fmin = kInf;
   bool ovf = false;
   const uint32_t wbits = a.g.wbits;
-  const unsigned long long W = (unsigned long long)gridDim.x * NW;
-  const unsigned long long gw = (unsigned long long)blockIdx.x * NW + warp;
-  const uint32_t w0 = (uint32_t)((Etot * gw) / W), w1 = (uint32_t)((Etot * (gw + 1)) / W);
+  // equal edge shares of at least GG_WARP_MIN_EDGES: a small superstep runs
+  // on fewer warps (spread one per CTA first), so fewer of them pay the
+  // per-warp fixed work and the appends' counter atomics
+  const unsigned long long Wall = (unsigned long long)gridDim.x * NW;
+  // (not with local rounds, whose work grows with the warps that stream)
+  constexpr uint32_t kMinShare = LOCAL ? 0u : (uint32_t)GG_WARP_MIN_EDGES;
+  const unsigned long long Wneed = kMinShare > 0 ? ((unsigned long long)Etot + kMinShare - 1) / kMinShare : Wall;
+  const bool reduced = Wneed < Wall;
+  const unsigned long long W = reduced ? (Wneed > 0 ? Wneed : 1ull) : Wall;
+  const unsigned long long gw = reduced ? (unsigned long long)warp * gridDim.x + blockIdx.x
+                                        : (unsigned long long)blockIdx.x * NW + warp;
+  const bool wact = gw < W;
+  const uint32_t w0 = wact ? (uint32_t)((Etot * gw) / W) : 0u, w1 = wact ? (uint32_t)((Etot * (gw + 1)) / W) : 0u;
 
   auto flush_near = [&]() {
     __syncwarp();
@@ -726,6 +743,132 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
       fo.nfv[pos0 + i] = qv[i];
       fo.nfr[pos0 + i] = qr[i];
       fo.nfs[pos0 + i] = eb0 + qd[i];
+    }
+    qn = 0;
+    __syncwarp();
+  };
+  // End flush for the whole CTA (deferred dedup only; CTA-uniform): every warp
+  // test-and-sets its queued vertices and reads their rows, then one 64-bit
+  // counter atomic per list and CTA places the winners of all warps (per-warp
+  // flushes would make each of the grid's warps hit the same counters).
+  const bool cta_end = GG_CTA_FLUSH && !LOCAL && GG_DEFER_DEDUP && !fo.sinks;
+  auto cta_flush = [&]() {
+    static_assert(QW == 128, "four queue entries per lane");
+    uint32_t* const qe = sm.eb + warp * QW;   // row end (the entry arrays are unused here)
+    uint32_t* const qf = sm.ec + warp * QW;   // 1: light (or plain) list, 2: R list
+    const bool lhm = fo.lh != 0u;
+    const uint32_t rj = fo.lh - 1u;
+    __syncwarp();
+    uint32_t vq[4];
+    bool kp[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {   // the queue's test-and-sets in flight together
+      const uint32_t i = 32u * c + lane;
+      vq[c] = i < qn ? qv[i] : 0u;
+      kp[c] = false;
+      if (i < qn) {
+        const uint32_t bit = 1u << (vq[c] & 31);
+        kp[c] = !(atomicOr(fo.bm_next + (vq[c] >> 5), bit) & bit);
+      }
+    }
+    uint32_t rs[4], le[4], re[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {   // then the rows of the winners
+      rs[c] = le[c] = re[c] = 0u;
+      if (kp[c]) {
+        rs[c] = __ldg(fo.ro + vq[c]);
+        re[c] = __ldg(fo.ro + vq[c] + 1);
+        le[c] = lhm ? __ldg(a.lb.lend + vq[c]) : re[c];
+      }
+    }
+    uint32_t nl = 0, el = 0, nh = 0, eh = 0;   // warp totals
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint32_t i = 32u * c + lane;
+      uint32_t fl = 0;
+      if (kp[c]) {
+        if (le[c] > rs[c]) fl |= 1u;
+        if (lhm && re[c] > le[c]) {
+          const uint32_t bit = 1u << (vq[c] & 31);
+          if (!(atomicOr(pick2(a.lb.bm_r, rj) + (vq[c] >> 5), bit) & bit)) fl |= 2u;
+        }
+        qr[i] = rs[c];
+        qd[i] = le[c];
+        qe[i] = re[c];
+      }
+      if (i < qn) qf[i] = fl;
+      nl += __popc(__ballot_sync(FULL, fl & 1u));
+      nh += __popc(__ballot_sync(FULL, (fl & 2u) != 0u));
+      el += __reduce_add_sync(FULL, (fl & 1u) ? le[c] - rs[c] : 0u);
+      eh += __reduce_add_sync(FULL, (fl & 2u) ? re[c] - le[c] : 0u);
+    }
+    if (lane == 0) {
+      sm.wq[warp][0] = nl;
+      sm.wq[warp][1] = el;
+      sm.wq[warp][2] = nh;
+      sm.wq[warp][3] = eh;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {   // thread t: list t (the frontier; the R list)
+      const uint32_t t = threadIdx.x;
+      uint32_t cn = 0, ce = 0;
+      for (uint32_t w = 0; w < NW; ++w) {
+        cn += sm.wq[w][2 * t];
+        ce += sm.wq[w][2 * t + 1];
+      }
+      unsigned long long b = 0;
+      if (cn) b = atomicAdd(t == 0 ? fo.cnt_next : &a.ctl->rcnt[rj], ((unsigned long long)cn << 32) | ce);
+      uint32_t pn = (uint32_t)(b >> 32), pe = (uint32_t)b;
+      for (uint32_t w = 0; w < NW; ++w) {   // exclusive prefix over the warps, in place
+        const uint32_t n_w = sm.wq[w][2 * t], e_w = sm.wq[w][2 * t + 1];
+        sm.wq[w][2 * t] = pn;
+        sm.wq[w][2 * t + 1] = pe;
+        pn += n_w;
+        pe += e_w;
+      }
+    }
+    __syncthreads();
+    uint32_t pl = sm.wq[warp][0], ol = sm.wq[warp][1], ph = sm.wq[warp][2], oh = sm.wq[warp][3];
+    for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      const uint32_t fl = i < qn ? qf[i] : 0u;
+      uint32_t v = 0, r0 = 0, r1 = 0, r2 = 0;
+      if (fl) {
+        v = qv[i];
+        r0 = qr[i];
+        r1 = qd[i];
+        r2 = qe[i];
+      }
+#pragma unroll
+      for (int list = 0; list < 2; ++list) {
+        const bool mine = (fl & (list == 0 ? 1u : 2u)) != 0u;
+        const unsigned mb = __ballot_sync(FULL, mine);
+        if (mb == 0u) continue;   // warp-uniform
+        const uint32_t d = mine ? (list == 0 ? r1 - r0 : r2 - r1) : 0u;
+        uint32_t x = d;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(FULL, x, o);
+          if (lane >= (uint32_t)o) x += y;
+        }
+        uint32_t& pp = list == 0 ? pl : ph;
+        uint32_t& oo = list == 0 ? ol : oh;
+        if (mine) {
+          const uint32_t pos = pp + __popc(mb & lt);
+          const uint32_t coord = oo + x - d;
+          if (list == 0) {
+            fo.nfv[pos] = v;
+            fo.nfr[pos] = r0;
+            fo.nfs[pos] = coord;
+          } else {
+            pick2(a.lb.rv, rj)[pos] = v;
+            pick2(a.lb.rr, rj)[pos] = r1;
+            pick2(a.lb.rs, rj)[pos] = coord;
+          }
+        }
+        pp += __popc(mb);
+        oo += __shfl_sync(FULL, x, 31);
+      }
     }
     qn = 0;
     __syncwarp();
@@ -850,9 +993,10 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
       }
       b += 32u * nc;
     }
-    if (qn) flush_near();
+    if (qn && !cta_end) flush_near();
     if (fn) flush_far();
   }
+  if (cta_end) cta_flush();
   if (LOCAL) {
     uint32_t ledges = 0;   // warp-uniform
     for (int r = 0; r < GG_LOCAL_ROUNDS && lqn > 0; ++r) {   // warp-uniform
@@ -1224,7 +1368,8 @@ __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArg
   for (int o = 16; o; o >>= 1) fmin = min(fmin, __shfl_xor_sync(FULL, fmin, o));
   if (lane == 0) {
     if (fmin != kInf) atomicMin(&sm.fmin, fmin);
-    if (scanned) atomicAdd(&a.ctl->edges_scanned, scanned);
+    // per CTA (the finalize adds it once): one global atomic per CTA, not per warp
+    if (scanned) atomicAdd(&sm.ledges, (uint32_t)scanned);
   }
   if (__any_sync(FULL, ovf) && lane == 0) sm.ovf = 1u;
 }
@@ -1268,7 +1413,7 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
   if (threadIdx.x == 0) {
     if (sm.ovf) atomicOr(&ctl->status, DS_OVERFLOW);
     if (sm.fmin != kInf) atomicMin(&ctl->far_min, sm.fmin);
-    if (sm.ledges) atomicAdd(&ctl->edges_scanned, (unsigned long long)sm.ledges);   // warp-local rounds
+    if (sm.ledges) atomicAdd(&ctl->edges_scanned, (unsigned long long)sm.ledges);   // local rounds, heavy pull
     sm.last = arrive_last(&ctl->done_ctas, gridDim.x) ? 1u : 0u;
   }
   __syncthreads();
