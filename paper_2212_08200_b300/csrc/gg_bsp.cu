@@ -130,7 +130,8 @@ struct MPSmem {
   unsigned long long base;
   uint32_t fbase;
   uint32_t ledges;     // edges relaxed in warp-local rounds or scanned by a heavy pull (statistics)
-  uint32_t wq[BLOCK / 32][4];   // warp streaming, end flush: per warp (entries, edges) of both lists, then bases
+  uint32_t wq[BLOCK / 32][5];   // warp streaming, end flush: per warp (entries, edges) of both lists and the
+                                //   far-queue length, then the bases
   uint16_t own[TILE];  // push: entry that owns each edge slot of the tile
 };
 
@@ -749,8 +750,9 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
   };
   // End flush for the whole CTA (deferred dedup only; CTA-uniform): every warp
   // test-and-sets its queued vertices and reads their rows, then one 64-bit
-  // counter atomic per list and CTA places the winners of all warps (per-warp
-  // flushes would make each of the grid's warps hit the same counters).
+  // counter atomic per list and CTA places the winners of all warps, and one
+  // more the far queues (per-warp flushes would make each of the grid's warps
+  // hit the same counters).
   const bool cta_end = GG_CTA_FLUSH && !LOCAL && GG_DEFER_DEDUP && !fo.sinks;
   auto cta_flush = [&]() {
     static_assert(QW == 128, "four queue entries per lane");
@@ -807,8 +809,23 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
       sm.wq[warp][1] = el;
       sm.wq[warp][2] = nh;
       sm.wq[warp][3] = eh;
+      sm.wq[warp][4] = fn;
     }
     __syncthreads();
+    if (threadIdx.x == 32) {   // the far pile (another warp than the lists' threads)
+      uint32_t tot = 0;
+      for (uint32_t w = 0; w < NW; ++w) tot += sm.wq[w][4];
+      uint32_t b = 0;
+      if (tot) {
+        b = atomicAdd(fo.far_cnt, tot);
+        if (fo.far_add) atomicAdd(fo.far_add, tot);
+      }
+      for (uint32_t w = 0; w < NW; ++w) {
+        const uint32_t c = sm.wq[w][4];
+        sm.wq[w][4] = b;
+        b += c;
+      }
+    }
     if (threadIdx.x < 2) {   // thread t: list t (the frontier; the R list)
       const uint32_t t = threadIdx.x;
       uint32_t cn = 0, ce = 0;
@@ -829,6 +846,9 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
     }
     __syncthreads();
     uint32_t pl = sm.wq[warp][0], ol = sm.wq[warp][1], ph = sm.wq[warp][2], oh = sm.wq[warp][3];
+    const uint32_t fb = sm.wq[warp][4];
+    for (uint32_t i = lane; i < fn; i += 32) fo.far[fb + i] = fq[i];
+    fn = 0;
     for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
       const uint32_t i = i0 + lane;
       const uint32_t fl = i < qn ? qf[i] : 0u;
@@ -994,7 +1014,7 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
       b += 32u * nc;
     }
     if (qn && !cta_end) flush_near();
-    if (fn) flush_far();
+    if (fn && !cta_end) flush_far();
   }
   if (cta_end) cta_flush();
   if (LOCAL) {
