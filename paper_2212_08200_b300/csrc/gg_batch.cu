@@ -133,6 +133,9 @@ struct BSmem {
   uint32_t tabs[64], tprev[64], shs[64];
   uint32_t qn, j, last, ovf;
   unsigned long long base;
+  // per-CTA sums of what every warp reports (one global atomic per CTA at the end)
+  unsigned long long hacc, pedges;   // heavy edges of newly settled pairs; edges a pull scanned
+  uint32_t fmin;                     // smallest shifted distance parked
 };
 
 // Eight consecutive distances row[0..7] into d[], read only where bit q of
@@ -250,6 +253,9 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
   if (tid == 0) {
     sm.qn = 0;
     sm.ovf = 0;
+    sm.hacc = 0ull;
+    sm.pedges = 0ull;
+    sm.fmin = kInf;
   }
   __syncthreads();
   bool ovf = false;
@@ -351,8 +357,8 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
     if (fqn) ffl();
 #pragma unroll
     for (int o = 16; o; o >>= 1) wfm = min(wfm, __shfl_xor_sync(FULL, wfm, o));
-    if (lane == 0 && wfm != kInf) atomicMin(&ctl->far_min, wfm);
-    if (lane == 0 && scanned) atomicAdd(&ctl->pull_edges, scanned);
+    if (lane == 0 && wfm != kInf) atomicMin(&sm.fmin, wfm);
+    if (lane == 0 && scanned) atomicAdd(&sm.pedges, scanned);
   } else if (bmode == 3) {
     // before the tail's split: clear the three frontier mask arrays.  A vertex
     // without light edges may hold mask bits that no frontier list carries
@@ -459,8 +465,8 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
     if (kqn) kflush();
 #pragma unroll
     for (int o = 16; o; o >>= 1) wfm = min(wfm, __shfl_xor_sync(FULL, wfm, o));
-    if (lane == 0 && wfm != kInf) atomicMin(&ctl->far_min, wfm);
-    if (lane == 0 && hacc) atomicAdd(&ctl->heavy_settled, hacc);
+    if (lane == 0 && wfm != kInf) atomicMin(&sm.fmin, wfm);
+    if (lane == 0 && hacc) atomicAdd(&sm.hacc, hacc);
   } else if (F > 0) {
     // Warp streaming, no block barriers: every warp of the grid takes an
     // equal contiguous share of the frontier's edge coordinates and walks it
@@ -771,17 +777,20 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
       if (qn) flush();
       if (LH && rqn) rflush();
     }
-    if (lane == 0 && hacc) atomicAdd(&ctl->heavy_settled, hacc);
+    if (lane == 0 && hacc) atomicAdd(&sm.hacc, hacc);
     if (buckets) {
 #pragma unroll
       for (int o = 16; o; o >>= 1) wfm = min(wfm, __shfl_xor_sync(FULL, wfm, o));
-      if (lane == 0 && wfm != kInf) atomicMin(&ctl->far_min, wfm);
+      if (lane == 0 && wfm != kInf) atomicMin(&sm.fmin, wfm);
     }
   }
   if (ovf) sm.ovf = 1u;
   __syncthreads();
   if (tid == 0) {
     if (sm.ovf) atomicOr(&ctl->status, DS_OVERFLOW);
+    if (sm.fmin != kInf) atomicMin(&ctl->far_min, sm.fmin);
+    if (sm.hacc) atomicAdd(&ctl->heavy_settled, sm.hacc);
+    if (sm.pedges) atomicAdd(&ctl->pull_edges, sm.pedges);
     sm.last = arrive_last(&ctl->done_ctas, gridDim.x) ? 1u : 0u;
   }
   __syncthreads();

@@ -82,6 +82,9 @@
 #ifndef GG_CTA_FLUSH
 #define GG_CTA_FLUSH 1   // warp streaming: the near queues left at the end go out in one append per CTA
 #endif
+#ifndef GG_PULL_SEGMIN
+#define GG_PULL_SEGMIN 1   // heavy pull: per-owner minimum by a segmented shuffle scan (0: match + reduce)
+#endif
 #ifndef GG_PULL_TAIL
 #define GG_PULL_TAIL 1   // a heavy pull after which bucketing ends writes the plain tail's frontier
 #endif
@@ -1329,9 +1332,24 @@ __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArg
 #pragma unroll
       for (int u = 0; u < PU; ++u) {
         if (u == 0 || c + 32u * u < T) {   // warp-uniform
-          const unsigned same = __match_any_sync(FULL, k[u]);
-          const uint32_t r = __reduce_min_sync(same, cand[u]);
-          if (r != kInf && lane == (uint32_t)(__ffs(same) - 1)) atomicMin(&wbest[k[u]], r);
+          if (GG_PULL_SEGMIN) {
+            // owners are non-decreasing over the lanes: a segmented minimum by
+            // shuffles leaves each owner's minimum in its first lane
+            uint32_t r = cand[u];
+            const uint32_t kk = k[u];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const uint32_t rd = __shfl_down_sync(FULL, r, o);
+              const uint32_t kd = __shfl_down_sync(FULL, kk, o);
+              if (lane + (uint32_t)o < 32u && kd == kk) r = min(r, rd);
+            }
+            const uint32_t kp = __shfl_up_sync(FULL, kk, 1);
+            if (r != kInf && (lane == 0 || kp != kk)) atomicMin(&wbest[kk], r);
+          } else {
+            const unsigned same = __match_any_sync(FULL, k[u]);
+            const uint32_t r = __reduce_min_sync(same, cand[u]);
+            if (r != kInf && lane == (uint32_t)(__ffs(same) - 1)) atomicMin(&wbest[k[u]], r);
+          }
         }
       }
     }
