@@ -657,6 +657,108 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
   const bool wact = gw < W;
   const uint32_t w0 = wact ? (uint32_t)((Etot * gw) / W) : 0u, w1 = wact ? (uint32_t)((Etot * (gw + 1)) / W) : 0u;
 
+  // Near-queue appends with deferred dedup (sink-free graphs): collect
+  // test-and-sets the next-frontier bitmap (and, with buckets, the epoch's R
+  // bitmap) for the whole queue and reads the rows, all in flight together
+  // (none waits on another: a vertex without heavy edges may set its R bit,
+  // which only ever keeps it out of an R list it has nothing to bring to),
+  // marks each entry's lists and returns the warp's entries and edges per
+  // list; emit writes the marked entries from the given list positions and
+  // edge bases.
+  uint32_t* const qe = sm.eb + warp * QW;   // row end (the entry arrays are unused without local rounds)
+  uint32_t* const qf = sm.ec + warp * QW;   // 1: the frontier (light or plain edges), 2: the R list
+  auto near_collect = [&](uint32_t& nl, uint32_t& el, uint32_t& nh, uint32_t& eh) {
+    static_assert(QW == 128, "four queue entries per lane");
+    const bool lhm = fo.lh != 0u;
+    const uint32_t rj = fo.lh - 1u;
+    __syncwarp();
+    uint32_t vq[4], rs[4], le[4], re[4];
+    bool kp[4], hv[4];
+    // the next-frontier and R test-and-sets and the row reads of the whole
+    // queue, all in flight together (none waits on another: a vertex without
+    // heavy edges may set its R bit, which only ever keeps it out of an R list
+    // it has nothing to bring to)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint32_t i = 32u * c + lane;
+      vq[c] = i < qn ? qv[i] : 0u;
+      kp[c] = hv[c] = false;
+      rs[c] = le[c] = re[c] = 0u;
+      if (i < qn) {
+        const uint32_t bit = 1u << (vq[c] & 31);
+        kp[c] = !(atomicOr(fo.bm_next + (vq[c] >> 5), bit) & bit);
+        if (lhm) hv[c] = !(atomicOr(pick2(a.lb.bm_r, rj) + (vq[c] >> 5), bit) & bit);
+        rs[c] = __ldg(fo.ro + vq[c]);
+        re[c] = __ldg(fo.ro + vq[c] + 1);
+        le[c] = lhm ? __ldg(a.lb.lend + vq[c]) : re[c];
+      }
+    }
+    nl = el = nh = eh = 0;   // warp totals
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint32_t i = 32u * c + lane;
+      uint32_t fl = 0;
+      if (kp[c] && le[c] > rs[c]) fl |= 1u;
+      if (hv[c] && re[c] > le[c]) fl |= 2u;
+      if (fl) {
+        qr[i] = rs[c];
+        qd[i] = le[c];
+        qe[i] = re[c];
+      }
+      if (i < qn) qf[i] = fl;
+      nl += __popc(__ballot_sync(FULL, fl & 1u));
+      nh += __popc(__ballot_sync(FULL, (fl & 2u) != 0u));
+      el += __reduce_add_sync(FULL, (fl & 1u) ? le[c] - rs[c] : 0u);
+      eh += __reduce_add_sync(FULL, (fl & 2u) ? re[c] - le[c] : 0u);
+    }
+  };
+  auto near_emit = [&](uint32_t pl, uint32_t ol, uint32_t ph, uint32_t oh) {
+    const uint32_t rj = fo.lh - 1u;
+    __syncwarp();
+    for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
+      const uint32_t i = i0 + lane;
+      const uint32_t fl = i < qn ? qf[i] : 0u;
+      uint32_t v = 0, r0 = 0, r1 = 0, r2 = 0;
+      if (fl) {
+        v = qv[i];
+        r0 = qr[i];
+        r1 = qd[i];
+        r2 = qe[i];
+      }
+#pragma unroll
+      for (int list = 0; list < 2; ++list) {
+        const bool mine = (fl & (list == 0 ? 1u : 2u)) != 0u;
+        const unsigned mb = __ballot_sync(FULL, mine);
+        if (mb == 0u) continue;   // warp-uniform
+        const uint32_t d = mine ? (list == 0 ? r1 - r0 : r2 - r1) : 0u;
+        uint32_t x = d;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(FULL, x, o);
+          if (lane >= (uint32_t)o) x += y;
+        }
+        uint32_t& pp = list == 0 ? pl : ph;
+        uint32_t& oo = list == 0 ? ol : oh;
+        if (mine) {
+          const uint32_t pos = pp + __popc(mb & lt);
+          const uint32_t coord = oo + x - d;
+          if (list == 0) {
+            fo.nfv[pos] = v;
+            fo.nfr[pos] = r0;
+            fo.nfs[pos] = coord;
+          } else {
+            pick2(a.lb.rv, rj)[pos] = v;
+            pick2(a.lb.rr, rj)[pos] = r1;
+            pick2(a.lb.rs, rj)[pos] = coord;
+          }
+        }
+        pp += __popc(mb);
+        oo += __shfl_sync(FULL, x, 31);
+      }
+    }
+    qn = 0;
+    __syncwarp();
+  };
   auto flush_near = [&]() {
     __syncwarp();
     if (LOCAL) {
@@ -680,30 +782,18 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
     }
     if (GG_DEFER_DEDUP && !fo.sinks) {
       // deferred dedup: the queue holds every improved near vertex (repeats
-      // included); test-and-set them all here, the atomics of the whole queue
-      // in flight together, then append the winners
-      static_assert(QW <= 128, "four queue entries per lane");
-      uint32_t vq[4];
-      bool kp[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const uint32_t i = 32u * c + lane;
-        vq[c] = i < qn ? qv[i] : 0u;
-        kp[c] = false;
-        if (i < qn) {
-          const uint32_t bit = 1u << (vq[c] & 31);
-          kp[c] = !(atomicOr(fo.bm_next + (vq[c] >> 5), bit) & bit);
-        }
+      // included); collect test-and-sets them all, then one counter atomic
+      // per list places the warp's winners
+      uint32_t nl, el, nh, eh;
+      near_collect(nl, el, nh, eh);
+      unsigned long long b0 = 0, b1 = 0;
+      if (lane == 0) {
+        if (nl) b0 = atomicAdd(fo.cnt_next, ((unsigned long long)nl << 32) | el);
+        if (nh) b1 = atomicAdd(&a.ctl->rcnt[fo.lh - 1u], ((unsigned long long)nh << 32) | eh);
       }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (32u * c < qn) {   // warp-uniform
-          if (fo.lh) append32<true>(a, fo, kp[c], vq[c]);
-          else append32<false>(a, fo, kp[c], vq[c]);
-        }
-      }
-      qn = 0;
-      __syncwarp();
+      b0 = __shfl_sync(FULL, b0, 0);
+      b1 = __shfl_sync(FULL, b1, 0);
+      near_emit((uint32_t)(b0 >> 32), (uint32_t)b0, (uint32_t)(b1 >> 32), (uint32_t)b1);
       return;
     }
     if (fo.lh) {
@@ -758,55 +848,9 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
   // hit the same counters).
   const bool cta_end = GG_CTA_FLUSH && !LOCAL && GG_DEFER_DEDUP && !fo.sinks;
   auto cta_flush = [&]() {
-    static_assert(QW == 128, "four queue entries per lane");
-    uint32_t* const qe = sm.eb + warp * QW;   // row end (the entry arrays are unused here)
-    uint32_t* const qf = sm.ec + warp * QW;   // 1: light (or plain) list, 2: R list
-    const bool lhm = fo.lh != 0u;
+    uint32_t nl, el, nh, eh;
+    near_collect(nl, el, nh, eh);
     const uint32_t rj = fo.lh - 1u;
-    __syncwarp();
-    uint32_t vq[4];
-    bool kp[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {   // the queue's test-and-sets in flight together
-      const uint32_t i = 32u * c + lane;
-      vq[c] = i < qn ? qv[i] : 0u;
-      kp[c] = false;
-      if (i < qn) {
-        const uint32_t bit = 1u << (vq[c] & 31);
-        kp[c] = !(atomicOr(fo.bm_next + (vq[c] >> 5), bit) & bit);
-      }
-    }
-    uint32_t rs[4], le[4], re[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {   // then the rows of the winners
-      rs[c] = le[c] = re[c] = 0u;
-      if (kp[c]) {
-        rs[c] = __ldg(fo.ro + vq[c]);
-        re[c] = __ldg(fo.ro + vq[c] + 1);
-        le[c] = lhm ? __ldg(a.lb.lend + vq[c]) : re[c];
-      }
-    }
-    uint32_t nl = 0, el = 0, nh = 0, eh = 0;   // warp totals
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const uint32_t i = 32u * c + lane;
-      uint32_t fl = 0;
-      if (kp[c]) {
-        if (le[c] > rs[c]) fl |= 1u;
-        if (lhm && re[c] > le[c]) {
-          const uint32_t bit = 1u << (vq[c] & 31);
-          if (!(atomicOr(pick2(a.lb.bm_r, rj) + (vq[c] >> 5), bit) & bit)) fl |= 2u;
-        }
-        qr[i] = rs[c];
-        qd[i] = le[c];
-        qe[i] = re[c];
-      }
-      if (i < qn) qf[i] = fl;
-      nl += __popc(__ballot_sync(FULL, fl & 1u));
-      nh += __popc(__ballot_sync(FULL, (fl & 2u) != 0u));
-      el += __reduce_add_sync(FULL, (fl & 1u) ? le[c] - rs[c] : 0u);
-      eh += __reduce_add_sync(FULL, (fl & 2u) ? re[c] - le[c] : 0u);
-    }
     if (lane == 0) {
       sm.wq[warp][0] = nl;
       sm.wq[warp][1] = el;
@@ -848,53 +892,10 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
       }
     }
     __syncthreads();
-    uint32_t pl = sm.wq[warp][0], ol = sm.wq[warp][1], ph = sm.wq[warp][2], oh = sm.wq[warp][3];
+    near_emit(sm.wq[warp][0], sm.wq[warp][1], sm.wq[warp][2], sm.wq[warp][3]);
     const uint32_t fb = sm.wq[warp][4];
     for (uint32_t i = lane; i < fn; i += 32) fo.far[fb + i] = fq[i];
     fn = 0;
-    for (uint32_t i0 = 0; i0 < qn; i0 += 32) {
-      const uint32_t i = i0 + lane;
-      const uint32_t fl = i < qn ? qf[i] : 0u;
-      uint32_t v = 0, r0 = 0, r1 = 0, r2 = 0;
-      if (fl) {
-        v = qv[i];
-        r0 = qr[i];
-        r1 = qd[i];
-        r2 = qe[i];
-      }
-#pragma unroll
-      for (int list = 0; list < 2; ++list) {
-        const bool mine = (fl & (list == 0 ? 1u : 2u)) != 0u;
-        const unsigned mb = __ballot_sync(FULL, mine);
-        if (mb == 0u) continue;   // warp-uniform
-        const uint32_t d = mine ? (list == 0 ? r1 - r0 : r2 - r1) : 0u;
-        uint32_t x = d;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint32_t y = __shfl_up_sync(FULL, x, o);
-          if (lane >= (uint32_t)o) x += y;
-        }
-        uint32_t& pp = list == 0 ? pl : ph;
-        uint32_t& oo = list == 0 ? ol : oh;
-        if (mine) {
-          const uint32_t pos = pp + __popc(mb & lt);
-          const uint32_t coord = oo + x - d;
-          if (list == 0) {
-            fo.nfv[pos] = v;
-            fo.nfr[pos] = r0;
-            fo.nfs[pos] = coord;
-          } else {
-            pick2(a.lb.rv, rj)[pos] = v;
-            pick2(a.lb.rr, rj)[pos] = r1;
-            pick2(a.lb.rs, rj)[pos] = coord;
-          }
-        }
-        pp += __popc(mb);
-        oo += __shfl_sync(FULL, x, 31);
-      }
-    }
-    qn = 0;
-    __syncwarp();
   };
   auto flush_far = [&]() {
     __syncwarp();
