@@ -85,6 +85,9 @@
 #ifndef GG_PULL_SEGMIN
 #define GG_PULL_SEGMIN 1   // heavy pull: per-owner minimum by a segmented shuffle scan (0: match + reduce)
 #endif
+#ifndef GG_WARP_BALLOT_OWNER
+#define GG_WARP_BALLOT_OWNER 1   // warp streaming: each edge's window entry from one ballot and one OR-reduction
+#endif                           // (0: a 5-step shuffle search)
 #ifndef GG_PULL_TAIL
 #define GG_PULL_TAIL 1   // a heavy pull after which bucketing ends writes the plain tail's frontier
 #endif
@@ -101,6 +104,12 @@
 namespace gg {
 
 namespace {
+
+__device__ __forceinline__ uint32_t lanemask_le() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+  return m;
+}
 
 // push load-balancing schemes (template argument of the superstep kernels)
 constexpr int LB_TILE = 0;   // merge-path tiles of BLOCK*EPT edges per CTA
@@ -949,10 +958,23 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
         const uint32_t g = b + 32u * u + lane;
         act[u] = u < nc && g < w1;
         uint32_t k = 0;
+        if (GG_WARP_BALLOT_OWNER) {
+          // the chunk's first edge belongs to the last window entry starting at
+          // or before it; each entry that starts later inside the chunk moves the
+          // owner of the edges from its offset on by one (first coordinates
+          // increase strictly: every entry has edges)
+          const uint32_t cb = b + 32u * u;
+          const unsigned le0 = __ballot_sync(FULL, ws <= cb);
+          const uint32_t k0 = le0 ? 31u - (uint32_t)__clz(le0) : 0u;
+          const uint32_t off = ws - cb;   // entries before the chunk wrap to large values
+          const uint32_t starts = __reduce_or_sync(FULL, off - 1u < 31u ? 1u << off : 0u);
+          k = k0 + (uint32_t)__popc(starts & lanemask_le());
+        } else {
 #pragma unroll
-        for (int step = 16; step; step >>= 1) {
-          const uint32_t sv = __shfl_sync(FULL, ws, k + step);
-          if (sv <= g) k += step;
+          for (int step = 16; step; step >>= 1) {
+            const uint32_t sv = __shfl_sync(FULL, ws, k + step);
+            if (sv <= g) k += step;
+          }
         }
         const uint32_t ks = __shfl_sync(FULL, ws, k);
         const uint32_t kr = __shfl_sync(FULL, wr, k);
@@ -1280,16 +1302,23 @@ __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArg
   // 40 % of an RMAT graph, have nothing to pull)
   const uint32_t np = a.g.np;
   const uint32_t* __restrict__ pv = a.g.pv;
-  for (uint32_t base = (blockIdx.x * (BLOCK / 32) + warp) * 32u; base < np; base += W * 32u) {
+  // the next group's vertex and distance are read while this one is worked on
+  uint32_t base = (blockIdx.x * (BLOCK / 32) + warp) * 32u;
+  uint32_t nv = base + lane < np ? __ldg(pv + base + lane) : 0u;
+  uint32_t ndv = base + lane < np ? ld_cg(dist + nv) : 0u;
+  for (; base < np; base += W * 32u) {
     const bool have = base + lane < np;
-    const uint32_t v = have ? __ldg(pv + base + lane) : 0u;
-    uint32_t dv = 0, hs = 0, deg = 0;
-    if (have) {
-      dv = ld_cg(dist + v);
-      if (dv >= t_cur) {
-        hs = __ldg(lend + v);
-        deg = __ldg(fo.ro + v + 1) - hs;
-      }
+    const uint32_t v = nv;
+    uint32_t dv = ndv, hs = 0, deg = 0, rsv = 0;
+    if (have && dv >= t_cur) {
+      hs = __ldg(lend + v);
+      deg = __ldg(fo.ro + v + 1) - hs;
+      if (TAIL) rsv = __ldg(fo.ro + v);   // the row start a join needs
+    }
+    {
+      const uint32_t nb = base + W * 32u + lane;
+      nv = nb < np ? __ldg(pv + nb) : 0u;
+      if (nb < np) ndv = ld_cg(dist + nv);
     }
     uint32_t x = deg;
 #pragma unroll
@@ -1362,7 +1391,7 @@ __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArg
       if (have && dv >= t_cur) {
         if (best < dv) dist[v] = best;
         if (min(best, dv) != kInf) {
-          rs = __ldg(fo.ro + v);
+          rs = rsv;
           full = hs + deg - rs;   // the whole row: [ro[v], ro[v+1])
           join = full > 0;
         }
