@@ -88,6 +88,9 @@
 #ifndef GG_WARP_BALLOT_OWNER
 #define GG_WARP_BALLOT_OWNER 1   // warp streaming: each edge's window entry from one ballot and one OR-reduction
 #endif                           // (0: a 5-step shuffle search)
+#ifndef GG_EARLY_TAIL_DIV
+#define GG_EARLY_TAIL_DIV 256   // a light frontier of at most n / this many vertices may end the buckets early (0: never)
+#endif
 #ifndef GG_PULL_TAIL
 #define GG_PULL_TAIL 1   // a heavy pull after which bucketing ends writes the plain tail's frontier
 #endif
@@ -1245,7 +1248,8 @@ __device__ __forceinline__ void far_split(MPSmem<BLOCK, EPT>& sm, const StepArgs
 // per-warp queue) and the split step is skipped.
 template <int BLOCK, int EPT, bool PK, bool TAIL>
 __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArgs& a, const FilterOut& fo,
-                                           uint32_t* __restrict__ dist, uint32_t* __restrict__ bm_r_old) {
+                                           uint32_t* __restrict__ dist, uint32_t* __restrict__ bm_r_old,
+                                           const uint32_t* __restrict__ lfv, uint32_t lf) {
   const unsigned FULL = 0xFFFFFFFFu;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
@@ -1430,6 +1434,31 @@ __device__ __forceinline__ void heavy_pull(MPSmem<BLOCK, EPT>& sm, const StepArg
     scanned += T;
     __syncwarp();
   }
+  if (TAIL) {
+    // the light frontier of a pull that ends the buckets early (its vertices
+    // are below the threshold, so the loop above did not take them): whole rows
+    for (uint32_t b0 = (blockIdx.x * (BLOCK / 32) + warp) * 32u; b0 < lf; b0 += W * 32u) {
+      const uint32_t i = b0 + lane;
+      uint32_t v = 0, rs = 0, full = 0;
+      if (i < lf) {
+        v = __ldg(lfv + i);
+        rs = __ldg(fo.ro + v);
+        full = __ldg(fo.ro + v + 1) - rs;
+      }
+      const bool join = full > 0u;
+      const unsigned jb = __ballot_sync(FULL, join);
+      if (jb) {   // warp-uniform
+        if (join) {
+          const uint32_t off = tqn + __popc(jb & lt);
+          tqv[off] = v;
+          tqr[off] = rs;
+          tqd[off] = full;
+        }
+        tqn += __popc(jb);
+        if (tqn > kTailQ - 32) tail_flush();
+      }
+    }
+  }
   if (GG_FAR_Q && fn) far_q_flush(fq, fn, fo);
   if (TAIL && tqn) tail_flush();
 #pragma unroll
@@ -1530,12 +1559,19 @@ __device__ __forceinline__ void superstep_finalize(MPSmem<BLOCK, EPT>& sm, const
       // light edges of the near frontier first; when it is empty, one heavy
       // superstep over the vertices that settled since the last one
       nm = fn > 0 ? MODE_PUSH : MODE_HEAVY;
-      if (nm == MODE_HEAVY && heavy_pull_ok && t_cur != kInf) {
+      // a light frontier of at most n / GG_EARLY_TAIL_DIV vertices may end the
+      // buckets early: if the pull that ends them is due on the current R
+      // list, it runs now and takes the light frontier into the plain push's
+      // first frontier (whole rows), whose pushes do what the bucket's last
+      // light supersteps would
+      const bool early = GG_EARLY_TAIL_DIV != 0 && fn > 0 &&
+                         (unsigned long long)fn * (unsigned long long)GG_EARLY_TAIL_DIV <= a.g.n;
+      if ((nm == MODE_HEAVY || early) && heavy_pull_ok && t_cur != kInf) {
         // pull when R's heavy edges outnumber those still unsettled (plus the
         // cost of the dense pass over the distances)
         const unsigned long long left = heavy_total > heavy_done + rE ? heavy_total - heavy_done - rE : 0ull;
         if (rE > left + a.g.n / 8) {
-          nm = MODE_HEAVY_PULL;
+          if (nm == MODE_HEAVY) nm = MODE_HEAVY_PULL;
           // the split after this pull would end bucketing (the drain rule
           // below, on the heavy edges left once R's are relaxed): the pull
           // writes the plain tail's first frontier itself
@@ -1712,9 +1748,10 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_supers
   if (mode == MODE_SPLIT) {
     far_split(sm, a, fo, dist, a.fr.far[fp], fp ? fc1 : fc0, t_prev);
   } else if (LH && mode == MODE_HEAVY_PULL) {
-    heavy_pull<BLOCK, EPT, PK, false>(sm, a, fo, dist, pick2(a.lb.bm_r, ep & 1u));
+    heavy_pull<BLOCK, EPT, PK, false>(sm, a, fo, dist, pick2(a.lb.bm_r, ep & 1u), nullptr, 0u);
   } else if (LH && mode == MODE_HEAVY_PULL_TAIL) {
-    heavy_pull<BLOCK, EPT, PK, true>(sm, a, fo, dist, pick2(a.lb.bm_r, ep & 1u));
+    // f: the light frontier a pull that ends the buckets early takes along
+    heavy_pull<BLOCK, EPT, PK, true>(sm, a, fo, dist, pick2(a.lb.bm_r, ep & 1u), a.fr.fv[p], f);
   } else if (fw > 0) {
     if (mode == MODE_PUSH || mode == MODE_HEAVY) {
       if (LB == LB_BINS)

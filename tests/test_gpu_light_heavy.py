@@ -226,7 +226,10 @@ def test_heavy_pull_that_ends_bucketing_writes_the_tail_frontier():
     """From an RMAT hub the dense core settles in the first bucket; once its
     heavy pull leaves fewer than m / 8 heavy edges unsettled, that pull ends
     bucketing itself (kind 5): its next frontier is every unsettled vertex
-    with a finite distance, and only plain pushes follow (no split)."""
+    with a finite distance, and only plain pushes follow (no split).  It runs
+    as soon as the bucket's light frontier is small (at most n / 256
+    vertices), taking that frontier along."""
+    early = 0
     for name in ("rmat18", "rmat20"):
         ro, col, w, src = graphgen.workload(name)
         g = gg().Graph(ro, col, w, symmetric=True)
@@ -247,7 +250,9 @@ def test_heavy_pull_that_ends_bucketing_writes_the_tail_frontier():
             assert rest.size > 0 and (rest == 0).all(), kinds
             assert tr[k5[0], 3] > 0 and tr[k5[0] + 1, 0] == tr[k5[0], 3]
             assert st.device_status == 0
+            early += int(k5[0] > 0 and tr[k5[0] - 1, 3] > 0)   # a light frontier was still left
         g.close()
+    assert early > 0
 
 
 def test_bad_light_heavy_value_is_rejected():

@@ -12,7 +12,10 @@ buckets:
   becomes infinite, and the rest of the run is plain push over all edges;
 - when a heavy pull is what brings them below that share, the pull itself
   ends bucketing: every unsettled vertex with a finite distance forms the
-  plain push's first frontier, and no split follows.
+  plain push's first frontier, and no split follows;
+- that pull may run before the bucket's light frontier empties, once the
+  frontier holds at most n / 256 vertices: the frontier joins the plain push's
+  first frontier with whole rows.
 
 This model takes the same decisions superstep by superstep (synchronous
 relaxation within a superstep, which reaches the same fixed point as the
@@ -32,10 +35,13 @@ INF32 = 0xFFFFFFFF
 LIGHT, SPLIT, HEAVY_PUSH, HEAVY_PULL, HEAVY_PULL_TAIL = 0, 2, 3, 4, 5
 
 
-def schedule(ro, col, w, src, delta, symmetric, drain_div=8, tail=True, lh=True, pull_tail=True):
+def schedule(ro, col, w, src, delta, symmetric, drain_div=8, tail=True, lh=True, pull_tail=True, early_div=256):
     """Distances (uint32, INF32 = unreached) and the kind of every superstep.
     lh=False is the plain near-far loop (every edge light, no drain rule);
-    pull_tail=False keeps the split after a heavy pull that ends bucketing."""
+    pull_tail=False keeps the split after a heavy pull that ends bucketing;
+    early_div: a light frontier of at most n / early_div vertices lets that
+    pull run at once (0: never), taking the light frontier into the plain
+    push's first frontier."""
     ro = np.asarray(ro, np.int64)
     n, m = ro.size - 1, len(col)
     deg = np.diff(ro)
@@ -85,7 +91,13 @@ def schedule(ro, col, w, src, delta, symmetric, drain_div=8, tail=True, lh=True,
         return near[ldeg[near] > 0]
 
     while True:
-        if F.size and bucketed:
+        early = bool(bucketed and early_div and F.size and F.size * early_div <= n and R.any())
+        if early:   # the pull that ends the buckets, due now on the current R list
+            rE = int(hdeg[np.flatnonzero(R)].sum())
+            left = max(heavy_total - heavy_done - rE, 0)
+            early = (symmetric and t_cur < BIG and rE > left + n // 8 and pull_tail and tail
+                     and left * drain_div < m)
+        if F.size and bucketed and not early:
             kinds.append(LIGHT)
             F = near_far(push(F, ro[:-1], lend), R)
         elif bucketed and R.any():
@@ -96,6 +108,7 @@ def schedule(ro, col, w, src, delta, symmetric, drain_div=8, tail=True, lh=True,
             if symmetric and t_cur < BIG and rE > left + n // 8:
                 ends = pull_tail and tail and left * drain_div < m
                 kinds.append(HEAVY_PULL_TAIL if ends else HEAVY_PULL)
+                F_light = F   # non-empty only when the buckets end early
                 # every unsettled vertex takes the minimum over its heavy edges
                 # from settled vertices (symmetric: in-edges = out-edges)
                 un = np.flatnonzero(dist >= t_cur)
@@ -121,7 +134,8 @@ def schedule(ro, col, w, src, delta, symmetric, drain_div=8, tail=True, lh=True,
                     far[:] = False
                     t_prev, t_cur = t_cur, BIG
                     bucketed = False
-                    F = fv[deg[fv] > 0]
+                    # and the light frontier of an early end, with whole rows
+                    F = np.union1d(fv[deg[fv] > 0], F_light[deg[F_light] > 0])
             else:
                 kinds.append(HEAVY_PUSH)
                 F = near_far(push(Rv, lend, ro[1:]), R_next)
@@ -220,13 +234,14 @@ def test_plain_tail_removes_supersteps_not_distances():
 
 @pytest.mark.parametrize("scale,seed,delta", [(12, 1, 20), (13, 3, 20), (14, 5, 12)])
 def test_pull_that_ends_bucketing_replaces_the_split(scale, seed, delta):
+    # (early_div=0: the pull comes where the bucket's light frontier empties)
     # the pull after which the drain rule holds writes the plain frontier
     # itself: the same distances, one superstep (the split) fewer, and the
     # first plain push works on the vertices the split would have moved
     ro, col, w = graphgen.rmat(scale, 16, seed=seed, W=255)
     hub = graphgen.max_degree_vertex(ro)
-    got_p, kinds_p = schedule(ro, col, w, hub, delta, symmetric=True)
-    got_s, kinds_s = schedule(ro, col, w, hub, delta, symmetric=True, pull_tail=False)
+    got_p, kinds_p = schedule(ro, col, w, hub, delta, symmetric=True, early_div=0)
+    got_s, kinds_s = schedule(ro, col, w, hub, delta, symmetric=True, pull_tail=False, early_div=0)
     np.testing.assert_array_equal(got_p, oracle.dijkstra(ro, col, w, hub))
     np.testing.assert_array_equal(got_s, got_p)
     k = np.flatnonzero(kinds_p == HEAVY_PULL_TAIL)
@@ -258,3 +273,44 @@ def test_plain_near_far_schedule_matches_oracle(graph):
         np.testing.assert_array_equal(got, oracle.dijkstra(ro, col, w, s), err_msg=f"{graph} src={s} delta={delta}")
         assert not np.isin(kinds, (HEAVY_PUSH, HEAVY_PULL, HEAVY_PULL_TAIL)).any()
     assert SPLIT in kinds   # the far pile was used
+
+
+@pytest.mark.parametrize("scale,seed,delta", [(12, 1, 20), (13, 3, 20), (14, 5, 12), (14, 7, 16)])
+@pytest.mark.parametrize("early_div", [4, 16, 64])
+def test_early_end_of_the_buckets_keeps_the_distances(scale, seed, delta, early_div):
+    # a small light frontier lets the pull that ends the buckets run at once:
+    # the frontier's vertices (distances not final yet) go into the plain
+    # push's first frontier with their whole rows, and plain pushes finish
+    # what the bucket's last light supersteps would have done
+    ro, col, w = graphgen.rmat(scale, 16, seed=seed, W=255)
+    hub = graphgen.max_degree_vertex(ro)
+    ref = oracle.dijkstra(ro, col, w, hub)
+    got_e, kinds_e = schedule(ro, col, w, hub, delta, symmetric=True, early_div=early_div)
+    got_l, kinds_l = schedule(ro, col, w, hub, delta, symmetric=True, early_div=0)
+    np.testing.assert_array_equal(got_e, ref)
+    np.testing.assert_array_equal(got_l, ref)
+    k_e, k_l = np.flatnonzero(kinds_e == HEAVY_PULL_TAIL), np.flatnonzero(kinds_l == HEAVY_PULL_TAIL)
+    assert k_e.size == 1 and k_l.size == 1
+    assert (kinds_e[k_e[0] + 1:] == LIGHT).all()
+    assert k_e[0] < k_l[0]            # the buckets ended before their light frontier emptied
+    assert len(kinds_e) < len(kinds_l)
+
+
+def test_early_end_planted_mistake_is_caught():
+    # dropping the light frontier at an early end (instead of carrying it into
+    # the plain push) leaves distances too large: the oracle comparison sees it
+    ro, col, w = graphgen.rmat(14, 16, seed=5, W=255)
+    hub = graphgen.max_degree_vertex(ro)
+    src = open(__file__).read()
+    assert "F_light[deg[F_light] > 0]" in src
+    ns = {}
+    bad = src.replace("np.union1d(fv[deg[fv] > 0], F_light[deg[F_light] > 0])", "fv[deg[fv] > 0]")
+    exec(compile(bad, __file__, "exec"), ns)
+    ref = oracle.dijkstra(ro, col, w, hub)
+    found = False
+    for early_div in (4, 16, 64):
+        got, kinds = ns["schedule"](ro, col, w, hub, 12, symmetric=True, early_div=early_div)
+        early = HEAVY_PULL_TAIL in kinds.tolist()
+        if early and not np.array_equal(got, ref):
+            found = True
+    assert found
