@@ -397,16 +397,28 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
       kqn = 0;
       __syncwarp();
     };
-    for (uint32_t i = blockIdx.x * kBNW + warp; i < nfar; i += gridDim.x * kBNW) {   // warp-uniform
-      const uint32_t v = pick2(w.far_v, fsel)[i];
-      const unsigned long long bits = w.fmask[v];
+    // the next far vertex and its parked bits are read while this one is worked on
+    const uint32_t* far_in = pick2(w.far_v, fsel);
+    const uint32_t wstride = gridDim.x * kBNW;
+    uint32_t nv = 0, ni = blockIdx.x * kBNW + warp;
+    unsigned long long nbits = 0ull;
+    if (ni < nfar) {
+      nv = far_in[ni];
+      nbits = w.fmask[nv];
+    }
+    for (uint32_t i = blockIdx.x * kBNW + warp; i < nfar; i += wstride) {   // warp-uniform
+      const uint32_t v = nv;
+      const unsigned long long bits = nbits;
       const uint32_t* vrow = dist + (size_t)v * K + col0;
       const bool lo = (bits >> lane) & 1ull, hi = (bits >> (lane + 32)) & 1ull;
       const uint32_t dlo = lo ? ld_cg(vrow + lane) : 0u, dhi = hi ? ld_cg(vrow + lane + 32) : 0u;
+      ni = i + wstride;
+      if (ni < nfar) nv = far_in[ni];
       const bool mlo = lo && dlo >= tp_lo && dlo < tc_lo, mhi = hi && dhi >= tp_hi && dhi < tc_hi;
       const bool klo = lo && dlo >= tc_lo, khi = hi && dhi >= tc_hi;
       const unsigned nb_lo = __ballot_sync(FULL, mlo), nb_hi = __ballot_sync(FULL, mhi);
       const unsigned kb_lo = __ballot_sync(FULL, klo), kb_hi = __ballot_sync(FULL, khi);
+      if (ni < nfar) nbits = w.fmask[nv];   // far-list entries are distinct: not this vertex's word
       // smallest shifted distance left parked (one atomic per warp at the end)
       if (klo) wfm = min(wfm, (uint32_t)min(0xFFFFFFFFull, (unsigned long long)dlo + sh_lo));
       if (khi) wfm = min(wfm, (uint32_t)min(0xFFFFFFFFull, (unsigned long long)dhi + sh_hi));
