@@ -933,7 +933,9 @@ __device__ __forceinline__ void warp_advance(MPSmem<BLOCK, EPT>& sm, const StepA
         wr = R[idx];
         const uint32_t v = V[idx];
         wd = ld_cg(dist + v);
-        bm_cur[v >> 5] = 0u;   // the current bitmap is not read in push: clear as we go
+        // the current bitmap is not read in push: clear as we go (null: the
+        // next superstep's prologue clears it whole, as in light/heavy runs)
+        if (bm_cur != nullptr) bm_cur[v >> 5] = 0u;
       }
       wend = j + 32 < F ? S[j + 32] : Etot;   // first coordinate past the window
     };
@@ -1761,7 +1763,7 @@ __global__ void __launch_bounds__(BLOCK, superstep_min_blocks(LB, EPT)) k_supers
         warp_advance<BLOCK, EPT, PK>(sm, a, fw, Ew, fS, fR, fV, edges, dist, bm_cur, fo);   // pointer selects out
       else if (LB == LB_WARP || LB == LB_LOCAL)                                              // of the loop
         warp_advance<BLOCK, EPT, PK, LB == LB_LOCAL>(sm, a, f, E, a.fr.fs[p], a.fr.fr[p], a.fr.fv[p], edges, dist,
-                                                     a.fr.bm[it % 3], fo);
+                                                     LH ? nullptr : a.fr.bm[it % 3], fo);
       else
         mp_advance<BLOCK, EPT, false, PK>(sm, a, fw, Ew, fS, fR, fV, edges, dist, bm_cur, fo);
     } else {
