@@ -113,6 +113,9 @@ static_assert(kBNW * kBQW <= (uint32_t)kBCap, "per-warp queues fit the CTA queue
 #ifndef GG_NB_DRAIN
 #define GG_NB_DRAIN 8   // normalised buckets end once the unsettled pairs hold < 1/GG_NB_DRAIN of the heavy edges
 #endif
+#ifndef GG_BATCH_PULL_TAIL
+#define GG_BATCH_PULL_TAIL 1   // normalised buckets: a pull after which the buckets end writes the tail's frontier
+#endif
 #ifndef GG_BATCH_PULL
 #define GG_BATCH_PULL 1   // normalised buckets: heavy supersteps by pull on symmetric graphs
 #endif
@@ -214,7 +217,10 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
   const uint32_t pc = it % 3, pn = (it + 1) % 3, po = (it + 2) % 3;
   const uint32_t bmode0 = ctl->mode;
   const uint32_t ep = LH ? ctl->epoch : 0u;
-  const bool pull = LH && bmode0 == 4u;   // heavy superstep by pull (normalised buckets)
+  // heavy superstep by pull (normalised buckets); mode 5: a pull after which
+  // the buckets end, which writes the tail's first frontier itself
+  const bool pull = LH && (bmode0 == 4u || bmode0 == 5u);
+  const bool pull_tail = LH && bmode0 == 5u;
   const bool heavy = LH && (bmode0 == 2u || pull);
   const unsigned long long c = heavy ? ctl->rcnt[ep % 3] : ctl->cnt[pc];
   const uint32_t F = (uint32_t)(c >> 32), E = (uint32_t)c;
@@ -280,6 +286,27 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
     uint32_t fqn = 0;   // warp-uniform
     uint32_t wfm = kInf;
     unsigned long long scanned = 0ull;
+    // pull_tail: the tail's frontier queue (vertices with whole rows)
+    uint32_t* tq = sm.qv + warp * kBQW;
+    uint32_t tqn = 0;   // warp-uniform
+    unsigned long long* Mn_t = pick3(w.mask, pn);
+    auto tflush = [&]() {
+      __syncwarp();
+      for (uint32_t j0 = 0; j0 < tqn; j0 += 32)
+        b_append32(j0 + lane < tqn, j0 + lane < tqn ? tq[j0 + lane] : 0u, g.ro, g.ro + 1, &ctl->cnt[pn],
+                   pick3(w.fv, pn), pick3(w.fr, pn), pick3(w.fs, pn));
+      tqn = 0;
+      __syncwarp();
+    };
+    if (pull_tail) {
+      // the other two frontier mask arrays are cleared whole (a vertex
+      // without light edges may hold bits no list carries); the next
+      // frontier's mask is written for every vertex below
+      for (uint32_t i = blockIdx.x * kBB + tid; i < g.n; i += gridDim.x * kBB) {
+        pick3(w.mask, pc)[i] = 0ull;
+        pick3(w.mask, po)[i] = 0ull;
+      }
+    }
     auto ffl = [&]() {
       __syncwarp();
       uint32_t pos = 0;
@@ -292,11 +319,21 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
     const uint32_t nwarps = gridDim.x * kBNW;
     for (uint32_t v = blockIdx.x * kBNW + warp; v < g.n; v += nwarps) {   // warp-uniform
       const uint32_t hs = __ldg(w.lend + v), he = __ldg(g.ro + v + 1);
-      if (hs >= he) continue;
+      if (pull_tail) {
+        if (__ldg(g.ro + v) >= he) {   // no edges: nothing to expand
+          if (lane == 0) Mn_t[v] = 0ull;
+          continue;
+        }
+      } else if (hs >= he) {
+        continue;
+      }
       uint32_t* vrow = dist + (size_t)v * K + col0;
       const uint32_t dlo = vlo ? ld_cg(vrow + lane) : 0u, dhi = vhi ? ld_cg(vrow + lane + 32) : 0u;
       const unsigned Ulo = __ballot_sync(FULL, vlo && dlo >= tc_lo), Uhi = __ballot_sync(FULL, vhi && dhi >= tc_hi);
-      if ((Ulo | Uhi) == 0u) continue;
+      if ((Ulo | Uhi) == 0u) {
+        if (pull_tail && lane == 0) Mn_t[v] = 0ull;
+        continue;
+      }
       const unsigned long long U = ((unsigned long long)Uhi << 32) | Ulo;
       scanned += he - hs;
       uint32_t clo = dlo, chi = dhi;
@@ -344,6 +381,20 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
         vrow[lane + 32] = chi;
         wfm = min(wfm, (uint32_t)min(0xFFFFFFFFull, (unsigned long long)chi + sh_hi));
       }
+      if (pull_tail) {
+        // the tail's first frontier: every pair not settled (at or above the
+        // threshold) with a finite distance (the pairs a split would release
+        // from the far masks), with whole rows
+        const unsigned Tl = __ballot_sync(FULL, vlo && clo >= tc_lo && clo != kInf);
+        const unsigned Th = __ballot_sync(FULL, vhi && chi >= tc_hi && chi != kInf);
+        const unsigned long long tb = ((unsigned long long)Th << 32) | Tl;
+        if (lane == 0) Mn_t[v] = tb;
+        if (tb) {
+          if (lane == 0) tq[tqn] = v;
+          if (++tqn == kBQW) tflush();
+        }
+        continue;
+      }
       const unsigned Il = __ballot_sync(FULL, il), Ih = __ballot_sync(FULL, ih);
       if (Il | Ih) {   // park the improved pairs
         bool fapp = false;
@@ -355,9 +406,10 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
       }
     }
     if (fqn) ffl();
+    if (tqn) tflush();
 #pragma unroll
     for (int o = 16; o; o >>= 1) wfm = min(wfm, __shfl_xor_sync(FULL, wfm, o));
-    if (lane == 0 && wfm != kInf) atomicMin(&sm.fmin, wfm);
+    if (lane == 0 && wfm != kInf && !pull_tail) atomicMin(&sm.fmin, wfm);
     if (lane == 0 && scanned) atomicAdd(&sm.pedges, scanned);
   } else if (bmode == 3) {
     // before the tail's split: clear the three frontier mask arrays.  A vertex
@@ -857,9 +909,22 @@ __global__ void __launch_bounds__(kBB, GG_BMINB) k_batch_superstep(DevGraph g, B
           const unsigned long long hk = ctl->heavy_total_k;
           const unsigned long long open = hk > done ? hk - done : 0ull;
           if (ctl->pull_ok && done - ctl->settled_mark > open) mode_next = 4u;
+          // a pull settles no pair, so the drain rule holds after it exactly
+          // when it holds now: the split after it would end the buckets, so
+          // the pull writes the tail's first frontier itself
+          if (mode_next == 4u && GG_BATCH_PULL_TAIL && open < hk / ctl->drain_div) mode_next = 5u;
           ctl->settled_mark = done;
         }
-        if (bmode == 3) {   // masks cleared: the tail's split follows
+        if (bmode0 == 5u) {   // the pull ended the buckets: plain push from its frontier on
+          ctl->tail = 1u;
+          ctl->t_prev = ctl->t_cur;
+          ctl->t_cur = kInf;
+          ctl->far_min = kInf;
+          ctl->fcnt[0] = 0u;
+          ctl->fcnt[1] = 0u;
+          mode_next = 0u;
+          more = fn != 0;
+        } else if (bmode == 3) {   // masks cleared: the tail's split follows
           mode_next = 1u;
           more = true;
         } else if (!more && nfar > 0) {

@@ -14,7 +14,10 @@ when no near pair and no R pair is left, T rises to max(T + width, smallest
 parked shifted distance + 1) and a split moves the parked pairs below it into
 the frontier; once the pairs not yet settled hold fewer than 1/drain of the
 heavy edges (counted per pair when it first joins an R mask), T becomes
-infinite and the rest is plain push over all edges.
+infinite and the rest is plain push over all edges.  When the heavy
+superstep before that split is a pull, the pull itself starts the plain
+push (the kernel's default): every pair not settled with a finite distance
+forms the tail's first frontier, and no split follows.
 
 The models take these steps in this order (synchronous relaxation per
 superstep) and must reach the oracle's distances for every source, whatever
@@ -85,13 +88,18 @@ def rounds(ro, col, w, srcs, delta):
     return np.where(dist >= BIG, INF32, dist).astype(np.uint32), light, heavy
 
 
-def normalised_buckets(ro, col, w, srcs, delta, offs, width=None, drain=8, mistake=None, pull=False):
+def normalised_buckets(ro, col, w, srcs, delta, offs, width=None, drain=8, mistake=None, pull=False,
+                       pull_tail=False):
     """(k, n) distances, supersteps and splits of the normalised-bucket
     schedule.  mistake (for the pin-strength test only) plants one error:
     "split_floor" drops the pairs at exactly the previous threshold,
     "split_no_r" leaves the pairs a split releases out of the R mask,
-    "tail_light" gives the tail light rows only.  pull: heavy supersteps
-    update only the pairs not yet settled (as the kernel's pull does)."""
+    "tail_light" gives the tail light rows only, "pull_tail_parked" gives the
+    tail only the pairs the ending pull improved.  pull: heavy supersteps
+    update only the pairs not yet settled (as the kernel's pull does).
+    pull_tail: a pull after which the drain rule holds ends the buckets
+    itself (no split): every pair not settled with a finite distance starts
+    the tail."""
     ro = np.asarray(ro, np.int64)
     n, k = ro.size - 1, len(srcs)
     width = delta if width is None else width
@@ -192,6 +200,16 @@ def normalised_buckets(ro, col, w, srcs, delta, offs, width=None, drain=8, mista
                 imp = relax(R, lend, ro[1:])
                 dist[:] = np.where(open_, dist, keep)
                 imp &= open_
+                # a pull settles no pair: the drain rule after it is decided now
+                if pull_tail and not tail and heavy_k - settled < heavy_k // drain:
+                    if mistake == "pull_tail_parked":
+                        F = imp & (deg > 0)
+                    else:
+                        F = open_ & (dist < BIG) & (deg > 0)
+                    R = np.zeros((k, n), bool)
+                    far = np.zeros((k, n), bool)
+                    tail, tprev, T = True, T, BIG
+                    continue
             else:
                 imp = relax(R, lend, ro[1:])
             R = np.zeros((k, n), bool)
@@ -282,3 +300,34 @@ def test_normalised_buckets_planted_mistakes_fail(mistake):
     np.testing.assert_array_equal(got, ref)
     bad, _, _ = normalised_buckets(ro, col, w, srcs, 12, offs, mistake=mistake)
     assert not np.array_equal(bad, ref)
+
+
+@pytest.mark.parametrize("scale,delta,k", [(10, 12, 16), (11, 14, 9), (12, 12, 24)])
+def test_pull_that_ends_the_buckets_replaces_mask_clear_and_split(scale, delta, k):
+    # the pull after which the drain rule holds starts the tail itself: the same
+    # distances as the split after the pull, in fewer supersteps and one split fewer
+    ro, col, w = graphgen.rmat(scale, 16, seed=scale, W=255)
+    hub = graphgen.max_degree_vertex(ro)
+    srcs = graphgen.sample_sources(ro, k, seed=3)
+    offs = oracle.dijkstra(ro, col, w, hub)[srcs]
+    ref = oracle.dijkstra_many(ro, col, w, srcs)
+    got_t, steps_t, splits_t = normalised_buckets(ro, col, w, srcs, delta, offs, pull=True, pull_tail=True)
+    got_s, steps_s, splits_s = normalised_buckets(ro, col, w, srcs, delta, offs, pull=True)
+    np.testing.assert_array_equal(got_t, ref)
+    np.testing.assert_array_equal(got_s, ref)
+    assert splits_t < splits_s and steps_t < steps_s
+
+
+def test_pull_that_ends_the_buckets_planted_mistake_fails():
+    # starting the tail from only the pairs the pull improved (dropping the
+    # pairs parked earlier) must be caught by the oracle comparison
+    caught = False
+    for scale, delta, k in ((10, 12, 16), (11, 14, 9), (12, 12, 24)):
+        ro, col, w = graphgen.rmat(scale, 16, seed=scale, W=255)
+        hub = graphgen.max_degree_vertex(ro)
+        srcs = graphgen.sample_sources(ro, k, seed=3)
+        offs = oracle.dijkstra(ro, col, w, hub)[srcs]
+        got, _, _ = normalised_buckets(ro, col, w, srcs, delta, offs, pull=True, pull_tail=True,
+                                       mistake="pull_tail_parked")
+        caught |= not np.array_equal(got, oracle.dijkstra_many(ro, col, w, srcs))
+    assert caught
