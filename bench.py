@@ -387,7 +387,7 @@ def run_batched(gg, torch, k=64, seed=1, scale=22, policy="graph", cpu_sample=Tr
     g.check()
     if trace_file:
         np.savetxt(trace_file, trace.cpu().numpy().reshape(-1, 4)[:min(st.iterations, 65536)], fmt="%d",
-                   header="kind (0 light, 1 split, 2 heavy push, 3 mask clear, 4 heavy pull; +16 after bucketing) "
+                   header="kind (0 light, 1 split, 2 heavy push, 3 mask clear, 4 heavy pull, 5 heavy pull that ends the buckets; +16 after bucketing) "
                           "entries edges next_frontier")
     rec = golden().get(f"rmat{scale}_batch{k}")
     verified = None

@@ -346,10 +346,12 @@ gg_status gg_sssp_batch(gg_graph_t g, const uint32_t* srcs, uint32_t k, uint32_t
 /* As gg_sssp_batch with options: max_iterations, stats (summed over the
  * 64-source groups; setting stats synchronises the stream), trace (first
  * 64-source group only: per superstep kind | 16 once bucketing has ended
- * (kind 0 light or plain push, 1 split, 2 heavy, 3 mask clear before the
- * tail), entries, edges, next frontier size), delta, light_heavy and the
- * policy GG_POLICY_BSP_HOST (supersteps launched one by one from the host,
- * synchronising after each; every other policy runs the CUDA-graph loop);
+ * (kind 0 light or plain push, 1 split, 2 heavy push, 3 mask clear before
+ * the tail, 4 heavy pull, 5 heavy pull that ends the buckets and writes the
+ * tail's first frontier), entries, edges, next frontier size), delta,
+ * light_heavy and the policy GG_POLICY_BSP_HOST (supersteps launched one by
+ * one from the host, synchronising after each; every other policy runs the
+ * CUDA-graph loop);
  * direction and load-balance fields are ignored.
  *
  * On graphs with a light/heavy width (mean degree >= 8, integer weights),
