@@ -164,3 +164,29 @@ def test_batch_directed_graph_normalised_buckets():
     got, _ = run_batch(g, srcs)
     np.testing.assert_array_equal(got.T, oracle.dijkstra_many(ro, col, w, srcs, threads=8))
     g.close()
+
+
+@pytest.mark.parametrize("name,k,policy", [("rmat16", 64, 0), ("rmat16", 40, 2), ("rmat18", 64, 0)])
+def test_batch_pull_that_ends_the_buckets(name, k, policy):
+    """On a skewed symmetric graph the dense bucket's heavy superstep pulls,
+    and the drain rule then holds: that pull (trace kind 5) starts the plain
+    push itself, so only tail pushes (kind 16) follow, with no mask clear and
+    no split; every column equals the oracle."""
+    ro, col, w, _ = graphgen.workload(name)
+    srcs = graphgen.sample_sources(ro, k, seed=29)
+    g = gg().Graph(ro, col, w, symmetric=True)
+    m = gg()
+    trace = torch.zeros(4 * 4096, dtype=torch.uint32, device="cuda")
+    st = m.gg_stats()
+    d = g.sssp_batch(srcs, stats=st, policy=policy, trace=trace, trace_cap=4096)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(d.cpu().numpy().T, oracle.dijkstra_many(ro, col, w, srcs, threads=8))
+    assert st.device_status == 0
+    tr = trace.cpu().numpy().reshape(-1, 4)[:st.iterations]
+    kinds = tr[:, 0]
+    k5 = np.flatnonzero(kinds == 5)
+    assert k5.size == 1, kinds
+    rest = kinds[k5[0] + 1:]
+    assert rest.size > 0 and (rest == 16).all(), kinds
+    assert tr[k5[0], 3] > 0 and tr[k5[0] + 1, 1] == tr[k5[0], 3]   # its frontier feeds the first tail push
+    g.close()
